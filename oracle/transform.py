@@ -38,8 +38,15 @@ left triangle (k, l, p), right triangle (l, k, q):
   coarse faces meeting at the corner with the minimum-norm circulation, which
   gives (s_k - s_l)/2 per corner with s_k = A_{k,m_lp} c_{m_lp},
   s_l = A_{l,m_kp} c_{m_kp}.  Then sum_{e at k} R_F0 = A_k^j c_k + sum_m A_km c_m.
-  The x fluxes of Eq. (restr_flux) are taken as zero: Sec. 4.2 notes that the
-  commutation holds whatever interpolation gives them.
+  The x fluxes of Eq. (restr_flux) (reading): at each coarse corner the three
+  fine hexagons of the edge midpoints meet at the circumcentre W of the central
+  fine triangle, not at the coarse vertex V.  The fine-face construction above
+  measures the flux up to W; the flux through the short segment V -> W,
+  x_T = G.((W - V) x V) with G the flux vector fitted (least squares) to the
+  three fine faces meeting at W, is taken off.  For each coarse triangle it is a
+  circulation around the corner (-x_T on each coarse face oriented
+  counter-clockwise around T), so, as Sec. 4.2 notes, the commutation holds
+  whatever value it has; it makes R_F exact for uniform flows.
   R'_F: Eq. (ho_flux) is read as the corrective flux through the single coarse
   face k -> l_{2j} (the outer sum adds the faces of cell k), with
   (kml) = A_km A_lm / A_m (c_k - c_l), Eq. (kml).
@@ -253,6 +260,8 @@ class FluxStencils:
             return third(t, a, b)
 
         mid = Hy.mid[j - 1]
+        self.tl, self.tr = tp, tq
+        self._corner_geometry(Hy, j)
         self.k, self.l, self.p, self.q = k, l, p, q
         self.m = mid[np.arange(E)]
         self.m_kp, self.m_lp = mid[cedge(k, p)], mid[cedge(l, p)]
@@ -271,6 +280,51 @@ class FluxStencils:
         self.ring_nodes = F.nbr_nodes[self.m]
         self.ring_edges = F.nbr_edges[self.m]
         self.ring_sign = F.nbr_sign[self.m]
+
+    def _corner_geometry(self, Hy, j):
+        """Per coarse triangle: the three fine edges of its central fine triangle,
+        their unit tangents in the tangent plane at the coarse vertex V, and the
+        rotated segment (W - V) x V (m) used by x_T."""
+        C, F = Hy.levels[j - 1], Hy.levels[j]
+        mid = Hy.mid[j - 1]
+        te = C.tri_edges
+        cm = mid[te]                                    # (T, 3) midpoint nodes of the sides
+        fkey = F.edges[:, 0] * F.N + F.edges[:, 1]
+        forder = np.argsort(fkey)
+
+        def fine_edge(a, b):
+            kk = np.minimum(a, b) * F.N + np.maximum(a, b)
+            idx = forder[np.searchsorted(fkey[forder], kk)]
+            assert np.array_equal(fkey[idx], kk)
+            return idx
+
+        self.cen_edges = np.stack([fine_edge(cm[:, c], cm[:, (c + 1) % 3]) for c in range(3)], axis=1)
+        # central fine triangle = the one holding the three midpoints
+        t = F.left[self.cen_edges[:, 0]]
+        t = np.where(np.isin(F.tri[t], cm).all(axis=1), t, F.right[self.cen_edges[:, 0]])
+        assert np.sort(F.tri[t], axis=1).tolist() == np.sort(cm, axis=1).tolist()
+        V = C.cc
+        W = F.cc[t]
+        e1, e2 = _local_basis(V)
+        ft = F.edge_tangents()[self.cen_edges]          # (T, 3, 3)
+        self.cen_t1 = np.einsum("tck,tk->tc", ft, e1)
+        self.cen_t2 = np.einsum("tck,tk->tc", ft, e2)
+        seg = np.cross(W - V, V) * C.radius
+        self.seg1 = np.sum(seg * e1, axis=1)
+        self.seg2 = np.sum(seg * e2, axis=1)
+
+    def corner_flux(self, Ff):
+        """x_T for every coarse triangle from fine fluxes per unit length."""
+        f = Ff[self.cen_edges]
+        a11 = np.sum(self.cen_t1 ** 2, 1)
+        a12 = np.sum(self.cen_t1 * self.cen_t2, 1)
+        a22 = np.sum(self.cen_t2 ** 2, 1)
+        b1 = np.sum(self.cen_t1 * f, 1)
+        b2 = np.sum(self.cen_t2 * f, 1)
+        det = a11 * a22 - a12 * a12
+        g1 = (a22 * b1 - a12 * b2) / det
+        g2 = (a11 * b2 - a12 * b1) / det
+        return g1 * self.seg1 + g2 * self.seg2
 
     def overlap(self, y, x):
         r = x - self._n0
@@ -306,4 +360,5 @@ def restrict_flux(FS, Ff, lf, c):
     corr = kml(k, m, l) + kml(k, FS.m_kp, l) + kml(k, FS.m_kq, l) + kml(k, FS.m_lp, l) + kml(k, FS.m_lq, l) \
         + 0.5 * kml(k, FS.m_lp, FS.pp1) + 0.5 * kml(k, FS.m_lq, FS.qq1) \
         + 0.5 * kml(FS.pp2, FS.m_kp, l) + 0.5 * kml(FS.qq2, FS.m_kq, l)
-    return F1 + corner + corr
+    xT = FS.corner_flux(Ff)
+    return F1 + corner + corr - xT[FS.tl] + xT[FS.tr]

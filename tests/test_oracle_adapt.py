@@ -1,0 +1,217 @@
+"""Pins for the oracle's adapted grid and adaptive step (Sec. 2.3, Sec. 3.1).
+
+* the mask equals a literal set construction written with Python sets and
+  loops (one rule at a time, as the rules are stated);
+* the ghost band equals breadth-first distances;
+* mass is conserved to roundoff over adaptive steps (Sec. 4.1, Eq. divRcommute);
+* trends at covered coarse nodes are the restriction of the fine trends;
+* the adapted solution tracks the uniform fine solution with an error that
+  shrinks with eps (error control, Sec. 6.2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import adapt, grid, model, transform
+
+
+def brute_mask(Hy, sig_sets):
+    """Rules of Sec. 2.3 / 3.1 applied literally with sets of node ids."""
+    jmin, jmax = Hy.jmin, Hy.jmax
+    nbrs = {j: [set(int(x) for x in Hy.levels[j].nbr_nodes[i] if x >= 0) for i in range(Hy.levels[j].N)]
+            for j in range(jmin, jmax + 1)}
+    T = {j: set() for j in range(jmin, jmax + 1)}
+    for j in range(jmin + 1, jmax + 1):
+        for x in sig_sets[j]:
+            T[j].add(x)
+            T[j] |= nbrs[j][x]                                 # adjacent in space
+            if j + 1 <= jmax:
+                T[j + 1].add(x)                                # adjacent in scale: same place
+                T[j + 1] |= nbrs[j + 1][x]                     # and its fine neighbours
+    for j in range(jmax, jmin, -1):
+        n0 = Hy.levels[j - 1].N
+        for x in list(T[j]):
+            if x >= n0:
+                T[j] |= set(int(k) for k in Hy.K[j][x - n0])    # prediction parents
+        if j - 1 > jmin:
+            for x in T[j]:
+                if x < n0:
+                    T[j - 1].add(x)                            # coarse node of a live even node
+    return T
+
+
+def test_mask_matches_literal_rules():
+    Hy = grid.Hierarchy(2, 4)
+    rng = np.random.default_rng(0)
+    sig = {}
+    sig_sets = {}
+    for j in range(3, 5):
+        N = Hy.levels[j].N
+        s = rng.random(N) < 0.02
+        sig[j] = s
+        sig_sets[j] = set(np.nonzero(s)[0].tolist())
+    live_n, live_e = adapt.build_mask(Hy, sig)
+    T = brute_mask(Hy, sig_sets)
+    for j in range(3, 5):
+        assert set(np.nonzero(live_n[j])[0].tolist()) == T[j]
+        L = Hy.levels[j]
+        for e in range(L.E):
+            a, b = L.edges[e]
+            assert live_e[j][e] == (a in T[j] or b in T[j])
+    assert live_n[2].all()
+
+
+def test_ghost_band_is_bfs_distance():
+    Hy = grid.Hierarchy(2, 4)
+    rng = np.random.default_rng(1)
+    live = {2: np.ones(Hy.levels[2].N, bool)}
+    live_e = {}
+    for j in (3, 4):
+        live[j] = rng.random(Hy.levels[j].N) < 0.01
+    for j in (2, 3, 4):
+        live_e[j] = adapt.edges_touching(Hy.levels[j], live[j])
+    gn, ge = adapt.ghost_band(Hy, live, live_e)
+    L = Hy.levels[4]
+    dist = np.full(L.N, 99)
+    frontier = list(np.nonzero(live[4])[0])
+    dist[frontier] = 0
+    d = 0
+    while frontier and d < adapt.GHOST_HOPS:
+        d += 1
+        nxt = []
+        for x in frontier:
+            for y in L.nbr_nodes[x]:
+                if y >= 0 and dist[y] > d:
+                    dist[y] = d
+                    nxt.append(y)
+        frontier = nxt
+    assert np.array_equal(gn[4], (dist >= 1) & (dist <= adapt.GHOST_HOPS))
+
+
+def make_model(jmin=2, jmax=4, kind="jet", eps=1e-2, seed=0, rk="rk4"):
+    Hy = grid.Hierarchy(jmin, jmax)
+    M = model.Model(Hy, eps=eps, rk=rk)
+    W = workloads.Workload(kind, seed=seed)
+    L = Hy.levels[jmax]
+    dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    M.set_uniform(dh, u)
+    M.adapt()
+    return M
+
+
+@pytest.mark.parametrize("rk", ["rk4", "ssp43"])
+def test_adaptive_mass_conserved(rk):
+    M = make_model(rk=rk)
+    assert 0 < M.active_nodes() < sum(M.Hy.levels[j].N for j in M.levels)
+    m0 = M.mass()
+    dt = M.dt_cfl()
+    for _ in range(8):
+        M.step(dt)
+    assert abs(M.mass() / m0 - 1) < 1e-15
+
+
+def test_covered_trends_are_restrictions():
+    M = make_model()
+    dht, _ = M.rhs(M._copy(M.dh), M._copy(M.u))
+    Hy = M.Hy
+    checked = 0
+    for j in range(M.jmin, M.jmax):
+        cov = M.covered(j)
+        odd = Hy.odd[j + 1]
+        fine = np.nan_to_num(dht[j + 1])
+        d = np.where(M.live_n[j + 1][odd], transform.height_detail(Hy, j + 1, fine), 0.0)
+        full = np.zeros(Hy.levels[j + 1].N)
+        full[: Hy.levels[j].N] = np.where(cov, fine[: Hy.levels[j].N], 0.0)
+        hc = transform.height_update(Hy, j + 1, full, d)
+        if cov.any():
+            assert np.abs(hc[cov] - dht[j][cov]).max() < 1e-12 * np.abs(dht[j][cov]).max()
+            checked += 1
+    assert checked >= 1
+
+
+def test_velocity_stays_consistent_across_levels():
+    """On coarse edges whose two ends are covered, u^j = R_u(u^{j+1}) after steps."""
+    M = make_model()
+    dt = M.dt_cfl()
+    for _ in range(3):
+        M.step(dt, adapt_after=False)
+    Hy = M.Hy
+    for j in range(M.jmin, M.jmax):
+        cov = M.covered(j)
+        C = Hy.levels[j]
+        e = cov[C.edges[:, 0]] & cov[C.edges[:, 1]]
+        if e.any():
+            r = transform.restrict_velocity(Hy, j + 1, M.u[j + 1])
+            assert np.abs(r[e] - M.u[j][e]).max() < 1e-12 * np.nanmax(np.abs(M.u[j]))
+
+
+def test_uniform_field_is_reproduced_exactly():
+    """A constant depth perturbation has zero coefficients everywhere: thresholding
+    keeps only Jmin, and prolongation onto any mask reproduces the constant."""
+    Hy = grid.Hierarchy(2, 4)
+    M = model.Model(Hy)
+    L = Hy.levels[4]
+    M.set_uniform(np.full(L.N, 5.0), np.zeros(L.E))
+    M.adapt(eps_h=1e-9, eps_u=1e-9)
+    assert M.live_n[3].sum() == 0 and M.live_n[4].sum() == 0
+    rng = np.random.default_rng(7)
+    sig = {j: rng.random(Hy.levels[j].N) < 0.01 for j in (3, 4)}
+    live_n, live_e = adapt.build_mask(Hy, sig)
+    zeros = {j: np.zeros(Hy.odd[j].size) for j in (3, 4)}
+    ue = {j: np.zeros(Hy.levels[j - 1].E) for j in (3, 4)}
+    ui = {j: np.zeros((Hy.levels[j - 1].T, 3)) for j in (3, 4)}
+    M.apply_mask(live_n, live_e, zeros, ue, ui)
+    assert M.live_n[4].sum() > 0 and M.ghost_n[4].sum() > 0
+    for j in M.levels:
+        v = M.dh[j][~np.isnan(M.dh[j])]
+        assert v.size > 0 and np.abs(v - 5.0).max() < 1e-12
+        w = M.u[j][~np.isnan(M.u[j])]
+        assert np.abs(w).max() == 0.0
+
+
+def test_dt_is_cfl_minimum():
+    M = make_model()
+    dt = M.dt_cfl()
+    # brute force over live points with the reading omega = sqrt(f^2 + g h (pi/dx)^2)
+    best = math.inf
+    for j in M.levels:
+        L = M.Hy.levels[j]
+        dx = grid.nominal_spacing(j, L.radius)
+        for i in np.nonzero(M.live_n[j])[0][:: max(1, L.N // 200)]:
+            f = 2 * M.Hy.omega * L.xyz[i, 2]
+            w = math.sqrt(f * f + M.g * (M.H + M.dh[j][i]) * (math.pi / dx) ** 2)
+            best = min(best, 1 / w)
+    assert dt <= M.cfl * best * (1 + 1e-12)
+    assert dt > 0.3 * M.cfl * best
+
+
+def test_error_controlled_by_eps():
+    """Against the uniform Jmax solution, the adapted solution's error drops as
+    eps drops (Sec. 6.2, Fig. 10 right)."""
+    jmin, jmax = 2, 4
+    Hy = grid.Hierarchy(jmin, jmax)
+    W = workloads.Workload("jet", seed=0)
+    L = Hy.levels[jmax]
+    dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    ref = model.Model(grid.Hierarchy(jmax, jmax))
+    ref.set_uniform(dh, u)
+    dt = 300.0
+    nsteps = 6
+    for _ in range(nsteps):
+        ref.step(dt)
+    errs = []
+    for eps in (3e-2, 1e-2, 3e-3):
+        M = model.Model(Hy, eps=eps)
+        M.set_uniform(dh, u)
+        M.adapt()
+        for _ in range(nsteps):
+            M.step(dt)
+        # compare on Jmin, where both solutions are complete
+        jm = M.jmin
+        r = ref.dh[jmax]
+        for j in range(jmax, jm, -1):
+            r = transform.restrict_height(Hy, j, r)
+        errs.append(np.abs(M.dh[jm] - r).max())
+    assert errs[2] < errs[0]

@@ -1,0 +1,202 @@
+"""Pins for the oracle's TRiSK operators (Sec. 3.1) and transforms (Sec. 2.2, 4).
+
+Each check is something the mathematics fixes independently of the code: the
+discrete mimetic identities of TRiSK, the Thuburn (steady geostrophic mode)
+condition, energy neutrality of the Coriolis term, invertibility and mass
+conservation of the lifting scheme, reproduction of constants and linear
+fields, second-order decay of the wavelet coefficients of a smooth field, and
+the commutation R_h o div = div o R_F of Eq. (divRcommute)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import grid, transform, trisk
+
+
+@pytest.fixture(scope="module")
+def L3():
+    return grid.Hierarchy(3, 3).levels[3]
+
+
+def test_div_of_rotational_flow_is_zero(L3):
+    rng = np.random.default_rng(0)
+    psi = rng.standard_normal(L3.T)
+    u = -(psi[L3.left] - psi[L3.right]) / L3.l_e
+    div = trisk.divergence(L3, u)
+    assert np.abs(div * L3.A_i).max() < 1e-12 * np.abs(u * L3.l_e).max()
+
+
+def test_curl_of_gradient_is_zero(L3):
+    rng = np.random.default_rng(1)
+    phi = rng.standard_normal(L3.N)
+    z = trisk.vorticity(L3, trisk.gradient(L3, phi))
+    assert np.abs(z * L3.A_v).max() < 1e-12
+
+
+def test_coriolis_is_energy_neutral(L3):
+    rng = np.random.default_rng(2)
+    F = rng.standard_normal(L3.E)
+    q = rng.standard_normal(L3.T)
+    cor = trisk.coriolis_tendency(L3, F, q)
+    work = L3.d_e * L3.l_e * F * cor
+    assert abs(work.sum()) < 1e-13 * np.abs(work).sum()
+
+
+def test_thuburn_condition(L3):
+    """Uniform q: the net flux of the reconstructed perpendicular flux out of a
+    dual triangle equals the kite-weighted sum of the cell divergences."""
+    rng = np.random.default_rng(3)
+    F = rng.standard_normal(L3.E)
+    cor = trisk.coriolis_tendency(L3, F, np.ones(L3.T))
+    e = L3.tri_edges
+    out_of_triangle = -np.sum(L3.tri_esign * cor[e] * L3.d_e[e], axis=1)
+    kf = L3.kite / L3.A_kite[L3.tri]
+    rhs = np.sum(kf * trisk.outflux(L3, F)[L3.tri], axis=1)
+    assert np.abs(out_of_triangle - rhs).max() < 1e-13 * np.abs(rhs).max()
+
+
+def test_perp_reconstruction_sign_and_size():
+    """For a smooth solid-body flow the reconstruction approaches F.n_left in the
+    rms sense (its maximum error on plain bisection grids does not vanish: the
+    known inconsistency of the scheme near the icosahedron's edges)."""
+    rms = []
+    for J in (3, 4, 5):
+        L = grid.Hierarchy(J, J).levels[J]
+        m, t = L.edge_midpoints(), L.edge_tangents()
+        east = np.stack([-m[:, 1], m[:, 0], 0 * m[:, 0]], 1)
+        u = np.sum(east * t, 1)
+        exact = np.sum(east * np.cross(m, t), 1)
+        err = trisk.coriolis_tendency(L, u, np.ones(L.T)) - exact
+        rms.append(np.sqrt(np.mean(err ** 2)))
+    assert rms[0] < 0.05 and rms[1] < rms[0] and rms[2] < rms[1]
+
+
+def test_kinetic_energy_sum(L3):
+    """sum_i A_i K_i = sum_e (l_e d_e / 2) u_e^2."""
+    u = np.random.default_rng(4).standard_normal(L3.E)
+    K = trisk.kinetic_energy(L3, u)
+    assert abs((L3.A_i * K).sum() / (0.5 * L3.l_e * L3.d_e * u ** 2).sum() - 1) < 1e-14
+
+
+def test_resting_state_has_zero_trend(L3):
+    dh = np.zeros(L3.N)
+    u = np.zeros(L3.E)
+    a, b = trisk.trend(L3, dh, u, 1.0e4, 9.80616)
+    assert np.abs(a).max() == 0.0 and np.abs(b).max() == 0.0
+
+
+def test_tc2_balance_improves_with_resolution():
+    """Williamson TC2 is steady; its trend (the discrete imbalance) shrinks in the
+    rms with resolution (Sec. 6.2)."""
+    g = 9.80616
+    rms = []
+    for J in (3, 4, 5):
+        L = grid.Hierarchy(J, J).levels[J]
+        W = workloads.Workload("tc2", mean_depth=2.94e4 / g)
+        dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+        a, b = trisk.trend(L, dh, u, 2.94e4 / g, g)
+        rms.append(math.sqrt(np.mean(b ** 2)))
+    assert rms[1] < rms[0] and rms[2] < rms[1]
+
+
+# ----------------------------------------------------------------------------- transforms
+
+@pytest.mark.parametrize("j", [3, 4, 5])
+def test_height_lifting_inverts_and_conserves(hier25, j):
+    C, F = hier25.levels[j - 1], hier25.levels[j]
+    rng = np.random.default_rng(j)
+    hf = rng.standard_normal(F.N) + 3.0
+    d = transform.height_detail(hier25, j, hf)
+    hc = transform.height_update(hier25, j, hf, d)
+    assert np.abs(transform.inverse_height(hier25, j, hc, d) - hf).max() < 1e-14
+    assert abs(C.A_i @ hc / (F.A_i @ hf) - 1) < 1e-15 * 8
+    assert np.abs(transform.height_detail(hier25, j, np.full(F.N, 7.0))).max() < 1e-14
+
+
+def test_height_details_decay_second_order(hier25):
+    W = workloads.Workload("harmonic", seed=2)
+    mx = []
+    for j in (3, 4, 5):
+        F = hier25.levels[j]
+        dh, _ = W.fields(F.xyz, F.edge_midpoints(), F.edge_tangents())
+        mx.append(np.abs(transform.height_detail(hier25, j, dh)).max())
+    assert 3.0 < mx[0] / mx[1] < 5.0 and 3.0 < mx[1] / mx[2] < 5.0
+
+
+@pytest.mark.parametrize("j", [3, 4, 5])
+def test_velocity_transform_inverts(hier25, j):
+    F = hier25.levels[j]
+    VS = transform.VelocityStencils(hier25, j)
+    uf = np.random.default_rng(j).standard_normal(F.E)
+    uc = transform.restrict_velocity(hier25, j, uf)
+    de, di = transform.velocity_detail(VS, uc, uf)
+    assert np.abs(transform.inverse_velocity(VS, uc, de, di, F.E) - uf).max() < 1e-14
+
+
+def test_velocity_weights_reproduce_linear_fields(hier25):
+    """Constructing a linear tangent field in each fine edge's orthographic plane,
+    the weighted coarse values give the fine value exactly."""
+    j = 4
+    C, F = hier25.levels[j - 1], hier25.levels[j]
+    VS = transform.VelocityStencils(hier25, j)
+    rng = np.random.default_rng(5)
+    fe = VS.int_edge[:, 0]
+    p = F.edge_midpoints()[fe]
+    tf = F.edge_tangents()[fe]
+    e1, e2 = grid._local_basis(p)
+    st = VS.int_st[:, 0]
+    xs, ts = C.edge_midpoints()[st], C.edge_tangents()[st]
+    A = rng.standard_normal((p.shape[0], 2, 3))    # V(x) = a0 + A1 (x.e1, x.e2)
+
+    def field(x, t):
+        xi = np.stack([np.einsum("bik,bk->bi", x, e1), np.einsum("bik,bk->bi", x, e2)], -1)
+        v = A[:, None, :, 0] + A[:, None, :, 1] * xi[..., :1] + A[:, None, :, 2] * xi[..., 1:]
+        tt = np.stack([np.einsum("bik,bk->bi", t, e1), np.einsum("bik,bk->bi", t, e2)], -1)
+        return np.sum(v * tt, -1)
+
+    vals = field(xs, ts)
+    target = field(p[:, None, :] * 0.0, tf[:, None, :])[:, 0]
+    pred = np.sum(VS.int_w[:, 0] * vals, axis=1)
+    assert np.abs(pred - target).max() < 1e-12
+
+
+def test_velocity_details_decay(hier25):
+    W = workloads.Workload("harmonic", seed=3)
+    me, mi = [], []
+    for j in (3, 4, 5):
+        F = hier25.levels[j]
+        _, u = W.fields(F.xyz, F.edge_midpoints(), F.edge_tangents())
+        VS = transform.VelocityStencils(hier25, j)
+        de, di = transform.velocity_detail(VS, transform.restrict_velocity(hier25, j, u), u)
+        me.append(np.abs(de).max())
+        mi.append(np.abs(di).max())
+    assert me[0] / me[1] > 3.0 and me[1] / me[2] > 3.0
+    assert mi[0] / mi[1] > 3.0 and mi[1] / mi[2] > 3.0
+
+
+@pytest.mark.parametrize("j", [3, 4, 5])
+def test_flux_restriction_commutes(hier25, j):
+    """Eq. (divRcommute): R_h(div_j F) = div_{j-1}(R_F F) for random fluxes."""
+    C, F = hier25.levels[j - 1], hier25.levels[j]
+    Ff = np.random.default_rng(10 + j).standard_normal(F.E)
+    c = trisk.divergence(F, Ff)
+    FS = transform.FluxStencils(hier25, j)
+    Fc = transform.restrict_flux(FS, Ff, F.l_e, c)
+    lhs = transform.restrict_height(hier25, j, c)
+    rhs = trisk.divergence(C, Fc / C.l_e)
+    assert np.abs(lhs - rhs).max() < 1e-14 * np.abs(lhs).max()
+
+
+def test_flux_restriction_of_uniform_flow_is_consistent(hier25):
+    """A smooth flow's restricted flux approximates the coarse-level flux
+    (the restriction is a consistent average, not only a conservative one)."""
+    j = 5
+    C, F = hier25.levels[j - 1], hier25.levels[j]
+    W = workloads.Workload("harmonic", seed=4)
+    _, uf = W.fields(F.xyz, F.edge_midpoints(), F.edge_tangents())
+    _, uc = W.fields(C.xyz, C.edge_midpoints(), C.edge_tangents())
+    FS = transform.FluxStencils(hier25, j)
+    Fc = transform.restrict_flux(FS, uf, F.l_e, trisk.divergence(F, uf)) / C.l_e
+    assert np.sqrt(np.mean((Fc - uc) ** 2)) < 0.05 * np.sqrt(np.mean(uc ** 2))
