@@ -1,0 +1,153 @@
+/*
+ * sww.h -- C ABI of the GB300 adaptive wavelet TRiSK shallow-water library.
+ *
+ * Aechtner, Kevlahan & Dubos, "A conservative adaptive wavelet method for the
+ * shallow water equations on the sphere" (arXiv:1404.0405).  The library holds
+ * one dynamically adapted, staggered hexagonal C-grid on the icosahedral sphere
+ * (levels Jmin..Jmax, Sec. 2.2, Table 1) and advances the rotating shallow-water
+ * equations (Sec. 3.1, Eqs. height and velo) with the TRiSK discretisation, the
+ * lifting wavelet transforms (Eqs. 1, 2, Rh), the conservative flux restriction
+ * (Sec. 4.2-4.3, Eqs. restr_flux, ho_flux, kml) and the threshold-plus-neighbour
+ * grid adaptation (Sec. 2.3).  All arithmetic runs in CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - Each level j holds N_j = 10*4^j + 2 nodes, E_j = 30*4^j edges and
+ *     T_j = 20*4^j triangles in the library's own order (query it with
+ *     sww_get_grid).  Heights are the perturbation dh = h - H at nodes (m);
+ *     velocities are the component along each edge from its origin node to its
+ *     end node (m/s).
+ *   - Host arrays are owned by the caller and only read/written during the
+ *     call.  Pointers flagged as device pointers must be device memory of the
+ *     handle's GPU; the library reads them on the handle's stream.
+ *   - Every call returns SWW_OK (0) or a negative error code; sww_last_error
+ *     gives a message for the last failure on the calling thread.  A failed
+ *     call leaves the handle usable unless it returns SWW_E_CUDA.
+ *   - A handle is not thread-safe.  Work is issued on the stream given to
+ *     sww_create; calls returning host data synchronise that stream.
+ */
+#ifndef SWW_H
+#define SWW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SWW_OK = 0,
+    SWW_E_ARG = -1,      /* invalid argument (bad level, null pointer, bad config) */
+    SWW_E_CUDA = -2,     /* a CUDA call failed; the handle should be destroyed */
+    SWW_E_POOL = -3,     /* device memory exhausted at creation */
+    SWW_E_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    SWW_E_STATE = -5,    /* call out of order (e.g. step before set_state) */
+    SWW_E_NUMERIC = -6   /* non-finite value detected in the state */
+};
+
+enum { SWW_RK4 = 0, SWW_SSP43 = 1 };
+
+/* Quantities readable per level with sww_get_level (element type in brackets). */
+enum {
+    SWW_DH = 0,        /* [double N_j]  depth perturbation at nodes                      */
+    SWW_U = 1,         /* [double E_j]  velocity along edges                              */
+    SWW_DH_T = 2,      /* [double N_j]  last trend d(dh)/dt (valid at live nodes)         */
+    SWW_U_T = 3,       /* [double E_j]  last trend du/dt (valid at live edges)            */
+    SWW_NODE_FLAGS = 4,/* [uint8 N_j]   bit0 live, bit1 ghost, bit2 covered (R_h applies) */
+    SWW_EDGE_FLAGS = 5,/* [uint8 E_j]   bit0 live, bit1 ghost                              */
+    SWW_HDET = 6,      /* [double N_j]  height coefficient at odd nodes of level j (0 elsewhere) */
+    SWW_UDET_E = 7,    /* [double E_{j-1}] velocity coefficient per coarse edge           */
+    SWW_UDET_I = 8,    /* [double E_j]  velocity coefficient at interior fine edges (0 elsewhere) */
+    SWW_SIG = 9        /* [uint8 N_j]   significance set of the last adaptation          */
+};
+
+typedef struct {
+    int jmin, jmax;    /* coarsest and finest level, 1 <= jmin <= jmax <= 11           */
+    double radius;     /* sphere radius (m)                                            */
+    double omega;      /* rotation rate (1/s)                                          */
+    double g;          /* gravity (m/s^2)                                              */
+    double H;          /* mean depth (m)                                               */
+    int patch;         /* patch side p (power of two); levels with 2^j < p use 2^j     */
+    int rk;            /* SWW_RK4 or SWW_SSP43                                         */
+    double cfl;        /* dt = cfl * min(1/omega_max, min dx/|u|) when dt <= 0         */
+    double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u| */
+} sww_config;
+
+typedef struct {
+    double t;                 /* model time (s)                                        */
+    double dt;                /* last time step (s)                                    */
+    double mass;              /* sum over Jmin of A_k (H + dh_k) (m^3), compensated   */
+    double energy;            /* Sec. 7.2 energy on Jmin (m^5/s^2 ... as printed)      */
+    double eps_h, eps_u;      /* thresholds of the last adaptation                     */
+    int64_t steps;
+    int64_t live_nodes[16];   /* per level j (index j), live nodes                     */
+    int64_t ghost_nodes[16];
+    int64_t live_edges[16];
+    int64_t active_patches[16];
+} sww_stats;
+
+typedef struct sww_handle sww_handle;
+
+/* Build the grid and its geometry for levels Jmin..Jmax (host FP64, uploaded).
+ * stream: a cudaStream_t (may be NULL for the default stream).  *out receives
+ * the handle, owned by the library until sww_destroy. */
+int sww_create(const sww_config* cfg, void* stream, sww_handle** out);
+int sww_destroy(sww_handle* h);
+
+/* Sizes of level j: nodes, edges, triangles, patches. */
+int sww_level_sizes(const sww_handle* h, int level, int64_t* n_nodes, int64_t* n_edges,
+                    int64_t* n_tris, int64_t* n_patches);
+
+/* Geometry of level j into host arrays: node_xyz[3*N] unit vectors,
+ * edge_nodes[2*E] (origin, end) node ids.  Either pointer may be NULL. */
+int sww_get_grid(const sww_handle* h, int level, double* node_xyz, int32_t* edge_nodes);
+
+/* Fields on the full finest level Jmax (dh[N_Jmax], u[E_Jmax]); every coarser
+ * level receives their restriction (R_h for height, the mean of the two half
+ * edges for velocity) and every point becomes live (Sec. 3.1 initialisation).
+ * device_ptrs != 0: dh, u are device pointers. */
+int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs);
+
+/* Adapt the grid (Sec. 2.3): wavelet coefficients at live points, thresholds
+ * (eps_h, eps_u > 0 given explicitly, else eps times the live maxima),
+ * significance, neighbours in space and scale, graded closure, ghost band,
+ * patch lists, and the inverse transform of the retained coefficients. */
+int sww_adapt(sww_handle* h, double eps_h, double eps_u);
+
+/* Same mask construction from caller-provided coefficients: hdet[N_j] per
+ * level j (values at odd nodes), udet_e[E_{j-1}], udet_i[E_j] (interior fine
+ * edges), for j = Jmin+1..Jmax in order, host arrays concatenated by level.
+ * Values are not applied to the state; only flags and patch lists change,
+ * then the inverse transform runs with these coefficients. */
+int sww_mask_from_coeffs(sww_handle* h, const double* hdet, const double* udet_e,
+                         const double* udet_i, double eps_h, double eps_u);
+
+/* Evaluate the trend of the current state (ghosts refreshed, restrictions
+ * applied, Sec. 3.1) into the SWW_DH_T / SWW_U_T buffers. */
+int sww_rhs(sww_handle* h);
+
+/* Advance nsteps RK steps.  dt <= 0 uses the CFL step of the current state.
+ * adapt != 0 runs the partial height transform and sww_adapt after each step;
+ * adapt == 0 runs only the partial height transform. */
+int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
+
+/* Copy one per-level quantity (SWW_DH ... SWW_SIG) to the host. */
+int sww_get_level(const sww_handle* h, int level, int what, void* out);
+
+/* Write the depth perturbation and velocity of level j (host arrays). */
+int sww_set_level(sww_handle* h, int level, const double* dh, const double* u);
+
+/* Active patch list of level j (ascending patch ids) into out[n_patches];
+ * *count receives its length. */
+int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count);
+
+/* Diagnostics (synchronises the stream). */
+int sww_stats_get(sww_handle* h, sww_stats* st);
+
+/* Message of the last error on the calling thread. */
+int sww_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

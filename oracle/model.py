@@ -233,6 +233,7 @@ class Model:
             un[j][~self.live_e[j]] = np.nan
         self.dh, self.u = hn, un
         self.partial_transform()
+        self.fill_ghosts()
         if adapt_after:
             self.adapt()
         else:

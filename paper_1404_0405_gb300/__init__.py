@@ -1,0 +1,214 @@
+"""GB300 adaptive wavelet TRiSK shallow-water library (arXiv:1404.0405), Python binding.
+
+A thin ctypes layer over the C ABI in ``include/sww.h``: argument marshalling
+only.  Every step of the method runs in the CUDA kernels of ``libsww.so``; there
+is no CPU fallback, and the calls raise if the library or a GPU is missing.
+Device pointers may be passed as torch CUDA tensors; the default stream is
+torch's current stream when torch has CUDA.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .buildlib import LIB, build
+
+__all__ = ["Model", "SwwError", "load", "lib_path", "DH", "U", "DH_T", "U_T", "NODE_FLAGS", "EDGE_FLAGS",
+           "HDET", "UDET_E", "UDET_I", "SIG", "LIVE", "GHOST", "COVERED"]
+
+DH, U, DH_T, U_T, NODE_FLAGS, EDGE_FLAGS, HDET, UDET_E, UDET_I, SIG = range(10)
+LIVE, GHOST, COVERED = 1, 2, 4
+RK4, SSP43 = 0, 1
+EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
+           "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
+           "sww_stats_get", "sww_last_error"]
+
+
+class SwwError(RuntimeError):
+    pass
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("jmin", ctypes.c_int), ("jmax", ctypes.c_int), ("radius", ctypes.c_double),
+                ("omega", ctypes.c_double), ("g", ctypes.c_double), ("H", ctypes.c_double),
+                ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
+                ("energy", ctypes.c_double), ("eps_h", ctypes.c_double), ("eps_u", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("live_nodes", ctypes.c_int64 * 16), ("ghost_nodes", ctypes.c_int64 * 16),
+                ("live_edges", ctypes.c_int64 * 16), ("active_patches", ctypes.c_int64 * 16)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libsww.so (building it in-tree first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        if not build_if_missing:
+            raise SwwError(f"{LIB} is missing; run paper_1404_0405_gb300.buildlib")
+        build()
+    lib = ctypes.CDLL(LIB)
+    P, I, D, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "sww_create": [ctypes.POINTER(Config), P, ctypes.POINTER(P)],
+        "sww_destroy": [P],
+        "sww_level_sizes": [P, I, I64, I64, I64, I64],
+        "sww_get_grid": [P, I, P, P],
+        "sww_set_state": [P, P, P, I],
+        "sww_adapt": [P, D, D],
+        "sww_mask_from_coeffs": [P, P, P, P, D, D],
+        "sww_rhs": [P],
+        "sww_step": [P, D, I, I],
+        "sww_get_level": [P, I, I, P],
+        "sww_set_level": [P, I, P, P],
+        "sww_get_patches": [P, I, P, ctypes.POINTER(ctypes.c_int32)],
+        "sww_stats_get": [P, ctypes.POINTER(Stats)],
+        "sww_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        buf = ctypes.create_string_buffer(1024)
+        _lib.sww_last_error(buf, 1024)
+        raise SwwError(f"sww error {rc}: {buf.value.decode(errors='replace')}")
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a torch tensor."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p), 0
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    raise TypeError(type(a))
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(None)
+
+
+class Model:
+    """One adapted grid Jmin..Jmax and its state on the GPU (sww_create)."""
+
+    def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
+                 cfl=0.8, eps=1e-2, stream=None):
+        lib = load()
+        self.jmin, self.jmax = jmin, jmax
+        self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps)
+        h = ctypes.c_void_p()
+        _check(lib.sww_create(ctypes.byref(self.cfg), stream if stream is not None else _default_stream(),
+                              ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sww_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ grid
+    def sizes(self, level):
+        out = [ctypes.c_int64() for _ in range(4)]
+        _check(load().sww_level_sizes(self._h, level, *[ctypes.byref(o) for o in out]))
+        return tuple(o.value for o in out)
+
+    def grid(self, level):
+        """(node_xyz[N,3] unit vectors, edge_nodes[E,2] origin/end)."""
+        N, E, _, _ = self.sizes(level)
+        xyz = np.empty((N, 3))
+        en = np.empty((E, 2), dtype=np.int32)
+        _check(load().sww_get_grid(self._h, level, _ptr(xyz)[0], _ptr(en)[0]))
+        return xyz, en
+
+    # ------------------------------------------------------------------ state
+    def set_state(self, dh, u):
+        """Fields on the full level Jmax (numpy host arrays or torch CUDA tensors, float64)."""
+        if isinstance(dh, np.ndarray):
+            dh = np.ascontiguousarray(dh, dtype=np.float64)
+            u = np.ascontiguousarray(u, dtype=np.float64)
+        pd, dev = _ptr(dh)
+        pu, _ = _ptr(u)
+        _check(load().sww_set_state(self._h, pd, pu, dev))
+
+    def adapt(self, eps_h=-1.0, eps_u=-1.0):
+        _check(load().sww_adapt(self._h, eps_h, eps_u))
+
+    def mask_from_coeffs(self, hdet, udet_e, udet_i, eps_h, eps_u):
+        """hdet/udet_e/udet_i: dicts level -> array (level Jmin+1..Jmax)."""
+        cat = lambda d: np.ascontiguousarray(np.concatenate([d[j] for j in range(self.jmin + 1, self.jmax + 1)]),
+                                             dtype=np.float64)
+        a, b, c = cat(hdet), cat(udet_e), cat(udet_i)
+        _check(load().sww_mask_from_coeffs(self._h, _ptr(a)[0], _ptr(b)[0], _ptr(c)[0], eps_h, eps_u))
+
+    def rhs(self):
+        _check(load().sww_rhs(self._h))
+
+    def step(self, dt=-1.0, nsteps=1, adapt=True):
+        _check(load().sww_step(self._h, float(dt), int(nsteps), int(bool(adapt))))
+
+    def get(self, level, what):
+        N, E, _, _ = self.sizes(level)
+        if what in (DH, DH_T, HDET):
+            out = np.empty(N)
+        elif what in (U, U_T, UDET_I):
+            out = np.empty(E)
+        elif what == UDET_E:
+            out = np.empty(self.sizes(level - 1)[1])
+        elif what in (NODE_FLAGS, SIG):
+            out = np.empty(N, dtype=np.uint8)
+        elif what == EDGE_FLAGS:
+            out = np.empty(E, dtype=np.uint8)
+        else:
+            raise ValueError(what)
+        _check(load().sww_get_level(self._h, level, what, _ptr(out)[0]))
+        return out
+
+    def set_level(self, level, dh=None, u=None):
+        a = None if dh is None else np.ascontiguousarray(dh, dtype=np.float64)
+        b = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        _check(load().sww_set_level(self._h, level, None if a is None else _ptr(a)[0], None if b is None else _ptr(b)[0]))
+
+    def patches(self, level):
+        n = self.sizes(level)[3]
+        out = np.empty(n, dtype=np.int32)
+        cnt = ctypes.c_int32()
+        _check(load().sww_get_patches(self._h, level, _ptr(out)[0], ctypes.byref(cnt)))
+        return out[: cnt.value].copy()
+
+    def stats(self):
+        st = Stats()
+        _check(load().sww_stats_get(self._h, ctypes.byref(st)))
+        lv = range(self.jmin, self.jmax + 1)
+        return {"t": st.t, "dt": st.dt, "mass": st.mass, "energy": st.energy, "eps_h": st.eps_h, "eps_u": st.eps_u,
+                "steps": st.steps, "live_nodes": {j: st.live_nodes[j] for j in lv},
+                "ghost_nodes": {j: st.ghost_nodes[j] for j in lv}, "live_edges": {j: st.live_edges[j] for j in lv},
+                "active_patches": {j: st.active_patches[j] for j in lv}}

@@ -1,0 +1,551 @@
+// C ABI (include/sww.h): handle lifetime, upload of the host-built grid, and the
+// sequencing of kernels for one trend evaluation, one RK step and one adaptation.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "grid.h"
+#include "sww.h"
+#include "sww_core.cuh"
+#include "sww_kernels.h"
+
+using namespace sww;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+struct CudaError : std::runtime_error {
+    using std::runtime_error::runtime_error;
+};
+
+void ck(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) throw CudaError(std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+__global__ void k_set(double* p, double v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+__global__ void k_reset_red(unsigned long long* red) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        red[0] = 0ull;
+        red[1] = ~0ull;
+    }
+}
+
+constexpr int GHOST_HOPS = 5;
+
+}  // namespace
+
+struct sww_handle {
+    sww_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::vector<DevLevel> lv;
+    std::vector<std::vector<double>> xyz;     // host node positions per level (flattened)
+    std::vector<std::vector<int32_t>> edges;  // host edge (origin, end) pairs per level
+    std::vector<void*> allocs;
+    unsigned long long *red = nullptr, *cnt = nullptr;
+    double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
+    double t = 0, last_dt = 0;
+    int64_t steps = 0;
+    bool has_state = false;
+
+    template <typename T>
+    T* alloc(size_t n) {
+        void* p = nullptr;
+        ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
+        allocs.push_back(p);
+        return static_cast<T*>(p);
+    }
+    template <typename T>
+    T* up(const std::vector<T>& v) {
+        T* p = alloc<T>(v.size());
+        ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+        return p;
+    }
+    template <typename T, int K>
+    T* up_slots(const std::vector<T> (&v)[K], int count) {
+        size_t n = v[0].size();
+        std::vector<T> flat(n * count);
+        for (int k = 0; k < count; ++k) std::memcpy(flat.data() + k * n, v[k].data(), n * sizeof(T));
+        return up(flat);
+    }
+    ~sww_handle() {
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side, int64_t coarse_E) {
+    DevLevel D{};
+    D.J = L.J, D.n = L.n, D.p = L.p, D.np = L.np, D.nelem = L.nelem, D.N = L.N, D.E = L.E, D.T = L.T, D.npatch = L.npatch;
+    D.en = h->up_slots(L.en, 2);
+    D.et = h->up_slots(L.et, 2);
+    D.tn = h->up_slots(L.tn, 3);
+    D.te = h->up_slots(L.te, 3);
+    D.deg = h->up(L.deg);
+    D.ring_e = h->up_slots(L.ring_e, 6);
+    D.A_i = h->up(L.A_i), D.A_v = h->up(L.A_v), D.kite = h->up_slots(L.kite, 3);
+    D.d_e = h->up(L.d_e), D.l_e = h->up(L.l_e), D.f_v = h->up(L.f_v), D.f_n = h->up(L.f_n);
+    D.cor_i = h->up_slots(L.cor_i, COR);
+    D.cor_w = h->up_slots(L.cor_w, COR);
+    if (fine_side) {
+        D.par = h->up_slots(L.par, 4);
+        D.ptw = h->up_slots(L.ptw, 4);
+        D.fe_kind = h->up(L.fe_kind);
+        D.fe_ce = h->up(L.fe_ce);
+        D.vst = h->up_slots(L.vst, VST);
+        D.vw = h->up_slots(L.vw, VST);
+    }
+    if (coarse_side) {
+        D.c2f = h->up(L.c2f), D.mid = h->up(L.mid), D.half = h->up_slots(L.half, 2);
+        D.mk_i = h->up_slots(L.mk_i, 12);
+        D.mk_w = h->up_slots(L.mk_w, 12);
+        D.rf_fi = h->up_slots(L.rf_fi, RF_F);
+        D.rf_fw = h->up_slots(L.rf_fw, RF_F);
+        D.rf_ci = h->up_slots(L.rf_ci, RF_C);
+        D.rf_cw = h->up_slots(L.rf_cw, RF_C);
+    }
+    const int64_t N = L.N, E = L.E, T = L.T;
+    double** dN[] = {&D.dh, &D.dh0, &D.dha, &D.dht, &D.B, &D.c, &D.hdet};
+    for (auto p : dN) *p = h->alloc<double>(N);
+    double** dE[] = {&D.u, &D.u0, &D.ua, &D.ut, &D.F, &D.Q, &D.ui};
+    for (auto p : dE) *p = h->alloc<double>(E);
+    D.q = h->alloc<double>(T);
+    D.ue = h->alloc<double>(coarse_E > 0 ? coarse_E : 1);
+    uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
+    for (auto p : bN) *p = h->alloc<uint8_t>(N);
+    D.eflag = h->alloc<uint8_t>(E);
+    D.pflag = h->alloc<uint8_t>(L.npatch);
+    D.patches = h->alloc<int32_t>(L.npatch);
+    D.npatches = h->alloc<int32_t>(1);
+    // f2c of this level: coarse node at the same place (-1 for odd nodes)
+    {
+        std::vector<int32_t> f2c(N, -1);
+        if (fine_side) {
+            // even element (2i, 2j) <-> coarse element (i, j); poles map to poles
+            int64_t n = L.n, p = L.p, np = L.np;
+            int64_t cn = n / 2, cp = std::min<int64_t>(L.p, cn), cnp = cn / cp;
+            for (int64_t e = 0; e < L.nelem; ++e) {
+                int64_t pp = p * p, pid = e / pp, loc = e % pp;
+                int64_t pj = pid % np, pi = (pid / np) % np, d = pid / (np * np);
+                int64_t i = pi * p + loc / p, j = pj * p + loc % p;
+                if ((i & 1) || (j & 1)) continue;
+                int64_t ci = i / 2, cj = j / 2;
+                f2c[e] = int32_t(((d * cnp + ci / cp) * cnp + cj / cp) * cp * cp + (ci % cp) * cp + (cj % cp));
+            }
+            f2c[L.nelem] = int32_t(10 * cn * cn);
+            f2c[L.nelem + 1] = int32_t(10 * cn * cn + 1);
+        }
+        D.f2c = h->up(f2c);
+    }
+    for (double* p : {D.dh, D.dh0, D.dha, D.dht, D.B, D.c, D.hdet}) ck(cudaMemset(p, 0, N * sizeof(double)), "memset");
+    for (double* p : {D.u, D.u0, D.ua, D.ut, D.F, D.Q, D.ui}) ck(cudaMemset(p, 0, E * sizeof(double)), "memset");
+    ck(cudaMemset(D.q, 0, T * sizeof(double)), "memset");
+    for (uint8_t* p : {D.nflag, D.sig, D.tmask, D.band0, D.band1}) ck(cudaMemset(p, 0, N), "memset");
+    ck(cudaMemset(D.eflag, 0, E), "memset");
+    ck(cudaMemset(D.ue, 0, (coarse_E > 0 ? coarse_E : 1) * sizeof(double)), "memset");
+    ck(cudaMemset(D.npatches, 0, sizeof(int32_t)), "memset");
+    h->lv[L.J] = D;
+}
+
+void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
+
+// ------------------------------------------------------------------ sequences
+
+void fill_ghosts(sww_handle* h) {
+    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    for (int j = j0 + 1; j <= j1; ++j) launch_fill(h->lv[j], h->lv[j - 1], h->stream);
+}
+
+// one trend evaluation (Sec. 3.1): ghosts, q/K/B/F/qF^perp on every level, then the
+// restriction of B, F and q F^perp from Jmax-1 down to Jmin
+void trend(sww_handle* h) {
+    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    fill_ghosts(h);
+    for (int j = j0; j <= j1; ++j) launch_trend_level(h->lv[j], h->cfg.H, h->cfg.g, h->stream);
+    for (int j = j1 - 1; j >= j0; --j) launch_restrict(h->lv[j], h->lv[j + 1], h->stream);
+}
+
+void update(sww_handle* h, const RKStage& st) {
+    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j) launch_update(h->lv[j], st, h->dt, h->stream);
+}
+
+void compute_dt(sww_handle* h) {
+    k_reset_red<<<1, 32, 0, h->stream>>>(h->red);
+    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j)
+        launch_dt(h->lv[j], h->cfg.H, h->cfg.g, nominal_spacing(j, h->cfg.radius), h->red, h->stream);
+    launch_dt_final(h->red, h->cfg.cfl, h->dt, h->stream);
+}
+
+void mask_and_inverse(sww_handle* h) {
+    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    cudaStream_t s = h->stream;
+    // significance with the current (old) live flags
+    for (int j = j0 + 1; j <= j1; ++j) {
+        ck(cudaMemsetAsync(h->lv[j].sig, 0, h->lv[j].N, s), "memset sig");
+        launch_sig(h->lv[j], h->lv[j - 1], h->thr, s);
+    }
+    for (int j = j0 + 1; j <= j1; ++j) launch_adjacent(h->lv[j], h->lv[j - 1], j - 1 > j0, s);
+    for (int j = j1; j > j0; --j) {
+        bool finer = j < j1;
+        launch_close(h->lv[j], finer ? h->lv[j + 1] : h->lv[j], finer, s);
+    }
+    for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], j == j0, s);
+    for (int j = j0 + 1; j <= j1; ++j) launch_ghost_band(h->lv[j], GHOST_HOPS, s);
+    for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
+    for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+    // inverse transform of the retained coefficients, coarse to fine, ghosts per level
+    for (int j = j0 + 1; j <= j1; ++j) {
+        launch_inverse(h->lv[j], h->lv[j - 1], s);
+        launch_fill(h->lv[j], h->lv[j - 1], s);
+    }
+}
+
+void adapt(sww_handle* h, double eh, double eu) {
+    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    cudaStream_t s = h->stream;
+    for (int j = j0 + 1; j <= j1; ++j) launch_details(h->lv[j], h->lv[j - 1], s);
+    ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
+    for (int j = j0; j <= j1; ++j) launch_maxabs(h->lv[j], h->red, s);
+    launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
+    mask_and_inverse(h);
+}
+
+const RKStage* stages(int rk, int& n) {
+    // classical RK4 (acc holds k1 + 2 k2 + 2 k3) and the 4-stage, third-order SSP
+    // scheme of Spiteri & Ruuth (Sec. 3.1)
+    static const RKStage rk4[4] = {
+        {1, 1.0, 0.0, 0.5, 0.0, 0.0, 1.0},
+        {1, 1.0, 0.0, 0.5, 0.0, 1.0, 2.0},
+        {1, 1.0, 0.0, 1.0, 0.0, 1.0, 2.0},
+        {1, 1.0, 0.0, 1.0 / 6.0, 1.0 / 6.0, 1.0, 0.0},
+    };
+    static const RKStage ssp[4] = {
+        {1, 0.0, 1.0, 0.5, 0.0, 0.0, 0.0},
+        {1, 0.0, 1.0, 0.5, 0.0, 0.0, 0.0},
+        {1, 2.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0, 0.0, 0.0, 0.0},
+        {1, 0.0, 1.0, 0.5, 0.0, 0.0, 0.0},
+    };
+    n = 4;
+    return rk == SWW_SSP43 ? ssp : rk4;
+}
+
+void one_step(sww_handle* h, double dt, bool do_adapt) {
+    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    if (dt > 0)
+        k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
+    else
+        compute_dt(h);
+    for (int j = j0; j <= j1; ++j) launch_save_base(h->lv[j], h->stream);
+    int ns;
+    const RKStage* st = stages(h->cfg.rk, ns);
+    for (int k = 0; k < ns; ++k) {
+        trend(h);
+        update(h, st[k]);
+    }
+    for (int j = j1 - 1; j >= j0; --j) launch_partial(h->lv[j], h->lv[j + 1], h->stream);
+    fill_ghosts(h);
+    if (do_adapt) adapt(h, -1.0, -1.0);
+}
+
+int check_level(const sww_handle* h, int level) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (level < h->cfg.jmin || level > h->cfg.jmax) return fail(SWW_E_ARG, "level out of range");
+    return SWW_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const CudaError& e) {
+        return fail(SWW_E_CUDA, e.what());
+    } catch (const std::bad_alloc&) {
+        return fail(SWW_E_POOL, "host allocation failed");
+    } catch (const std::exception& e) {
+        return fail(SWW_E_ARG, e.what());
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
+    if (!cfg || !out) return fail(SWW_E_ARG, "null argument");
+    *out = nullptr;
+    if (cfg->jmin < 1 || cfg->jmax < cfg->jmin || cfg->jmax > 11) return fail(SWW_E_ARG, "need 1 <= jmin <= jmax <= 11");
+    if (!(cfg->radius > 0) || !(cfg->g > 0) || !(cfg->H > 0) || !(cfg->cfl > 0) || !(cfg->eps > 0))
+        return fail(SWW_E_ARG, "radius, g, H, cfl and eps must be positive");
+    if (cfg->patch < 1 || (cfg->patch & (cfg->patch - 1)) || cfg->patch > 16)
+        return fail(SWW_E_ARG, "patch must be a power of two <= 16");
+    if (cfg->rk != SWW_RK4 && cfg->rk != SWW_SSP43) return fail(SWW_E_ARG, "rk must be SWW_RK4 or SWW_SSP43");
+    sww_handle* h = new (std::nothrow) sww_handle();
+    if (!h) return fail(SWW_E_POOL, "host allocation failed");
+    int rc = guarded([&]() -> int {
+        h->cfg = *cfg;
+        h->stream = static_cast<cudaStream_t>(stream);
+        Hierarchy H;
+        build_hierarchy(H, cfg->jmin, cfg->jmax, cfg->patch, cfg->radius, cfg->omega);
+        h->lv.assign(cfg->jmax + 1, DevLevel{});
+        h->xyz.assign(cfg->jmax + 1, {});
+        h->edges.assign(cfg->jmax + 1, {});
+        for (int j = cfg->jmin; j <= cfg->jmax; ++j) {
+            HostLevel& L = H.lv[j];
+            upload_level(h, L, j > cfg->jmin, j < cfg->jmax, j > cfg->jmin ? H.lv[j - 1].E : 0);
+            h->xyz[j].resize(3 * L.N);
+            for (int64_t v = 0; v < L.N; ++v) h->xyz[j][3 * v] = L.xyz[v].x, h->xyz[j][3 * v + 1] = L.xyz[v].y, h->xyz[j][3 * v + 2] = L.xyz[v].z;
+            h->edges[j].resize(2 * L.E);
+            for (int64_t e = 0; e < L.E; ++e) h->edges[j][2 * e] = L.en[0][e], h->edges[j][2 * e + 1] = L.en[1][e];
+        }
+        h->red = h->alloc<unsigned long long>(4);
+        h->cnt = h->alloc<unsigned long long>(4);
+        h->thr = h->alloc<double>(2);
+        h->dt = h->alloc<double>(1);
+        h->sums = h->alloc<double>(2);
+        h->part = h->alloc<double>(4 * size_t(sums_blocks(h->lv[cfg->jmin])));
+        ck(cudaMemset(h->thr, 0, 2 * sizeof(double)), "memset");
+        ck(cudaMemset(h->dt, 0, sizeof(double)), "memset");
+        ck(cudaDeviceSynchronize(), "create");
+        return SWW_OK;
+    });
+    if (rc != SWW_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SWW_OK;
+}
+
+int sww_destroy(sww_handle* h) {
+    if (!h) return SWW_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    delete h;
+    return SWW_OK;
+}
+
+int sww_level_sizes(const sww_handle* h, int level, int64_t* nn, int64_t* ne, int64_t* nt, int64_t* np) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    const DevLevel& L = h->lv[level];
+    if (nn) *nn = L.N;
+    if (ne) *ne = L.E;
+    if (nt) *nt = L.T;
+    if (np) *np = L.npatch;
+    return SWW_OK;
+}
+
+int sww_get_grid(const sww_handle* h, int level, double* node_xyz, int32_t* edge_nodes) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (node_xyz) std::memcpy(node_xyz, h->xyz[level].data(), h->xyz[level].size() * sizeof(double));
+    if (edge_nodes) std::memcpy(edge_nodes, h->edges[level].data(), h->edges[level].size() * sizeof(int32_t));
+    return SWW_OK;
+}
+
+int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
+    if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
+    return guarded([&]() -> int {
+        const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+        DevLevel& F = h->lv[j1];
+        cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, h->stream), "set_state dh");
+        ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, h->stream), "set_state u");
+        for (int j = j1; j > j0; --j) launch_restrict_full(h->lv[j - 1], h->lv[j], h->stream);
+        for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], 1, h->stream);
+        for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], h->stream);
+        for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], h->stream);
+        check_launch();
+        ck(cudaStreamSynchronize(h->stream), "set_state");
+        h->has_state = true;
+        h->t = 0;
+        h->steps = 0;
+        return SWW_OK;
+    });
+}
+
+int sww_adapt(sww_handle* h, double eps_h, double eps_u) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    return guarded([&]() -> int {
+        adapt(h, eps_h, eps_u);
+        check_launch();
+        ck(cudaStreamSynchronize(h->stream), "adapt");
+        return SWW_OK;
+    });
+}
+
+int sww_mask_from_coeffs(sww_handle* h, const double* hdet, const double* udet_e, const double* udet_i, double eps_h,
+                         double eps_u) {
+    if (!h || !hdet || !udet_e || !udet_i) return fail(SWW_E_ARG, "null argument");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    if (!(eps_h > 0) || !(eps_u > 0)) return fail(SWW_E_ARG, "explicit positive thresholds required");
+    return guarded([&]() -> int {
+        size_t oh = 0, oe = 0, oi = 0;
+        for (int j = h->cfg.jmin + 1; j <= h->cfg.jmax; ++j) {
+            DevLevel& F = h->lv[j];
+            int64_t ce = h->lv[j - 1].E;
+            ck(cudaMemcpyAsync(F.hdet, hdet + oh, F.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "hdet");
+            ck(cudaMemcpyAsync(F.ue, udet_e + oe, ce * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ue");
+            ck(cudaMemcpyAsync(F.ui, udet_i + oi, F.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ui");
+            oh += F.N, oe += ce, oi += F.E;
+        }
+        double th[2] = {eps_h, eps_u};
+        ck(cudaMemcpyAsync(h->thr, th, sizeof(th), cudaMemcpyHostToDevice, h->stream), "thr");
+        mask_and_inverse(h);
+        check_launch();
+        ck(cudaStreamSynchronize(h->stream), "mask");
+        return SWW_OK;
+    });
+}
+
+int sww_rhs(sww_handle* h) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    return guarded([&]() -> int {
+        trend(h);
+        RKStage none{0, 0, 0, 0, 0, 0, 0};
+        update(h, none);
+        check_launch();
+        ck(cudaStreamSynchronize(h->stream), "rhs");
+        return SWW_OK;
+    });
+}
+
+int sww_step(sww_handle* h, double dt, int nsteps, int do_adapt) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    if (nsteps < 0) return fail(SWW_E_ARG, "nsteps < 0");
+    return guarded([&]() -> int {
+        for (int s = 0; s < nsteps; ++s) {
+            one_step(h, dt, do_adapt != 0);
+            check_launch();
+            double d = 0;
+            ck(cudaMemcpyAsync(&d, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
+            ck(cudaStreamSynchronize(h->stream), "step");
+            if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
+            h->t += d;
+            h->last_dt = d;
+            h->steps += 1;
+        }
+        return SWW_OK;
+    });
+}
+
+int sww_get_level(const sww_handle* h, int level, int what, void* out) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (!out) return fail(SWW_E_ARG, "null output");
+    const DevLevel& L = h->lv[level];
+    const void* src = nullptr;
+    size_t bytes = 0;
+    switch (what) {
+        case SWW_DH: src = L.dh, bytes = L.N * sizeof(double); break;
+        case SWW_U: src = L.u, bytes = L.E * sizeof(double); break;
+        case SWW_DH_T: src = L.dht, bytes = L.N * sizeof(double); break;
+        case SWW_U_T: src = L.ut, bytes = L.E * sizeof(double); break;
+        case SWW_NODE_FLAGS: src = L.nflag, bytes = L.N; break;
+        case SWW_EDGE_FLAGS: src = L.eflag, bytes = L.E; break;
+        case SWW_HDET: src = L.hdet, bytes = L.N * sizeof(double); break;
+        case SWW_UDET_E:
+            if (level == h->cfg.jmin) return fail(SWW_E_ARG, "no coefficients on Jmin");
+            src = L.ue, bytes = h->lv[level - 1].E * sizeof(double);
+            break;
+        case SWW_UDET_I: src = L.ui, bytes = L.E * sizeof(double); break;
+        case SWW_SIG: src = L.sig, bytes = L.N; break;
+        default: return fail(SWW_E_ARG, "unknown quantity");
+    }
+    return guarded([&]() -> int {
+        ck(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, h->stream), "get_level");
+        ck(cudaStreamSynchronize(h->stream), "get_level");
+        return SWW_OK;
+    });
+}
+
+int sww_set_level(sww_handle* h, int level, const double* dh, const double* u) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    return guarded([&]() -> int {
+        const DevLevel& L = h->lv[level];
+        if (dh) ck(cudaMemcpyAsync(L.dh, dh, L.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set dh");
+        if (u) ck(cudaMemcpyAsync(L.u, u, L.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set u");
+        ck(cudaStreamSynchronize(h->stream), "set_level");
+        return SWW_OK;
+    });
+}
+
+int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (!count) return fail(SWW_E_ARG, "null count");
+    return guarded([&]() -> int {
+        const DevLevel& L = h->lv[level];
+        ck(cudaMemcpyAsync(count, L.npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "npatches");
+        ck(cudaStreamSynchronize(h->stream), "npatches");
+        if (out && *count > 0) {
+            ck(cudaMemcpyAsync(out, L.patches, size_t(*count) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "patches");
+            ck(cudaStreamSynchronize(h->stream), "patches");
+        }
+        return SWW_OK;
+    });
+}
+
+int sww_stats_get(sww_handle* h, sww_stats* st) {
+    if (!h || !st) return fail(SWW_E_ARG, "null argument");
+    return guarded([&]() -> int {
+        std::memset(st, 0, sizeof(*st));
+        for (int j = h->cfg.jmin; j <= h->cfg.jmax && j < 16; ++j) {
+            unsigned long long c[3] = {0, 0, 0};
+            ck(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), h->stream), "memset cnt");
+            launch_count(h->lv[j], h->cnt, h->stream);
+            ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
+            int32_t np = 0;
+            ck(cudaMemcpyAsync(&np, h->lv[j].npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "np");
+            ck(cudaStreamSynchronize(h->stream), "stats");
+            st->live_nodes[j] = int64_t(c[0]);
+            st->ghost_nodes[j] = int64_t(c[1]);
+            st->live_edges[j] = int64_t(c[2]);
+            st->active_patches[j] = np;
+        }
+        const DevLevel& L0 = h->lv[h->cfg.jmin];
+        launch_sums(L0, h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
+        double s[2], th[2];
+        ck(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "sums");
+        ck(cudaMemcpyAsync(th, h->thr, sizeof(th), cudaMemcpyDeviceToHost, h->stream), "thr");
+        check_launch();
+        ck(cudaStreamSynchronize(h->stream), "stats");
+        double AS = 4.0 * M_PI * h->cfg.radius * h->cfg.radius;
+        double c2 = h->cfg.g * s[0] / AS;
+        st->mass = s[0];
+        st->energy = s[1] - 0.5 * c2 * c2 * AS;
+        st->eps_h = th[0];
+        st->eps_u = th[1];
+        st->t = h->t;
+        st->dt = h->last_dt;
+        st->steps = h->steps;
+        return SWW_OK;
+    });
+}
+
+int sww_last_error(char* buf, size_t len) {
+    if (!buf || len == 0) return SWW_E_ARG;
+    std::snprintf(buf, len, "%s", g_err.c_str());
+    return SWW_OK;
+}
+
+}  // extern "C"

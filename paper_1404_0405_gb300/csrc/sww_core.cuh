@@ -1,0 +1,52 @@
+// Device-side data of one level and the launch helpers shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace sww {
+
+// Node/edge flag bits.
+constexpr uint8_t LIVE = 1, GHOST = 2, COVERED = 4;
+constexpr uint8_t AVAIL = LIVE | GHOST;
+
+// One level on the device.  All arrays are dense over the level (see grid.h for
+// the element layout); slot-major tables store slot s of item i at s*count + i.
+struct DevLevel {
+    int J;
+    int64_t n, p, np, nelem, N, E, T, npatch;
+    // topology
+    const int32_t *en, *et;        // [2*E] origin/end node, left/right triangle
+    const int32_t *tn, *te;        // [3*T] nodes, side edges (2e + against)
+    const uint8_t* deg;            // [N]
+    const int32_t *ring_e;         // [6*N] (2e + edge points into the node), -1 padded
+    const int32_t* f2c;            // [N] coarse node at the same place (-1: odd node)
+    // geometry
+    const double *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
+    const int32_t* cor_i;          // [10*E]
+    const double* cor_w;           // [10*E]
+    // fine side of the pair (J-1, J)
+    const int32_t* par;            // [4*N] prediction parents of odd nodes (fine ids)
+    const double* ptw;             // [4*N] s~_km
+    const int8_t* fe_kind;         // [E] 0/1 half of a coarse edge, 2 interior
+    const int32_t* fe_ce;          // [E] coarse edge of a half
+    const int32_t* vst;            // [12*E] coarse stencil
+    const double* vw;              // [12*E]
+    // coarse side of the pair (J, J+1)
+    const int32_t *c2f, *mid, *half;  // [N], [E], [2*E]
+    const int32_t* mk_i;           // [12*N]
+    const double* mk_w;            // [12*N]
+    const int32_t *rf_fi, *rf_ci;  // [12*E], [11*E]
+    const double *rf_fw, *rf_cw;
+    // state and work arrays
+    double *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
+    double *F, *q, *B, *c, *Q;
+    uint8_t *nflag, *eflag, *sig, *tmask, *band0, *band1;
+    double *hdet, *ue, *ui;        // [N], [E of level J-1], [E]
+    uint8_t* pflag;                // [npatch]
+    int32_t* patches;              // [npatch]
+    int32_t* npatches;             // [1]
+};
+
+inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
+
+}  // namespace sww

@@ -1,0 +1,40 @@
+// Host-side launchers of the kernels in sww_kernels.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "sww_core.cuh"
+
+namespace sww {
+
+// One Runge-Kutta stage: y <- a*y0 + b*y + (cdt*dt)*k + (ddt*dt)*acc, acc <- al*acc + be*k.
+// apply == 0 only stores the trend k.
+struct RKStage {
+    int apply;
+    double a, b, cdt, ddt, al, be;
+};
+
+void launch_trend_level(const DevLevel& L, double H, double g, cudaStream_t s);
+void launch_restrict(const DevLevel& C, const DevLevel& F, cudaStream_t s);
+void launch_update(const DevLevel& L, const RKStage& st, const double* dt, cudaStream_t s);
+void launch_save_base(const DevLevel& L, cudaStream_t s);
+void launch_fill(const DevLevel& F, const DevLevel& C, cudaStream_t s);
+void launch_partial(const DevLevel& C, const DevLevel& F, cudaStream_t s);
+void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s);
+void launch_details(const DevLevel& F, const DevLevel& C, cudaStream_t s);
+void launch_maxabs(const DevLevel& L, unsigned long long* red, cudaStream_t s);
+void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s);
+void launch_sig(const DevLevel& F, const DevLevel& C, const double* thr, cudaStream_t s);
+void launch_adjacent(const DevLevel& F, const DevLevel& C, int children, cudaStream_t s);
+void launch_close(const DevLevel& F, const DevLevel& Fp, int has_finer, cudaStream_t s);
+void launch_live(const DevLevel& L, int all, cudaStream_t s);
+void launch_ghost_band(const DevLevel& L, int hops, cudaStream_t s);
+void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s);
+void launch_patches(const DevLevel& L, cudaStream_t s);
+void launch_inverse(const DevLevel& F, const DevLevel& C, cudaStream_t s);
+void launch_dt(const DevLevel& L, double H, double g, double dx, unsigned long long* red, cudaStream_t s);
+void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
+int sums_blocks(const DevLevel& L);
+void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s);
+void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s);
+
+}  // namespace sww
