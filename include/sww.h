@@ -84,6 +84,7 @@ typedef struct {
     int64_t ghost_nodes[16];
     int64_t live_edges[16];
     int64_t active_patches[16];
+    int64_t kernel_launches;  /* library kernel launches so far in this process            */
 } sww_stats;
 
 typedef struct sww_handle sww_handle;
@@ -116,9 +117,10 @@ int sww_adapt(sww_handle* h, double eps_h, double eps_u);
 
 /* Same mask construction from caller-provided coefficients: hdet[N_j] per
  * level j (values at odd nodes), udet_e[E_{j-1}], udet_i[E_j] (interior fine
- * edges), for j = Jmin+1..Jmax in order, host arrays concatenated by level.
- * Values are not applied to the state; only flags and patch lists change,
- * then the inverse transform runs with these coefficients. */
+ * edges), for j = Jmin+1..Jmax in order, host arrays concatenated by level,
+ * with explicit thresholds.  Significance uses the current live flags; the new
+ * flags, patch lists and the inverse transform of these coefficients onto the
+ * new live set replace the current ones (the state changes accordingly). */
 int sww_mask_from_coeffs(sww_handle* h, const double* hdet, const double* udet_e,
                          const double* udet_i, double eps_h, double eps_u);
 
@@ -143,6 +145,33 @@ int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count
 
 /* Diagnostics (synchronises the stream). */
 int sww_stats_get(sww_handle* h, sww_stats* st);
+
+/* Kernel classes timed by the tracing hook below. */
+enum {
+    SWW_K_PV = 0,        /* potential vorticity at triangles                         */
+    SWW_K_FLUX = 1,      /* thickness flux at edges                                  */
+    SWW_K_NODE = 2,      /* divergence, kinetic energy, Bernoulli at nodes           */
+    SWW_K_CORIOLIS = 3,  /* energy-conserving q F^perp at live edges                 */
+    SWW_K_RESTRICT = 4,  /* restriction of B, F, q F^perp and the coarse divergence  */
+    SWW_K_UPDATE = 5,    /* trends and Runge-Kutta stage combination                 */
+    SWW_K_FILL = 6,      /* ghost prolongation                                       */
+    SWW_K_PARTIAL = 7,   /* partial height transform                                 */
+    SWW_K_COEFF = 8,     /* wavelet coefficients                                     */
+    SWW_K_MASK = 9,      /* thresholds, significance, closure, ghosts, patches       */
+    SWW_K_INVERSE = 10,  /* inverse transform onto the new mask                      */
+    SWW_K_DT = 11,       /* CFL time step reduction                                  */
+    SWW_K_NCLASS = 12
+};
+
+/* Tracing: from now on record a pair of CUDA events on the handle's stream around
+ * every launch of the kernel classes whose bit is set in class_mask (bit k for
+ * class k); 0 stops recording.  Previous records are discarded. */
+int sww_profile(sww_handle* h, uint32_t class_mask);
+
+/* Sum of the recorded launch durations (ms[SWW_K_NCLASS]) and launch counts
+ * (launches[SWW_K_NCLASS]) per class since sww_profile; synchronises the stream
+ * and clears the records (recording continues). */
+int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
 
 /* Message of the last error on the calling thread. */
 int sww_last_error(char* buf, size_t len);

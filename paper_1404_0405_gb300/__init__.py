@@ -23,7 +23,9 @@ LIVE, GHOST, COVERED = 1, 2, 4
 RK4, SSP43 = 0, 1
 EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
-           "sww_stats_get", "sww_last_error"]
+           "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read"]
+KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
+                  "inverse", "dt"]
 
 
 class SwwError(RuntimeError):
@@ -40,7 +42,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt", ctypes.c_double), ("mass", ctypes.c_double),
                 ("energy", ctypes.c_double), ("eps_h", ctypes.c_double), ("eps_u", ctypes.c_double),
                 ("steps", ctypes.c_int64), ("live_nodes", ctypes.c_int64 * 16), ("ghost_nodes", ctypes.c_int64 * 16),
-                ("live_edges", ctypes.c_int64 * 16), ("active_patches", ctypes.c_int64 * 16)]
+                ("live_edges", ctypes.c_int64 * 16), ("active_patches", ctypes.c_int64 * 16),
+                ("kernel_launches", ctypes.c_int64)]
 
 
 _lib = None
@@ -76,6 +79,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_get_patches": [P, I, P, ctypes.POINTER(ctypes.c_int32)],
         "sww_stats_get": [P, ctypes.POINTER(Stats)],
         "sww_last_error": [ctypes.c_char_p, ctypes.c_size_t],
+        "sww_profile": [P, ctypes.c_uint32],
+        "sww_profile_read": [P, ctypes.POINTER(ctypes.c_double), I64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -204,6 +209,20 @@ class Model:
         _check(load().sww_get_patches(self._h, level, _ptr(out)[0], ctypes.byref(cnt)))
         return out[: cnt.value].copy()
 
+    def profile(self, classes=()):
+        """Start recording CUDA-event durations for the named kernel classes."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << KERNEL_CLASSES.index(c)
+        _check(load().sww_profile(self._h, mask))
+
+    def profile_read(self):
+        """{class: (total ms, launches)} since profile() / the last read."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        n = (ctypes.c_int64 * len(KERNEL_CLASSES))()
+        _check(load().sww_profile_read(self._h, ms, n))
+        return {c: (ms[i], n[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
     def stats(self):
         st = Stats()
         _check(load().sww_stats_get(self._h, ctypes.byref(st)))
@@ -211,4 +230,4 @@ class Model:
         return {"t": st.t, "dt": st.dt, "mass": st.mass, "energy": st.energy, "eps_h": st.eps_h, "eps_u": st.eps_u,
                 "steps": st.steps, "live_nodes": {j: st.live_nodes[j] for j in lv},
                 "ghost_nodes": {j: st.ghost_nodes[j] for j in lv}, "live_edges": {j: st.live_edges[j] for j in lv},
-                "active_patches": {j: st.active_patches[j] for j in lv}}
+                "active_patches": {j: st.active_patches[j] for j in lv}, "kernel_launches": st.kernel_launches}

@@ -62,6 +62,24 @@ struct sww_handle {
     double t = 0, last_dt = 0;
     int64_t steps = 0;
     bool has_state = false;
+    // tracing: per-class event pairs
+    uint32_t prof_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    cudaEvent_t take_event() {
+        if (!ev_pool.empty()) {
+            cudaEvent_t e = ev_pool.back();
+            ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        ck(cudaEventCreate(&e), "cudaEventCreate");
+        return e;
+    }
 
     template <typename T>
     T* alloc(size_t n) {
@@ -84,6 +102,8 @@ struct sww_handle {
         return up(flat);
     }
     ~sww_handle() {
+        for (auto& r : recs) cudaEventDestroy(r.a), cudaEventDestroy(r.b);
+        for (auto e : ev_pool) cudaEventDestroy(e);
         for (void* p : allocs) cudaFree(p);
     }
 };
@@ -165,11 +185,34 @@ void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side,
 
 void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
 
+// Records a pair of events around the launches made during its lifetime when the
+// handle traces class `cls`.
+struct Trace {
+    sww_handle* h;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Trace(sww_handle* h_, int c) : h(h_), cls(c) {
+        if (h->prof_mask & (1u << cls)) {
+            a = h->take_event();
+            ck(cudaEventRecord(a, h->stream), "cudaEventRecord");
+        }
+    }
+    ~Trace() {
+        if (!a) return;
+        cudaEvent_t b = h->take_event();
+        cudaEventRecord(b, h->stream);
+        h->recs.push_back({cls, a, b});
+    }
+};
+
 // ------------------------------------------------------------------ sequences
 
 void fill_ghosts(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
-    for (int j = j0 + 1; j <= j1; ++j) launch_fill(h->lv[j], h->lv[j - 1], h->stream);
+    for (int j = j0 + 1; j <= j1; ++j) {
+        Trace t(h, SWW_K_FILL);
+        launch_fill(h->lv[j], h->lv[j - 1], h->stream);
+    }
 }
 
 // one trend evaluation (Sec. 3.1): ghosts, q/K/B/F/qF^perp on every level, then the
@@ -177,15 +220,29 @@ void fill_ghosts(sww_handle* h) {
 void trend(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
     fill_ghosts(h);
-    for (int j = j0; j <= j1; ++j) launch_trend_level(h->lv[j], h->cfg.H, h->cfg.g, h->stream);
-    for (int j = j1 - 1; j >= j0; --j) launch_restrict(h->lv[j], h->lv[j + 1], h->stream);
+    for (int j = j0; j <= j1; ++j) {
+        const DevLevel& L = h->lv[j];
+        { Trace t(h, SWW_K_PV); launch_tri_q(L, h->cfg.H, h->stream); }
+        { Trace t(h, SWW_K_FLUX); launch_edge_flux(L, h->cfg.H, h->stream); }
+        { Trace t(h, SWW_K_NODE); launch_node(L, h->cfg.g, h->stream); }
+        { Trace t(h, SWW_K_CORIOLIS); launch_coriolis(L, h->stream); }
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+        Trace t(h, SWW_K_RESTRICT);
+        launch_restrict(h->lv[j], h->lv[j + 1], h->stream);
+    }
 }
 
 void update(sww_handle* h, const RKStage& st) {
-    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j) launch_update(h->lv[j], st, h->dt, h->stream);
+    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j) {
+        Trace t(h, SWW_K_UPDATE);
+        launch_update(h->lv[j], st, h->dt, h->stream);
+    }
 }
 
 void compute_dt(sww_handle* h) {
+    Trace t(h, SWW_K_DT);
+    count_launch(1);
     k_reset_red<<<1, 32, 0, h->stream>>>(h->red);
     for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j)
         launch_dt(h->lv[j], h->cfg.H, h->cfg.g, nominal_spacing(j, h->cfg.radius), h->red, h->stream);
@@ -195,6 +252,7 @@ void compute_dt(sww_handle* h) {
 void mask_and_inverse(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
     cudaStream_t s = h->stream;
+    Trace* tm = new Trace(h, SWW_K_MASK);
     // significance with the current (old) live flags
     for (int j = j0 + 1; j <= j1; ++j) {
         ck(cudaMemsetAsync(h->lv[j].sig, 0, h->lv[j].N, s), "memset sig");
@@ -209,20 +267,27 @@ void mask_and_inverse(sww_handle* h) {
     for (int j = j0 + 1; j <= j1; ++j) launch_ghost_band(h->lv[j], GHOST_HOPS, s);
     for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
     for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+    delete tm;
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
     for (int j = j0 + 1; j <= j1; ++j) {
-        launch_inverse(h->lv[j], h->lv[j - 1], s);
-        launch_fill(h->lv[j], h->lv[j - 1], s);
+        { Trace t(h, SWW_K_INVERSE); launch_inverse(h->lv[j], h->lv[j - 1], s); }
+        { Trace t(h, SWW_K_FILL); launch_fill(h->lv[j], h->lv[j - 1], s); }
     }
 }
 
 void adapt(sww_handle* h, double eh, double eu) {
     const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
     cudaStream_t s = h->stream;
-    for (int j = j0 + 1; j <= j1; ++j) launch_details(h->lv[j], h->lv[j - 1], s);
-    ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
-    for (int j = j0; j <= j1; ++j) launch_maxabs(h->lv[j], h->red, s);
-    launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
+    for (int j = j0 + 1; j <= j1; ++j) {
+        Trace t(h, SWW_K_COEFF);
+        launch_details(h->lv[j], h->lv[j - 1], s);
+    }
+    {
+        Trace t(h, SWW_K_MASK);
+        ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
+        for (int j = j0; j <= j1; ++j) launch_maxabs(h->lv[j], h->red, s);
+        launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
+    }
     mask_and_inverse(h);
 }
 
@@ -247,18 +312,26 @@ const RKStage* stages(int rk, int& n) {
 
 void one_step(sww_handle* h, double dt, bool do_adapt) {
     const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
-    if (dt > 0)
+    if (dt > 0) {
+        count_launch(1);
         k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
-    else
+    } else {
         compute_dt(h);
-    for (int j = j0; j <= j1; ++j) launch_save_base(h->lv[j], h->stream);
+    }
+    for (int j = j0; j <= j1; ++j) {
+        Trace t(h, SWW_K_UPDATE);
+        launch_save_base(h->lv[j], h->stream);
+    }
     int ns;
     const RKStage* st = stages(h->cfg.rk, ns);
     for (int k = 0; k < ns; ++k) {
         trend(h);
         update(h, st[k]);
     }
-    for (int j = j1 - 1; j >= j0; --j) launch_partial(h->lv[j], h->lv[j + 1], h->stream);
+    for (int j = j1 - 1; j >= j0; --j) {
+        Trace t(h, SWW_K_PARTIAL);
+        launch_partial(h->lv[j], h->lv[j + 1], h->stream);
+    }
     fill_ghosts(h);
     if (do_adapt) adapt(h, -1.0, -1.0);
 }
@@ -538,6 +611,35 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
         st->t = h->t;
         st->dt = h->last_dt;
         st->steps = h->steps;
+        st->kernel_launches = kernel_launches();
+        return SWW_OK;
+    });
+}
+
+int sww_profile(sww_handle* h, uint32_t class_mask) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    return guarded([&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "profile");
+        for (auto& r : h->recs) h->ev_pool.push_back(r.a), h->ev_pool.push_back(r.b);
+        h->recs.clear();
+        h->prof_mask = class_mask;
+        return SWW_OK;
+    });
+}
+
+int sww_profile_read(sww_handle* h, double* ms, int64_t* launches) {
+    if (!h || !ms || !launches) return fail(SWW_E_ARG, "null argument");
+    return guarded([&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "profile_read");
+        for (int k = 0; k < SWW_K_NCLASS; ++k) ms[k] = 0, launches[k] = 0;
+        for (auto& r : h->recs) {
+            float t = 0;
+            ck(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+            ms[r.cls] += t;
+            launches[r.cls] += 1;
+            h->ev_pool.push_back(r.a), h->ev_pool.push_back(r.b);
+        }
+        h->recs.clear();
         return SWW_OK;
     });
 }

@@ -5,6 +5,7 @@
 // leave at once after reading one flag byte.  Passages followed are cited at
 // each kernel; the readings of silent or garbled passages are those stated in
 // grid.cpp and listed with the design notes.
+#include <atomic>
 #include <cmath>
 
 #include "sww_core.cuh"
@@ -266,15 +267,16 @@ __global__ void k_details(DevLevel F, DevLevel C) {
     }
 }
 
+// block-wide reduction; `idle` is the operation's identity (fills lanes without a warp)
 template <typename T, typename Op>
-__device__ T block_reduce(T v, Op op, T* sh) {
+__device__ T block_reduce(T v, Op op, T* sh, T idle) {
     for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = v;
     __syncthreads();
     int nw = blockDim.x >> 5;
     if (w == 0) {
-        v = l < nw ? sh[l] : sh[0];
+        v = l < nw ? sh[l] : idle;
         for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
     }
     return v;
@@ -297,10 +299,10 @@ __global__ void k_maxabs(DevLevel L, unsigned long long* red) {
     unsigned long long a = 0, b = 0;
     if (i < L.N && (L.nflag[i] & LIVE)) a = dbits(fabs(L.dh[i]));
     if (i < L.E && (L.eflag[i] & LIVE)) b = dbits(fabs(L.u[i]));
-    a = block_reduce(a, MaxOp(), sh);
+    a = block_reduce(a, MaxOp(), sh, 0ull);
     if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
     __syncthreads();
-    b = block_reduce(b, MaxOp(), sh);
+    b = block_reduce(b, MaxOp(), sh, 0ull);
     if (threadIdx.x == 0 && b) atomicMax(&red[1], b);
 }
 
@@ -501,10 +503,10 @@ __global__ void k_dt(DevLevel L, double H, double g, double dx, unsigned long lo
         double au = fabs(L.u[i]);
         if (au > 0) b = dbits(dx / au);
     }
-    a = block_reduce(a, MaxOp(), sh);
+    a = block_reduce(a, MaxOp(), sh, 0ull);
     if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
     __syncthreads();
-    b = block_reduce(b, MinOp(), sh);
+    b = block_reduce(b, MinOp(), sh, ~0ull);
     if (threadIdx.x == 0 && b != ~0ull) atomicMin(&red[1], b);
 }
 
@@ -570,13 +572,13 @@ __global__ void k_count(DevLevel L, unsigned long long* cnt) {
     if (i < L.N) a = (L.nflag[i] & LIVE) ? 1 : 0, b = (L.nflag[i] & GHOST) ? 1 : 0;
     if (i < L.E) c = (L.eflag[i] & LIVE) ? 1 : 0;
     AddOp add;
-    a = block_reduce(a, add, sh);
+    a = block_reduce(a, add, sh, 0ull);
     if (threadIdx.x == 0) atomicAdd(&cnt[0], a);
     __syncthreads();
-    b = block_reduce(b, add, sh);
+    b = block_reduce(b, add, sh, 0ull);
     if (threadIdx.x == 0) atomicAdd(&cnt[1], b);
     __syncthreads();
-    c = block_reduce(c, add, sh);
+    c = block_reduce(c, add, sh, 0ull);
     if (threadIdx.x == 0) atomicAdd(&cnt[2], c);
 }
 
@@ -586,14 +588,17 @@ int64_t span(const DevLevel& L) { return L.E > L.N ? L.E : L.N; }
 
 // ---------------------------------------------------------------------------- launchers
 
-#define LAUNCH(kernel, n, ...) kernel<<<blocks_for((n), TPB), TPB, 0, s>>>(__VA_ARGS__)
+std::atomic<int64_t> g_launches{0};
 
-void launch_trend_level(const DevLevel& L, double H, double g, cudaStream_t s) {
-    LAUNCH(k_tri_q, L.T, L, H);
-    LAUNCH(k_edge_flux, L.E, L, H);
-    LAUNCH(k_node, L.N, L, g);
-    LAUNCH(k_coriolis, L.E, L);
-}
+int64_t kernel_launches() { return g_launches.load(); }
+void count_launch(int64_t n) { g_launches += n; }
+
+#define LAUNCH(kernel, n, ...) (g_launches++, kernel<<<blocks_for((n), TPB), TPB, 0, s>>>(__VA_ARGS__))
+
+void launch_tri_q(const DevLevel& L, double H, cudaStream_t s) { LAUNCH(k_tri_q, L.T, L, H); }
+void launch_edge_flux(const DevLevel& L, double H, cudaStream_t s) { LAUNCH(k_edge_flux, L.E, L, H); }
+void launch_node(const DevLevel& L, double g, cudaStream_t s) { LAUNCH(k_node, L.N, L, g); }
+void launch_coriolis(const DevLevel& L, cudaStream_t s) { LAUNCH(k_coriolis, L.E, L); }
 
 void launch_restrict(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
     LAUNCH(k_restrict, span(C), C, F);
@@ -622,6 +627,7 @@ void launch_details(const DevLevel& F, const DevLevel& C, cudaStream_t s) {
 void launch_maxabs(const DevLevel& L, unsigned long long* red, cudaStream_t s) { LAUNCH(k_maxabs, span(L), L, red); }
 
 void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s) {
+    g_launches++;
     k_thresholds<<<1, 32, 0, s>>>(red, eps, eh, eu, thr);
 }
 
@@ -660,6 +666,7 @@ void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s) { LAUN
 void launch_patches(const DevLevel& L, cudaStream_t s) {
     int t = int(L.p * L.p < 256 ? L.p * L.p : 256);
     t = t < 32 ? 32 : t;
+    g_launches += 2;
     k_patch_flags<<<unsigned(L.npatch), t, 0, s>>>(L);
     k_patch_scan<<<1, 1024, 0, s>>>(L);
 }
@@ -674,6 +681,7 @@ void launch_dt(const DevLevel& L, double H, double g, double dx, unsigned long l
 }
 
 void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
+    g_launches++;
     k_dt_final<<<1, 32, 0, s>>>(red, cfl, dt);
 }
 
@@ -681,6 +689,7 @@ int sums_blocks(const DevLevel& L) { return int(blocks_for(L.N, TPB)); }
 
 void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s) {
     int nb = sums_blocks(L);
+    g_launches += 2;
     k_sums<<<nb, TPB, 0, s>>>(L, H, g, part);
     k_sums_final<<<1, 32, 0, s>>>(part, nb, out);
 }

@@ -13,7 +13,10 @@ struct RKStage {
     double a, b, cdt, ddt, al, be;
 };
 
-void launch_trend_level(const DevLevel& L, double H, double g, cudaStream_t s);
+void launch_tri_q(const DevLevel& L, double H, cudaStream_t s);
+void launch_edge_flux(const DevLevel& L, double H, cudaStream_t s);
+void launch_node(const DevLevel& L, double g, cudaStream_t s);
+void launch_coriolis(const DevLevel& L, cudaStream_t s);
 void launch_restrict(const DevLevel& C, const DevLevel& F, cudaStream_t s);
 void launch_update(const DevLevel& L, const RKStage& st, const double* dt, cudaStream_t s);
 void launch_save_base(const DevLevel& L, cudaStream_t s);
@@ -36,5 +39,9 @@ void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cuda
 int sums_blocks(const DevLevel& L);
 void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s);
 void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s);
+// Process-wide number of library kernel launches (count_launch adds launches made
+// outside the launchers above).
+int64_t kernel_launches();
+void count_launch(int64_t n);
 
 }  // namespace sww
