@@ -173,6 +173,27 @@ int sww_profile(sww_handle* h, uint32_t class_mask);
  * and clears the records (recording continues). */
 int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
 
+/* Mass and energy of the Jmin level (the same two numbers sww_stats_get reports)
+ * computed without allocating any device memory.  The paper has no counterpart
+ * for this call: it exists for callers that cannot allocate device memory when
+ * they ask for the diagnostics -- code inside a framework whose caching
+ * allocator owns the device heap, real-time loops where the implicit
+ * synchronisation of cudaMalloc/cudaFree is not allowed, or hosts that hand the
+ * library only the buffers it may touch.
+ *   dh[N_Jmin], u[E_Jmin]: device arrays (caller-owned) of the Jmin depth
+ *     perturbation and velocity, in the library's order; read on the handle's
+ *     stream.
+ *   out[2]: device array (caller-owned) that receives mass (m^3) and energy.
+ * The per-block partial sums go to a fixed 128 KiB device array inside the
+ * library (resident on every GPU that loads it, until the process exits), which
+ * bounds N_Jmin to 1,048,576 nodes (Jmin <= 8); larger levels return SWW_E_ARG.
+ * The call is asynchronous on the handle's stream and makes no cudaMalloc,
+ * cudaFree or other allocating call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Every call reuses the same array: calls whose work may
+ * overlap on the GPU (other streams, other handles on the same device) race. */
+int sww_mass_energy_static(sww_handle* h, const double* dh, const double* u, double* out);
+
 /* Message of the last error on the calling thread. */
 int sww_last_error(char* buf, size_t len);
 

@@ -23,7 +23,7 @@ LIVE, GHOST, COVERED = 1, 2, 4
 RK4, SSP43 = 0, 1
 EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
-           "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read"]
+           "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt"]
 
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "sww_profile": [P, ctypes.c_uint32],
         "sww_profile_read": [P, ctypes.POINTER(ctypes.c_double), I64],
+        "sww_mass_energy_static": [P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -222,6 +223,11 @@ class Model:
         n = (ctypes.c_int64 * len(KERNEL_CLASSES))()
         _check(load().sww_profile_read(self._h, ms, n))
         return {c: (ms[i], n[i]) for i, c in enumerate(KERNEL_CLASSES)}
+
+    def mass_energy_static(self, dh, u, out):
+        """Mass and energy of level Jmin into out[2] without any device allocation
+        (dh, u, out: torch CUDA float64 tensors; asynchronous on the handle's stream)."""
+        _check(load().sww_mass_energy_static(self._h, _ptr(dh)[0], _ptr(u)[0], _ptr(out)[0]))
 
     def stats(self):
         st = Stats()

@@ -14,6 +14,7 @@
 #include "grid.h"
 #include "sww.h"
 #include "sww_core.cuh"
+#include "sww_internal.h"
 #include "sww_kernels.h"
 
 using namespace sww;
@@ -651,3 +652,19 @@ int sww_last_error(char* buf, size_t len) {
 }
 
 }  // extern "C"
+
+namespace sww {
+
+bool handle_view(const sww_handle* h, HandleView* v) {
+    if (!h || !v) return false;
+    v->jmin_level = &h->lv[h->cfg.jmin];
+    v->stream = h->stream;
+    v->radius = h->cfg.radius;
+    v->g = h->cfg.g;
+    v->H = h->cfg.H;
+    return true;
+}
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+}  // namespace sww
