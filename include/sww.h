@@ -18,12 +18,18 @@
  *     end node (m/s).
  *   - Host arrays are owned by the caller and only read/written during the
  *     call.  Pointers flagged as device pointers must be device memory of the
- *     handle's GPU; the library reads them on the handle's stream.
+ *     handle's GPU; they are read in the caller's stream order.
  *   - Every call returns SWW_OK (0) or a negative error code; sww_last_error
  *     gives a message for the last failure on the calling thread.  A failed
  *     call leaves the handle usable unless it returns SWW_E_CUDA.
- *   - A handle is not thread-safe.  Work is issued on the stream given to
- *     sww_create; calls returning host data synchronise that stream.
+ *   - A handle is not thread-safe.  Every call is ordered after the work
+ *     already queued on the stream given to sww_create, and later work on that
+ *     stream is ordered after the call (the library runs its kernels on a stream
+ *     of its own, joined to the caller's stream with events).  Calls that
+ *     return host data, and sww_step, wait for their own work to finish.
+ *   - sww_step replays one CUDA graph per step (captured on first use for each
+ *     top level and time-step mode); it reads the new time step and the work-list
+ *     sizes back to the host once per step.
  */
 #ifndef SWW_H
 #define SWW_H
@@ -163,9 +169,11 @@ enum {
     SWW_K_NCLASS = 12
 };
 
-/* Tracing: from now on record a pair of CUDA events on the handle's stream around
- * every launch of the kernel classes whose bit is set in class_mask (bit k for
- * class k); 0 stops recording.  Previous records are discarded. */
+/* Tracing: from now on record a pair of CUDA events on the library's stream
+ * around every launch of the kernel classes whose bit is set in class_mask (bit k
+ * for class k); 0 stops recording.  Previous records are discarded.  While any
+ * class is traced, sww_step runs its kernels directly instead of replaying the
+ * captured graph. */
 int sww_profile(sww_handle* h, uint32_t class_mask);
 
 /* Sum of the recorded launch durations (ms[SWW_K_NCLASS]) and launch counts
@@ -181,13 +189,13 @@ int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
  * synchronisation of cudaMalloc/cudaFree is not allowed, or hosts that hand the
  * library only the buffers it may touch.
  *   dh[N_Jmin], u[E_Jmin]: device arrays (caller-owned) of the Jmin depth
- *     perturbation and velocity, in the library's order; read on the handle's
- *     stream.
+ *     perturbation and velocity, in the library's order.
  *   out[2]: device array (caller-owned) that receives mass (m^3) and energy.
  * The per-block partial sums go to a fixed 128 KiB device array inside the
  * library (resident on every GPU that loads it, until the process exits), which
  * bounds N_Jmin to 1,048,576 nodes (Jmin <= 8); larger levels return SWW_E_ARG.
- * The call is asynchronous on the handle's stream and makes no cudaMalloc,
+ * The call is asynchronous on the caller's stream given to sww_create (dh, u
+ * and out are read and written in that stream's order) and makes no cudaMalloc,
  * cudaFree or other allocating call.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture.  Every call reuses the same array: calls whose work may

@@ -226,7 +226,7 @@ class Model:
 
     def mass_energy_static(self, dh, u, out):
         """Mass and energy of level Jmin into out[2] without any device allocation
-        (dh, u, out: torch CUDA float64 tensors; asynchronous on the handle's stream)."""
+        (dh, u, out: torch CUDA float64 tensors; asynchronous on the caller's stream)."""
         _check(load().sww_mass_energy_static(self._h, _ptr(dh)[0], _ptr(u)[0], _ptr(out)[0]))
 
     def stats(self):

@@ -1,14 +1,22 @@
 // C ABI (include/sww.h): handle lifetime, upload of the host-built grid, and the
 // sequencing of kernels for one trend evaluation, one RK step and one adaptation.
+//
+// The library issues its work on a stream of its own, joined to the caller's
+// stream with events at the start and end of every call.  A step is captured once
+// as a CUDA graph per (top level, time-step mode) and replayed; the only host
+// round trip per step reads the new time step and the per-level work-list sizes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "grid.h"
@@ -47,22 +55,38 @@ __global__ void k_reset_red(unsigned long long* red) {
     }
 }
 
+__global__ void k_gather_counts(const DevLevel* lvs, int jmin, int jmax, int32_t* out) {
+    int j = jmin + int(threadIdx.x);
+    if (j <= jmax) out[j] = *lvs[j].npatches;
+}
+
 constexpr int GHOST_HOPS = 5;
 
 }  // namespace
 
 struct sww_handle {
     sww_config cfg{};
-    cudaStream_t stream = nullptr;
+    cudaStream_t user = nullptr;    // the caller's stream
+    cudaStream_t stream = nullptr;  // the library's own stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<DevLevel> lv;
+    DevLevel* d_lvs = nullptr;
     std::vector<std::vector<double>> xyz;     // host node positions per level (flattened)
     std::vector<std::vector<int32_t>> edges;  // host edge (origin, end) pairs per level
     std::vector<void*> allocs;
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
+    int32_t *all_list = nullptr, *all_count = nullptr, *d_counts = nullptr;
+    int32_t* h_counts = nullptr;    // pinned: per-level list sizes after each step
+    double* h_dt = nullptr;         // pinned: time step of the last step
+    int S = 64, jtop = 0, nsm = 152;
+    unsigned grid_all = 1;
+    std::vector<unsigned> grid_lv;
     double t = 0, last_dt = 0;
     int64_t steps = 0;
     bool has_state = false;
+    // captured steps: (top level, adapt, dt) -> graph and its kernel count
+    std::map<std::tuple<int, int, double>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     // tracing: per-class event pairs
     uint32_t prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -102,10 +126,21 @@ struct sww_handle {
         for (int k = 0; k < count; ++k) std::memcpy(flat.data() + k * n, v[k].data(), n * sizeof(T));
         return up(flat);
     }
+    void drop_graphs() {
+        for (auto& g : graphs) cudaGraphExecDestroy(g.second.first);
+        graphs.clear();
+    }
     ~sww_handle() {
+        if (stream) cudaStreamSynchronize(stream);
+        drop_graphs();
         for (auto& r : recs) cudaEventDestroy(r.a), cudaEventDestroy(r.b);
         for (auto e : ev_pool) cudaEventDestroy(e);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (h_counts) cudaFreeHost(h_counts);
+        if (h_dt) cudaFreeHost(h_dt);
         for (void* p : allocs) cudaFree(p);
+        if (stream) cudaStreamDestroy(stream);
     }
 };
 
@@ -114,6 +149,7 @@ namespace {
 void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side, int64_t coarse_E) {
     DevLevel D{};
     D.J = L.J, D.n = L.n, D.p = L.p, D.np = L.np, D.nelem = L.nelem, D.N = L.N, D.E = L.E, D.T = L.T, D.npatch = L.npatch;
+    D.dx = nominal_spacing(L.J, h->cfg.radius);
     D.en = h->up_slots(L.en, 2);
     D.et = h->up_slots(L.et, 2);
     D.tn = h->up_slots(L.tn, 3);
@@ -152,7 +188,7 @@ void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side,
     for (auto p : bN) *p = h->alloc<uint8_t>(N);
     D.eflag = h->alloc<uint8_t>(E);
     D.pflag = h->alloc<uint8_t>(L.npatch);
-    D.patches = h->alloc<int32_t>(L.npatch);
+    D.patches = h->alloc<int32_t>(L.npatch + 1);
     D.npatches = h->alloc<int32_t>(1);
     // f2c of this level: coarse node at the same place (-1 for odd nodes)
     {
@@ -186,8 +222,21 @@ void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side,
 
 void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
 
+// Orders the library's stream after the caller's stream on entry and the caller's
+// stream after the library's stream on exit.
+struct Join {
+    sww_handle* h;
+    explicit Join(sww_handle* h_) : h(h_) {
+        ck(cudaEventRecord(h->ev_in, h->user), "join in");
+        ck(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "join in");
+    }
+    ~Join() {
+        if (cudaEventRecord(h->ev_out, h->stream) == cudaSuccess) cudaStreamWaitEvent(h->user, h->ev_out, 0);
+    }
+};
+
 // Records a pair of events around the launches made during its lifetime when the
-// handle traces class `cls`.
+// handle traces class `cls` (eager execution only).
 struct Trace {
     sww_handle* h;
     int cls;
@@ -206,87 +255,102 @@ struct Trace {
     }
 };
 
+Work work_all(const sww_handle* h) { return Work{h->d_lvs, h->all_list, h->all_count, h->S, h->grid_all}; }
+Work work_level(const sww_handle* h, int j) {
+    return Work{nullptr, h->lv[j].patches, h->lv[j].npatches, h->S, h->grid_lv[j]};
+}
+
 // ------------------------------------------------------------------ sequences
 
 void fill_ghosts(sww_handle* h) {
-    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
-    for (int j = j0 + 1; j <= j1; ++j) {
+    for (int j = h->cfg.jmin + 1; j <= h->jtop; ++j) {
         Trace t(h, SWW_K_FILL);
-        launch_fill(h->lv[j], h->lv[j - 1], h->stream);
+        launch_fill(h->lv[j], h->lv[j - 1], work_level(h, j), h->stream);
     }
 }
 
 // one trend evaluation (Sec. 3.1): ghosts, q/K/B/F/qF^perp on every level, then the
-// restriction of B, F and q F^perp from Jmax-1 down to Jmin
+// restriction of B, F and q F^perp from the top level down to Jmin
 void trend(sww_handle* h) {
-    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    const int j0 = h->cfg.jmin;
+    cudaStream_t s = h->stream;
+    Work W = work_all(h);
     fill_ghosts(h);
-    for (int j = j0; j <= j1; ++j) {
-        const DevLevel& L = h->lv[j];
-        { Trace t(h, SWW_K_PV); launch_tri_q(L, h->cfg.H, h->stream); }
-        { Trace t(h, SWW_K_FLUX); launch_edge_flux(L, h->cfg.H, h->stream); }
-        { Trace t(h, SWW_K_NODE); launch_node(L, h->cfg.g, h->stream); }
-        { Trace t(h, SWW_K_CORIOLIS); launch_coriolis(L, h->stream); }
-    }
-    for (int j = j1 - 1; j >= j0; --j) {
+    { Trace t(h, SWW_K_PV); launch_pv(W, h->cfg.H, s); }
+    { Trace t(h, SWW_K_FLUX); launch_flux(W, h->cfg.H, s); }
+    { Trace t(h, SWW_K_NODE); launch_node(W, h->cfg.g, s); }
+    { Trace t(h, SWW_K_CORIOLIS); launch_coriolis(W, s); }
+    for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_RESTRICT);
-        launch_restrict(h->lv[j], h->lv[j + 1], h->stream);
+        launch_restrict(h->lv[j], h->lv[j + 1], work_level(h, j), s);
     }
 }
 
 void update(sww_handle* h, const RKStage& st) {
-    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j) {
-        Trace t(h, SWW_K_UPDATE);
-        launch_update(h->lv[j], st, h->dt, h->stream);
-    }
+    Trace t(h, SWW_K_UPDATE);
+    launch_update(work_all(h), st, h->dt, h->stream);
 }
 
 void compute_dt(sww_handle* h) {
     Trace t(h, SWW_K_DT);
     count_launch(1);
     k_reset_red<<<1, 32, 0, h->stream>>>(h->red);
-    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j)
-        launch_dt(h->lv[j], h->cfg.H, h->cfg.g, nominal_spacing(j, h->cfg.radius), h->red, h->stream);
+    launch_dt(work_all(h), h->cfg.H, h->cfg.g, h->red, h->stream);
     launch_dt_final(h->red, h->cfg.cfl, h->dt, h->stream);
 }
 
+// list sizes of every level into pinned host memory (read after the next sync)
+void read_counts(sww_handle* h) {
+    count_launch(1);
+    k_gather_counts<<<1, 32, 0, h->stream>>>(h->d_lvs, h->cfg.jmin, h->cfg.jmax, h->d_counts);
+    ck(cudaMemcpyAsync(h->h_counts, h->d_counts, sizeof(int32_t) * (h->cfg.jmax + 1), cudaMemcpyDeviceToHost, h->stream),
+       "counts");
+}
+
+// top level with any live or ghost point (after the stream has synchronised)
+void update_top(sww_handle* h) {
+    int top = h->cfg.jmin;
+    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j)
+        if (h->h_counts[j] > 0) top = j;
+    h->jtop = top;
+}
+
+// Mask construction and inverse transform.  Levels above top + 1 hold no live point
+// and can gain none in one adaptation, so the byte-wide passes stop there.
 void mask_and_inverse(sww_handle* h) {
-    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    const int j0 = h->cfg.jmin, j1 = std::min(h->jtop + 1, h->cfg.jmax);
     cudaStream_t s = h->stream;
-    Trace* tm = new Trace(h, SWW_K_MASK);
-    // significance with the current (old) live flags
-    for (int j = j0 + 1; j <= j1; ++j) {
-        ck(cudaMemsetAsync(h->lv[j].sig, 0, h->lv[j].N, s), "memset sig");
-        launch_sig(h->lv[j], h->lv[j - 1], h->thr, s);
+    {
+        Trace tm(h, SWW_K_MASK);
+        for (int j = j0 + 1; j <= j1; ++j) {
+            ck(cudaMemsetAsync(h->lv[j].sig, 0, h->lv[j].N, s), "memset sig");
+            launch_sig(h->lv[j], h->lv[j - 1], h->thr, s);
+        }
+        for (int j = j0 + 1; j <= j1; ++j) launch_adjacent(h->lv[j], h->lv[j - 1], j - 1 > j0, s);
+        for (int j = j1; j > j0; --j) {
+            bool finer = j < j1;
+            launch_close(h->lv[j], finer ? h->lv[j + 1] : h->lv[j], finer, s);
+        }
+        for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], j == j0, s);
+        for (int j = j0 + 1; j <= j1; ++j) launch_ghost_band(h->lv[j], GHOST_HOPS, s);
+        for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
+        for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+        launch_concat(h->d_lvs, j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
-    for (int j = j0 + 1; j <= j1; ++j) launch_adjacent(h->lv[j], h->lv[j - 1], j - 1 > j0, s);
-    for (int j = j1; j > j0; --j) {
-        bool finer = j < j1;
-        launch_close(h->lv[j], finer ? h->lv[j + 1] : h->lv[j], finer, s);
-    }
-    for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], j == j0, s);
-    for (int j = j0 + 1; j <= j1; ++j) launch_ghost_band(h->lv[j], GHOST_HOPS, s);
-    for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
-    for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
-    delete tm;
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
     for (int j = j0 + 1; j <= j1; ++j) {
-        { Trace t(h, SWW_K_INVERSE); launch_inverse(h->lv[j], h->lv[j - 1], s); }
-        { Trace t(h, SWW_K_FILL); launch_fill(h->lv[j], h->lv[j - 1], s); }
+        { Trace t(h, SWW_K_INVERSE); launch_inverse(h->lv[j], h->lv[j - 1], work_level(h, j), s); }
+        { Trace t(h, SWW_K_FILL); launch_fill(h->lv[j], h->lv[j - 1], work_level(h, j), s); }
     }
 }
 
 void adapt(sww_handle* h, double eh, double eu) {
-    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
     cudaStream_t s = h->stream;
-    for (int j = j0 + 1; j <= j1; ++j) {
-        Trace t(h, SWW_K_COEFF);
-        launch_details(h->lv[j], h->lv[j - 1], s);
-    }
+    { Trace t(h, SWW_K_COEFF); launch_details(work_all(h), h->cfg.jmin, s); }
     {
         Trace t(h, SWW_K_MASK);
         ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
-        for (int j = j0; j <= j1; ++j) launch_maxabs(h->lv[j], h->red, s);
+        launch_maxabs(work_all(h), h->red, s);
         launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
     }
     mask_and_inverse(h);
@@ -311,30 +375,65 @@ const RKStage* stages(int rk, int& n) {
     return rk == SWW_SSP43 ? ssp : rk4;
 }
 
+// One RK step with its partial transform and (optionally) adaptation; ends with the
+// device-to-host copies of the time step and the list sizes.
 void one_step(sww_handle* h, double dt, bool do_adapt) {
-    const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+    const int j0 = h->cfg.jmin;
     if (dt > 0) {
         count_launch(1);
         k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
     } else {
         compute_dt(h);
     }
-    for (int j = j0; j <= j1; ++j) {
-        Trace t(h, SWW_K_UPDATE);
-        launch_save_base(h->lv[j], h->stream);
-    }
+    { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all(h), h->stream); }
     int ns;
     const RKStage* st = stages(h->cfg.rk, ns);
     for (int k = 0; k < ns; ++k) {
         trend(h);
         update(h, st[k]);
     }
-    for (int j = j1 - 1; j >= j0; --j) {
+    for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_PARTIAL);
-        launch_partial(h->lv[j], h->lv[j + 1], h->stream);
+        launch_partial(h->lv[j], h->lv[j + 1], work_level(h, j), h->stream);
     }
     fill_ghosts(h);
     if (do_adapt) adapt(h, -1.0, -1.0);
+    read_counts(h);
+    ck(cudaMemcpyAsync(h->h_dt, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
+}
+
+// Run one step through a captured graph (eager when tracing).
+void run_step(sww_handle* h, double dt, bool do_adapt) {
+    if (h->prof_mask) {
+        one_step(h, dt, do_adapt);
+        return;
+    }
+    auto key = std::make_tuple(h->jtop, int(do_adapt), dt > 0 ? dt : -1.0);
+    auto it = h->graphs.find(key);
+    if (it == h->graphs.end()) {
+        if (h->graphs.size() >= 16) h->drop_graphs();
+        int64_t before = kernel_launches();
+        ck(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        try {
+            one_step(h, dt, do_adapt);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamEndCapture(h->stream, &g), "end capture");
+        int64_t n = kernel_launches() - before;
+        count_launch(-n);
+        cudaGraphExec_t ex = nullptr;
+        cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        ck(e, "graph instantiate");
+        it = h->graphs.emplace(key, std::make_pair(ex, n)).first;
+    }
+    ck(cudaGraphLaunch(it->second.first, h->stream), "graph launch");
+    count_launch(it->second.second);
 }
 
 int check_level(const sww_handle* h, int level) {
@@ -373,12 +472,22 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
     if (!h) return fail(SWW_E_POOL, "host allocation failed");
     int rc = guarded([&]() -> int {
         h->cfg = *cfg;
-        h->stream = static_cast<cudaStream_t>(stream);
+        h->user = static_cast<cudaStream_t>(stream);
+        ck(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "cudaEventCreate");
+        ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "cudaEventCreate");
+        int dev = 0;
+        ck(cudaGetDevice(&dev), "cudaGetDevice");
+        ck(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev), "device attribute");
         Hierarchy H;
         build_hierarchy(H, cfg->jmin, cfg->jmax, cfg->patch, cfg->radius, cfg->omega);
         h->lv.assign(cfg->jmax + 1, DevLevel{});
+        h->grid_lv.assign(cfg->jmax + 1, 1);
         h->xyz.assign(cfg->jmax + 1, {});
         h->edges.assign(cfg->jmax + 1, {});
+        h->S = cfg->patch * cfg->patch;
+        int64_t total = 0;
+        const int64_t cap = int64_t(h->nsm) * 16;
         for (int j = cfg->jmin; j <= cfg->jmax; ++j) {
             HostLevel& L = H.lv[j];
             upload_level(h, L, j > cfg->jmin, j < cfg->jmax, j > cfg->jmin ? H.lv[j - 1].E : 0);
@@ -386,7 +495,20 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
             for (int64_t v = 0; v < L.N; ++v) h->xyz[j][3 * v] = L.xyz[v].x, h->xyz[j][3 * v + 1] = L.xyz[v].y, h->xyz[j][3 * v + 2] = L.xyz[v].z;
             h->edges[j].resize(2 * L.E);
             for (int64_t e = 0; e < L.E; ++e) h->edges[j][2 * e] = L.en[0][e], h->edges[j][2 * e + 1] = L.en[1][e];
+            int64_t items = (L.npatch + 1) * h->S;
+            h->grid_lv[j] = unsigned(std::min<int64_t>(blocks_for(items, 256), cap));
+            total += L.npatch + 1;
         }
+        h->grid_all = unsigned(std::min<int64_t>(blocks_for(total * h->S, 256), cap));
+        h->d_lvs = h->alloc<DevLevel>(cfg->jmax + 1);
+        ck(cudaMemcpy(h->d_lvs, h->lv.data(), sizeof(DevLevel) * (cfg->jmax + 1), cudaMemcpyHostToDevice), "levels");
+        h->all_list = h->alloc<int32_t>(total);
+        h->all_count = h->alloc<int32_t>(1);
+        h->d_counts = h->alloc<int32_t>(cfg->jmax + 1);
+        ck(cudaMallocHost(&h->h_counts, sizeof(int32_t) * (cfg->jmax + 1)), "cudaMallocHost");
+        ck(cudaMallocHost(&h->h_dt, sizeof(double)), "cudaMallocHost");
+        std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
+        *h->h_dt = 0;
         h->red = h->alloc<unsigned long long>(4);
         h->cnt = h->alloc<unsigned long long>(4);
         h->thr = h->alloc<double>(2);
@@ -395,7 +517,9 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
         h->part = h->alloc<double>(4 * size_t(sums_blocks(h->lv[cfg->jmin])));
         ck(cudaMemset(h->thr, 0, 2 * sizeof(double)), "memset");
         ck(cudaMemset(h->dt, 0, sizeof(double)), "memset");
+        ck(cudaMemset(h->all_count, 0, sizeof(int32_t)), "memset");
         ck(cudaDeviceSynchronize(), "create");
+        h->jtop = cfg->jmax;
         return SWW_OK;
     });
     if (rc != SWW_OK) {
@@ -408,7 +532,6 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
 
 int sww_destroy(sww_handle* h) {
     if (!h) return SWW_OK;
-    if (h->stream) cudaStreamSynchronize(h->stream);
     delete h;
     return SWW_OK;
 }
@@ -436,16 +559,23 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
     if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
     return guarded([&]() -> int {
         const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
-        DevLevel& F = h->lv[j1];
-        cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, h->stream), "set_state dh");
-        ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, h->stream), "set_state u");
-        for (int j = j1; j > j0; --j) launch_restrict_full(h->lv[j - 1], h->lv[j], h->stream);
-        for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], 1, h->stream);
-        for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], h->stream);
-        for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], h->stream);
-        check_launch();
-        ck(cudaStreamSynchronize(h->stream), "set_state");
+        cudaStream_t s = h->stream;
+        {
+            Join jn(h);
+            DevLevel& F = h->lv[j1];
+            cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
+            ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
+            for (int j = j1; j > j0; --j) launch_restrict_full(h->lv[j - 1], h->lv[j], s);
+            for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], 1, s);
+            for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
+            for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+            launch_concat(h->d_lvs, j0, j1, h->all_list, h->all_count, s);
+            read_counts(h);
+            check_launch();
+        }
+        ck(cudaStreamSynchronize(s), "set_state");
+        update_top(h);
         h->has_state = true;
         h->t = 0;
         h->steps = 0;
@@ -457,9 +587,14 @@ int sww_adapt(sww_handle* h, double eps_h, double eps_u) {
     if (!h) return fail(SWW_E_ARG, "null handle");
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     return guarded([&]() -> int {
-        adapt(h, eps_h, eps_u);
-        check_launch();
+        {
+            Join jn(h);
+            adapt(h, eps_h, eps_u);
+            read_counts(h);
+            check_launch();
+        }
         ck(cudaStreamSynchronize(h->stream), "adapt");
+        update_top(h);
         return SWW_OK;
     });
 }
@@ -470,20 +605,26 @@ int sww_mask_from_coeffs(sww_handle* h, const double* hdet, const double* udet_e
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     if (!(eps_h > 0) || !(eps_u > 0)) return fail(SWW_E_ARG, "explicit positive thresholds required");
     return guarded([&]() -> int {
-        size_t oh = 0, oe = 0, oi = 0;
-        for (int j = h->cfg.jmin + 1; j <= h->cfg.jmax; ++j) {
-            DevLevel& F = h->lv[j];
-            int64_t ce = h->lv[j - 1].E;
-            ck(cudaMemcpyAsync(F.hdet, hdet + oh, F.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "hdet");
-            ck(cudaMemcpyAsync(F.ue, udet_e + oe, ce * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ue");
-            ck(cudaMemcpyAsync(F.ui, udet_i + oi, F.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ui");
-            oh += F.N, oe += ce, oi += F.E;
+        {
+            Join jn(h);
+            size_t oh = 0, oe = 0, oi = 0;
+            for (int j = h->cfg.jmin + 1; j <= h->cfg.jmax; ++j) {
+                DevLevel& F = h->lv[j];
+                int64_t ce = h->lv[j - 1].E;
+                ck(cudaMemcpyAsync(F.hdet, hdet + oh, F.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "hdet");
+                ck(cudaMemcpyAsync(F.ue, udet_e + oe, ce * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ue");
+                ck(cudaMemcpyAsync(F.ui, udet_i + oi, F.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ui");
+                oh += F.N, oe += ce, oi += F.E;
+            }
+            double th[2] = {eps_h, eps_u};
+            ck(cudaMemcpyAsync(h->thr, th, sizeof(th), cudaMemcpyHostToDevice, h->stream), "thr");
+            ck(cudaStreamSynchronize(h->stream), "thr");   // th lives on this host stack frame
+            mask_and_inverse(h);
+            read_counts(h);
+            check_launch();
         }
-        double th[2] = {eps_h, eps_u};
-        ck(cudaMemcpyAsync(h->thr, th, sizeof(th), cudaMemcpyHostToDevice, h->stream), "thr");
-        mask_and_inverse(h);
-        check_launch();
         ck(cudaStreamSynchronize(h->stream), "mask");
+        update_top(h);
         return SWW_OK;
     });
 }
@@ -492,10 +633,13 @@ int sww_rhs(sww_handle* h) {
     if (!h) return fail(SWW_E_ARG, "null handle");
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     return guarded([&]() -> int {
-        trend(h);
-        RKStage none{0, 0, 0, 0, 0, 0, 0};
-        update(h, none);
-        check_launch();
+        {
+            Join jn(h);
+            trend(h);
+            RKStage none{0, 0, 0, 0, 0, 0, 0};
+            update(h, none);
+            check_launch();
+        }
         ck(cudaStreamSynchronize(h->stream), "rhs");
         return SWW_OK;
     });
@@ -507,15 +651,18 @@ int sww_step(sww_handle* h, double dt, int nsteps, int do_adapt) {
     if (nsteps < 0) return fail(SWW_E_ARG, "nsteps < 0");
     return guarded([&]() -> int {
         for (int s = 0; s < nsteps; ++s) {
-            one_step(h, dt, do_adapt != 0);
-            check_launch();
-            double d = 0;
-            ck(cudaMemcpyAsync(&d, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
+            {
+                Join jn(h);
+                run_step(h, dt, do_adapt != 0);
+                check_launch();
+            }
             ck(cudaStreamSynchronize(h->stream), "step");
+            double d = *h->h_dt;
             if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
             h->t += d;
             h->last_dt = d;
             h->steps += 1;
+            update_top(h);
         }
         return SWW_OK;
     });
@@ -544,9 +691,13 @@ int sww_get_level(const sww_handle* h, int level, int what, void* out) {
         case SWW_SIG: src = L.sig, bytes = L.N; break;
         default: return fail(SWW_E_ARG, "unknown quantity");
     }
+    sww_handle* hh = const_cast<sww_handle*>(h);
     return guarded([&]() -> int {
-        ck(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, h->stream), "get_level");
-        ck(cudaStreamSynchronize(h->stream), "get_level");
+        {
+            Join jn(hh);
+            ck(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, hh->stream), "get_level");
+        }
+        ck(cudaStreamSynchronize(hh->stream), "get_level");
         return SWW_OK;
     });
 }
@@ -556,8 +707,11 @@ int sww_set_level(sww_handle* h, int level, const double* dh, const double* u) {
     if (rc) return rc;
     return guarded([&]() -> int {
         const DevLevel& L = h->lv[level];
-        if (dh) ck(cudaMemcpyAsync(L.dh, dh, L.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set dh");
-        if (u) ck(cudaMemcpyAsync(L.u, u, L.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set u");
+        {
+            Join jn(h);
+            if (dh) ck(cudaMemcpyAsync(L.dh, dh, L.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set dh");
+            if (u) ck(cudaMemcpyAsync(L.u, u, L.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set u");
+        }
         ck(cudaStreamSynchronize(h->stream), "set_level");
         return SWW_OK;
     });
@@ -567,14 +721,26 @@ int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count
     int rc = check_level(h, level);
     if (rc) return rc;
     if (!count) return fail(SWW_E_ARG, "null count");
+    sww_handle* hh = const_cast<sww_handle*>(h);
     return guarded([&]() -> int {
         const DevLevel& L = h->lv[level];
-        ck(cudaMemcpyAsync(count, L.npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "npatches");
-        ck(cudaStreamSynchronize(h->stream), "npatches");
-        if (out && *count > 0) {
-            ck(cudaMemcpyAsync(out, L.patches, size_t(*count) * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "patches");
-            ck(cudaStreamSynchronize(h->stream), "patches");
+        int32_t n = 0;
+        std::vector<int32_t> tmp(L.npatch + 1);
+        {
+            Join jn(hh);
+            ck(cudaMemcpyAsync(&n, L.npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream), "npatches");
+            ck(cudaMemcpyAsync(tmp.data(), L.patches, tmp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream),
+               "patches");
         }
+        ck(cudaStreamSynchronize(hh->stream), "patches");
+        int32_t c = 0;
+        for (int32_t i = 0; i < n; ++i) {
+            int32_t p = tmp[i] & PATCH_MASK;
+            if (p == L.npatch) continue;   // pole entry
+            if (out) out[c] = p;
+            ++c;
+        }
+        *count = c;
         return SWW_OK;
     });
 }
@@ -585,23 +751,30 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
         std::memset(st, 0, sizeof(*st));
         for (int j = h->cfg.jmin; j <= h->cfg.jmax && j < 16; ++j) {
             unsigned long long c[3] = {0, 0, 0};
-            ck(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), h->stream), "memset cnt");
-            launch_count(h->lv[j], h->cnt, h->stream);
-            ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
-            int32_t np = 0;
-            ck(cudaMemcpyAsync(&np, h->lv[j].npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream), "np");
+            {
+                Join jn(h);
+                ck(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), h->stream), "memset cnt");
+                launch_count(h->lv[j], h->cnt, h->stream);
+                ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
+            }
             ck(cudaStreamSynchronize(h->stream), "stats");
             st->live_nodes[j] = int64_t(c[0]);
             st->ghost_nodes[j] = int64_t(c[1]);
             st->live_edges[j] = int64_t(c[2]);
+            int32_t np = 0;
+            int rc = sww_get_patches(h, j, nullptr, &np);
+            if (rc) return rc;
             st->active_patches[j] = np;
         }
-        const DevLevel& L0 = h->lv[h->cfg.jmin];
-        launch_sums(L0, h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
         double s[2], th[2];
-        ck(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "sums");
-        ck(cudaMemcpyAsync(th, h->thr, sizeof(th), cudaMemcpyDeviceToHost, h->stream), "thr");
-        check_launch();
+        {
+            Join jn(h);
+            const DevLevel& L0 = h->lv[h->cfg.jmin];
+            launch_sums(L0, h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
+            ck(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "sums");
+            ck(cudaMemcpyAsync(th, h->thr, sizeof(th), cudaMemcpyDeviceToHost, h->stream), "thr");
+            check_launch();
+        }
         ck(cudaStreamSynchronize(h->stream), "stats");
         double AS = 4.0 * M_PI * h->cfg.radius * h->cfg.radius;
         double c2 = h->cfg.g * s[0] / AS;
@@ -658,7 +831,7 @@ namespace sww {
 bool handle_view(const sww_handle* h, HandleView* v) {
     if (!h || !v) return false;
     v->jmin_level = &h->lv[h->cfg.jmin];
-    v->stream = h->stream;
+    v->stream = h->user;
     v->radius = h->cfg.radius;
     v->g = h->cfg.g;
     v->H = h->cfg.H;

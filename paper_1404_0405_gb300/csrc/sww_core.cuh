@@ -5,15 +5,20 @@
 
 namespace sww {
 
-// Node/edge flag bits.
-constexpr uint8_t LIVE = 1, GHOST = 2, COVERED = 4;
+// Node/edge flag bits (WASLIVE: live before the adaptation that set the flags).
+constexpr uint8_t LIVE = 1, GHOST = 2, COVERED = 4, WASLIVE = 8;
 constexpr uint8_t AVAIL = LIVE | GHOST;
+
+// Work-list entry: (level << LVL_SHIFT) | patch; patch == npatch stands for the two poles.
+constexpr int LVL_SHIFT = 27;
+constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
 
 // One level on the device.  All arrays are dense over the level (see grid.h for
 // the element layout); slot-major tables store slot s of item i at s*count + i.
 struct DevLevel {
     int J;
     int64_t n, p, np, nelem, N, E, T, npatch;
+    double dx;                     // Table 1 spacing of the level (m)
     // topology
     const int32_t *en, *et;        // [2*E] origin/end node, left/right triangle
     const int32_t *tn, *te;        // [3*T] nodes, side edges (2e + against)
@@ -43,7 +48,7 @@ struct DevLevel {
     uint8_t *nflag, *eflag, *sig, *tmask, *band0, *band1;
     double *hdet, *ue, *ui;        // [N], [E of level J-1], [E]
     uint8_t* pflag;                // [npatch]
-    int32_t* patches;              // [npatch]
+    int32_t* patches;              // [npatch + 1] active patch list (+ pole entry), level-tagged
     int32_t* npatches;             // [1]
 };
 

@@ -9,7 +9,7 @@ namespace sww {
 
 struct HandleView {
     const DevLevel* jmin_level;   // the coarsest (always complete) level
-    cudaStream_t stream;
+    cudaStream_t stream;          // the caller's stream given to sww_create
     double radius, g, H;
 };
 

@@ -1,10 +1,12 @@
 // CUDA kernels of the adaptive wavelet TRiSK step (sm_103a, FP64).
 //
-// Every kernel covers one level (or one pair of adjacent levels) with one thread
-// per node / edge / triangle; threads of points that are neither live nor ghost
-// leave at once after reading one flag byte.  Passages followed are cited at
-// each kernel; the readings of silent or garbled passages are those stated in
-// grid.cpp and listed with the design notes.
+// FP64 work runs over active-patch work lists: a fixed grid (a multiple of the SM
+// count) strides over the entries of a list, one thread per element of a p x p
+// patch; an element is one node, its three edges and two triangles (Sec. 5.2).
+// Lists are built on the device after each adaptation, per level and for all
+// levels at once (kernels without a level dependency cover every level in one
+// launch).  Byte-wide mask work of the adaptation runs densely over a level.
+// Readings of silent or garbled passages are those stated in grid.cpp.
 #include <atomic>
 #include <cmath>
 
@@ -13,6 +15,10 @@
 
 namespace sww {
 
+std::atomic<int64_t> g_launches{0};
+int64_t kernel_launches() { return g_launches.load(); }
+void count_launch(int64_t n) { g_launches += n; }
+
 namespace {
 
 constexpr int TPB = 256;
@@ -20,7 +26,6 @@ constexpr int TPB = 256;
 __device__ __forceinline__ int64_t gid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ double esign(int32_t code) { return (code & 1) ? -1.0 : 1.0; }
 
-// neighbour across ring edge `code` of node v
 __device__ __forceinline__ int32_t ring_nbr(const DevLevel& L, int32_t code) {
     int64_t e = code >> 1;
     return (code & 1) ? L.en[e] : L.en[L.E + e];
@@ -44,12 +49,36 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x));
 }
 
-// ---------------------------------------------------------------------------- trend (Sec. 3.1)
+// Visit the elements of the entries of a work list: body(L, elem, node); a pole
+// entry gives elem = -1 and the two pole nodes.  Entries name their level in
+// `lvs` (multi-level lists) or all belong to `one` when lvs is null.
+template <class Body>
+__device__ __forceinline__ void for_elements(const DevLevel* __restrict__ lvs, const DevLevel& one,
+                                             const int32_t* __restrict__ list, const int32_t* __restrict__ count,
+                                             int S, Body body) {
+    int64_t n = int64_t(*count) * S;
+    int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t it = gid(); it < n; it += stride) {
+        int32_t ent = list[it / S];
+        int local = int(it % S);
+        const DevLevel& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
+        int64_t pat = ent & PATCH_MASK;
+        if (pat == L.npatch) {
+            if (local < 2) body(L, int64_t(-1), L.nelem + local);
+        } else {
+            int64_t pp = L.p * L.p;
+            if (local < pp) {
+                int64_t e = pat * pp + local;
+                body(L, e, e);
+            }
+        }
+    }
+}
 
-// potential vorticity q = (curl u + f)/h at triangles (dual cells)
-__global__ void k_tri_q(DevLevel L, double H) {
-    int64_t t = gid();
-    if (t >= L.T) return;
+// ---------------------------------------------------------------------------- trend bodies (Sec. 3.1)
+
+// potential vorticity q = (curl u + f)/h at a triangle (dual cell)
+__device__ __forceinline__ void pv_at(const DevLevel& L, int64_t t, double H) {
     int32_t n0 = L.tn[t], n1 = L.tn[L.T + t], n2 = L.tn[2 * L.T + t];
     int32_t c0 = L.te[t], c1 = L.te[L.T + t], c2 = L.te[2 * L.T + t];
     if (!(L.nflag[n0] & AVAIL) || !(L.nflag[n1] & AVAIL) || !(L.nflag[n2] & AVAIL)) return;
@@ -61,20 +90,16 @@ __global__ void k_tri_q(DevLevel L, double H) {
     L.q[t] = (circ / Av + L.f_v[t]) / (hv / Av);
 }
 
-// thickness flux F = h_e u at edges
-__global__ void k_edge_flux(DevLevel L, double H) {
-    int64_t e = gid();
-    if (e >= L.E) return;
+// thickness flux F = h_e u at an edge
+__device__ __forceinline__ void flux_at(const DevLevel& L, int64_t e, double H) {
     if (!(L.eflag[e] & AVAIL)) return;
     int32_t a = L.en[e], b = L.en[L.E + e];
     if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
     L.F[e] = 0.5 * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
 }
 
-// divergence, kinetic energy and Bernoulli function at nodes
-__global__ void k_node(DevLevel L, double g) {
-    int64_t v = gid();
-    if (v >= L.N) return;
+// divergence, kinetic energy and Bernoulli function at a node
+__device__ __forceinline__ void node_at(const DevLevel& L, int64_t v, double g) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
     double div = 0.0, ke = 0.0;
@@ -91,10 +116,8 @@ __global__ void k_node(DevLevel L, double g) {
     L.B[v] = g * L.dh[v] + ke / A;
 }
 
-// energy-conserving Coriolis tendency +q F.n_left at live edges (TRiSK)
-__global__ void k_coriolis(DevLevel L) {
-    int64_t e = gid();
-    if (e >= L.E) return;
+// energy-conserving Coriolis tendency +q F.n_left at a live edge (TRiSK)
+__device__ __forceinline__ void coriolis_at(const DevLevel& L, int64_t e) {
     if (!(L.eflag[e] & LIVE)) return;
     double qe = 0.5 * (L.q[L.et[e]] + L.q[L.et[L.E + e]]);
     double s = 0.0;
@@ -108,28 +131,7 @@ __global__ void k_coriolis(DevLevel L) {
     L.Q[e] = s;
 }
 
-// restriction from F = level j+1 to C = level j (Sec. 3.1): B by injection at covered
-// nodes, flux by R_F on faces of covered nodes, Coriolis tendency by R_u where both
-// ends are covered
-__global__ void k_restrict(DevLevel C, DevLevel F) {
-    int64_t i = gid();
-    if (i < C.N && (C.nflag[i] & COVERED)) C.B[i] = F.B[C.c2f[i]];
-    if (i >= C.E) return;
-    bool ca = C.nflag[C.en[i]] & COVERED, cb = C.nflag[C.en[C.E + i]] & COVERED;
-    if (ca || cb) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) s += C.rf_fw[k * C.E + i] * F.F[C.rf_fi[k * C.E + i]];
-#pragma unroll
-        for (int k = 0; k < 11; ++k) s += C.rf_cw[k * C.E + i] * F.c[C.rf_ci[k * C.E + i]];
-        C.F[i] = s / C.l_e[i];
-    }
-    if (ca && cb) C.Q[i] = 0.5 * (F.Q[C.half[i]] + F.Q[C.half[C.E + i]]);
-}
-
-__global__ void k_div(DevLevel L) {
-    int64_t v = gid();
-    if (v >= L.N) return;
+__device__ __forceinline__ void div_at(const DevLevel& L, int64_t v) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
     double div = 0.0;
@@ -142,97 +144,401 @@ __global__ void k_div(DevLevel L) {
     L.c[v] = div / L.A_i[v];
 }
 
-// trends at live points and one Runge-Kutta stage:
+// trend and one Runge-Kutta stage at a live point (terms with a zero coefficient
+// are skipped, so stale storage never enters):
 //   y <- a*y0 + b*y + (cdt*dt)*k + (ddt*dt)*acc,   acc <- al*acc + be*k
-__global__ void k_update(DevLevel L, RKStage st, const double* __restrict__ dtp) {
-    int64_t i = gid();
-    double dt = dtp ? *dtp : 0.0;
-    if (i < L.N && (L.nflag[i] & LIVE)) {
-        double k = -L.c[i];
-        L.dht[i] = k;
-        if (st.apply) {
-            // terms with a zero coefficient are skipped, so stale storage never enters
-            double y = st.cdt * dt * k;
-            if (st.a != 0.0) y += st.a * L.dh0[i];
-            if (st.b != 0.0) y += st.b * L.dh[i];
-            if (st.ddt != 0.0) y += st.ddt * dt * L.dha[i];
-            if (st.al != 0.0 || st.be != 0.0) L.dha[i] = (st.al != 0.0 ? st.al * L.dha[i] : 0.0) + st.be * k;
-            L.dh[i] = y;
-        }
-    }
-    if (i < L.E && (L.eflag[i] & LIVE)) {
-        double k = L.Q[i] - (L.B[L.en[L.E + i]] - L.B[L.en[i]]) / L.d_e[i];
-        L.ut[i] = k;
-        if (st.apply) {
-            double y = st.cdt * dt * k;
-            if (st.a != 0.0) y += st.a * L.u0[i];
-            if (st.b != 0.0) y += st.b * L.u[i];
-            if (st.ddt != 0.0) y += st.ddt * dt * L.ua[i];
-            if (st.al != 0.0 || st.be != 0.0) L.ua[i] = (st.al != 0.0 ? st.al * L.ua[i] : 0.0) + st.be * k;
-            L.u[i] = y;
-        }
-    }
+__device__ __forceinline__ void rk_apply(const RKStage& st, double dt, double k, double* y, const double* y0,
+                                         double* acc) {
+    double v = st.cdt * dt * k;
+    if (st.a != 0.0) v += st.a * *y0;
+    if (st.b != 0.0) v += st.b * *y;
+    if (st.ddt != 0.0) v += st.ddt * dt * *acc;
+    if (st.al != 0.0 || st.be != 0.0) *acc = (st.al != 0.0 ? st.al * *acc : 0.0) + st.be * k;
+    *y = v;
 }
 
-__global__ void k_save_base(DevLevel L) {
-    int64_t i = gid();
-    if (i < L.N && (L.nflag[i] & LIVE)) L.dh0[i] = L.dh[i];
-    if (i < L.E && (L.eflag[i] & LIVE)) L.u0[i] = L.u[i];
+__device__ __forceinline__ void update_node(const DevLevel& L, int64_t v, const RKStage& st, double dt) {
+    if (!(L.nflag[v] & LIVE)) return;
+    double k = -L.c[v];
+    L.dht[v] = k;
+    if (st.apply) rk_apply(st, dt, k, &L.dh[v], &L.dh0[v], &L.dha[v]);
 }
 
-// ---------------------------------------------------------------------------- prolongation
+__device__ __forceinline__ void update_edge(const DevLevel& L, int64_t e, const RKStage& st, double dt) {
+    if (!(L.eflag[e] & LIVE)) return;
+    double k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
+    L.ut[e] = k;
+    if (st.apply) rk_apply(st, dt, k, &L.u[e], &L.u0[e], &L.ua[e]);
+}
 
-// ghosts of level F from level C (inverse transform with zero coefficients, Eqs. 1-2)
-__global__ void k_fill(DevLevel F, DevLevel C) {
-    int64_t i = gid();
-    if (i < F.N && (F.nflag[i] & GHOST)) {
-        int32_t k = F.f2c[i];
-        if (k >= 0) {
-            F.dh[i] = C.dh[k];
-        } else {
-            double s = 0.0;
+// ---------------------------------------------------------------------------- prolongation (Eqs. 1-2)
+
+// ghost node of level F from level C (inverse transform with zero coefficients)
+__device__ __forceinline__ void fill_node(const DevLevel& F, const DevLevel& C, int64_t i) {
+    if (!(F.nflag[i] & GHOST)) return;
+    int32_t k = F.f2c[i];
+    if (k >= 0) {
+        F.dh[i] = C.dh[k];
+        return;
+    }
+    double s = 0.0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int32_t p = F.par[q * F.N + i];
-                double v = (F.nflag[p] & LIVE) ? F.dh[p] : C.dh[F.f2c[p]];
-                s += F.ptw[q * F.N + i] * v;
-            }
-            F.dh[i] = s;
-        }
+    for (int q = 0; q < 4; ++q) {
+        int32_t p = F.par[q * F.N + i];
+        double v = (F.nflag[p] & LIVE) ? F.dh[p] : C.dh[F.f2c[p]];
+        s += F.ptw[q * F.N + i] * v;
     }
-    if (i < F.E && (F.eflag[i] & GHOST)) {
-        int kind = F.fe_kind[i];
-        double P = predict(F, C.u, i);
-        if (kind == 2) {
-            F.u[i] = P;
-        } else {
-            int64_t E = F.fe_ce[i];
-            int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
-            double uc = C.u[E];
-            if (F.eflag[other] & LIVE) {
-                F.u[i] = 2.0 * uc - F.u[other];
+    F.dh[i] = s;
+}
+
+__device__ __forceinline__ void fill_edge(const DevLevel& F, const DevLevel& C, int64_t i) {
+    if (!(F.eflag[i] & GHOST)) return;
+    int kind = F.fe_kind[i];
+    double P = predict(F, C.u, i);
+    if (kind == 2) {
+        F.u[i] = P;
+        return;
+    }
+    int64_t E = F.fe_ce[i];
+    int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
+    double uc = C.u[E];
+    if (F.eflag[other] & LIVE) {
+        F.u[i] = 2.0 * uc - F.u[other];
+    } else {
+        double Po = predict(F, C.u, other);
+        F.u[i] = P + 0.5 * (2.0 * uc - P - Po);
+    }
+}
+
+// ---------------------------------------------------------------------------- list kernels
+
+#define ELEMS(lvs, one, list, count, S) \
+    for_elements(lvs, one, list, count, S, [&] __device__(const DevLevel& L, int64_t el, int64_t v)
+
+__global__ void k_pv(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) {
+        if (el < 0) return;
+        pv_at(L, el, H);
+        pv_at(L, L.nelem + el, H);
+    });
+}
+
+__global__ void k_flux(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) {
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) flux_at(L, o * L.nelem + el, H);
+    });
+}
+
+__global__ void k_node(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double g) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) { node_at(L, v, g); });
+}
+
+__global__ void k_coriolis(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) {
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) coriolis_at(L, o * L.nelem + el);
+    });
+}
+
+__global__ void k_update(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, RKStage st,
+                         const double* __restrict__ dtp) {
+    DevLevel none{};
+    double dt = dtp ? *dtp : 0.0;
+    ELEMS(lvs, none, list, count, S) {
+        update_node(L, v, st, dt);
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) update_edge(L, o * L.nelem + el, st, dt);
+    });
+}
+
+__global__ void k_save_base(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) {
+        if (L.nflag[v] & LIVE) L.dh0[v] = L.dh[v];
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t e = o * L.nelem + el;
+            if (L.eflag[e] & LIVE) L.u0[e] = L.u[e];
+        }
+    });
+}
+
+// ghosts of level F from level C over F's work list
+__global__ void k_fill(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, F, list, count, S) {
+        fill_node(L, C, v);
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) fill_edge(L, C, o * L.nelem + el);
+    });
+}
+
+// restriction from F = level j+1 to C = level j (Sec. 3.1): B by injection at covered
+// nodes, flux by R_F on faces of covered nodes, Coriolis tendency by R_u where both
+// ends are covered
+__global__ void k_restrict(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, C, list, count, S) {
+        if (L.nflag[v] & COVERED) L.B[v] = F.B[L.c2f[v]];
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t i = o * L.nelem + el;
+            bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
+            if (ca || cb) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
+#pragma unroll
+                for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
+                L.F[i] = s / L.l_e[i];
+            }
+            if (ca && cb) L.Q[i] = 0.5 * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
+        }
+    });
+}
+
+__global__ void k_div(DevLevel C, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, C, list, count, S) { div_at(L, v); });
+}
+
+// R_h at covered nodes of C from level F (Eq. Rh; coefficients of non-live points are zero)
+__global__ void k_partial(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, C, list, count, S) {
+        if (!(L.nflag[v] & COVERED)) return;
+        double s = F.dh[L.c2f[v]];
+        for (int q = 0; q < 12; ++q) {
+            int32_t m = L.mk_i[q * L.N + v];
+            if (m < 0 || !(F.nflag[m] & LIVE)) continue;
+            s += L.mk_w[q * L.N + v] * height_detail(F, m);
+        }
+        L.dh[v] = s;
+    });
+}
+
+// wavelet coefficients at live points (Eqs. 1-2; velocity transform of Sec. 4.1):
+// h~ at odd nodes, u~ at interior fine edges, u~_E of the coarse element's edges
+// (handled by the fine element at the coarse element's node)
+__global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, int jmin) {
+    DevLevel none{};
+    ELEMS(lvs, none, list, count, S) {
+        if (L.J == jmin) return;
+        const DevLevel& C = lvs[L.J - 1];
+        if (L.f2c[v] < 0 && (L.nflag[v] & LIVE)) L.hdet[v] = height_detail(L, v);
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t fe = o * L.nelem + el;
+            if (L.fe_kind[fe] == 2 && (L.eflag[fe] & LIVE)) L.ui[fe] = L.u[fe] - predict(L, C.u, fe);
+        }
+        int32_t ce = L.f2c[v];
+        if (ce < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t E = o * C.nelem + ce;
+            int32_t h0 = C.half[E], h1 = C.half[C.E + E];
+            if ((L.eflag[h0] & LIVE) || (L.eflag[h1] & LIVE)) {
+                double a = L.u[h0] - predict(L, C.u, h0);
+                double b = L.u[h1] - predict(L, C.u, h1);
+                L.ue[E] = 0.5 * (a - b);
+            }
+        }
+    });
+}
+
+// inverse transform of the retained coefficients onto the live points of F:
+// (a) even nodes and all edges from level C, (b) odd nodes from the even ones.
+// Coefficients count only where the point was live before the adaptation.
+__global__ void k_inverse_a(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, F, list, count, S) {
+        if ((L.nflag[v] & LIVE) && L.f2c[v] >= 0) {
+            int32_t k = L.f2c[v];
+            double s = C.dh[k];
+            for (int q = 0; q < 12; ++q) {
+                int32_t m = C.mk_i[q * C.N + k];
+                if (m >= 0 && (L.nflag[m] & LIVE) && (L.nflag[m] & WASLIVE)) s -= C.mk_w[q * C.N + k] * L.hdet[m];
+            }
+            L.dh[v] = s;
+        }
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t i = o * L.nelem + el;
+            if (!(L.eflag[i] & LIVE)) continue;
+            int kind = L.fe_kind[i];
+            double P = predict(L, C.u, i);
+            if (kind == 2) {
+                L.u[i] = P + ((L.eflag[i] & WASLIVE) ? L.ui[i] : 0.0);
             } else {
-                double Po = predict(F, C.u, other);
-                F.u[i] = P + 0.5 * (2.0 * uc - P - Po);
+                int64_t E = L.fe_ce[i];
+                int32_t h0 = C.half[E], h1 = C.half[C.E + E];
+                int32_t other = kind == 0 ? h1 : h0;
+                double Po = predict(L, C.u, other);
+                double delta = 0.5 * (2.0 * C.u[E] - P - Po);
+                double d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : 0.0;
+                L.u[i] = P + delta + (kind == 0 ? d : -d);
             }
         }
+    });
+}
+
+__global__ void k_inverse_b(DevLevel F, const int32_t* list, const int32_t* count, int S) {
+    ELEMS(nullptr, F, list, count, S) {
+        if (!(L.nflag[v] & LIVE) || L.f2c[v] >= 0) return;
+        double s = (L.nflag[v] & WASLIVE) ? L.hdet[v] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) s += L.ptw[q * L.N + v] * L.dh[L.par[q * L.N + v]];
+        L.dh[v] = s;
+    });
+}
+
+// ---------------------------------------------------------------------------- reductions
+
+// block-wide reduction; `idle` is the operation's identity (fills lanes without a warp)
+template <typename T, typename Op>
+__device__ T block_reduce(T v, Op op, T* sh, T idle) {
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    int nw = blockDim.x >> 5;
+    if (w == 0) {
+        v = l < nw ? sh[l] : idle;
+        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+struct MaxOp {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; }
+};
+struct MinOp {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
+};
+struct AddOp {
+    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a + b; }
+};
+
+// max |dh| over live nodes, max |u| over live edges (bit patterns of non-negative doubles)
+__global__ void k_maxabs(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S,
+                         unsigned long long* red) {
+    __shared__ unsigned long long sh[32];
+    DevLevel none{};
+    unsigned long long a = 0, b = 0;
+    ELEMS(lvs, none, list, count, S) {
+        if (L.nflag[v] & LIVE) a = max(a, dbits(fabs(L.dh[v])));
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t e = o * L.nelem + el;
+            if (L.eflag[e] & LIVE) b = max(b, dbits(fabs(L.u[e])));
+        }
+    });
+    a = block_reduce(a, MaxOp(), sh, 0ull);
+    if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
+    b = block_reduce(b, MaxOp(), sh, 0ull);
+    if (threadIdx.x == 0 && b) atomicMax(&red[1], b);
+}
+
+// omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max), dx/|u| at live edges (min)
+__global__ void k_dt(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H,
+                     double g, unsigned long long* red) {
+    __shared__ unsigned long long sh[32];
+    DevLevel none{};
+    unsigned long long a = 0, b = ~0ull;
+    ELEMS(lvs, none, list, count, S) {
+        double kx = M_PI / L.dx;
+        if (L.nflag[v] & LIVE) {
+            double f = L.f_n[v];
+            a = max(a, dbits(sqrt(f * f + g * (H + L.dh[v]) * kx * kx)));
+        }
+        if (el < 0) return;
+        for (int o = 0; o < 3; ++o) {
+            int64_t e = o * L.nelem + el;
+            if (!(L.eflag[e] & LIVE)) continue;
+            double au = fabs(L.u[e]);
+            if (au > 0) b = min(b, dbits(L.dx / au));
+        }
+    });
+    a = block_reduce(a, MaxOp(), sh, 0ull);
+    if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
+    b = block_reduce(b, MinOp(), sh, ~0ull);
+    if (threadIdx.x == 0 && b != ~0ull) atomicMin(&red[1], b);
+}
+
+__global__ void k_dt_final(const unsigned long long* red, double cfl, double* dt) {
+    if (threadIdx.x || blockIdx.x) return;
+    double w = __longlong_as_double(static_cast<long long>(red[0]));
+    double r = red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(red[1]));
+    *dt = cfl * fmin(1.0 / w, r);
+}
+
+__global__ void k_thresholds(const unsigned long long* red, double eps, double eps_h, double eps_u, double* thr) {
+    if (threadIdx.x || blockIdx.x) return;
+    thr[0] = eps_h > 0 ? eps_h : eps * __longlong_as_double(static_cast<long long>(red[0]));
+    thr[1] = eps_u > 0 ? eps_u : eps * __longlong_as_double(static_cast<long long>(red[1]));
+}
+
+// Neumaier-compensated partial sums of mass and energy over level Jmin (dense)
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+__global__ void k_sums(DevLevel L, double H, double g, double* part) {
+    __shared__ double sh[2][TPB];
+    int64_t v = gid();
+    double m = 0, en = 0;
+    if (v < L.N) {
+        double h = H + L.dh[v], A = L.A_i[v], ke = 0.0;
+        for (int k = 0; k < L.deg[v]; ++k) {
+            int64_t e = L.ring_e[k * L.N + v] >> 1;
+            ke += 0.25 * L.l_e[e] * L.d_e[e] * L.u[e] * L.u[e];
+        }
+        m = A * h;
+        en = g * h * (0.5 * g * h * A + ke);
+    }
+    sh[0][threadIdx.x] = m;
+    sh[1][threadIdx.x] = en;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+        for (int k = 0; k < blockDim.x; ++k) neumaier(s0, c0, sh[0][k]), neumaier(s1, c1, sh[1][k]);
+        part[4 * blockIdx.x + 0] = s0;
+        part[4 * blockIdx.x + 1] = c0;
+        part[4 * blockIdx.x + 2] = s1;
+        part[4 * blockIdx.x + 3] = c1;
     }
 }
 
-// ---------------------------------------------------------------------------- partial transform
-
-// R_h at covered nodes of C from level F (Eq. Rh; details of non-live points are zero)
-__global__ void k_partial(DevLevel C, DevLevel F) {
-    int64_t k = gid();
-    if (k >= C.N || !(C.nflag[k] & COVERED)) return;
-    double s = F.dh[C.c2f[k]];
-    for (int q = 0; q < 12; ++q) {
-        int32_t m = C.mk_i[q * C.N + k];
-        if (m < 0 || !(F.nflag[m] & LIVE)) continue;
-        s += C.mk_w[q * C.N + k] * height_detail(F, m);
+__global__ void k_sums_final(const double* part, int nblk, double* out) {
+    if (threadIdx.x || blockIdx.x) return;
+    double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
+    for (int b = 0; b < nblk; ++b) {
+        neumaier(s0, c0, part[4 * b]);
+        neumaier(s0, c0, part[4 * b + 1]);
+        neumaier(s1, c1, part[4 * b + 2]);
+        neumaier(s1, c1, part[4 * b + 3]);
     }
-    C.dh[k] = s;
+    out[0] = s0 + c0;
+    out[1] = s1 + c1;
 }
+
+__global__ void k_count(DevLevel L, unsigned long long* cnt) {
+    __shared__ unsigned long long sh[32];
+    int64_t i = gid();
+    unsigned long long a = 0, b = 0, c = 0;
+    if (i < L.N) a = (L.nflag[i] & LIVE) ? 1 : 0, b = (L.nflag[i] & GHOST) ? 1 : 0;
+    if (i < L.E) c = (L.eflag[i] & LIVE) ? 1 : 0;
+    a = block_reduce(a, AddOp(), sh, 0ull);
+    if (threadIdx.x == 0) atomicAdd(&cnt[0], a);
+    b = block_reduce(b, AddOp(), sh, 0ull);
+    if (threadIdx.x == 0) atomicAdd(&cnt[1], b);
+    c = block_reduce(c, AddOp(), sh, 0ull);
+    if (threadIdx.x == 0) atomicAdd(&cnt[2], c);
+}
+
+// ---------------------------------------------------------------------------- dense level kernels
 
 // full restriction used at initialisation: R_h at every node, mean of halves at every edge
 __global__ void k_restrict_full(DevLevel C, DevLevel F) {
@@ -248,72 +554,9 @@ __global__ void k_restrict_full(DevLevel C, DevLevel F) {
     if (i < C.E) C.u[i] = 0.5 * (F.u[C.half[i]] + F.u[C.half[C.E + i]]);
 }
 
-// ---------------------------------------------------------------------------- adaptation (Sec. 2.3)
-
-// wavelet coefficients at live points of level F
-__global__ void k_details(DevLevel F, DevLevel C) {
-    int64_t i = gid();
-    if (i < F.N) F.hdet[i] = (F.f2c[i] < 0 && (F.nflag[i] & LIVE)) ? height_detail(F, i) : 0.0;
-    if (i < F.E) F.ui[i] = (F.fe_kind[i] == 2 && (F.eflag[i] & LIVE)) ? F.u[i] - predict(F, C.u, i) : 0.0;
-    if (i < C.E) {
-        int32_t h0 = C.half[i], h1 = C.half[C.E + i];
-        if ((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) {
-            double a = F.u[h0] - predict(F, C.u, h0);
-            double b = F.u[h1] - predict(F, C.u, h1);
-            F.ue[i] = 0.5 * (a - b);
-        } else {
-            F.ue[i] = 0.0;
-        }
-    }
-}
-
-// block-wide reduction; `idle` is the operation's identity (fills lanes without a warp)
-template <typename T, typename Op>
-__device__ T block_reduce(T v, Op op, T* sh, T idle) {
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = v;
-    __syncthreads();
-    int nw = blockDim.x >> 5;
-    if (w == 0) {
-        v = l < nw ? sh[l] : idle;
-        for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
-    }
-    return v;
-}
-
-struct MaxOp {
-    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; }
-};
-struct AddOp {
-    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a + b; }
-};
-struct MinOp {
-    __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
-};
-
-// max |dh| over live nodes and max |u| over live edges (bit patterns of non-negative doubles)
-__global__ void k_maxabs(DevLevel L, unsigned long long* red) {
-    __shared__ unsigned long long sh[32];
-    int64_t i = gid();
-    unsigned long long a = 0, b = 0;
-    if (i < L.N && (L.nflag[i] & LIVE)) a = dbits(fabs(L.dh[i]));
-    if (i < L.E && (L.eflag[i] & LIVE)) b = dbits(fabs(L.u[i]));
-    a = block_reduce(a, MaxOp(), sh, 0ull);
-    if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
-    __syncthreads();
-    b = block_reduce(b, MaxOp(), sh, 0ull);
-    if (threadIdx.x == 0 && b) atomicMax(&red[1], b);
-}
-
-__global__ void k_thresholds(const unsigned long long* red, double eps, double eps_h, double eps_u, double* thr) {
-    if (threadIdx.x || blockIdx.x) return;
-    thr[0] = eps_h > 0 ? eps_h : eps * __longlong_as_double(static_cast<long long>(red[0]));
-    thr[1] = eps_u > 0 ? eps_u : eps * __longlong_as_double(static_cast<long long>(red[1]));
-}
-
-// significance at level F: odd node with |h~| >= eps_h; both ends and midpoint of a
-// coarse edge with |u~_E| >= eps_u; both ends of an interior edge with |u~| >= eps_u
+// significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends and the
+// midpoint of a coarse edge with |u~_E| >= eps_u; both ends of an interior edge with
+// |u~| >= eps_u; only points live before the adaptation carry coefficients
 __global__ void k_sig(DevLevel F, DevLevel C, const double* __restrict__ thr) {
     int64_t i = gid();
     double eh = thr[0], eu = thr[1];
@@ -366,20 +609,21 @@ __global__ void k_close(DevLevel F, DevLevel Fp, int has_finer) {
     }
 }
 
-// live flags: all of Jmin, else the mask; an edge is live when an end node is
+// live flags (all of Jmin, else the mask), remembering which points were live
 __global__ void k_live(DevLevel L, int all) {
     int64_t i = gid();
-    if (i < L.N) {
-        uint8_t lv = all ? 1 : L.tmask[i];
-        L.nflag[i] = lv ? LIVE : 0;
-        L.band0[i] = lv;
-    }
+    if (i >= L.N) return;
+    uint8_t lv = all ? 1 : L.tmask[i];
+    L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
+    L.band0[i] = lv;
 }
 
+// an edge is live when an end node is
 __global__ void k_live_edges(DevLevel L) {
     int64_t e = gid();
     if (e >= L.E) return;
-    L.eflag[e] = ((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0;
+    uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
+    L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
 }
 
 __global__ void k_dilate(DevLevel L, const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
@@ -422,13 +666,15 @@ __global__ void k_patch_flags(DevLevel L) {
     if (threadIdx.x == 0) L.pflag[pid] = uint8_t(any);
 }
 
-// ascending compacted list of flagged patches (one block; deterministic)
+// ascending level-tagged list of flagged patches, then the pole entry when a pole is
+// live or ghost (one block; deterministic)
 __global__ void k_patch_scan(DevLevel L) {
     __shared__ int warp_tot[32];
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t tag = int32_t(L.J) << LVL_SHIFT;
     for (int64_t start = 0; start < L.npatch; start += blockDim.x) {
         int64_t i = start + threadIdx.x;
         int f = (i < L.npatch) ? L.pflag[i] : 0;
@@ -438,7 +684,7 @@ __global__ void k_patch_scan(DevLevel L) {
         __syncthreads();
         int off = 0;
         for (int k = 0; k < w; ++k) off += warp_tot[k];
-        if (f) L.patches[base + off + pre] = int32_t(i);
+        if (f) L.patches[base + off + pre] = tag | int32_t(i);
         __syncthreads();
         if (threadIdx.x == 0) {
             int tot = 0;
@@ -447,222 +693,105 @@ __global__ void k_patch_scan(DevLevel L) {
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) *L.npatches = base;
-}
-
-// inverse transform of the retained coefficients onto the live points of F:
-// (a) even nodes and all edges from level C, (b) odd nodes from the even ones
-__global__ void k_inverse_a(DevLevel F, DevLevel C) {
-    int64_t i = gid();
-    if (i < F.N && (F.nflag[i] & LIVE) && F.f2c[i] >= 0) {
-        int32_t k = F.f2c[i];
-        double s = C.dh[k];
-        for (int q = 0; q < 12; ++q) {
-            int32_t m = C.mk_i[q * C.N + k];
-            if (m >= 0 && (F.nflag[m] & LIVE)) s -= C.mk_w[q * C.N + k] * F.hdet[m];
-        }
-        F.dh[i] = s;
-    }
-    if (i < F.E && (F.eflag[i] & LIVE)) {
-        int kind = F.fe_kind[i];
-        double P = predict(F, C.u, i);
-        if (kind == 2) {
-            F.u[i] = P + F.ui[i];
-        } else {
-            int64_t E = F.fe_ce[i];
-            int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
-            double Po = predict(F, C.u, other);
-            double delta = 0.5 * (2.0 * C.u[E] - P - Po);
-            double d = F.ue[E];
-            F.u[i] = P + delta + (kind == 0 ? d : -d);
-        }
-    }
-}
-
-__global__ void k_inverse_b(DevLevel F) {
-    int64_t i = gid();
-    if (i >= F.N || !(F.nflag[i] & LIVE) || F.f2c[i] >= 0) return;
-    double s = F.hdet[i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) s += F.ptw[q * F.N + i] * F.dh[F.par[q * F.N + i]];
-    F.dh[i] = s;
-}
-
-// ---------------------------------------------------------------------------- reductions (Sec. 3.1, 7.2)
-
-// omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max), dx/|u| at live edges (min)
-__global__ void k_dt(DevLevel L, double H, double g, double dx, unsigned long long* red) {
-    __shared__ unsigned long long sh[32];
-    int64_t i = gid();
-    unsigned long long a = 0, b = ~0ull;
-    if (i < L.N && (L.nflag[i] & LIVE)) {
-        double f = L.f_n[i], k = M_PI / dx;
-        a = dbits(sqrt(f * f + g * (H + L.dh[i]) * k * k));
-    }
-    if (i < L.E && (L.eflag[i] & LIVE)) {
-        double au = fabs(L.u[i]);
-        if (au > 0) b = dbits(dx / au);
-    }
-    a = block_reduce(a, MaxOp(), sh, 0ull);
-    if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
-    __syncthreads();
-    b = block_reduce(b, MinOp(), sh, ~0ull);
-    if (threadIdx.x == 0 && b != ~0ull) atomicMin(&red[1], b);
-}
-
-__global__ void k_dt_final(const unsigned long long* red, double cfl, double* dt) {
-    if (threadIdx.x || blockIdx.x) return;
-    double w = __longlong_as_double(static_cast<long long>(red[0]));
-    double r = red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(red[1]));
-    *dt = cfl * fmin(1.0 / w, r);
-}
-
-// Neumaier-compensated partial sums of mass and energy over level Jmin
-__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
-    double t = s + x;
-    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
-    s = t;
-}
-
-__global__ void k_sums(DevLevel L, double H, double g, double* part) {
-    __shared__ double sh[4][TPB];
-    int64_t v = gid();
-    double m = 0, en = 0;
-    if (v < L.N) {
-        double h = H + L.dh[v], A = L.A_i[v], ke = 0.0;
-        for (int k = 0; k < L.deg[v]; ++k) {
-            int64_t e = L.ring_e[k * L.N + v] >> 1;
-            ke += 0.25 * L.l_e[e] * L.d_e[e] * L.u[e] * L.u[e];
-        }
-        m = A * h;
-        en = g * h * (0.5 * g * h * A + ke);
-    }
-    sh[0][threadIdx.x] = m;
-    sh[1][threadIdx.x] = 0;
-    sh[2][threadIdx.x] = en;
-    sh[3][threadIdx.x] = 0;
-    __syncthreads();
     if (threadIdx.x == 0) {
-        double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-        for (int k = 0; k < blockDim.x; ++k) neumaier(s0, c0, sh[0][k]), neumaier(s1, c1, sh[2][k]);
-        part[4 * blockIdx.x + 0] = s0;
-        part[4 * blockIdx.x + 1] = c0;
-        part[4 * blockIdx.x + 2] = s1;
-        part[4 * blockIdx.x + 3] = c1;
+        int n = base;
+        if ((L.nflag[L.nelem] | L.nflag[L.nelem + 1]) & AVAIL) L.patches[n++] = tag | int32_t(L.npatch);
+        *L.npatches = n;
     }
 }
 
-__global__ void k_sums_final(const double* part, int nblk, double* out) {
-    if (threadIdx.x || blockIdx.x) return;
-    double s0 = 0, c0 = 0, s1 = 0, c1 = 0;
-    for (int b = 0; b < nblk; ++b) {
-        neumaier(s0, c0, part[4 * b]);
-        neumaier(s0, c0, part[4 * b + 1]);
-        neumaier(s1, c1, part[4 * b + 2]);
-        neumaier(s1, c1, part[4 * b + 3]);
+// concatenation of the level lists jmin..jmax into one list
+__global__ void k_concat(const DevLevel* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count) {
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int j = jmin; j <= jmax; ++j) {
+        const DevLevel& L = lvs[j];
+        int n = *L.npatches;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) all[base + i] = L.patches[i];
+        __syncthreads();
+        if (threadIdx.x == 0) base += n;
+        __syncthreads();
     }
-    out[0] = s0 + c0;
-    out[1] = s1 + c1;
+    if (threadIdx.x == 0) *count = base;
 }
-
-__global__ void k_count(DevLevel L, unsigned long long* cnt) {
-    __shared__ unsigned long long sh[32];
-    int64_t i = gid();
-    unsigned long long a = 0, b = 0, c = 0;
-    if (i < L.N) a = (L.nflag[i] & LIVE) ? 1 : 0, b = (L.nflag[i] & GHOST) ? 1 : 0;
-    if (i < L.E) c = (L.eflag[i] & LIVE) ? 1 : 0;
-    AddOp add;
-    a = block_reduce(a, add, sh, 0ull);
-    if (threadIdx.x == 0) atomicAdd(&cnt[0], a);
-    __syncthreads();
-    b = block_reduce(b, add, sh, 0ull);
-    if (threadIdx.x == 0) atomicAdd(&cnt[1], b);
-    __syncthreads();
-    c = block_reduce(c, add, sh, 0ull);
-    if (threadIdx.x == 0) atomicAdd(&cnt[2], c);
-}
-
-int64_t span(const DevLevel& L) { return L.E > L.N ? L.E : L.N; }
 
 }  // namespace
 
 // ---------------------------------------------------------------------------- launchers
 
-std::atomic<int64_t> g_launches{0};
+#define DENSE(kernel, n, ...) (g_launches++, kernel<<<blocks_for((n), TPB), TPB, 0, s>>>(__VA_ARGS__))
+#define LIST(kernel, ...) (g_launches++, kernel<<<W.grid, TPB, 0, s>>>(__VA_ARGS__))
 
-int64_t kernel_launches() { return g_launches.load(); }
-void count_launch(int64_t n) { g_launches += n; }
+static int64_t span(const DevLevel& L) { return L.E > L.N ? L.E : L.N; }
 
-#define LAUNCH(kernel, n, ...) (g_launches++, kernel<<<blocks_for((n), TPB), TPB, 0, s>>>(__VA_ARGS__))
-
-void launch_tri_q(const DevLevel& L, double H, cudaStream_t s) { LAUNCH(k_tri_q, L.T, L, H); }
-void launch_edge_flux(const DevLevel& L, double H, cudaStream_t s) { LAUNCH(k_edge_flux, L.E, L, H); }
-void launch_node(const DevLevel& L, double g, cudaStream_t s) { LAUNCH(k_node, L.N, L, g); }
-void launch_coriolis(const DevLevel& L, cudaStream_t s) { LAUNCH(k_coriolis, L.E, L); }
-
-void launch_restrict(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
-    LAUNCH(k_restrict, span(C), C, F);
-    LAUNCH(k_div, C.N, C);
+void launch_pv(const Work& W, double H, cudaStream_t s) { LIST(k_pv, W.lvs, W.list, W.count, W.S, H); }
+void launch_flux(const Work& W, double H, cudaStream_t s) { LIST(k_flux, W.lvs, W.list, W.count, W.S, H); }
+void launch_node(const Work& W, double g, cudaStream_t s) { LIST(k_node, W.lvs, W.list, W.count, W.S, g); }
+void launch_coriolis(const Work& W, cudaStream_t s) { LIST(k_coriolis, W.lvs, W.list, W.count, W.S); }
+void launch_update(const Work& W, const RKStage& st, const double* dt, cudaStream_t s) {
+    LIST(k_update, W.lvs, W.list, W.count, W.S, st, dt);
 }
-
-void launch_update(const DevLevel& L, const RKStage& st, const double* dt, cudaStream_t s) {
-    LAUNCH(k_update, span(L), L, st, dt);
+void launch_save_base(const Work& W, cudaStream_t s) { LIST(k_save_base, W.lvs, W.list, W.count, W.S); }
+void launch_fill(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s) {
+    LIST(k_fill, F, C, W.list, W.count, W.S);
 }
-
-void launch_save_base(const DevLevel& L, cudaStream_t s) { LAUNCH(k_save_base, span(L), L); }
-
-void launch_fill(const DevLevel& F, const DevLevel& C, cudaStream_t s) { LAUNCH(k_fill, span(F), F, C); }
-
-void launch_partial(const DevLevel& C, const DevLevel& F, cudaStream_t s) { LAUNCH(k_partial, C.N, C, F); }
-
-void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
-    LAUNCH(k_restrict_full, span(C), C, F);
+void launch_restrict(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s) {
+    LIST(k_restrict, C, F, W.list, W.count, W.S);
+    LIST(k_div, C, W.list, W.count, W.S);
 }
-
-void launch_details(const DevLevel& F, const DevLevel& C, cudaStream_t s) {
-    int64_t n = span(F) > C.E ? span(F) : C.E;
-    LAUNCH(k_details, n, F, C);
+void launch_partial(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s) {
+    LIST(k_partial, C, F, W.list, W.count, W.S);
 }
-
-void launch_maxabs(const DevLevel& L, unsigned long long* red, cudaStream_t s) { LAUNCH(k_maxabs, span(L), L, red); }
-
+void launch_details(const Work& W, int jmin, cudaStream_t s) { LIST(k_details, W.lvs, W.list, W.count, W.S, jmin); }
+void launch_inverse(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s) {
+    LIST(k_inverse_a, F, C, W.list, W.count, W.S);
+    LIST(k_inverse_b, F, W.list, W.count, W.S);
+}
+void launch_maxabs(const Work& W, unsigned long long* red, cudaStream_t s) {
+    LIST(k_maxabs, W.lvs, W.list, W.count, W.S, red);
+}
+void launch_dt(const Work& W, double H, double g, unsigned long long* red, cudaStream_t s) {
+    LIST(k_dt, W.lvs, W.list, W.count, W.S, H, g, red);
+}
+void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
+    g_launches++;
+    k_dt_final<<<1, 32, 0, s>>>(red, cfl, dt);
+}
 void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s) {
     g_launches++;
     k_thresholds<<<1, 32, 0, s>>>(red, eps, eh, eu, thr);
 }
 
+void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
+    DENSE(k_restrict_full, span(C), C, F);
+}
 void launch_sig(const DevLevel& F, const DevLevel& C, const double* thr, cudaStream_t s) {
     int64_t n = span(F) > C.E ? span(F) : C.E;
-    LAUNCH(k_sig, n, F, C, thr);
+    DENSE(k_sig, n, F, C, thr);
 }
-
 void launch_adjacent(const DevLevel& F, const DevLevel& C, int children, cudaStream_t s) {
-    LAUNCH(k_adjacent, F.N, F, C, children);
+    DENSE(k_adjacent, F.N, F, C, children);
 }
-
 void launch_close(const DevLevel& F, const DevLevel& Fp, int has_finer, cudaStream_t s) {
-    LAUNCH(k_close, F.N, F, Fp, has_finer);
+    DENSE(k_close, F.N, F, Fp, has_finer);
 }
-
 void launch_live(const DevLevel& L, int all, cudaStream_t s) {
-    LAUNCH(k_live, L.N, L, all);
-    LAUNCH(k_live_edges, L.E, L);
+    DENSE(k_live, L.N, L, all);
+    DENSE(k_live_edges, L.E, L);
 }
-
 void launch_ghost_band(const DevLevel& L, int hops, cudaStream_t s) {
     uint8_t* a = L.band0;
     uint8_t* b = L.band1;
     for (int h = 0; h < hops; ++h) {
-        LAUNCH(k_dilate, L.N, L, a, b);
+        DENSE(k_dilate, L.N, L, a, b);
         uint8_t* t = a;
         a = b;
         b = t;
     }
-    LAUNCH(k_ghost, span(L), L, a);
+    DENSE(k_ghost, span(L), L, a);
 }
-
-void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s) { LAUNCH(k_covered, C.N, C, F); }
-
+void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s) { DENSE(k_covered, C.N, C, F); }
 void launch_patches(const DevLevel& L, cudaStream_t s) {
     int t = int(L.p * L.p < 256 ? L.p * L.p : 256);
     t = t < 32 ? 32 : t;
@@ -670,30 +799,17 @@ void launch_patches(const DevLevel& L, cudaStream_t s) {
     k_patch_flags<<<unsigned(L.npatch), t, 0, s>>>(L);
     k_patch_scan<<<1, 1024, 0, s>>>(L);
 }
-
-void launch_inverse(const DevLevel& F, const DevLevel& C, cudaStream_t s) {
-    LAUNCH(k_inverse_a, span(F), F, C);
-    LAUNCH(k_inverse_b, F.N, F);
-}
-
-void launch_dt(const DevLevel& L, double H, double g, double dx, unsigned long long* red, cudaStream_t s) {
-    LAUNCH(k_dt, span(L), L, H, g, dx, red);
-}
-
-void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
+void launch_concat(const DevLevel* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
     g_launches++;
-    k_dt_final<<<1, 32, 0, s>>>(red, cfl, dt);
+    k_concat<<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
 }
-
 int sums_blocks(const DevLevel& L) { return int(blocks_for(L.N, TPB)); }
-
 void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s) {
     int nb = sums_blocks(L);
     g_launches += 2;
     k_sums<<<nb, TPB, 0, s>>>(L, H, g, part);
     k_sums_final<<<1, 32, 0, s>>>(part, nb, out);
 }
-
-void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s) { LAUNCH(k_count, span(L), L, cnt); }
+void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s) { DENSE(k_count, span(L), L, cnt); }
 
 }  // namespace sww

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "sww_core.cuh"
 
 namespace sww {
@@ -13,19 +15,36 @@ struct RKStage {
     double a, b, cdt, ddt, al, be;
 };
 
-void launch_tri_q(const DevLevel& L, double H, cudaStream_t s);
-void launch_edge_flux(const DevLevel& L, double H, cudaStream_t s);
-void launch_node(const DevLevel& L, double g, cudaStream_t s);
-void launch_coriolis(const DevLevel& L, cudaStream_t s);
-void launch_restrict(const DevLevel& C, const DevLevel& F, cudaStream_t s);
-void launch_update(const DevLevel& L, const RKStage& st, const double* dt, cudaStream_t s);
-void launch_save_base(const DevLevel& L, cudaStream_t s);
-void launch_fill(const DevLevel& F, const DevLevel& C, cudaStream_t s);
-void launch_partial(const DevLevel& C, const DevLevel& F, cudaStream_t s);
-void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s);
-void launch_details(const DevLevel& F, const DevLevel& C, cudaStream_t s);
-void launch_maxabs(const DevLevel& L, unsigned long long* red, cudaStream_t s);
+// A work list on the device: entries (level-tagged patches), their count, the
+// device array of levels (for multi-level lists; null for a single level's list),
+// threads per entry S (the configured patch area) and the fixed grid size.
+struct Work {
+    const DevLevel* lvs;
+    const int32_t* list;
+    const int32_t* count;
+    int S;
+    unsigned grid;
+};
+
+// list kernels (FP64, active patches)
+void launch_pv(const Work& W, double H, cudaStream_t s);
+void launch_flux(const Work& W, double H, cudaStream_t s);
+void launch_node(const Work& W, double g, cudaStream_t s);
+void launch_coriolis(const Work& W, cudaStream_t s);
+void launch_update(const Work& W, const RKStage& st, const double* dt, cudaStream_t s);
+void launch_save_base(const Work& W, cudaStream_t s);
+void launch_fill(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s);
+void launch_restrict(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s);
+void launch_partial(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s);
+void launch_details(const Work& W, int jmin, cudaStream_t s);
+void launch_inverse(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s);
+void launch_maxabs(const Work& W, unsigned long long* red, cudaStream_t s);
+void launch_dt(const Work& W, double H, double g, unsigned long long* red, cudaStream_t s);
+void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
 void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s);
+
+// dense level kernels (masks, initialisation, diagnostics)
+void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s);
 void launch_sig(const DevLevel& F, const DevLevel& C, const double* thr, cudaStream_t s);
 void launch_adjacent(const DevLevel& F, const DevLevel& C, int children, cudaStream_t s);
 void launch_close(const DevLevel& F, const DevLevel& Fp, int has_finer, cudaStream_t s);
@@ -33,12 +52,11 @@ void launch_live(const DevLevel& L, int all, cudaStream_t s);
 void launch_ghost_band(const DevLevel& L, int hops, cudaStream_t s);
 void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s);
 void launch_patches(const DevLevel& L, cudaStream_t s);
-void launch_inverse(const DevLevel& F, const DevLevel& C, cudaStream_t s);
-void launch_dt(const DevLevel& L, double H, double g, double dx, unsigned long long* red, cudaStream_t s);
-void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
+void launch_concat(const DevLevel* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s);
 int sums_blocks(const DevLevel& L);
 void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s);
 void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s);
+
 // Process-wide number of library kernel launches (count_launch adds launches made
 // outside the launchers above).
 int64_t kernel_launches();
