@@ -160,12 +160,15 @@ def run_reference(a, rank):
 
 # ----------------------------------------------------------------------------- our arm
 
-# Algorithmic bytes per live edge of one launch of the Coriolis kernel (FP64): the
-# ten reconstruction weights and edge ids (10 x 12 B), the edge's own flux, its
-# two triangle potential vorticities and the two triangle ids (8 + 16 + 8 B), and
-# the tendency it writes (8 B).  Neighbour fluxes and vorticities are shared with
-# the neighbouring edges and counted once, with their own edge.
-CORIOLIS_BYTES_PER_EDGE = 10 * 12 + 8 + 16 + 8 + 8
+# Algorithmic bytes per live edge of one launch of the second trend pass
+# (k_node_coriolis, FP64).  Coriolis part, per live edge: the ten reconstruction
+# weights and edge ids (10 x 12 B), the edge's own flux, its two triangle ids and
+# potential vorticities (8 + 8 + 16 B), and the tendency it writes (8 B).  Node
+# part, per node (three edges per node on the grid): area, depth, degree, six
+# ring-edge codes, face and edge lengths already counted with the edges, and the
+# divergence and Bernoulli function written (8 + 8 + 1 + 24 + 16 B = 57 B), i.e.
+# 19 B per edge.  Values shared with neighbours are counted once, with their owner.
+CORIOLIS_BYTES_PER_EDGE = 10 * 12 + 8 + 8 + 16 + 8 + 19
 
 
 def run_ours(a, rank, world):
@@ -246,7 +249,7 @@ def run_ours(a, rank, world):
         peak, peak_src = peaks["hbm_gbs"], "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    roofline = {"bound": "hbm", "kernel": "k_coriolis", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"bound": "hbm", "kernel": "k_node_coriolis", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)",
                 "traffic": None, "avg_launch_us": cor_ms * 1e3 / max(cor_n, 1), "launches": cor_n,
                 "bytes_per_live_edge": CORIOLIS_BYTES_PER_EDGE}

@@ -76,7 +76,7 @@ struct sww_handle {
     std::vector<void*> allocs;
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
-    int32_t *all_list = nullptr, *all_count = nullptr, *d_counts = nullptr;
+    int32_t *all_list = nullptr, *all_count = nullptr, *d_counts = nullptr, *sig_any = nullptr;
     int32_t* h_counts = nullptr;    // pinned: per-level list sizes after each step
     double* h_dt = nullptr;         // pinned: time step of the last step
     int S = 64, jtop = 0, nsm = 152;
@@ -276,10 +276,8 @@ void trend(sww_handle* h) {
     cudaStream_t s = h->stream;
     Work W = work_all(h);
     fill_ghosts(h);
-    { Trace t(h, SWW_K_PV); launch_pv(W, h->cfg.H, s); }
-    { Trace t(h, SWW_K_FLUX); launch_flux(W, h->cfg.H, s); }
-    { Trace t(h, SWW_K_NODE); launch_node(W, h->cfg.g, s); }
-    { Trace t(h, SWW_K_CORIOLIS); launch_coriolis(W, s); }
+    { Trace t(h, SWW_K_PV); launch_pv_flux(W, h->cfg.H, s); }
+    { Trace t(h, SWW_K_CORIOLIS); launch_node_coriolis(W, h->cfg.g, s); }
     for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_RESTRICT);
         launch_restrict(h->lv[j], h->lv[j + 1], work_level(h, j), s);
@@ -315,6 +313,40 @@ void update_top(sww_handle* h) {
     h->jtop = top;
 }
 
+// Thread ranges of levels ja..jb for a multi-level dense launch.
+template <typename Count>
+Span span_of(const sww_handle* h, int ja, int jb, Count count) {
+    Span sp{};
+    sp.ja = ja, sp.jb = jb;
+    int64_t t = 0;
+    for (int j = ja; j <= jb; ++j) {
+        sp.off[j - ja] = t;
+        t += count(h->lv[j]);
+    }
+    sp.off[jb + 1 - ja] = t;
+    return sp;
+}
+
+MaskArgs mask_args(const sww_handle* h, int j0, int j1) {
+    MaskArgs a{};
+    a.lvs = h->d_lvs, a.host = h->lv.data(), a.ja = j0, a.jb = j1, a.hops = GHOST_HOPS, a.thr = h->thr;
+    auto N = [](const DevLevel& L) { return L.N; };
+    auto E = [](const DevLevel& L) { return L.E; };
+    auto P = [](const DevLevel& L) { return L.npatch; };
+    int jf = std::min(j0 + 1, j1);
+    a.nodes_f = span_of(h, jf, j1, N);
+    a.edges_f = span_of(h, jf, j1, E);
+    if (j1 == j0) a.nodes_f.off[1] = 0, a.edges_f.off[1] = 0;   // no level above Jmin
+    a.nodes = span_of(h, j0, j1, N);
+    a.edges = span_of(h, j0, j1, E);
+    a.nodes_c = span_of(h, j0, std::max(j0, j1 - 1), N);
+    a.patches = span_of(h, j0, j1, P);
+    a.sig_any = h->sig_any;
+    a.sig_any_len = h->cfg.jmax + 2;
+    a.skip = j1 > h->jtop ? j1 : -1;
+    return a;
+}
+
 // Mask construction and inverse transform.  Levels above top + 1 hold no live point
 // and can gain none in one adaptation, so the byte-wide passes stop there.
 void mask_and_inverse(sww_handle* h) {
@@ -322,19 +354,8 @@ void mask_and_inverse(sww_handle* h) {
     cudaStream_t s = h->stream;
     {
         Trace tm(h, SWW_K_MASK);
-        for (int j = j0 + 1; j <= j1; ++j) {
-            ck(cudaMemsetAsync(h->lv[j].sig, 0, h->lv[j].N, s), "memset sig");
-            launch_sig(h->lv[j], h->lv[j - 1], h->thr, s);
-        }
-        for (int j = j0 + 1; j <= j1; ++j) launch_adjacent(h->lv[j], h->lv[j - 1], j - 1 > j0, s);
-        for (int j = j1; j > j0; --j) {
-            bool finer = j < j1;
-            launch_close(h->lv[j], finer ? h->lv[j + 1] : h->lv[j], finer, s);
-        }
-        for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], j == j0, s);
-        for (int j = j0 + 1; j <= j1; ++j) launch_ghost_band(h->lv[j], GHOST_HOPS, s);
-        for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
-        for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+        MaskArgs a = mask_args(h, j0, j1);
+        launch_mask(a, s);
         launch_concat(h->d_lvs, j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
@@ -487,7 +508,7 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
         h->edges.assign(cfg->jmax + 1, {});
         h->S = cfg->patch * cfg->patch;
         int64_t total = 0;
-        const int64_t cap = int64_t(h->nsm) * 16;
+        const int64_t cap = int64_t(h->nsm) * 4;   // grid-stride launches: 4 blocks of 256 per SM
         for (int j = cfg->jmin; j <= cfg->jmax; ++j) {
             HostLevel& L = H.lv[j];
             upload_level(h, L, j > cfg->jmin, j < cfg->jmax, j > cfg->jmin ? H.lv[j - 1].E : 0);
@@ -505,6 +526,8 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
         h->all_list = h->alloc<int32_t>(total);
         h->all_count = h->alloc<int32_t>(1);
         h->d_counts = h->alloc<int32_t>(cfg->jmax + 1);
+        h->sig_any = h->alloc<int32_t>(cfg->jmax + 2);
+        ck(cudaMemset(h->sig_any, 0, sizeof(int32_t) * (cfg->jmax + 2)), "memset");
         ck(cudaMallocHost(&h->h_counts, sizeof(int32_t) * (cfg->jmax + 1)), "cudaMallocHost");
         ck(cudaMallocHost(&h->h_dt, sizeof(double)), "cudaMallocHost");
         std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
@@ -567,9 +590,10 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
             ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
             ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
             for (int j = j1; j > j0; --j) launch_restrict_full(h->lv[j - 1], h->lv[j], s);
-            for (int j = j0; j <= j1; ++j) launch_live(h->lv[j], 1, s);
-            for (int j = j0; j < j1; ++j) launch_covered(h->lv[j], h->lv[j + 1], s);
-            for (int j = j0; j <= j1; ++j) launch_patches(h->lv[j], s);
+            MaskArgs a = mask_args(h, j0, j1);
+            launch_live_all(h->d_lvs, a.nodes, a.edges, s);
+            if (j1 > j0) launch_covered_all(h->d_lvs, a.nodes_c, s);
+            launch_patches_all(h->d_lvs, a.patches, s);
             launch_concat(h->d_lvs, j0, j1, h->all_list, h->all_count, s);
             read_counts(h);
             check_launch();

@@ -49,29 +49,65 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x));
 }
 
-// Visit the elements of the entries of a work list: body(L, elem, node); a pole
-// entry gives elem = -1 and the two pole nodes.  Entries name their level in
-// `lvs` (multi-level lists) or all belong to `one` when lvs is null.
-template <class Body>
-__device__ __forceinline__ void for_elements(const DevLevel* __restrict__ lvs, const DevLevel& one,
-                                             const int32_t* __restrict__ list, const int32_t* __restrict__ count,
-                                             int S, Body body) {
-    int64_t n = int64_t(*count) * S;
-    int64_t stride = int64_t(gridDim.x) * blockDim.x;
+// Item kinds of a work-list entry, in slot order.
+constexpr int K_NODE = 1, K_EDGE = 2, K_TRI = 4, K_CEDGE = 8;
+
+template <int KINDS>
+__host__ __device__ constexpr int slots_of() {
+    return ((KINDS & K_NODE) ? 1 : 0) + ((KINDS & K_EDGE) ? 3 : 0) + ((KINDS & K_TRI) ? 2 : 0) + ((KINDS & K_CEDGE) ? 3 : 0);
+}
+
+// Visit the items of the entries of a work list, one thread per item:
+// body(L, kind, id, elem).  An entry covers slots x P threads (P = configured patch
+// area): one slot of nodes, three of edges (orientation 0, 1, 2), two of triangles
+// and three of the edges of the coarse element under an even element (id = the
+// orientation), as KINDS selects.  A pole entry yields the two pole nodes with
+// elem = -1.  Entries name their level in `lvs` (multi-level lists) or all belong
+// to `one` when lvs is null.
+template <int KINDS, class Body>
+__device__ __forceinline__ void for_items(const DevLevel* __restrict__ lvs, const DevLevel& one,
+                                          const int32_t* __restrict__ list, const int32_t* __restrict__ count, int P,
+                                          Body body) {
+    constexpr int NS = slots_of<KINDS>();
+    const int64_t S = int64_t(NS) * P;
+    const int64_t n = int64_t(*count) * S;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t it = gid(); it < n; it += stride) {
         int32_t ent = list[it / S];
-        int local = int(it % S);
+        int64_t local = it % S;
+        int slot = int(local / P);
+        int64_t idx = local % P;
         const DevLevel& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
         int64_t pat = ent & PATCH_MASK;
         if (pat == L.npatch) {
-            if (local < 2) body(L, int64_t(-1), L.nelem + local);
-        } else {
-            int64_t pp = L.p * L.p;
-            if (local < pp) {
-                int64_t e = pat * pp + local;
-                body(L, e, e);
-            }
+            if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
+            continue;
         }
+        int64_t pp = L.p * L.p;
+        if (idx >= pp) continue;
+        int64_t el = pat * pp + idx;
+        if (KINDS & K_NODE) {
+            if (slot == 0) {
+                body(L, K_NODE, el, el);
+                continue;
+            }
+            slot -= 1;
+        }
+        if (KINDS & K_EDGE) {
+            if (slot < 3) {
+                body(L, K_EDGE, slot * L.nelem + el, el);
+                continue;
+            }
+            slot -= 3;
+        }
+        if (KINDS & K_TRI) {
+            if (slot < 2) {
+                body(L, K_TRI, slot * L.nelem + el, el);
+                continue;
+            }
+            slot -= 2;
+        }
+        if (KINDS & K_CEDGE) body(L, K_CEDGE, int64_t(slot), el);
     }
 }
 
@@ -212,130 +248,124 @@ __device__ __forceinline__ void fill_edge(const DevLevel& F, const DevLevel& C, 
 
 // ---------------------------------------------------------------------------- list kernels
 
-#define ELEMS(lvs, one, list, count, S) \
-    for_elements(lvs, one, list, count, S, [&] __device__(const DevLevel& L, int64_t el, int64_t v)
+#define ITEMS(KINDS, lvs, one, list, count, P) \
+    for_items<KINDS>(lvs, one, list, count, P, [&] __device__(const DevLevel& L, int kind, int64_t id, int64_t el)
 
-__global__ void k_pv(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H) {
+// pass 1 of a trend: potential vorticity at triangles and thickness flux at edges
+// (both read only the state)
+__global__ void k_pv_flux(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, double H) {
     DevLevel none{};
-    ELEMS(lvs, none, list, count, S) {
-        if (el < 0) return;
-        pv_at(L, el, H);
-        pv_at(L, L.nelem + el, H);
+    ITEMS(K_EDGE | K_TRI, lvs, none, list, count, P) {
+        if (kind == K_EDGE)
+            flux_at(L, id, H);
+        else
+            pv_at(L, id, H);
     });
 }
 
-__global__ void k_flux(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H) {
+// pass 2: divergence, kinetic energy and Bernoulli function at nodes, Coriolis
+// tendency at edges (both read pass-1 results of neighbours)
+__global__ void k_node_coriolis(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
+                                double g) {
     DevLevel none{};
-    ELEMS(lvs, none, list, count, S) {
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) flux_at(L, o * L.nelem + el, H);
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
+        if (kind == K_NODE)
+            node_at(L, id, g);
+        else
+            coriolis_at(L, id);
     });
 }
 
-__global__ void k_node(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double g) {
-    DevLevel none{};
-    ELEMS(lvs, none, list, count, S) { node_at(L, v, g); });
-}
-
-__global__ void k_coriolis(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S) {
-    DevLevel none{};
-    ELEMS(lvs, none, list, count, S) {
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) coriolis_at(L, o * L.nelem + el);
-    });
-}
-
-__global__ void k_update(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, RKStage st,
+__global__ void k_update(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, RKStage st,
                          const double* __restrict__ dtp) {
     DevLevel none{};
     double dt = dtp ? *dtp : 0.0;
-    ELEMS(lvs, none, list, count, S) {
-        update_node(L, v, st, dt);
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) update_edge(L, o * L.nelem + el, st, dt);
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
+        if (kind == K_NODE)
+            update_node(L, id, st, dt);
+        else
+            update_edge(L, id, st, dt);
     });
 }
 
-__global__ void k_save_base(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S) {
+__global__ void k_save_base(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P) {
     DevLevel none{};
-    ELEMS(lvs, none, list, count, S) {
-        if (L.nflag[v] & LIVE) L.dh0[v] = L.dh[v];
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t e = o * L.nelem + el;
-            if (L.eflag[e] & LIVE) L.u0[e] = L.u[e];
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
+        if (kind == K_NODE) {
+            if (L.nflag[id] & LIVE) L.dh0[id] = L.dh[id];
+        } else if (L.eflag[id] & LIVE) {
+            L.u0[id] = L.u[id];
         }
     });
 }
 
 // ghosts of level F from level C over F's work list
-__global__ void k_fill(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, F, list, count, S) {
-        fill_node(L, C, v);
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) fill_edge(L, C, o * L.nelem + el);
+__global__ void k_fill(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, nullptr, F, list, count, P) {
+        if (kind == K_NODE)
+            fill_node(L, C, id);
+        else
+            fill_edge(L, C, id);
     });
 }
 
 // restriction from F = level j+1 to C = level j (Sec. 3.1): B by injection at covered
 // nodes, flux by R_F on faces of covered nodes, Coriolis tendency by R_u where both
 // ends are covered
-__global__ void k_restrict(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, C, list, count, S) {
-        if (L.nflag[v] & COVERED) L.B[v] = F.B[L.c2f[v]];
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t i = o * L.nelem + el;
-            bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
-            if (ca || cb) {
-                double s = 0.0;
-#pragma unroll
-                for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
-#pragma unroll
-                for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
-                L.F[i] = s / L.l_e[i];
-            }
-            if (ca && cb) L.Q[i] = 0.5 * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
+__global__ void k_restrict(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, nullptr, C, list, count, P) {
+        if (kind == K_NODE) {
+            if (L.nflag[id] & COVERED) L.B[id] = F.B[L.c2f[id]];
+            return;
         }
+        int64_t i = id;
+        bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
+        if (ca || cb) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
+#pragma unroll
+            for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
+            L.F[i] = s / L.l_e[i];
+        }
+        if (ca && cb) L.Q[i] = 0.5 * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
     });
 }
 
-__global__ void k_div(DevLevel C, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, C, list, count, S) { div_at(L, v); });
+__global__ void k_div(DevLevel C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, nullptr, C, list, count, P) { div_at(L, id); });
 }
 
 // R_h at covered nodes of C from level F (Eq. Rh; coefficients of non-live points are zero)
-__global__ void k_partial(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, C, list, count, S) {
-        if (!(L.nflag[v] & COVERED)) return;
-        double s = F.dh[L.c2f[v]];
+__global__ void k_partial(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, nullptr, C, list, count, P) {
+        if (!(L.nflag[id] & COVERED)) return;
+        double s = F.dh[L.c2f[id]];
         for (int q = 0; q < 12; ++q) {
-            int32_t m = L.mk_i[q * L.N + v];
+            int32_t m = L.mk_i[q * L.N + id];
             if (m < 0 || !(F.nflag[m] & LIVE)) continue;
-            s += L.mk_w[q * L.N + v] * height_detail(F, m);
+            s += L.mk_w[q * L.N + id] * height_detail(F, m);
         }
-        L.dh[v] = s;
+        L.dh[id] = s;
     });
 }
 
 // wavelet coefficients at live points (Eqs. 1-2; velocity transform of Sec. 4.1):
-// h~ at odd nodes, u~ at interior fine edges, u~_E of the coarse element's edges
-// (handled by the fine element at the coarse element's node)
-__global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, int jmin) {
+// h~ at odd nodes, u~ at interior fine edges, u~_E at the edges of the coarse element
+// under each even fine element
+__global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, int jmin) {
     DevLevel none{};
-    ELEMS(lvs, none, list, count, S) {
+    ITEMS(K_NODE | K_EDGE | K_CEDGE, lvs, none, list, count, P) {
         if (L.J == jmin) return;
         const DevLevel& C = lvs[L.J - 1];
-        if (L.f2c[v] < 0 && (L.nflag[v] & LIVE)) L.hdet[v] = height_detail(L, v);
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t fe = o * L.nelem + el;
-            if (L.fe_kind[fe] == 2 && (L.eflag[fe] & LIVE)) L.ui[fe] = L.u[fe] - predict(L, C.u, fe);
-        }
-        int32_t ce = L.f2c[v];
-        if (ce < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t E = o * C.nelem + ce;
+        if (kind == K_NODE) {
+            if (L.f2c[id] < 0 && (L.nflag[id] & LIVE)) L.hdet[id] = height_detail(L, id);
+        } else if (kind == K_EDGE) {
+            if (L.fe_kind[id] == 2 && (L.eflag[id] & LIVE)) L.ui[id] = L.u[id] - predict(L, C.u, id);
+        } else {
+            int32_t ce = L.f2c[el];
+            if (ce < 0) return;
+            int64_t E = id * C.nelem + ce;
             int32_t h0 = C.half[E], h1 = C.half[C.E + E];
             if ((L.eflag[h0] & LIVE) || (L.eflag[h1] & LIVE)) {
                 double a = L.u[h0] - predict(L, C.u, h0);
@@ -349,45 +379,44 @@ __global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list,
 // inverse transform of the retained coefficients onto the live points of F:
 // (a) even nodes and all edges from level C, (b) odd nodes from the even ones.
 // Coefficients count only where the point was live before the adaptation.
-__global__ void k_inverse_a(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, F, list, count, S) {
-        if ((L.nflag[v] & LIVE) && L.f2c[v] >= 0) {
-            int32_t k = L.f2c[v];
+__global__ void k_inverse_a(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, nullptr, F, list, count, P) {
+        if (kind == K_NODE) {
+            if (!(L.nflag[id] & LIVE) || L.f2c[id] < 0) return;
+            int32_t k = L.f2c[id];
             double s = C.dh[k];
             for (int q = 0; q < 12; ++q) {
                 int32_t m = C.mk_i[q * C.N + k];
                 if (m >= 0 && (L.nflag[m] & LIVE) && (L.nflag[m] & WASLIVE)) s -= C.mk_w[q * C.N + k] * L.hdet[m];
             }
-            L.dh[v] = s;
+            L.dh[id] = s;
+            return;
         }
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t i = o * L.nelem + el;
-            if (!(L.eflag[i] & LIVE)) continue;
-            int kind = L.fe_kind[i];
-            double P = predict(L, C.u, i);
-            if (kind == 2) {
-                L.u[i] = P + ((L.eflag[i] & WASLIVE) ? L.ui[i] : 0.0);
-            } else {
-                int64_t E = L.fe_ce[i];
-                int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-                int32_t other = kind == 0 ? h1 : h0;
-                double Po = predict(L, C.u, other);
-                double delta = 0.5 * (2.0 * C.u[E] - P - Po);
-                double d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : 0.0;
-                L.u[i] = P + delta + (kind == 0 ? d : -d);
-            }
+        int64_t i = id;
+        if (!(L.eflag[i] & LIVE)) return;
+        int fk = L.fe_kind[i];
+        double Pr = predict(L, C.u, i);
+        if (fk == 2) {
+            L.u[i] = Pr + ((L.eflag[i] & WASLIVE) ? L.ui[i] : 0.0);
+        } else {
+            int64_t E = L.fe_ce[i];
+            int32_t h0 = C.half[E], h1 = C.half[C.E + E];
+            int32_t other = fk == 0 ? h1 : h0;
+            double Po = predict(L, C.u, other);
+            double delta = 0.5 * (2.0 * C.u[E] - Pr - Po);
+            double d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : 0.0;
+            L.u[i] = Pr + delta + (fk == 0 ? d : -d);
         }
     });
 }
 
-__global__ void k_inverse_b(DevLevel F, const int32_t* list, const int32_t* count, int S) {
-    ELEMS(nullptr, F, list, count, S) {
-        if (!(L.nflag[v] & LIVE) || L.f2c[v] >= 0) return;
-        double s = (L.nflag[v] & WASLIVE) ? L.hdet[v] : 0.0;
+__global__ void k_inverse_b(DevLevel F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, nullptr, F, list, count, P) {
+        if (!(L.nflag[id] & LIVE) || L.f2c[id] >= 0) return;
+        double s = (L.nflag[id] & WASLIVE) ? L.hdet[id] : 0.0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) s += L.ptw[q * L.N + v] * L.dh[L.par[q * L.N + v]];
-        L.dh[v] = s;
+        for (int q = 0; q < 4; ++q) s += L.ptw[q * L.N + id] * L.dh[L.par[q * L.N + id]];
+        L.dh[id] = s;
     });
 }
 
@@ -425,12 +454,11 @@ __global__ void k_maxabs(const DevLevel* __restrict__ lvs, const int32_t* list, 
     __shared__ unsigned long long sh[32];
     DevLevel none{};
     unsigned long long a = 0, b = 0;
-    ELEMS(lvs, none, list, count, S) {
-        if (L.nflag[v] & LIVE) a = max(a, dbits(fabs(L.dh[v])));
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t e = o * L.nelem + el;
-            if (L.eflag[e] & LIVE) b = max(b, dbits(fabs(L.u[e])));
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
+        if (kind == K_NODE) {
+            if (L.nflag[id] & LIVE) a = max(a, dbits(fabs(L.dh[id])));
+        } else if (L.eflag[id] & LIVE) {
+            b = max(b, dbits(fabs(L.u[id])));
         }
     });
     a = block_reduce(a, MaxOp(), sh, 0ull);
@@ -445,17 +473,13 @@ __global__ void k_dt(const DevLevel* __restrict__ lvs, const int32_t* list, cons
     __shared__ unsigned long long sh[32];
     DevLevel none{};
     unsigned long long a = 0, b = ~0ull;
-    ELEMS(lvs, none, list, count, S) {
-        double kx = M_PI / L.dx;
-        if (L.nflag[v] & LIVE) {
-            double f = L.f_n[v];
-            a = max(a, dbits(sqrt(f * f + g * (H + L.dh[v]) * kx * kx)));
-        }
-        if (el < 0) return;
-        for (int o = 0; o < 3; ++o) {
-            int64_t e = o * L.nelem + el;
-            if (!(L.eflag[e] & LIVE)) continue;
-            double au = fabs(L.u[e]);
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
+        if (kind == K_NODE) {
+            if (!(L.nflag[id] & LIVE)) return;
+            double f = L.f_n[id], kx = M_PI / L.dx;
+            a = max(a, dbits(sqrt(f * f + g * (H + L.dh[id]) * kx * kx)));
+        } else if (L.eflag[id] & LIVE) {
+            double au = fabs(L.u[id]);
             if (au > 0) b = min(b, dbits(L.dx / au));
         }
     });
@@ -540,6 +564,16 @@ __global__ void k_count(DevLevel L, unsigned long long* cnt) {
 
 // ---------------------------------------------------------------------------- dense level kernels
 
+// thread t of a multi-level dense launch -> (level, index within the level)
+__device__ __forceinline__ bool locate(const Span& sp, int64_t t, int& j, int64_t& i) {
+    for (j = sp.ja; j <= sp.jb; ++j)
+        if (t < sp.off[j + 1 - sp.ja]) {
+            i = t - sp.off[j - sp.ja];
+            return true;
+        }
+    return false;
+}
+
 // full restriction used at initialisation: R_h at every node, mean of halves at every edge
 __global__ void k_restrict_full(DevLevel C, DevLevel F) {
     int64_t i = gid();
@@ -557,13 +591,32 @@ __global__ void k_restrict_full(DevLevel C, DevLevel F) {
 // significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends and the
 // midpoint of a coarse edge with |u~_E| >= eps_u; both ends of an interior edge with
 // |u~| >= eps_u; only points live before the adaptation carry coefficients
-__global__ void k_sig(DevLevel F, DevLevel C, const double* __restrict__ thr) {
-    int64_t i = gid();
+// Multi-level mask kernels take (sig_any, skip): level `skip` (the level above the
+// top live level) can only gain points as children of significant points one level
+// down, so its threads leave at once when sig_any[skip - 1] is 0.
+__global__ void k_zero_sig(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t i;
+    if (!locate(sp, gid(), j, i)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    lvs[j].sig[i] = 0;
+}
+
+__global__ void k_sig(const DevLevel* __restrict__ lvs, Span sp, const double* __restrict__ thr, int32_t* sig_any,
+                      int skip) {
+    int j;
+    int64_t i;
+    if (!locate(sp, gid(), j, i)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    bool any = false;
+    const DevLevel& F = lvs[j];
+    const DevLevel& C = lvs[j - 1];
     double eh = thr[0], eu = thr[1];
-    if (i < F.N && F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(F.hdet[i]) >= eh) F.sig[i] = 1;
+    if (i < F.N && F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(F.hdet[i]) >= eh) F.sig[i] = 1, any = true;
     if (i < F.E && F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(F.ui[i]) >= eu) {
         F.sig[F.en[i]] = 1;
         F.sig[F.en[F.E + i]] = 1;
+        any = true;
     }
     if (i < C.E) {
         int32_t h0 = C.half[i], h1 = C.half[C.E + i];
@@ -571,14 +624,21 @@ __global__ void k_sig(DevLevel F, DevLevel C, const double* __restrict__ thr) {
             F.sig[C.c2f[C.en[i]]] = 1;
             F.sig[C.c2f[C.en[C.E + i]]] = 1;
             F.sig[C.mid[i]] = 1;
+            any = true;
         }
     }
+    if (any) sig_any[j] = 1;
 }
 
 // T = S + same-level neighbours of S + children of the coarser significance set
-__global__ void k_adjacent(DevLevel F, DevLevel C, int children) {
-    int64_t x = gid();
-    if (x >= F.N) return;
+__global__ void k_adjacent(const DevLevel* __restrict__ lvs, Span sp, int jmin, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t x;
+    if (!locate(sp, gid(), j, x)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& F = lvs[j];
+    const DevLevel& C = lvs[j - 1];
+    bool children = j - 1 > jmin;
     int dg = F.deg[x];
     uint8_t t = F.sig[x];
     for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
@@ -596,9 +656,10 @@ __global__ void k_adjacent(DevLevel F, DevLevel C, int children) {
 
 // graded closure at level F: coarse node of a live node of the finer level Fp, and the
 // prediction parents of every live odd node (only ever sets bytes to 1)
-__global__ void k_close(DevLevel F, DevLevel Fp, int has_finer) {
+__global__ void k_close(DevLevel F, DevLevel Fp, int has_finer, const int32_t* sig_any, int skip) {
     int64_t x = gid();
     if (x >= F.N) return;
+    if (F.J == skip && !sig_any[F.J - 1]) return;
     uint8_t t = F.tmask[x];
     if (has_finer && Fp.tmask[F.c2f[x]]) t = 1;
     if (!t) return;
@@ -610,41 +671,62 @@ __global__ void k_close(DevLevel F, DevLevel Fp, int has_finer) {
 }
 
 // live flags (all of Jmin, else the mask), remembering which points were live
-__global__ void k_live(DevLevel L, int all) {
-    int64_t i = gid();
-    if (i >= L.N) return;
-    uint8_t lv = all ? 1 : L.tmask[i];
+__global__ void k_live(const DevLevel* __restrict__ lvs, Span sp, int all_level, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t i;
+    if (!locate(sp, gid(), j, i)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
+    uint8_t lv = (all_level == -2 || j == all_level) ? 1 : L.tmask[i];
     L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
     L.band0[i] = lv;
 }
 
 // an edge is live when an end node is
-__global__ void k_live_edges(DevLevel L) {
-    int64_t e = gid();
-    if (e >= L.E) return;
+__global__ void k_live_edges(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t e;
+    if (!locate(sp, gid(), j, e)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
     uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
     L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
 }
 
-__global__ void k_dilate(DevLevel L, const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
-    int64_t x = gid();
-    if (x >= L.N) return;
+// one neighbour hop of the ghost band on every level: band1 <- dilate(band0) when
+// `forward`, band0 <- dilate(band1) otherwise
+__global__ void k_dilate(const DevLevel* __restrict__ lvs, Span sp, int forward, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t x;
+    if (!locate(sp, gid(), j, x)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
+    const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
+    uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
     uint8_t t = in[x];
     int dg = L.deg[x];
     for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
     out[x] = t;
 }
 
-__global__ void k_ghost(DevLevel L, const uint8_t* __restrict__ band) {
-    int64_t i = gid();
+__global__ void k_ghost(const DevLevel* __restrict__ lvs, Span sp, int in_band1, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t i;
+    if (!locate(sp, gid(), j, i)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
+    const uint8_t* __restrict__ band = in_band1 ? L.band1 : L.band0;
     if (i < L.N && !(L.nflag[i] & LIVE) && band[i]) L.nflag[i] |= GHOST;
     if (i < L.E && !(L.eflag[i] & LIVE) && band[L.en[i]] && band[L.en[L.E + i]]) L.eflag[i] |= GHOST;
 }
 
 // covered coarse nodes: the fine node at the same place and all of M_k live
-__global__ void k_covered(DevLevel C, DevLevel F) {
-    int64_t k = gid();
-    if (k >= C.N) return;
+__global__ void k_covered(const DevLevel* __restrict__ lvs, Span sp) {
+    int j;
+    int64_t k;
+    if (!locate(sp, gid(), j, k)) return;
+    const DevLevel& C = lvs[j];
+    const DevLevel& F = lvs[j + 1];
     if (!(F.nflag[C.c2f[k]] & LIVE)) return;
     for (int q = 0; q < 12; ++q) {
         int32_t m = C.mk_i[q * C.N + k];
@@ -654,8 +736,12 @@ __global__ void k_covered(DevLevel C, DevLevel F) {
 }
 
 // patches holding any live or ghost node or edge (one block per patch)
-__global__ void k_patch_flags(DevLevel L) {
-    int64_t pid = blockIdx.x;
+__global__ void k_patch_flags(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
+    int j;
+    int64_t pid;
+    if (!locate(sp, int64_t(blockIdx.x), j, pid)) return;
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
     int64_t pp = L.p * L.p;
     int any = 0;
     for (int64_t l = threadIdx.x; l < pp; l += blockDim.x) {
@@ -668,7 +754,10 @@ __global__ void k_patch_flags(DevLevel L) {
 
 // ascending level-tagged list of flagged patches, then the pole entry when a pole is
 // live or ghost (one block; deterministic)
-__global__ void k_patch_scan(DevLevel L) {
+__global__ void k_patch_scan(const DevLevel* __restrict__ lvs, int ja, const int32_t* sig_any, int skip) {
+    int j = ja + int(blockIdx.x);
+    if (j == skip && !sig_any[j - 1]) return;
+    const DevLevel& L = lvs[j];
     __shared__ int warp_tot[32];
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
@@ -725,10 +814,10 @@ __global__ void k_concat(const DevLevel* __restrict__ lvs, int jmin, int jmax, i
 
 static int64_t span(const DevLevel& L) { return L.E > L.N ? L.E : L.N; }
 
-void launch_pv(const Work& W, double H, cudaStream_t s) { LIST(k_pv, W.lvs, W.list, W.count, W.S, H); }
-void launch_flux(const Work& W, double H, cudaStream_t s) { LIST(k_flux, W.lvs, W.list, W.count, W.S, H); }
-void launch_node(const Work& W, double g, cudaStream_t s) { LIST(k_node, W.lvs, W.list, W.count, W.S, g); }
-void launch_coriolis(const Work& W, cudaStream_t s) { LIST(k_coriolis, W.lvs, W.list, W.count, W.S); }
+void launch_pv_flux(const Work& W, double H, cudaStream_t s) { LIST(k_pv_flux, W.lvs, W.list, W.count, W.S, H); }
+void launch_node_coriolis(const Work& W, double g, cudaStream_t s) {
+    LIST(k_node_coriolis, W.lvs, W.list, W.count, W.S, g);
+}
 void launch_update(const Work& W, const RKStage& st, const double* dt, cudaStream_t s) {
     LIST(k_update, W.lvs, W.list, W.count, W.S, st, dt);
 }
@@ -766,43 +855,60 @@ void launch_thresholds(const unsigned long long* red, double eps, double eh, dou
 void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
     DENSE(k_restrict_full, span(C), C, F);
 }
-void launch_sig(const DevLevel& F, const DevLevel& C, const double* thr, cudaStream_t s) {
-    int64_t n = span(F) > C.E ? span(F) : C.E;
-    DENSE(k_sig, n, F, C, thr);
-}
-void launch_adjacent(const DevLevel& F, const DevLevel& C, int children, cudaStream_t s) {
-    DENSE(k_adjacent, F.N, F, C, children);
-}
-void launch_close(const DevLevel& F, const DevLevel& Fp, int has_finer, cudaStream_t s) {
-    DENSE(k_close, F.N, F, Fp, has_finer);
-}
-void launch_live(const DevLevel& L, int all, cudaStream_t s) {
-    DENSE(k_live, L.N, L, all);
-    DENSE(k_live_edges, L.E, L);
-}
-void launch_ghost_band(const DevLevel& L, int hops, cudaStream_t s) {
-    uint8_t* a = L.band0;
-    uint8_t* b = L.band1;
-    for (int h = 0; h < hops; ++h) {
-        DENSE(k_dilate, L.N, L, a, b);
-        uint8_t* t = a;
-        a = b;
-        b = t;
+#define MULTI(kernel, sp, ...)                                                  \
+    do {                                                                        \
+        int64_t n_ = (sp).off[(sp).jb + 1 - (sp).ja];                           \
+        if (n_ > 0) {                                                           \
+            g_launches++;                                                       \
+            kernel<<<blocks_for(n_, TPB), TPB, 0, s>>>(__VA_ARGS__);            \
+        }                                                                       \
+    } while (0)
+
+void launch_mask(const MaskArgs& a, cudaStream_t s) {
+    const int32_t* any = a.sig_any;
+    const int sk = a.skip;
+    cudaMemsetAsync(a.sig_any, 0, sizeof(int32_t) * a.sig_any_len, s);
+    // significance, adjacency in space and scale (levels ja+1..jb, independent)
+    MULTI(k_zero_sig, a.nodes_f, a.lvs, a.nodes_f, any, sk);
+    MULTI(k_sig, a.edges_f, a.lvs, a.edges_f, a.thr, a.sig_any, sk);
+    MULTI(k_adjacent, a.nodes_f, a.lvs, a.nodes_f, a.ja, any, sk);
+    // graded closure, from the top level down
+    for (int j = a.jb; j > a.ja; --j) {
+        const DevLevel& F = a.host[j];
+        bool finer = j < a.jb;
+        DENSE(k_close, F.N, F, finer ? a.host[j + 1] : F, finer, any, sk);
     }
-    DENSE(k_ghost, span(L), L, a);
-}
-void launch_covered(const DevLevel& C, const DevLevel& F, cudaStream_t s) { DENSE(k_covered, C.N, C, F); }
-void launch_patches(const DevLevel& L, cudaStream_t s) {
-    int t = int(L.p * L.p < 256 ? L.p * L.p : 256);
-    t = t < 32 ? 32 : t;
+    // live flags, ghost band, covered nodes, patch lists (levels ja..jb)
+    MULTI(k_live, a.nodes, a.lvs, a.nodes, a.ja, any, sk);
+    MULTI(k_live_edges, a.edges, a.lvs, a.edges, any, sk);
+    for (int h = 0; h < a.hops; ++h) MULTI(k_dilate, a.nodes_f, a.lvs, a.nodes_f, h % 2 == 0, any, sk);
+    MULTI(k_ghost, a.edges_f, a.lvs, a.edges_f, a.hops % 2 == 1, any, sk);
+    if (a.jb > a.ja) MULTI(k_covered, a.nodes_c, a.lvs, a.nodes_c);
     g_launches += 2;
-    k_patch_flags<<<unsigned(L.npatch), t, 0, s>>>(L);
-    k_patch_scan<<<1, 1024, 0, s>>>(L);
+    k_patch_flags<<<unsigned(a.patches.off[a.jb + 1 - a.ja]), 64, 0, s>>>(a.lvs, a.patches, any, sk);
+    k_patch_scan<<<unsigned(a.jb - a.ja + 1), 1024, 0, s>>>(a.lvs, a.ja, any, sk);
 }
+
+void launch_live_all(const DevLevel* lvs, const Span& nodes, const Span& edges, cudaStream_t s) {
+    MULTI(k_live, nodes, lvs, nodes, -2, nullptr, -1);
+    MULTI(k_live_edges, edges, lvs, edges, nullptr, -1);
+}
+
+void launch_covered_all(const DevLevel* lvs, const Span& nodes_c, cudaStream_t s) {
+    MULTI(k_covered, nodes_c, lvs, nodes_c);
+}
+
+void launch_patches_all(const DevLevel* lvs, const Span& patches, cudaStream_t s) {
+    g_launches += 2;
+    k_patch_flags<<<unsigned(patches.off[patches.jb + 1 - patches.ja]), 64, 0, s>>>(lvs, patches, nullptr, -1);
+    k_patch_scan<<<unsigned(patches.jb - patches.ja + 1), 1024, 0, s>>>(lvs, patches.ja, nullptr, -1);
+}
+
 void launch_concat(const DevLevel* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
     g_launches++;
     k_concat<<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
 }
+
 int sums_blocks(const DevLevel& L) { return int(blocks_for(L.N, TPB)); }
 void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s) {
     int nb = sums_blocks(L);
