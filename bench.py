@@ -158,6 +158,22 @@ def run_reference(a, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- ranks
+
+def combine_ranks(seconds, cells, device, world):
+    """Whole-job figures of independent members, one per rank: the slowest rank's
+    time and the sum of all ranks' active-cell steps."""
+    if world <= 1:
+        return float(seconds), float(cells)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([cells], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(c[0])
+
+
 # ----------------------------------------------------------------------------- our arm
 
 # Algorithmic bytes per live edge of one launch of the second trend pass
@@ -169,6 +185,10 @@ def run_reference(a, rank):
 # divergence and Bernoulli function written (8 + 8 + 1 + 24 + 16 B = 57 B), i.e.
 # 19 B per edge.  Values shared with neighbours are counted once, with their owner.
 CORIOLIS_BYTES_PER_EDGE = 10 * 12 + 8 + 8 + 16 + 8 + 19
+# DRAM bytes (read + write) per launch of k_node_coriolis from one ncu capture of
+# the jet at Jmin=4..Jmax=8, eps=1e-2 (the same active set and launches as
+# Jmax=9); None once the kernel changes.
+CORIOLIS_TRAFFIC_PER_LAUNCH = 15.933184e6 + 0.344064e6
 
 
 def run_ours(a, rank, world):
@@ -219,15 +239,7 @@ def run_ours(a, rank, world):
     clk = clocks.stop()
     launches = m.stats()["kernel_launches"] - launches0
     total = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total, sum(cells)], dtype=torch.float64, device="cuda")
-        tmax = t[0].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_all, cells_all = float(tmax), float(t[1])
-    else:
-        total_all, cells_all = total, sum(cells)
+    total_all, cells_all = combine_ranks(total, sum(cells), "cuda", world)
     value = cells_all / total_all
 
     # live per-launch timing of the dominant kernel (Coriolis) over the same number of steps
@@ -240,7 +252,7 @@ def run_ours(a, rank, world):
     prof = m.profile_read()
     m.profile([])
     cor_ms, cor_n = prof["coriolis"]
-    # every step launches the kernel once per level and stage; bytes use the live edges
+    # one launch per RK stage covers every level; bytes use the live edges
     per_step_bytes = 4 * sum(live_edges.values()) * CORIOLIS_BYTES_PER_EDGE
     achieved = per_step_bytes * a.steps / (cor_ms / 1e3) / 1e9
     peaks = {}
@@ -251,7 +263,8 @@ def run_ours(a, rank, world):
         peak, peak_src = 6800.0, "fallback"
     roofline = {"bound": "hbm", "kernel": "k_node_coriolis", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)",
-                "traffic": None, "avg_launch_us": cor_ms * 1e3 / max(cor_n, 1), "launches": cor_n,
+                "traffic": CORIOLIS_TRAFFIC_PER_LAUNCH if a.jmax >= 8 and a.eps == 1e-2 else None,
+                "avg_launch_us": cor_ms * 1e3 / max(cor_n, 1), "launches": cor_n,
                 "bytes_per_live_edge": CORIOLIS_BYTES_PER_EDGE}
 
     # end to end through the public API from pinned host buffers
@@ -267,7 +280,7 @@ def run_ours(a, rank, world):
         s = m.stats()
         ecells += sum(s["live_nodes"].values())
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s, ecells = combine_ranks(time.perf_counter() - t0, ecells, "cuda", world)
     N, E, _, _ = m.sizes(a.jmax)
     e2e = {"value": ecells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * (N + E) / a.steps),
            "d2h_bytes_per_step": int(8 + 8 * 70), "note": "sww_set_state from pinned host arrays + adapt + "

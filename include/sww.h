@@ -76,7 +76,7 @@ typedef struct {
     int patch;         /* patch side p (power of two); levels with 2^j < p use 2^j     */
     int rk;            /* SWW_RK4 or SWW_SSP43                                         */
     double cfl;        /* dt = cfl * min(1/omega_max, min dx/|u|) when dt <= 0         */
-    double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u| */
+    double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u|; 0 keeps every point */
 } sww_config;
 
 typedef struct {

@@ -484,8 +484,9 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
     if (!cfg || !out) return fail(SWW_E_ARG, "null argument");
     *out = nullptr;
     if (cfg->jmin < 1 || cfg->jmax < cfg->jmin || cfg->jmax > 11) return fail(SWW_E_ARG, "need 1 <= jmin <= jmax <= 11");
-    if (!(cfg->radius > 0) || !(cfg->g > 0) || !(cfg->H > 0) || !(cfg->cfl > 0) || !(cfg->eps > 0))
-        return fail(SWW_E_ARG, "radius, g, H, cfl and eps must be positive");
+    if (!(cfg->radius > 0) || !(cfg->g > 0) || !(cfg->H > 0) || !(cfg->cfl > 0))
+        return fail(SWW_E_ARG, "radius, g, H and cfl must be positive");
+    if (!(cfg->eps >= 0)) return fail(SWW_E_ARG, "eps must be >= 0 (0: every point significant, no compression)");
     if (cfg->patch < 1 || (cfg->patch & (cfg->patch - 1)) || cfg->patch > 16)
         return fail(SWW_E_ARG, "patch must be a power of two <= 16");
     if (cfg->rk != SWW_RK4 && cfg->rk != SWW_SSP43) return fail(SWW_E_ARG, "rk must be SWW_RK4 or SWW_SSP43");
