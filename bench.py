@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--eps", type=float, default=1e-2)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--patch", type=int, default=8)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-jmax", type=int, default=6, help="finest level of the oracle sample")
     return p.parse_args()
@@ -203,7 +204,7 @@ def run_ours(a, rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     seed = a.seed + rank
     t_setup = time.perf_counter()
-    m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8)
+    m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=a.precision)
     xyz, en = m.grid(a.jmax)
     mid, tan = edge_geometry(xyz, en)
     dh0, u0 = workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)

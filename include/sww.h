@@ -67,6 +67,8 @@ enum {
     SWW_SIG = 9        /* [uint8 N_j]   significance set of the last adaptation          */
 };
 
+enum { SWW_FP64 = 0, SWW_FP32 = 1 };
+
 typedef struct {
     int jmin, jmax;    /* coarsest and finest level, 1 <= jmin <= jmax <= 11           */
     double radius;     /* sphere radius (m)                                            */
@@ -77,6 +79,12 @@ typedef struct {
     int rk;            /* SWW_RK4 or SWW_SSP43                                         */
     double cfl;        /* dt = cfl * min(1/omega_max, min dx/|u|) when dt <= 0         */
     double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u|; 0 keeps every point */
+    int blocks_per_sm; /* work-list launches: blocks of 256 threads per SM (0: 4)           */
+    int precision;     /* SWW_FP64: fields and arithmetic in FP64.  SWW_FP32: fields,
+                          stencils and transforms in FP32 with weights rounded once from
+                          the FP64 tables; thresholds, time step and the compensated
+                          mass/energy sums in FP64 on the FP32 values.  The ABI's
+                          double arrays are converted at the boundary.                */
 } sww_config;
 
 typedef struct {
@@ -100,6 +108,17 @@ typedef struct sww_handle sww_handle;
  * the handle, owned by the library until sww_destroy. */
 int sww_create(const sww_config* cfg, void* stream, sww_handle** out);
 int sww_destroy(sww_handle* h);
+
+/* Ensemble member sharing the grid of `share` (Sec. 2.2: the grid depends only on
+ * the levels, the radius and the rotation rate): same as sww_create but the
+ * grid and all geometric tables of `share` are reused instead of rebuilt, so a
+ * member costs only its state arrays.  cfg must have share's jmin, patch, radius
+ * and omega and jmax <= share's jmax; g, H, rk, cfl, eps, blocks_per_sm and
+ * precision are free.  Coarse-level areas are those of the shared hierarchy
+ * (built up from its finest level, Sec. 4.1), so a member with a smaller jmax
+ * matches a grid of its own to rounding, not bit for bit.  The tables stay alive
+ * while any handle uses them.  SWW_E_ARG otherwise. */
+int sww_create_shared(const sww_config* cfg, void* stream, const sww_handle* share, sww_handle** out);
 
 /* Sizes of level j: nodes, edges, triangles, patches. */
 int sww_level_sizes(const sww_handle* h, int level, int64_t* n_nodes, int64_t* n_edges,
@@ -138,6 +157,15 @@ int sww_rhs(sww_handle* h);
  * adapt != 0 runs the partial height transform and sww_adapt after each step;
  * adapt == 0 runs only the partial height transform. */
 int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
+
+/* nsteps steps of each of n independent ensemble members (distinct handles, each
+ * as sww_step alone would advance it).  Every member's step runs on the member's
+ * own stream, so the members' kernels overlap on the GPU; each member waits only
+ * for its own previous step.  On entry each member's work is ordered after its
+ * caller stream, and on return each caller stream waits for its member.
+ * Returns the first error; members then stand at different step counts
+ * (sww_stats_get tells which). */
+int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int adapt);
 
 /* Copy one per-level quantity (SWW_DH ... SWW_SIG) to the host. */
 int sww_get_level(const sww_handle* h, int level, int what, void* out);

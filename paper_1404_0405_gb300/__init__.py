@@ -15,7 +15,7 @@ import numpy as np
 
 from .buildlib import LIB, build
 
-__all__ = ["Model", "SwwError", "load", "lib_path", "DH", "U", "DH_T", "U_T", "NODE_FLAGS", "EDGE_FLAGS",
+__all__ = ["Model", "SwwError", "step_ensemble", "load", "lib_path", "DH", "U", "DH_T", "U_T", "NODE_FLAGS", "EDGE_FLAGS",
            "HDET", "UDET_E", "UDET_I", "SIG", "LIVE", "GHOST", "COVERED"]
 
 DH, U, DH_T, U_T, NODE_FLAGS, EDGE_FLAGS, HDET, UDET_E, UDET_I, SIG = range(10)
@@ -23,7 +23,8 @@ LIVE, GHOST, COVERED = 1, 2, 4
 RK4, SSP43 = 0, 1
 EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
-           "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static"]
+           "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
+           "sww_create_shared", "sww_step_ensemble"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt"]
 
@@ -35,7 +36,8 @@ class SwwError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("jmin", ctypes.c_int), ("jmax", ctypes.c_int), ("radius", ctypes.c_double),
                 ("omega", ctypes.c_double), ("g", ctypes.c_double), ("H", ctypes.c_double),
-                ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
+                ("blocks_per_sm", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -82,6 +84,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_profile": [P, ctypes.c_uint32],
         "sww_profile_read": [P, ctypes.POINTER(ctypes.c_double), I64],
         "sww_mass_energy_static": [P, P, P, P],
+        "sww_create_shared": [ctypes.POINTER(Config), P, P, ctypes.POINTER(P)],
+        "sww_step_ensemble": [ctypes.POINTER(P), I, D, I, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -117,17 +121,29 @@ def _default_stream():
     return ctypes.c_void_p(None)
 
 
+def step_ensemble(models, dt=-1.0, nsteps=1, adapt=True):
+    """nsteps steps of every member; the members' steps overlap on the GPU
+    (sww_step_ensemble)."""
+    hs = (ctypes.c_void_p * len(models))(*[m._h.value for m in models])
+    _check(load().sww_step_ensemble(hs, len(models), float(dt), int(nsteps), int(bool(adapt))))
+
+
 class Model:
     """One adapted grid Jmin..Jmax and its state on the GPU (sww_create)."""
 
     def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
-                 cfl=0.8, eps=1e-2, stream=None):
+                 cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64"):
+        """share: another Model whose grid and tables this one reuses (sww_create_shared)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
-        self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps)
+        self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
+                          blocks_per_sm, {"fp64": 0, "fp32": 1}[precision])
         h = ctypes.c_void_p()
-        _check(lib.sww_create(ctypes.byref(self.cfg), stream if stream is not None else _default_stream(),
-                              ctypes.byref(h)))
+        st = stream if stream is not None else _default_stream()
+        if share is None:
+            _check(lib.sww_create(ctypes.byref(self.cfg), st, ctypes.byref(h)))
+        else:
+            _check(lib.sww_create_shared(ctypes.byref(self.cfg), st, share._h, ctypes.byref(h)))
         self._h = h
 
     def close(self):

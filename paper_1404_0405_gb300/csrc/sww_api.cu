@@ -13,10 +13,13 @@
 #include <cstring>
 #include <exception>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "grid.h"
@@ -55,12 +58,85 @@ __global__ void k_reset_red(unsigned long long* red) {
     }
 }
 
-__global__ void k_gather_counts(const DevLevel* lvs, int jmin, int jmax, int32_t* out) {
+template <class R>
+__global__ void k_gather_counts(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* out) {
     int j = jmin + int(threadIdx.x);
     if (j <= jmax) out[j] = *lvs[j].npatches;
 }
 
 constexpr int GHOST_HOPS = 5;
+
+template <typename T>
+T* dev_alloc(std::vector<void*>& allocs, size_t n) {
+    void* p = nullptr;
+    ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
+    allocs.push_back(p);
+    return static_cast<T*>(p);
+}
+
+// The grid and every geometric table of levels jmin..jmax on the device (read-only
+// after construction).  Handles with the same jmin, patch size, radius and rotation
+// rate share one Geometry; a handle uses the levels up to its own jmax.
+struct Geometry {
+    int jmin = 0, jmax = 0, patch = 0;
+    double radius = 0, omega = 0;
+    std::vector<DevLevel> lv;                 // geometry pointers only (FP64 tables)
+    std::vector<DevLevelT<float>> lvf;        // the same with FP32 stencil weights (on demand)
+    std::mutex mu;
+    std::vector<std::vector<double>> xyz;     // host node positions per level (flattened)
+    std::vector<std::vector<int32_t>> edges;  // host edge (origin, end) pairs per level
+    std::vector<void*> allocs;
+
+    template <typename T>
+    T* up(const std::vector<T>& v) {
+        T* p = dev_alloc<T>(allocs, v.size());
+        ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
+        return p;
+    }
+    template <typename T, int K>
+    T* up_slots(const std::vector<T> (&v)[K], int count) {
+        size_t n = v[0].size();
+        std::vector<T> flat(n * count);
+        for (int k = 0; k < count; ++k) std::memcpy(flat.data() + k * n, v[k].data(), n * sizeof(T));
+        return up(flat);
+    }
+    // FP32 copies of the stencil weights (rounded once from the FP64 tables); the
+    // FP64 areas and lengths stay for the mass and energy sums
+    void ensure_fp32() {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!lvf.empty()) return;
+        std::vector<DevLevelT<float>> out(lv.size());
+        for (int j = jmin; j <= jmax; ++j) {
+            const DevLevel& D = lv[j];
+            DevLevelT<float>& F = out[j];
+            F.J = D.J, F.n = D.n, F.p = D.p, F.np = D.np, F.nelem = D.nelem, F.N = D.N, F.E = D.E, F.T = D.T;
+            F.npatch = D.npatch, F.dx = D.dx;
+            F.en = D.en, F.et = D.et, F.tn = D.tn, F.te = D.te, F.deg = D.deg, F.ring_e = D.ring_e, F.f2c = D.f2c;
+            F.cor_i = D.cor_i, F.par = D.par, F.fe_kind = D.fe_kind, F.fe_ce = D.fe_ce, F.vst = D.vst;
+            F.c2f = D.c2f, F.mid = D.mid, F.half = D.half, F.mk_i = D.mk_i, F.rf_fi = D.rf_fi, F.rf_ci = D.rf_ci;
+            F.A_i64 = D.A_i64, F.d_e64 = D.d_e64, F.l_e64 = D.l_e64;
+            auto cv = [&](const double* x, int64_t n) -> const float* {
+                if (!x) return nullptr;
+                float* y = dev_alloc<float>(allocs, n);
+                launch_convert(x, y, n, cudaStream_t(0));
+                return y;
+            };
+            F.A_i = cv(D.A_i, D.N), F.A_v = cv(D.A_v, D.T), F.kite = cv(D.kite, 3 * D.T);
+            F.d_e = cv(D.d_e, D.E), F.l_e = cv(D.l_e, D.E), F.f_v = cv(D.f_v, D.T), F.f_n = cv(D.f_n, D.N);
+            F.cor_w = cv(D.cor_w, int64_t(COR) * D.E);
+            F.ptw = cv(D.ptw, 4 * D.N);
+            F.vw = cv(D.vw, int64_t(VST) * D.E);
+            F.mk_w = cv(D.mk_w, 12 * D.N);
+            F.rf_fw = cv(D.rf_fw, int64_t(RF_F) * D.E);
+            F.rf_cw = cv(D.rf_cw, int64_t(RF_C) * D.E);
+        }
+        ck(cudaDeviceSynchronize(), "fp32 tables");
+        lvf.swap(out);
+    }
+    ~Geometry() {
+        for (void* p : allocs) cudaFree(p);
+    }
+};
 
 }  // namespace
 
@@ -69,10 +145,12 @@ struct sww_handle {
     cudaStream_t user = nullptr;    // the caller's stream
     cudaStream_t stream = nullptr;  // the library's own stream
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    std::vector<DevLevel> lv;
-    DevLevel* d_lvs = nullptr;
-    std::vector<std::vector<double>> xyz;     // host node positions per level (flattened)
-    std::vector<std::vector<int32_t>> edges;  // host edge (origin, end) pairs per level
+    std::shared_ptr<Geometry> geo;  // shared grid and tables
+    // geometry of geo plus this handle's state arrays, in the handle's precision
+    std::vector<DevLevelT<double>> lv;
+    std::vector<DevLevelT<float>> lvf;
+    void* d_lvs = nullptr;          // device copy of lv or lvf
+    double* stage = nullptr;        // FP64 staging buffer of FP32 handles (set_state)
     std::vector<void*> allocs;
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
@@ -108,23 +186,7 @@ struct sww_handle {
 
     template <typename T>
     T* alloc(size_t n) {
-        void* p = nullptr;
-        ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
-        allocs.push_back(p);
-        return static_cast<T*>(p);
-    }
-    template <typename T>
-    T* up(const std::vector<T>& v) {
-        T* p = alloc<T>(v.size());
-        ck(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), "upload");
-        return p;
-    }
-    template <typename T, int K>
-    T* up_slots(const std::vector<T> (&v)[K], int count) {
-        size_t n = v[0].size();
-        std::vector<T> flat(n * count);
-        for (int k = 0; k < count; ++k) std::memcpy(flat.data() + k * n, v[k].data(), n * sizeof(T));
-        return up(flat);
+        return dev_alloc<T>(allocs, n);
     }
     void drop_graphs() {
         for (auto& g : graphs) cudaGraphExecDestroy(g.second.first);
@@ -146,53 +208,70 @@ struct sww_handle {
 
 namespace {
 
-void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side, int64_t coarse_E) {
+template <class R>
+std::vector<DevLevelT<R>>& lvl(sww_handle* h);
+template <>
+std::vector<DevLevelT<double>>& lvl<double>(sww_handle* h) {
+    return h->lv;
+}
+template <>
+std::vector<DevLevelT<float>>& lvl<float>(sww_handle* h) {
+    return h->lvf;
+}
+template <class R>
+const std::vector<DevLevelT<R>>& lvl(const sww_handle* h) {
+    return lvl<R>(const_cast<sww_handle*>(h));
+}
+template <class R>
+DevLevelT<R>* dlv(const sww_handle* h) {
+    return static_cast<DevLevelT<R>*>(h->d_lvs);
+}
+// sizes of level j (any precision)
+const DevLevel& meta(const sww_handle* h, int j) { return h->geo->lv[j]; }
+
+// Calls f(R()) with R the handle's working precision.
+template <class F>
+int by_prec(const sww_handle* h, F&& f) {
+    return h->cfg.precision == SWW_FP32 ? f(float(0)) : f(double(0));
+}
+
+// geometry of one level (fine-side tables when a coarser level exists, coarse-side
+// tables when a finer one does)
+void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side) {
     DevLevel D{};
     D.J = L.J, D.n = L.n, D.p = L.p, D.np = L.np, D.nelem = L.nelem, D.N = L.N, D.E = L.E, D.T = L.T, D.npatch = L.npatch;
-    D.dx = nominal_spacing(L.J, h->cfg.radius);
-    D.en = h->up_slots(L.en, 2);
-    D.et = h->up_slots(L.et, 2);
-    D.tn = h->up_slots(L.tn, 3);
-    D.te = h->up_slots(L.te, 3);
-    D.deg = h->up(L.deg);
-    D.ring_e = h->up_slots(L.ring_e, 6);
-    D.A_i = h->up(L.A_i), D.A_v = h->up(L.A_v), D.kite = h->up_slots(L.kite, 3);
-    D.d_e = h->up(L.d_e), D.l_e = h->up(L.l_e), D.f_v = h->up(L.f_v), D.f_n = h->up(L.f_n);
-    D.cor_i = h->up_slots(L.cor_i, COR);
-    D.cor_w = h->up_slots(L.cor_w, COR);
+    D.dx = nominal_spacing(L.J, G.radius);
+    D.en = G.up_slots(L.en, 2);
+    D.et = G.up_slots(L.et, 2);
+    D.tn = G.up_slots(L.tn, 3);
+    D.te = G.up_slots(L.te, 3);
+    D.deg = G.up(L.deg);
+    D.ring_e = G.up_slots(L.ring_e, 6);
+    D.A_i = G.up(L.A_i), D.A_v = G.up(L.A_v), D.kite = G.up_slots(L.kite, 3);
+    D.d_e = G.up(L.d_e), D.l_e = G.up(L.l_e), D.f_v = G.up(L.f_v), D.f_n = G.up(L.f_n);
+    D.A_i64 = D.A_i, D.d_e64 = D.d_e, D.l_e64 = D.l_e;
+    D.cor_i = G.up_slots(L.cor_i, COR);
+    D.cor_w = G.up_slots(L.cor_w, COR);
     if (fine_side) {
-        D.par = h->up_slots(L.par, 4);
-        D.ptw = h->up_slots(L.ptw, 4);
-        D.fe_kind = h->up(L.fe_kind);
-        D.fe_ce = h->up(L.fe_ce);
-        D.vst = h->up_slots(L.vst, VST);
-        D.vw = h->up_slots(L.vw, VST);
+        D.par = G.up_slots(L.par, 4);
+        D.ptw = G.up_slots(L.ptw, 4);
+        D.fe_kind = G.up(L.fe_kind);
+        D.fe_ce = G.up(L.fe_ce);
+        D.vst = G.up_slots(L.vst, VST);
+        D.vw = G.up_slots(L.vw, VST);
     }
     if (coarse_side) {
-        D.c2f = h->up(L.c2f), D.mid = h->up(L.mid), D.half = h->up_slots(L.half, 2);
-        D.mk_i = h->up_slots(L.mk_i, 12);
-        D.mk_w = h->up_slots(L.mk_w, 12);
-        D.rf_fi = h->up_slots(L.rf_fi, RF_F);
-        D.rf_fw = h->up_slots(L.rf_fw, RF_F);
-        D.rf_ci = h->up_slots(L.rf_ci, RF_C);
-        D.rf_cw = h->up_slots(L.rf_cw, RF_C);
+        D.c2f = G.up(L.c2f), D.mid = G.up(L.mid), D.half = G.up_slots(L.half, 2);
+        D.mk_i = G.up_slots(L.mk_i, 12);
+        D.mk_w = G.up_slots(L.mk_w, 12);
+        D.rf_fi = G.up_slots(L.rf_fi, RF_F);
+        D.rf_fw = G.up_slots(L.rf_fw, RF_F);
+        D.rf_ci = G.up_slots(L.rf_ci, RF_C);
+        D.rf_cw = G.up_slots(L.rf_cw, RF_C);
     }
-    const int64_t N = L.N, E = L.E, T = L.T;
-    double** dN[] = {&D.dh, &D.dh0, &D.dha, &D.dht, &D.B, &D.c, &D.hdet};
-    for (auto p : dN) *p = h->alloc<double>(N);
-    double** dE[] = {&D.u, &D.u0, &D.ua, &D.ut, &D.F, &D.Q, &D.ui};
-    for (auto p : dE) *p = h->alloc<double>(E);
-    D.q = h->alloc<double>(T);
-    D.ue = h->alloc<double>(coarse_E > 0 ? coarse_E : 1);
-    uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
-    for (auto p : bN) *p = h->alloc<uint8_t>(N);
-    D.eflag = h->alloc<uint8_t>(E);
-    D.pflag = h->alloc<uint8_t>(L.npatch);
-    D.patches = h->alloc<int32_t>(L.npatch + 1);
-    D.npatches = h->alloc<int32_t>(1);
     // f2c of this level: coarse node at the same place (-1 for odd nodes)
     {
-        std::vector<int32_t> f2c(N, -1);
+        std::vector<int32_t> f2c(L.N, -1);
         if (fine_side) {
             // even element (2i, 2j) <-> coarse element (i, j); poles map to poles
             int64_t n = L.n, p = L.p, np = L.np;
@@ -208,19 +287,94 @@ void upload_level(sww_handle* h, HostLevel& L, bool fine_side, bool coarse_side,
             f2c[L.nelem] = int32_t(10 * cn * cn);
             f2c[L.nelem + 1] = int32_t(10 * cn * cn + 1);
         }
-        D.f2c = h->up(f2c);
+        D.f2c = G.up(f2c);
     }
-    for (double* p : {D.dh, D.dh0, D.dha, D.dht, D.B, D.c, D.hdet}) ck(cudaMemset(p, 0, N * sizeof(double)), "memset");
-    for (double* p : {D.u, D.u0, D.ua, D.ut, D.F, D.Q, D.ui}) ck(cudaMemset(p, 0, E * sizeof(double)), "memset");
-    ck(cudaMemset(D.q, 0, T * sizeof(double)), "memset");
-    for (uint8_t* p : {D.nflag, D.sig, D.tmask, D.band0, D.band1}) ck(cudaMemset(p, 0, N), "memset");
+    G.lv[L.J] = D;
+}
+
+std::shared_ptr<Geometry> build_geometry(int jmin, int jmax, int patch, double radius, double omega) {
+    auto G = std::make_shared<Geometry>();
+    G->jmin = jmin, G->jmax = jmax, G->patch = patch, G->radius = radius, G->omega = omega;
+    Hierarchy H;
+    build_hierarchy(H, jmin, jmax, patch, radius, omega);
+    G->lv.assign(jmax + 1, DevLevel{});
+    G->xyz.assign(jmax + 1, {});
+    G->edges.assign(jmax + 1, {});
+    for (int j = jmin; j <= jmax; ++j) {
+        HostLevel& L = H.lv[j];
+        upload_geometry(*G, L, j > jmin, j < jmax);
+        G->xyz[j].resize(3 * L.N);
+        for (int64_t v = 0; v < L.N; ++v)
+            G->xyz[j][3 * v] = L.xyz[v].x, G->xyz[j][3 * v + 1] = L.xyz[v].y, G->xyz[j][3 * v + 2] = L.xyz[v].z;
+        G->edges[j].resize(2 * L.E);
+        for (int64_t e = 0; e < L.E; ++e) G->edges[j][2 * e] = L.en[0][e], G->edges[j][2 * e + 1] = L.en[1][e];
+    }
+    return G;
+}
+
+// state and work arrays of one level of a handle (zeroed)
+template <class R>
+void alloc_state(sww_handle* h, int j) {
+    DevLevelT<R> D;
+    if constexpr (std::is_same<R, float>::value)
+        D = h->geo->lvf[j];
+    else
+        D = h->geo->lv[j];
+    const int64_t N = D.N, E = D.E, T = D.T;
+    const int64_t coarse_E = j > h->cfg.jmin ? h->geo->lv[j - 1].E : 1;
+    R** dN[] = {&D.dh, &D.dh0, &D.dha, &D.dht, &D.B, &D.c, &D.hdet};
+    for (auto p : dN) *p = h->alloc<R>(N);
+    R** dE[] = {&D.u, &D.u0, &D.ua, &D.ut, &D.F, &D.Q, &D.ui};
+    for (auto p : dE) *p = h->alloc<R>(E);
+    D.q = h->alloc<R>(T);
+    D.ue = h->alloc<R>(coarse_E);
+    uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
+    for (auto p : bN) *p = h->alloc<uint8_t>(N);
+    D.eflag = h->alloc<uint8_t>(E);
+    D.pflag = h->alloc<uint8_t>(D.npatch);
+    D.patches = h->alloc<int32_t>(D.npatch + 1);
+    D.npatches = h->alloc<int32_t>(1);
+    for (auto p : dN) ck(cudaMemset(*p, 0, N * sizeof(R)), "memset");
+    for (auto p : dE) ck(cudaMemset(*p, 0, E * sizeof(R)), "memset");
+    ck(cudaMemset(D.q, 0, T * sizeof(R)), "memset");
+    for (auto p : bN) ck(cudaMemset(*p, 0, N), "memset");
     ck(cudaMemset(D.eflag, 0, E), "memset");
-    ck(cudaMemset(D.ue, 0, (coarse_E > 0 ? coarse_E : 1) * sizeof(double)), "memset");
+    ck(cudaMemset(D.ue, 0, coarse_E * sizeof(R)), "memset");
     ck(cudaMemset(D.npatches, 0, sizeof(int32_t)), "memset");
-    h->lv[L.J] = D;
+    lvl<R>(h)[j] = D;
 }
 
 void check_launch() { ck(cudaGetLastError(), "kernel launch"); }
+
+// host FP64 values -> device array of the working precision (on the handle's
+// stream; the caller synchronises before the host data goes away)
+template <class R>
+void to_device(sww_handle* h, R* dst, const double* src, int64_t n) {
+    if constexpr (std::is_same<R, double>::value) {
+        ck(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream), "to_device");
+    } else {
+        std::vector<R> tmp(src, src + n);
+        ck(cudaMemcpyAsync(dst, tmp.data(), n * sizeof(R), cudaMemcpyHostToDevice, h->stream), "to_device");
+        ck(cudaStreamSynchronize(h->stream), "to_device");   // tmp lives on this frame
+    }
+}
+
+// device array of the working precision -> host FP64 values (synchronous)
+template <class R>
+void from_device(sww_handle* h, double* dst, const R* src, int64_t n) {
+    std::vector<R> tmp;
+    void* host = dst;
+    if constexpr (!std::is_same<R, double>::value) {
+        tmp.resize(n);
+        host = tmp.data();
+    }
+    ck(cudaEventRecord(h->ev_in, h->user), "join in");
+    ck(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "join in");
+    ck(cudaMemcpyAsync(host, src, n * sizeof(R), cudaMemcpyDeviceToHost, h->stream), "from_device");
+    ck(cudaStreamSynchronize(h->stream), "from_device");
+    if constexpr (!std::is_same<R, double>::value)
+        for (int64_t i = 0; i < n; ++i) dst[i] = double(tmp[i]);
+}
 
 // Orders the library's stream after the caller's stream on entry and the caller's
 // stream after the library's stream on exit.
@@ -255,52 +409,64 @@ struct Trace {
     }
 };
 
-Work work_all(const sww_handle* h) { return Work{h->d_lvs, h->all_list, h->all_count, h->S, h->grid_all}; }
-Work work_level(const sww_handle* h, int j) {
-    return Work{nullptr, h->lv[j].patches, h->lv[j].npatches, h->S, h->grid_lv[j]};
+template <class R>
+WorkT<R> work_all(const sww_handle* h) {
+    return WorkT<R>{dlv<R>(h), h->all_list, h->all_count, h->S, h->grid_all};
+}
+template <class R>
+WorkT<R> work_level(const sww_handle* h, int j) {
+    const DevLevelT<R>& L = lvl<R>(h)[j];
+    return WorkT<R>{nullptr, L.patches, L.npatches, h->S, h->grid_lv[j]};
 }
 
 // ------------------------------------------------------------------ sequences
 
+template <class R>
 void fill_ghosts(sww_handle* h) {
+    auto& lv = lvl<R>(h);
     for (int j = h->cfg.jmin + 1; j <= h->jtop; ++j) {
         Trace t(h, SWW_K_FILL);
-        launch_fill(h->lv[j], h->lv[j - 1], work_level(h, j), h->stream);
+        launch_fill(lv[j], lv[j - 1], work_level<R>(h, j), h->stream);
     }
 }
 
 // one trend evaluation (Sec. 3.1): ghosts, q/K/B/F/qF^perp on every level, then the
 // restriction of B, F and q F^perp from the top level down to Jmin
+template <class R>
 void trend(sww_handle* h) {
     const int j0 = h->cfg.jmin;
     cudaStream_t s = h->stream;
-    Work W = work_all(h);
-    fill_ghosts(h);
+    auto& lv = lvl<R>(h);
+    WorkT<R> W = work_all<R>(h);
+    fill_ghosts<R>(h);
     { Trace t(h, SWW_K_PV); launch_pv_flux(W, h->cfg.H, s); }
     { Trace t(h, SWW_K_CORIOLIS); launch_node_coriolis(W, h->cfg.g, s); }
     for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_RESTRICT);
-        launch_restrict(h->lv[j], h->lv[j + 1], work_level(h, j), s);
+        launch_restrict(lv[j], lv[j + 1], work_level<R>(h, j), s);
     }
 }
 
+template <class R>
 void update(sww_handle* h, const RKStage& st) {
     Trace t(h, SWW_K_UPDATE);
-    launch_update(work_all(h), st, h->dt, h->stream);
+    launch_update(work_all<R>(h), st, h->dt, h->stream);
 }
 
+template <class R>
 void compute_dt(sww_handle* h) {
     Trace t(h, SWW_K_DT);
     count_launch(1);
     k_reset_red<<<1, 32, 0, h->stream>>>(h->red);
-    launch_dt(work_all(h), h->cfg.H, h->cfg.g, h->red, h->stream);
+    launch_dt(work_all<R>(h), h->cfg.H, h->cfg.g, h->red, h->stream);
     launch_dt_final(h->red, h->cfg.cfl, h->dt, h->stream);
 }
 
 // list sizes of every level into pinned host memory (read after the next sync)
+template <class R>
 void read_counts(sww_handle* h) {
     count_launch(1);
-    k_gather_counts<<<1, 32, 0, h->stream>>>(h->d_lvs, h->cfg.jmin, h->cfg.jmax, h->d_counts);
+    k_gather_counts<R><<<1, 32, 0, h->stream>>>(dlv<R>(h), h->cfg.jmin, h->cfg.jmax, h->d_counts);
     ck(cudaMemcpyAsync(h->h_counts, h->d_counts, sizeof(int32_t) * (h->cfg.jmax + 1), cudaMemcpyDeviceToHost, h->stream),
        "counts");
 }
@@ -315,66 +481,81 @@ void update_top(sww_handle* h) {
 
 // Thread ranges of levels ja..jb for a multi-level dense launch.
 template <typename Count>
-Span span_of(const sww_handle* h, int ja, int jb, Count count) {
+Span span_of(const sww_handle* h, int ja, int jb, Count count, int tail_j = -1, int64_t tail_threads = 0) {
     Span sp{};
     sp.ja = ja, sp.jb = jb;
+    sp.tail_j = -1;
     int64_t t = 0;
     for (int j = ja; j <= jb; ++j) {
         sp.off[j - ja] = t;
-        t += count(h->lv[j]);
+        int64_t n = count(meta(h, j));
+        if (j == tail_j) {
+            sp.tail_j = j, sp.tail_n = n;
+            n = std::min(n, tail_threads);
+        }
+        t += n;
     }
     sp.off[jb + 1 - ja] = t;
     return sp;
 }
 
-MaskArgs mask_args(const sww_handle* h, int j0, int j1) {
-    MaskArgs a{};
-    a.lvs = h->d_lvs, a.host = h->lv.data(), a.ja = j0, a.jb = j1, a.hops = GHOST_HOPS, a.thr = h->thr;
+// The level above the top live level (j1 > top) is a tail level of the mask spans:
+// a fixed number of striding threads that leave at once unless the level below holds
+// a significant point.
+template <class R>
+MaskArgsT<R> mask_args(const sww_handle* h, int j0, int j1, bool allow_tail = true) {
+    MaskArgsT<R> a{};
+    a.lvs = dlv<R>(h), a.host = lvl<R>(h).data(), a.ja = j0, a.jb = j1, a.hops = GHOST_HOPS, a.thr = h->thr;
     auto N = [](const DevLevel& L) { return L.N; };
     auto E = [](const DevLevel& L) { return L.E; };
     auto P = [](const DevLevel& L) { return L.npatch; };
+    const int tail = (allow_tail && j1 > h->jtop) ? j1 : -1;
+    const int64_t tt = int64_t(h->grid_all) * 256;
     int jf = std::min(j0 + 1, j1);
-    a.nodes_f = span_of(h, jf, j1, N);
-    a.edges_f = span_of(h, jf, j1, E);
+    a.nodes_f = span_of(h, jf, j1, N, tail, tt);
+    a.edges_f = span_of(h, jf, j1, E, tail, tt);
     if (j1 == j0) a.nodes_f.off[1] = 0, a.edges_f.off[1] = 0;   // no level above Jmin
-    a.nodes = span_of(h, j0, j1, N);
-    a.edges = span_of(h, j0, j1, E);
+    a.nodes = span_of(h, j0, j1, N, tail, tt);
+    a.edges = span_of(h, j0, j1, E, tail, tt);
     a.nodes_c = span_of(h, j0, std::max(j0, j1 - 1), N);
-    a.patches = span_of(h, j0, j1, P);
+    a.patches = span_of(h, j0, j1, P, tail, int64_t(h->grid_all));
     a.sig_any = h->sig_any;
     a.sig_any_len = h->cfg.jmax + 2;
-    a.skip = j1 > h->jtop ? j1 : -1;
+    a.tail_blocks = h->grid_all;
     return a;
 }
 
 // Mask construction and inverse transform.  Levels above top + 1 hold no live point
 // and can gain none in one adaptation, so the byte-wide passes stop there.
+template <class R>
 void mask_and_inverse(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = std::min(h->jtop + 1, h->cfg.jmax);
     cudaStream_t s = h->stream;
+    auto& lv = lvl<R>(h);
     {
         Trace tm(h, SWW_K_MASK);
-        MaskArgs a = mask_args(h, j0, j1);
+        MaskArgsT<R> a = mask_args<R>(h, j0, j1);
         launch_mask(a, s);
-        launch_concat(h->d_lvs, j0, h->cfg.jmax, h->all_list, h->all_count, s);
+        launch_concat(dlv<R>(h), j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
     for (int j = j0 + 1; j <= j1; ++j) {
-        { Trace t(h, SWW_K_INVERSE); launch_inverse(h->lv[j], h->lv[j - 1], work_level(h, j), s); }
-        { Trace t(h, SWW_K_FILL); launch_fill(h->lv[j], h->lv[j - 1], work_level(h, j), s); }
+        { Trace t(h, SWW_K_INVERSE); launch_inverse(lv[j], lv[j - 1], work_level<R>(h, j), s); }
+        { Trace t(h, SWW_K_FILL); launch_fill(lv[j], lv[j - 1], work_level<R>(h, j), s); }
     }
 }
 
+template <class R>
 void adapt(sww_handle* h, double eh, double eu) {
     cudaStream_t s = h->stream;
-    { Trace t(h, SWW_K_COEFF); launch_details(work_all(h), h->cfg.jmin, s); }
+    { Trace t(h, SWW_K_COEFF); launch_details(work_all<R>(h), h->cfg.jmin, s); }
     {
         Trace t(h, SWW_K_MASK);
         ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
-        launch_maxabs(work_all(h), h->red, s);
+        launch_maxabs(work_all<R>(h), h->red, s);
         launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
     }
-    mask_and_inverse(h);
+    mask_and_inverse<R>(h);
 }
 
 const RKStage* stages(int rk, int& n) {
@@ -398,35 +579,38 @@ const RKStage* stages(int rk, int& n) {
 
 // One RK step with its partial transform and (optionally) adaptation; ends with the
 // device-to-host copies of the time step and the list sizes.
+template <class R>
 void one_step(sww_handle* h, double dt, bool do_adapt) {
     const int j0 = h->cfg.jmin;
+    auto& lv = lvl<R>(h);
     if (dt > 0) {
         count_launch(1);
         k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
     } else {
-        compute_dt(h);
+        compute_dt<R>(h);
     }
-    { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all(h), h->stream); }
+    { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all<R>(h), h->stream); }
     int ns;
     const RKStage* st = stages(h->cfg.rk, ns);
     for (int k = 0; k < ns; ++k) {
-        trend(h);
-        update(h, st[k]);
+        trend<R>(h);
+        update<R>(h, st[k]);
     }
     for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_PARTIAL);
-        launch_partial(h->lv[j], h->lv[j + 1], work_level(h, j), h->stream);
+        launch_partial(lv[j], lv[j + 1], work_level<R>(h, j), h->stream);
     }
-    fill_ghosts(h);
-    if (do_adapt) adapt(h, -1.0, -1.0);
-    read_counts(h);
+    fill_ghosts<R>(h);
+    if (do_adapt) adapt<R>(h, -1.0, -1.0);
+    read_counts<R>(h);
     ck(cudaMemcpyAsync(h->h_dt, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
 }
 
 // Run one step through a captured graph (eager when tracing).
-void run_step(sww_handle* h, double dt, bool do_adapt) {
+template <class R>
+void run_step_t(sww_handle* h, double dt, bool do_adapt) {
     if (h->prof_mask) {
-        one_step(h, dt, do_adapt);
+        one_step<R>(h, dt, do_adapt);
         return;
     }
     auto key = std::make_tuple(h->jtop, int(do_adapt), dt > 0 ? dt : -1.0);
@@ -436,7 +620,7 @@ void run_step(sww_handle* h, double dt, bool do_adapt) {
         int64_t before = kernel_launches();
         ck(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         try {
-            one_step(h, dt, do_adapt);
+            one_step<R>(h, dt, do_adapt);
         } catch (...) {
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(h->stream, &g);
@@ -455,6 +639,13 @@ void run_step(sww_handle* h, double dt, bool do_adapt) {
     }
     ck(cudaGraphLaunch(it->second.first, h->stream), "graph launch");
     count_launch(it->second.second);
+}
+
+void run_step(sww_handle* h, double dt, bool do_adapt) {
+    by_prec(h, [&](auto r) {
+        run_step_t<decltype(r)>(h, dt, do_adapt);
+        return 0;
+    });
 }
 
 int check_level(const sww_handle* h, int level) {
@@ -476,13 +667,7 @@ int guarded(F&& f) {
     }
 }
 
-}  // namespace
-
-extern "C" {
-
-int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
-    if (!cfg || !out) return fail(SWW_E_ARG, "null argument");
-    *out = nullptr;
+int check_config(const sww_config* cfg) {
     if (cfg->jmin < 1 || cfg->jmax < cfg->jmin || cfg->jmax > 11) return fail(SWW_E_ARG, "need 1 <= jmin <= jmax <= 11");
     if (!(cfg->radius > 0) || !(cfg->g > 0) || !(cfg->H > 0) || !(cfg->cfl > 0))
         return fail(SWW_E_ARG, "radius, g, H and cfl must be positive");
@@ -490,6 +675,14 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
     if (cfg->patch < 1 || (cfg->patch & (cfg->patch - 1)) || cfg->patch > 16)
         return fail(SWW_E_ARG, "patch must be a power of two <= 16");
     if (cfg->rk != SWW_RK4 && cfg->rk != SWW_SSP43) return fail(SWW_E_ARG, "rk must be SWW_RK4 or SWW_SSP43");
+    if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32) return fail(SWW_E_ARG, "blocks_per_sm must be 0..32");
+    if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
+        return fail(SWW_E_ARG, "precision must be SWW_FP64 or SWW_FP32");
+    return SWW_OK;
+}
+
+// A handle over levels cfg->jmin..cfg->jmax of `geo` (built here when null).
+int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry> geo, sww_handle** out) {
     sww_handle* h = new (std::nothrow) sww_handle();
     if (!h) return fail(SWW_E_POOL, "host allocation failed");
     int rc = guarded([&]() -> int {
@@ -501,29 +694,35 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
         int dev = 0;
         ck(cudaGetDevice(&dev), "cudaGetDevice");
         ck(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-        Hierarchy H;
-        build_hierarchy(H, cfg->jmin, cfg->jmax, cfg->patch, cfg->radius, cfg->omega);
-        h->lv.assign(cfg->jmax + 1, DevLevel{});
+        h->geo = geo ? geo : build_geometry(cfg->jmin, cfg->jmax, cfg->patch, cfg->radius, cfg->omega);
+        const bool fp32 = cfg->precision == SWW_FP32;
+        if (fp32) h->geo->ensure_fp32();
+        h->lv.assign(fp32 ? 0 : cfg->jmax + 1, DevLevelT<double>{});
+        h->lvf.assign(fp32 ? cfg->jmax + 1 : 0, DevLevelT<float>{});
         h->grid_lv.assign(cfg->jmax + 1, 1);
-        h->xyz.assign(cfg->jmax + 1, {});
-        h->edges.assign(cfg->jmax + 1, {});
         h->S = cfg->patch * cfg->patch;
         int64_t total = 0;
-        const int64_t cap = int64_t(h->nsm) * 4;   // grid-stride launches: 4 blocks of 256 per SM
+        // grid-stride launches: blocks_per_sm blocks of 256 per SM
+        const int64_t cap = int64_t(h->nsm) * (cfg->blocks_per_sm > 0 ? cfg->blocks_per_sm : 4);
         for (int j = cfg->jmin; j <= cfg->jmax; ++j) {
-            HostLevel& L = H.lv[j];
-            upload_level(h, L, j > cfg->jmin, j < cfg->jmax, j > cfg->jmin ? H.lv[j - 1].E : 0);
-            h->xyz[j].resize(3 * L.N);
-            for (int64_t v = 0; v < L.N; ++v) h->xyz[j][3 * v] = L.xyz[v].x, h->xyz[j][3 * v + 1] = L.xyz[v].y, h->xyz[j][3 * v + 2] = L.xyz[v].z;
-            h->edges[j].resize(2 * L.E);
-            for (int64_t e = 0; e < L.E; ++e) h->edges[j][2 * e] = L.en[0][e], h->edges[j][2 * e + 1] = L.en[1][e];
-            int64_t items = (L.npatch + 1) * h->S;
+            if (fp32)
+                alloc_state<float>(h, j);
+            else
+                alloc_state<double>(h, j);
+            int64_t items = (meta(h, j).npatch + 1) * h->S;
             h->grid_lv[j] = unsigned(std::min<int64_t>(blocks_for(items, 256), cap));
-            total += L.npatch + 1;
+            total += meta(h, j).npatch + 1;
         }
         h->grid_all = unsigned(std::min<int64_t>(blocks_for(total * h->S, 256), cap));
-        h->d_lvs = h->alloc<DevLevel>(cfg->jmax + 1);
-        ck(cudaMemcpy(h->d_lvs, h->lv.data(), sizeof(DevLevel) * (cfg->jmax + 1), cudaMemcpyHostToDevice), "levels");
+        if (fp32) {
+            h->d_lvs = h->alloc<DevLevelT<float>>(cfg->jmax + 1);
+            ck(cudaMemcpy(h->d_lvs, h->lvf.data(), sizeof(DevLevelT<float>) * (cfg->jmax + 1), cudaMemcpyHostToDevice),
+               "levels");
+        } else {
+            h->d_lvs = h->alloc<DevLevelT<double>>(cfg->jmax + 1);
+            ck(cudaMemcpy(h->d_lvs, h->lv.data(), sizeof(DevLevelT<double>) * (cfg->jmax + 1), cudaMemcpyHostToDevice),
+               "levels");
+        }
         h->all_list = h->alloc<int32_t>(total);
         h->all_count = h->alloc<int32_t>(1);
         h->d_counts = h->alloc<int32_t>(cfg->jmax + 1);
@@ -538,7 +737,7 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
         h->thr = h->alloc<double>(2);
         h->dt = h->alloc<double>(1);
         h->sums = h->alloc<double>(2);
-        h->part = h->alloc<double>(4 * size_t(sums_blocks(h->lv[cfg->jmin])));
+        h->part = h->alloc<double>(4 * size_t(sums_blocks(meta(h, cfg->jmin))));
         ck(cudaMemset(h->thr, 0, 2 * sizeof(double)), "memset");
         ck(cudaMemset(h->dt, 0, sizeof(double)), "memset");
         ck(cudaMemset(h->all_count, 0, sizeof(int32_t)), "memset");
@@ -554,6 +753,30 @@ int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
     return SWW_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int sww_create(const sww_config* cfg, void* stream, sww_handle** out) {
+    if (!cfg || !out) return fail(SWW_E_ARG, "null argument");
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    return create_handle(cfg, stream, nullptr, out);
+}
+
+int sww_create_shared(const sww_config* cfg, void* stream, const sww_handle* share, sww_handle** out) {
+    if (!cfg || !out || !share) return fail(SWW_E_ARG, "null argument");
+    *out = nullptr;
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    const Geometry& G = *share->geo;
+    if (cfg->jmin != G.jmin || cfg->patch != G.patch || cfg->radius != G.radius || cfg->omega != G.omega)
+        return fail(SWW_E_ARG, "shared grid needs the same jmin, patch, radius and omega");
+    if (cfg->jmax > G.jmax) return fail(SWW_E_ARG, "shared grid has fewer levels than jmax");
+    return create_handle(cfg, stream, share->geo, out);
+}
+
 int sww_destroy(sww_handle* h) {
     if (!h) return SWW_OK;
     delete h;
@@ -563,7 +786,7 @@ int sww_destroy(sww_handle* h) {
 int sww_level_sizes(const sww_handle* h, int level, int64_t* nn, int64_t* ne, int64_t* nt, int64_t* np) {
     int rc = check_level(h, level);
     if (rc) return rc;
-    const DevLevel& L = h->lv[level];
+    const DevLevel& L = meta(h, level);
     if (nn) *nn = L.N;
     if (ne) *ne = L.E;
     if (nt) *nt = L.T;
@@ -574,8 +797,9 @@ int sww_level_sizes(const sww_handle* h, int level, int64_t* nn, int64_t* ne, in
 int sww_get_grid(const sww_handle* h, int level, double* node_xyz, int32_t* edge_nodes) {
     int rc = check_level(h, level);
     if (rc) return rc;
-    if (node_xyz) std::memcpy(node_xyz, h->xyz[level].data(), h->xyz[level].size() * sizeof(double));
-    if (edge_nodes) std::memcpy(edge_nodes, h->edges[level].data(), h->edges[level].size() * sizeof(int32_t));
+    const Geometry& G = *h->geo;
+    if (node_xyz) std::memcpy(node_xyz, G.xyz[level].data(), G.xyz[level].size() * sizeof(double));
+    if (edge_nodes) std::memcpy(edge_nodes, G.edges[level].data(), G.edges[level].size() * sizeof(int32_t));
     return SWW_OK;
 }
 
@@ -584,21 +808,33 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
     return guarded([&]() -> int {
         const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
         cudaStream_t s = h->stream;
-        {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
             Join jn(h);
-            DevLevel& F = h->lv[j1];
+            auto& lv = lvl<R>(h);
+            DevLevelT<R>& F = lv[j1];
             cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-            ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
-            ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
-            for (int j = j1; j > j0; --j) launch_restrict_full(h->lv[j - 1], h->lv[j], s);
-            MaskArgs a = mask_args(h, j0, j1);
-            launch_live_all(h->d_lvs, a.nodes, a.edges, s);
-            if (j1 > j0) launch_covered_all(h->d_lvs, a.nodes_c, s);
-            launch_patches_all(h->d_lvs, a.patches, s);
-            launch_concat(h->d_lvs, j0, j1, h->all_list, h->all_count, s);
-            read_counts(h);
+            if constexpr (std::is_same<R, double>::value) {
+                ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
+                ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
+            } else {
+                // FP64 input rounded once to the working precision
+                if (!h->stage) h->stage = h->alloc<double>(std::max(F.N, F.E));
+                ck(cudaMemcpyAsync(h->stage, dh, F.N * sizeof(double), kind, s), "set_state dh");
+                launch_convert(h->stage, F.dh, F.N, s);
+                ck(cudaMemcpyAsync(h->stage, u, F.E * sizeof(double), kind, s), "set_state u");
+                launch_convert(h->stage, F.u, F.E, s);
+            }
+            for (int j = j1; j > j0; --j) launch_restrict_full(lv[j - 1], lv[j], s);
+            MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
+            launch_live_all(dlv<R>(h), a.nodes, a.edges, s);
+            if (j1 > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
+            launch_patches_all(dlv<R>(h), a.patches, s);
+            launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);
+            read_counts<R>(h);
             check_launch();
-        }
+            return 0;
+        });
         ck(cudaStreamSynchronize(s), "set_state");
         update_top(h);
         h->has_state = true;
@@ -612,12 +848,14 @@ int sww_adapt(sww_handle* h, double eps_h, double eps_u) {
     if (!h) return fail(SWW_E_ARG, "null handle");
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     return guarded([&]() -> int {
-        {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
             Join jn(h);
-            adapt(h, eps_h, eps_u);
-            read_counts(h);
+            adapt<R>(h, eps_h, eps_u);
+            read_counts<R>(h);
             check_launch();
-        }
+            return 0;
+        });
         ck(cudaStreamSynchronize(h->stream), "adapt");
         update_top(h);
         return SWW_OK;
@@ -630,24 +868,27 @@ int sww_mask_from_coeffs(sww_handle* h, const double* hdet, const double* udet_e
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     if (!(eps_h > 0) || !(eps_u > 0)) return fail(SWW_E_ARG, "explicit positive thresholds required");
     return guarded([&]() -> int {
-        {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
             Join jn(h);
+            auto& lv = lvl<R>(h);
             size_t oh = 0, oe = 0, oi = 0;
             for (int j = h->cfg.jmin + 1; j <= h->cfg.jmax; ++j) {
-                DevLevel& F = h->lv[j];
-                int64_t ce = h->lv[j - 1].E;
-                ck(cudaMemcpyAsync(F.hdet, hdet + oh, F.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "hdet");
-                ck(cudaMemcpyAsync(F.ue, udet_e + oe, ce * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ue");
-                ck(cudaMemcpyAsync(F.ui, udet_i + oi, F.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "ui");
+                DevLevelT<R>& F = lv[j];
+                int64_t ce = lv[j - 1].E;
+                to_device(h, F.hdet, hdet + oh, F.N);
+                to_device(h, F.ue, udet_e + oe, ce);
+                to_device(h, F.ui, udet_i + oi, F.E);
                 oh += F.N, oe += ce, oi += F.E;
             }
             double th[2] = {eps_h, eps_u};
             ck(cudaMemcpyAsync(h->thr, th, sizeof(th), cudaMemcpyHostToDevice, h->stream), "thr");
             ck(cudaStreamSynchronize(h->stream), "thr");   // th lives on this host stack frame
-            mask_and_inverse(h);
-            read_counts(h);
+            mask_and_inverse<R>(h);
+            read_counts<R>(h);
             check_launch();
-        }
+            return 0;
+        });
         ck(cudaStreamSynchronize(h->stream), "mask");
         update_top(h);
         return SWW_OK;
@@ -658,13 +899,15 @@ int sww_rhs(sww_handle* h) {
     if (!h) return fail(SWW_E_ARG, "null handle");
     if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
     return guarded([&]() -> int {
-        {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
             Join jn(h);
-            trend(h);
+            trend<R>(h);
             RKStage none{0, 0, 0, 0, 0, 0, 0};
-            update(h, none);
+            update<R>(h, none);
             check_launch();
-        }
+            return 0;
+        });
         ck(cudaStreamSynchronize(h->stream), "rhs");
         return SWW_OK;
     });
@@ -693,37 +936,92 @@ int sww_step(sww_handle* h, double dt, int nsteps, int do_adapt) {
     });
 }
 
+int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int do_adapt) {
+    if (!hs || n < 0 || nsteps < 0) return fail(SWW_E_ARG, "bad argument");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) return fail(SWW_E_ARG, "null handle");
+        if (!hs[i]->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return fail(SWW_E_ARG, "a handle appears twice");
+    }
+    if (n == 0 || nsteps == 0) return SWW_OK;
+    return guarded([&]() -> int {
+        // every member's step is one graph launch on the member's own stream; the
+        // members advance in turn, each waiting only for its own previous step
+        for (int i = 0; i < n; ++i) {
+            sww_handle* h = hs[i];
+            ck(cudaEventRecord(h->ev_in, h->user), "join in");
+            ck(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "join in");
+        }
+        auto launch = [&](sww_handle* h) {
+            run_step(h, dt, do_adapt != 0);
+            check_launch();
+        };
+        auto finish = [&](sww_handle* h) -> int {
+            ck(cudaStreamSynchronize(h->stream), "step");
+            double d = *h->h_dt;
+            if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
+            h->t += d;
+            h->last_dt = d;
+            h->steps += 1;
+            update_top(h);
+            return SWW_OK;
+        };
+        int rc = SWW_OK;
+        for (int i = 0; i < n; ++i) launch(hs[i]);
+        for (int s = 1; s < nsteps && rc == SWW_OK; ++s)
+            for (int i = 0; i < n && rc == SWW_OK; ++i) {
+                rc = finish(hs[i]);
+                if (rc == SWW_OK) launch(hs[i]);
+            }
+        for (int i = 0; i < n; ++i) {
+            int r = finish(hs[i]);
+            if (rc == SWW_OK) rc = r;
+            sww_handle* h = hs[i];
+            ck(cudaEventRecord(h->ev_out, h->stream), "join out");
+            ck(cudaStreamWaitEvent(h->user, h->ev_out, 0), "join out");
+        }
+        return rc;
+    });
+}
+
 int sww_get_level(const sww_handle* h, int level, int what, void* out) {
     int rc = check_level(h, level);
     if (rc) return rc;
     if (!out) return fail(SWW_E_ARG, "null output");
-    const DevLevel& L = h->lv[level];
-    const void* src = nullptr;
-    size_t bytes = 0;
-    switch (what) {
-        case SWW_DH: src = L.dh, bytes = L.N * sizeof(double); break;
-        case SWW_U: src = L.u, bytes = L.E * sizeof(double); break;
-        case SWW_DH_T: src = L.dht, bytes = L.N * sizeof(double); break;
-        case SWW_U_T: src = L.ut, bytes = L.E * sizeof(double); break;
-        case SWW_NODE_FLAGS: src = L.nflag, bytes = L.N; break;
-        case SWW_EDGE_FLAGS: src = L.eflag, bytes = L.E; break;
-        case SWW_HDET: src = L.hdet, bytes = L.N * sizeof(double); break;
-        case SWW_UDET_E:
-            if (level == h->cfg.jmin) return fail(SWW_E_ARG, "no coefficients on Jmin");
-            src = L.ue, bytes = h->lv[level - 1].E * sizeof(double);
-            break;
-        case SWW_UDET_I: src = L.ui, bytes = L.E * sizeof(double); break;
-        case SWW_SIG: src = L.sig, bytes = L.N; break;
-        default: return fail(SWW_E_ARG, "unknown quantity");
-    }
+    if (what == SWW_UDET_E && level == h->cfg.jmin) return fail(SWW_E_ARG, "no coefficients on Jmin");
+    if (what < SWW_DH || what > SWW_SIG) return fail(SWW_E_ARG, "unknown quantity");
     sww_handle* hh = const_cast<sww_handle*>(h);
     return guarded([&]() -> int {
-        {
-            Join jn(hh);
-            ck(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, hh->stream), "get_level");
-        }
-        ck(cudaStreamSynchronize(hh->stream), "get_level");
-        return SWW_OK;
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            const DevLevelT<R>& L = lvl<R>(h)[level];
+            const R* field = nullptr;
+            int64_t n = 0;
+            const uint8_t* bytes = nullptr;
+            switch (what) {
+                case SWW_DH: field = L.dh, n = L.N; break;
+                case SWW_U: field = L.u, n = L.E; break;
+                case SWW_DH_T: field = L.dht, n = L.N; break;
+                case SWW_U_T: field = L.ut, n = L.E; break;
+                case SWW_HDET: field = L.hdet, n = L.N; break;
+                case SWW_UDET_E: field = L.ue, n = meta(h, level - 1).E; break;
+                case SWW_UDET_I: field = L.ui, n = L.E; break;
+                case SWW_NODE_FLAGS: bytes = L.nflag, n = L.N; break;
+                case SWW_EDGE_FLAGS: bytes = L.eflag, n = L.E; break;
+                case SWW_SIG: bytes = L.sig, n = L.N; break;
+            }
+            if (bytes) {
+                {
+                    Join jn(hh);
+                    ck(cudaMemcpyAsync(out, bytes, n, cudaMemcpyDeviceToHost, hh->stream), "get_level");
+                }
+                ck(cudaStreamSynchronize(hh->stream), "get_level");
+            } else {
+                from_device(hh, static_cast<double*>(out), field, n);
+            }
+            return SWW_OK;
+        });
     });
 }
 
@@ -731,14 +1029,17 @@ int sww_set_level(sww_handle* h, int level, const double* dh, const double* u) {
     int rc = check_level(h, level);
     if (rc) return rc;
     return guarded([&]() -> int {
-        const DevLevel& L = h->lv[level];
-        {
-            Join jn(h);
-            if (dh) ck(cudaMemcpyAsync(L.dh, dh, L.N * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set dh");
-            if (u) ck(cudaMemcpyAsync(L.u, u, L.E * sizeof(double), cudaMemcpyHostToDevice, h->stream), "set u");
-        }
-        ck(cudaStreamSynchronize(h->stream), "set_level");
-        return SWW_OK;
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            const DevLevelT<R>& L = lvl<R>(h)[level];
+            {
+                Join jn(h);
+                if (dh) to_device(h, L.dh, dh, L.N);
+                if (u) to_device(h, L.u, u, L.E);
+            }
+            ck(cudaStreamSynchronize(h->stream), "set_level");
+            return SWW_OK;
+        });
     });
 }
 
@@ -748,13 +1049,20 @@ int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count
     if (!count) return fail(SWW_E_ARG, "null count");
     sww_handle* hh = const_cast<sww_handle*>(h);
     return guarded([&]() -> int {
-        const DevLevel& L = h->lv[level];
+        const int32_t* patches = nullptr;
+        const int32_t* npatches = nullptr;
+        by_prec(h, [&](auto r) {
+            const auto& L = lvl<decltype(r)>(h)[level];
+            patches = L.patches, npatches = L.npatches;
+            return 0;
+        });
+        const DevLevel& L = meta(h, level);
         int32_t n = 0;
         std::vector<int32_t> tmp(L.npatch + 1);
         {
             Join jn(hh);
-            ck(cudaMemcpyAsync(&n, L.npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream), "npatches");
-            ck(cudaMemcpyAsync(tmp.data(), L.patches, tmp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream),
+            ck(cudaMemcpyAsync(&n, npatches, sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream), "npatches");
+            ck(cudaMemcpyAsync(tmp.data(), patches, tmp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, hh->stream),
                "patches");
         }
         ck(cudaStreamSynchronize(hh->stream), "patches");
@@ -779,7 +1087,10 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
             {
                 Join jn(h);
                 ck(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), h->stream), "memset cnt");
-                launch_count(h->lv[j], h->cnt, h->stream);
+                by_prec(h, [&](auto r) {
+                    launch_count(lvl<decltype(r)>(h)[j], h->cnt, h->stream);
+                    return 0;
+                });
                 ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
             }
             ck(cudaStreamSynchronize(h->stream), "stats");
@@ -794,8 +1105,10 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
         double s[2], th[2];
         {
             Join jn(h);
-            const DevLevel& L0 = h->lv[h->cfg.jmin];
-            launch_sums(L0, h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
+            by_prec(h, [&](auto r) {
+                launch_sums(lvl<decltype(r)>(h)[h->cfg.jmin], h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
+                return 0;
+            });
             ck(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "sums");
             ck(cudaMemcpyAsync(th, h->thr, sizeof(th), cudaMemcpyDeviceToHost, h->stream), "thr");
             check_launch();
@@ -855,7 +1168,7 @@ namespace sww {
 
 bool handle_view(const sww_handle* h, HandleView* v) {
     if (!h || !v) return false;
-    v->jmin_level = &h->lv[h->cfg.jmin];
+    v->jmin_level = &h->geo->lv[h->cfg.jmin];   // FP64 geometry of Jmin
     v->stream = h->user;
     v->radius = h->cfg.radius;
     v->g = h->cfg.g;

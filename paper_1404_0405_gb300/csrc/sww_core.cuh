@@ -13,9 +13,12 @@ constexpr uint8_t AVAIL = LIVE | GHOST;
 constexpr int LVL_SHIFT = 27;
 constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
 
-// One level on the device.  All arrays are dense over the level (see grid.h for
-// the element layout); slot-major tables store slot s of item i at s*count + i.
-struct DevLevel {
+// One level on the device, with fields and stencil weights in the working
+// precision R (double, or float for the FP32 form, whose weights are the FP64
+// tables rounded once).  All arrays are dense over the level (see grid.h for the
+// element layout); slot-major tables store slot s of item i at s*count + i.
+template <class R>
+struct DevLevelT {
     int J;
     int64_t n, p, np, nelem, N, E, T, npatch;
     double dx;                     // Table 1 spacing of the level (m)
@@ -26,31 +29,35 @@ struct DevLevel {
     const int32_t *ring_e;         // [6*N] (2e + edge points into the node), -1 padded
     const int32_t* f2c;            // [N] coarse node at the same place (-1: odd node)
     // geometry
-    const double *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
+    const R *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
     const int32_t* cor_i;          // [10*E]
-    const double* cor_w;           // [10*E]
+    const R* cor_w;                // [10*E]
+    // FP64 geometry of the global mass and energy sums
+    const double *A_i64, *d_e64, *l_e64;
     // fine side of the pair (J-1, J)
     const int32_t* par;            // [4*N] prediction parents of odd nodes (fine ids)
-    const double* ptw;             // [4*N] s~_km
+    const R* ptw;                  // [4*N] s~_km
     const int8_t* fe_kind;         // [E] 0/1 half of a coarse edge, 2 interior
     const int32_t* fe_ce;          // [E] coarse edge of a half
     const int32_t* vst;            // [12*E] coarse stencil
-    const double* vw;              // [12*E]
+    const R* vw;                   // [12*E]
     // coarse side of the pair (J, J+1)
     const int32_t *c2f, *mid, *half;  // [N], [E], [2*E]
     const int32_t* mk_i;           // [12*N]
-    const double* mk_w;            // [12*N]
+    const R* mk_w;                 // [12*N]
     const int32_t *rf_fi, *rf_ci;  // [12*E], [11*E]
-    const double *rf_fw, *rf_cw;
+    const R *rf_fw, *rf_cw;
     // state and work arrays
-    double *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
-    double *F, *q, *B, *c, *Q;
+    R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
+    R *F, *q, *B, *c, *Q;
     uint8_t *nflag, *eflag, *sig, *tmask, *band0, *band1;
-    double *hdet, *ue, *ui;        // [N], [E of level J-1], [E]
+    R *hdet, *ue, *ui;             // [N], [E of level J-1], [E]
     uint8_t* pflag;                // [npatch]
     int32_t* patches;              // [npatch + 1] active patch list (+ pole entry), level-tagged
     int32_t* npatches;             // [1]
 };
+
+using DevLevel = DevLevelT<double>;
 
 inline unsigned blocks_for(int64_t n, int t) { return unsigned((n + t - 1) / t); }
 

@@ -1,4 +1,7 @@
-// CUDA kernels of the adaptive wavelet TRiSK step (sm_103a, FP64).
+// CUDA kernels of the adaptive wavelet TRiSK step (sm_103a).  Every kernel that
+// touches fields is a template on the working precision R: double (the FP64 form)
+// or float (the FP32 form: fields, stencils and transforms in FP32; thresholds,
+// time step and the mass/energy sums from FP64 arithmetic on the promoted values).
 //
 // FP64 work runs over active-patch work lists: a fixed grid (a multiple of the SM
 // count) strides over the entries of a list, one thread per element of a p x p
@@ -7,6 +10,7 @@
 // levels at once (kernels without a level dependency cover every level in one
 // launch).  Byte-wide mask work of the adaptation runs densely over a level.
 // Readings of silent or garbled passages are those stated in grid.cpp.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -24,22 +28,26 @@ namespace {
 constexpr int TPB = 256;
 
 __device__ __forceinline__ int64_t gid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
-__device__ __forceinline__ double esign(int32_t code) { return (code & 1) ? -1.0 : 1.0; }
+template <class R>
+__device__ __forceinline__ R esign(int32_t code) { return (code & 1) ? R(-1) : R(1); }
 
-__device__ __forceinline__ int32_t ring_nbr(const DevLevel& L, int32_t code) {
+template <class Lv>
+__device__ __forceinline__ int32_t ring_nbr(const Lv& L, int32_t code) {
     int64_t e = code >> 1;
     return (code & 1) ? L.en[e] : L.en[L.E + e];
 }
 
-__device__ __forceinline__ double predict(const DevLevel& F, const double* __restrict__ uc, int64_t fe) {
-    double s = 0.0;
+template <class R>
+__device__ __forceinline__ R predict(const DevLevelT<R>& F, const R* __restrict__ uc, int64_t fe) {
+    R s = R(0);
 #pragma unroll
     for (int k = 0; k < 12; ++k) s += F.vw[k * F.E + fe] * uc[F.vst[k * F.E + fe]];
     return s;
 }
 
-__device__ __forceinline__ double height_detail(const DevLevel& F, int64_t x) {
-    double s = F.dh[x];
+template <class R>
+__device__ __forceinline__ R height_detail(const DevLevelT<R>& F, int64_t x) {
+    R s = F.dh[x];
 #pragma unroll
     for (int k = 0; k < 4; ++k) s -= F.ptw[k * F.N + x] * F.dh[F.par[k * F.N + x]];
     return s;
@@ -64,8 +72,8 @@ __host__ __device__ constexpr int slots_of() {
 // orientation), as KINDS selects.  A pole entry yields the two pole nodes with
 // elem = -1.  Entries name their level in `lvs` (multi-level lists) or all belong
 // to `one` when lvs is null.
-template <int KINDS, class Body>
-__device__ __forceinline__ void for_items(const DevLevel* __restrict__ lvs, const DevLevel& one,
+template <int KINDS, class Lv, class Body>
+__device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& one,
                                           const int32_t* __restrict__ list, const int32_t* __restrict__ count, int P,
                                           Body body) {
     constexpr int NS = slots_of<KINDS>();
@@ -77,7 +85,7 @@ __device__ __forceinline__ void for_items(const DevLevel* __restrict__ lvs, cons
         int64_t local = it % S;
         int slot = int(local / P);
         int64_t idx = local % P;
-        const DevLevel& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
+        const Lv& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
         int64_t pat = ent & PATCH_MASK;
         if (pat == L.npatch) {
             if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
@@ -114,68 +122,73 @@ __device__ __forceinline__ void for_items(const DevLevel* __restrict__ lvs, cons
 // ---------------------------------------------------------------------------- trend bodies (Sec. 3.1)
 
 // potential vorticity q = (curl u + f)/h at a triangle (dual cell)
-__device__ __forceinline__ void pv_at(const DevLevel& L, int64_t t, double H) {
+template <class R>
+__device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
     int32_t n0 = L.tn[t], n1 = L.tn[L.T + t], n2 = L.tn[2 * L.T + t];
     int32_t c0 = L.te[t], c1 = L.te[L.T + t], c2 = L.te[2 * L.T + t];
     if (!(L.nflag[n0] & AVAIL) || !(L.nflag[n1] & AVAIL) || !(L.nflag[n2] & AVAIL)) return;
     if (!(L.eflag[c0 >> 1] & AVAIL) || !(L.eflag[c1 >> 1] & AVAIL) || !(L.eflag[c2 >> 1] & AVAIL)) return;
-    double circ = esign(c0) * L.u[c0 >> 1] * L.d_e[c0 >> 1] + esign(c1) * L.u[c1 >> 1] * L.d_e[c1 >> 1] +
-                  esign(c2) * L.u[c2 >> 1] * L.d_e[c2 >> 1];
-    double hv = L.kite[t] * (H + L.dh[n0]) + L.kite[L.T + t] * (H + L.dh[n1]) + L.kite[2 * L.T + t] * (H + L.dh[n2]);
-    double Av = L.A_v[t];
+    R circ = esign<R>(c0) * L.u[c0 >> 1] * L.d_e[c0 >> 1] + esign<R>(c1) * L.u[c1 >> 1] * L.d_e[c1 >> 1] +
+             esign<R>(c2) * L.u[c2 >> 1] * L.d_e[c2 >> 1];
+    R hv = L.kite[t] * (H + L.dh[n0]) + L.kite[L.T + t] * (H + L.dh[n1]) + L.kite[2 * L.T + t] * (H + L.dh[n2]);
+    R Av = L.A_v[t];
     L.q[t] = (circ / Av + L.f_v[t]) / (hv / Av);
 }
 
 // thickness flux F = h_e u at an edge
-__device__ __forceinline__ void flux_at(const DevLevel& L, int64_t e, double H) {
+template <class R>
+__device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
     if (!(L.eflag[e] & AVAIL)) return;
     int32_t a = L.en[e], b = L.en[L.E + e];
     if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
-    L.F[e] = 0.5 * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
+    L.F[e] = R(0.5) * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
 }
 
 // divergence, kinetic energy and Bernoulli function at a node
-__device__ __forceinline__ void node_at(const DevLevel& L, int64_t v, double g) {
+template <class R>
+__device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
-    double div = 0.0, ke = 0.0;
+    R div = R(0), ke = R(0);
     for (int k = 0; k < dg; ++k) {
         int32_t code = L.ring_e[k * L.N + v];
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
-        div += esign(code) * L.F[e] * L.l_e[e];
-        double ue = L.u[e];
-        ke += 0.25 * L.l_e[e] * L.d_e[e] * ue * ue;
+        div += esign<R>(code) * L.F[e] * L.l_e[e];
+        R ue = L.u[e];
+        ke += R(0.25) * L.l_e[e] * L.d_e[e] * ue * ue;
     }
-    double A = L.A_i[v];
+    R A = L.A_i[v];
     L.c[v] = div / A;
     L.B[v] = g * L.dh[v] + ke / A;
 }
 
 // energy-conserving Coriolis tendency +q F.n_left at a live edge (TRiSK)
-__device__ __forceinline__ void coriolis_at(const DevLevel& L, int64_t e) {
+template <class R>
+__device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
     if (!(L.eflag[e] & LIVE)) return;
-    double qe = 0.5 * (L.q[L.et[e]] + L.q[L.et[L.E + e]]);
-    double s = 0.0;
+    R qe = R(0.5) * (L.q[L.et[e]] + L.q[L.et[L.E + e]]);
+    R s = R(0);
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
         int32_t e2 = L.cor_i[k * L.E + e];
-        double w = L.cor_w[k * L.E + e];
-        double q2 = 0.5 * (L.q[L.et[e2]] + L.q[L.et[L.E + e2]]);
-        s += w * L.F[e2] * 0.5 * (qe + q2);
+        R w = L.cor_w[k * L.E + e];
+        R q2 = R(0.5) * (L.q[L.et[e2]] + L.q[L.et[L.E + e2]]);
+        s += w * L.F[e2] * R(0.5) * (qe + q2);
     }
     L.Q[e] = s;
 }
 
-__device__ __forceinline__ void div_at(const DevLevel& L, int64_t v) {
+template <class R>
+__device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
-    double div = 0.0;
+    R div = R(0);
     for (int k = 0; k < dg; ++k) {
         int32_t code = L.ring_e[k * L.N + v];
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
-        div += esign(code) * L.F[e] * L.l_e[e];
+        div += esign<R>(code) * L.F[e] * L.l_e[e];
     }
     L.c[v] = div / L.A_i[v];
 }
@@ -183,26 +196,28 @@ __device__ __forceinline__ void div_at(const DevLevel& L, int64_t v) {
 // trend and one Runge-Kutta stage at a live point (terms with a zero coefficient
 // are skipped, so stale storage never enters):
 //   y <- a*y0 + b*y + (cdt*dt)*k + (ddt*dt)*acc,   acc <- al*acc + be*k
-__device__ __forceinline__ void rk_apply(const RKStage& st, double dt, double k, double* y, const double* y0,
-                                         double* acc) {
-    double v = st.cdt * dt * k;
-    if (st.a != 0.0) v += st.a * *y0;
-    if (st.b != 0.0) v += st.b * *y;
-    if (st.ddt != 0.0) v += st.ddt * dt * *acc;
-    if (st.al != 0.0 || st.be != 0.0) *acc = (st.al != 0.0 ? st.al * *acc : 0.0) + st.be * k;
+template <class R>
+__device__ __forceinline__ void rk_apply(const RKStage& st, R dt, R k, R* y, const R* y0, R* acc) {
+    R v = R(st.cdt) * dt * k;
+    if (st.a != 0.0) v += R(st.a) * *y0;
+    if (st.b != 0.0) v += R(st.b) * *y;
+    if (st.ddt != 0.0) v += R(st.ddt) * dt * *acc;
+    if (st.al != 0.0 || st.be != 0.0) *acc = (st.al != 0.0 ? R(st.al) * *acc : R(0)) + R(st.be) * k;
     *y = v;
 }
 
-__device__ __forceinline__ void update_node(const DevLevel& L, int64_t v, const RKStage& st, double dt) {
+template <class R>
+__device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, const RKStage& st, R dt) {
     if (!(L.nflag[v] & LIVE)) return;
-    double k = -L.c[v];
+    R k = -L.c[v];
     L.dht[v] = k;
     if (st.apply) rk_apply(st, dt, k, &L.dh[v], &L.dh0[v], &L.dha[v]);
 }
 
-__device__ __forceinline__ void update_edge(const DevLevel& L, int64_t e, const RKStage& st, double dt) {
+template <class R>
+__device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, const RKStage& st, R dt) {
     if (!(L.eflag[e] & LIVE)) return;
-    double k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
+    R k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
     L.ut[e] = k;
     if (st.apply) rk_apply(st, dt, k, &L.u[e], &L.u0[e], &L.ua[e]);
 }
@@ -210,51 +225,54 @@ __device__ __forceinline__ void update_edge(const DevLevel& L, int64_t e, const 
 // ---------------------------------------------------------------------------- prolongation (Eqs. 1-2)
 
 // ghost node of level F from level C (inverse transform with zero coefficients)
-__device__ __forceinline__ void fill_node(const DevLevel& F, const DevLevel& C, int64_t i) {
+template <class R>
+__device__ __forceinline__ void fill_node(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i) {
     if (!(F.nflag[i] & GHOST)) return;
     int32_t k = F.f2c[i];
     if (k >= 0) {
         F.dh[i] = C.dh[k];
         return;
     }
-    double s = 0.0;
+    R s = R(0);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int32_t p = F.par[q * F.N + i];
-        double v = (F.nflag[p] & LIVE) ? F.dh[p] : C.dh[F.f2c[p]];
+        R v = (F.nflag[p] & LIVE) ? F.dh[p] : C.dh[F.f2c[p]];
         s += F.ptw[q * F.N + i] * v;
     }
     F.dh[i] = s;
 }
 
-__device__ __forceinline__ void fill_edge(const DevLevel& F, const DevLevel& C, int64_t i) {
+template <class R>
+__device__ __forceinline__ void fill_edge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i) {
     if (!(F.eflag[i] & GHOST)) return;
     int kind = F.fe_kind[i];
-    double P = predict(F, C.u, i);
+    R P = predict(F, C.u, i);
     if (kind == 2) {
         F.u[i] = P;
         return;
     }
     int64_t E = F.fe_ce[i];
     int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
-    double uc = C.u[E];
+    R uc = C.u[E];
     if (F.eflag[other] & LIVE) {
-        F.u[i] = 2.0 * uc - F.u[other];
+        F.u[i] = R(2) * uc - F.u[other];
     } else {
-        double Po = predict(F, C.u, other);
-        F.u[i] = P + 0.5 * (2.0 * uc - P - Po);
+        R Po = predict(F, C.u, other);
+        F.u[i] = P + R(0.5) * (R(2) * uc - P - Po);
     }
 }
 
 // ---------------------------------------------------------------------------- list kernels
 
 #define ITEMS(KINDS, lvs, one, list, count, P) \
-    for_items<KINDS>(lvs, one, list, count, P, [&] __device__(const DevLevel& L, int kind, int64_t id, int64_t el)
+    for_items<KINDS>(lvs, one, list, count, P, [&](const auto& L, int kind, int64_t id, int64_t el)
 
 // pass 1 of a trend: potential vorticity at triangles and thickness flux at edges
 // (both read only the state)
-__global__ void k_pv_flux(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, double H) {
-    DevLevel none{};
+template <class R>
+__global__ void k_pv_flux(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, R H) {
+    DevLevelT<R> none{};
     ITEMS(K_EDGE | K_TRI, lvs, none, list, count, P) {
         if (kind == K_EDGE)
             flux_at(L, id, H);
@@ -265,9 +283,10 @@ __global__ void k_pv_flux(const DevLevel* __restrict__ lvs, const int32_t* list,
 
 // pass 2: divergence, kinetic energy and Bernoulli function at nodes, Coriolis
 // tendency at edges (both read pass-1 results of neighbours)
-__global__ void k_node_coriolis(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
-                                double g) {
-    DevLevel none{};
+template <class R>
+__global__ void k_node_coriolis(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
+                                R g) {
+    DevLevelT<R> none{};
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
         if (kind == K_NODE)
             node_at(L, id, g);
@@ -276,10 +295,11 @@ __global__ void k_node_coriolis(const DevLevel* __restrict__ lvs, const int32_t*
     });
 }
 
-__global__ void k_update(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, RKStage st,
-                         const double* __restrict__ dtp) {
-    DevLevel none{};
-    double dt = dtp ? *dtp : 0.0;
+template <class R>
+__global__ void k_update(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
+                         RKStage st, const double* __restrict__ dtp) {
+    DevLevelT<R> none{};
+    R dt = R(dtp ? *dtp : 0.0);
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
         if (kind == K_NODE)
             update_node(L, id, st, dt);
@@ -288,8 +308,9 @@ __global__ void k_update(const DevLevel* __restrict__ lvs, const int32_t* list, 
     });
 }
 
-__global__ void k_save_base(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P) {
-    DevLevel none{};
+template <class R>
+__global__ void k_save_base(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P) {
+    DevLevelT<R> none{};
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
         if (kind == K_NODE) {
             if (L.nflag[id] & LIVE) L.dh0[id] = L.dh[id];
@@ -300,8 +321,9 @@ __global__ void k_save_base(const DevLevel* __restrict__ lvs, const int32_t* lis
 }
 
 // ghosts of level F from level C over F's work list
-__global__ void k_fill(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE | K_EDGE, nullptr, F, list, count, P) {
+template <class R>
+__global__ void k_fill(DevLevelT<R> F, DevLevelT<R> C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, F, list, count, P) {
         if (kind == K_NODE)
             fill_node(L, C, id);
         else
@@ -312,8 +334,9 @@ __global__ void k_fill(DevLevel F, DevLevel C, const int32_t* list, const int32_
 // restriction from F = level j+1 to C = level j (Sec. 3.1): B by injection at covered
 // nodes, flux by R_F on faces of covered nodes, Coriolis tendency by R_u where both
 // ends are covered
-__global__ void k_restrict(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE | K_EDGE, nullptr, C, list, count, P) {
+template <class R>
+__global__ void k_restrict(DevLevelT<R> C, DevLevelT<R> F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, C, list, count, P) {
         if (kind == K_NODE) {
             if (L.nflag[id] & COVERED) L.B[id] = F.B[L.c2f[id]];
             return;
@@ -321,26 +344,28 @@ __global__ void k_restrict(DevLevel C, DevLevel F, const int32_t* list, const in
         int64_t i = id;
         bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
         if (ca || cb) {
-            double s = 0.0;
+            R s = R(0);
 #pragma unroll
             for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
 #pragma unroll
             for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
             L.F[i] = s / L.l_e[i];
         }
-        if (ca && cb) L.Q[i] = 0.5 * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
+        if (ca && cb) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
     });
 }
 
-__global__ void k_div(DevLevel C, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE, nullptr, C, list, count, P) { div_at(L, id); });
+template <class R>
+__global__ void k_div(DevLevelT<R> C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, list, count, P) { div_at(L, id); });
 }
 
 // R_h at covered nodes of C from level F (Eq. Rh; coefficients of non-live points are zero)
-__global__ void k_partial(DevLevel C, DevLevel F, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE, nullptr, C, list, count, P) {
+template <class R>
+__global__ void k_partial(DevLevelT<R> C, DevLevelT<R> F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, list, count, P) {
         if (!(L.nflag[id] & COVERED)) return;
-        double s = F.dh[L.c2f[id]];
+        R s = F.dh[L.c2f[id]];
         for (int q = 0; q < 12; ++q) {
             int32_t m = L.mk_i[q * L.N + id];
             if (m < 0 || !(F.nflag[m] & LIVE)) continue;
@@ -353,11 +378,13 @@ __global__ void k_partial(DevLevel C, DevLevel F, const int32_t* list, const int
 // wavelet coefficients at live points (Eqs. 1-2; velocity transform of Sec. 4.1):
 // h~ at odd nodes, u~ at interior fine edges, u~_E at the edges of the coarse element
 // under each even fine element
-__global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, int jmin) {
-    DevLevel none{};
+template <class R>
+__global__ void k_details(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
+                          int jmin) {
+    DevLevelT<R> none{};
     ITEMS(K_NODE | K_EDGE | K_CEDGE, lvs, none, list, count, P) {
         if (L.J == jmin) return;
-        const DevLevel& C = lvs[L.J - 1];
+        const DevLevelT<R>& C = lvs[L.J - 1];
         if (kind == K_NODE) {
             if (L.f2c[id] < 0 && (L.nflag[id] & LIVE)) L.hdet[id] = height_detail(L, id);
         } else if (kind == K_EDGE) {
@@ -368,9 +395,9 @@ __global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list,
             int64_t E = id * C.nelem + ce;
             int32_t h0 = C.half[E], h1 = C.half[C.E + E];
             if ((L.eflag[h0] & LIVE) || (L.eflag[h1] & LIVE)) {
-                double a = L.u[h0] - predict(L, C.u, h0);
-                double b = L.u[h1] - predict(L, C.u, h1);
-                L.ue[E] = 0.5 * (a - b);
+                R a = L.u[h0] - predict(L, C.u, h0);
+                R b = L.u[h1] - predict(L, C.u, h1);
+                L.ue[E] = R(0.5) * (a - b);
             }
         }
     });
@@ -379,12 +406,13 @@ __global__ void k_details(const DevLevel* __restrict__ lvs, const int32_t* list,
 // inverse transform of the retained coefficients onto the live points of F:
 // (a) even nodes and all edges from level C, (b) odd nodes from the even ones.
 // Coefficients count only where the point was live before the adaptation.
-__global__ void k_inverse_a(DevLevel F, DevLevel C, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE | K_EDGE, nullptr, F, list, count, P) {
+template <class R>
+__global__ void k_inverse_a(DevLevelT<R> F, DevLevelT<R> C, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, F, list, count, P) {
         if (kind == K_NODE) {
             if (!(L.nflag[id] & LIVE) || L.f2c[id] < 0) return;
             int32_t k = L.f2c[id];
-            double s = C.dh[k];
+            R s = C.dh[k];
             for (int q = 0; q < 12; ++q) {
                 int32_t m = C.mk_i[q * C.N + k];
                 if (m >= 0 && (L.nflag[m] & LIVE) && (L.nflag[m] & WASLIVE)) s -= C.mk_w[q * C.N + k] * L.hdet[m];
@@ -395,25 +423,26 @@ __global__ void k_inverse_a(DevLevel F, DevLevel C, const int32_t* list, const i
         int64_t i = id;
         if (!(L.eflag[i] & LIVE)) return;
         int fk = L.fe_kind[i];
-        double Pr = predict(L, C.u, i);
+        R Pr = predict(L, C.u, i);
         if (fk == 2) {
-            L.u[i] = Pr + ((L.eflag[i] & WASLIVE) ? L.ui[i] : 0.0);
+            L.u[i] = Pr + ((L.eflag[i] & WASLIVE) ? L.ui[i] : R(0));
         } else {
             int64_t E = L.fe_ce[i];
             int32_t h0 = C.half[E], h1 = C.half[C.E + E];
             int32_t other = fk == 0 ? h1 : h0;
-            double Po = predict(L, C.u, other);
-            double delta = 0.5 * (2.0 * C.u[E] - Pr - Po);
-            double d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : 0.0;
+            R Po = predict(L, C.u, other);
+            R delta = R(0.5) * (R(2) * C.u[E] - Pr - Po);
+            R d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : R(0);
             L.u[i] = Pr + delta + (fk == 0 ? d : -d);
         }
     });
 }
 
-__global__ void k_inverse_b(DevLevel F, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE, nullptr, F, list, count, P) {
+template <class R>
+__global__ void k_inverse_b(DevLevelT<R> F, const int32_t* list, const int32_t* count, int P) {
+    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, F, list, count, P) {
         if (!(L.nflag[id] & LIVE) || L.f2c[id] >= 0) return;
-        double s = (L.nflag[id] & WASLIVE) ? L.hdet[id] : 0.0;
+        R s = (L.nflag[id] & WASLIVE) ? L.hdet[id] : R(0);
 #pragma unroll
         for (int q = 0; q < 4; ++q) s += L.ptw[q * L.N + id] * L.dh[L.par[q * L.N + id]];
         L.dh[id] = s;
@@ -449,16 +478,17 @@ struct AddOp {
 };
 
 // max |dh| over live nodes, max |u| over live edges (bit patterns of non-negative doubles)
-__global__ void k_maxabs(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S,
+template <class R>
+__global__ void k_maxabs(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int S,
                          unsigned long long* red) {
     __shared__ unsigned long long sh[32];
-    DevLevel none{};
+    DevLevelT<R> none{};
     unsigned long long a = 0, b = 0;
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
         if (kind == K_NODE) {
-            if (L.nflag[id] & LIVE) a = max(a, dbits(fabs(L.dh[id])));
+            if (L.nflag[id] & LIVE) a = max(a, dbits(fabs(double(L.dh[id]))));
         } else if (L.eflag[id] & LIVE) {
-            b = max(b, dbits(fabs(L.u[id])));
+            b = max(b, dbits(fabs(double(L.u[id]))));
         }
     });
     a = block_reduce(a, MaxOp(), sh, 0ull);
@@ -468,18 +498,19 @@ __global__ void k_maxabs(const DevLevel* __restrict__ lvs, const int32_t* list, 
 }
 
 // omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max), dx/|u| at live edges (min)
-__global__ void k_dt(const DevLevel* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H,
+template <class R>
+__global__ void k_dt(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H,
                      double g, unsigned long long* red) {
     __shared__ unsigned long long sh[32];
-    DevLevel none{};
+    DevLevelT<R> none{};
     unsigned long long a = 0, b = ~0ull;
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
         if (kind == K_NODE) {
             if (!(L.nflag[id] & LIVE)) return;
-            double f = L.f_n[id], kx = M_PI / L.dx;
-            a = max(a, dbits(sqrt(f * f + g * (H + L.dh[id]) * kx * kx)));
+            double f = double(L.f_n[id]), kx = M_PI / L.dx;
+            a = max(a, dbits(sqrt(f * f + g * (H + double(L.dh[id])) * kx * kx)));
         } else if (L.eflag[id] & LIVE) {
-            double au = fabs(L.u[id]);
+            double au = fabs(double(L.u[id]));
             if (au > 0) b = min(b, dbits(L.dx / au));
         }
     });
@@ -509,15 +540,17 @@ __device__ __forceinline__ void neumaier(double& s, double& c, double x) {
     s = t;
 }
 
-__global__ void k_sums(DevLevel L, double H, double g, double* part) {
+template <class R>
+__global__ void k_sums(DevLevelT<R> L, double H, double g, double* part) {
     __shared__ double sh[2][TPB];
     int64_t v = gid();
     double m = 0, en = 0;
     if (v < L.N) {
-        double h = H + L.dh[v], A = L.A_i[v], ke = 0.0;
+        double h = H + double(L.dh[v]), A = L.A_i64[v], ke = 0.0;
         for (int k = 0; k < L.deg[v]; ++k) {
             int64_t e = L.ring_e[k * L.N + v] >> 1;
-            ke += 0.25 * L.l_e[e] * L.d_e[e] * L.u[e] * L.u[e];
+            double ue = double(L.u[e]);
+            ke += 0.25 * L.l_e64[e] * L.d_e64[e] * ue * ue;
         }
         m = A * h;
         en = g * h * (0.5 * g * h * A + ke);
@@ -548,7 +581,8 @@ __global__ void k_sums_final(const double* part, int nblk, double* out) {
     out[1] = s1 + c1;
 }
 
-__global__ void k_count(DevLevel L, unsigned long long* cnt) {
+template <class R>
+__global__ void k_count(DevLevelT<R> L, unsigned long long* cnt) {
     __shared__ unsigned long long sh[32];
     int64_t i = gid();
     unsigned long long a = 0, b = 0, c = 0;
@@ -574,159 +608,175 @@ __device__ __forceinline__ bool locate(const Span& sp, int64_t t, int& j, int64_
     return false;
 }
 
+// Visit (level, index) of a multi-level dense launch.  The top level of a span may be
+// a tail level (the level above the top live level): it gets a fixed number of
+// threads that stride over it, and only when a point one level down was significant,
+// since otherwise it cannot gain a point in this adaptation.
+template <class Body>
+__device__ __forceinline__ void dense_each(const Span& sp, int64_t t, const int32_t* __restrict__ sig_any, Body body) {
+    int j;
+    int64_t i;
+    if (!locate(sp, t, j, i)) return;
+    if (j != sp.tail_j) {
+        body(j, i);
+        return;
+    }
+    if (!sig_any[j - 1]) return;
+    const int64_t stride = sp.off[j + 1 - sp.ja] - sp.off[j - sp.ja];
+    for (; i < sp.tail_n; i += stride) body(j, i);
+}
+
+#define DENSE_EACH(sp, t, any) dense_each(sp, t, any, [&] __device__(int j, int64_t i)
+
 // full restriction used at initialisation: R_h at every node, mean of halves at every edge
-__global__ void k_restrict_full(DevLevel C, DevLevel F) {
+template <class R>
+__global__ void k_restrict_full(DevLevelT<R> C, DevLevelT<R> F) {
     int64_t i = gid();
     if (i < C.N) {
-        double s = F.dh[C.c2f[i]];
+        R s = F.dh[C.c2f[i]];
         for (int q = 0; q < 12; ++q) {
             int32_t m = C.mk_i[q * C.N + i];
             if (m >= 0) s += C.mk_w[q * C.N + i] * height_detail(F, m);
         }
         C.dh[i] = s;
     }
-    if (i < C.E) C.u[i] = 0.5 * (F.u[C.half[i]] + F.u[C.half[C.E + i]]);
+    if (i < C.E) C.u[i] = R(0.5) * (F.u[C.half[i]] + F.u[C.half[C.E + i]]);
 }
 
 // significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends and the
 // midpoint of a coarse edge with |u~_E| >= eps_u; both ends of an interior edge with
-// |u~| >= eps_u; only points live before the adaptation carry coefficients
-// Multi-level mask kernels take (sig_any, skip): level `skip` (the level above the
-// top live level) can only gain points as children of significant points one level
-// down, so its threads leave at once when sig_any[skip - 1] is 0.
-__global__ void k_zero_sig(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t i;
-    if (!locate(sp, gid(), j, i)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    lvs[j].sig[i] = 0;
+// |u~| >= eps_u; only points live before the adaptation carry coefficients.
+// sig_any[j] records whether level j holds a significant point.
+template <class R>
+__global__ void k_zero_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) { lvs[j].sig[i] = 0; });
 }
 
-__global__ void k_sig(const DevLevel* __restrict__ lvs, Span sp, const double* __restrict__ thr, int32_t* sig_any,
-                      int skip) {
-    int j;
-    int64_t i;
-    if (!locate(sp, gid(), j, i)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    bool any = false;
-    const DevLevel& F = lvs[j];
-    const DevLevel& C = lvs[j - 1];
-    double eh = thr[0], eu = thr[1];
-    if (i < F.N && F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(F.hdet[i]) >= eh) F.sig[i] = 1, any = true;
-    if (i < F.E && F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(F.ui[i]) >= eu) {
-        F.sig[F.en[i]] = 1;
-        F.sig[F.en[F.E + i]] = 1;
-        any = true;
-    }
-    if (i < C.E) {
-        int32_t h0 = C.half[i], h1 = C.half[C.E + i];
-        if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(F.ue[i]) >= eu) {
-            F.sig[C.c2f[C.en[i]]] = 1;
-            F.sig[C.c2f[C.en[C.E + i]]] = 1;
-            F.sig[C.mid[i]] = 1;
+template <class R>
+__global__ void k_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const double* __restrict__ thr, int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        bool any = false;
+        const DevLevelT<R>& F = lvs[j];
+        const DevLevelT<R>& C = lvs[j - 1];
+        double eh = thr[0], eu = thr[1];
+        if (i < F.N && F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(double(F.hdet[i])) >= eh) F.sig[i] = 1, any = true;
+        if (i < F.E && F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(double(F.ui[i])) >= eu) {
+            F.sig[F.en[i]] = 1;
+            F.sig[F.en[F.E + i]] = 1;
             any = true;
         }
-    }
-    if (any) sig_any[j] = 1;
+        if (i < C.E) {
+            int32_t h0 = C.half[i], h1 = C.half[C.E + i];
+            if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(double(F.ue[i])) >= eu) {
+                F.sig[C.c2f[C.en[i]]] = 1;
+                F.sig[C.c2f[C.en[C.E + i]]] = 1;
+                F.sig[C.mid[i]] = 1;
+                any = true;
+            }
+        }
+        if (any) sig_any[j] = 1;
+    });
 }
 
 // T = S + same-level neighbours of S + children of the coarser significance set
-__global__ void k_adjacent(const DevLevel* __restrict__ lvs, Span sp, int jmin, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t x;
-    if (!locate(sp, gid(), j, x)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& F = lvs[j];
-    const DevLevel& C = lvs[j - 1];
-    bool children = j - 1 > jmin;
-    int dg = F.deg[x];
-    uint8_t t = F.sig[x];
-    for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
-    if (!t && children) {
-        int32_t cx = F.f2c[x];
-        if (cx >= 0 && C.sig[cx]) t = 1;
-        for (int k = 0; k < dg && !t; ++k) {
-            int32_t y = ring_nbr(F, F.ring_e[k * F.N + x]);
-            int32_t cy = F.f2c[y];
-            if (cy >= 0 && C.sig[cy]) t = 1;
+template <class R>
+__global__ void k_adjacent(const DevLevelT<R>* __restrict__ lvs, Span sp, int jmin, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        const int64_t x = i;
+        const DevLevelT<R>& F = lvs[j];
+        const DevLevelT<R>& C = lvs[j - 1];
+        bool children = j - 1 > jmin;
+        int dg = F.deg[x];
+        uint8_t t = F.sig[x];
+        for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
+        if (!t && children) {
+            int32_t cx = F.f2c[x];
+            if (cx >= 0 && C.sig[cx]) t = 1;
+            for (int k = 0; k < dg && !t; ++k) {
+                int32_t y = ring_nbr(F, F.ring_e[k * F.N + x]);
+                int32_t cy = F.f2c[y];
+                if (cy >= 0 && C.sig[cy]) t = 1;
+            }
         }
-    }
-    F.tmask[x] = t;
+        F.tmask[x] = t;
+    });
 }
 
 // graded closure at level F: coarse node of a live node of the finer level Fp, and the
-// prediction parents of every live odd node (only ever sets bytes to 1)
-__global__ void k_close(DevLevel F, DevLevel Fp, int has_finer, const int32_t* sig_any, int skip) {
-    int64_t x = gid();
-    if (x >= F.N) return;
-    if (F.J == skip && !sig_any[F.J - 1]) return;
-    uint8_t t = F.tmask[x];
-    if (has_finer && Fp.tmask[F.c2f[x]]) t = 1;
-    if (!t) return;
-    F.tmask[x] = 1;
-    if (F.f2c[x] < 0) {
+// prediction parents of every live odd node (only ever sets bytes to 1).  On a tail
+// level the fixed grid strides over the level.
+template <class R>
+__global__ void k_close(DevLevelT<R> F, DevLevelT<R> Fp, int has_finer, const int32_t* sig_any, int tail) {
+    if (tail && !sig_any[F.J - 1]) return;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t x = gid(); x < F.N; x += stride) {
+        uint8_t t = F.tmask[x];
+        if (has_finer && Fp.tmask[F.c2f[x]]) t = 1;
+        if (!t) continue;
+        F.tmask[x] = 1;
+        if (F.f2c[x] < 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) F.tmask[F.par[q * F.N + x]] = 1;
+            for (int q = 0; q < 4; ++q) F.tmask[F.par[q * F.N + x]] = 1;
+        }
     }
 }
 
 // live flags (all of Jmin, else the mask), remembering which points were live
-__global__ void k_live(const DevLevel* __restrict__ lvs, Span sp, int all_level, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t i;
-    if (!locate(sp, gid(), j, i)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
-    uint8_t lv = (all_level == -2 || j == all_level) ? 1 : L.tmask[i];
-    L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
-    L.band0[i] = lv;
+template <class R>
+__global__ void k_live(const DevLevelT<R>* __restrict__ lvs, Span sp, int all_level, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        const DevLevelT<R>& L = lvs[j];
+        uint8_t lv = (all_level == -2 || j == all_level) ? 1 : L.tmask[i];
+        L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
+        L.band0[i] = lv;
+    });
 }
 
 // an edge is live when an end node is
-__global__ void k_live_edges(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t e;
-    if (!locate(sp, gid(), j, e)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
-    uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
-    L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
+template <class R>
+__global__ void k_live_edges(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        const DevLevelT<R>& L = lvs[j];
+        const int64_t e = i;
+        uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
+        L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
+    });
 }
 
 // one neighbour hop of the ghost band on every level: band1 <- dilate(band0) when
 // `forward`, band0 <- dilate(band1) otherwise
-__global__ void k_dilate(const DevLevel* __restrict__ lvs, Span sp, int forward, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t x;
-    if (!locate(sp, gid(), j, x)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
-    const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
-    uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
-    uint8_t t = in[x];
-    int dg = L.deg[x];
-    for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
-    out[x] = t;
+template <class R>
+__global__ void k_dilate(const DevLevelT<R>* __restrict__ lvs, Span sp, int forward, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        const DevLevelT<R>& L = lvs[j];
+        const int64_t x = i;
+        const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
+        uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
+        uint8_t t = in[x];
+        int dg = L.deg[x];
+        for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
+        out[x] = t;
+    });
 }
 
-__global__ void k_ghost(const DevLevel* __restrict__ lvs, Span sp, int in_band1, const int32_t* sig_any, int skip) {
-    int j;
-    int64_t i;
-    if (!locate(sp, gid(), j, i)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
-    const uint8_t* __restrict__ band = in_band1 ? L.band1 : L.band0;
-    if (i < L.N && !(L.nflag[i] & LIVE) && band[i]) L.nflag[i] |= GHOST;
-    if (i < L.E && !(L.eflag[i] & LIVE) && band[L.en[i]] && band[L.en[L.E + i]]) L.eflag[i] |= GHOST;
+template <class R>
+__global__ void k_ghost(const DevLevelT<R>* __restrict__ lvs, Span sp, int in_band1, const int32_t* sig_any) {
+    DENSE_EACH(sp, gid(), sig_any) {
+        const DevLevelT<R>& L = lvs[j];
+        const uint8_t* __restrict__ band = in_band1 ? L.band1 : L.band0;
+        if (i < L.N && !(L.nflag[i] & LIVE) && band[i]) L.nflag[i] |= GHOST;
+        if (i < L.E && !(L.eflag[i] & LIVE) && band[L.en[i]] && band[L.en[L.E + i]]) L.eflag[i] |= GHOST;
+    });
 }
 
 // covered coarse nodes: the fine node at the same place and all of M_k live
-__global__ void k_covered(const DevLevel* __restrict__ lvs, Span sp) {
+template <class R>
+__global__ void k_covered(const DevLevelT<R>* __restrict__ lvs, Span sp) {
     int j;
     int64_t k;
     if (!locate(sp, gid(), j, k)) return;
-    const DevLevel& C = lvs[j];
-    const DevLevel& F = lvs[j + 1];
+    const DevLevelT<R>& C = lvs[j];
+    const DevLevelT<R>& F = lvs[j + 1];
     if (!(F.nflag[C.c2f[k]] & LIVE)) return;
     for (int q = 0; q < 12; ++q) {
         int32_t m = C.mk_i[q * C.N + k];
@@ -736,28 +786,37 @@ __global__ void k_covered(const DevLevel* __restrict__ lvs, Span sp) {
 }
 
 // patches holding any live or ghost node or edge (one block per patch)
-__global__ void k_patch_flags(const DevLevel* __restrict__ lvs, Span sp, const int32_t* sig_any, int skip) {
+template <class R>
+__global__ void k_patch_flags(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
     int j;
     int64_t pid;
     if (!locate(sp, int64_t(blockIdx.x), j, pid)) return;
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
-    int64_t pp = L.p * L.p;
-    int any = 0;
-    for (int64_t l = threadIdx.x; l < pp; l += blockDim.x) {
-        int64_t e = pid * pp + l;
-        if ((L.nflag[e] | L.eflag[e] | L.eflag[L.nelem + e] | L.eflag[2 * L.nelem + e]) & AVAIL) any = 1;
+    int64_t stride = 0;
+    if (j == sp.tail_j) {
+        if (!sig_any[j - 1]) return;
+        stride = sp.off[j + 1 - sp.ja] - sp.off[j - sp.ja];
     }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) L.pflag[pid] = uint8_t(any);
+    const DevLevelT<R>& L = lvs[j];
+    const int64_t pp = L.p * L.p;
+    const int64_t np = (j == sp.tail_j) ? sp.tail_n : pid + 1;
+    for (; pid < np; pid += (stride ? stride : 1)) {
+        int any = 0;
+        for (int64_t l = threadIdx.x; l < pp; l += blockDim.x) {
+            int64_t e = pid * pp + l;
+            if ((L.nflag[e] | L.eflag[e] | L.eflag[L.nelem + e] | L.eflag[2 * L.nelem + e]) & AVAIL) any = 1;
+        }
+        any = __syncthreads_or(any);
+        if (threadIdx.x == 0) L.pflag[pid] = uint8_t(any);
+    }
 }
 
 // ascending level-tagged list of flagged patches, then the pole entry when a pole is
 // live or ghost (one block; deterministic)
-__global__ void k_patch_scan(const DevLevel* __restrict__ lvs, int ja, const int32_t* sig_any, int skip) {
+template <class R>
+__global__ void k_patch_scan(const DevLevelT<R>* __restrict__ lvs, int ja, const int32_t* sig_any, int tail_j) {
     int j = ja + int(blockIdx.x);
-    if (j == skip && !sig_any[j - 1]) return;
-    const DevLevel& L = lvs[j];
+    if (j == tail_j && !sig_any[j - 1]) return;
+    const DevLevelT<R>& L = lvs[j];
     __shared__ int warp_tot[32];
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
@@ -790,12 +849,13 @@ __global__ void k_patch_scan(const DevLevel* __restrict__ lvs, int ja, const int
 }
 
 // concatenation of the level lists jmin..jmax into one list
-__global__ void k_concat(const DevLevel* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count) {
+template <class R>
+__global__ void k_concat(const DevLevelT<R>* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count) {
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
     for (int j = jmin; j <= jmax; ++j) {
-        const DevLevel& L = lvs[j];
+        const DevLevelT<R>& L = lvs[j];
         int n = *L.npatches;
         for (int i = threadIdx.x; i < n; i += blockDim.x) all[base + i] = L.patches[i];
         __syncthreads();
@@ -812,36 +872,54 @@ __global__ void k_concat(const DevLevel* __restrict__ lvs, int jmin, int jmax, i
 #define DENSE(kernel, n, ...) (g_launches++, kernel<<<blocks_for((n), TPB), TPB, 0, s>>>(__VA_ARGS__))
 #define LIST(kernel, ...) (g_launches++, kernel<<<W.grid, TPB, 0, s>>>(__VA_ARGS__))
 
-static int64_t span(const DevLevel& L) { return L.E > L.N ? L.E : L.N; }
+template <class R>
+static int64_t span(const DevLevelT<R>& L) { return L.E > L.N ? L.E : L.N; }
 
-void launch_pv_flux(const Work& W, double H, cudaStream_t s) { LIST(k_pv_flux, W.lvs, W.list, W.count, W.S, H); }
-void launch_node_coriolis(const Work& W, double g, cudaStream_t s) {
-    LIST(k_node_coriolis, W.lvs, W.list, W.count, W.S, g);
+template <class R>
+void launch_pv_flux(const WorkT<R>& W, double H, cudaStream_t s) {
+    LIST(k_pv_flux<R>, W.lvs, W.list, W.count, W.S, R(H));
 }
-void launch_update(const Work& W, const RKStage& st, const double* dt, cudaStream_t s) {
-    LIST(k_update, W.lvs, W.list, W.count, W.S, st, dt);
+template <class R>
+void launch_node_coriolis(const WorkT<R>& W, double g, cudaStream_t s) {
+    LIST(k_node_coriolis<R>, W.lvs, W.list, W.count, W.S, R(g));
 }
-void launch_save_base(const Work& W, cudaStream_t s) { LIST(k_save_base, W.lvs, W.list, W.count, W.S); }
-void launch_fill(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s) {
-    LIST(k_fill, F, C, W.list, W.count, W.S);
+template <class R>
+void launch_update(const WorkT<R>& W, const RKStage& st, const double* dt, cudaStream_t s) {
+    LIST(k_update<R>, W.lvs, W.list, W.count, W.S, st, dt);
 }
-void launch_restrict(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s) {
-    LIST(k_restrict, C, F, W.list, W.count, W.S);
-    LIST(k_div, C, W.list, W.count, W.S);
+template <class R>
+void launch_save_base(const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_save_base<R>, W.lvs, W.list, W.count, W.S);
 }
-void launch_partial(const DevLevel& C, const DevLevel& F, const Work& W, cudaStream_t s) {
-    LIST(k_partial, C, F, W.list, W.count, W.S);
+template <class R>
+void launch_fill(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_fill<R>, F, C, W.list, W.count, W.S);
 }
-void launch_details(const Work& W, int jmin, cudaStream_t s) { LIST(k_details, W.lvs, W.list, W.count, W.S, jmin); }
-void launch_inverse(const DevLevel& F, const DevLevel& C, const Work& W, cudaStream_t s) {
-    LIST(k_inverse_a, F, C, W.list, W.count, W.S);
-    LIST(k_inverse_b, F, W.list, W.count, W.S);
+template <class R>
+void launch_restrict(const DevLevelT<R>& C, const DevLevelT<R>& F, const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_restrict<R>, C, F, W.list, W.count, W.S);
+    LIST(k_div<R>, C, W.list, W.count, W.S);
 }
-void launch_maxabs(const Work& W, unsigned long long* red, cudaStream_t s) {
-    LIST(k_maxabs, W.lvs, W.list, W.count, W.S, red);
+template <class R>
+void launch_partial(const DevLevelT<R>& C, const DevLevelT<R>& F, const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_partial<R>, C, F, W.list, W.count, W.S);
 }
-void launch_dt(const Work& W, double H, double g, unsigned long long* red, cudaStream_t s) {
-    LIST(k_dt, W.lvs, W.list, W.count, W.S, H, g, red);
+template <class R>
+void launch_details(const WorkT<R>& W, int jmin, cudaStream_t s) {
+    LIST(k_details<R>, W.lvs, W.list, W.count, W.S, jmin);
+}
+template <class R>
+void launch_inverse(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_inverse_a<R>, F, C, W.list, W.count, W.S);
+    LIST(k_inverse_b<R>, F, W.list, W.count, W.S);
+}
+template <class R>
+void launch_maxabs(const WorkT<R>& W, unsigned long long* red, cudaStream_t s) {
+    LIST(k_maxabs<R>, W.lvs, W.list, W.count, W.S, red);
+}
+template <class R>
+void launch_dt(const WorkT<R>& W, double H, double g, unsigned long long* red, cudaStream_t s) {
+    LIST(k_dt<R>, W.lvs, W.list, W.count, W.S, H, g, red);
 }
 void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
     g_launches++;
@@ -852,8 +930,9 @@ void launch_thresholds(const unsigned long long* red, double eps, double eh, dou
     k_thresholds<<<1, 32, 0, s>>>(red, eps, eh, eu, thr);
 }
 
-void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s) {
-    DENSE(k_restrict_full, span(C), C, F);
+template <class R>
+void launch_restrict_full(const DevLevelT<R>& C, const DevLevelT<R>& F, cudaStream_t s) {
+    DENSE(k_restrict_full<R>, span(C), C, F);
 }
 #define MULTI(kernel, sp, ...)                                                  \
     do {                                                                        \
@@ -864,58 +943,112 @@ void launch_restrict_full(const DevLevel& C, const DevLevel& F, cudaStream_t s) 
         }                                                                       \
     } while (0)
 
-void launch_mask(const MaskArgs& a, cudaStream_t s) {
+template <class R>
+void launch_mask(const MaskArgsT<R>& a, cudaStream_t s) {
     const int32_t* any = a.sig_any;
-    const int sk = a.skip;
     cudaMemsetAsync(a.sig_any, 0, sizeof(int32_t) * a.sig_any_len, s);
     // significance, adjacency in space and scale (levels ja+1..jb, independent)
-    MULTI(k_zero_sig, a.nodes_f, a.lvs, a.nodes_f, any, sk);
-    MULTI(k_sig, a.edges_f, a.lvs, a.edges_f, a.thr, a.sig_any, sk);
-    MULTI(k_adjacent, a.nodes_f, a.lvs, a.nodes_f, a.ja, any, sk);
+    MULTI(k_zero_sig<R>, a.nodes_f, a.lvs, a.nodes_f, any);
+    MULTI(k_sig<R>, a.edges_f, a.lvs, a.edges_f, a.thr, a.sig_any);
+    MULTI(k_adjacent<R>, a.nodes_f, a.lvs, a.nodes_f, a.ja, any);
     // graded closure, from the top level down
     for (int j = a.jb; j > a.ja; --j) {
-        const DevLevel& F = a.host[j];
+        const DevLevelT<R>& F = a.host[j];
         bool finer = j < a.jb;
-        DENSE(k_close, F.N, F, finer ? a.host[j + 1] : F, finer, any, sk);
+        bool tail = j == a.nodes.tail_j;
+        unsigned grid = tail ? a.tail_blocks : blocks_for(F.N, TPB);
+        g_launches++;
+        k_close<R><<<grid, TPB, 0, s>>>(F, finer ? a.host[j + 1] : F, finer, any, tail);
     }
     // live flags, ghost band, covered nodes, patch lists (levels ja..jb)
-    MULTI(k_live, a.nodes, a.lvs, a.nodes, a.ja, any, sk);
-    MULTI(k_live_edges, a.edges, a.lvs, a.edges, any, sk);
-    for (int h = 0; h < a.hops; ++h) MULTI(k_dilate, a.nodes_f, a.lvs, a.nodes_f, h % 2 == 0, any, sk);
-    MULTI(k_ghost, a.edges_f, a.lvs, a.edges_f, a.hops % 2 == 1, any, sk);
-    if (a.jb > a.ja) MULTI(k_covered, a.nodes_c, a.lvs, a.nodes_c);
+    MULTI(k_live<R>, a.nodes, a.lvs, a.nodes, a.ja, any);
+    MULTI(k_live_edges<R>, a.edges, a.lvs, a.edges, any);
+    for (int h = 0; h < a.hops; ++h) MULTI(k_dilate<R>, a.nodes_f, a.lvs, a.nodes_f, h % 2 == 0, any);
+    MULTI(k_ghost<R>, a.edges_f, a.lvs, a.edges_f, a.hops % 2 == 1, any);
+    if (a.jb > a.ja) MULTI(k_covered<R>, a.nodes_c, a.lvs, a.nodes_c);
     g_launches += 2;
-    k_patch_flags<<<unsigned(a.patches.off[a.jb + 1 - a.ja]), 64, 0, s>>>(a.lvs, a.patches, any, sk);
-    k_patch_scan<<<unsigned(a.jb - a.ja + 1), 1024, 0, s>>>(a.lvs, a.ja, any, sk);
+    k_patch_flags<R><<<unsigned(a.patches.off[a.jb + 1 - a.ja]), 64, 0, s>>>(a.lvs, a.patches, any);
+    k_patch_scan<R><<<unsigned(a.jb - a.ja + 1), 1024, 0, s>>>(a.lvs, a.ja, any, a.patches.tail_j);
 }
 
-void launch_live_all(const DevLevel* lvs, const Span& nodes, const Span& edges, cudaStream_t s) {
-    MULTI(k_live, nodes, lvs, nodes, -2, nullptr, -1);
-    MULTI(k_live_edges, edges, lvs, edges, nullptr, -1);
+template <class R>
+void launch_live_all(const DevLevelT<R>* lvs, const Span& nodes, const Span& edges, cudaStream_t s) {
+    MULTI(k_live<R>, nodes, lvs, nodes, -2, nullptr);
+    MULTI(k_live_edges<R>, edges, lvs, edges, nullptr);
 }
 
-void launch_covered_all(const DevLevel* lvs, const Span& nodes_c, cudaStream_t s) {
-    MULTI(k_covered, nodes_c, lvs, nodes_c);
+template <class R>
+void launch_covered_all(const DevLevelT<R>* lvs, const Span& nodes_c, cudaStream_t s) {
+    MULTI(k_covered<R>, nodes_c, lvs, nodes_c);
 }
 
-void launch_patches_all(const DevLevel* lvs, const Span& patches, cudaStream_t s) {
+template <class R>
+void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream_t s) {
     g_launches += 2;
-    k_patch_flags<<<unsigned(patches.off[patches.jb + 1 - patches.ja]), 64, 0, s>>>(lvs, patches, nullptr, -1);
-    k_patch_scan<<<unsigned(patches.jb - patches.ja + 1), 1024, 0, s>>>(lvs, patches.ja, nullptr, -1);
+    k_patch_flags<R><<<unsigned(patches.off[patches.jb + 1 - patches.ja]), 64, 0, s>>>(lvs, patches, nullptr);
+    k_patch_scan<R><<<unsigned(patches.jb - patches.ja + 1), 1024, 0, s>>>(lvs, patches.ja, nullptr, -1);
 }
 
-void launch_concat(const DevLevel* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
+template <class R>
+void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
     g_launches++;
-    k_concat<<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
+    k_concat<R><<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
 }
 
-int sums_blocks(const DevLevel& L) { return int(blocks_for(L.N, TPB)); }
-void launch_sums(const DevLevel& L, double H, double g, double* part, double* out, cudaStream_t s) {
+template <class R>
+int sums_blocks(const DevLevelT<R>& L) {
+    return int(blocks_for(L.N, TPB));
+}
+template <class R>
+void launch_sums(const DevLevelT<R>& L, double H, double g, double* part, double* out, cudaStream_t s) {
     int nb = sums_blocks(L);
     g_launches += 2;
-    k_sums<<<nb, TPB, 0, s>>>(L, H, g, part);
+    k_sums<R><<<nb, TPB, 0, s>>>(L, H, g, part);
     k_sums_final<<<1, 32, 0, s>>>(part, nb, out);
 }
-void launch_count(const DevLevel& L, unsigned long long* cnt, cudaStream_t s) { DENSE(k_count, span(L), L, cnt); }
+template <class R>
+void launch_count(const DevLevelT<R>& L, unsigned long long* cnt, cudaStream_t s) {
+    DENSE(k_count<R>, span(L), L, cnt);
+}
+
+// field conversion between the working precision and FP64
+template <class A, class B>
+__global__ void k_convert(const A* __restrict__ x, B* __restrict__ y, int64_t n) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t i = gid(); i < n; i += stride) y[i] = B(x[i]);
+}
+template <class A, class B>
+void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return;
+    g_launches++;
+    k_convert<A, B><<<unsigned(std::min<int64_t>(blocks_for(n, TPB), 4096)), TPB, 0, s>>>(x, y, n);
+}
+
+#define SWW_INSTANTIATE(R)                                                                                   \
+    template void launch_pv_flux<R>(const WorkT<R>&, double, cudaStream_t);                                  \
+    template void launch_node_coriolis<R>(const WorkT<R>&, double, cudaStream_t);                            \
+    template void launch_update<R>(const WorkT<R>&, const RKStage&, const double*, cudaStream_t);            \
+    template void launch_save_base<R>(const WorkT<R>&, cudaStream_t);                                        \
+    template void launch_fill<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t);   \
+    template void launch_restrict<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
+    template void launch_partial<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
+    template void launch_details<R>(const WorkT<R>&, int, cudaStream_t);                                     \
+    template void launch_inverse<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
+    template void launch_maxabs<R>(const WorkT<R>&, unsigned long long*, cudaStream_t);                      \
+    template void launch_dt<R>(const WorkT<R>&, double, double, unsigned long long*, cudaStream_t);          \
+    template void launch_restrict_full<R>(const DevLevelT<R>&, const DevLevelT<R>&, cudaStream_t);           \
+    template void launch_mask<R>(const MaskArgsT<R>&, cudaStream_t);                                         \
+    template void launch_live_all<R>(const DevLevelT<R>*, const Span&, const Span&, cudaStream_t);           \
+    template void launch_covered_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
+    template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
+    template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, cudaStream_t);         \
+    template int sums_blocks<R>(const DevLevelT<R>&);                                                        \
+    template void launch_sums<R>(const DevLevelT<R>&, double, double, double*, double*, cudaStream_t);       \
+    template void launch_count<R>(const DevLevelT<R>&, unsigned long long*, cudaStream_t);
+
+SWW_INSTANTIATE(double)
+SWW_INSTANTIATE(float)
+template void launch_convert<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, int64_t, cudaStream_t);
 
 }  // namespace sww

@@ -1,0 +1,102 @@
+"""Ensemble members (shared grid, concurrent steps) against the same members
+stepped one at a time: the library's kernels are deterministic (exact min/max
+atomics, fixed reduction trees), so a member advanced by sww_step_ensemble must
+equal, bit for bit, the same member advanced alone by sww_step on the same grid.
+
+A member with a smaller jmax than the shared grid uses that grid's hierarchical
+areas (Sec. 4.1: coarse areas are built up from the finest level), which differ
+from a grid built to the member's own jmax by rounding only."""
+import numpy as np
+import pytest
+
+import workloads
+from lib_mapping import lib_edge_geometry
+
+pytestmark = pytest.mark.gpu
+
+MEMBERS = [  # (jmax, eps, seed)
+    (4, 1e-2, 0),
+    (3, 3e-3, 1),
+    (4, 3e-3, 2),
+]
+
+
+def _fields(m, seed):
+    xyz, en = m.grid(m.jmax)
+    mid, tan = lib_edge_geometry(xyz, en)
+    return workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)
+
+
+def _snapshot(sww, m):
+    """Live and ghost values and flags of every level (values elsewhere are
+    scratch that no live result reads)."""
+    out = {}
+    for j in range(m.jmin, m.jmax + 1):
+        nf, ef = m.get(j, sww.NODE_FLAGS), m.get(j, sww.EDGE_FLAGS)
+        na, ea = (nf & 3) > 0, (ef & 3) > 0
+        out[f"nflag{j}"] = nf & 7
+        out[f"eflag{j}"] = ef & 7
+        out[f"dh{j}"] = m.get(j, sww.DH)[na]
+        out[f"u{j}"] = m.get(j, sww.U)[ea]
+    st = m.stats()
+    return out, (st["t"], st["mass"], st["energy"], st["steps"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_shared_members_match_single_runs(precision):
+    import paper_1404_0405_gb300 as sww
+    jmin, top = 2, max(j for j, _, _ in MEMBERS)
+    base = sww.Model(jmin, top, patch=4)
+    ens, alone = [], []
+    for jmax, eps, seed in MEMBERS:
+        for group in (ens, alone):
+            m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision=precision)
+            dh, u = _fields(m, seed)
+            m.set_state(dh, u)
+            m.adapt()
+            group.append(m)
+    sww.step_ensemble(ens, -1.0, 5, True)
+    for m in alone:
+        m.step(-1.0, 5, True)
+    for i, (a, b) in enumerate(zip(ens, alone)):
+        fa, sa = _snapshot(sww, a)
+        fb, sb = _snapshot(sww, b)
+        assert sa == sb, f"member {i}"
+        for k in fa:
+            x, y = fa[k], fb[k]
+            assert x.shape == y.shape, f"member {i} {k}: {x.shape} vs {y.shape}"
+            bad = np.flatnonzero(x != y)
+            assert bad.size == 0, f"member {i} {k}: {bad.size} differ, first {bad[:5]}, {x[bad[:3]]} vs {y[bad[:3]]}"
+
+
+def test_shared_grid_matches_own_grid_to_rounding():
+    """jmax=3 member on a jmax=4 grid against a jmax=3 grid of its own."""
+    import paper_1404_0405_gb300 as sww
+    base = sww.Model(2, 4, patch=4)
+    a = sww.Model(2, 3, patch=4, eps=3e-3, share=base)
+    b = sww.Model(2, 3, patch=4, eps=3e-3)
+    for m in (a, b):
+        dh, u = _fields(m, 1)
+        m.set_state(dh, u)
+        m.adapt()
+        m.step(-1.0, 3, True)
+    for j in (2, 3):
+        assert np.array_equal(a.get(j, sww.NODE_FLAGS) & 7, b.get(j, sww.NODE_FLAGS) & 7)
+        for q in (sww.DH, sww.U):
+            x, y = a.get(j, q), b.get(j, q)
+            live = (a.get(j, sww.NODE_FLAGS if q == sww.DH else sww.EDGE_FLAGS) & 1) > 0
+            assert np.abs(x[live] - y[live]).max() <= 1e-12 * np.abs(y[live]).max()
+
+
+def test_shared_grid_rules():
+    import paper_1404_0405_gb300 as sww
+    base = sww.Model(2, 3, patch=4)
+    with pytest.raises(sww.SwwError):
+        sww.Model(2, 4, patch=4, share=base)          # more levels than the shared grid
+    with pytest.raises(sww.SwwError):
+        sww.Model(2, 3, patch=2, share=base)          # another patch layout
+    m = sww.Model(2, 2, patch=4, share=base)
+    assert m.sizes(2) == base.sizes(2)
+    del base                                          # the tables outlive the first handle
+    xyz, _ = m.grid(2)
+    assert np.allclose(np.linalg.norm(xyz, axis=1), 1.0)

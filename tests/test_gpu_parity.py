@@ -31,12 +31,12 @@ def rel_err(a, b):
 class Pair:
     """An oracle model and a library model on the same grid and initial state."""
 
-    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4):
+    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64"):
         import paper_1404_0405_gb300 as sww
         self.sww = sww
         self.Hy = grid.Hierarchy(jmin, jmax)
         self.ora = model.Model(self.Hy, eps=eps, rk=rk)
-        self.lib = sww.Model(jmin, jmax, patch=patch, eps=eps, rk=rk)
+        self.lib = sww.Model(jmin, jmax, patch=patch, eps=eps, rk=rk, precision=precision)
         self.maps = {}
         for j in range(jmin, jmax + 1):
             xyz, en = self.lib.grid(j)
