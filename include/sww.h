@@ -230,6 +230,67 @@ int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
  * overlap on the GPU (other streams, other handles on the same device) race. */
 int sww_mass_energy_static(sww_handle* h, const double* dh, const double* u, double* out);
 
+/* ---------------------------------------------------------------------------
+ * Learned refinement proposal (an extension: the paper's criterion is the
+ * threshold rule of Sec. 2.3, which stays the judge).
+ *
+ * After the coefficients and thresholds of an adaptation, each patch of the
+ * levels above Jmin that hold active patches gets SWW_MLP_FEATURES features:
+ *   0 log2(1 + max|h~|/eps_h) over its live odd nodes
+ *   1 log2(1 + max|u~|/eps_u) over its live interior edges and the pair
+ *     coefficients of the coarse edges under its even nodes
+ *   2, 3  features 0, 1 of the coarse patch under it (0 on the level above Jmin)
+ *   4, 5  maxima of features 0, 1 over its neighbour patches
+ *   6 fraction of its nodes that are live
+ *   7 (level - Jmin) / (Jmax - Jmin)
+ * A two-layer perceptron (SWW_MLP_HIDDEN ReLU units; BF16 weights, FP32
+ * accumulation) maps them to the probability that the exact rules will need the
+ * patch at the next adaptation; a patch that is not active yet and scores above
+ * tau is proposed (a refinement ahead of the exact rules), and all its nodes
+ * join the set T of the mask (Sec. 2.3) before the graded closure, so the mask is
+ * the exact one plus the proposed patches.  Parameters (FP32 masters, rounded to
+ * BF16 for use): W1[F][H] row-major, b1[H], w2[H], b2. */
+enum { SWW_MLP_FEATURES = 8, SWW_MLP_HIDDEN = 32, SWW_MLP_PARAMS = 8 * 32 + 32 + 32 + 1 };
+enum { SWW_MLP_WORK = 256 * (SWW_MLP_PARAMS + 1) };   /* floats of the gradient work buffer */
+enum { SWW_P_FEATURES = 0, SWW_P_EXACT = 1, SWW_P_PROPOSAL = 2, SWW_P_ACTIVE = 3 };
+
+/* mode 0: off; 1: compute the features at every adaptation (for training data);
+ * 2: features and proposal with params (host [SWW_MLP_PARAMS]) and 0 < tau < 1.
+ * Drops the handle's captured step graphs. */
+int sww_set_learned(sww_handle* h, int mode, const float* params, float tau);
+
+/* Explicit proposal for the next adaptation only: flags[n_patches + 1] (host; the
+ * last entry is the two poles) of level j > Jmin.  A learned proposal (mode 2)
+ * replaces it on the levels the perceptron covers. */
+int sww_propose(sww_handle* h, int level, const uint8_t* flags);
+
+/* Per-patch data of level j into host memory:
+ *   SWW_P_FEATURES float[SWW_MLP_FEATURES * (n_patches + 1)], feature-major
+ *                  (feature f of patch P at f * (n_patches + 1) + P), last adaptation;
+ *   SWW_P_EXACT    uint8[n_patches + 1]: the patch holds a point of the exact
+ *                  rules' set T of the last mask;
+ *   SWW_P_PROPOSAL uint8[n_patches + 1]: proposal applied by the last mask;
+ *   SWW_P_ACTIVE   uint8[n_patches]: active patches (live or ghost point). */
+int sww_get_patch_data(const sww_handle* h, int level, int what, void* out);
+
+/* Cumulative counts since the last reset, over all levels above Jmin:
+ * out[0] misses: patches the exact set reached that were not active during the
+ * step before (late refinements); out[1] over-refined: patches the previous
+ * proposal named that hold none of the exact set; out[2] proposed patches. */
+int sww_learn_stats(sww_handle* h, int64_t* out, int reset);
+
+/* Training kernels on device arrays (stream: the caller's).  X[n][F] features, y[n]
+ * labels in {0, 1}, params[SWW_MLP_PARAMS] FP32 masters.  loss_grad writes the mean
+ * weighted binary cross-entropy (positive class weight pos_weight) and its gradient:
+ * out[0..SWW_MLP_PARAMS) = d loss / d params (through the BF16 rounding, passed
+ * straight through), out[SWW_MLP_PARAMS] = loss; work holds SWW_MLP_WORK floats.
+ * adam: one Adam update (beta 0.9, 0.999, eps 1e-8) of params with step count t >= 1
+ * and moments m, v.  predict: p[n] = sigmoid(logit). */
+int sww_mlp_loss_grad(const float* X, const float* y, int64_t n, const float* params, float pos_weight, float* work,
+                      float* out, void* stream);
+int sww_mlp_adam(float* params, const float* grad, float* m, float* v, int t, float lr, void* stream);
+int sww_mlp_predict(const float* X, int64_t n, const float* params, float* p, void* stream);
+
 /* Message of the last error on the calling thread. */
 int sww_last_error(char* buf, size_t len);
 

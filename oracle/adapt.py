@@ -75,9 +75,11 @@ def significance(Hy, j, live_n, live_e, hdet, udet_e, udet_i, VS, eps_h, eps_u):
     return S
 
 
-def build_mask(Hy, sig):
-    """Steps 2-4.  sig[j] = significance set of level j (j > Jmin).  Returns live
-    node and edge sets per level."""
+def build_mask(Hy, sig, extra=None):
+    """Steps 2-4.  sig[j] = significance set of level j (j > Jmin).  extra[j]
+    (optional): nodes of level j added to T after step 2 (an external refinement
+    proposal; the closure then treats them like any other point of T).  Returns
+    live node and edge sets per level."""
     jmin, jmax = Hy.jmin, Hy.jmax
     T = {}
     for j in range(jmin + 1, jmax + 1):
@@ -87,6 +89,8 @@ def build_mask(Hy, sig):
             ch = np.zeros(F.N, dtype=bool)
             ch[: Hy.levels[j - 1].N] = sig[j - 1]
             t |= dilate(F, ch)
+        if extra is not None and j in extra:
+            t |= extra[j]
         T[j] = t
     for j in range(jmax, jmin, -1):
         F = Hy.levels[j]

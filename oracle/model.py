@@ -105,9 +105,10 @@ class Model:
                                         self.VS[j], eps_h, eps_u)
         return sig
 
-    def adapt(self, eps_h=None, eps_u=None):
+    def adapt(self, eps_h=None, eps_u=None, extra=None):
         """Coefficients -> thresholds -> mask -> inverse transform of the retained
-        coefficients onto the new live set -> ghosts.
+        coefficients onto the new live set -> ghosts.  extra[j]: nodes of level j
+        joining the set T before the closure (an external refinement proposal).
 
         Reading: the adapted field is the inverse wavelet transform of the
         coefficients kept (Sec. 2.3: dropping a coefficient sets it to zero), so the
@@ -118,7 +119,7 @@ class Model:
             eps_h, eps_u = self.thresholds()
         self.eps_h, self.eps_u = eps_h, eps_u
         sig = self.significance(hdet, ue, ui, eps_h, eps_u)
-        live_n, live_e = adapt.build_mask(self.Hy, sig)
+        live_n, live_e = adapt.build_mask(self.Hy, sig, extra)
         self.apply_mask(live_n, live_e, hdet, ue, ui)
         return hdet, ue, ui
 

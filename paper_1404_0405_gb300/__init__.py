@@ -15,16 +15,21 @@ import numpy as np
 
 from .buildlib import LIB, build
 
-__all__ = ["Model", "SwwError", "step_ensemble", "load", "lib_path", "DH", "U", "DH_T", "U_T", "NODE_FLAGS", "EDGE_FLAGS",
+__all__ = ["Model", "SwwError", "step_ensemble", "mlp_loss_grad", "mlp_adam", "mlp_predict", "load", "lib_path", "DH", "U", "DH_T", "U_T", "NODE_FLAGS", "EDGE_FLAGS",
            "HDET", "UDET_E", "UDET_I", "SIG", "LIVE", "GHOST", "COVERED"]
 
 DH, U, DH_T, U_T, NODE_FLAGS, EDGE_FLAGS, HDET, UDET_E, UDET_I, SIG = range(10)
 LIVE, GHOST, COVERED = 1, 2, 4
+MLP_FEATURES, MLP_HIDDEN = 8, 32
+MLP_PARAMS = MLP_FEATURES * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
+MLP_WORK = 256 * (MLP_PARAMS + 1)
+P_FEATURES, P_EXACT, P_PROPOSAL, P_ACTIVE = range(4)
 RK4, SSP43 = 0, 1
 EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
            "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
-           "sww_create_shared", "sww_step_ensemble"]
+           "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
+           "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt"]
 
@@ -86,6 +91,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_mass_energy_static": [P, P, P, P],
         "sww_create_shared": [ctypes.POINTER(Config), P, P, ctypes.POINTER(P)],
         "sww_step_ensemble": [ctypes.POINTER(P), I, D, I, I],
+        "sww_set_learned": [P, I, P, ctypes.c_float],
+        "sww_propose": [P, I, P],
+        "sww_get_patch_data": [P, I, I, P],
+        "sww_learn_stats": [P, I64, I],
+        "sww_mlp_loss_grad": [P, P, ctypes.c_int64, P, ctypes.c_float, P, P, P],
+        "sww_mlp_adam": [P, P, P, P, I, ctypes.c_float, P],
+        "sww_mlp_predict": [P, ctypes.c_int64, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -126,6 +138,24 @@ def step_ensemble(models, dt=-1.0, nsteps=1, adapt=True):
     (sww_step_ensemble)."""
     hs = (ctypes.c_void_p * len(models))(*[m._h.value for m in models])
     _check(load().sww_step_ensemble(hs, len(models), float(dt), int(nsteps), int(bool(adapt))))
+
+
+def mlp_loss_grad(X, y, params, pos_weight, work, out, stream=None):
+    """Device tensors: X[n, 8], y[n], params[MLP_PARAMS], work[MLP_WORK], out[MLP_PARAMS + 1]
+    (gradient, then the mean loss) -- sww_mlp_loss_grad."""
+    st = stream if stream is not None else _default_stream()
+    _check(load().sww_mlp_loss_grad(_ptr(X)[0], _ptr(y)[0], X.shape[0], _ptr(params)[0], float(pos_weight),
+                                    _ptr(work)[0], _ptr(out)[0], st))
+
+
+def mlp_adam(params, grad, m, v, t, lr, stream=None):
+    st = stream if stream is not None else _default_stream()
+    _check(load().sww_mlp_adam(_ptr(params)[0], _ptr(grad)[0], _ptr(m)[0], _ptr(v)[0], int(t), float(lr), st))
+
+
+def mlp_predict(X, params, out, stream=None):
+    st = stream if stream is not None else _default_stream()
+    _check(load().sww_mlp_predict(_ptr(X)[0], X.shape[0], _ptr(params)[0], _ptr(out)[0], st))
 
 
 class Model:
@@ -244,6 +274,38 @@ class Model:
         """Mass and energy of level Jmin into out[2] without any device allocation
         (dh, u, out: torch CUDA float64 tensors; asynchronous on the caller's stream)."""
         _check(load().sww_mass_energy_static(self._h, _ptr(dh)[0], _ptr(u)[0], _ptr(out)[0]))
+
+    # ------------------------------------------------------------------ learned proposal
+    def set_learned(self, mode, params=None, tau=0.5):
+        """mode 0 off, 1 features only, 2 features and proposal (params: MLP_PARAMS floats)."""
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+            assert buf.size == MLP_PARAMS
+        _check(load().sww_set_learned(self._h, int(mode), None if buf is None else _ptr(buf)[0], float(tau)))
+
+    def propose(self, level, flags):
+        f = np.ascontiguousarray(np.asarray(flags, dtype=np.uint8))
+        assert f.size == self.sizes(level)[3] + 1
+        _check(load().sww_propose(self._h, level, _ptr(f)[0]))
+
+    def patch_data(self, level, what):
+        np1 = self.sizes(level)[3] + 1
+        if what == P_FEATURES:
+            out = np.empty((MLP_FEATURES, np1), dtype=np.float32)
+        elif what in (P_EXACT, P_PROPOSAL):
+            out = np.empty(np1, dtype=np.uint8)
+        elif what == P_ACTIVE:
+            out = np.empty(np1 - 1, dtype=np.uint8)
+        else:
+            raise ValueError(what)
+        _check(load().sww_get_patch_data(self._h, level, what, _ptr(out)[0]))
+        return out
+
+    def learn_stats(self, reset=False):
+        out = (ctypes.c_int64 * 3)()
+        _check(load().sww_learn_stats(self._h, out, int(bool(reset))))
+        return {"misses": out[0], "over": out[1], "proposed": out[2]}
 
     def stats(self):
         st = Stats()

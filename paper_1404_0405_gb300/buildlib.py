@@ -1,6 +1,6 @@
 """Build the in-tree shared library libsww.so for sm_103a with nvcc.
 
-The three translation units compile in parallel; the library is linked with
+The translation units compile in parallel; the library is linked with
 the host OpenMP runtime (the grid builder is multithreaded).  Run as
 ``python -m paper_1404_0405_gb300.buildlib``.
 """
@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libsww.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu"]
+SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu", "sww_learn.cu"]
 
 
 def nvcc():

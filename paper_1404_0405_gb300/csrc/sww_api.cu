@@ -27,6 +27,7 @@
 #include "sww_core.cuh"
 #include "sww_internal.h"
 #include "sww_kernels.h"
+#include "sww_learn.h"
 
 using namespace sww;
 
@@ -114,6 +115,7 @@ struct Geometry {
             F.en = D.en, F.et = D.et, F.tn = D.tn, F.te = D.te, F.deg = D.deg, F.ring_e = D.ring_e, F.f2c = D.f2c;
             F.cor_i = D.cor_i, F.par = D.par, F.fe_kind = D.fe_kind, F.fe_ce = D.fe_ce, F.vst = D.vst;
             F.c2f = D.c2f, F.mid = D.mid, F.half = D.half, F.mk_i = D.mk_i, F.rf_fi = D.rf_fi, F.rf_ci = D.rf_ci;
+            F.ppar = D.ppar, F.pnbr = D.pnbr;
             F.A_i64 = D.A_i64, F.d_e64 = D.d_e64, F.l_e64 = D.l_e64;
             auto cv = [&](const double* x, int64_t n) -> const float* {
                 if (!x) return nullptr;
@@ -151,6 +153,11 @@ struct sww_handle {
     std::vector<DevLevelT<float>> lvf;
     void* d_lvs = nullptr;          // device copy of lv or lvf
     double* stage = nullptr;        // FP64 staging buffer of FP32 handles (set_state)
+    // learned refinement proposal: 0 off, 1 features only, 2 features and proposal
+    int learn_mode = 0;
+    float tau = 0.5f;
+    MlpWeights net{};
+    unsigned long long* lstat = nullptr;   // [3] misses, over-refined, proposed (cumulative)
     std::vector<void*> allocs;
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
@@ -288,6 +295,35 @@ void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side
             f2c[L.nelem + 1] = int32_t(10 * cn * cn + 1);
         }
         D.f2c = G.up(f2c);
+        // patch graph: same-level neighbour patches (any node of one adjacent to a
+        // node of the other) and the coarse patch under each patch
+        const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
+        auto patch_of = [&](int64_t v) { return v < L.nelem ? v / pp : L.npatch; };
+        std::vector<int32_t> nbr(NB * np1, -1), par(np1, -1);
+        std::vector<int> cnt(np1, 0);
+        for (int64_t v = 0; v < L.N; ++v) {
+            int64_t P = patch_of(v);
+            for (int k = 0; k < L.deg[v]; ++k) {
+                int64_t Q = patch_of(L.ring_n[k][v]);
+                if (Q == P) continue;
+                bool seen = false;
+                for (int q = 0; q < cnt[P]; ++q) seen = seen || nbr[q * np1 + P] == Q;
+                if (seen) continue;
+                if (cnt[P] >= NB) throw std::runtime_error("patch with more than NB neighbour patches");
+                nbr[cnt[P]++ * np1 + P] = int32_t(Q);
+            }
+        }
+        if (fine_side) {
+            const int64_t cp = std::min<int64_t>(L.p, L.n / 2), cpp = cp * cp, cnelem = 10 * (L.n / 2) * (L.n / 2);
+            for (int64_t v = 0; v < L.N; ++v) {
+                int64_t P = patch_of(v);
+                if (par[P] >= 0) continue;
+                int64_t k = f2c[v] >= 0 ? f2c[v] : f2c[L.par[0][v]];
+                par[P] = int32_t(k < cnelem ? k / cpp : cnelem / cpp);
+            }
+        }
+        D.pnbr = G.up(nbr);
+        D.ppar = G.up(par);
     }
     G.lv[L.J] = D;
 }
@@ -332,6 +368,13 @@ void alloc_state(sww_handle* h, int j) {
     for (auto p : bN) *p = h->alloc<uint8_t>(N);
     D.eflag = h->alloc<uint8_t>(E);
     D.pflag = h->alloc<uint8_t>(D.npatch);
+    D.pfeat = h->alloc<float>(NF * (D.npatch + 1));
+    D.prop = h->alloc<uint8_t>(D.npatch + 1);
+    D.prop_prev = h->alloc<uint8_t>(D.npatch + 1);
+    D.pexact = h->alloc<uint8_t>(D.npatch + 1);
+    uint8_t* pz[] = {D.prop, D.prop_prev, D.pexact};
+    for (uint8_t* p : pz) ck(cudaMemset(p, 0, D.npatch + 1), "memset");
+    ck(cudaMemset(D.pfeat, 0, NF * (D.npatch + 1) * sizeof(float)), "memset");
     D.patches = h->alloc<int32_t>(D.npatch + 1);
     D.npatches = h->alloc<int32_t>(1);
     for (auto p : dN) ck(cudaMemset(*p, 0, N * sizeof(R)), "memset");
@@ -522,6 +565,7 @@ MaskArgsT<R> mask_args(const sww_handle* h, int j0, int j1, bool allow_tail = tr
     a.sig_any = h->sig_any;
     a.sig_any_len = h->cfg.jmax + 2;
     a.tail_blocks = h->grid_all;
+    a.lstat = h->lstat;
     return a;
 }
 
@@ -535,7 +579,18 @@ void mask_and_inverse(sww_handle* h) {
     {
         Trace tm(h, SWW_K_MASK);
         MaskArgsT<R> a = mask_args<R>(h, j0, j1);
+        ck(cudaMemsetAsync(h->sig_any, 0, sizeof(int32_t) * (h->cfg.jmax + 2), s), "memset sig_any");
+        // learned proposal for this mask: features of the current coefficients on the
+        // levels above Jmin up to the mask's top level, then the perceptron
+        if (h->learn_mode > 0 && j1 > j0) {
+            const Span pf = span_of(h, j0 + 1, j1, [](const DevLevel& L) { return L.npatch + 1; });
+            launch_features(dlv<R>(h), pf, h->thr, j0, h->cfg.jmax, s);
+            if (h->learn_mode > 1) launch_propose(dlv<R>(h), pf, h->net, h->tau, s);
+        }
+        const Span props = span_of(h, j0 + 1, h->cfg.jmax, [](const DevLevel& L) { return L.npatch + 1; });
+        if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 0, h->sig_any, s);
         launch_mask(a, s);
+        if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 1, h->sig_any, s);
         launch_concat(dlv<R>(h), j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
@@ -733,6 +788,8 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
         *h->h_dt = 0;
         h->red = h->alloc<unsigned long long>(4);
+        h->lstat = h->alloc<unsigned long long>(4);
+        ck(cudaMemset(h->lstat, 0, 4 * sizeof(unsigned long long)), "memset");
         h->cnt = h->alloc<unsigned long long>(4);
         h->thr = h->alloc<double>(2);
         h->dt = h->alloc<double>(1);
@@ -1124,6 +1181,84 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
         st->dt = h->last_dt;
         st->steps = h->steps;
         st->kernel_launches = kernel_launches();
+        return SWW_OK;
+    });
+}
+
+int sww_set_learned(sww_handle* h, int mode, const float* params, float tau) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (mode < 0 || mode > 2) return fail(SWW_E_ARG, "mode must be 0, 1 or 2");
+    if (mode == 2 && (!params || !(tau > 0.f) || !(tau < 1.f))) return fail(SWW_E_ARG, "mode 2 needs params and 0 < tau < 1");
+    return guarded([&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "set_learned");
+        h->learn_mode = mode;
+        h->tau = tau;
+        if (params) h->net = mlp_weights(params);
+        h->drop_graphs();
+        return SWW_OK;
+    });
+}
+
+int sww_propose(sww_handle* h, int level, const uint8_t* flags) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (!flags) return fail(SWW_E_ARG, "null flags");
+    if (level == h->cfg.jmin) return fail(SWW_E_ARG, "Jmin is always complete");
+    return guarded([&]() -> int {
+        uint8_t* prop = nullptr;
+        by_prec(h, [&](auto r) {
+            prop = lvl<decltype(r)>(h)[level].prop;
+            return 0;
+        });
+        {
+            Join jn(h);
+            ck(cudaMemcpyAsync(prop, flags, meta(h, level).npatch + 1, cudaMemcpyHostToDevice, h->stream), "propose");
+        }
+        ck(cudaStreamSynchronize(h->stream), "propose");
+        return SWW_OK;
+    });
+}
+
+int sww_get_patch_data(const sww_handle* h, int level, int what, void* out) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (!out) return fail(SWW_E_ARG, "null output");
+    sww_handle* hh = const_cast<sww_handle*>(h);
+    return guarded([&]() -> int {
+        const void* src = nullptr;
+        size_t bytes = 0;
+        const int64_t np1 = meta(h, level).npatch + 1;
+        by_prec(h, [&](auto r) {
+            const auto& L = lvl<decltype(r)>(h)[level];
+            switch (what) {
+                case SWW_P_FEATURES: src = L.pfeat, bytes = NF * np1 * sizeof(float); break;
+                case SWW_P_EXACT: src = L.pexact, bytes = np1; break;
+                case SWW_P_PROPOSAL: src = L.prop_prev, bytes = np1; break;
+                case SWW_P_ACTIVE: src = L.pflag, bytes = np1 - 1; break;
+            }
+            return 0;
+        });
+        if (!src) return fail(SWW_E_ARG, "unknown patch quantity");
+        {
+            Join jn(hh);
+            ck(cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, hh->stream), "patch data");
+        }
+        ck(cudaStreamSynchronize(hh->stream), "patch data");
+        return SWW_OK;
+    });
+}
+
+int sww_learn_stats(sww_handle* h, int64_t* out, int reset) {
+    if (!h || !out) return fail(SWW_E_ARG, "null argument");
+    return guarded([&]() -> int {
+        unsigned long long c[3] = {0, 0, 0};
+        {
+            Join jn(h);
+            ck(cudaMemcpyAsync(c, h->lstat, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "learn stats");
+            if (reset) ck(cudaMemsetAsync(h->lstat, 0, sizeof(c), h->stream), "learn stats");
+        }
+        ck(cudaStreamSynchronize(h->stream), "learn stats");
+        for (int k = 0; k < 3; ++k) out[k] = int64_t(c[k]);
         return SWW_OK;
     });
 }

@@ -9,6 +9,11 @@ namespace sww {
 constexpr uint8_t LIVE = 1, GHOST = 2, COVERED = 4, WASLIVE = 8;
 constexpr uint8_t AVAIL = LIVE | GHOST;
 
+// Learned refinement proposal: NF features per patch, NH hidden units, NB
+// same-level neighbour patches at most.
+constexpr int NF = 8, NH = 32, NB = 12;
+constexpr int MLP_PARAMS = NF * NH + NH + NH + 1;   // W1[NF][NH], b1[NH], w2[NH], b2
+
 // Work-list entry: (level << LVL_SHIFT) | patch; patch == npatch stands for the two poles.
 constexpr int LVL_SHIFT = 27;
 constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
@@ -47,12 +52,19 @@ struct DevLevelT {
     const R* mk_w;                 // [12*N]
     const int32_t *rf_fi, *rf_ci;  // [12*E], [11*E]
     const R *rf_fw, *rf_cw;
+    // patch graph (index npatch is the two poles)
+    const int32_t* ppar;           // [npatch+1] patch of level J-1 under each patch (-1 on the coarsest level)
+    const int32_t* pnbr;           // [NB*(npatch+1)] same-level neighbour patches, -1 padded
     // state and work arrays
     R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
     R *F, *q, *B, *c, *Q;
     uint8_t *nflag, *eflag, *sig, *tmask, *band0, *band1;
     R *hdet, *ue, *ui;             // [N], [E of level J-1], [E]
     uint8_t* pflag;                // [npatch]
+    // learned refinement proposal (per patch)
+    float* pfeat;                  // [NF*(npatch+1)] features of the last adaptation
+    uint8_t *prop, *prop_prev;     // [npatch+1] proposal for the next / used by the last mask
+    uint8_t* pexact;               // [npatch+1] patch holds a point of the exact rules' set
     int32_t* patches;              // [npatch + 1] active patch list (+ pole entry), level-tagged
     int32_t* npatches;             // [1]
 };

@@ -698,6 +698,13 @@ __global__ void k_adjacent(const DevLevelT<R>* __restrict__ lvs, Span sp, int jm
                 if (cy >= 0 && C.sig[cy]) t = 1;
             }
         }
+        // a patch the learned proposal names joins T as a whole (the exact rules' own
+        // set is recorded per patch for the proposal's statistics)
+        const int64_t P = x < F.nelem ? x / (F.p * F.p) : F.npatch;
+        if (t)
+            F.pexact[P] = 1;
+        else if (F.prop[P])
+            t = 1;
         F.tmask[x] = t;
     });
 }
@@ -786,8 +793,12 @@ __global__ void k_covered(const DevLevelT<R>* __restrict__ lvs, Span sp) {
 }
 
 // patches holding any live or ghost node or edge (one block per patch)
+// With lstat, also counts per patch above Jmin: [0] the exact rules' set reaches a
+// patch that was not active during the step (a late refinement), [1] a patch the
+// previous proposal named holds none of the exact set, [2] the patches proposed.
 template <class R>
-__global__ void k_patch_flags(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
+__global__ void k_patch_flags(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any,
+                              unsigned long long* lstat) {
     int j;
     int64_t pid;
     if (!locate(sp, int64_t(blockIdx.x), j, pid)) return;
@@ -806,7 +817,14 @@ __global__ void k_patch_flags(const DevLevelT<R>* __restrict__ lvs, Span sp, con
             if ((L.nflag[e] | L.eflag[e] | L.eflag[L.nelem + e] | L.eflag[2 * L.nelem + e]) & AVAIL) any = 1;
         }
         any = __syncthreads_or(any);
-        if (threadIdx.x == 0) L.pflag[pid] = uint8_t(any);
+        if (threadIdx.x == 0) {
+            if (lstat && j > sp.ja) {
+                if (L.pexact[pid] && !L.pflag[pid]) atomicAdd(&lstat[0], 1ull);
+                if (L.prop_prev[pid] && !L.pexact[pid]) atomicAdd(&lstat[1], 1ull);
+                if (L.prop[pid]) atomicAdd(&lstat[2], 1ull);
+            }
+            L.pflag[pid] = uint8_t(any);
+        }
     }
 }
 
@@ -945,8 +963,8 @@ void launch_restrict_full(const DevLevelT<R>& C, const DevLevelT<R>& F, cudaStre
 
 template <class R>
 void launch_mask(const MaskArgsT<R>& a, cudaStream_t s) {
+    // a.sig_any is cleared by the caller (a proposal may already have marked levels)
     const int32_t* any = a.sig_any;
-    cudaMemsetAsync(a.sig_any, 0, sizeof(int32_t) * a.sig_any_len, s);
     // significance, adjacency in space and scale (levels ja+1..jb, independent)
     MULTI(k_zero_sig<R>, a.nodes_f, a.lvs, a.nodes_f, any);
     MULTI(k_sig<R>, a.edges_f, a.lvs, a.edges_f, a.thr, a.sig_any);
@@ -967,7 +985,7 @@ void launch_mask(const MaskArgsT<R>& a, cudaStream_t s) {
     MULTI(k_ghost<R>, a.edges_f, a.lvs, a.edges_f, a.hops % 2 == 1, any);
     if (a.jb > a.ja) MULTI(k_covered<R>, a.nodes_c, a.lvs, a.nodes_c);
     g_launches += 2;
-    k_patch_flags<R><<<unsigned(a.patches.off[a.jb + 1 - a.ja]), 64, 0, s>>>(a.lvs, a.patches, any);
+    k_patch_flags<R><<<unsigned(a.patches.off[a.jb + 1 - a.ja]), 64, 0, s>>>(a.lvs, a.patches, any, a.lstat);
     k_patch_scan<R><<<unsigned(a.jb - a.ja + 1), 1024, 0, s>>>(a.lvs, a.ja, any, a.patches.tail_j);
 }
 
@@ -985,7 +1003,8 @@ void launch_covered_all(const DevLevelT<R>* lvs, const Span& nodes_c, cudaStream
 template <class R>
 void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream_t s) {
     g_launches += 2;
-    k_patch_flags<R><<<unsigned(patches.off[patches.jb + 1 - patches.ja]), 64, 0, s>>>(lvs, patches, nullptr);
+    k_patch_flags<R><<<unsigned(patches.off[patches.jb + 1 - patches.ja]), 64, 0, s>>>(lvs, patches, nullptr,
+                                                                                         nullptr);
     k_patch_scan<R><<<unsigned(patches.jb - patches.ja + 1), 1024, 0, s>>>(lvs, patches.ja, nullptr, -1);
 }
 

@@ -51,6 +51,7 @@ struct MaskArgsT {
     int32_t* sig_any;           // [sig_any_len] per level: any significant point (device)
     int sig_any_len;
     unsigned tail_blocks;       // blocks of a per-level launch on the tail level
+    unsigned long long* lstat;  // learned-proposal counters (misses, over, proposed) or null
 };
 
 // Launchers; R = double (FP64 form) or float (FP32 form), instantiated for both.
