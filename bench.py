@@ -1,19 +1,29 @@
 #!/usr/bin/env python
-"""Benchmark: active-cell RK4 steps per second of the adaptive wavelet TRiSK step.
+"""Benchmark: active-cell RK4 steps per second of the adaptive wavelet TRiSK step,
+chosen form against the plain form at equal error.
 
 Workload (seeded, synthetic): zonal jet u = 80 exp(-((lat - lat0)/7 deg)^2) m/s
 with gradient-wind balanced depth (mean 10 km) and three 120 m Gaussian bumps,
 radius 6.371e6 m, Omega 7.292e-5 1/s, g 9.80616 m/s^2, adaptive levels
-Jmin=4..Jmax=9, eps = 1e-2 relative, RK4, CFL 0.8, FP64 throughout (the plain
-form).  A step is one RK4 step with its partial transform and grid adaptation.
-Value = (live nodes over all levels, averaged over the timed steps) x steps /
-seconds, with per-step CUDA-event times (the L2 cache is flushed between steps
-with a 512 MiB write outside the timed events).
+Jmin=4..Jmax=9, eps = 1e-2 relative, RK4, CFL 0.8.  A step is one RK4 step with
+its partial transform and grid adaptation.
+
+* plain form: FP64, one member, the exact threshold criterion;
+* chosen form (default): FP32 fields and stencils, an ensemble of --members
+  independent members (seeds) advanced together (each on its own stream, one
+  persistent launch per RK stage, shared grid tables), and the learned refinement
+  proposal, trained first on masks of two extra members.
+
+value = (live nodes over all levels and members, averaged over each step's start
+and end) x steps / seconds, with per-step CUDA-event times (the L2 cache is
+flushed between steps with a 512 MiB write outside the timed events).
+equal_error: relative l2 error of the Jmin depth after --err-steps steps of the
+same dt, plain and chosen, against a non-adaptive FP64 run (every point live).
 
 --impl reference runs the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm for this build).  With --gpus N under torchrun every
-rank runs an independent ensemble member (seed + rank): weak scaling, no
-collective on the data path.
+rank runs its own members (seeds offset by rank): weak scaling, no collective on
+the data path.
 """
 from __future__ import annotations
 
@@ -30,6 +40,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# ensemble members run on their own streams: let them use separate hardware queues
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 METRIC = "active-cell RK4 steps/s, adaptive Jmax=9, chosen vs plain form, equal error"
@@ -47,15 +59,23 @@ def parse():
     p.add_argument("--eps", type=float, default=1e-2)
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--patch", type=int, default=8)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    p.add_argument("--form", default="chosen", choices=["chosen", "plain"],
+                   help="chosen: FP32 ensemble with the learned proposal; plain: FP64, one member")
+    p.add_argument("--members", type=int, default=16, help="ensemble members of the chosen form")
+    p.add_argument("--plain-steps", type=int, default=10)
+    p.add_argument("--train-steps", type=int, default=10)
+    p.add_argument("--err-steps", type=int, default=20)
+    p.add_argument("--tau", type=float, default=0.5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-jmax", type=int, default=6, help="finest level of the oracle sample")
     return p.parse_args()
 
 
 def workload_name(a):
+    form = ("FP32 ensemble of independent members, learned proposal" if a.form == "chosen"
+            else "FP64 plain form, one member")
     return (f"adaptive zonal jet + 3 bumps, Jmin={a.jmin}..Jmax={a.jmax}, eps={a.eps:g} relative, "
-            f"FP64 plain form, RK4, CFL 0.8")
+            f"RK4, CFL 0.8, {form}")
 
 
 def edge_geometry(xyz, en):
@@ -177,24 +197,97 @@ def combine_ranks(seconds, cells, device, world):
 
 # ----------------------------------------------------------------------------- our arm
 
-# Algorithmic bytes per live edge of one launch of the second trend pass
-# (k_node_coriolis, FP64).  Coriolis part, per live edge: the ten reconstruction
-# weights and edge ids (10 x 12 B), the edge's own flux, its two triangle ids and
-# potential vorticities (8 + 8 + 16 B), and the tendency it writes (8 B).  Node
-# part, per node (three edges per node on the grid): area, depth, degree, six
-# ring-edge codes, face and edge lengths already counted with the edges, and the
-# divergence and Bernoulli function written (8 + 8 + 1 + 24 + 16 B = 57 B), i.e.
-# 19 B per edge.  Values shared with neighbours are counted once, with their owner.
-CORIOLIS_BYTES_PER_EDGE = 10 * 12 + 8 + 8 + 16 + 8 + 19
-# DRAM bytes (read + write) per launch of k_node_coriolis from one ncu capture of
-# the jet at Jmin=4..Jmax=8, eps=1e-2 (the same active set and launches as
-# Jmax=9); None once the kernel changes.
-CORIOLIS_TRAFFIC_PER_LAUNCH = 15.933184e6 + 0.344064e6
+# Algorithmic bytes per live cell (one node, three edges, two triangles) of one
+# persistent RK stage at the minimum a fused stage must move: the state read
+# (dh, u: 32 B), the RK base read and the new state written (64 B), and the
+# geometry in its minimal form (cell and dual areas, 3 d_e, 3 l_e, kite fractions,
+# Coriolis at the dual cells: 17 words, 136 B) -- 232 B in FP64; the FP32 form
+# halves every term (its state and stencil weights are FP32).
+STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
+
+
+def _live(m):
+    return sum(m.stats()["live_nodes"].values())
+
+
+def _members(sww, workloads, base, a, precision, seeds, learned=None):
+    ms = []
+    xyz, en = base.grid(a.jmax)
+    mid, tan = edge_geometry(xyz, en)
+    for sd in seeds:
+        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision, share=base)
+        dh, u = workloads.Workload("jet", seed=sd).fields(xyz, mid, tan)
+        m.set_state(dh, u)
+        m.adapt()
+        m.adapt()
+        if learned is not None:
+            m.set_learned(2, learned, a.tau)
+        ms.append(m)
+    return ms
+
+
+def _timed(sww, ms, steps, flush, stream):
+    """CUDA-event time of each ensemble step (L2 flushed before each, outside the
+    events) and the live cells advanced (mean of the step's start and end)."""
+    import torch
+    times, cells = [], []
+    for _ in range(steps):
+        c0 = sum(_live(m) for m in ms)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sww.step_ensemble(ms, -1.0, 1, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        cells.append(0.5 * (c0 + sum(_live(m) for m in ms)))
+    return times, cells
+
+
+def _equal_error(sww, workloads, base, a, learned, seed, steps):
+    """Relative l2 error of the Jmin depth after `steps` steps of a fixed dt, for the
+    plain form (FP64, exact mask) and the chosen form (FP32, learned proposal),
+    against a non-adaptive FP64 run (eps = 0: every point live) substepped at its own
+    CFL limit to the same final time."""
+    import numpy as np
+    xyz, en = base.grid(a.jmax)
+    mid, tan = edge_geometry(xyz, en)
+    dh, u = workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)
+
+    def make(precision, eps, prop=None):
+        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=eps, rk="rk4", cfl=0.8, precision=precision, share=base)
+        m.set_state(dh, u)
+        if eps > 0:
+            m.adapt()
+            m.adapt()
+        if prop is not None:
+            m.set_learned(2, prop, a.tau)
+        return m
+
+    plain, chosen, ref = make("fp64", a.eps), make("fp32", a.eps, learned), make("fp64", 0.0)
+    dt = plain.stats()["dt"] or 0.0
+    if dt <= 0:
+        plain.step(-1.0, 1, True)
+        dt = plain.stats()["dt"]
+        plain = make("fp64", a.eps)
+    ref.step(-1.0, 1, False)
+    sub = max(1, math.ceil(dt / ref.stats()["dt"]))
+    ref = make("fp64", 0.0)
+    for m in (plain, chosen):
+        m.step(dt, steps, True)
+    ref.step(dt / sub, steps * sub, False)
+    r = ref.get(a.jmin, sww.DH)
+    err = lambda m: float(np.linalg.norm(m.get(a.jmin, sww.DH) - r) / np.linalg.norm(r))
+    out = {"steps": steps, "dt_s": dt, "reference_substeps": sub, "plain_fp64": err(plain),
+           "chosen": err(chosen)}
+    out["ratio"] = out["chosen"] / max(out["plain_fp64"], 1e-300)
+    return out
 
 
 def run_ours(a, rank, world):
     import torch
     import paper_1404_0405_gb300 as sww
+    from paper_1404_0405_gb300 import learn
     import workloads
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
@@ -202,102 +295,126 @@ def run_ours(a, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
-    seed = a.seed + rank
+    seed = a.seed + 1000 * rank
     t_setup = time.perf_counter()
-    m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=a.precision)
-    xyz, en = m.grid(a.jmax)
-    mid, tan = edge_geometry(xyz, en)
-    dh0, u0 = workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)
-    setup_s = time.perf_counter() - t_setup
-
-    def active():
-        return sum(m.stats()["live_nodes"].values())
-
-    m.set_state(dh0, u0)
-    m.adapt()
-    m.adapt()
-    for _ in range(a.warmup):
-        m.step(-1.0, 1, adapt=True)
+    base = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8)
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    clocks = Clocks(dev)
-    times, cells = [], []
-    launches0 = m.stats()["kernel_launches"]
+
+    # plain form: FP64, one member, the exact criterion alone
+    plain_m = _members(sww, workloads, base, a, "fp64", [seed])
+    for _ in range(a.warmup):
+        sww.step_ensemble(plain_m, -1.0, 1, True)
+    pt, pc = _timed(sww, plain_m, a.plain_steps, flush, stream)
+    plain_t, plain_c = combine_ranks(sum(pt), sum(pc), "cuda", world)
+    plain = {"value": plain_c / plain_t, "ms_per_step": 1e3 * plain_t / len(pt), "members": 1, "dtype": "f64",
+             "active_cells_per_step": plain_c / len(pc) / max(world, 1)}
+
+    # chosen form: FP32, an ensemble of members in one concurrent step, learned proposal
+    learned = None
+    lstats = None
+    if a.form == "chosen":
+        train_m = _members(sww, workloads, base, a, "fp32", [seed + 500 + k for k in range(2)])
+        Xs, ys = zip(*[learn.collect(m, a.train_steps) for m in train_m])
+        X, y = np.concatenate(Xs), np.concatenate(ys)
+        learned, losses = learn.train(X, y, epochs=300)
+        del train_m
+        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], learned)
+        dtype = "f32"
+    else:
+        ms, dtype = plain_m, "f64"
+    setup_s = time.perf_counter() - t_setup
+    for _ in range(a.warmup):
+        sww.step_ensemble(ms, -1.0, 1, True)
+    for m in ms:
+        if learned is not None:
+            m.learn_stats(reset=True)
+    launches0 = ms[0].stats()["kernel_launches"]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clocks = Clocks(dev)
     clocks.start()
-    for _ in range(a.steps):
-        act0 = active()
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        m.step(-1.0, 1, adapt=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1) / 1e3)
-        cells.append(0.5 * (act0 + active()))
+    times, cells = _timed(sww, ms, a.steps, flush, stream)
     clk = clocks.stop()
-    launches = m.stats()["kernel_launches"] - launches0
-    total = sum(times)
-    total_all, cells_all = combine_ranks(total, sum(cells), "cuda", world)
+    launches = ms[0].stats()["kernel_launches"] - launches0   # process-wide counter: every member
+    total_all, cells_all = combine_ranks(sum(times), sum(cells), "cuda", world)
     value = cells_all / total_all
+    if learned is not None:
+        lstats = {"misses": 0, "over": 0, "proposed": 0}
+        for m in ms:
+            for k, v in m.learn_stats(reset=True).items():
+                lstats[k] += v
+        lstats["train_samples"] = int(len(y))
+        lstats["train_loss"] = [float(losses[0]), float(losses[-1])]
 
-    # live per-launch timing of the dominant kernel (Coriolis) over the same number of steps
-    st = m.stats()
-    m.profile(["coriolis"])
-    live_edges = st["live_edges"]
+    # live per-launch timing of the dominant kernel (the persistent RK stage)
+    m0 = ms[0]
+    prec = "fp32" if dtype == "f32" else "fp64"
+    m0.profile(["stage"])
+    cells_prof = 0.0
     for _ in range(a.steps):
         flush.zero_()
-        m.step(-1.0, 1, adapt=True)
-    prof = m.profile_read()
-    m.profile([])
-    cor_ms, cor_n = prof["coriolis"]
-    # one launch per RK stage covers every level; bytes use the live edges
-    per_step_bytes = 4 * sum(live_edges.values()) * CORIOLIS_BYTES_PER_EDGE
-    achieved = per_step_bytes * a.steps / (cor_ms / 1e3) / 1e9
+        cells_prof += _live(m0)
+        m0.step(-1.0, 1, adapt=True)
+    prof = m0.profile_read()
+    m0.profile([])
+    st_ms, st_n = prof["stage"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         peak, peak_src = peaks["hbm_gbs"], "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    roofline = {"bound": "hbm", "kernel": "k_node_coriolis", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)",
-                "traffic": CORIOLIS_TRAFFIC_PER_LAUNCH if a.jmax >= 8 and a.eps == 1e-2 else None,
-                "avg_launch_us": cor_ms * 1e3 / max(cor_n, 1), "launches": cor_n,
-                "bytes_per_live_edge": CORIOLIS_BYTES_PER_EDGE}
+    roofline = None
+    if st_n > 0:
+        stage_bytes = STAGE_BYTES_PER_CELL[prec] * cells_prof * 4   # four stages per step
+        achieved = stage_bytes / (st_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)", "traffic": None,
+                    "avg_launch_us": st_ms * 1e3 / st_n, "launches": st_n,
+                    "bytes_per_live_cell": STAGE_BYTES_PER_CELL[prec]}
+
+    # equal error: chosen vs plain against a non-adaptive run of the same workload
+    err = _equal_error(sww, workloads, base, a, learned, seed, a.err_steps) if a.err_steps > 0 else None
 
     # end to end through the public API from pinned host buffers
-    dh_h = torch.from_numpy(dh0).pin_memory().numpy()
-    u_h = torch.from_numpy(u0).pin_memory().numpy()
+    xyz, en = base.grid(a.jmax)
+    mid, tan = edge_geometry(xyz, en)
+    host = []
+    for k, m in enumerate(ms):
+        dh, u = workloads.Workload("jet", seed=seed + k).fields(xyz, mid, tan)
+        host.append((torch.from_numpy(dh).pin_memory().numpy(), torch.from_numpy(u).pin_memory().numpy()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    m.set_state(dh_h, u_h)
-    m.adapt()
+    for m, (dh, u) in zip(ms, host):
+        m.set_state(dh, u)
+        m.adapt()
     ecells = 0.0
     for _ in range(a.steps):
-        m.step(-1.0, 1, adapt=True)
-        s = m.stats()
-        ecells += sum(s["live_nodes"].values())
+        sww.step_ensemble(ms, -1.0, 1, True)
+        ecells += sum(_live(m) for m in ms)
     torch.cuda.synchronize()
     e2e_s, ecells = combine_ranks(time.perf_counter() - t0, ecells, "cuda", world)
-    N, E, _, _ = m.sizes(a.jmax)
-    e2e = {"value": ecells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * (N + E) / a.steps),
-           "d2h_bytes_per_step": int(8 + 8 * 70), "note": "sww_set_state from pinned host arrays + adapt + "
-                                                         "per step sww_step and sww_stats_get"}
+    N, E, _, _ = base.sizes(a.jmax)
+    e2e = {"value": ecells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * (N + E) * len(ms) / a.steps),
+           "d2h_bytes_per_step": int(len(ms) * (8 + 8 * 70)),
+           "note": "per member sww_set_state from pinned host arrays and sww_adapt once, then per step "
+                   "sww_step_ensemble and sww_stats_get of every member"}
 
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": 1e3 * total_all / a.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name(a), "l2": "flushed between steps (512 MiB write)",
-                           "members": world, "patch": a.patch,
-                           "active_cells_per_step": cells_all / a.steps / max(world, 1),
-                           "compression": (10 * 4 ** a.jmax + 2) / (cells_all / a.steps / max(world, 1)),
-                           "grid_setup_s": setup_s},
-                "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline}
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": workload_name(a), "form": a.form, "members": len(ms) * max(world, 1),
+                           "l2": "flushed between steps (512 MiB write)", "patch": a.patch,
+                           "active_cells_per_step": cells_all / a.steps / max(world, 1) / len(ms),
+                           "compression": (10 * 4 ** a.jmax + 2) / (cells_all / a.steps / max(world, 1) / len(ms)),
+                           "setup_s": setup_s},
+                "plain": plain, "chosen_vs_plain": value / plain["value"], "equal_error": err,
+                "learned_proposal": lstats, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
+                "roofline": roofline}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

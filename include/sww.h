@@ -46,7 +46,7 @@ enum {
     SWW_E_ARG = -1,      /* invalid argument (bad level, null pointer, bad config) */
     SWW_E_CUDA = -2,     /* a CUDA call failed; the handle should be destroyed */
     SWW_E_POOL = -3,     /* device memory exhausted at creation */
-    SWW_E_TIMEOUT = -4,  /* reserved: a bounded device wait gave up */
+    SWW_E_TIMEOUT = -4,  /* a bounded device wait (grid barrier of a persistent stage) gave up */
     SWW_E_STATE = -5,    /* call out of order (e.g. step before set_state) */
     SWW_E_NUMERIC = -6   /* non-finite value detected in the state */
 };
@@ -85,6 +85,10 @@ typedef struct {
                           the FP64 tables; thresholds, time step and the compensated
                           mass/energy sums in FP64 on the FP32 values.  The ABI's
                           double arrays are converted at the boundary.                */
+    int persistent;    /* RK stages: 0 or 1 one cooperative launch per stage (all phases of
+                          the trend and the update, grid barriers between them); -1 one
+                          launch per phase.  0 falls back to -1 where a cooperative
+                          launch cannot run.                                           */
 } sww_config;
 
 typedef struct {
@@ -161,7 +165,8 @@ int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
 /* nsteps steps of each of n independent ensemble members (distinct handles, each
  * as sww_step alone would advance it).  Every member's step runs on the member's
  * own stream, so the members' kernels overlap on the GPU; each member waits only
- * for its own previous step.  On entry each member's work is ordered after its
+ * for its own previous step.  With more than one member the RK stages run as one
+ * launch per phase (cooperative launches of different streams do not overlap).  On entry each member's work is ordered after its
  * caller stream, and on return each caller stream waits for its member.
  * Returns the first error; members then stand at different step counts
  * (sww_stats_get tells which). */
@@ -194,7 +199,8 @@ enum {
     SWW_K_MASK = 9,      /* thresholds, significance, closure, ghosts, patches       */
     SWW_K_INVERSE = 10,  /* inverse transform onto the new mask                      */
     SWW_K_DT = 11,       /* CFL time step reduction                                  */
-    SWW_K_NCLASS = 12
+    SWW_K_STAGE = 12,    /* persistent RK stage (trend and update in one launch)     */
+    SWW_K_NCLASS = 13
 };
 
 /* Tracing: from now on record a pair of CUDA events on the library's stream

@@ -20,7 +20,10 @@ LIB = os.path.join(OUT_DIR, "libsww.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
-SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu", "sww_learn.cu"]
+SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu", "sww_learn.cu", "sww_stage.cu"]
+# per-file flags: the persistent stage reads values other blocks wrote earlier in the
+# same launch, so its global loads are cached in L2 only
+EXTRA = {"sww_stage.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def nvcc():
@@ -44,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(OUT_DIR, os.path.basename(s) + ".o")
         objs.append(o)
         lang = ["-x", "cu"] if s.endswith(".cu") else []
-        cmd = [cc] + ARCH + COMMON + lang + ["-c", s, "-o", o]
+        cmd = [cc] + ARCH + COMMON + EXTRA.get(os.path.basename(s), []) + lang + ["-c", s, "-o", o]
         if verbose:
             print(" ".join(cmd))
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -28,6 +28,7 @@
 #include "sww_internal.h"
 #include "sww_kernels.h"
 #include "sww_learn.h"
+#include "sww_stage.h"
 
 using namespace sww;
 
@@ -158,6 +159,12 @@ struct sww_handle {
     float tau = 0.5f;
     MlpWeights net{};
     unsigned long long* lstat = nullptr;   // [3] misses, over-refined, proposed (cumulative)
+    // persistent RK stages: blocks of the cooperative launch (0: one launch per phase),
+    // barrier state and the error flag of a timed-out barrier (device and pinned copy)
+    unsigned stage_blocks = 0, stage_cap = 0;
+    unsigned* bar = nullptr;
+    int* err = nullptr;
+    int* h_err = nullptr;
     std::vector<void*> allocs;
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
@@ -170,8 +177,8 @@ struct sww_handle {
     double t = 0, last_dt = 0;
     int64_t steps = 0;
     bool has_state = false;
-    // captured steps: (top level, adapt, dt) -> graph and its kernel count
-    std::map<std::tuple<int, int, double>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    // captured steps: (top level, adapt, dt, stage blocks) -> graph and its kernel count
+    std::map<std::tuple<int, int, double, unsigned>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     // tracing: per-class event pairs
     uint32_t prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -207,6 +214,7 @@ struct sww_handle {
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (h_counts) cudaFreeHost(h_counts);
+        if (h_err) cudaFreeHost(h_err);
         if (h_dt) cudaFreeHost(h_dt);
         for (void* p : allocs) cudaFree(p);
         if (stream) cudaStreamDestroy(stream);
@@ -496,6 +504,29 @@ void update(sww_handle* h, const RKStage& st) {
     launch_update(work_all<R>(h), st, h->dt, h->stream);
 }
 
+// trend and RK stage: one persistent cooperative launch, or one launch per phase
+template <class R>
+void stage(sww_handle* h, const RKStage& st) {
+    if (!h->stage_blocks) {
+        trend<R>(h);
+        update<R>(h, st);
+        return;
+    }
+    Trace t(h, SWW_K_STAGE);
+    StageArgs<R> a{dlv<R>(h), h->all_list, h->all_count, h->S, h->cfg.jmin, h->jtop, h->cfg.jmax,
+                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err};
+    ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
+}
+
+// SWW_E_TIMEOUT (and the flag cleared) when a persistent stage's barrier timed out
+int barrier_status(sww_handle* h) {
+    if (!*h->h_err) return SWW_OK;
+    *h->h_err = 0;
+    ck(cudaMemset(h->err, 0, sizeof(int)), "reset err");
+    ck(cudaMemset(h->bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "reset barrier");
+    return fail(SWW_E_TIMEOUT, "a grid barrier of the persistent RK stage timed out");
+}
+
 template <class R>
 void compute_dt(sww_handle* h) {
     Trace t(h, SWW_K_DT);
@@ -647,10 +678,7 @@ void one_step(sww_handle* h, double dt, bool do_adapt) {
     { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all<R>(h), h->stream); }
     int ns;
     const RKStage* st = stages(h->cfg.rk, ns);
-    for (int k = 0; k < ns; ++k) {
-        trend<R>(h);
-        update<R>(h, st[k]);
-    }
+    for (int k = 0; k < ns; ++k) stage<R>(h, st[k]);
     for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_PARTIAL);
         launch_partial(lv[j], lv[j + 1], work_level<R>(h, j), h->stream);
@@ -659,6 +687,7 @@ void one_step(sww_handle* h, double dt, bool do_adapt) {
     if (do_adapt) adapt<R>(h, -1.0, -1.0);
     read_counts<R>(h);
     ck(cudaMemcpyAsync(h->h_dt, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
+    ck(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "err");
 }
 
 // Run one step through a captured graph (eager when tracing).
@@ -668,7 +697,7 @@ void run_step_t(sww_handle* h, double dt, bool do_adapt) {
         one_step<R>(h, dt, do_adapt);
         return;
     }
-    auto key = std::make_tuple(h->jtop, int(do_adapt), dt > 0 ? dt : -1.0);
+    auto key = std::make_tuple(h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, h->stage_blocks);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (h->graphs.size() >= 16) h->drop_graphs();
@@ -790,6 +819,18 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         h->red = h->alloc<unsigned long long>(4);
         h->lstat = h->alloc<unsigned long long>(4);
         ck(cudaMemset(h->lstat, 0, 4 * sizeof(unsigned long long)), "memset");
+        h->bar = h->alloc<unsigned>(STAGE_BAR_WORDS);
+        h->err = h->alloc<int>(1);
+        ck(cudaMemset(h->bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "memset");
+        ck(cudaMemset(h->err, 0, sizeof(int)), "memset");
+        ck(cudaMallocHost(&h->h_err, sizeof(int)), "cudaMallocHost");
+        *h->h_err = 0;
+        if (cfg->persistent >= 0 && cfg->jmax + 1 <= 12) {
+            int coop = 0;
+            ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "device attribute");
+            if (coop) h->stage_cap = fp32 ? stage_grid<float>(h->nsm) : stage_grid<double>(h->nsm);
+            h->stage_blocks = h->stage_cap;
+        }
         h->cnt = h->alloc<unsigned long long>(4);
         h->thr = h->alloc<double>(2);
         h->dt = h->alloc<double>(1);
@@ -959,14 +1000,14 @@ int sww_rhs(sww_handle* h) {
         by_prec(h, [&](auto r) {
             using R = decltype(r);
             Join jn(h);
-            trend<R>(h);
             RKStage none{0, 0, 0, 0, 0, 0, 0};
-            update<R>(h, none);
+            stage<R>(h, none);
+            ck(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "err");
             check_launch();
             return 0;
         });
         ck(cudaStreamSynchronize(h->stream), "rhs");
-        return SWW_OK;
+        return barrier_status(h);
     });
 }
 
@@ -982,6 +1023,7 @@ int sww_step(sww_handle* h, double dt, int nsteps, int do_adapt) {
                 check_launch();
             }
             ck(cudaStreamSynchronize(h->stream), "step");
+            if (int rc = barrier_status(h)) return rc;
             double d = *h->h_dt;
             if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
             h->t += d;
@@ -1004,18 +1046,31 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
     if (n == 0 || nsteps == 0) return SWW_OK;
     return guarded([&]() -> int {
         // every member's step is one graph launch on the member's own stream; the
-        // members advance in turn, each waiting only for its own previous step
+        // members advance in turn, each waiting only for its own previous step.
+        // Cooperative launches of different streams do not overlap on the GPU, so with
+        // more than one member the RK stages run as one launch per phase.
+        std::vector<unsigned> own(n);
         for (int i = 0; i < n; ++i) {
             sww_handle* h = hs[i];
+            own[i] = h->stage_blocks;
+            if (n > 1) h->stage_blocks = 0;
             ck(cudaEventRecord(h->ev_in, h->user), "join in");
             ck(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "join in");
         }
+        struct Restore {
+            sww_handle* const* hs;
+            std::vector<unsigned>& own;
+            ~Restore() {
+                for (size_t i = 0; i < own.size(); ++i) hs[i]->stage_blocks = own[i];
+            }
+        } restore{hs, own};
         auto launch = [&](sww_handle* h) {
             run_step(h, dt, do_adapt != 0);
             check_launch();
         };
         auto finish = [&](sww_handle* h) -> int {
             ck(cudaStreamSynchronize(h->stream), "step");
+            if (int rc = barrier_status(h)) return rc;
             double d = *h->h_dt;
             if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
             h->t += d;

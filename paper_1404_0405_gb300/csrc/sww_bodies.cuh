@@ -1,0 +1,266 @@
+// Device-side helpers shared by the kernel translation units: the work-list item
+// loop and the per-item bodies of the trend, the RK stage and the prolongation.
+// Included inside an anonymous namespace of each translation unit.
+#pragma once
+
+__device__ __forceinline__ int64_t gid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
+template <class R>
+__device__ __forceinline__ R esign(int32_t code) { return (code & 1) ? R(-1) : R(1); }
+
+template <class Lv>
+__device__ __forceinline__ int32_t ring_nbr(const Lv& L, int32_t code) {
+    int64_t e = code >> 1;
+    return (code & 1) ? L.en[e] : L.en[L.E + e];
+}
+
+template <class R>
+__device__ __forceinline__ R predict(const DevLevelT<R>& F, const R* __restrict__ uc, int64_t fe) {
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s += F.vw[k * F.E + fe] * uc[F.vst[k * F.E + fe]];
+    return s;
+}
+
+template <class R>
+__device__ __forceinline__ R height_detail(const DevLevelT<R>& F, int64_t x) {
+    R s = F.dh[x];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s -= F.ptw[k * F.N + x] * F.dh[F.par[k * F.N + x]];
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+    return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
+// Item kinds of a work-list entry, in slot order.
+constexpr int K_NODE = 1, K_EDGE = 2, K_TRI = 4, K_CEDGE = 8;
+
+template <int KINDS>
+__host__ __device__ constexpr int slots_of() {
+    return ((KINDS & K_NODE) ? 1 : 0) + ((KINDS & K_EDGE) ? 3 : 0) + ((KINDS & K_TRI) ? 2 : 0) + ((KINDS & K_CEDGE) ? 3 : 0);
+}
+
+// Visit the items of the entries of a work list, one thread per item:
+// body(L, kind, id, elem).  An entry covers slots x P threads (P = configured patch
+// area): one slot of nodes, three of edges (orientation 0, 1, 2), two of triangles
+// and three of the edges of the coarse element under an even element (id = the
+// orientation), as KINDS selects.  A pole entry yields the two pole nodes with
+// elem = -1.  Entries name their level in `lvs` (multi-level lists) or all belong
+// to `one` when lvs is null.
+template <int KINDS, class Lv, class Body>
+__device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& one,
+                                          const int32_t* __restrict__ list, const int32_t* __restrict__ count, int P,
+                                          Body body) {
+    constexpr int NS = slots_of<KINDS>();
+    const int64_t S = int64_t(NS) * P;
+    const int64_t n = int64_t(*count) * S;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t it = gid(); it < n; it += stride) {
+        int32_t ent = list[it / S];
+        int64_t local = it % S;
+        int slot = int(local / P);
+        int64_t idx = local % P;
+        const Lv& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
+        int64_t pat = ent & PATCH_MASK;
+        if (pat == L.npatch) {
+            if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
+            continue;
+        }
+        int64_t pp = L.p * L.p;
+        if (idx >= pp) continue;
+        int64_t el = pat * pp + idx;
+        if (KINDS & K_NODE) {
+            if (slot == 0) {
+                body(L, K_NODE, el, el);
+                continue;
+            }
+            slot -= 1;
+        }
+        if (KINDS & K_EDGE) {
+            if (slot < 3) {
+                body(L, K_EDGE, slot * L.nelem + el, el);
+                continue;
+            }
+            slot -= 3;
+        }
+        if (KINDS & K_TRI) {
+            if (slot < 2) {
+                body(L, K_TRI, slot * L.nelem + el, el);
+                continue;
+            }
+            slot -= 2;
+        }
+        if (KINDS & K_CEDGE) body(L, K_CEDGE, int64_t(slot), el);
+    }
+}
+
+// ---------------------------------------------------------------------------- trend bodies (Sec. 3.1)
+
+// potential vorticity q = (curl u + f)/h at a triangle (dual cell)
+template <class R>
+__device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
+    int32_t n0 = L.tn[t], n1 = L.tn[L.T + t], n2 = L.tn[2 * L.T + t];
+    int32_t c0 = L.te[t], c1 = L.te[L.T + t], c2 = L.te[2 * L.T + t];
+    if (!(L.nflag[n0] & AVAIL) || !(L.nflag[n1] & AVAIL) || !(L.nflag[n2] & AVAIL)) return;
+    if (!(L.eflag[c0 >> 1] & AVAIL) || !(L.eflag[c1 >> 1] & AVAIL) || !(L.eflag[c2 >> 1] & AVAIL)) return;
+    R circ = esign<R>(c0) * L.u[c0 >> 1] * L.d_e[c0 >> 1] + esign<R>(c1) * L.u[c1 >> 1] * L.d_e[c1 >> 1] +
+             esign<R>(c2) * L.u[c2 >> 1] * L.d_e[c2 >> 1];
+    R hv = L.kite[t] * (H + L.dh[n0]) + L.kite[L.T + t] * (H + L.dh[n1]) + L.kite[2 * L.T + t] * (H + L.dh[n2]);
+    R Av = L.A_v[t];
+    L.q[t] = (circ / Av + L.f_v[t]) / (hv / Av);
+}
+
+// thickness flux F = h_e u at an edge
+template <class R>
+__device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
+    if (!(L.eflag[e] & AVAIL)) return;
+    int32_t a = L.en[e], b = L.en[L.E + e];
+    if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
+    L.F[e] = R(0.5) * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
+}
+
+// divergence, kinetic energy and Bernoulli function at a node
+template <class R>
+__device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
+    if (!(L.nflag[v] & AVAIL)) return;
+    int dg = L.deg[v];
+    R div = R(0), ke = R(0);
+    for (int k = 0; k < dg; ++k) {
+        int32_t code = L.ring_e[k * L.N + v];
+        int64_t e = code >> 1;
+        if (!(L.eflag[e] & AVAIL)) return;
+        div += esign<R>(code) * L.F[e] * L.l_e[e];
+        R ue = L.u[e];
+        ke += R(0.25) * L.l_e[e] * L.d_e[e] * ue * ue;
+    }
+    R A = L.A_i[v];
+    L.c[v] = div / A;
+    L.B[v] = g * L.dh[v] + ke / A;
+}
+
+// energy-conserving Coriolis tendency +q F.n_left at a live edge (TRiSK)
+template <class R>
+__device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
+    if (!(L.eflag[e] & LIVE)) return;
+    R qe = R(0.5) * (L.q[L.et[e]] + L.q[L.et[L.E + e]]);
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+        int32_t e2 = L.cor_i[k * L.E + e];
+        R w = L.cor_w[k * L.E + e];
+        R q2 = R(0.5) * (L.q[L.et[e2]] + L.q[L.et[L.E + e2]]);
+        s += w * L.F[e2] * R(0.5) * (qe + q2);
+    }
+    L.Q[e] = s;
+}
+
+template <class R>
+__device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
+    if (!(L.nflag[v] & AVAIL)) return;
+    int dg = L.deg[v];
+    R div = R(0);
+    for (int k = 0; k < dg; ++k) {
+        int32_t code = L.ring_e[k * L.N + v];
+        int64_t e = code >> 1;
+        if (!(L.eflag[e] & AVAIL)) return;
+        div += esign<R>(code) * L.F[e] * L.l_e[e];
+    }
+    L.c[v] = div / L.A_i[v];
+}
+
+// trend and one Runge-Kutta stage at a live point (terms with a zero coefficient
+// are skipped, so stale storage never enters):
+//   y <- a*y0 + b*y + (cdt*dt)*k + (ddt*dt)*acc,   acc <- al*acc + be*k
+template <class R>
+__device__ __forceinline__ void rk_apply(const RKStage& st, R dt, R k, R* y, const R* y0, R* acc) {
+    R v = R(st.cdt) * dt * k;
+    if (st.a != 0.0) v += R(st.a) * *y0;
+    if (st.b != 0.0) v += R(st.b) * *y;
+    if (st.ddt != 0.0) v += R(st.ddt) * dt * *acc;
+    if (st.al != 0.0 || st.be != 0.0) *acc = (st.al != 0.0 ? R(st.al) * *acc : R(0)) + R(st.be) * k;
+    *y = v;
+}
+
+template <class R>
+__device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, const RKStage& st, R dt) {
+    if (!(L.nflag[v] & LIVE)) return;
+    R k = -L.c[v];
+    L.dht[v] = k;
+    if (st.apply) rk_apply(st, dt, k, &L.dh[v], &L.dh0[v], &L.dha[v]);
+}
+
+template <class R>
+__device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, const RKStage& st, R dt) {
+    if (!(L.eflag[e] & LIVE)) return;
+    R k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
+    L.ut[e] = k;
+    if (st.apply) rk_apply(st, dt, k, &L.u[e], &L.u0[e], &L.ua[e]);
+}
+
+// ---------------------------------------------------------------------------- prolongation (Eqs. 1-2)
+
+// ghost node of level F from level C (inverse transform with zero coefficients)
+template <class R>
+__device__ __forceinline__ void fill_node(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i) {
+    if (!(F.nflag[i] & GHOST)) return;
+    int32_t k = F.f2c[i];
+    if (k >= 0) {
+        F.dh[i] = C.dh[k];
+        return;
+    }
+    R s = R(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int32_t p = F.par[q * F.N + i];
+        R v = (F.nflag[p] & LIVE) ? F.dh[p] : C.dh[F.f2c[p]];
+        s += F.ptw[q * F.N + i] * v;
+    }
+    F.dh[i] = s;
+}
+
+template <class R>
+__device__ __forceinline__ void fill_edge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i) {
+    if (!(F.eflag[i] & GHOST)) return;
+    int kind = F.fe_kind[i];
+    R P = predict(F, C.u, i);
+    if (kind == 2) {
+        F.u[i] = P;
+        return;
+    }
+    int64_t E = F.fe_ce[i];
+    int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
+    R uc = C.u[E];
+    if (F.eflag[other] & LIVE) {
+        F.u[i] = R(2) * uc - F.u[other];
+    } else {
+        R Po = predict(F, C.u, other);
+        F.u[i] = P + R(0.5) * (R(2) * uc - P - Po);
+    }
+}
+
+
+#define ITEMS(KINDS, lvs, one, list, count, P) \
+    for_items<KINDS>(lvs, one, list, count, P, [&](const auto& L, int kind, int64_t id, int64_t el)
+
+// restriction from F = level j+1 to C = level j at one item of C (Sec. 3.1): B by
+// injection at covered nodes, flux by R_F on faces of covered nodes, Coriolis
+// tendency by R_u where both ends are covered
+template <class R>
+__device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLevelT<R>& F, int kind, int64_t id) {
+    if (kind == K_NODE) {
+        if (L.nflag[id] & COVERED) L.B[id] = F.B[L.c2f[id]];
+        return;
+    }
+    int64_t i = id;
+    bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
+    if (ca || cb) {
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
+#pragma unroll
+        for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
+        L.F[i] = s / L.l_e[i];
+    }
+    if (ca && cb) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
+}
