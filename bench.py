@@ -66,6 +66,7 @@ def parse():
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--err-steps", type=int, default=20)
     p.add_argument("--tau", type=float, default=0.5)
+    p.add_argument("--no-learned", action="store_true", help="chosen form without the learned proposal")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-jmax", type=int, default=6, help="finest level of the oracle sample")
     return p.parse_args()
@@ -313,7 +314,10 @@ def run_ours(a, rank, world):
     # chosen form: FP32, an ensemble of members in one concurrent step, learned proposal
     learned = None
     lstats = None
-    if a.form == "chosen":
+    if a.form == "chosen" and a.no_learned:
+        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)])
+        dtype = "f32"
+    elif a.form == "chosen":
         train_m = _members(sww, workloads, base, a, "fp32", [seed + 500 + k for k in range(2)])
         Xs, ys = zip(*[learn.collect(m, a.train_steps) for m in train_m])
         X, y = np.concatenate(Xs), np.concatenate(ys)

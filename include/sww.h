@@ -89,6 +89,8 @@ typedef struct {
                           the trend and the update, grid barriers between them); -1 one
                           launch per phase.  0 falls back to -1 where a cooperative
                           launch cannot run.                                           */
+    int mask;          /* 0: mask passes over candidate patches (near the active grid);
+                          1: dense passes over every point of the levels (same mask)    */
 } sww_config;
 
 typedef struct {

@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
     _fields_ = [("jmin", ctypes.c_int), ("jmax", ctypes.c_int), ("radius", ctypes.c_double),
                 ("omega", ctypes.c_double), ("g", ctypes.c_double), ("H", ctypes.c_double),
                 ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
-                ("blocks_per_sm", ctypes.c_int), ("precision", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("precision", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("mask", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -162,12 +163,14 @@ class Model:
     """One adapted grid Jmin..Jmax and its state on the GPU (sww_create)."""
 
     def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
-                 cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True):
+                 cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
+                 mask="lists"):
         """share: another Model whose grid and tables this one reuses (sww_create_shared)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
-                          blocks_per_sm, {"fp64": 0, "fp32": 1}[precision], 0 if persistent else -1)
+                          blocks_per_sm, {"fp64": 0, "fp32": 1}[precision], 0 if persistent else -1,
+                          {"lists": 0, "dense": 1}[mask])
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()
         if share is None:

@@ -29,6 +29,7 @@
 #include "sww_kernels.h"
 #include "sww_learn.h"
 #include "sww_stage.h"
+#include "sww_mask.h"
 
 using namespace sww;
 
@@ -116,7 +117,7 @@ struct Geometry {
             F.en = D.en, F.et = D.et, F.tn = D.tn, F.te = D.te, F.deg = D.deg, F.ring_e = D.ring_e, F.f2c = D.f2c;
             F.cor_i = D.cor_i, F.par = D.par, F.fe_kind = D.fe_kind, F.fe_ce = D.fe_ce, F.vst = D.vst;
             F.c2f = D.c2f, F.mid = D.mid, F.half = D.half, F.mk_i = D.mk_i, F.rf_fi = D.rf_fi, F.rf_ci = D.rf_ci;
-            F.ppar = D.ppar, F.pnbr = D.pnbr;
+            F.ppar = D.ppar, F.pnbr = D.pnbr, F.pchild = D.pchild;
             F.A_i64 = D.A_i64, F.d_e64 = D.d_e64, F.l_e64 = D.l_e64;
             auto cv = [&](const double* x, int64_t n) -> const float* {
                 if (!x) return nullptr;
@@ -169,6 +170,9 @@ struct sww_handle {
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
     int32_t *all_list = nullptr, *all_count = nullptr, *d_counts = nullptr, *sig_any = nullptr;
+    // candidate lists of the list-based mask (all levels)
+    int32_t *cand = nullptr, *cand_count = nullptr, *gcand = nullptr, *gcand_count = nullptr;
+    int64_t total_entries = 0;
     int32_t* h_counts = nullptr;    // pinned: per-level list sizes after each step
     double* h_dt = nullptr;         // pinned: time step of the last step
     int S = 64, jtop = 0, nsm = 152;
@@ -303,22 +307,28 @@ void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side
             f2c[L.nelem + 1] = int32_t(10 * cn * cn + 1);
         }
         D.f2c = G.up(f2c);
-        // patch graph: same-level neighbour patches (any node of one adjacent to a
-        // node of the other) and the coarse patch under each patch
+        // patch graph: same-level neighbour patches (a node of one within two hops of
+        // a node of the other, so that every patch around P within p hops is one),
+        // the coarse patch under each patch, and the fine patches over it
         const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
         auto patch_of = [&](int64_t v) { return v < L.nelem ? v / pp : L.npatch; };
-        std::vector<int32_t> nbr(NB * np1, -1), par(np1, -1);
+        std::vector<int32_t> nbr(NB * np1, -1), par(np1, -1), child(4 * np1, -1);
         std::vector<int> cnt(np1, 0);
+        auto add = [&](std::vector<int32_t>& tab, std::vector<int>& c, int cap, int64_t P, int64_t Q) {
+            for (int q = 0; q < c[P]; ++q)
+                if (tab[q * np1 + P] == Q) return;
+            if (c[P] >= cap) throw std::runtime_error("patch table overflow");
+            tab[c[P]++ * np1 + P] = int32_t(Q);
+        };
         for (int64_t v = 0; v < L.N; ++v) {
-            int64_t P = patch_of(v);
+            const int64_t P = patch_of(v);
             for (int k = 0; k < L.deg[v]; ++k) {
-                int64_t Q = patch_of(L.ring_n[k][v]);
-                if (Q == P) continue;
-                bool seen = false;
-                for (int q = 0; q < cnt[P]; ++q) seen = seen || nbr[q * np1 + P] == Q;
-                if (seen) continue;
-                if (cnt[P] >= NB) throw std::runtime_error("patch with more than NB neighbour patches");
-                nbr[cnt[P]++ * np1 + P] = int32_t(Q);
+                const int64_t w = L.ring_n[k][v];
+                if (patch_of(w) != P) add(nbr, cnt, NB, P, patch_of(w));
+                for (int k2 = 0; k2 < L.deg[w]; ++k2) {
+                    const int64_t Q = patch_of(L.ring_n[k2][w]);
+                    if (Q != P) add(nbr, cnt, NB, P, Q);
+                }
             }
         }
         if (fine_side) {
@@ -330,6 +340,15 @@ void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side
                 par[P] = int32_t(k < cnelem ? k / cpp : cnelem / cpp);
             }
         }
+        if (coarse_side) {
+            const int64_t fn = 2 * L.n, fp = std::min<int64_t>(G.patch, fn), fpp = fp * fp, fnelem = 10 * fn * fn;
+            std::vector<int> cc(np1, 0);
+            for (int64_t v = 0; v < L.N; ++v) {
+                const int64_t x = L.c2f[v];
+                add(child, cc, 4, patch_of(v), x < fnelem ? x / fpp : fnelem / fpp);
+            }
+        }
+        D.pchild = G.up(child);
         D.pnbr = G.up(nbr);
         D.ppar = G.up(par);
     }
@@ -376,6 +395,7 @@ void alloc_state(sww_handle* h, int j) {
     for (auto p : bN) *p = h->alloc<uint8_t>(N);
     D.eflag = h->alloc<uint8_t>(E);
     D.pflag = h->alloc<uint8_t>(D.npatch);
+    ck(cudaMemset(D.pflag, 0, D.npatch), "memset");
     D.pfeat = h->alloc<float>(NF * (D.npatch + 1));
     D.prop = h->alloc<uint8_t>(D.npatch + 1);
     D.prop_prev = h->alloc<uint8_t>(D.npatch + 1);
@@ -385,6 +405,16 @@ void alloc_state(sww_handle* h, int j) {
     ck(cudaMemset(D.pfeat, 0, NF * (D.npatch + 1) * sizeof(float)), "memset");
     D.patches = h->alloc<int32_t>(D.npatch + 1);
     D.npatches = h->alloc<int32_t>(1);
+    uint8_t** cf[] = {&D.zflag, &D.sflag, &D.cflag, &D.lflag, &D.gflag};
+    for (auto p : cf) {
+        *p = h->alloc<uint8_t>(D.npatch + 1);
+        ck(cudaMemset(*p, 0, D.npatch + 1), "memset");
+    }
+    int32_t** cl[] = {&D.cand, &D.ncand, &D.gcand, &D.ngcand};
+    for (auto p : cl) {
+        *p = h->alloc<int32_t>(D.npatch + 1);
+        ck(cudaMemset(*p, 0, (D.npatch + 1) * sizeof(int32_t)), "memset");
+    }
     for (auto p : dN) ck(cudaMemset(*p, 0, N * sizeof(R)), "memset");
     for (auto p : dE) ck(cudaMemset(*p, 0, E * sizeof(R)), "memset");
     ck(cudaMemset(D.q, 0, T * sizeof(R)), "memset");
@@ -620,7 +650,22 @@ void mask_and_inverse(sww_handle* h) {
         }
         const Span props = span_of(h, j0 + 1, h->cfg.jmax, [](const DevLevel& L) { return L.npatch + 1; });
         if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 0, h->sig_any, s);
-        launch_mask(a, s);
+        // the candidate lists need patches of at least 4 x 4 (one or two rings reach
+        // the five hops of the ghost band)
+        if (h->cfg.mask == 0 && h->cfg.patch >= 4) {
+            MaskListArgs<R> b{};
+            b.lvs = dlv<R>(h), b.host = lvl<R>(h).data(), b.grid_lv = h->grid_lv.data();
+            b.ja = j0, b.jb = j1, b.hops = GHOST_HOPS, b.rings = h->cfg.patch >= 8 ? 1 : 2, b.P = h->S;
+            b.grid = h->grid_all, b.max_entries = h->total_entries;
+            b.active = h->all_list, b.active_count = h->all_count, b.thr = h->thr, b.sig_any = h->sig_any;
+            b.patches = span_of(h, j0, j1, [](const DevLevel& L) { return L.npatch + 1; });
+            b.cand = h->cand, b.cand_count = h->cand_count, b.gcand = h->gcand, b.gcand_count = h->gcand_count;
+            b.lstat = h->lstat;
+            launch_mask_lists(b, s);
+            launch_patch_scan(dlv<R>(h), j0, j1, s);
+        } else {
+            launch_mask(a, s);
+        }
         if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 1, h->sig_any, s);
         launch_concat(dlv<R>(h), j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
@@ -762,6 +807,7 @@ int check_config(const sww_config* cfg) {
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32) return fail(SWW_E_ARG, "blocks_per_sm must be 0..32");
     if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
         return fail(SWW_E_ARG, "precision must be SWW_FP64 or SWW_FP32");
+    if (cfg->mask != 0 && cfg->mask != 1) return fail(SWW_E_ARG, "mask must be 0 (candidate lists) or 1 (dense)");
     return SWW_OK;
 }
 
@@ -809,6 +855,13 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         }
         h->all_list = h->alloc<int32_t>(total);
         h->all_count = h->alloc<int32_t>(1);
+        h->total_entries = total;
+        h->cand = h->alloc<int32_t>(total);
+        h->gcand = h->alloc<int32_t>(total);
+        h->cand_count = h->alloc<int32_t>(1);
+        h->gcand_count = h->alloc<int32_t>(1);
+        ck(cudaMemset(h->cand_count, 0, sizeof(int32_t)), "memset");
+        ck(cudaMemset(h->gcand_count, 0, sizeof(int32_t)), "memset");
         h->d_counts = h->alloc<int32_t>(cfg->jmax + 1);
         h->sig_any = h->alloc<int32_t>(cfg->jmax + 2);
         ck(cudaMemset(h->sig_any, 0, sizeof(int32_t) * (cfg->jmax + 2)), "memset");
@@ -926,6 +979,11 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
             for (int j = j1; j > j0; --j) launch_restrict_full(lv[j - 1], lv[j], s);
             MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
             launch_live_all(dlv<R>(h), a.nodes, a.edges, s);
+            // the list-based mask expects the band bytes zero away from its candidates
+            for (int j = j0; j <= j1; ++j) {
+                ck(cudaMemsetAsync(lv[j].band0, 0, lv[j].N, s), "memset band");
+                ck(cudaMemsetAsync(lv[j].band1, 0, lv[j].N, s), "memset band");
+            }
             if (j1 > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
             launch_patches_all(dlv<R>(h), a.patches, s);
             launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);

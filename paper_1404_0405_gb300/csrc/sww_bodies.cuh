@@ -264,3 +264,127 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
     }
     if (ca && cb) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
 }
+
+// ---------------------------------------------------------------------------- mask items (Sec. 2.3)
+
+// significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends of an
+// interior edge with |u~| >= eps_u; both ends and the midpoint of a coarse edge with
+// |u~_E| >= eps_u; only points live before the adaptation carry coefficients
+template <class R>
+__device__ __forceinline__ bool sig_node(const DevLevelT<R>& F, int64_t i, double eh) {
+    if (F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(double(F.hdet[i])) >= eh) {
+        F.sig[i] = 1;
+        return true;
+    }
+    return false;
+}
+
+template <class R>
+__device__ __forceinline__ bool sig_edge(const DevLevelT<R>& F, int64_t i, double eu) {
+    if (F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(double(F.ui[i])) >= eu) {
+        F.sig[F.en[i]] = 1;
+        F.sig[F.en[F.E + i]] = 1;
+        return true;
+    }
+    return false;
+}
+
+template <class R>
+__device__ __forceinline__ bool sig_cedge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i, double eu) {
+    const int32_t h0 = C.half[i], h1 = C.half[C.E + i];
+    if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(double(F.ue[i])) >= eu) {
+        F.sig[C.c2f[C.en[i]]] = 1;
+        F.sig[C.c2f[C.en[C.E + i]]] = 1;
+        F.sig[C.mid[i]] = 1;
+        return true;
+    }
+    return false;
+}
+
+// T = S + same-level neighbours of S + children of the coarser significance set; a
+// patch the learned proposal names joins T as a whole (the exact rules' own set is
+// recorded per patch for the proposal's statistics)
+template <class R>
+__device__ __forceinline__ void adjacent_node(const DevLevelT<R>& F, const DevLevelT<R>& C, bool children, int64_t x) {
+    const int dg = F.deg[x];
+    uint8_t t = F.sig[x];
+    for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
+    if (!t && children) {
+        const int32_t cx = F.f2c[x];
+        if (cx >= 0 && C.sig[cx]) t = 1;
+        for (int k = 0; k < dg && !t; ++k) {
+            const int32_t y = ring_nbr(F, F.ring_e[k * F.N + x]);
+            const int32_t cy = F.f2c[y];
+            if (cy >= 0 && C.sig[cy]) t = 1;
+        }
+    }
+    const int64_t P = x < F.nelem ? x / (F.p * F.p) : F.npatch;
+    if (t)
+        F.pexact[P] = 1;
+    else if (F.prop[P])
+        t = 1;
+    F.tmask[x] = t;
+}
+
+// graded closure at level F: coarse node of a live node of the finer level Fp, and
+// the prediction parents of every live odd node (only ever sets bytes to 1)
+template <class R>
+__device__ __forceinline__ void close_node(const DevLevelT<R>& F, const DevLevelT<R>& Fp, bool has_finer, int64_t x) {
+    uint8_t t = F.tmask[x];
+    if (has_finer && Fp.tmask[F.c2f[x]]) t = 1;
+    if (!t) return;
+    F.tmask[x] = 1;
+    if (F.f2c[x] < 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F.tmask[F.par[q * F.N + x]] = 1;
+    }
+}
+
+// live flag (every node when `all`, else the mask), remembering whether it was live
+template <class R>
+__device__ __forceinline__ uint8_t live_node(const DevLevelT<R>& L, int64_t i, bool all) {
+    const uint8_t lv = all ? 1 : L.tmask[i];
+    L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
+    L.band0[i] = lv;
+    return lv;
+}
+
+// an edge is live when an end node is
+template <class R>
+__device__ __forceinline__ void live_edge(const DevLevelT<R>& L, int64_t e) {
+    const uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
+    L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
+}
+
+// one neighbour hop of the ghost band: band1 <- dilate(band0) when `forward`,
+// band0 <- dilate(band1) otherwise
+template <class R>
+__device__ __forceinline__ void dilate_node(const DevLevelT<R>& L, int64_t x, bool forward) {
+    const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
+    uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
+    uint8_t t = in[x];
+    const int dg = L.deg[x];
+    for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
+    out[x] = t;
+}
+
+template <class R>
+__device__ __forceinline__ void ghost_node(const DevLevelT<R>& L, int64_t i, const uint8_t* band) {
+    if (!(L.nflag[i] & LIVE) && band[i]) L.nflag[i] |= GHOST;
+}
+
+template <class R>
+__device__ __forceinline__ void ghost_edge(const DevLevelT<R>& L, int64_t e, const uint8_t* band) {
+    if (!(L.eflag[e] & LIVE) && band[L.en[e]] && band[L.en[L.E + e]]) L.eflag[e] |= GHOST;
+}
+
+// covered coarse node: the fine node at the same place and all of M_k live
+template <class R>
+__device__ __forceinline__ void covered_node(const DevLevelT<R>& C, const DevLevelT<R>& F, int64_t k) {
+    if (!(F.nflag[C.c2f[k]] & LIVE)) return;
+    for (int q = 0; q < 12; ++q) {
+        const int32_t m = C.mk_i[q * C.N + k];
+        if (m >= 0 && !(F.nflag[m] & LIVE)) return;
+    }
+    C.nflag[k] |= COVERED;
+}

@@ -9,9 +9,9 @@ namespace sww {
 constexpr uint8_t LIVE = 1, GHOST = 2, COVERED = 4, WASLIVE = 8;
 constexpr uint8_t AVAIL = LIVE | GHOST;
 
-// Learned refinement proposal: NF features per patch, NH hidden units, NB
+// Learned refinement proposal: NF features per patch, NH hidden units; NB
 // same-level neighbour patches at most.
-constexpr int NF = 8, NH = 32, NB = 12;
+constexpr int NF = 8, NH = 32, NB = 24;
 constexpr int MLP_PARAMS = NF * NH + NH + NH + 1;   // W1[NF][NH], b1[NH], w2[NH], b2
 
 // Work-list entry: (level << LVL_SHIFT) | patch; patch == npatch stands for the two poles.
@@ -54,7 +54,8 @@ struct DevLevelT {
     const R *rf_fw, *rf_cw;
     // patch graph (index npatch is the two poles)
     const int32_t* ppar;           // [npatch+1] patch of level J-1 under each patch (-1 on the coarsest level)
-    const int32_t* pnbr;           // [NB*(npatch+1)] same-level neighbour patches, -1 padded
+    const int32_t* pnbr;           // [NB*(npatch+1)] patches with a node within two hops, -1 padded
+    const int32_t* pchild;         // [4*(npatch+1)] patches of level J+1 over each patch, -1 padded
     // state and work arrays
     R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
     R *F, *q, *B, *c, *Q;
@@ -67,6 +68,11 @@ struct DevLevelT {
     uint8_t* pexact;               // [npatch+1] patch holds a point of the exact rules' set
     int32_t* patches;              // [npatch + 1] active patch list (+ pole entry), level-tagged
     int32_t* npatches;             // [1]
+    // candidate patches of the list-based mask (index npatch: the two poles)
+    uint8_t *zflag, *sflag, *cflag, *lflag, *gflag;   // [npatch+1] seeds, significance, candidates,
+                                                      //   live nodes, ghost candidates
+    int32_t *cand, *ncand;         // [npatch + 1] candidates of the live set (level-tagged), [1]
+    int32_t *gcand, *ngcand;       // [npatch + 1] candidates of the ghost band, [1]
 };
 
 using DevLevel = DevLevelT<double>;

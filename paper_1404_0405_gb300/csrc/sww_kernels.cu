@@ -388,10 +388,8 @@ __global__ void k_restrict_full(DevLevelT<R> C, DevLevelT<R> F) {
     if (i < C.E) C.u[i] = R(0.5) * (F.u[C.half[i]] + F.u[C.half[C.E + i]]);
 }
 
-// significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends and the
-// midpoint of a coarse edge with |u~_E| >= eps_u; both ends of an interior edge with
-// |u~| >= eps_u; only points live before the adaptation carry coefficients.
-// sig_any[j] records whether level j holds a significant point.
+// Dense multi-level mask kernels (bodies in sww_bodies.cuh).  sig_any[j] records
+// whether level j holds a significant point.
 template <class R>
 __global__ void k_zero_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
     DENSE_EACH(sp, gid(), sig_any) { lvs[j].sig[i] = 0; });
@@ -400,141 +398,60 @@ __global__ void k_zero_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const 
 template <class R>
 __global__ void k_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const double* __restrict__ thr, int32_t* sig_any) {
     DENSE_EACH(sp, gid(), sig_any) {
-        bool any = false;
         const DevLevelT<R>& F = lvs[j];
         const DevLevelT<R>& C = lvs[j - 1];
-        double eh = thr[0], eu = thr[1];
-        if (i < F.N && F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(double(F.hdet[i])) >= eh) F.sig[i] = 1, any = true;
-        if (i < F.E && F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(double(F.ui[i])) >= eu) {
-            F.sig[F.en[i]] = 1;
-            F.sig[F.en[F.E + i]] = 1;
-            any = true;
-        }
-        if (i < C.E) {
-            int32_t h0 = C.half[i], h1 = C.half[C.E + i];
-            if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(double(F.ue[i])) >= eu) {
-                F.sig[C.c2f[C.en[i]]] = 1;
-                F.sig[C.c2f[C.en[C.E + i]]] = 1;
-                F.sig[C.mid[i]] = 1;
-                any = true;
-            }
-        }
+        bool any = false;
+        if (i < F.N) any |= sig_node(F, i, thr[0]);
+        if (i < F.E) any |= sig_edge(F, i, thr[1]);
+        if (i < C.E) any |= sig_cedge(F, C, i, thr[1]);
         if (any) sig_any[j] = 1;
     });
 }
 
-// T = S + same-level neighbours of S + children of the coarser significance set
 template <class R>
 __global__ void k_adjacent(const DevLevelT<R>* __restrict__ lvs, Span sp, int jmin, const int32_t* sig_any) {
-    DENSE_EACH(sp, gid(), sig_any) {
-        const int64_t x = i;
-        const DevLevelT<R>& F = lvs[j];
-        const DevLevelT<R>& C = lvs[j - 1];
-        bool children = j - 1 > jmin;
-        int dg = F.deg[x];
-        uint8_t t = F.sig[x];
-        for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
-        if (!t && children) {
-            int32_t cx = F.f2c[x];
-            if (cx >= 0 && C.sig[cx]) t = 1;
-            for (int k = 0; k < dg && !t; ++k) {
-                int32_t y = ring_nbr(F, F.ring_e[k * F.N + x]);
-                int32_t cy = F.f2c[y];
-                if (cy >= 0 && C.sig[cy]) t = 1;
-            }
-        }
-        // a patch the learned proposal names joins T as a whole (the exact rules' own
-        // set is recorded per patch for the proposal's statistics)
-        const int64_t P = x < F.nelem ? x / (F.p * F.p) : F.npatch;
-        if (t)
-            F.pexact[P] = 1;
-        else if (F.prop[P])
-            t = 1;
-        F.tmask[x] = t;
-    });
+    DENSE_EACH(sp, gid(), sig_any) { adjacent_node(lvs[j], lvs[j - 1], j - 1 > jmin, i); });
 }
 
-// graded closure at level F: coarse node of a live node of the finer level Fp, and the
-// prediction parents of every live odd node (only ever sets bytes to 1).  On a tail
-// level the fixed grid strides over the level.
+// On a tail level the fixed grid strides over the level.
 template <class R>
 __global__ void k_close(DevLevelT<R> F, DevLevelT<R> Fp, int has_finer, const int32_t* sig_any, int tail) {
     if (tail && !sig_any[F.J - 1]) return;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t x = gid(); x < F.N; x += stride) {
-        uint8_t t = F.tmask[x];
-        if (has_finer && Fp.tmask[F.c2f[x]]) t = 1;
-        if (!t) continue;
-        F.tmask[x] = 1;
-        if (F.f2c[x] < 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) F.tmask[F.par[q * F.N + x]] = 1;
-        }
-    }
+    for (int64_t x = gid(); x < F.N; x += stride) close_node(F, Fp, has_finer != 0, x);
 }
 
-// live flags (all of Jmin, else the mask), remembering which points were live
 template <class R>
 __global__ void k_live(const DevLevelT<R>* __restrict__ lvs, Span sp, int all_level, const int32_t* sig_any) {
-    DENSE_EACH(sp, gid(), sig_any) {
-        const DevLevelT<R>& L = lvs[j];
-        uint8_t lv = (all_level == -2 || j == all_level) ? 1 : L.tmask[i];
-        L.nflag[i] = uint8_t((lv ? LIVE : 0) | ((L.nflag[i] & LIVE) ? WASLIVE : 0));
-        L.band0[i] = lv;
-    });
+    DENSE_EACH(sp, gid(), sig_any) { live_node(lvs[j], i, all_level == -2 || j == all_level); });
 }
 
-// an edge is live when an end node is
 template <class R>
 __global__ void k_live_edges(const DevLevelT<R>* __restrict__ lvs, Span sp, const int32_t* sig_any) {
-    DENSE_EACH(sp, gid(), sig_any) {
-        const DevLevelT<R>& L = lvs[j];
-        const int64_t e = i;
-        uint8_t was = (L.eflag[e] & LIVE) ? WASLIVE : 0;
-        L.eflag[e] = uint8_t((((L.nflag[L.en[e]] | L.nflag[L.en[L.E + e]]) & LIVE) ? LIVE : 0) | was);
-    });
+    DENSE_EACH(sp, gid(), sig_any) { live_edge(lvs[j], i); });
 }
 
-// one neighbour hop of the ghost band on every level: band1 <- dilate(band0) when
-// `forward`, band0 <- dilate(band1) otherwise
 template <class R>
 __global__ void k_dilate(const DevLevelT<R>* __restrict__ lvs, Span sp, int forward, const int32_t* sig_any) {
-    DENSE_EACH(sp, gid(), sig_any) {
-        const DevLevelT<R>& L = lvs[j];
-        const int64_t x = i;
-        const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
-        uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
-        uint8_t t = in[x];
-        int dg = L.deg[x];
-        for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
-        out[x] = t;
-    });
+    DENSE_EACH(sp, gid(), sig_any) { dilate_node(lvs[j], i, forward != 0); });
 }
 
 template <class R>
 __global__ void k_ghost(const DevLevelT<R>* __restrict__ lvs, Span sp, int in_band1, const int32_t* sig_any) {
     DENSE_EACH(sp, gid(), sig_any) {
         const DevLevelT<R>& L = lvs[j];
-        const uint8_t* __restrict__ band = in_band1 ? L.band1 : L.band0;
-        if (i < L.N && !(L.nflag[i] & LIVE) && band[i]) L.nflag[i] |= GHOST;
-        if (i < L.E && !(L.eflag[i] & LIVE) && band[L.en[i]] && band[L.en[L.E + i]]) L.eflag[i] |= GHOST;
+        const uint8_t* band = in_band1 ? L.band1 : L.band0;
+        if (i < L.N) ghost_node(L, i, band);
+        if (i < L.E) ghost_edge(L, i, band);
     });
 }
 
-// covered coarse nodes: the fine node at the same place and all of M_k live
 template <class R>
 __global__ void k_covered(const DevLevelT<R>* __restrict__ lvs, Span sp) {
     int j;
     int64_t k;
     if (!locate(sp, gid(), j, k)) return;
-    const DevLevelT<R>& C = lvs[j];
-    const DevLevelT<R>& F = lvs[j + 1];
-    if (!(F.nflag[C.c2f[k]] & LIVE)) return;
-    for (int q = 0; q < 12; ++q) {
-        int32_t m = C.mk_i[q * C.N + k];
-        if (m >= 0 && !(F.nflag[m] & LIVE)) return;
-    }
-    C.nflag[k] |= COVERED;
+    covered_node(lvs[j], lvs[j + 1], k);
 }
 
 // patches holding any live or ghost node or edge (one block per patch)
@@ -754,6 +671,12 @@ void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream
 }
 
 template <class R>
+void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s) {
+    g_launches++;
+    k_patch_scan<R><<<unsigned(jb - ja + 1), 1024, 0, s>>>(lvs, ja, nullptr, -1);
+}
+
+template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
     g_launches++;
     k_concat<R><<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
@@ -806,6 +729,7 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
     template void launch_covered_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
     template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
     template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, cudaStream_t);         \
+    template void launch_patch_scan<R>(const DevLevelT<R>*, int, int, cudaStream_t);                         \
     template int sums_blocks<R>(const DevLevelT<R>&);                                                        \
     template void launch_sums<R>(const DevLevelT<R>&, double, double, double*, double*, cudaStream_t);       \
     template void launch_count<R>(const DevLevelT<R>&, unsigned long long*, cudaStream_t);

@@ -81,6 +81,8 @@ template <class R> void launch_covered_all(const DevLevelT<R>* lvs, const Span& 
 template <class R> void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream_t s);
 template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s);
+// ascending active-patch lists of levels ja..jb from the patch flags
+template <class R> void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s);
 template <class R> int sums_blocks(const DevLevelT<R>& L);
 template <class R>
 void launch_sums(const DevLevelT<R>& L, double H, double g, double* part, double* out, cudaStream_t s);

@@ -33,50 +33,55 @@ __device__ __forceinline__ float feat_log(double x) { return float(log2(1.0 + x)
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// Own features of a patch (one block of 64 threads per patch): log2(1 + max|h~|/eps_h)
-// over its live odd nodes, log2(1 + max|u~|/eps_u) over its live interior edges and
-// the pair coefficients of the coarse edges under its even nodes, and the fraction of
-// its nodes that are live.
+// Own features of a patch (one warp per patch): log2(1 + max|h~|/eps_h) over its
+// live odd nodes, log2(1 + max|u~|/eps_u) over its live interior edges and the pair
+// coefficients of the coarse edges under its even nodes, and the fraction of its
+// nodes that are live.  An inactive patch has no live point: all three are 0.
 template <class R>
 __global__ void k_feat_own(const DevLevelT<R>* __restrict__ lvs, Span sp, const double* __restrict__ thr) {
+    const int lane = threadIdx.x & 31;
     int j;
     int64_t P;
-    if (!lfind(sp, int64_t(blockIdx.x), j, P)) return;
+    if (!lfind(sp, lgid() >> 5, j, P)) return;
     const DevLevelT<R>& L = lvs[j];
-    const DevLevelT<R>& C = lvs[j - 1];
     const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
-    const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
-    double mh = 0, mu = 0;
-    int live = 0;
     const bool pole = P == L.npatch;
+    if (!pole && !L.pflag[P]) {
+        if (lane == 0) L.pfeat[0 * np1 + P] = 0.f, L.pfeat[1 * np1 + P] = 0.f, L.pfeat[6 * np1 + P] = 0.f;
+        return;
+    }
+    const DevLevelT<R>& C = lvs[j - 1];
+    R mh = R(0), mu = R(0);
+    int live = 0;
     const int64_t nn = pole ? 2 : pp;
-    for (int64_t l = threadIdx.x; l < nn; l += blockDim.x) {
+    for (int64_t l = lane; l < nn; l += 32) {
         const int64_t v = pole ? L.nelem + l : P * pp + l;
         const uint8_t f = L.nflag[v];
         live += (f & LIVE) ? 1 : 0;
-        if ((f & LIVE) && L.f2c[v] < 0) mh = fmax(mh, fabs(double(L.hdet[v])));
+        if ((f & LIVE) && L.f2c[v] < 0) mh = fmax(mh, fabs(L.hdet[v]));
         if (pole) continue;
         for (int o = 0; o < 3; ++o) {
             const int64_t e = o * L.nelem + v;
-            if ((L.eflag[e] & LIVE) && L.fe_kind[e] == 2) mu = fmax(mu, fabs(double(L.ui[e])));
+            if ((L.eflag[e] & LIVE) && L.fe_kind[e] == 2) mu = fmax(mu, fabs(L.ui[e]));
         }
         const int32_t ce = L.f2c[v];
         if (ce >= 0 && ce < C.nelem) {
             for (int o = 0; o < 3; ++o) {
                 const int64_t E = o * C.nelem + ce;
                 const int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-                if ((L.eflag[h0] | L.eflag[h1]) & LIVE) mu = fmax(mu, fabs(double(L.ue[E])));
+                if ((L.eflag[h0] | L.eflag[h1]) & LIVE) mu = fmax(mu, fabs(L.ue[E]));
             }
         }
     }
-    __shared__ double sh[2][64];
-    __shared__ int sl[64];
-    sh[0][threadIdx.x] = mh, sh[1][threadIdx.x] = mu, sl[threadIdx.x] = live;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 1; k < blockDim.x; ++k) mh = fmax(mh, sh[0][k]), mu = fmax(mu, sh[1][k]), live += sl[k];
-        L.pfeat[0 * np1 + P] = feat_log(mh / eh);
-        L.pfeat[1 * np1 + P] = feat_log(mu / eu);
+    for (int o = 16; o > 0; o >>= 1) {
+        mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+        mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+        live += __shfl_xor_sync(0xffffffffu, live, o);
+    }
+    if (lane == 0) {
+        const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
+        L.pfeat[0 * np1 + P] = feat_log(double(mh) / eh);
+        L.pfeat[1 * np1 + P] = feat_log(double(mu) / eu);
         L.pfeat[6 * np1 + P] = float(live) / float(nn);
     }
 }
@@ -123,7 +128,10 @@ __device__ __forceinline__ float mlp_logit(const MlpWeights& w, const float* x, 
 }
 
 template <class R>
-__global__ void k_propose(const DevLevelT<R>* __restrict__ lvs, Span sp, MlpWeights w, float logit_tau) {
+__global__ void k_propose(const DevLevelT<R>* __restrict__ lvs, Span sp, MlpWeights wp, float logit_tau) {
+    __shared__ MlpWeights w;   // staged once per block (indexed loads from the parameter would go to local memory)
+    if (threadIdx.x == 0) w = wp;
+    __syncthreads();
     int j;
     int64_t P;
     if (!lfind(sp, lgid(), j, P)) return;
@@ -283,7 +291,7 @@ void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const doubl
     const int64_t n = patches_f.off[patches_f.jb + 1 - patches_f.ja];
     if (n <= 0) return;
     count_launch(2);
-    k_feat_own<R><<<unsigned(n), 64, 0, s>>>(lvs, patches_f, thr);
+    k_feat_own<R><<<blocks_for(n * 32, 256), 256, 0, s>>>(lvs, patches_f, thr);
     k_feat_ctx<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, jmin, jmax);
 }
 
