@@ -206,17 +206,42 @@ def combine_ranks(seconds, cells, device, world):
 # halves every term (its state and stencil weights are FP32).
 STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
 
+# DRAM bytes (read + write) per launch of k_restrict, mean over the 24 launches of
+# two steps of one ncu capture of the same jet at Jmin=4..Jmax=8 (the same active
+# set and launches as Jmax=9; profiles/k_restrict_jet_J4-8_fp32.md); remove an
+# entry when the kernel changes.
+RESTRICT_TRAFFIC_PER_LAUNCH = {"fp32": 1822954.7}
+
+# Algorithmic bytes of one launch of the restriction kernel (k_restrict, level j from
+# level j+1, Sec. 3.1 and 4.2-4.3) with R-byte reals, from the coarse level's flags:
+# every item of the level's active patches reads its flags (node 1 B, edge 8 B of end
+# ids + 2 B of flags); a covered node injects B (c2f id 4 B, B read and write 2R); an
+# edge with a covered end applies R_F (12 fine and 11 coarse weights and ids, the 23
+# values they gather, the face length and the flux written: 23(4 + 2R) + 2R); an edge
+# with both ends covered averages q F^perp over its halves (ids 8 B, 3R).
+def restrict_launch_bytes(sww, m, j, edges, R):
+    N, E, T, npatch = m.sizes(j)
+    pp = (E // 3) // npatch
+    act = len(m.patches(j))
+    cov = (m.get(j, sww.NODE_FLAGS) & 4) > 0
+    e1 = cov[edges[:, 0]] | cov[edges[:, 1]]
+    e2 = cov[edges[:, 0]] & cov[edges[:, 1]]
+    items_n, items_e = act * pp + 2, 3 * act * pp
+    return (items_n * 1 + int(cov.sum()) * (4 + 2 * R) + items_e * 10 + int(e1.sum()) * (23 * (4 + 2 * R) + 2 * R)
+            + int(e2.sum()) * (8 + 3 * R))
+
 
 def _live(m):
     return sum(m.stats()["live_nodes"].values())
 
 
-def _members(sww, workloads, base, a, precision, seeds, learned=None):
+def _members(sww, workloads, base, a, precision, seeds, learned=None, persistent=True):
     ms = []
     xyz, en = base.grid(a.jmax)
     mid, tan = edge_geometry(xyz, en)
     for sd in seeds:
-        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision, share=base)
+        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision, share=base,
+                      persistent=persistent)
         dh, u = workloads.Workload("jet", seed=sd).fields(xyz, mid, tan)
         m.set_state(dh, u)
         m.adapt()
@@ -315,7 +340,7 @@ def run_ours(a, rank, world):
     learned = None
     lstats = None
     if a.form == "chosen" and a.no_learned:
-        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)])
+        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], persistent=False)
         dtype = "f32"
     elif a.form == "chosen":
         train_m = _members(sww, workloads, base, a, "fp32", [seed + 500 + k for k in range(2)])
@@ -323,7 +348,8 @@ def run_ours(a, rank, world):
         X, y = np.concatenate(Xs), np.concatenate(ys)
         learned, losses = learn.train(X, y, epochs=300)
         del train_m
-        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], learned)
+        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], learned,
+                      persistent=False)
         dtype = "f32"
     else:
         ms, dtype = plain_m, "f64"
@@ -352,18 +378,24 @@ def run_ours(a, rank, world):
         lstats["train_samples"] = int(len(y))
         lstats["train_loss"] = [float(losses[0]), float(losses[-1])]
 
-    # live per-launch timing of the dominant kernel (the persistent RK stage)
+    # live per-launch timing of the dominant kernel of the timed steps: the
+    # restriction k_restrict (members step their RK stages as one launch per phase),
+    # on member 0 stepping alone in eager mode with CUDA events per launch
     m0 = ms[0]
     prec = "fp32" if dtype == "f32" else "fp64"
-    m0.profile(["stage"])
-    cells_prof = 0.0
+    R = 4 if prec == "fp32" else 8
+    edges = {j: base.grid(j)[1] for j in range(a.jmin, a.jmax)}
+    m0.profile(["restrict"])
+    rbytes = 0
     for _ in range(a.steps):
         flush.zero_()
-        cells_prof += _live(m0)
+        act = m0.stats()["active_patches"]
+        top = max(j for j in range(a.jmin, a.jmax + 1) if act.get(j, 0) > 0)
+        rbytes += 4 * sum(restrict_launch_bytes(sww, m0, j, edges[j], R) for j in range(a.jmin, top))
         m0.step(-1.0, 1, adapt=True)
     prof = m0.profile_read()
     m0.profile([])
-    st_ms, st_n = prof["stage"]
+    r_ms, r_n = prof["restrict"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -371,13 +403,29 @@ def run_ours(a, rank, world):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     roofline = None
-    if st_n > 0:
-        stage_bytes = STAGE_BYTES_PER_CELL[prec] * cells_prof * 4   # four stages per step
-        achieved = stage_bytes / (st_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_stage", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)", "traffic": None,
-                    "avg_launch_us": st_ms * 1e3 / st_n, "launches": st_n,
-                    "bytes_per_live_cell": STAGE_BYTES_PER_CELL[prec]}
+    if r_n > 0:
+        achieved = rbytes / (r_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_restrict", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)",
+                    "traffic": RESTRICT_TRAFFIC_PER_LAUNCH.get(prec) if a.jmax >= 8 and a.eps == 1e-2 else None,
+                    "avg_launch_us": r_ms * 1e3 / r_n, "launches": r_n,
+                    "algorithmic_bytes_per_launch": rbytes / r_n}
+    # the persistent RK stage of the plain form's single member (fused trend + update)
+    pm = plain_m[0]
+    pm.profile(["stage"])
+    pcells = 0.0
+    for _ in range(a.plain_steps):
+        flush.zero_()
+        pcells += _live(pm)
+        pm.step(-1.0, 1, adapt=True)
+    sprof = pm.profile_read()["stage"]
+    pm.profile([])
+    stage_roof = None
+    if sprof[1] > 0:
+        ach = STAGE_BYTES_PER_CELL["fp64"] * pcells * 4 / (sprof[0] / 1e3) / 1e9
+        stage_roof = {"kernel": "k_stage (plain form, FP64)", "achieved": ach, "peak": peak, "unit": "GB/s",
+                      "frac": ach / peak, "avg_launch_us": sprof[0] * 1e3 / sprof[1],
+                      "bytes_per_live_cell": STAGE_BYTES_PER_CELL["fp64"]}
 
     # equal error: chosen vs plain against a non-adaptive run of the same workload
     err = _equal_error(sww, workloads, base, a, learned, seed, a.err_steps) if a.err_steps > 0 else None
@@ -418,7 +466,7 @@ def run_ours(a, rank, world):
                            "setup_s": setup_s},
                 "plain": plain, "chosen_vs_plain": value / plain["value"], "equal_error": err,
                 "learned_proposal": lstats, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roofline}
+                "roofline": roofline, "roofline_persistent_stage": stage_roof}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -191,9 +191,9 @@ int sww_stats_get(sww_handle* h, sww_stats* st);
 enum {
     SWW_K_PV = 0,        /* potential vorticity at triangles                         */
     SWW_K_FLUX = 1,      /* thickness flux at edges                                  */
-    SWW_K_NODE = 2,      /* divergence, kinetic energy, Bernoulli at nodes           */
+    SWW_K_NODE = 2,      /* divergence of the restricted fluxes at coarse nodes      */
     SWW_K_CORIOLIS = 3,  /* energy-conserving q F^perp at live edges                 */
-    SWW_K_RESTRICT = 4,  /* restriction of B, F, q F^perp and the coarse divergence  */
+    SWW_K_RESTRICT = 4,  /* restriction of B, F and q F^perp                         */
     SWW_K_UPDATE = 5,    /* trends and Runge-Kutta stage combination                 */
     SWW_K_FILL = 6,      /* ghost prolongation                                       */
     SWW_K_PARTIAL = 7,   /* partial height transform                                 */

@@ -523,8 +523,8 @@ void trend(sww_handle* h) {
     { Trace t(h, SWW_K_PV); launch_pv_flux(W, h->cfg.H, s); }
     { Trace t(h, SWW_K_CORIOLIS); launch_node_coriolis(W, h->cfg.g, s); }
     for (int j = h->jtop - 1; j >= j0; --j) {
-        Trace t(h, SWW_K_RESTRICT);
-        launch_restrict(lv[j], lv[j + 1], work_level<R>(h, j), s);
+        { Trace t(h, SWW_K_RESTRICT); launch_restrict(lv[j], lv[j + 1], work_level<R>(h, j), s); }
+        { Trace t(h, SWW_K_NODE); launch_div(lv[j], work_level<R>(h, j), s); }
     }
 }
 

@@ -578,6 +578,9 @@ void launch_fill(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W
 template <class R>
 void launch_restrict(const DevLevelT<R>& C, const DevLevelT<R>& F, const WorkT<R>& W, cudaStream_t s) {
     LIST(k_restrict<R>, C, F, W.list, W.count, W.S);
+}
+template <class R>
+void launch_div(const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s) {
     LIST(k_div<R>, C, W.list, W.count, W.S);
 }
 template <class R>
@@ -718,6 +721,7 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
     template void launch_save_base<R>(const WorkT<R>&, cudaStream_t);                                        \
     template void launch_fill<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t);   \
     template void launch_restrict<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
+    template void launch_div<R>(const DevLevelT<R>&, const WorkT<R>&, cudaStream_t);                          \
     template void launch_partial<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
     template void launch_details<R>(const WorkT<R>&, int, cudaStream_t);                                     \
     template void launch_inverse<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \

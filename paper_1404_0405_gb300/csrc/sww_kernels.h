@@ -61,7 +61,10 @@ template <class R> void launch_node_coriolis(const WorkT<R>& W, double g, cudaSt
 template <class R> void launch_update(const WorkT<R>& W, const RKStage& st, const double* dt, cudaStream_t s);
 template <class R> void launch_save_base(const WorkT<R>& W, cudaStream_t s);
 template <class R> void launch_fill(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s);
+// restriction of B, F, q F^perp from level j+1 (F) to level j (C); then the
+// divergence of the restricted fluxes at C's nodes
 template <class R> void launch_restrict(const DevLevelT<R>& C, const DevLevelT<R>& F, const WorkT<R>& W, cudaStream_t s);
+template <class R> void launch_div(const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s);
 template <class R> void launch_partial(const DevLevelT<R>& C, const DevLevelT<R>& F, const WorkT<R>& W, cudaStream_t s);
 template <class R> void launch_details(const WorkT<R>& W, int jmin, cudaStream_t s);
 template <class R> void launch_inverse(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s);
