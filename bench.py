@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--err-steps", type=int, default=20)
     p.add_argument("--tau", type=float, default=0.5)
     p.add_argument("--no-learned", action="store_true", help="chosen form without the learned proposal")
+    p.add_argument("--no-tune", action="store_true", help="chosen form without the autotuner (patch, 4 blocks/SM)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-jmax", type=int, default=6, help="finest level of the oracle sample")
     return p.parse_args()
@@ -235,13 +236,13 @@ def _live(m):
     return sum(m.stats()["live_nodes"].values())
 
 
-def _members(sww, workloads, base, a, precision, seeds, learned=None, persistent=True):
+def _members(sww, workloads, base, a, precision, seeds, learned=None, persistent=True, patch=None, bps=0):
     ms = []
     xyz, en = base.grid(a.jmax)
     mid, tan = edge_geometry(xyz, en)
     for sd in seeds:
-        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision, share=base,
-                      persistent=persistent)
+        m = sww.Model(a.jmin, a.jmax, patch=patch or a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision,
+                      share=base, persistent=persistent, blocks_per_sm=bps)
         dh, u = workloads.Workload("jet", seed=sd).fields(xyz, mid, tan)
         m.set_state(dh, u)
         m.adapt()
@@ -270,18 +271,27 @@ def _timed(sww, ms, steps, flush, stream):
     return times, cells
 
 
-def _equal_error(sww, workloads, base, a, learned, seed, steps):
+def _equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, steps):
     """Relative l2 error of the Jmin depth after `steps` steps of a fixed dt, for the
     plain form (FP64, exact mask) and the chosen form (FP32, learned proposal),
     against a non-adaptive FP64 run (eps = 0: every point live) substepped at its own
     CFL limit to the same final time."""
     import numpy as np
-    xyz, en = base.grid(a.jmax)
-    mid, tan = edge_geometry(xyz, en)
-    dh, u = workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)
+
+    def state(b):
+        xyz, en = b.grid(a.jmax)
+        mid, tan = edge_geometry(xyz, en)
+        return workloads.Workload("jet", seed=seed).fields(xyz, mid, tan)
+
+    s_plain = state(base)
+    s_chosen = s_plain if cbase is base else state(cbase)
 
     def make(precision, eps, prop=None):
-        m = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=eps, rk="rk4", cfl=0.8, precision=precision, share=base)
+        chosen = precision == "fp32"
+        b = cbase if chosen else base
+        dh, u = s_chosen if chosen else s_plain
+        m = sww.Model(a.jmin, a.jmax, patch=cpatch if chosen else a.patch, eps=eps, rk="rk4", cfl=0.8,
+                      precision=precision, share=b, blocks_per_sm=cbps if chosen else 0)
         m.set_state(dh, u)
         if eps > 0:
             m.adapt()
@@ -336,20 +346,37 @@ def run_ours(a, rank, world):
     plain = {"value": plain_c / plain_t, "ms_per_step": 1e3 * plain_t / len(pt), "members": 1, "dtype": "f64",
              "active_cells_per_step": plain_c / len(pc) / max(world, 1)}
 
-    # chosen form: FP32, an ensemble of members in one concurrent step, learned proposal
+    # chosen form: FP32, an ensemble of members in one concurrent step, learned
+    # proposal; patch side and work-list grid from the autotuner
     learned = None
     lstats = None
+    tuned = None
+    cbase, cpatch, cbps = base, a.patch, 0
+    if a.form == "chosen" and not a.no_tune:
+        from paper_1404_0405_gb300 import autotune
+
+        def fields_of(xyz, en):
+            mid, tan = edge_geometry(xyz, en)
+            return [workloads.Workload("jet", seed=seed + 900 + k).fields(xyz, mid, tan) for k in range(4)]
+
+        best, trials = autotune.tune(a.jmin, a.jmax, a.eps, fields_of, members=4, key_extra="jet")
+        tuned = {"best": best, "trials": trials}
+        cpatch, cbps = best["patch"], best["blocks_per_sm"]
+        if cpatch != a.patch:
+            cbase = sww.Model(a.jmin, a.jmax, patch=cpatch, eps=a.eps, rk="rk4", cfl=0.8)
     if a.form == "chosen" and a.no_learned:
-        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], persistent=False)
+        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], persistent=False,
+                      patch=cpatch, bps=cbps)
         dtype = "f32"
     elif a.form == "chosen":
-        train_m = _members(sww, workloads, base, a, "fp32", [seed + 500 + k for k in range(2)])
+        train_m = _members(sww, workloads, cbase, a, "fp32", [seed + 500 + k for k in range(2)], patch=cpatch,
+                           bps=cbps)
         Xs, ys = zip(*[learn.collect(m, a.train_steps) for m in train_m])
         X, y = np.concatenate(Xs), np.concatenate(ys)
         learned, losses = learn.train(X, y, epochs=300)
         del train_m
-        ms = _members(sww, workloads, base, a, "fp32", [seed + k for k in range(a.members)], learned,
-                      persistent=False)
+        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], learned,
+                      persistent=False, patch=cpatch, bps=cbps)
         dtype = "f32"
     else:
         ms, dtype = plain_m, "f64"
@@ -384,7 +411,7 @@ def run_ours(a, rank, world):
     m0 = ms[0]
     prec = "fp32" if dtype == "f32" else "fp64"
     R = 4 if prec == "fp32" else 8
-    edges = {j: base.grid(j)[1] for j in range(a.jmin, a.jmax)}
+    edges = {j: cbase.grid(j)[1] for j in range(a.jmin, a.jmax)}
     m0.profile(["restrict"])
     rbytes = 0
     for _ in range(a.steps):
@@ -428,10 +455,11 @@ def run_ours(a, rank, world):
                       "bytes_per_live_cell": STAGE_BYTES_PER_CELL["fp64"]}
 
     # equal error: chosen vs plain against a non-adaptive run of the same workload
-    err = _equal_error(sww, workloads, base, a, learned, seed, a.err_steps) if a.err_steps > 0 else None
+    err = (_equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, a.err_steps)
+           if a.err_steps > 0 else None)
 
     # end to end through the public API from pinned host buffers
-    xyz, en = base.grid(a.jmax)
+    xyz, en = cbase.grid(a.jmax)
     mid, tan = edge_geometry(xyz, en)
     host = []
     for k, m in enumerate(ms):
@@ -460,7 +488,8 @@ def run_ours(a, rank, world):
                 "warmup": a.warmup, "ms_per_step": 1e3 * total_all / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
                 "config": {"workload": workload_name(a), "form": a.form, "members": len(ms) * max(world, 1),
-                           "l2": "flushed between steps (512 MiB write)", "patch": a.patch,
+                           "l2": "flushed between steps (512 MiB write)", "patch": cpatch,
+                           "blocks_per_sm": cbps or 4, "autotune": tuned,
                            "active_cells_per_step": cells_all / a.steps / max(world, 1) / len(ms),
                            "compression": (10 * 4 ** a.jmax + 2) / (cells_all / a.steps / max(world, 1) / len(ms)),
                            "setup_s": setup_s},

@@ -100,3 +100,21 @@ def test_shared_grid_rules():
     del base                                          # the tables outlive the first handle
     xyz, _ = m.grid(2)
     assert np.allclose(np.linalg.norm(xyz, axis=1), 1.0)
+
+
+def test_autotuner_picks_the_fastest_trial(tmp_path, monkeypatch):
+    import paper_1404_0405_gb300 as sww
+    from paper_1404_0405_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+
+    def fields_of(xyz, en):
+        mid, tan = lib_edge_geometry(xyz, en)
+        return [workloads.Workload("jet", seed=s).fields(xyz, mid, tan) for s in (1, 2)]
+
+    best, trials = autotune.tune(2, 4, 1e-2, fields_of, members=2, patches=(4, 8), blocks=(2, 4), steps=2,
+                                 warmup=1, key_extra="test")
+    assert len(trials) == 4
+    assert best == max(trials, key=lambda t: t["rate"])
+    assert all(t["rate"] > 0 for t in trials)
+    again, _ = autotune.tune(2, 4, 1e-2, fields_of, members=2, patches=(4, 8), blocks=(2, 4), key_extra="test")
+    assert again == best                              # cached
