@@ -85,10 +85,13 @@ typedef struct {
                           the FP64 tables; thresholds, time step and the compensated
                           mass/energy sums in FP64 on the FP32 values.  The ABI's
                           double arrays are converted at the boundary.                */
-    int persistent;    /* RK stages: 0 or 1 one cooperative launch per stage (all phases of
-                          the trend and the update, grid barriers between them); -1 one
-                          launch per phase.  0 falls back to -1 where a cooperative
-                          launch cannot run.                                           */
+    int persistent;    /* RK stages.  0: one cooperative launch per stage (all phases of
+                          the trend and the update, grid barriers between them) for a
+                          handle stepping alone, one launch per phase inside
+                          sww_step_ensemble (the members' steps then overlap); 1: also
+                          one cooperative launch per stage over all ensemble members;
+                          -1: one launch per phase always.  Falls back to -1 where a
+                          cooperative launch cannot run.                               */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
 } sww_config;
@@ -168,7 +171,10 @@ int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
  * as sww_step alone would advance it).  Every member's step runs on the member's
  * own stream, so the members' kernels overlap on the GPU; each member waits only
  * for its own previous step.  With more than one member the RK stages run as one
- * launch per phase (cooperative launches of different streams do not overlap).  On entry each member's work is ordered after its
+ * launch per phase (cooperative launches of different streams do not overlap),
+ * unless every member has persistent = 1 and they share precision, Jmin, patch,
+ * H, g and scheme: then each RK stage of all members is one cooperative launch
+ * between the members' other work (all members synchronise at every stage).  On entry each member's work is ordered after its
  * caller stream, and on return each caller stream waits for its member.
  * Returns the first error; members then stand at different step counts
  * (sww_stats_get tells which). */

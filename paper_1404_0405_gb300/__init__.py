@@ -165,11 +165,14 @@ class Model:
     def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
                  cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
                  mask="lists"):
-        """share: another Model whose grid and tables this one reuses (sww_create_shared)."""
+        """share: another Model whose grid and tables this one reuses (sww_create_shared).
+        persistent: True/"auto", "always" (also batched over ensemble members) or
+        False/"never" (see sww_config.persistent)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
-                          blocks_per_sm, {"fp64": 0, "fp32": 1}[precision], 0 if persistent else -1,
+                          blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
+                          {True: 0, "auto": 0, "always": 1, False: -1, "never": -1}[persistent],
                           {"lists": 0, "dense": 1}[mask])
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()

@@ -163,6 +163,16 @@ struct sww_handle {
     // persistent RK stages: blocks of the cooperative launch (0: one launch per phase),
     // barrier state and the error flag of a timed-out barrier (device and pinned copy)
     unsigned stage_blocks = 0, stage_cap = 0;
+    // buffers of ensemble steps led by this handle (allocated on first use)
+    struct {
+        uint8_t* refs = nullptr;    // device MemberRef array
+        uint8_t* h_refs = nullptr;  // pinned staging of the refs
+        unsigned* bar = nullptr;
+        int* err = nullptr;
+        int* h_err = nullptr;
+        cudaEvent_t ev = nullptr;
+        unsigned grid = 0;
+    } ens;
     unsigned* bar = nullptr;
     int* err = nullptr;
     int* h_err = nullptr;
@@ -181,8 +191,8 @@ struct sww_handle {
     double t = 0, last_dt = 0;
     int64_t steps = 0;
     bool has_state = false;
-    // captured steps: (top level, adapt, dt, stage blocks) -> graph and its kernel count
-    std::map<std::tuple<int, int, double, unsigned>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+    // captured steps: (part, top level, adapt, dt, stage blocks) -> graph and its kernel count
+    std::map<std::tuple<int, int, int, double, unsigned>, std::pair<cudaGraphExec_t, int64_t>> graphs;
     // tracing: per-class event pairs
     uint32_t prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -219,6 +229,9 @@ struct sww_handle {
         if (ev_out) cudaEventDestroy(ev_out);
         if (h_counts) cudaFreeHost(h_counts);
         if (h_err) cudaFreeHost(h_err);
+        if (ens.h_refs) cudaFreeHost(ens.h_refs);
+        if (ens.h_err) cudaFreeHost(ens.h_err);
+        if (ens.ev) cudaEventDestroy(ens.ev);
         if (h_dt) cudaFreeHost(h_dt);
         for (void* p : allocs) cudaFree(p);
         if (stream) cudaStreamDestroy(stream);
@@ -709,21 +722,28 @@ const RKStage* stages(int rk, int& n) {
 }
 
 // One RK step with its partial transform and (optionally) adaptation; ends with the
-// device-to-host copies of the time step and the list sizes.
+// device-to-host copies of the time step and the list sizes.  part 1 is what comes
+// before the RK stages (time step, RK base), part 2 what follows them; part 0 is the
+// whole step.
 template <class R>
-void one_step(sww_handle* h, double dt, bool do_adapt) {
+void one_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     const int j0 = h->cfg.jmin;
     auto& lv = lvl<R>(h);
-    if (dt > 0) {
-        count_launch(1);
-        k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
-    } else {
-        compute_dt<R>(h);
+    if (part != 2) {
+        if (dt > 0) {
+            count_launch(1);
+            k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
+        } else {
+            compute_dt<R>(h);
+        }
+        { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all<R>(h), h->stream); }
     }
-    { Trace t(h, SWW_K_UPDATE); launch_save_base(work_all<R>(h), h->stream); }
-    int ns;
-    const RKStage* st = stages(h->cfg.rk, ns);
-    for (int k = 0; k < ns; ++k) stage<R>(h, st[k]);
+    if (part == 0) {
+        int ns;
+        const RKStage* st = stages(h->cfg.rk, ns);
+        for (int k = 0; k < ns; ++k) stage<R>(h, st[k]);
+    }
+    if (part == 1) return;
     for (int j = h->jtop - 1; j >= j0; --j) {
         Trace t(h, SWW_K_PARTIAL);
         launch_partial(lv[j], lv[j + 1], work_level<R>(h, j), h->stream);
@@ -735,21 +755,21 @@ void one_step(sww_handle* h, double dt, bool do_adapt) {
     ck(cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "err");
 }
 
-// Run one step through a captured graph (eager when tracing).
+// Run one step (or part of one) through a captured graph (eager when tracing).
 template <class R>
-void run_step_t(sww_handle* h, double dt, bool do_adapt) {
+void run_step_t(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     if (h->prof_mask) {
-        one_step<R>(h, dt, do_adapt);
+        one_step<R>(h, dt, do_adapt, part);
         return;
     }
-    auto key = std::make_tuple(h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, h->stage_blocks);
+    auto key = std::make_tuple(part, h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, h->stage_blocks);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
-        if (h->graphs.size() >= 16) h->drop_graphs();
+        if (h->graphs.size() >= 24) h->drop_graphs();
         int64_t before = kernel_launches();
         ck(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         try {
-            one_step<R>(h, dt, do_adapt);
+            one_step<R>(h, dt, do_adapt, part);
         } catch (...) {
             cudaGraph_t g = nullptr;
             cudaStreamEndCapture(h->stream, &g);
@@ -770,11 +790,55 @@ void run_step_t(sww_handle* h, double dt, bool do_adapt) {
     count_launch(it->second.second);
 }
 
-void run_step(sww_handle* h, double dt, bool do_adapt) {
+void run_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     by_prec(h, [&](auto r) {
-        run_step_t<decltype(r)>(h, dt, do_adapt);
+        run_step_t<decltype(r)>(h, dt, do_adapt, part);
         return 0;
     });
+}
+
+// The RK stages of every member of an ensemble as one persistent launch per stage
+// (k_stage_batch) on the first member's stream, after every member's part 1 and
+// before its part 2.
+template <class R>
+void ensemble_stages(sww_handle* const* hs, int n) {
+    sww_handle* lead = hs[0];
+    auto& E = lead->ens;
+    if (!E.refs) {
+        E.refs = lead->alloc<uint8_t>(sizeof(MemberRef<double>) * 128);
+        E.bar = lead->alloc<unsigned>(STAGE_BAR_WORDS);
+        E.err = lead->alloc<int>(1);
+        ck(cudaMemset(E.bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "memset");
+        ck(cudaMemset(E.err, 0, sizeof(int)), "memset");
+        ck(cudaMallocHost(&E.h_refs, sizeof(MemberRef<double>) * 128), "cudaMallocHost");
+        ck(cudaMallocHost(&E.h_err, sizeof(int)), "cudaMallocHost");
+        *E.h_err = 0;
+        ck(cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming), "cudaEventCreate");
+        E.grid = stage_batch_grid<R>(lead->nsm);
+        if (!E.grid) throw CudaError("persistent ensemble stage cannot run");
+    }
+    MemberRef<R>* refs = reinterpret_cast<MemberRef<R>*>(E.h_refs);
+    int jtop = 0;
+    for (int i = 0; i < n; ++i) {
+        sww_handle* h = hs[i];
+        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop};
+        jtop = std::max(jtop, h->jtop);
+        if (i > 0) {
+            ck(cudaEventRecord(h->ev_out, h->stream), "ensemble join");
+            ck(cudaStreamWaitEvent(lead->stream, h->ev_out, 0), "ensemble join");
+        }
+    }
+    ck(cudaMemcpyAsync(E.refs, refs, sizeof(MemberRef<R>) * n, cudaMemcpyHostToDevice, lead->stream), "refs");
+    int ns;
+    const RKStage* st = stages(lead->cfg.rk, ns);
+    for (int k = 0; k < ns; ++k) {
+        BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
+                       lead->cfg.H, lead->cfg.g, st[k], E.bar, E.err};
+        ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
+    }
+    ck(cudaMemcpyAsync(E.h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, lead->stream), "err");
+    ck(cudaEventRecord(E.ev, lead->stream), "ensemble fork");
+    for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
 }
 
 int check_level(const sww_handle* h, int level) {
@@ -1102,18 +1166,72 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
             if (hs[k] == hs[i]) return fail(SWW_E_ARG, "a handle appears twice");
     }
     if (n == 0 || nsteps == 0) return SWW_OK;
+    // one persistent launch per RK stage over all members (every member asks for it
+    // with persistent = 1, and they share precision, Jmin, patch side, depth, gravity
+    // and scheme); otherwise the members' whole steps overlap on their own streams
+    bool batched = n > 1 && n <= 128;
+    for (int i = 0; i < n && batched; ++i) {
+        const sww_config &a = hs[0]->cfg, &b = hs[i]->cfg;
+        batched = hs[i]->stage_cap > 0 && hs[i]->cfg.persistent == 1 && a.precision == b.precision &&
+                  a.jmin == b.jmin && a.patch == b.patch && a.H == b.H && a.g == b.g && a.rk == b.rk;
+    }
     return guarded([&]() -> int {
-        // every member's step is one graph launch on the member's own stream; the
-        // members advance in turn, each waiting only for its own previous step.
-        // Cooperative launches of different streams do not overlap on the GPU, so with
-        // more than one member the RK stages run as one launch per phase.
-        std::vector<unsigned> own(n);
         for (int i = 0; i < n; ++i) {
             sww_handle* h = hs[i];
-            own[i] = h->stage_blocks;
-            if (n > 1) h->stage_blocks = 0;
             ck(cudaEventRecord(h->ev_in, h->user), "join in");
             ck(cudaStreamWaitEvent(h->stream, h->ev_in, 0), "join in");
+        }
+        auto finish = [&](sww_handle* h) -> int {
+            ck(cudaStreamSynchronize(h->stream), "step");
+            if (int rc = barrier_status(h)) return rc;
+            double d = *h->h_dt;
+            if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
+            h->t += d;
+            h->last_dt = d;
+            h->steps += 1;
+            update_top(h);
+            return SWW_OK;
+        };
+        auto join_out = [&]() {
+            for (int i = 0; i < n; ++i) {
+                sww_handle* h = hs[i];
+                ck(cudaEventRecord(h->ev_out, h->stream), "join out");
+                ck(cudaStreamWaitEvent(h->user, h->ev_out, 0), "join out");
+            }
+        };
+        int rc = SWW_OK;
+        if (batched) {
+            for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
+                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
+                by_prec(hs[0], [&](auto r) {
+                    ensemble_stages<decltype(r)>(hs, n);
+                    return 0;
+                });
+                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 2);
+                check_launch();
+                for (int i = 0; i < n; ++i) {
+                    int r = finish(hs[i]);
+                    if (rc == SWW_OK) rc = r;
+                }
+                auto& E = hs[0]->ens;
+                if (rc == SWW_OK && *E.h_err) {
+                    *E.h_err = 0;
+                    ck(cudaMemset(E.err, 0, sizeof(int)), "reset err");
+                    ck(cudaMemset(E.bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "reset barrier");
+                    rc = fail(SWW_E_TIMEOUT, "a grid barrier of the persistent ensemble stage timed out");
+                }
+            }
+            join_out();
+            return rc;
+        }
+        // otherwise every member's step is one graph launch on the member's own
+        // stream, the members advancing in turn, each waiting only for its own
+        // previous step; cooperative launches of different streams do not overlap,
+        // so the RK stages run as one launch per phase
+        std::vector<unsigned> own(n);
+        for (int i = 0; i < n; ++i) {
+            own[i] = hs[i]->stage_blocks;
+            if (n > 1) hs[i]->stage_blocks = 0;
         }
         struct Restore {
             sww_handle* const* hs;
@@ -1126,18 +1244,6 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
             run_step(h, dt, do_adapt != 0);
             check_launch();
         };
-        auto finish = [&](sww_handle* h) -> int {
-            ck(cudaStreamSynchronize(h->stream), "step");
-            if (int rc = barrier_status(h)) return rc;
-            double d = *h->h_dt;
-            if (!std::isfinite(d) || !(d > 0)) return fail(SWW_E_NUMERIC, "non-finite or non-positive time step");
-            h->t += d;
-            h->last_dt = d;
-            h->steps += 1;
-            update_top(h);
-            return SWW_OK;
-        };
-        int rc = SWW_OK;
         for (int i = 0; i < n; ++i) launch(hs[i]);
         for (int s = 1; s < nsteps && rc == SWW_OK; ++s)
             for (int i = 0; i < n && rc == SWW_OK; ++i) {
@@ -1147,10 +1253,8 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         for (int i = 0; i < n; ++i) {
             int r = finish(hs[i]);
             if (rc == SWW_OK) rc = r;
-            sww_handle* h = hs[i];
-            ck(cudaEventRecord(h->ev_out, h->stream), "join out");
-            ck(cudaStreamWaitEvent(h->user, h->ev_out, 0), "join out");
         }
+        join_out();
         return rc;
     });
 }

@@ -48,6 +48,43 @@ __host__ __device__ constexpr int slots_of() {
 // orientation), as KINDS selects.  A pole entry yields the two pole nodes with
 // elem = -1.  Entries name their level in `lvs` (multi-level lists) or all belong
 // to `one` when lvs is null.
+// Item `local` (0 <= local < slots x P) of work-list entry patch `pat` of level L:
+// body(L, kind, id, elem) when the slot holds an item (see for_items).
+template <int KINDS, class Lv, class Body>
+__device__ __forceinline__ void visit_item(const Lv& L, int64_t pat, int64_t local, int P, Body& body) {
+    int slot = int(local / P);
+    const int64_t idx = local % P;
+    if (pat == L.npatch) {
+        if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
+        return;
+    }
+    const int64_t pp = L.p * L.p;
+    if (idx >= pp) return;
+    const int64_t el = pat * pp + idx;
+    if (KINDS & K_NODE) {
+        if (slot == 0) {
+            body(L, K_NODE, el, el);
+            return;
+        }
+        slot -= 1;
+    }
+    if (KINDS & K_EDGE) {
+        if (slot < 3) {
+            body(L, K_EDGE, slot * L.nelem + el, el);
+            return;
+        }
+        slot -= 3;
+    }
+    if (KINDS & K_TRI) {
+        if (slot < 2) {
+            body(L, K_TRI, slot * L.nelem + el, el);
+            return;
+        }
+        slot -= 2;
+    }
+    if (KINDS & K_CEDGE) body(L, K_CEDGE, int64_t(slot), el);
+}
+
 template <int KINDS, class Lv, class Body>
 __device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& one,
                                           const int32_t* __restrict__ list, const int32_t* __restrict__ count, int P,
@@ -57,41 +94,9 @@ __device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& 
     const int64_t n = int64_t(*count) * S;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t it = gid(); it < n; it += stride) {
-        int32_t ent = list[it / S];
-        int64_t local = it % S;
-        int slot = int(local / P);
-        int64_t idx = local % P;
+        const int32_t ent = list[it / S];
         const Lv& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
-        int64_t pat = ent & PATCH_MASK;
-        if (pat == L.npatch) {
-            if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
-            continue;
-        }
-        int64_t pp = L.p * L.p;
-        if (idx >= pp) continue;
-        int64_t el = pat * pp + idx;
-        if (KINDS & K_NODE) {
-            if (slot == 0) {
-                body(L, K_NODE, el, el);
-                continue;
-            }
-            slot -= 1;
-        }
-        if (KINDS & K_EDGE) {
-            if (slot < 3) {
-                body(L, K_EDGE, slot * L.nelem + el, el);
-                continue;
-            }
-            slot -= 3;
-        }
-        if (KINDS & K_TRI) {
-            if (slot < 2) {
-                body(L, K_TRI, slot * L.nelem + el, el);
-                continue;
-            }
-            slot -= 2;
-        }
-        if (KINDS & K_CEDGE) body(L, K_CEDGE, int64_t(slot), el);
+        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it % S, P, body);
     }
 }
 

@@ -145,6 +145,97 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
     });
 }
 
+// ------------------------------------------------------------------ ensembles
+
+constexpr int MAXM = 128;
+
+// Items of one phase over the members of an ensemble.  mode < 0: each member's
+// all-level list; else the level-j list of the members whose top level is at
+// least j + mode (0 ghosts, -1 restriction).  body(L, kind, id, el, member).
+template <int KINDS, class R, class Body>
+__device__ __forceinline__ void batch_items(const BatchArgs<R>& a, int j, int mode, int64_t* pre, Body body) {
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int m = 0; m < a.nm; ++m) {
+            pre[m] = acc;
+            const MemberRef<R>& M = a.m[m];
+            if (mode < 0)
+                acc += *M.all_count;
+            else if (j <= M.jtop + mode)
+                acc += *M.lvs[j].npatches;
+        }
+        pre[a.nm] = acc;
+    }
+    __syncthreads();
+    constexpr int NS = slots_of<KINDS>();
+    const int64_t S = int64_t(NS) * a.P;
+    const int64_t n = pre[a.nm] * S;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t it = gid(); it < n; it += stride) {
+        const int64_t e = it / S;
+        int lo = 0, hi = a.nm - 1;   // last member whose first entry is <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= e) lo = mid; else hi = mid - 1;
+        }
+        const MemberRef<R>& M = a.m[lo];
+        const int32_t ent = mode < 0 ? M.all_list[e - pre[lo]] : M.lvs[j].patches[e - pre[lo]];
+        const DevLevelT<R>& L = M.lvs[ent >> LVL_SHIFT];
+        auto b = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t el) { body(LL, kind, id, el, M); };
+        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it % S, a.P, b);
+    }
+    __syncthreads();
+}
+
+// One RK stage of every member of an ensemble, the phases of k_stage in order,
+// each phase over all members (the levels of member m are a contiguous record
+// array, so the coarser and finer records of L are (&L)[-1] and (&L)[1]).
+template <class R>
+__global__ void __launch_bounds__(STAGE_TPB) k_stage_batch(BatchArgs<R> a) {
+    __shared__ int64_t pre[MAXM + 1];
+    const R H = R(a.H), g = R(a.g);
+    for (int j = a.jmin + 1; j <= a.jtop_max; ++j) {
+        batch_items<K_NODE | K_EDGE>(a, j, 0, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
+            if (kind == K_NODE)
+                fill_node(L, (&L)[-1], id);
+            else
+                fill_edge(L, (&L)[-1], id);
+        });
+        if (!grid_sync(a.bar, a.err)) return;
+    }
+    batch_items<K_EDGE | K_TRI>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
+        if (kind == K_EDGE)
+            flux_at(L, id, H);
+        else
+            pv_at(L, id, H);
+    });
+    if (!grid_sync(a.bar, a.err)) return;
+    batch_items<K_NODE | K_EDGE>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
+        if (kind == K_NODE)
+            node_at(L, id, g);
+        else
+            coriolis_at(L, id);
+    });
+    if (!grid_sync(a.bar, a.err)) return;
+    for (int j = a.jtop_max - 1; j >= a.jmin; --j) {
+        batch_items<K_NODE | K_EDGE>(a, j, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
+            restrict_item(L, (&L)[1], kind, id);
+        });
+        if (!grid_sync(a.bar, a.err)) return;
+        batch_items<K_NODE>(a, j, -1, pre, [&](const DevLevelT<R>& L, int, int64_t id, int64_t, const MemberRef<R>&) {
+            div_at(L, id);
+        });
+        if (!grid_sync(a.bar, a.err)) return;
+    }
+    batch_items<K_NODE | K_EDGE>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>& M) {
+        const R dt = R(*M.dt);
+        if (kind == K_NODE)
+            update_node(L, id, a.st, dt);
+        else
+            update_edge(L, id, a.st, dt);
+    });
+}
+
 }  // namespace
 
 template <class R>
@@ -171,9 +262,37 @@ cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, k_stage<R>, a);
 }
 
+template <class R>
+unsigned stage_batch_grid(int nsm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_batch<R>, STAGE_TPB, 0) != cudaSuccess) return 0;
+    return unsigned(std::max(per_sm, 0) * nsm);
+}
+
+template <class R>
+cudaError_t launch_stage_batch(const BatchArgs<R>& a, unsigned grid, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(STAGE_TPB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch(1);
+    return cudaLaunchKernelEx(&cfg, k_stage_batch<R>, a);
+}
+
 template unsigned stage_grid<double>(int);
 template unsigned stage_grid<float>(int);
 template cudaError_t launch_stage<double>(const StageArgs<double>&, unsigned, cudaStream_t);
 template cudaError_t launch_stage<float>(const StageArgs<float>&, unsigned, cudaStream_t);
+template unsigned stage_batch_grid<double>(int);
+template unsigned stage_batch_grid<float>(int);
+template cudaError_t launch_stage_batch<double>(const BatchArgs<double>&, unsigned, cudaStream_t);
+template cudaError_t launch_stage_batch<float>(const BatchArgs<float>&, unsigned, cudaStream_t);
 
 }  // namespace sww

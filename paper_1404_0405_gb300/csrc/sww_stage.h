@@ -30,10 +30,37 @@ struct StageArgs {
     int* err;
 };
 
+// One member of an ensemble stage: its level records (contiguous, levels 0..jmax),
+// its all-level active list, its time step and its top level.
+template <class R>
+struct MemberRef {
+    const DevLevelT<R>* lvs;
+    const int32_t* all_list;
+    const int32_t* all_count;
+    const double* dt;
+    int jtop;
+};
+
+// One persistent RK stage of nm members (m: device array of nm refs, nm <= 128)
+// with a common patch area P, Jmin, mean depth H and gravity g.
+template <class R>
+struct BatchArgs {
+    const MemberRef<R>* m;
+    int nm, P, jmin, jtop_max;
+    double H, g;
+    RKStage st;
+    unsigned* bar;
+    int* err;
+};
+
 // co-resident blocks of the stage kernel on nsm SMs (0 when it cannot run)
 template <class R>
 unsigned stage_grid(int nsm);
 template <class R>
 cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s);
+template <class R>
+unsigned stage_batch_grid(int nsm);
+template <class R>
+cudaError_t launch_stage_batch(const BatchArgs<R>& a, unsigned grid, cudaStream_t s);
 
 }  // namespace sww

@@ -42,15 +42,18 @@ def _snapshot(sww, m):
     return out, (st["t"], st["mass"], st["energy"], st["steps"])
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_shared_members_match_single_runs(precision):
+@pytest.mark.parametrize("precision,persistent", [("fp64", "auto"), ("fp32", "auto"), ("fp64", "always"),
+                                                  ("fp32", "always")])
+def test_shared_members_match_single_runs(precision, persistent):
+    """persistent "auto": the members' steps overlap on their streams; "always":
+    one cooperative launch per RK stage over all members."""
     import paper_1404_0405_gb300 as sww
     jmin, top = 2, max(j for j, _, _ in MEMBERS)
     base = sww.Model(jmin, top, patch=4)
     ens, alone = [], []
     for jmax, eps, seed in MEMBERS:
         for group in (ens, alone):
-            m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision=precision)
+            m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision=precision, persistent=persistent)
             dh, u = _fields(m, seed)
             m.set_state(dh, u)
             m.adapt()
