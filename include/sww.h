@@ -90,8 +90,10 @@ typedef struct {
                           handle stepping alone, one launch per phase inside
                           sww_step_ensemble (the members' steps then overlap); 1: also
                           one cooperative launch per stage over all ensemble members;
-                          -1: one launch per phase always.  Falls back to -1 where a
-                          cooperative launch cannot run.                               */
+                          2: inside sww_step_ensemble, each member's stage as one
+                          thread-block cluster (up to 16 blocks, hardware barriers
+                          between the phases); -1: one launch per phase always.  Falls
+                          back to -1 where the chosen launch cannot run.               */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
 } sww_config;

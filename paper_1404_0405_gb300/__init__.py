@@ -166,13 +166,14 @@ class Model:
                  cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
                  mask="lists"):
         """share: another Model whose grid and tables this one reuses (sww_create_shared).
-        persistent: True/"auto", "always" (also batched over ensemble members) or
+        persistent: True/"auto", "always" (also batched over ensemble members),
+        "cluster" (ensemble members' stages as thread-block clusters) or
         False/"never" (see sww_config.persistent)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
                           blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
-                          {True: 0, "auto": 0, "always": 1, False: -1, "never": -1}[persistent],
+                          {True: 0, "auto": 0, "always": 1, "cluster": 2, False: -1, "never": -1}[persistent],
                           {"lists": 0, "dense": 1}[mask])
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()

@@ -163,6 +163,10 @@ struct sww_handle {
     // persistent RK stages: blocks of the cooperative launch (0: one launch per phase),
     // barrier state and the error flag of a timed-out barrier (device and pinned copy)
     unsigned stage_blocks = 0, stage_cap = 0;
+    // RK stages as one thread-block cluster of cluster_cap blocks (members of an
+    // overlapped ensemble step); 0 when clusters of stage blocks cannot run
+    int cluster_cap = 0;
+    bool use_cluster = false;
     // buffers of ensemble steps led by this handle (allocated on first use)
     struct {
         uint8_t* refs = nullptr;    // device MemberRef array
@@ -550,15 +554,18 @@ void update(sww_handle* h, const RKStage& st) {
 // trend and RK stage: one persistent cooperative launch, or one launch per phase
 template <class R>
 void stage(sww_handle* h, const RKStage& st) {
-    if (!h->stage_blocks) {
+    if (!h->stage_blocks && !h->use_cluster) {
         trend<R>(h);
         update<R>(h, st);
         return;
     }
     Trace t(h, SWW_K_STAGE);
     StageArgs<R> a{dlv<R>(h), h->all_list, h->all_count, h->S, h->cfg.jmin, h->jtop, h->cfg.jmax,
-                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err};
-    ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
+                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err, h->use_cluster ? 1 : 0};
+    if (h->use_cluster)
+        ck(launch_stage_cluster(a, h->cluster_cap, h->stream), "cluster stage launch");
+    else
+        ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
 }
 
 // SWW_E_TIMEOUT (and the flag cleared) when a persistent stage's barrier timed out
@@ -762,7 +769,8 @@ void run_step_t(sww_handle* h, double dt, bool do_adapt, int part = 0) {
         one_step<R>(h, dt, do_adapt, part);
         return;
     }
-    auto key = std::make_tuple(part, h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, h->stage_blocks);
+    const unsigned mode = h->use_cluster ? (0x80000000u | unsigned(h->cluster_cap)) : h->stage_blocks;
+    auto key = std::make_tuple(part, h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, mode);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
         if (h->graphs.size() >= 24) h->drop_graphs();
@@ -947,6 +955,7 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
             ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "device attribute");
             if (coop) h->stage_cap = fp32 ? stage_grid<float>(h->nsm) : stage_grid<double>(h->nsm);
             h->stage_blocks = h->stage_cap;
+            h->cluster_cap = fp32 ? stage_cluster_size<float>() : stage_cluster_size<double>();
         }
         h->cnt = h->alloc<unsigned long long>(4);
         h->thr = h->alloc<double>(2);
@@ -1226,18 +1235,22 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         }
         // otherwise every member's step is one graph launch on the member's own
         // stream, the members advancing in turn, each waiting only for its own
-        // previous step; cooperative launches of different streams do not overlap,
-        // so the RK stages run as one launch per phase
+        // previous step.  Cooperative launches of different streams do not overlap,
+        // so a member's RK stage runs as one launch per phase, or (persistent = 2)
+        // as one thread-block cluster with hardware barriers between the phases
         std::vector<unsigned> own(n);
         for (int i = 0; i < n; ++i) {
             own[i] = hs[i]->stage_blocks;
-            if (n > 1) hs[i]->stage_blocks = 0;
+            if (n > 1) {
+                hs[i]->stage_blocks = 0;
+                hs[i]->use_cluster = hs[i]->cluster_cap > 0 && hs[i]->cfg.persistent == 2;
+            }
         }
         struct Restore {
             sww_handle* const* hs;
             std::vector<unsigned>& own;
             ~Restore() {
-                for (size_t i = 0; i < own.size(); ++i) hs[i]->stage_blocks = own[i];
+                for (size_t i = 0; i < own.size(); ++i) hs[i]->stage_blocks = own[i], hs[i]->use_cluster = false;
             }
         } restore{hs, own};
         auto launch = [&](sww_handle* h) {

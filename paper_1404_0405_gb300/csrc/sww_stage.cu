@@ -87,6 +87,19 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
     return ok != 0;
 }
 
+// Barrier between phases: the grid barrier of a cooperative launch, or the
+// hardware barrier of a thread-block cluster when the launch is one cluster (all
+// its blocks are co-scheduled, and every thread runs every phase).
+template <class R>
+__device__ __forceinline__ bool stage_sync(const StageArgs<R>& a) {
+    if (a.cluster) {
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+    return grid_sync(a.bar, a.err);
+}
+
 template <class R>
 __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
     __shared__ DevLevelT<R> sl[MAXL];
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
             else
                 fill_edge(L, C, id);
         });
-        if (!grid_sync(a.bar, a.err)) return;
+        if (!stage_sync(a)) return;
     }
     ITEMS(K_EDGE | K_TRI, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
         if (kind == K_EDGE)
@@ -117,14 +130,14 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
         else
             pv_at(L, id, H);
     });
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!stage_sync(a)) return;
     ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
         if (kind == K_NODE)
             node_at(L, id, g);
         else
             coriolis_at(L, id);
     });
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!stage_sync(a)) return;
     // restriction, fine to coarse
     for (int j = a.jtop - 1; j >= a.jmin; --j) {
         const DevLevelT<R>& C = lv[j];
@@ -132,9 +145,9 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
         ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, C, C.patches, C.npatches, a.P) {
             restrict_item(L, F, kind, id);
         });
-        if (!grid_sync(a.bar, a.err)) return;
+        if (!stage_sync(a)) return;
         ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, C.patches, C.npatches, a.P) { div_at(L, id); });
-        if (!grid_sync(a.bar, a.err)) return;
+        if (!stage_sync(a)) return;
     }
     const R dt = R(a.dt ? *a.dt : 0.0);
     ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
@@ -262,6 +275,54 @@ cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s) {
     return cudaLaunchKernelEx(&cfg, k_stage<R>, a);
 }
 
+// One RK stage as a single thread-block cluster (up to 16 blocks): for members of an
+// ensemble whose steps overlap on their own streams.
+template <class R>
+cudaError_t launch_stage_cluster(const StageArgs<R>& a, int blocks, cudaStream_t s) {
+    if (a.jmax + 1 > MAXL || !a.cluster) return cudaErrorInvalidValue;
+    if (blocks > 8) {
+        cudaError_t e = cudaFuncSetAttribute(k_stage<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(STAGE_TPB);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = blocks;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch(1);
+    return cudaLaunchKernelEx(&cfg, k_stage<R>, a);
+}
+
+// largest cluster of stage blocks that can be resident (16, else 8, else 0)
+template <class R>
+int stage_cluster_size() {
+    for (int c : {16, 8}) {
+        if (c > 8 && cudaFuncSetAttribute(k_stage<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+            continue;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(STAGE_TPB);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_stage<R>, &cfg) == cudaSuccess && n > 0) return c;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
 template <class R>
 unsigned stage_batch_grid(int nsm) {
     int per_sm = 0;
@@ -290,6 +351,10 @@ template unsigned stage_grid<double>(int);
 template unsigned stage_grid<float>(int);
 template cudaError_t launch_stage<double>(const StageArgs<double>&, unsigned, cudaStream_t);
 template cudaError_t launch_stage<float>(const StageArgs<float>&, unsigned, cudaStream_t);
+template cudaError_t launch_stage_cluster<double>(const StageArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_stage_cluster<float>(const StageArgs<float>&, int, cudaStream_t);
+template int stage_cluster_size<double>();
+template int stage_cluster_size<float>();
 template unsigned stage_batch_grid<double>(int);
 template unsigned stage_batch_grid<float>(int);
 template cudaError_t launch_stage_batch<double>(const BatchArgs<double>&, unsigned, cudaStream_t);

@@ -28,6 +28,7 @@ struct StageArgs {
     const double* dt;
     unsigned* bar;
     int* err;
+    int cluster;   // 1: the launch is one thread-block cluster (hardware barrier)
 };
 
 // One member of an ensemble stage: its level records (contiguous, levels 0..jmax),
@@ -58,6 +59,10 @@ template <class R>
 unsigned stage_grid(int nsm);
 template <class R>
 cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s);
+template <class R>
+cudaError_t launch_stage_cluster(const StageArgs<R>& a, int blocks, cudaStream_t s);
+template <class R>
+int stage_cluster_size();
 template <class R>
 unsigned stage_batch_grid(int nsm);
 template <class R>

@@ -43,10 +43,11 @@ def _snapshot(sww, m):
 
 
 @pytest.mark.parametrize("precision,persistent", [("fp64", "auto"), ("fp32", "auto"), ("fp64", "always"),
-                                                  ("fp32", "always")])
+                                                  ("fp32", "always"), ("fp64", "cluster"), ("fp32", "cluster")])
 def test_shared_members_match_single_runs(precision, persistent):
     """persistent "auto": the members' steps overlap on their streams; "always":
-    one cooperative launch per RK stage over all members."""
+    one cooperative launch per RK stage over all members; "cluster": each member's
+    stage as one thread-block cluster."""
     import paper_1404_0405_gb300 as sww
     jmin, top = 2, max(j for j, _, _ in MEMBERS)
     base = sww.Model(jmin, top, patch=4)
