@@ -96,6 +96,9 @@ typedef struct {
                           back to -1 where the chosen launch cannot run.               */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
+    double nu;         /* viscosity (m^2/s) of the viscous form (Sec. 3.1): nu div grad dh
+                          on the height, nu (grad div u - grad^perp curl u) on the velocity;
+                          0: inviscid.  The time step rule has no viscous bound.      */
 } sww_config;
 
 typedef struct {

@@ -35,8 +35,9 @@ from . import adapt, grid, transform, trisk
 
 
 class Model:
-    def __init__(self, Hy, H=1.0e4, g=9.80616, eps=1e-2, rk="rk4", cfl=0.8):
+    def __init__(self, Hy, H=1.0e4, g=9.80616, eps=1e-2, rk="rk4", cfl=0.8, nu=0.0):
         self.Hy, self.H, self.g, self.eps, self.rk, self.cfl = Hy, H, g, eps, rk, cfl
+        self.nu = nu
         self.jmin, self.jmax = Hy.jmin, Hy.jmax
         self.VS = {j: transform.VelocityStencils(Hy, j) for j in range(self.jmin + 1, self.jmax + 1)}
         self.FS = {j: transform.FluxStencils(Hy, j) for j in range(self.jmin + 1, self.jmax + 1)}
@@ -164,13 +165,21 @@ class Model:
         self.fill_ghosts(dh, u)
         F, q, B, c, Q = {}, {}, {}, {}, {}
         with np.errstate(invalid="ignore"):
+            nu = self.nu
             for j in self.levels:
                 L = Hy.levels[j]
                 F[j] = trisk.thickness_flux(L, dh[j], u[j], H)
                 q[j] = trisk.potential_vorticity(L, dh[j], u[j], H)
                 B[j] = trisk.bernoulli(L, dh[j], u[j], g)
-                c[j] = trisk.divergence(L, F[j])
                 Q[j] = -trisk.coriolis_tendency(L, F[j], q[j])
+                if nu:
+                    # viscous form: the diffusive height flux joins F after the Coriolis
+                    # term (which takes the mass flux), -nu div u joins B, and
+                    # nu grad^perp curl u joins Q; the restriction then carries them
+                    F[j] = F[j] - nu * trisk.gradient(L, dh[j])
+                    B[j] = B[j] - nu * trisk.divergence(L, u[j])
+                    Q[j] = Q[j] + nu * trisk.perp_gradient(L, trisk.vorticity(L, u[j]))
+                c[j] = trisk.divergence(L, F[j])
             for j in range(self.jmax - 1, self.jmin - 1, -1):
                 C, Fl = Hy.levels[j], Hy.levels[j + 1]
                 cov_n = self.covered(j)

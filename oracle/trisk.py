@@ -127,9 +127,35 @@ def bernoulli(L, dh, u, g):
     return g * dh + kinetic_energy(L, u)
 
 
-def trend(L, dh, u, H, g):
-    """Uniform-level trend (d dh/dt, du/dt) of Eqs. (height), (velo)."""
+def perp_gradient(L, z):
+    """grad^perp of a dual-cell field at every edge: (1/l_e) sum_{v at e} t_{e,v} z_v,
+    the adjoint of the vorticity (sum_e l_e d_e u_e (grad^perp z)_e = sum_v A_v z_v zeta_v)."""
+    out = np.zeros(L.E)
+    for k in range(3):
+        np.add.at(out, L.tri_edges[:, k], L.tri_esign[:, k] * z)
+    return out / L.l_e
+
+
+def laplacian(L, a):
+    """div grad of a node field (Sec. 3.1, viscous form)."""
+    return divergence(L, gradient(L, a))
+
+
+def vector_laplacian(L, u):
+    """grad div u - grad^perp curl u at every edge (Sec. 3.1, viscous form)."""
+    return gradient(L, divergence(L, u)) - perp_gradient(L, vorticity(L, u))
+
+
+def trend(L, dh, u, H, g, nu=0.0):
+    """Uniform-level trend (d dh/dt, du/dt) of Eqs. (height), (velo); with nu > 0 the
+    viscous form: nu div grad(dh) on the height, nu (grad div u - grad^perp curl u) on
+    the velocity (the Bernoulli gradient stays grad B; B already holds K)."""
     F = thickness_flux(L, dh, u, H)
     q = potential_vorticity(L, dh, u, H)
     B = bernoulli(L, dh, u, g)
-    return -divergence(L, F), coriolis_tendency(L, F, q) - gradient(L, B)
+    a = -divergence(L, F)
+    b = coriolis_tendency(L, F, q) - gradient(L, B)
+    if nu:
+        a = a + nu * laplacian(L, dh)
+        b = b + nu * vector_laplacian(L, u)
+    return a, b

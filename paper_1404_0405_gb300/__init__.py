@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
                 ("omega", ctypes.c_double), ("g", ctypes.c_double), ("H", ctypes.c_double),
                 ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int), ("precision", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("mask", ctypes.c_int)]
+                ("mask", ctypes.c_int), ("nu", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -164,7 +164,7 @@ class Model:
 
     def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
                  cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
-                 mask="lists"):
+                 mask="lists", nu=0.0):
         """share: another Model whose grid and tables this one reuses (sww_create_shared).
         persistent: True/"auto", "always" (also batched over ensemble members),
         "cluster" (ensemble members' stages as thread-block clusters) or
@@ -174,7 +174,7 @@ class Model:
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
                           blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
                           {True: 0, "auto": 0, "always": 1, "cluster": 2, False: -1, "never": -1}[persistent],
-                          {"lists": 0, "dense": 1}[mask])
+                          {"lists": 0, "dense": 1}[mask], float(nu))
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()
         if share is None:

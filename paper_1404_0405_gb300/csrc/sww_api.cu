@@ -404,9 +404,12 @@ void alloc_state(sww_handle* h, int j) {
     const int64_t coarse_E = j > h->cfg.jmin ? h->geo->lv[j - 1].E : 1;
     R** dN[] = {&D.dh, &D.dh0, &D.dha, &D.dht, &D.B, &D.c, &D.hdet};
     for (auto p : dN) *p = h->alloc<R>(N);
-    R** dE[] = {&D.u, &D.u0, &D.ua, &D.ut, &D.F, &D.Q, &D.ui};
+    R** dE[] = {&D.u, &D.u0, &D.ua, &D.ut, &D.F, &D.Q, &D.ui, &D.Fd};
     for (auto p : dE) *p = h->alloc<R>(E);
     D.q = h->alloc<R>(T);
+    D.zeta = h->alloc<R>(T);
+    ck(cudaMemset(D.zeta, 0, T * sizeof(R)), "memset");
+    D.nu = h->cfg.nu;
     D.ue = h->alloc<R>(coarse_E);
     uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
     for (auto p : bN) *p = h->alloc<uint8_t>(N);
@@ -880,6 +883,7 @@ int check_config(const sww_config* cfg) {
     if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
         return fail(SWW_E_ARG, "precision must be SWW_FP64 or SWW_FP32");
     if (cfg->mask != 0 && cfg->mask != 1) return fail(SWW_E_ARG, "mask must be 0 (candidate lists) or 1 (dense)");
+    if (!(cfg->nu >= 0)) return fail(SWW_E_ARG, "nu must be >= 0");
     return SWW_OK;
 }
 

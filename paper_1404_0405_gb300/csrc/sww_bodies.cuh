@@ -113,6 +113,7 @@ __device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
              esign<R>(c2) * L.u[c2 >> 1] * L.d_e[c2 >> 1];
     R hv = L.kite[t] * (H + L.dh[n0]) + L.kite[L.T + t] * (H + L.dh[n1]) + L.kite[2 * L.T + t] * (H + L.dh[n2]);
     R Av = L.A_v[t];
+    if (L.nu != 0.0) L.zeta[t] = circ / Av;
     L.q[t] = (circ / Av + L.f_v[t]) / (hv / Av);
 }
 
@@ -123,6 +124,8 @@ __device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
     int32_t a = L.en[e], b = L.en[L.E + e];
     if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
     L.F[e] = R(0.5) * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
+    // viscous form: diffusive height flux -nu grad(dh) (joins F in the divergence)
+    if (L.nu != 0.0) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / L.d_e[e];
 }
 
 // divergence, kinetic energy and Bernoulli function at a node
@@ -130,16 +133,20 @@ template <class R>
 __device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
-    R div = R(0), ke = R(0);
+    R div = R(0), ke = R(0), du = R(0);
+    const bool visc = L.nu != 0.0;
     for (int k = 0; k < dg; ++k) {
         int32_t code = L.ring_e[k * L.N + v];
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
-        div += esign<R>(code) * L.F[e] * L.l_e[e];
         R ue = L.u[e];
+        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
+        if (visc) du += esign<R>(code) * ue * L.l_e[e];
         ke += R(0.25) * L.l_e[e] * L.d_e[e] * ue * ue;
     }
     R A = L.A_i[v];
+    // viscous form: -nu div u joins B (so that -grad B gains +nu grad div u)
+    if (visc) ke -= R(L.nu) * du;
     L.c[v] = div / A;
     L.B[v] = g * L.dh[v] + ke / A;
 }
@@ -157,6 +164,18 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
         R q2 = R(0.5) * (L.q[L.et[e2]] + L.q[L.et[L.E + e2]]);
         s += w * L.F[e2] * R(0.5) * (qe + q2);
     }
+    // viscous form: -nu grad^perp curl u, grad^perp zeta = (1/l_e) sum_{v at e} t_{e,v} zeta_v
+    if (L.nu != 0.0) {
+        R gp = R(0);
+        for (int side = 0; side < 2; ++side) {
+            const int32_t t = L.et[side * L.E + e];
+            for (int k = 0; k < 3; ++k) {
+                const int32_t code = L.te[k * L.T + t];
+                if ((code >> 1) == e) gp += esign<R>(code) * L.zeta[t];
+            }
+        }
+        s -= R(L.nu) * gp / L.l_e[e];
+    }
     L.Q[e] = s;
 }
 
@@ -165,11 +184,12 @@ __device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
     R div = R(0);
+    const bool visc = L.nu != 0.0;
     for (int k = 0; k < dg; ++k) {
         int32_t code = L.ring_e[k * L.N + v];
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
-        div += esign<R>(code) * L.F[e] * L.l_e[e];
+        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
     }
     L.c[v] = div / L.A_i[v];
 }
@@ -260,12 +280,19 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
     int64_t i = id;
     bool ca = L.nflag[L.en[i]] & COVERED, cb = L.nflag[L.en[L.E + i]] & COVERED;
     if (ca || cb) {
+        // the restricted total height flux (mass flux plus the viscous form's
+        // diffusive flux) goes to F; the coarse diffusive flux is then zero
+        const bool visc = L.nu != 0.0;
         R s = R(0);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) s += L.rf_fw[k * L.E + i] * F.F[L.rf_fi[k * L.E + i]];
+        for (int k = 0; k < 12; ++k) {
+            const int32_t f = L.rf_fi[k * L.E + i];
+            s += L.rf_fw[k * L.E + i] * (visc ? F.F[f] + F.Fd[f] : F.F[f]);
+        }
 #pragma unroll
         for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
         L.F[i] = s / L.l_e[i];
+        if (visc) L.Fd[i] = R(0);
     }
     if (ca && cb) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
 }

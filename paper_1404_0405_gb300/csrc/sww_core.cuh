@@ -27,6 +27,7 @@ struct DevLevelT {
     int J;
     int64_t n, p, np, nelem, N, E, T, npatch;
     double dx;                     // Table 1 spacing of the level (m)
+    double nu;                     // viscosity (m^2/s) of the viscous form; 0: inviscid
     // topology
     const int32_t *en, *et;        // [2*E] origin/end node, left/right triangle
     const int32_t *tn, *te;        // [3*T] nodes, side edges (2e + against)
@@ -59,6 +60,7 @@ struct DevLevelT {
     // state and work arrays
     R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
     R *F, *q, *B, *c, *Q;
+    R *Fd, *zeta;                  // [E] diffusive height flux, [T] relative vorticity (nu > 0)
     uint8_t *nflag, *eflag, *sig, *tmask, *band0, *band1;
     R *hdet, *ue, *ui;             // [N], [E of level J-1], [E]
     uint8_t* pflag;                // [npatch]

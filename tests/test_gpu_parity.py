@@ -31,12 +31,12 @@ def rel_err(a, b):
 class Pair:
     """An oracle model and a library model on the same grid and initial state."""
 
-    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64"):
+    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64", nu=0.0):
         import paper_1404_0405_gb300 as sww
         self.sww = sww
         self.Hy = grid.Hierarchy(jmin, jmax)
-        self.ora = model.Model(self.Hy, eps=eps, rk=rk)
-        self.lib = sww.Model(jmin, jmax, patch=patch, eps=eps, rk=rk, precision=precision)
+        self.ora = model.Model(self.Hy, eps=eps, rk=rk, nu=nu)
+        self.lib = sww.Model(jmin, jmax, patch=patch, eps=eps, rk=rk, precision=precision, nu=nu)
         self.maps = {}
         for j in range(jmin, jmax + 1):
             xyz, en = self.lib.grid(j)
@@ -223,3 +223,31 @@ def test_diagnostics_match(built):
     for j in P.ora.levels:
         assert st["live_nodes"][j] == P.ora.live_n[j].sum()
         assert st["ghost_nodes"][j] == P.ora.ghost_n[j].sum()
+
+
+# ----------------------------------------------------------------------------- viscous form (Sec. 3.1)
+
+NU = 2e5   # m^2/s: the diffusion number nu dt / dx^2 stays below 0.05 on these grids
+
+
+def test_viscous_trend_matches(built):
+    P = Pair(2, 4, nu=NU)
+    P.rhs()
+    P.check_fields(which="trend")
+    P2 = Pair(2, 4, nu=NU)
+    P2.adapt()
+    P2.rhs()
+    P2.check_fields(which="trend")
+
+
+def test_viscous_adaptive_steps_match(built):
+    P = Pair(2, 4, nu=NU)
+    P.adapt()
+    m0 = P.lib.stats()["mass"]
+    for _ in range(3):
+        dt = P.ora.dt_cfl()
+        P.ora.step(dt)
+        P.lib.step(dt, 1, adapt=True)
+        P.check_masks()
+        P.check_fields()
+    assert abs(P.lib.stats()["mass"] / m0 - 1) < 1e-14

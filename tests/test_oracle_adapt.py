@@ -90,9 +90,9 @@ def test_ghost_band_is_bfs_distance():
     assert np.array_equal(gn[4], (dist >= 1) & (dist <= adapt.GHOST_HOPS))
 
 
-def make_model(jmin=2, jmax=4, kind="jet", eps=1e-2, seed=0, rk="rk4"):
+def make_model(jmin=2, jmax=4, kind="jet", eps=1e-2, seed=0, rk="rk4", nu=0.0):
     Hy = grid.Hierarchy(jmin, jmax)
-    M = model.Model(Hy, eps=eps, rk=rk)
+    M = model.Model(Hy, eps=eps, rk=rk, nu=nu)
     W = workloads.Workload(kind, seed=seed)
     L = Hy.levels[jmax]
     dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
@@ -101,9 +101,11 @@ def make_model(jmin=2, jmax=4, kind="jet", eps=1e-2, seed=0, rk="rk4"):
     return M
 
 
-@pytest.mark.parametrize("rk", ["rk4", "ssp43"])
-def test_adaptive_mass_conserved(rk):
-    M = make_model(rk=rk)
+@pytest.mark.parametrize("rk,nu", [("rk4", 0.0), ("ssp43", 0.0), ("rk4", 2e5)])
+def test_adaptive_mass_conserved(rk, nu):
+    """With nu > 0 the diffusive height flux goes through the conservative flux
+    restriction with the mass flux, so the viscous form conserves mass too."""
+    M = make_model(rk=rk, nu=nu)
     assert 0 < M.active_nodes() < sum(M.Hy.levels[j].N for j in M.levels)
     m0 = M.mass()
     dt = M.dt_cfl()

@@ -200,3 +200,84 @@ def test_flux_restriction_of_uniform_flow_is_consistent(hier25):
     FS = transform.FluxStencils(hier25, j)
     Fc = transform.restrict_flux(FS, uf, F.l_e, trisk.divergence(F, uf)) / C.l_e
     assert np.sqrt(np.mean((Fc - uc) ** 2)) < 0.05 * np.sqrt(np.mean(uc ** 2))
+
+
+# ----------------------------------------------------------------------------- viscous form (Sec. 3.1)
+
+def test_scalar_laplacian_identities(L3):
+    """div grad: conserves mass and is the negative of the discrete gradient energy,
+    sum_i A_i a_i (div grad a)_i = -sum_e l_e d_e (grad a)_e^2 (summation by parts)."""
+    rng = np.random.default_rng(21)
+    a = rng.normal(0, 1, L3.N)
+    lap = trisk.laplacian(L3, a)
+    assert abs(np.sum(L3.A_i * lap)) < 1e-10 * np.sum(L3.A_i * np.abs(lap))
+    gr = trisk.gradient(L3, a)
+    lhs = np.sum(L3.A_i * a * lap)
+    rhs = -np.sum(L3.l_e * L3.d_e * gr ** 2)
+    assert rhs < 0 and abs(lhs / rhs - 1) < 1e-12
+
+
+def test_vector_laplacian_energy_identity(L3):
+    """sum_e l_e d_e u_e (grad div u - grad^perp curl u)_e = -sum_i A_i D_i^2
+    - sum_v A_v zeta_v^2: both parts dissipate, with the signs of the paper's form."""
+    rng = np.random.default_rng(22)
+    u = rng.normal(0, 1, L3.E)
+    lap = trisk.vector_laplacian(L3, u)
+    D = trisk.divergence(L3, u)
+    z = trisk.vorticity(L3, u)
+    lhs = np.sum(L3.l_e * L3.d_e * u * lap)
+    rhs = -np.sum(L3.A_i * D ** 2) - np.sum(L3.A_v * z ** 2)
+    assert abs(lhs / rhs - 1) < 1e-12
+
+
+def _y2(xyz):
+    """A degree-2 real spherical harmonic (xy), eigenfunction of the sphere's
+    Laplacian with eigenvalue -l(l+1)/R^2 = -6/R^2."""
+    return xyz[:, 0] * xyz[:, 1]
+
+
+@pytest.mark.parametrize("kind", ["scalar", "gradient"])
+def test_laplacians_of_a_spherical_harmonic_converge(kind):
+    """The discrete Laplacians of a degree-2 harmonic (scalar, and its gradient
+    field) approach -6/R^2 times it as the grid is refined."""
+    errs = []
+    for J in (3, 4, 5):
+        L = grid.Hierarchy(J, J).levels[J]
+        R = L.radius
+        if kind == "scalar":
+            y = _y2(L.xyz)
+            got, want = trisk.laplacian(L, y), -6.0 / R ** 2 * y
+        else:
+            u = trisk.gradient(L, _y2(L.xyz))
+            got, want = trisk.vector_laplacian(L, u), -6.0 / R ** 2 * u
+        errs.append(np.sqrt(np.mean((got - want) ** 2)) / np.sqrt(np.mean(want ** 2)))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 0.05
+
+
+def test_viscous_trend_adds_the_laplacians(L3):
+    rng = np.random.default_rng(23)
+    dh = rng.normal(0, 50, L3.N)
+    u = rng.normal(0, 5, L3.E)
+    a0, b0 = trisk.trend(L3, dh, u, 1e4, 9.80616)
+    a1, b1 = trisk.trend(L3, dh, u, 1e4, 9.80616, nu=1e5)
+    assert np.allclose(a1 - a0, 1e5 * trisk.laplacian(L3, dh), rtol=1e-9, atol=1e-18)
+    assert np.allclose(b1 - b0, 1e5 * trisk.vector_laplacian(L3, u), rtol=1e-9, atol=1e-18)
+
+
+def test_rotational_laplacian_rayleigh_quotient():
+    """The curl-curl part on the dual cells does not converge pointwise on grids
+    refined by bisection (the paper notes the Laplacian's non-convergence on such
+    grids, Sec. 3.2); its weak form does: for the rotated gradient of a degree-2
+    harmonic, <u, Lap u> / <u, u> (l d weights) stays within 5 % of -6/R^2 and the
+    field is divergence-free to rounding."""
+    for J in (3, 4, 5):
+        L = grid.Hierarchy(J, J).levels[J]
+        R = L.radius
+        cc = L.cc / np.linalg.norm(L.cc, axis=1)[:, None]
+        u = trisk.perp_gradient(L, _y2(cc))
+        lap = trisk.vector_laplacian(L, u)
+        w = L.l_e * L.d_e
+        ratio = np.sum(w * u * lap) / np.sum(w * u * u) / (-6.0 / R ** 2)
+        assert 0.95 < ratio < 1.05
+        assert np.abs(trisk.divergence(L, u)).max() * R < 1e-12 * np.abs(u).max() * 1e3
