@@ -78,7 +78,7 @@ typedef struct {
     int patch;         /* patch side p (power of two); levels with 2^j < p use 2^j     */
     int rk;            /* SWW_RK4 or SWW_SSP43                                         */
     double cfl;        /* dt = cfl * min(1/omega_max, min dx/|u|) when dt <= 0         */
-    double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u|; 0 keeps every point */
+    double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u| (see regime); 0 keeps every point */
     int blocks_per_sm; /* work-list launches: blocks of 256 threads per SM (0: 4)           */
     int precision;     /* SWW_FP64: fields and arithmetic in FP64.  SWW_FP32: fields,
                           stencils and transforms in FP32 with weights rounded once from
@@ -99,6 +99,18 @@ typedef struct {
     double nu;         /* viscosity (m^2/s) of the viscous form (Sec. 3.1): nu div grad dh
                           on the height, nu (grad div u - grad^perp curl u) on the velocity;
                           0: inviscid.  The time step rule has no viscous bound.      */
+    int advect;        /* 1: prescribed velocity (the advection test case of Sec. 7.1): the
+                          velocity set by sww_set_state (restricted to every level) never
+                          changes; the depth h = H + dh is carried by the flux h_e u_e
+                          through the same flux restriction, transforms and adaptation.
+                          The velocity takes no part in the significance test (eps_u
+                          infinite unless passed to sww_adapt), the time step is
+                          cfl * min dx/|u| (no gravity waves), and H may be 0.  0: the
+                          full shallow-water equations.                                */
+    int regime;        /* how eps sets the coefficient thresholds.  0: eps_h = eps max|dh|,
+                          eps_u = eps max|u|.  1: eps is the trend tolerance of Sec. 2.3
+                          and the thresholds scale as eps^{3/2} (eps*sqrt(eps) in place of
+                          eps above), the scaling both regimes of the paper share.     */
 } sww_config;
 
 typedef struct {

@@ -23,8 +23,20 @@ classical RK4 ("rk4") or the 4-stage 3rd-order SSP scheme of Spiteri & Ruuth
 ("ssp43", Sec. 3.1).  dt = cfl * min(1/omega_max, min dx/|u|) with
 omega = sqrt(f^2 + g h (pi/dx)^2) (the printed omega is dimensionally
 inconsistent; this reading restores pi/dx squared) and dx the Table 1 spacing of
-each point's level.  Diagnostics: mass = sum_{Jmin} A_k h_k (Jmin is always
+each point's level.  Thresholds: eps_h = eps max|dh|, eps_u = eps max|u| over live
+points (the printed formulas are dimensionally inconsistent; this relative
+reading keeps their eps^{3/2} scaling as an option, ``regime=1``, which puts
+eps^{3/2} in place of eps).  Diagnostics: mass = sum_{Jmin} A_k h_k (Jmin is always
 full); energy of Sec. 7.2 evaluated on Jmin with the TRiSK kinetic energy.
+
+Prescribed-velocity mode (``advect=True``, the advection test case of Sec. 7.1):
+the velocity is the field given to ``set_uniform`` and its restrictions R_u on
+every coarser level, at every point of every level, for all time; only the
+depth evolves, d h/dt = -div(h_e u_e) with the same flux restriction, partial
+transform and adaptation.  Readings (the paper gives the test, not the mode's
+details): the velocity takes no part in the significance test (eps_u infinite),
+newly active edges take the prescribed value rather than a prediction, and
+dt = cfl * min dx/|u| (no gravity waves to resolve).
 """
 from __future__ import annotations
 
@@ -35,9 +47,9 @@ from . import adapt, grid, transform, trisk
 
 
 class Model:
-    def __init__(self, Hy, H=1.0e4, g=9.80616, eps=1e-2, rk="rk4", cfl=0.8, nu=0.0):
+    def __init__(self, Hy, H=1.0e4, g=9.80616, eps=1e-2, rk="rk4", cfl=0.8, nu=0.0, advect=False, regime=0):
         self.Hy, self.H, self.g, self.eps, self.rk, self.cfl = Hy, H, g, eps, rk, cfl
-        self.nu = nu
+        self.nu, self.advect, self.regime = nu, advect, regime
         self.jmin, self.jmax = Hy.jmin, Hy.jmax
         self.VS = {j: transform.VelocityStencils(Hy, j) for j in range(self.jmin + 1, self.jmax + 1)}
         self.FS = {j: transform.FluxStencils(Hy, j) for j in range(self.jmin + 1, self.jmax + 1)}
@@ -54,6 +66,7 @@ class Model:
         for j in range(self.jmax, self.jmin, -1):
             self.dh[j - 1] = transform.restrict_height(Hy, j, self.dh[j])
             self.u[j - 1] = transform.restrict_velocity(Hy, j, self.u[j])
+        self.u_set = {j: self.u[j].copy() for j in self.levels}
         self.live_n = {j: np.ones(Hy.levels[j].N, dtype=bool) for j in self.levels}
         self.live_e = {j: np.ones(Hy.levels[j].E, dtype=bool) for j in self.levels}
         self.ghost_n = {j: np.zeros(Hy.levels[j].N, dtype=bool) for j in self.levels}
@@ -66,6 +79,15 @@ class Model:
             av_e = self.live_e[j] | self.ghost_e[j]
             self.dh[j][~av_n] = np.nan
             self.u[j][~av_e] = np.nan
+        self._prescribe(self.u)
+
+    def _prescribe(self, u):
+        """Prescribed-velocity mode: the set velocity at every live or ghost edge."""
+        if not self.advect:
+            return
+        for j in self.levels:
+            av_e = self.live_e[j] | self.ghost_e[j]
+            u[j] = np.where(av_e, self.u_set[j], np.nan)
 
     def fill_ghosts(self, dh=None, u=None):
         dh = self.dh if dh is None else dh
@@ -73,6 +95,7 @@ class Model:
         for j in range(self.jmin + 1, self.jmax + 1):
             adapt.prolong_level(self.Hy, self.VS[j], j, dh, u, self.live_n[j], self.live_e[j],
                                 self.ghost_n[j], self.ghost_e[j])
+        self._prescribe(u)
 
     # ------------------------------------------------------------------ wavelet coefficients
     def details(self):
@@ -95,9 +118,15 @@ class Model:
         return hdet, ue, ui
 
     def thresholds(self):
-        mh = max(np.nanmax(np.abs(self.dh[j][self.live_n[j]])) for j in self.levels)
-        mu = max(np.nanmax(np.abs(self.u[j][self.live_e[j]])) for j in self.levels)
-        return self.eps * mh, self.eps * mu
+        # regime 1: eps is the trend tolerance of Sec. 2.3 and the coefficient
+        # thresholds scale as eps^{3/2} (the factor both of the paper's regimes share)
+        e = self.eps * math.sqrt(self.eps) if self.regime == 1 else self.eps
+        # levels without live points contribute nothing
+        mh = max(float(np.nanmax(np.abs(self.dh[j][self.live_n[j]]), initial=0.0)) for j in self.levels)
+        if self.advect:
+            return e * mh, math.inf
+        mu = max(float(np.nanmax(np.abs(self.u[j][self.live_e[j]]), initial=0.0)) for j in self.levels)
+        return e * mh, e * mu
 
     def significance(self, hdet, ue, ui, eps_h, eps_u):
         sig = {}
@@ -169,6 +198,12 @@ class Model:
             for j in self.levels:
                 L = Hy.levels[j]
                 F[j] = trisk.thickness_flux(L, dh[j], u[j], H)
+                if self.advect:
+                    # prescribed velocity: the height flux alone (plus diffusion)
+                    if nu:
+                        F[j] = F[j] - nu * trisk.gradient(L, dh[j])
+                    c[j] = trisk.divergence(L, F[j])
+                    continue
                 q[j] = trisk.potential_vorticity(L, dh[j], u[j], H)
                 B[j] = trisk.bernoulli(L, dh[j], u[j], g)
                 Q[j] = -trisk.coriolis_tendency(L, F[j], q[j])
@@ -183,12 +218,13 @@ class Model:
             for j in range(self.jmax - 1, self.jmin - 1, -1):
                 C, Fl = Hy.levels[j], Hy.levels[j + 1]
                 cov_n = self.covered(j)
-                B[j][cov_n] = B[j + 1][: C.N][cov_n]
-                VS = self.VS[j + 1]
-                h0, h1 = VS.half[:, 0], VS.half[:, 1]
-                s0, s1 = VS.half_sign[:, 0], VS.half_sign[:, 1]
-                cov_e = cov_n[C.edges[:, 0]] & cov_n[C.edges[:, 1]]
-                Q[j][cov_e] = 0.5 * (s0[cov_e] * Q[j + 1][h0[cov_e]] + s1[cov_e] * Q[j + 1][h1[cov_e]])
+                if not self.advect:
+                    B[j][cov_n] = B[j + 1][: C.N][cov_n]
+                    VS = self.VS[j + 1]
+                    h0, h1 = VS.half[:, 0], VS.half[:, 1]
+                    s0, s1 = VS.half_sign[:, 0], VS.half_sign[:, 1]
+                    cov_e = cov_n[C.edges[:, 0]] & cov_n[C.edges[:, 1]]
+                    Q[j][cov_e] = 0.5 * (s0[cov_e] * Q[j + 1][h0[cov_e]] + s1[cov_e] * Q[j + 1][h1[cov_e]])
                 rf = cov_n[C.edges[:, 0]] | cov_n[C.edges[:, 1]]
                 Fint = transform.restrict_flux(self.FS[j + 1], F[j + 1], Fl.l_e, c[j + 1])
                 F[j][rf] = Fint[rf] / C.l_e[rf]
@@ -198,7 +234,7 @@ class Model:
             L = Hy.levels[j]
             with np.errstate(invalid="ignore"):
                 a = -c[j]
-                b = -Q[j] - trisk.gradient(L, B[j])
+                b = np.zeros(L.E) if self.advect else -Q[j] - trisk.gradient(L, B[j])
             a[~self.live_n[j]] = np.nan
             b[~self.live_e[j]] = np.nan
             assert not np.isnan(a[self.live_n[j]]).any(), f"incomplete stencil for a live node at level {j}"
@@ -274,13 +310,14 @@ class Model:
             f = 2.0 * self.Hy.omega * L.xyz[:, 2]
             h = self.H + self.dh[j]
             ln = self.live_n[j]
-            w = np.sqrt(f[ln] ** 2 + self.g * h[ln] * (math.pi / dx) ** 2)
-            wmax = max(wmax, float(w.max()))
+            if not self.advect:
+                w = np.sqrt(f[ln] ** 2 + self.g * h[ln] * (math.pi / dx) ** 2)
+                wmax = max(wmax, float(w.max(initial=0.0)))
             au = np.abs(self.u[j][self.live_e[j]])
             au = au[au > 0]
             if au.size:
                 rmin = min(rmin, float((dx / au).min()))
-        return self.cfl * min(1.0 / wmax, rmin)
+        return self.cfl * min(1.0 / wmax if wmax > 0 else math.inf, rmin)
 
     # ------------------------------------------------------------------ diagnostics
     def mass(self):

@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
                 ("omega", ctypes.c_double), ("g", ctypes.c_double), ("H", ctypes.c_double),
                 ("patch", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double), ("eps", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int), ("precision", ctypes.c_int), ("persistent", ctypes.c_int),
-                ("mask", ctypes.c_int), ("nu", ctypes.c_double)]
+                ("mask", ctypes.c_int), ("nu", ctypes.c_double), ("advect", ctypes.c_int), ("regime", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -164,17 +164,19 @@ class Model:
 
     def __init__(self, jmin, jmax, radius=6.371e6, omega=7.292e-5, g=9.80616, H=1.0e4, patch=8, rk="rk4",
                  cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
-                 mask="lists", nu=0.0):
+                 mask="lists", nu=0.0, advect=False, regime=0):
         """share: another Model whose grid and tables this one reuses (sww_create_shared).
         persistent: True/"auto", "always" (also batched over ensemble members),
         "cluster" (ensemble members' stages as thread-block clusters) or
-        False/"never" (see sww_config.persistent)."""
+        False/"never" (see sww_config.persistent).  advect: prescribed velocity
+        (see sww_config.advect).  regime: 1 scales the thresholds by eps^{3/2}
+        (see sww_config.regime)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
                           blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
                           {True: 0, "auto": 0, "always": 1, "cluster": 2, False: -1, "never": -1}[persistent],
-                          {"lists": 0, "dense": 1}[mask], float(nu))
+                          {"lists": 0, "dense": 1}[mask], float(nu), int(bool(advect)), int(regime))
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()
         if share is None:

@@ -410,6 +410,7 @@ void alloc_state(sww_handle* h, int j) {
     D.zeta = h->alloc<R>(T);
     ck(cudaMemset(D.zeta, 0, T * sizeof(R)), "memset");
     D.nu = h->cfg.nu;
+    D.advect = h->cfg.advect;
     D.ue = h->alloc<R>(coarse_E);
     uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
     for (auto p : bN) *p = h->alloc<uint8_t>(N);
@@ -699,6 +700,10 @@ void mask_and_inverse(sww_handle* h) {
     }
 }
 
+// relative coefficient tolerance: eps, or eps^{3/2} when eps is read as the trend
+// tolerance of Sec. 2.3 (both regimes of the paper scale the thresholds by eps^{3/2})
+double eps_coeff(const sww_config& c) { return c.regime == 1 ? c.eps * std::sqrt(c.eps) : c.eps; }
+
 template <class R>
 void adapt(sww_handle* h, double eh, double eu) {
     cudaStream_t s = h->stream;
@@ -707,7 +712,7 @@ void adapt(sww_handle* h, double eh, double eu) {
         Trace t(h, SWW_K_MASK);
         ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
         launch_maxabs(work_all<R>(h), h->red, s);
-        launch_thresholds(h->red, h->cfg.eps, eh, eu, h->thr, s);
+        launch_thresholds(h->red, eps_coeff(h->cfg), eh, eu, h->cfg.advect, h->thr, s);
     }
     mask_and_inverse<R>(h);
 }
@@ -873,8 +878,12 @@ int guarded(F&& f) {
 
 int check_config(const sww_config* cfg) {
     if (cfg->jmin < 1 || cfg->jmax < cfg->jmin || cfg->jmax > 11) return fail(SWW_E_ARG, "need 1 <= jmin <= jmax <= 11");
-    if (!(cfg->radius > 0) || !(cfg->g > 0) || !(cfg->H > 0) || !(cfg->cfl > 0))
-        return fail(SWW_E_ARG, "radius, g, H and cfl must be positive");
+    if (cfg->advect != 0 && cfg->advect != 1) return fail(SWW_E_ARG, "advect must be 0 or 1");
+    if (cfg->regime != 0 && cfg->regime != 1) return fail(SWW_E_ARG, "regime must be 0 or 1");
+    // a prescribed velocity never divides by the depth, so it may vanish (h = dh)
+    const bool depth_ok = cfg->advect ? cfg->H >= 0 : cfg->H > 0;
+    if (!(cfg->radius > 0) || !(cfg->g > 0) || !depth_ok || !(cfg->cfl > 0))
+        return fail(SWW_E_ARG, "radius, g and cfl must be positive, H positive (>= 0 with advect)");
     if (!(cfg->eps >= 0)) return fail(SWW_E_ARG, "eps must be >= 0 (0: every point significant, no compression)");
     if (cfg->patch < 1 || (cfg->patch & (cfg->patch - 1)) || cfg->patch > 16)
         return fail(SWW_E_ARG, "patch must be a power of two <= 16");

@@ -105,6 +105,7 @@ __device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& 
 // potential vorticity q = (curl u + f)/h at a triangle (dual cell)
 template <class R>
 __device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
+    if (L.advect) return;   // no velocity trend, no q
     int32_t n0 = L.tn[t], n1 = L.tn[L.T + t], n2 = L.tn[2 * L.T + t];
     int32_t c0 = L.te[t], c1 = L.te[L.T + t], c2 = L.te[2 * L.T + t];
     if (!(L.nflag[n0] & AVAIL) || !(L.nflag[n1] & AVAIL) || !(L.nflag[n2] & AVAIL)) return;
@@ -128,9 +129,26 @@ __device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
     if (L.nu != 0.0) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / L.d_e[e];
 }
 
+// divergence of the height flux (with the diffusive flux of the viscous form) at a node
+template <class R>
+__device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
+    if (!(L.nflag[v] & AVAIL)) return;
+    int dg = L.deg[v];
+    R div = R(0);
+    const bool visc = L.nu != 0.0;
+    for (int k = 0; k < dg; ++k) {
+        int32_t code = L.ring_e[k * L.N + v];
+        int64_t e = code >> 1;
+        if (!(L.eflag[e] & AVAIL)) return;
+        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
+    }
+    L.c[v] = div / L.A_i[v];
+}
+
 // divergence, kinetic energy and Bernoulli function at a node
 template <class R>
 __device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
+    if (L.advect) return div_at(L, v);   // prescribed velocity: no Bernoulli function
     if (!(L.nflag[v] & AVAIL)) return;
     int dg = L.deg[v];
     R div = R(0), ke = R(0), du = R(0);
@@ -154,7 +172,7 @@ __device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
 // energy-conserving Coriolis tendency +q F.n_left at a live edge (TRiSK)
 template <class R>
 __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
-    if (!(L.eflag[e] & LIVE)) return;
+    if (L.advect || !(L.eflag[e] & LIVE)) return;
     R qe = R(0.5) * (L.q[L.et[e]] + L.q[L.et[L.E + e]]);
     R s = R(0);
 #pragma unroll
@@ -177,21 +195,6 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
         s -= R(L.nu) * gp / L.l_e[e];
     }
     L.Q[e] = s;
-}
-
-template <class R>
-__device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
-    if (!(L.nflag[v] & AVAIL)) return;
-    int dg = L.deg[v];
-    R div = R(0);
-    const bool visc = L.nu != 0.0;
-    for (int k = 0; k < dg; ++k) {
-        int32_t code = L.ring_e[k * L.N + v];
-        int64_t e = code >> 1;
-        if (!(L.eflag[e] & AVAIL)) return;
-        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
-    }
-    L.c[v] = div / L.A_i[v];
 }
 
 // trend and one Runge-Kutta stage at a live point (terms with a zero coefficient
@@ -218,6 +221,10 @@ __device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, co
 template <class R>
 __device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, const RKStage& st, R dt) {
     if (!(L.eflag[e] & LIVE)) return;
+    if (L.advect) {   // prescribed velocity: zero trend, u untouched
+        L.ut[e] = R(0);
+        return;
+    }
     R k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
     L.ut[e] = k;
     if (st.apply) rk_apply(st, dt, k, &L.u[e], &L.u0[e], &L.ua[e]);
@@ -246,7 +253,7 @@ __device__ __forceinline__ void fill_node(const DevLevelT<R>& F, const DevLevelT
 
 template <class R>
 __device__ __forceinline__ void fill_edge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i) {
-    if (!(F.eflag[i] & GHOST)) return;
+    if (F.advect || !(F.eflag[i] & GHOST)) return;   // prescribed velocity is kept everywhere
     int kind = F.fe_kind[i];
     R P = predict(F, C.u, i);
     if (kind == 2) {
@@ -274,7 +281,7 @@ __device__ __forceinline__ void fill_edge(const DevLevelT<R>& F, const DevLevelT
 template <class R>
 __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLevelT<R>& F, int kind, int64_t id) {
     if (kind == K_NODE) {
-        if (L.nflag[id] & COVERED) L.B[id] = F.B[L.c2f[id]];
+        if (!L.advect && (L.nflag[id] & COVERED)) L.B[id] = F.B[L.c2f[id]];
         return;
     }
     int64_t i = id;
@@ -294,7 +301,7 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
         L.F[i] = s / L.l_e[i];
         if (visc) L.Fd[i] = R(0);
     }
-    if (ca && cb) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
+    if (ca && cb && !L.advect) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
 }
 
 // ---------------------------------------------------------------------------- mask items (Sec. 2.3)

@@ -28,6 +28,7 @@ struct DevLevelT {
     int64_t n, p, np, nelem, N, E, T, npatch;
     double dx;                     // Table 1 spacing of the level (m)
     double nu;                     // viscosity (m^2/s) of the viscous form; 0: inviscid
+    int advect;                    // 1: prescribed velocity (advection test case): u never changes
     // topology
     const int32_t *en, *et;        // [2*E] origin/end node, left/right triangle
     const int32_t *tn, *te;        // [3*T] nodes, side edges (2e + against)

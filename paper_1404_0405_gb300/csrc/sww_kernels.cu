@@ -166,7 +166,7 @@ __global__ void k_inverse_a(DevLevelT<R> F, DevLevelT<R> C, const int32_t* list,
             return;
         }
         int64_t i = id;
-        if (!(L.eflag[i] & LIVE)) return;
+        if (L.advect || !(L.eflag[i] & LIVE)) return;   // a prescribed velocity is kept as set
         int fk = L.fe_kind[i];
         R Pr = predict(L, C.u, i);
         if (fk == 2) {
@@ -242,7 +242,8 @@ __global__ void k_maxabs(const DevLevelT<R>* __restrict__ lvs, const int32_t* li
     if (threadIdx.x == 0 && b) atomicMax(&red[1], b);
 }
 
-// omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max), dx/|u| at live edges (min)
+// omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max; none with a prescribed
+// velocity, which carries no waves), dx/|u| at live edges (min)
 template <class R>
 __global__ void k_dt(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H,
                      double g, unsigned long long* red) {
@@ -251,7 +252,7 @@ __global__ void k_dt(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, 
     unsigned long long a = 0, b = ~0ull;
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
         if (kind == K_NODE) {
-            if (!(L.nflag[id] & LIVE)) return;
+            if (L.advect || !(L.nflag[id] & LIVE)) return;
             double f = double(L.f_n[id]), kx = M_PI / L.dx;
             a = max(a, dbits(sqrt(f * f + g * (H + double(L.dh[id])) * kx * kx)));
         } else if (L.eflag[id] & LIVE) {
@@ -272,10 +273,13 @@ __global__ void k_dt_final(const unsigned long long* red, double cfl, double* dt
     *dt = cfl * fmin(1.0 / w, r);
 }
 
-__global__ void k_thresholds(const unsigned long long* red, double eps, double eps_h, double eps_u, double* thr) {
+// a prescribed velocity takes no part in the significance test (eps_u infinite
+// unless given)
+__global__ void k_thresholds(const unsigned long long* red, double eps, double eps_h, double eps_u, int advect,
+                             double* thr) {
     if (threadIdx.x || blockIdx.x) return;
     thr[0] = eps_h > 0 ? eps_h : eps * __longlong_as_double(static_cast<long long>(red[0]));
-    thr[1] = eps_u > 0 ? eps_u : eps * __longlong_as_double(static_cast<long long>(red[1]));
+    thr[1] = eps_u > 0 ? eps_u : advect ? INFINITY : eps * __longlong_as_double(static_cast<long long>(red[1]));
 }
 
 // Neumaier-compensated partial sums of mass and energy over level Jmin (dense)
@@ -608,9 +612,10 @@ void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cuda
     g_launches++;
     k_dt_final<<<1, 32, 0, s>>>(red, cfl, dt);
 }
-void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s) {
+void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, int advect, double* thr,
+                       cudaStream_t s) {
     g_launches++;
-    k_thresholds<<<1, 32, 0, s>>>(red, eps, eh, eu, thr);
+    k_thresholds<<<1, 32, 0, s>>>(red, eps, eh, eu, advect, thr);
 }
 
 template <class R>

@@ -71,7 +71,8 @@ template <class R> void launch_inverse(const DevLevelT<R>& F, const DevLevelT<R>
 template <class R> void launch_maxabs(const WorkT<R>& W, unsigned long long* red, cudaStream_t s);
 template <class R> void launch_dt(const WorkT<R>& W, double H, double g, unsigned long long* red, cudaStream_t s);
 void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
-void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, double* thr, cudaStream_t s);
+void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, int advect, double* thr,
+                       cudaStream_t s);
 
 // dense level kernels (masks, initialisation, diagnostics)
 template <class R> void launch_restrict_full(const DevLevelT<R>& C, const DevLevelT<R>& F, cudaStream_t s);

@@ -31,18 +31,21 @@ def rel_err(a, b):
 class Pair:
     """An oracle model and a library model on the same grid and initial state."""
 
-    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64", nu=0.0):
+    def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64", nu=0.0,
+                 advect=False, alpha=0.0, persistent=True, regime=0):
         import paper_1404_0405_gb300 as sww
         self.sww = sww
         self.Hy = grid.Hierarchy(jmin, jmax)
-        self.ora = model.Model(self.Hy, eps=eps, rk=rk, nu=nu)
-        self.lib = sww.Model(jmin, jmax, patch=patch, eps=eps, rk=rk, precision=precision, nu=nu)
+        H = 0.0 if advect else 1.0e4       # the advection test carries the bell itself
+        self.ora = model.Model(self.Hy, H=H, eps=eps, rk=rk, nu=nu, advect=advect, regime=regime)
+        self.lib = sww.Model(jmin, jmax, H=H, patch=patch, eps=eps, rk=rk, precision=precision, nu=nu,
+                             advect=advect, persistent=persistent, regime=regime)
         self.maps = {}
         for j in range(jmin, jmax + 1):
             xyz, en = self.lib.grid(j)
             self.maps[j] = LevelMap(xyz, en, self.Hy.levels[j])
         L = self.Hy.levels[jmax]
-        W = workloads.Workload(kind, seed=seed)
+        W = workloads.Workload(kind, seed=seed, alpha=alpha)
         dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
         self.ora.set_uniform(dh, u)
         M = self.maps[jmax]
@@ -144,6 +147,17 @@ def test_adapt_masks_bit_exact(built, kind, seed):
     if kind == "jet":
         live = sum(P.ora.live_n[j].sum() for j in P.ora.levels)
         assert live < sum(P.Hy.levels[j].N for j in P.ora.levels)
+
+
+def test_trend_tolerance_regime(built):
+    """regime 1: thresholds from eps^{3/2} (eps = 0.05 gives about 0.0112 relative)."""
+    P = Pair(2, 4, kind="jet", seed=2, eps=0.05, regime=1)
+    P.adapt()
+    st = P.lib.stats()
+    assert abs(st["eps_h"] / P.ora.eps_h - 1) < 1e-12 and abs(st["eps_u"] / P.ora.eps_u - 1) < 1e-12
+    assert abs(P.ora.eps_h / (0.05 * math.sqrt(0.05) * np.nanmax(np.abs(P.ora.dh[2]))) - 1) < 0.2
+    P.check_masks()
+    P.check_fields()
 
 
 def test_mask_from_identical_coefficients(built):
@@ -250,4 +264,39 @@ def test_viscous_adaptive_steps_match(built):
         P.lib.step(dt, 1, adapt=True)
         P.check_masks()
         P.check_fields()
+    assert abs(P.lib.stats()["mass"] / m0 - 1) < 1e-14
+
+
+# ----------------------------------------------------------------------------- prescribed velocity (Sec. 7.1)
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_advect_trend_matches(built, persistent):
+    """Advection of the cosine bell by the tilted rotation: depth trend through the
+    flux restriction, zero velocity trend on both sides."""
+    P = Pair(2, 4, kind="tc1_cosine", eps=0.02, advect=True, alpha=math.pi / 4, persistent=persistent)
+    P.adapt()
+    assert P.lib.stats()["eps_u"] == math.inf and P.ora.eps_u == math.inf
+    P.check_masks()
+    P.rhs()
+    P.check_fields(which="trend")
+    for j in range(2, 5):
+        assert np.all(P.maps[j].edges_to_ora(P.lib.get(j, P.sww.U_T))[P.ora.live_e[j]] == 0.0)
+
+
+@pytest.mark.parametrize("kind,rk", [("tc1_cosine", "rk4"), ("tc1_smooth", "ssp43")])
+def test_advect_adaptive_steps_match(built, kind, rk):
+    P = Pair(2, 4, kind=kind, rk=rk, eps=0.02, advect=True, alpha=math.pi / 4)
+    P.adapt()
+    u_set = {j: P.lib.get(j, P.sww.U).copy() for j in range(2, 5)}
+    m0 = P.lib.stats()["mass"]
+    for _ in range(4):
+        dt_o = P.ora.dt_cfl()
+        P.ora.step(dt_o)
+        P.lib.step(-1.0, 1, adapt=True)
+        assert abs(P.lib.stats()["dt"] / dt_o - 1) < 1e-12
+        P.check_masks()
+        P.check_fields()
+    for j in range(2, 5):
+        assert np.array_equal(P.lib.get(j, P.sww.U), u_set[j])   # never written
     assert abs(P.lib.stats()["mass"] / m0 - 1) < 1e-14

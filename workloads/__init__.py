@@ -15,6 +15,13 @@ Workloads (all seeded; numpy PCG64):
     height bumps of 120 m (e-folding radius 500 km) at seeded sites.
   * ``tc2``: Williamson test case 2 (solid-body zonal flow, u0 = 2 pi R / 12 d,
     g*H = 2.94e4 m^2/s^2), depth from the same gradient-wind balance.
+  * ``tc1_cosine`` / ``tc1_smooth``: the advection test of Sec. 7.1 -- a bell
+    of height 1000 m and radius L = R/3 centred at lat 0, lon 0 (the cosine
+    bell (H/2)(1 + cos(pi r/L)) for r < L, or the smooth bell
+    H exp(r^2/(r^2 - 2 L^2)) for r < sqrt(2) L; zero outside, the reading of
+    both), carried by solid-body rotation of speed U = 2 pi R / 12 d about an
+    axis tilted by ``alpha`` from the pole.  The depth is the bell itself
+    (``mean_depth`` 0); ``exact(xyz, t)`` is the bell rotated by U t / R.
 """
 from __future__ import annotations
 
@@ -122,7 +129,7 @@ class Workload:
     dh is the depth perturbation about ``mean_depth``.
     """
 
-    def __init__(self, kind, seed=0, radius=6.371e6, omega=7.292e-5, g=9.80616, mean_depth=1.0e4):
+    def __init__(self, kind, seed=0, radius=6.371e6, omega=7.292e-5, g=9.80616, mean_depth=1.0e4, alpha=0.0):
         self.kind, self.seed = kind, seed
         self.radius, self.omega, self.g, self.mean_depth = radius, omega, g, mean_depth
         rng = np.random.Generator(np.random.PCG64(seed))
@@ -144,6 +151,14 @@ class Workload:
             self.bumps = np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)], axis=-1)
             self.bump_amp, self.bump_radius = 120.0, 5.0e5
             self._h = _zonal_balance(self._ujet, radius, omega, g, mean_depth)
+        elif kind in ("tc1_cosine", "tc1_smooth"):
+            self.mean_depth = 0.0
+            self.u0 = 2.0 * math.pi * radius / (12.0 * DAY)
+            self.bell_h, self.bell_L = 1000.0, radius / 3.0
+            self.alpha = alpha
+            # v = U a x r^ with the unit axis a: east component U (cos(lat) cos(alpha)
+            # + sin(lat) cos(lon) sin(alpha)), north component -U sin(lon) sin(alpha)
+            self.axis = np.array([-math.sin(alpha), 0.0, math.cos(alpha)])
         elif kind == "tc2":
             self.u0 = 2.0 * math.pi * radius / (12.0 * DAY)
             gH = 2.94e4
@@ -154,9 +169,27 @@ class Workload:
     def _ujet(self, lat):
         return self.u0 * np.exp(-(((lat - self.lat0) / self.width) ** 2))
 
+    def _bell(self, xyz):
+        xyz = np.asarray(xyz, dtype=np.float64)
+        xyz = xyz / np.linalg.norm(xyz, axis=-1, keepdims=True)
+        r = self.radius * np.arccos(np.clip(xyz[..., 0], -1.0, 1.0))   # distance to lat 0, lon 0
+        H, L = self.bell_h, self.bell_L
+        if self.kind == "tc1_cosine":
+            return np.where(r < L, 0.5 * H * (1.0 + np.cos(math.pi * np.minimum(r, L) / L)), 0.0)
+        inside = r < math.sqrt(2.0) * L
+        rr = np.where(inside, r, 0.0)
+        return np.where(inside, H * np.exp(rr * rr / (rr * rr - 2.0 * L * L)), 0.0)
+
+    def exact(self, xyz, t):
+        """Depth at time t of the advection test: the initial bell rotated by U t / R."""
+        back = _rotate(np.asarray(xyz, dtype=np.float64), self.axis, -self.u0 * t / self.radius)
+        return self._bell(back)
+
     def depth(self, xyz):
         """Total depth h at unit-sphere points."""
         xyz = np.asarray(xyz, dtype=np.float64)
+        if self.kind.startswith("tc1"):
+            return self._bell(xyz)
         if self.kind == "harmonic":
             return self.mean_depth + self._scale * self._harm(xyz)
         lat, _ = _latlon(xyz)
@@ -175,6 +208,9 @@ class Workload:
             psi = lambda p: self.g * self._scale * self._harm(p) / self.f0
             # u = k x grad(psi);  u . t = -d psi / d n_left
             return -_normal_derivative(psi, mid, tan, self.radius)
+        if self.kind.startswith("tc1"):
+            m = mid / np.linalg.norm(mid, axis=-1, keepdims=True)
+            return self.u0 * np.sum(np.cross(self.axis, m) * tan, axis=-1)
         east, _ = _east_north(mid)
         lat, _ = _latlon(mid)
         uz = self._ujet(lat) if self.kind == "jet" else self.u0 * np.cos(lat)
