@@ -203,6 +203,45 @@ int sww_get_level(const sww_handle* h, int level, int what, void* out);
 /* Write the depth perturbation and velocity of level j (host arrays). */
 int sww_set_level(sww_handle* h, int level, const double* dh, const double* u);
 
+/* Forward wavelet transform of the active grid (Eqs. 1-2 and the velocity
+ * transform of Sec. 4.1): the coefficients of every live point above Jmin into
+ * the coefficient buffers (h~ at odd nodes, the pair coefficient per coarse edge,
+ * u~ at interior fine edges), read with sww_get_coeffs.  The state is unchanged. */
+int sww_forward(sww_handle* h);
+
+/* Inverse wavelet transform onto the current live set, coarse to fine: the live
+ * points of each level above Jmin are rebuilt from the level below and the
+ * stored coefficients of live points (set by sww_forward, sww_adapt or
+ * sww_set_coeffs), ghosts refilled.  Inverse after forward returns the state to
+ * rounding.  A prescribed velocity (advect) is left as set. */
+int sww_inverse(sww_handle* h);
+
+/* Coefficients of level j > Jmin: hdet[N_j] (values at odd nodes, 0 elsewhere),
+ * udet_e[E_{j-1}], udet_i[E_j] (interior fine edges); any pointer may be null.
+ * sww_get_coeffs copies them to the host, sww_set_coeffs writes them for the
+ * next sww_inverse.  SWW_E_ARG for j = Jmin. */
+int sww_get_coeffs(const sww_handle* h, int level, double* hdet, double* udet_e, double* udet_i);
+int sww_set_coeffs(sww_handle* h, int level, const double* hdet, const double* udet_e, const double* udet_i);
+
+/* The state on the full level j (dh[N_j], u[E_j], host arrays; either may be
+ * null): live points keep their values, every other point is the inverse
+ * transform with zero coefficients of the full level j-1, recursively from Jmin
+ * (Sec. 2.2).  Uses the RK base arrays as scratch, so it runs between steps only
+ * (as every call does). */
+int sww_get_state(sww_handle* h, int level, double* dh, double* u);
+
+/* Checkpoint / resume.  sww_save writes the model time, step count, last dt and
+ * thresholds, and per level the depth, velocity (working precision, ghosts
+ * included) and node/edge flags to a binary file (little-endian as written by
+ * this host: "SWWCKPT1", a fixed header, the levels Jmin..Jmax, "SWWCKEND").
+ * sww_load reads one into a handle of the same Jmin, Jmax, patch, radius, omega
+ * and precision (else SWW_E_ARG; other settings are the handle's own), clears
+ * the per-adaptation scratch and rebuilds the patch lists; stepping then
+ * continues as the saved handle would, bit for bit.  A truncated or foreign file
+ * is SWW_E_ARG and leaves the handle unchanged. */
+int sww_save(const sww_handle* h, const char* path);
+int sww_load(sww_handle* h, const char* path);
+
 /* Active patch list of level j (ascending patch ids) into out[n_patches];
  * *count receives its length. */
 int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count);

@@ -174,6 +174,22 @@ class Model:
             adapt.prolong_level(Hy, VS, j, self.dh, self.u, live_n[j], live_e[j], ghost_n[j], ghost_e[j])
         self._mask_values()
 
+    def get_uniform(self, J):
+        """Fields of the full level J (Sec. 2.2): live points keep their values,
+        every other point takes the inverse transform with zero coefficients of
+        the full level J-1, from Jmin (always full) up.  A prescribed velocity is
+        returned as set."""
+        dh = {self.jmin: self.dh[self.jmin].copy()}
+        u = {self.jmin: self.u[self.jmin].copy()}
+        for j in range(self.jmin + 1, J + 1):
+            dh[j] = np.where(self.live_n[j], self.dh[j], 0.0)
+            u[j] = np.where(self.live_e[j], self.u[j], 0.0)
+            adapt.prolong_level(self.Hy, self.VS[j], j, dh, u, self.live_n[j], self.live_e[j],
+                                ~self.live_n[j], ~self.live_e[j])
+            if self.advect:
+                u[j] = self.u_set[j].copy()
+        return dh[J], u[J]
+
     # ------------------------------------------------------------------ trend
     def covered(self, j):
         """Coarse nodes of level j whose restriction stencil is complete at j+1: the

@@ -29,7 +29,8 @@ EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
            "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
            "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
-           "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict"]
+           "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
+           "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
@@ -99,6 +100,13 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_mlp_loss_grad": [P, P, ctypes.c_int64, P, ctypes.c_float, P, P, P],
         "sww_mlp_adam": [P, P, P, P, I, ctypes.c_float, P],
         "sww_mlp_predict": [P, ctypes.c_int64, P, P, P],
+        "sww_forward": [P],
+        "sww_inverse": [P],
+        "sww_get_coeffs": [P, I, P, P, P],
+        "sww_set_coeffs": [P, I, P, P, P],
+        "sww_get_state": [P, I, P, P],
+        "sww_save": [P, ctypes.c_char_p],
+        "sww_load": [P, ctypes.c_char_p],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -252,6 +260,39 @@ class Model:
             raise ValueError(what)
         _check(load().sww_get_level(self._h, level, what, _ptr(out)[0]))
         return out
+
+    def forward(self):
+        _check(load().sww_forward(self._h))
+
+    def inverse(self):
+        _check(load().sww_inverse(self._h))
+
+    def coeffs(self, level):
+        """(hdet[N_j], udet_e[E_{j-1}], udet_i[E_j]) of level j > Jmin."""
+        N, E, _, _ = self.sizes(level)
+        Ec = self.sizes(level - 1)[1]
+        out = (np.empty(N), np.empty(Ec), np.empty(E))
+        _check(load().sww_get_coeffs(self._h, level, *[o.ctypes.data_as(ctypes.c_void_p) for o in out]))
+        return out
+
+    def set_coeffs(self, level, hdet=None, udet_e=None, udet_i=None):
+        args = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (hdet, udet_e, udet_i)]
+        _check(load().sww_set_coeffs(self._h, level, *[None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+                                                         for a in args]))
+
+    def get_state(self, level):
+        """(dh[N_j], u[E_j]) on the full level j (zero coefficients away from live points)."""
+        N, E, _, _ = self.sizes(level)
+        dh, u = np.empty(N), np.empty(E)
+        _check(load().sww_get_state(self._h, level, dh.ctypes.data_as(ctypes.c_void_p),
+                                    u.ctypes.data_as(ctypes.c_void_p)))
+        return dh, u
+
+    def save(self, path):
+        _check(load().sww_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        _check(load().sww_load(self._h, os.fsencode(path)))
 
     def set_level(self, level, dh=None, u=None):
         a = None if dh is None else np.ascontiguousarray(dh, dtype=np.float64)

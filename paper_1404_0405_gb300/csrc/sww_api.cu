@@ -1343,6 +1343,246 @@ int sww_set_level(sww_handle* h, int level, const double* dh, const double* u) {
     });
 }
 
+int sww_forward(sww_handle* h) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    return guarded([&]() -> int {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
+            Join jn(h);
+            Trace t(h, SWW_K_COEFF);
+            launch_details(work_all<R>(h), h->cfg.jmin, h->stream);
+            check_launch();
+            return 0;
+        });
+        ck(cudaStreamSynchronize(h->stream), "forward");
+        return SWW_OK;
+    });
+}
+
+int sww_inverse(sww_handle* h) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    return guarded([&]() -> int {
+        by_prec(h, [&](auto r) {
+            using R = decltype(r);
+            Join jn(h);
+            auto& lv = lvl<R>(h);
+            cudaStream_t s = h->stream;
+            launch_mark_support(work_all<R>(h), s);
+            for (int j = h->cfg.jmin + 1; j <= h->jtop; ++j) {
+                { Trace t(h, SWW_K_INVERSE); launch_inverse(lv[j], lv[j - 1], work_level<R>(h, j), s); }
+                { Trace t(h, SWW_K_FILL); launch_fill(lv[j], lv[j - 1], work_level<R>(h, j), s); }
+            }
+            check_launch();
+            return 0;
+        });
+        ck(cudaStreamSynchronize(h->stream), "inverse");
+        return SWW_OK;
+    });
+}
+
+int sww_get_coeffs(const sww_handle* h, int level, double* hdet, double* udet_e, double* udet_i) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (level == h->cfg.jmin) return fail(SWW_E_ARG, "no coefficients on Jmin");
+    if (hdet && (rc = sww_get_level(h, level, SWW_HDET, hdet))) return rc;
+    if (udet_e && (rc = sww_get_level(h, level, SWW_UDET_E, udet_e))) return rc;
+    if (udet_i && (rc = sww_get_level(h, level, SWW_UDET_I, udet_i))) return rc;
+    return SWW_OK;
+}
+
+int sww_set_coeffs(sww_handle* h, int level, const double* hdet, const double* udet_e, const double* udet_i) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (level == h->cfg.jmin) return fail(SWW_E_ARG, "no coefficients on Jmin");
+    return guarded([&]() -> int {
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            const DevLevelT<R>& L = lvl<R>(h)[level];
+            {
+                Join jn(h);
+                if (hdet) to_device(h, L.hdet, hdet, L.N);
+                if (udet_e) to_device(h, L.ue, udet_e, meta(h, level - 1).E);
+                if (udet_i) to_device(h, L.ui, udet_i, L.E);
+            }
+            ck(cudaStreamSynchronize(h->stream), "set_coeffs");
+            return SWW_OK;
+        });
+    });
+}
+
+int sww_get_state(sww_handle* h, int level, double* dh, double* u) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (!h->has_state) return fail(SWW_E_STATE, "sww_set_state first");
+    return guarded([&]() -> int {
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            auto& lv = lvl<R>(h);
+            const int j0 = h->cfg.jmin;
+            // the full levels above Jmin go to the RK base arrays, which hold nothing
+            // between steps; Jmin is always full
+            {
+                Join jn(h);
+                for (int j = j0 + 1; j <= level; ++j) {
+                    const R* cdh = j - 1 == j0 ? lv[j0].dh : lv[j - 1].dh0;
+                    const R* cu = j - 1 == j0 ? lv[j0].u : lv[j - 1].u0;
+                    launch_uniform(lv[j], lv[j - 1], cdh, cu, lv[j].dh0, lv[j].u0, h->stream);
+                }
+                check_launch();
+            }
+            const DevLevelT<R>& L = lv[level];
+            if (dh) from_device(h, dh, level == j0 ? L.dh : L.dh0, L.N);
+            if (u) from_device(h, u, level == j0 ? L.u : L.u0, L.E);
+            ck(cudaStreamSynchronize(h->stream), "get_state");
+            return SWW_OK;
+        });
+    });
+}
+
+// ---------------------------------------------------------------- checkpoints
+// File: "SWWCKPT1", then the header below, then per level Jmin..Jmax the depth,
+// velocity (working precision), node flags and edge flags, then "SWWCKEND".
+namespace {
+struct CkptHeader {
+    uint32_t version, precision;
+    int32_t jmin, jmax, patch, reserved;
+    double radius, omega, t, dt, eps_h, eps_u;
+    int64_t steps;
+};
+const char CKPT_MAGIC[8] = {'S', 'W', 'W', 'C', 'K', 'P', 'T', '1'};
+const char CKPT_END[8] = {'S', 'W', 'W', 'C', 'K', 'E', 'N', 'D'};
+
+struct File {
+    FILE* f;
+    File(const char* path, const char* mode) : f(std::fopen(path, mode)) {}
+    ~File() {
+        if (f) std::fclose(f);
+    }
+    bool put(const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+    bool get(void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+};
+}  // namespace
+
+int sww_save(const sww_handle* hc, const char* path) {
+    if (!hc || !path) return fail(SWW_E_ARG, "null argument");
+    if (!hc->has_state) return fail(SWW_E_STATE, "nothing to save before sww_set_state");
+    sww_handle* h = const_cast<sww_handle*>(hc);
+    return guarded([&]() -> int {
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            File out(path, "wb");
+            if (!out.f) return fail(SWW_E_ARG, std::string("cannot open ") + path);
+            double thr[2];
+            {
+                Join jn(h);
+                ck(cudaMemcpyAsync(thr, h->thr, sizeof(thr), cudaMemcpyDeviceToHost, h->stream), "save thr");
+            }
+            ck(cudaStreamSynchronize(h->stream), "save");
+            CkptHeader hd{1u, uint32_t(h->cfg.precision), h->cfg.jmin, h->cfg.jmax, h->cfg.patch, 0,
+                          h->cfg.radius, h->cfg.omega, h->t, h->last_dt, thr[0], thr[1], h->steps};
+            bool ok = out.put(CKPT_MAGIC, 8) && out.put(&hd, sizeof(hd));
+            std::vector<R> buf;
+            std::vector<uint8_t> bytes;
+            for (int j = h->cfg.jmin; ok && j <= h->cfg.jmax; ++j) {
+                const DevLevelT<R>& L = lvl<R>(h)[j];
+                const int64_t ne[2] = {L.N, L.E};
+                ok = out.put(ne, sizeof(ne));
+                const R* fields[2] = {L.dh, L.u};
+                const uint8_t* flags[2] = {L.nflag, L.eflag};
+                for (int k = 0; ok && k < 2; ++k) {
+                    buf.resize(size_t(ne[k]));
+                    ck(cudaMemcpyAsync(buf.data(), fields[k], ne[k] * sizeof(R), cudaMemcpyDeviceToHost, h->stream),
+                       "save field");
+                    ck(cudaStreamSynchronize(h->stream), "save field");
+                    ok = out.put(buf.data(), ne[k] * sizeof(R));
+                }
+                for (int k = 0; ok && k < 2; ++k) {
+                    bytes.resize(size_t(ne[k]));
+                    ck(cudaMemcpyAsync(bytes.data(), flags[k], ne[k], cudaMemcpyDeviceToHost, h->stream), "save flags");
+                    ck(cudaStreamSynchronize(h->stream), "save flags");
+                    ok = out.put(bytes.data(), ne[k]);
+                }
+            }
+            ok = ok && out.put(CKPT_END, 8);
+            if (!ok) return fail(SWW_E_ARG, std::string("write failed: ") + path);
+            return SWW_OK;
+        });
+    });
+}
+
+int sww_load(sww_handle* h, const char* path) {
+    if (!h || !path) return fail(SWW_E_ARG, "null argument");
+    return guarded([&]() -> int {
+        return by_prec(h, [&](auto r) -> int {
+            using R = decltype(r);
+            File in(path, "rb");
+            if (!in.f) return fail(SWW_E_ARG, std::string("cannot open ") + path);
+            char magic[8];
+            CkptHeader hd{};
+            if (!in.get(magic, 8) || std::memcmp(magic, CKPT_MAGIC, 8) || !in.get(&hd, sizeof(hd)) || hd.version != 1)
+                return fail(SWW_E_ARG, "not a checkpoint of this library");
+            if (hd.precision != uint32_t(h->cfg.precision) || hd.jmin != h->cfg.jmin || hd.jmax != h->cfg.jmax ||
+                hd.patch != h->cfg.patch || hd.radius != h->cfg.radius || hd.omega != h->cfg.omega)
+                return fail(SWW_E_ARG, "checkpoint grid or precision differs from the handle's");
+            // read everything before touching the device state
+            const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
+            std::vector<std::vector<R>> fld(2 * (j1 + 1));
+            std::vector<std::vector<uint8_t>> flg(2 * (j1 + 1));
+            for (int j = j0; j <= j1; ++j) {
+                const DevLevelT<R>& L = lvl<R>(h)[j];
+                int64_t ne[2];
+                if (!in.get(ne, sizeof(ne)) || ne[0] != L.N || ne[1] != L.E)
+                    return fail(SWW_E_ARG, "checkpoint level sizes differ");
+                for (int k = 0; k < 2; ++k) {
+                    fld[2 * j + k].resize(size_t(ne[k]));
+                    if (!in.get(fld[2 * j + k].data(), ne[k] * sizeof(R))) return fail(SWW_E_ARG, "truncated checkpoint");
+                }
+                for (int k = 0; k < 2; ++k) {
+                    flg[2 * j + k].resize(size_t(ne[k]));
+                    if (!in.get(flg[2 * j + k].data(), ne[k])) return fail(SWW_E_ARG, "truncated checkpoint");
+                }
+            }
+            if (!in.get(magic, 8) || std::memcmp(magic, CKPT_END, 8)) return fail(SWW_E_ARG, "truncated checkpoint");
+            cudaStream_t s = h->stream;
+            {
+                Join jn(h);
+                auto& lv = lvl<R>(h);
+                for (int j = j0; j <= j1; ++j) {
+                    const DevLevelT<R>& L = lv[j];
+                    ck(cudaMemcpyAsync(L.dh, fld[2 * j].data(), L.N * sizeof(R), cudaMemcpyHostToDevice, s), "load");
+                    ck(cudaMemcpyAsync(L.u, fld[2 * j + 1].data(), L.E * sizeof(R), cudaMemcpyHostToDevice, s), "load");
+                    ck(cudaMemcpyAsync(L.nflag, flg[2 * j].data(), L.N, cudaMemcpyHostToDevice, s), "load");
+                    ck(cudaMemcpyAsync(L.eflag, flg[2 * j + 1].data(), L.E, cudaMemcpyHostToDevice, s), "load");
+                    // per-mask scratch starts clean (the list mask expects it zero away
+                    // from its candidates)
+                    uint8_t* nbytes[] = {L.sig, L.tmask, L.band0, L.band1};
+                    for (auto p : nbytes) ck(cudaMemsetAsync(p, 0, L.N, s), "load scratch");
+                    uint8_t* pbytes[] = {L.zflag, L.sflag, L.cflag, L.lflag, L.gflag, L.prop, L.prop_prev, L.pexact};
+                    for (auto p : pbytes) ck(cudaMemsetAsync(p, 0, L.npatch + 1, s), "load scratch");
+                }
+                ck(cudaMemsetAsync(h->cand_count, 0, sizeof(int32_t), s), "load scratch");
+                ck(cudaMemsetAsync(h->gcand_count, 0, sizeof(int32_t), s), "load scratch");
+                const double thr[2] = {hd.eps_h, hd.eps_u};
+                ck(cudaMemcpyAsync(h->thr, thr, sizeof(thr), cudaMemcpyHostToDevice, s), "load thr");
+                MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
+                launch_patches_all(dlv<R>(h), a.patches, s);
+                launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);
+                read_counts<R>(h);
+                check_launch();
+                ck(cudaStreamSynchronize(s), "load");   // host buffers live on this frame
+            }
+            update_top(h);
+            h->has_state = true;
+            h->t = hd.t;
+            h->last_dt = hd.dt;
+            h->steps = hd.steps;
+            return SWW_OK;
+        });
+    });
+}
+
 int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count) {
     int rc = check_level(h, level);
     if (rc) return rc;

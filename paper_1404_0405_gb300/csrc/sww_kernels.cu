@@ -392,6 +392,64 @@ __global__ void k_restrict_full(DevLevelT<R> C, DevLevelT<R> F) {
     if (i < C.E) C.u[i] = R(0.5) * (F.u[C.half[i]] + F.u[C.half[C.E + i]]);
 }
 
+// level F in full (Sec. 2.2): live points keep their values, every other point takes
+// the inverse transform with zero coefficients of the full level below (cdh, cu;
+// C gives the coarse half-edge table).  By the graded closure no live coefficient
+// touches a non-live even node, which therefore takes the coarse value.  A
+// prescribed velocity is kept as set.
+template <class R>
+__global__ void k_uniform(DevLevelT<R> F, DevLevelT<R> C, const R* __restrict__ cdh, const R* __restrict__ cu,
+                          R* __restrict__ odh, R* __restrict__ ou) {
+    const int64_t i = gid();
+    if (i < F.N) {
+        R v;
+        if (F.nflag[i] & LIVE) {
+            v = F.dh[i];
+        } else if (F.f2c[i] >= 0) {
+            v = cdh[F.f2c[i]];
+        } else {
+            v = R(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int32_t p = F.par[q * F.N + i];
+                v += F.ptw[q * F.N + i] * ((F.nflag[p] & LIVE) ? F.dh[p] : cdh[F.f2c[p]]);
+            }
+        }
+        odh[i] = v;
+    }
+    if (i < F.E) {
+        R v;
+        if (F.advect || (F.eflag[i] & LIVE)) {
+            v = F.u[i];
+        } else {
+            const R P = predict(F, cu, i);
+            const int kind = F.fe_kind[i];
+            if (kind == 2) {
+                v = P;
+            } else {
+                const int64_t E = F.fe_ce[i];
+                const int32_t other = C.half[(kind == 0 ? C.E : 0) + E];
+                const R uc = cu[E];
+                v = (F.eflag[other] & LIVE) ? R(2) * uc - F.u[other]
+                                            : P + R(0.5) * (R(2) * uc - P - predict(F, cu, other));
+            }
+        }
+        ou[i] = v;
+    }
+}
+
+// the current live set becomes the support of the stored coefficients (WASLIVE),
+// so that an inverse transform without adaptation uses every live coefficient
+template <class R>
+__global__ void k_mark_support(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count,
+                               int P) {
+    DevLevelT<R> none{};
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
+        uint8_t* f = kind == K_NODE ? &L.nflag[id] : &L.eflag[id];
+        *f = uint8_t((*f & ~WASLIVE) | ((*f & LIVE) ? WASLIVE : 0));
+    });
+}
+
 // Dense multi-level mask kernels (bodies in sww_bodies.cuh).  sig_any[j] records
 // whether level j holds a significant point.
 template <class R>
@@ -622,6 +680,15 @@ template <class R>
 void launch_restrict_full(const DevLevelT<R>& C, const DevLevelT<R>& F, cudaStream_t s) {
     DENSE(k_restrict_full<R>, span(C), C, F);
 }
+template <class R>
+void launch_uniform(const DevLevelT<R>& F, const DevLevelT<R>& C, const R* cdh, const R* cu, R* odh, R* ou,
+                    cudaStream_t s) {
+    DENSE(k_uniform<R>, span(F), F, C, cdh, cu, odh, ou);
+}
+template <class R>
+void launch_mark_support(const WorkT<R>& W, cudaStream_t s) {
+    LIST(k_mark_support<R>, W.lvs, W.list, W.count, W.S);
+}
 #define MULTI(kernel, sp, ...)                                                  \
     do {                                                                        \
         int64_t n_ = (sp).off[(sp).jb + 1 - (sp).ja];                           \
@@ -736,6 +803,9 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
     template void launch_mask<R>(const MaskArgsT<R>&, cudaStream_t);                                         \
     template void launch_live_all<R>(const DevLevelT<R>*, const Span&, const Span&, cudaStream_t);           \
     template void launch_covered_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
+    template void launch_uniform<R>(const DevLevelT<R>&, const DevLevelT<R>&, const R*, const R*, R*, R*,       \
+                                    cudaStream_t);                                                           \
+    template void launch_mark_support<R>(const WorkT<R>&, cudaStream_t);                                     \
     template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
     template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, cudaStream_t);         \
     template void launch_patch_scan<R>(const DevLevelT<R>*, int, int, cudaStream_t);                         \

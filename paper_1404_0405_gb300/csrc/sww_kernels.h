@@ -76,6 +76,12 @@ void launch_thresholds(const unsigned long long* red, double eps, double eh, dou
 
 // dense level kernels (masks, initialisation, diagnostics)
 template <class R> void launch_restrict_full(const DevLevelT<R>& C, const DevLevelT<R>& F, cudaStream_t s);
+// full level F from the full level below (zero coefficients away from live points)
+template <class R>
+void launch_uniform(const DevLevelT<R>& F, const DevLevelT<R>& C, const R* cdh, const R* cu, R* odh, R* ou,
+                    cudaStream_t s);
+// WASLIVE := LIVE on the listed patches (inverse transform of the stored coefficients)
+template <class R> void launch_mark_support(const WorkT<R>& W, cudaStream_t s);
 // significance, adjacency, closure, live flags, ghost band, covered nodes and
 // patch lists of levels a.ja..a.jb
 template <class R> void launch_mask(const MaskArgsT<R>& a, cudaStream_t s);

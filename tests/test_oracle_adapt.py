@@ -217,3 +217,41 @@ def test_error_controlled_by_eps():
             r = transform.restrict_height(Hy, j, r)
         errs.append(np.abs(M.dh[jm] - r).max())
     assert errs[2] < errs[0]
+
+
+def test_uniform_reconstruction_exact_on_full_grid():
+    """With every point live, the full level is the stored level itself: the
+    input, to the rounding of the inverse transform that adaptation applies."""
+    Hy = grid.Hierarchy(2, 4)
+    M = model.Model(Hy, eps=0.0)
+    L = Hy.levels[4]
+    dh, u = workloads.Workload("jet", seed=4).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    M.set_uniform(dh, u)
+    M.adapt()
+    h4, u4 = M.get_uniform(4)
+    assert np.array_equal(h4, M.dh[4]) and np.array_equal(u4, M.u[4])
+    assert np.abs(h4 - dh).max() < 1e-12 * np.abs(dh).max() and np.abs(u4 - u).max() < 1e-12 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("kind,seed", [("jet", 0), ("harmonic", 3)])
+def test_uniform_reconstruction_error_bounded_by_threshold(kind, seed):
+    """Dropping coefficients below eps (Sec. 2.3) perturbs the reconstructed
+    field by a small multiple of the thresholds (measured at most 0.61 eps_h and
+    0.41 eps_u on J2..5); a constant depth is reproduced exactly."""
+    Hy = grid.Hierarchy(2, 5)
+    L = Hy.levels[5]
+    W = workloads.Workload(kind, seed=seed)
+    dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    for eps in (3e-2, 1e-2):
+        M = model.Model(Hy, eps=eps)
+        M.set_uniform(dh, u)
+        M.adapt()
+        h5, u5 = M.get_uniform(5)
+        assert np.abs(h5 - dh).max() <= 1.0 * M.eps_h
+        assert np.abs(u5 - u).max() <= 1.0 * M.eps_u
+    M = model.Model(Hy, eps=1e-2)
+    M.set_uniform(np.full(L.N, 7.0), np.zeros(L.E))
+    M.adapt(eps_h=1e-9, eps_u=1e-9)
+    h5, u5 = M.get_uniform(5)
+    assert M.live_n[5].sum() == 0
+    assert np.abs(h5 - 7.0).max() < 1e-12 and np.abs(u5).max() == 0.0
