@@ -92,8 +92,11 @@ typedef struct {
                           one cooperative launch per stage over all ensemble members;
                           2: inside sww_step_ensemble, each member's stage as one
                           thread-block cluster (up to 16 blocks, hardware barriers
-                          between the phases); -1: one launch per phase always.  Falls
-                          back to -1 where the chosen launch cannot run.               */
+                          between the phases); 3: inside sww_step_ensemble, one regular
+                          launch per phase of each RK stage over all members (the
+                          members' other work overlaps on their streams); -1: one
+                          launch per phase always.  Falls back to -1 where the chosen
+                          launch cannot run.                                          */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
     double nu;         /* viscosity (m^2/s) of the viscous form (Sec. 3.1): nu div grad dh
@@ -189,8 +192,9 @@ int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
  * own stream, so the members' kernels overlap on the GPU; each member waits only
  * for its own previous step.  With more than one member the RK stages run as one
  * launch per phase (cooperative launches of different streams do not overlap),
- * unless every member has persistent = 1 and they share precision, Jmin, patch,
- * H, g and scheme: then each RK stage of all members is one cooperative launch
+ * unless every member has persistent = 1 (or every member 3) and they share
+ * precision, Jmin, patch, H, g and scheme: then each RK stage of all members is
+ * one cooperative launch (3: one regular launch per phase over all members)
  * between the members' other work (all members synchronise at every stage).  On entry each member's work is ordered after its
  * caller stream, and on return each caller stream waits for its member.
  * Returns the first error; members then stand at different step counts

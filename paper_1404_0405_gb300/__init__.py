@@ -175,7 +175,8 @@ class Model:
                  mask="lists", nu=0.0, advect=False, regime=0):
         """share: another Model whose grid and tables this one reuses (sww_create_shared).
         persistent: True/"auto", "always" (also batched over ensemble members),
-        "cluster" (ensemble members' stages as thread-block clusters) or
+        "cluster" (ensemble members' stages as thread-block clusters), "phased"
+        (ensemble stages as one launch per phase over all members) or
         False/"never" (see sww_config.persistent).  advect: prescribed velocity
         (see sww_config.advect).  regime: 1 scales the thresholds by eps^{3/2}
         (see sww_config.regime)."""
@@ -183,7 +184,7 @@ class Model:
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
                           blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
-                          {True: 0, "auto": 0, "always": 1, "cluster": 2, False: -1, "never": -1}[persistent],
+                          {True: 0, "auto": 0, "always": 1, "cluster": 2, "phased": 3, False: -1, "never": -1}[persistent],
                           {"lists": 0, "dense": 1}[mask], float(nu), int(bool(advect)), int(regime))
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()

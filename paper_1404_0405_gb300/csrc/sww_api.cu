@@ -740,11 +740,14 @@ const RKStage* stages(int rk, int& n) {
 // device-to-host copies of the time step and the list sizes.  part 1 is what comes
 // before the RK stages (time step, RK base), part 2 what follows them; part 0 is the
 // whole step.
+// part 0: the whole step; 1: time step and RK base only; 2: after the stages
+// (partial transform, ghosts, adaptation, read-backs); 3: adaptation and
+// read-backs only (the rest ran batched over an ensemble)
 template <class R>
 void one_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     const int j0 = h->cfg.jmin;
     auto& lv = lvl<R>(h);
-    if (part != 2) {
+    if (part == 0 || part == 1) {
         if (dt > 0) {
             count_launch(1);
             k_set<<<1, 32, 0, h->stream>>>(h->dt, dt);
@@ -759,11 +762,13 @@ void one_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
         for (int k = 0; k < ns; ++k) stage<R>(h, st[k]);
     }
     if (part == 1) return;
-    for (int j = h->jtop - 1; j >= j0; --j) {
-        Trace t(h, SWW_K_PARTIAL);
-        launch_partial(lv[j], lv[j + 1], work_level<R>(h, j), h->stream);
+    if (part != 3) {
+        for (int j = h->jtop - 1; j >= j0; --j) {
+            Trace t(h, SWW_K_PARTIAL);
+            launch_partial(lv[j], lv[j + 1], work_level<R>(h, j), h->stream);
+        }
+        fill_ghosts<R>(h);
     }
-    fill_ghosts<R>(h);
     if (do_adapt) adapt<R>(h, -1.0, -1.0);
     read_counts<R>(h);
     ck(cudaMemcpyAsync(h->h_dt, h->dt, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "dt");
@@ -813,11 +818,12 @@ void run_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     });
 }
 
-// The RK stages of every member of an ensemble as one persistent launch per stage
-// (k_stage_batch) on the first member's stream, after every member's part 1 and
-// before its part 2.
+// The RK stages of every member of an ensemble on the first member's stream, after
+// every member's part 1 and before its part 2: one persistent launch per stage
+// (k_stage_batch), or (phased) one regular launch per phase of a stage over all
+// members.
 template <class R>
-void ensemble_stages(sww_handle* const* hs, int n) {
+void ensemble_stages(sww_handle* const* hs, int n, bool phased, double dt) {
     sww_handle* lead = hs[0];
     auto& E = lead->ens;
     if (!E.refs) {
@@ -830,6 +836,8 @@ void ensemble_stages(sww_handle* const* hs, int n) {
         ck(cudaMallocHost(&E.h_err, sizeof(int)), "cudaMallocHost");
         *E.h_err = 0;
         ck(cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (!phased && !E.grid) {
         E.grid = stage_batch_grid<R>(lead->nsm);
         if (!E.grid) throw CudaError("persistent ensemble stage cannot run");
     }
@@ -837,7 +845,7 @@ void ensemble_stages(sww_handle* const* hs, int n) {
     int jtop = 0;
     for (int i = 0; i < n; ++i) {
         sww_handle* h = hs[i];
-        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop};
+        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop, h->red, h->cfg.cfl};
         jtop = std::max(jtop, h->jtop);
         if (i > 0) {
             ck(cudaEventRecord(h->ev_out, h->stream), "ensemble join");
@@ -847,11 +855,21 @@ void ensemble_stages(sww_handle* const* hs, int n) {
     ck(cudaMemcpyAsync(E.refs, refs, sizeof(MemberRef<R>) * n, cudaMemcpyHostToDevice, lead->stream), "refs");
     int ns;
     const RKStage* st = stages(lead->cfg.rk, ns);
+    // bound of the members' level-j list entries (for the phases' grid sizes)
+    std::vector<int64_t> entries(jtop + 1, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = lead->cfg.jmin; j <= std::min(jtop, hs[i]->cfg.jmax); ++j) entries[j] += meta(hs[i], j).npatch + 1;
+    BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
+                   lead->cfg.H, lead->cfg.g, st[0], E.bar, E.err, 0.0};
+    if (phased) ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, lead->stream), "batched ensemble step");
     for (int k = 0; k < ns; ++k) {
-        BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
-                       lead->cfg.H, lead->cfg.g, st[k], E.bar, E.err};
-        ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
+        a.st = st[k];
+        if (phased)
+            ck(launch_stage_batch_phases(a, entries.data(), lead->nsm, lead->stream), "batched ensemble stage");
+        else
+            ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
     }
+    if (phased) ck(launch_batch_post(a, entries.data(), lead->nsm, lead->stream), "batched ensemble step");
     ck(cudaMemcpyAsync(E.h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, lead->stream), "err");
     ck(cudaEventRecord(E.ev, lead->stream), "ensemble fork");
     for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
@@ -892,6 +910,7 @@ int check_config(const sww_config* cfg) {
     if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
         return fail(SWW_E_ARG, "precision must be SWW_FP64 or SWW_FP32");
     if (cfg->mask != 0 && cfg->mask != 1) return fail(SWW_E_ARG, "mask must be 0 (candidate lists) or 1 (dense)");
+    if (cfg->persistent < -1 || cfg->persistent > 3) return fail(SWW_E_ARG, "persistent must be -1..3");
     if (!(cfg->nu >= 0)) return fail(SWW_E_ARG, "nu must be >= 0");
     return SWW_OK;
 }
@@ -1191,10 +1210,13 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
     // one persistent launch per RK stage over all members (every member asks for it
     // with persistent = 1, and they share precision, Jmin, patch side, depth, gravity
     // and scheme); otherwise the members' whole steps overlap on their own streams
-    bool batched = n > 1 && n <= 128;
+    // (persistent = 3: one regular launch per phase of a stage over all members)
+    const int want = hs[0]->cfg.persistent;
+    const bool phased = want == 3;
+    bool batched = n > 1 && n <= 128 && (want == 1 || want == 3);
     for (int i = 0; i < n && batched; ++i) {
         const sww_config &a = hs[0]->cfg, &b = hs[i]->cfg;
-        batched = hs[i]->stage_cap > 0 && hs[i]->cfg.persistent == 1 && a.precision == b.precision &&
+        batched = (phased || hs[i]->stage_cap > 0) && b.persistent == want && a.precision == b.precision &&
                   a.jmin == b.jmin && a.patch == b.patch && a.H == b.H && a.g == b.g && a.rk == b.rk;
     }
     return guarded([&]() -> int {
@@ -1223,13 +1245,16 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         };
         int rc = SWW_OK;
         if (batched) {
+            // phased: the time step, RK base, stages, partial transform and ghosts of
+            // all members run batched; each member then adapts on its own stream
             for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
-                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
+                if (!phased)
+                    for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
                 by_prec(hs[0], [&](auto r) {
-                    ensemble_stages<decltype(r)>(hs, n);
+                    ensemble_stages<decltype(r)>(hs, n, phased, dt);
                     return 0;
                 });
-                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 2);
+                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, phased ? 3 : 2);
                 check_launch();
                 for (int i = 0; i < n; ++i) {
                     int r = finish(hs[i]);

@@ -1,0 +1,287 @@
+// RK stage of every member of an ensemble as one regular launch per phase (the
+// phases of one trend evaluation and its stage update, Sec. 3.1, in the order of
+// the persistent stage): ghosts level by level, q and F, div/K/B and q F^perp, the
+// restrictions level by level, the update.  The kernel boundary is the barrier.
+//
+// Blocks come in groups, one group per member: a block copies the level records of
+// its member that the phase touches into shared memory once, then strides over
+// that member's items only (no search for the member of an item, and every field
+// address from shared memory).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "sww_core.cuh"
+#include "sww_kernels.h"
+#include "sww_stage.h"
+
+namespace sww {
+
+namespace {
+
+#include "sww_bodies.cuh"
+
+constexpr int BATCH_TPB = 256;
+constexpr int MAXL = 12;
+constexpr int MAXM = 128;
+enum { PH_FILL = 0, PH_FLUX, PH_NODE, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL };
+
+struct MaxU64 {
+    __device__ unsigned long long operator()(unsigned long long x, unsigned long long y) const { return x > y ? x : y; }
+};
+struct MinU64 {
+    __device__ unsigned long long operator()(unsigned long long x, unsigned long long y) const { return x < y ? x : y; }
+};
+
+// block reduction of one word per thread (every thread returns the block's value)
+template <class Op>
+__device__ unsigned long long block_reduce_u64(unsigned long long v, Op op, unsigned long long* sh) {
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_down_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) v = op(v, sh[k]);
+        sh[0] = v;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// items of `n_entries` entries of `list` (levels from the staged records `sl`),
+// block b of bpm blocks of the member
+template <int KINDS, class R, class Body>
+__device__ __forceinline__ void member_items(const DevLevelT<R>* sl, const int32_t* __restrict__ list,
+                                             int64_t n_entries, int P, int b, int bpm, Body body) {
+    constexpr uint32_t NS = slots_of<KINDS>();
+    const int lp = __ffs(P) - 1;
+    const uint32_t n = uint32_t(n_entries) * (NS << lp);
+    const uint32_t stride = uint32_t(bpm) * blockDim.x;
+    for (uint32_t it = uint32_t(b) * blockDim.x + threadIdx.x; it < n; it += stride) {
+        const uint32_t e = (it >> lp) / NS;
+        const int32_t ent = list[e];
+        const DevLevelT<R>& L = sl[ent >> LVL_SHIFT];
+        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it - ((e * NS) << lp), P, body);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int phase, int j, int bpm) {
+    __shared__ DevLevelT<R> sl[MAXL];
+    const int m = blockIdx.x / bpm, b = blockIdx.x % bpm;
+    const MemberRef<R>* mr = a.m + m;
+    const int jtop = mr->jtop;
+    if (phase == PH_DT_FINAL) {   // one block per member
+        if (threadIdx.x == 0) {
+            const double w = __longlong_as_double(static_cast<long long>(mr->red[0]));
+            const double r = mr->red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(mr->red[1]));
+            *mr->dt = mr->cfl * fmin(1.0 / w, r);
+        }
+        return;
+    }
+    // level-serial phases skip the members that do not reach the level
+    if (phase == PH_FILL && j > jtop) return;
+    if ((phase == PH_RESTRICT || phase == PH_DIV || phase == PH_PARTIAL) && j > jtop - 1) return;
+    // the member's records of the levels the phase reads
+    const bool serial = phase == PH_RESTRICT || phase == PH_DIV || phase == PH_PARTIAL;
+    const int lo = phase == PH_FILL ? j - 1 : serial ? j : a.jmin;
+    const int hi = (phase == PH_RESTRICT || phase == PH_PARTIAL) ? j + 1 : (phase == PH_FILL || phase == PH_DIV) ? j : jtop;
+    {
+        const int words = int((hi - lo + 1) * sizeof(DevLevelT<R>) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(mr->lvs + lo);
+        int* dst = reinterpret_cast<int*>(sl + lo);
+        for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const R H = R(a.H), g = R(a.g);
+    switch (phase) {
+        case PH_FILL:
+            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE)
+                                                  fill_node(L, (&L)[-1], id);
+                                              else
+                                                  fill_edge(L, (&L)[-1], id);
+                                          });
+            break;
+        case PH_FLUX:
+            member_items<K_EDGE | K_TRI>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                         [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                             if (kind == K_EDGE)
+                                                 flux_at(L, id, H);
+                                             else
+                                                 pv_at(L, id, H);
+                                         });
+            break;
+        case PH_NODE:
+            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE)
+                                                  node_at(L, id, g);
+                                              else
+                                                  coriolis_at(L, id);
+                                          });
+            break;
+        case PH_RESTRICT:
+            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              restrict_item(L, (&L)[1], kind, id);
+                                          });
+            break;
+        case PH_DIV:
+            member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                 [&](const DevLevelT<R>& L, int, int64_t id, int64_t) { div_at(L, id); });
+            break;
+        case PH_SAVE:
+            // the RK base, and the time step: given (a.dt > 0) or its reduction words reset
+            if (b == 0 && threadIdx.x == 0) {
+                if (a.dt_given > 0) {
+                    *mr->dt = a.dt_given;
+                } else {
+                    mr->red[0] = 0ull;
+                    mr->red[1] = ~0ull;
+                }
+            }
+            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE) {
+                                                  if (L.nflag[id] & LIVE) L.dh0[id] = L.dh[id];
+                                              } else if (L.eflag[id] & LIVE) {
+                                                  L.u0[id] = L.u[id];
+                                              }
+                                          });
+            break;
+        case PH_DT: {
+            // omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max; none with a prescribed
+            // velocity), dx/|u| at live edges (min), as bit patterns of non-negative doubles
+            __shared__ unsigned long long sh[BATCH_TPB / 32];
+            unsigned long long wmax = 0, rmin = ~0ull;
+            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE) {
+                                                  if (L.advect || !(L.nflag[id] & LIVE)) return;
+                                                  const double f = double(L.f_n[id]), kx = M_PI / L.dx;
+                                                  const double w = sqrt(f * f + a.g * (a.H + double(L.dh[id])) * kx * kx);
+                                                  wmax = max(wmax, dbits(w));
+                                              } else if (L.eflag[id] & LIVE) {
+                                                  const double au = fabs(double(L.u[id]));
+                                                  if (au > 0) rmin = min(rmin, dbits(L.dx / au));
+                                              }
+                                          });
+            wmax = block_reduce_u64(wmax, MaxU64(), sh);
+            rmin = block_reduce_u64(rmin, MinU64(), sh);
+            if (threadIdx.x == 0) {
+                if (wmax) atomicMax(&mr->red[0], wmax);
+                if (rmin != ~0ull) atomicMin(&mr->red[1], rmin);
+            }
+            break;
+        }
+        case PH_PARTIAL:
+            // R_h at covered nodes of level j from level j + 1 (Eq. Rh)
+            member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                 [&](const DevLevelT<R>& L, int, int64_t id, int64_t) {
+                                     if (!(L.nflag[id] & COVERED)) return;
+                                     const DevLevelT<R>& F = (&L)[1];
+                                     R v = F.dh[L.c2f[id]];
+                                     for (int q = 0; q < 12; ++q) {
+                                         const int32_t mm = L.mk_i[q * L.N + id];
+                                         if (mm < 0 || !(F.nflag[mm] & LIVE)) continue;
+                                         v += L.mk_w[q * L.N + id] * height_detail(F, mm);
+                                     }
+                                     L.dh[id] = v;
+                                 });
+            break;
+        default: {
+            const R dt = R(*mr->dt);
+            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE)
+                                                  update_node(L, id, a.st, dt);
+                                              else
+                                                  update_edge(L, id, a.st, dt);
+                                          });
+        }
+    }
+}
+
+}  // namespace
+
+template <class R>
+cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
+    int64_t all = 0;
+    for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
+    // blocks per member: enough for the member's share of the bound, at most a
+    // full GPU (8 blocks of 256 per SM) over all members
+    const int cap = std::max(1, 8 * nsm / a.nm);
+    auto bpm = [&](int64_t entries, int slots) {
+        const int64_t per = (entries + a.nm - 1) / a.nm * a.P * slots;
+        return int(std::max<int64_t>(1, std::min<int64_t>((per + BATCH_TPB - 1) / BATCH_TPB, cap)));
+    };
+    auto go = [&](int phase, int j, int k) {
+        count_launch(1);
+        k_phase_batch<R><<<unsigned(a.nm * k), BATCH_TPB, 0, s>>>(a, phase, j, k);
+        return cudaGetLastError();
+    };
+    cudaError_t e = cudaSuccess;
+    for (int j = a.jmin + 1; j <= a.jtop_max && e == cudaSuccess; ++j) e = go(PH_FILL, j, bpm(level_entries[j], 4));
+    if (e == cudaSuccess) e = go(PH_FLUX, 0, bpm(all, 5));
+    if (e == cudaSuccess) e = go(PH_NODE, 0, bpm(all, 4));
+    for (int j = a.jtop_max - 1; j >= a.jmin && e == cudaSuccess; --j) {
+        e = go(PH_RESTRICT, j, bpm(level_entries[j], 4));
+        if (e == cudaSuccess) e = go(PH_DIV, j, bpm(level_entries[j], 1));
+    }
+    if (e == cudaSuccess) e = go(PH_UPDATE, 0, bpm(all, 4));
+    return e;
+}
+
+template <class R>
+static int batch_bpm(const BatchArgs<R>& a, int64_t entries, int slots, int nsm) {
+    const int cap = std::max(1, 8 * nsm / a.nm);
+    const int64_t per = (entries + a.nm - 1) / a.nm * a.P * slots;
+    return int(std::max<int64_t>(1, std::min<int64_t>((per + BATCH_TPB - 1) / BATCH_TPB, cap)));
+}
+
+template <class R>
+static cudaError_t batch_go(const BatchArgs<R>& a, int phase, int j, int k, cudaStream_t s) {
+    count_launch(1);
+    k_phase_batch<R><<<unsigned(a.nm * k), BATCH_TPB, 0, s>>>(a, phase, j, k);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_batch_pre(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, double dt, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
+    int64_t all = 0;
+    for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
+    BatchArgs<R> b = a;
+    b.dt_given = dt;
+    cudaError_t e = batch_go(b, PH_SAVE, 0, batch_bpm(b, all, 4, nsm), s);
+    if (e == cudaSuccess && !(dt > 0)) {
+        e = batch_go(b, PH_DT, 0, batch_bpm(b, all, 4, nsm), s);
+        if (e == cudaSuccess) e = batch_go(b, PH_DT_FINAL, 0, 1, s);
+    }
+    return e;
+}
+
+template <class R>
+cudaError_t launch_batch_post(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (int j = a.jtop_max - 1; j >= a.jmin && e == cudaSuccess; --j)
+        e = batch_go(a, PH_PARTIAL, j, batch_bpm(a, level_entries[j], 1, nsm), s);
+    for (int j = a.jmin + 1; j <= a.jtop_max && e == cudaSuccess; ++j)
+        e = batch_go(a, PH_FILL, j, batch_bpm(a, level_entries[j], 4, nsm), s);
+    return e;
+}
+
+template cudaError_t launch_batch_pre<double>(const BatchArgs<double>&, const int64_t*, int, double, cudaStream_t);
+template cudaError_t launch_batch_pre<float>(const BatchArgs<float>&, const int64_t*, int, double, cudaStream_t);
+template cudaError_t launch_batch_post<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_batch_post<float>(const BatchArgs<float>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_stage_batch_phases<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_stage_batch_phases<float>(const BatchArgs<float>&, const int64_t*, int, cudaStream_t);
+
+}  // namespace sww

@@ -50,10 +50,11 @@ __host__ __device__ constexpr int slots_of() {
 // to `one` when lvs is null.
 // Item `local` (0 <= local < slots x P) of work-list entry patch `pat` of level L:
 // body(L, kind, id, elem) when the slot holds an item (see for_items).
+// P is a power of two (the patch side is), so slot and index are a shift and a mask.
 template <int KINDS, class Lv, class Body>
-__device__ __forceinline__ void visit_item(const Lv& L, int64_t pat, int64_t local, int P, Body& body) {
-    int slot = int(local / P);
-    const int64_t idx = local % P;
+__device__ __forceinline__ void visit_item(const Lv& L, int64_t pat, uint32_t local, int P, Body& body) {
+    int slot = int(local >> (__ffs(P) - 1));
+    const int64_t idx = int64_t(local & uint32_t(P - 1));
     if (pat == L.npatch) {
         if ((KINDS & K_NODE) && slot == 0 && idx < 2) body(L, K_NODE, L.nelem + idx, int64_t(-1));
         return;
@@ -89,14 +90,16 @@ template <int KINDS, class Lv, class Body>
 __device__ __forceinline__ void for_items(const Lv* __restrict__ lvs, const Lv& one,
                                           const int32_t* __restrict__ list, const int32_t* __restrict__ count, int P,
                                           Body body) {
-    constexpr int NS = slots_of<KINDS>();
-    const int64_t S = int64_t(NS) * P;
-    const int64_t n = int64_t(*count) * S;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t it = gid(); it < n; it += stride) {
-        const int32_t ent = list[it / S];
+    // 32-bit item numbers: a list holds fewer than 2^31 items up to level 11
+    constexpr uint32_t NS = slots_of<KINDS>();
+    const int lp = __ffs(P) - 1;
+    const uint32_t n = uint32_t(*count) * (NS << lp);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += stride) {
+        const uint32_t e = (it >> lp) / NS;
+        const int32_t ent = list[e];
         const Lv& L = lvs ? lvs[ent >> LVL_SHIFT] : one;
-        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it % S, P, body);
+        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it - ((e * NS) << lp), P, body);
     }
 }
 

@@ -195,7 +195,7 @@ __device__ __forceinline__ void batch_items(const BatchArgs<R>& a, int j, int mo
         const int32_t ent = mode < 0 ? M.all_list[e - pre[lo]] : M.lvs[j].patches[e - pre[lo]];
         const DevLevelT<R>& L = M.lvs[ent >> LVL_SHIFT];
         auto b = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t el) { body(LL, kind, id, el, M); };
-        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), it % S, a.P, b);
+        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), uint32_t(it - e * S), a.P, b);
     }
     __syncthreads();
 }

@@ -38,8 +38,10 @@ struct MemberRef {
     const DevLevelT<R>* lvs;
     const int32_t* all_list;
     const int32_t* all_count;
-    const double* dt;
+    double* dt;
     int jtop;
+    unsigned long long* red;   // [2] reduction words of the CFL time step
+    double cfl;
 };
 
 // One persistent RK stage of nm members (m: device array of nm refs, nm <= 128)
@@ -52,6 +54,7 @@ struct BatchArgs {
     RKStage st;
     unsigned* bar;
     int* err;
+    double dt_given;   // phases before the stages: > 0 sets every member's time step
 };
 
 // co-resident blocks of the stage kernel on nsm SMs (0 when it cannot run)
@@ -67,5 +70,18 @@ template <class R>
 unsigned stage_batch_grid(int nsm);
 template <class R>
 cudaError_t launch_stage_batch(const BatchArgs<R>& a, unsigned grid, cudaStream_t s);
+// The same stage as one regular launch per phase over all members (level-serial
+// phases once per level); level_entries[j] bounds the members' level-j list
+// entries in total (for the grid sizes).
+template <class R>
+cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s);
+// Before the stages of a step, over all members: the RK base copy and the time
+// step (dt > 0 for every member, else each member's CFL step).
+template <class R>
+cudaError_t launch_batch_pre(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, double dt, cudaStream_t s);
+// After the stages: the partial height transform (top-1 down to Jmin) and the
+// ghosts (Jmin+1 up to the top) of every member.
+template <class R>
+cudaError_t launch_batch_post(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s);
 
 }  // namespace sww

@@ -43,11 +43,13 @@ def _snapshot(sww, m):
 
 
 @pytest.mark.parametrize("precision,persistent", [("fp64", "auto"), ("fp32", "auto"), ("fp64", "always"),
-                                                  ("fp32", "always"), ("fp64", "cluster"), ("fp32", "cluster")])
+                                                  ("fp32", "always"), ("fp64", "cluster"), ("fp32", "cluster"),
+                                                  ("fp64", "phased"), ("fp32", "phased")])
 def test_shared_members_match_single_runs(precision, persistent):
     """persistent "auto": the members' steps overlap on their streams; "always":
     one cooperative launch per RK stage over all members; "cluster": each member's
-    stage as one thread-block cluster."""
+    stage as one thread-block cluster; "phased": one regular launch per phase of a
+    stage over all members."""
     import paper_1404_0405_gb300 as sww
     jmin, top = 2, max(j for j, _, _ in MEMBERS)
     base = sww.Model(jmin, top, patch=4)
@@ -71,6 +73,30 @@ def test_shared_members_match_single_runs(precision, persistent):
             assert x.shape == y.shape, f"member {i} {k}: {x.shape} vs {y.shape}"
             bad = np.flatnonzero(x != y)
             assert bad.size == 0, f"member {i} {k}: {bad.size} differ, first {bad[:5]}, {x[bad[:3]]} vs {y[bad[:3]]}"
+
+
+@pytest.mark.parametrize("persistent", ["always", "phased"])
+def test_batched_members_with_given_time_step(persistent):
+    """A given time step (the same for every member) through the batched stages."""
+    import paper_1404_0405_gb300 as sww
+    jmin, top = 2, max(j for j, _, _ in MEMBERS)
+    base = sww.Model(jmin, top, patch=4)
+    ens, alone = [], []
+    for jmax, eps, seed in MEMBERS:
+        for group in (ens, alone):
+            m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision="fp32", persistent=persistent)
+            m.set_state(*_fields(m, seed))
+            m.adapt()
+            group.append(m)
+    sww.step_ensemble(ens, 120.0, 3, True)
+    for m in alone:
+        m.step(120.0, 3, True)
+    for a, b in zip(ens, alone):
+        fa, sa = _snapshot(sww, a)
+        fb, sb = _snapshot(sww, b)
+        assert sa == sb
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
 
 
 def test_shared_grid_matches_own_grid_to_rounding():
