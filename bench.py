@@ -10,9 +10,11 @@ its partial transform and grid adaptation.
 
 * plain form: FP64, one member, the exact threshold criterion;
 * chosen form (default): FP32 fields and stencils, an ensemble of --members
-  independent members (seeds) advanced together (each on its own stream, one
-  persistent launch per RK stage, shared grid tables), and the learned refinement
-  proposal, trained first on masks of two extra members.
+  independent members (seeds) advanced together on shared grid tables: the time
+  step, RK base, every phase of each RK stage, the partial transform and the
+  ghosts as one launch per phase over all members, then each member's adaptation
+  on its own stream; the learned refinement proposal, trained first on masks of
+  two extra members.
 
 value = (live nodes over all levels and members, averaged over each step's start
 and end) x steps / seconds, with per-step CUDA-event times (the L2 cache is
@@ -61,7 +63,7 @@ def parse():
     p.add_argument("--patch", type=int, default=8)
     p.add_argument("--form", default="chosen", choices=["chosen", "plain"],
                    help="chosen: FP32 ensemble with the learned proposal; plain: FP64, one member")
-    p.add_argument("--members", type=int, default=16, help="ensemble members of the chosen form")
+    p.add_argument("--members", type=int, default=64, help="ensemble members of the chosen form")
     p.add_argument("--plain-steps", type=int, default=10)
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--err-steps", type=int, default=20)
@@ -207,43 +209,34 @@ def combine_ranks(seconds, cells, device, world):
 # halves every term (its state and stencil weights are FP32).
 STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
 
-# DRAM bytes (read + write) per launch of k_restrict, mean over the 24 launches of
-# two steps of one ncu capture of the same jet at Jmin=4..Jmax=8 (the same active
-# set and launches as Jmax=9; profiles/k_restrict_jet_J4-8_fp32.md); remove an
-# entry when the kernel changes.
-RESTRICT_TRAFFIC_PER_LAUNCH = {"fp32": 1822954.7}
-
-# Algorithmic bytes of one launch of the restriction kernel (k_restrict, level j from
-# level j+1, Sec. 3.1 and 4.2-4.3) with R-byte reals, from the coarse level's flags:
-# every item of the level's active patches reads its flags (node 1 B, edge 8 B of end
-# ids + 2 B of flags); a covered node injects B (c2f id 4 B, B read and write 2R); an
-# edge with a covered end applies R_F (12 fine and 11 coarse weights and ids, the 23
-# values they gather, the face length and the flux written: 23(4 + 2R) + 2R); an edge
-# with both ends covered averages q F^perp over its halves (ids 8 B, 3R).
-def restrict_launch_bytes(sww, m, j, edges, R):
-    N, E, T, npatch = m.sizes(j)
-    pp = (E // 3) // npatch
-    act = len(m.patches(j))
-    cov = (m.get(j, sww.NODE_FLAGS) & 4) > 0
-    e1 = cov[edges[:, 0]] | cov[edges[:, 1]]
-    e2 = cov[edges[:, 0]] & cov[edges[:, 1]]
-    items_n, items_e = act * pp + 2, 3 * act * pp
-    return (items_n * 1 + int(cov.sum()) * (4 + 2 * R) + items_e * 10 + int(e1.sum()) * (23 * (4 + 2 * R) + 2 * R)
-            + int(e2.sum()) * (8 + 3 * R))
+# DRAM bytes (read + write) per launch of the batched stage kernel k_phase_batch,
+# mean over the launches of one ncu capture (None until taken for the current
+# kernel; remove the entry when the kernel changes).
+PHASE_TRAFFIC_PER_LAUNCH = {}
 
 
 def _live(m):
     return sum(m.stats()["live_nodes"].values())
 
 
+_SAMPLINGS = {}
+
+
+def _sampling(workloads, base, jmax):
+    """Latitudes and edge directions of the grid, shared by every member's fields."""
+    if id(base) not in _SAMPLINGS:
+        xyz, en = base.grid(jmax)
+        _SAMPLINGS[id(base)] = (base, workloads.Sampling(xyz, *edge_geometry(xyz, en)))
+    return _SAMPLINGS[id(base)][1]
+
+
 def _members(sww, workloads, base, a, precision, seeds, learned=None, persistent=True, patch=None, bps=0):
     ms = []
-    xyz, en = base.grid(a.jmax)
-    mid, tan = edge_geometry(xyz, en)
+    S = _sampling(workloads, base, a.jmax)
     for sd in seeds:
         m = sww.Model(a.jmin, a.jmax, patch=patch or a.patch, eps=a.eps, rk="rk4", cfl=0.8, precision=precision,
                       share=base, persistent=persistent, blocks_per_sm=bps)
-        dh, u = workloads.Workload("jet", seed=sd).fields(xyz, mid, tan)
+        dh, u = workloads.Workload("jet", seed=sd).fields_on(S)
         m.set_state(dh, u)
         m.adapt()
         m.adapt()
@@ -359,13 +352,14 @@ def run_ours(a, rank, world):
             mid, tan = edge_geometry(xyz, en)
             return [workloads.Workload("jet", seed=seed + 900 + k).fields(xyz, mid, tan) for k in range(4)]
 
-        best, trials = autotune.tune(a.jmin, a.jmax, a.eps, fields_of, members=4, key_extra="jet")
+        best, trials = autotune.tune(a.jmin, a.jmax, a.eps, fields_of, members=4, key_extra="jet",
+                                     persistent="phased")
         tuned = {"best": best, "trials": trials}
         cpatch, cbps = best["patch"], best["blocks_per_sm"]
         if cpatch != a.patch:
             cbase = sww.Model(a.jmin, a.jmax, patch=cpatch, eps=a.eps, rk="rk4", cfl=0.8)
     if a.form == "chosen" and a.no_learned:
-        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], persistent=False,
+        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], persistent="phased",
                       patch=cpatch, bps=cbps)
         dtype = "f32"
     elif a.form == "chosen":
@@ -376,7 +370,7 @@ def run_ours(a, rank, world):
         learned, losses = learn.train(X, y, epochs=300)
         del train_m
         ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], learned,
-                      persistent=False, patch=cpatch, bps=cbps)
+                      persistent="phased", patch=cpatch, bps=cbps)
         dtype = "f32"
     else:
         ms, dtype = plain_m, "f64"
@@ -405,24 +399,11 @@ def run_ours(a, rank, world):
         lstats["train_samples"] = int(len(y))
         lstats["train_loss"] = [float(losses[0]), float(losses[-1])]
 
-    # live per-launch timing of the dominant kernel of the timed steps: the
-    # restriction k_restrict (members step their RK stages as one launch per phase),
-    # on member 0 stepping alone in eager mode with CUDA events per launch
-    m0 = ms[0]
+    # live timing of the dominant kernel of the timed steps: the batched RK stage
+    # (k_phase_batch, one launch per phase over all members), from CUDA events the
+    # library records on the first member's stream around each RK stage, over the
+    # same number of ensemble steps (L2 flushed before each)
     prec = "fp32" if dtype == "f32" else "fp64"
-    R = 4 if prec == "fp32" else 8
-    edges = {j: cbase.grid(j)[1] for j in range(a.jmin, a.jmax)}
-    m0.profile(["restrict"])
-    rbytes = 0
-    for _ in range(a.steps):
-        flush.zero_()
-        act = m0.stats()["active_patches"]
-        top = max(j for j in range(a.jmin, a.jmax + 1) if act.get(j, 0) > 0)
-        rbytes += 4 * sum(restrict_launch_bytes(sww, m0, j, edges[j], R) for j in range(a.jmin, top))
-        m0.step(-1.0, 1, adapt=True)
-    prof = m0.profile_read()
-    m0.profile([])
-    r_ms, r_n = prof["restrict"]
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -430,13 +411,26 @@ def run_ours(a, rank, world):
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
     roofline = None
-    if r_n > 0:
-        achieved = rbytes / (r_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_restrict", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "peak_source": f"{peak_src} (burst copy)",
-                    "traffic": RESTRICT_TRAFFIC_PER_LAUNCH.get(prec) if a.jmax >= 8 and a.eps == 1e-2 else None,
-                    "avg_launch_us": r_ms * 1e3 / r_n, "launches": r_n,
-                    "algorithmic_bytes_per_launch": rbytes / r_n}
+    if a.form == "chosen":
+        m0 = ms[0]
+        m0.profile(["stage"])
+        sbytes = 0.0
+        for _ in range(a.steps):
+            c = sum(_live(m) for m in ms)
+            sbytes += STAGE_BYTES_PER_CELL[prec] * c * 4
+            flush.zero_()
+            sww.step_ensemble(ms, -1.0, 1, True)
+        s_ms, s_n = m0.profile_read()["stage"]
+        m0.profile([])
+        if s_n > 0:
+            achieved = sbytes / (s_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "kernel": "k_phase_batch (RK stage phases, all members)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": f"{peak_src} (burst copy)",
+                        "traffic": PHASE_TRAFFIC_PER_LAUNCH.get(prec), "avg_launch_us": s_ms * 1e3 / s_n,
+                        "launches": s_n, "algorithmic_bytes_per_launch": sbytes / s_n,
+                        "bytes_per_live_cell_per_stage": STAGE_BYTES_PER_CELL[prec],
+                        "stage_share_of_step": (s_ms / 1e3) / max(sum(times), 1e-30)}
     # the persistent RK stage of the plain form's single member (fused trend + update)
     pm = plain_m[0]
     pm.profile(["stage"])
@@ -459,11 +453,10 @@ def run_ours(a, rank, world):
            if a.err_steps > 0 else None)
 
     # end to end through the public API from pinned host buffers
-    xyz, en = cbase.grid(a.jmax)
-    mid, tan = edge_geometry(xyz, en)
+    S = _sampling(workloads, cbase, a.jmax)
     host = []
     for k, m in enumerate(ms):
-        dh, u = workloads.Workload("jet", seed=seed + k).fields(xyz, mid, tan)
+        dh, u = workloads.Workload("jet", seed=seed + k).fields_on(S)
         host.append((torch.from_numpy(dh).pin_memory().numpy(), torch.from_numpy(u).pin_memory().numpy()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()

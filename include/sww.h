@@ -272,15 +272,18 @@ enum {
 };
 
 /* Tracing: from now on record a pair of CUDA events on the library's stream
- * around every launch of the kernel classes whose bit is set in class_mask (bit k
- * for class k); 0 stops recording.  Previous records are discarded.  While any
- * class is traced, sww_step runs its kernels directly instead of replaying the
- * captured graph. */
+ * around every launch group of the kernel classes whose bit is set in class_mask
+ * (bit k for class k); 0 stops recording.  Previous records are discarded.  While
+ * any class is traced, sww_step runs its kernels directly instead of replaying
+ * the captured graph.  In sww_step_ensemble with batched stages (persistent 1
+ * or 3) the first member's records cover the batched launches of all members
+ * (SWW_K_STAGE per RK stage; with 3 also SWW_K_DT for the time step and RK base,
+ * SWW_K_PARTIAL for the partial transform and ghosts after the stages). */
 int sww_profile(sww_handle* h, uint32_t class_mask);
 
-/* Sum of the recorded launch durations (ms[SWW_K_NCLASS]) and launch counts
- * (launches[SWW_K_NCLASS]) per class since sww_profile; synchronises the stream
- * and clears the records (recording continues). */
+/* Sum of the recorded durations (ms[SWW_K_NCLASS]) and of the kernel launches
+ * inside the records (launches[SWW_K_NCLASS]) per class since sww_profile;
+ * synchronises the stream and clears the records (recording continues). */
 int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
 
 /* Mass and energy of the Jmin level (the same two numbers sww_stats_get reports)

@@ -30,12 +30,13 @@ def _live(m):
 
 
 def tune(jmin, jmax, eps, fields_of, members=4, precision="fp32", patches=(4, 8, 16), blocks=(2, 4, 8), steps=3,
-         warmup=2, key_extra="", use_cache=True):
+         warmup=2, key_extra="", use_cache=True, persistent=False):
     """fields_of(xyz, edges) -> list of (dh, u) initial states (one per member) on a
-    grid with the given node and edge order.  Returns ({"patch", "blocks_per_sm",
-    "rate"}, table of every trial)."""
+    grid with the given node and edge order; persistent: the members' stage mode
+    (see Model).  Returns ({"patch", "blocks_per_sm", "rate"}, table of every
+    trial)."""
     import torch
-    key = f"{_gpu_name()}|J{jmin}-{jmax}|eps{eps:g}|M{members}|{precision}|{key_extra}"
+    key = f"{_gpu_name()}|J{jmin}-{jmax}|eps{eps:g}|M{members}|{precision}|{persistent}|{key_extra}"
     cache = {}
     if use_cache and os.path.exists(CACHE):
         try:
@@ -53,7 +54,7 @@ def tune(jmin, jmax, eps, fields_of, members=4, precision="fp32", patches=(4, 8,
             ms = []
             for dh, u in states:
                 m = Model(jmin, jmax, patch=p, eps=eps, share=base, blocks_per_sm=b, precision=precision,
-                          persistent=False)
+                          persistent=persistent)
                 m.set_state(dh, u)
                 m.adapt()
                 ms.append(m)

@@ -203,6 +203,7 @@ struct sww_handle {
     struct Rec {
         int cls;
         cudaEvent_t a, b;
+        int64_t launches;   // kernel launches between the two events
     };
     std::vector<Rec> recs;
     cudaEvent_t take_event() {
@@ -497,17 +498,19 @@ struct Trace {
     sww_handle* h;
     int cls;
     cudaEvent_t a = nullptr;
+    int64_t l0 = 0;
     Trace(sww_handle* h_, int c) : h(h_), cls(c) {
         if (h->prof_mask & (1u << cls)) {
             a = h->take_event();
             ck(cudaEventRecord(a, h->stream), "cudaEventRecord");
+            l0 = kernel_launches();
         }
     }
     ~Trace() {
         if (!a) return;
         cudaEvent_t b = h->take_event();
         cudaEventRecord(b, h->stream);
-        h->recs.push_back({cls, a, b});
+        h->recs.push_back({cls, a, b, kernel_launches() - l0});
     }
 };
 
@@ -861,15 +864,23 @@ void ensemble_stages(sww_handle* const* hs, int n, bool phased, double dt) {
         for (int j = lead->cfg.jmin; j <= std::min(jtop, hs[i]->cfg.jmax); ++j) entries[j] += meta(hs[i], j).npatch + 1;
     BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
                    lead->cfg.H, lead->cfg.g, st[0], E.bar, E.err, 0.0};
-    if (phased) ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, lead->stream), "batched ensemble step");
+    // (traced on the first member: its records cover all members)
+    if (phased) {
+        Trace t(lead, SWW_K_DT);
+        ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, lead->stream), "batched ensemble step");
+    }
     for (int k = 0; k < ns; ++k) {
+        Trace t(lead, SWW_K_STAGE);
         a.st = st[k];
         if (phased)
             ck(launch_stage_batch_phases(a, entries.data(), lead->nsm, lead->stream), "batched ensemble stage");
         else
             ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
     }
-    if (phased) ck(launch_batch_post(a, entries.data(), lead->nsm, lead->stream), "batched ensemble step");
+    if (phased) {
+        Trace t(lead, SWW_K_PARTIAL);
+        ck(launch_batch_post(a, entries.data(), lead->nsm, lead->stream), "batched ensemble step");
+    }
     ck(cudaMemcpyAsync(E.h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, lead->stream), "err");
     ck(cudaEventRecord(E.ev, lead->stream), "ensemble fork");
     for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
@@ -1791,7 +1802,7 @@ int sww_profile_read(sww_handle* h, double* ms, int64_t* launches) {
             float t = 0;
             ck(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
             ms[r.cls] += t;
-            launches[r.cls] += 1;
+            launches[r.cls] += r.launches;
             h->ev_pool.push_back(r.a), h->ev_pool.push_back(r.b);
         }
         h->recs.clear();

@@ -121,6 +121,21 @@ def _zonal_balance(ufun, radius, omega, g, mean_depth, nq=200001, anchor="mean")
     return lambda la: np.interp(la, lat, h)
 
 
+class Sampling:
+    """The per-point quantities every workload evaluates on one grid (node
+    latitudes, edge latitudes and the eastward component of each edge tangent),
+    computed once for many seeded members on the same grid."""
+
+    def __init__(self, node_xyz, edge_mid, edge_tan):
+        self.node_xyz = np.asarray(node_xyz, dtype=np.float64)
+        self.edge_mid = np.asarray(edge_mid, dtype=np.float64)
+        self.edge_tan = np.asarray(edge_tan, dtype=np.float64)
+        self.node_lat, _ = _latlon(self.node_xyz)
+        east, _ = _east_north(self.edge_mid)
+        self.edge_lat, _ = _latlon(self.edge_mid)
+        self.east_tan = np.sum(east * self.edge_tan, axis=-1)
+
+
 class Workload:
     """A seeded initial condition: call ``fields(node_xyz, edge_mid, edge_tan)``.
 
@@ -185,14 +200,15 @@ class Workload:
         back = _rotate(np.asarray(xyz, dtype=np.float64), self.axis, -self.u0 * t / self.radius)
         return self._bell(back)
 
-    def depth(self, xyz):
-        """Total depth h at unit-sphere points."""
+    def depth(self, xyz, lat=None):
+        """Total depth h at unit-sphere points (lat: their latitudes, if known)."""
         xyz = np.asarray(xyz, dtype=np.float64)
         if self.kind.startswith("tc1"):
             return self._bell(xyz)
         if self.kind == "harmonic":
             return self.mean_depth + self._scale * self._harm(xyz)
-        lat, _ = _latlon(xyz)
+        if lat is None:
+            lat, _ = _latlon(xyz)
         h = self._h(lat)
         if self.kind == "jet":
             for b in self.bumps:
@@ -219,3 +235,11 @@ class Workload:
     def fields(self, node_xyz, edge_mid, edge_tan):
         dh = self.depth(node_xyz) - self.mean_depth
         return dh, self.velocity(edge_mid, edge_tan)
+
+    def fields_on(self, S):
+        """fields() on a precomputed Sampling (the same values)."""
+        if self.kind not in ("jet", "tc2"):
+            return self.fields(S.node_xyz, S.edge_mid, S.edge_tan)
+        dh = self.depth(S.node_xyz, S.node_lat) - self.mean_depth
+        uz = self._ujet(S.edge_lat) if self.kind == "jet" else self.u0 * np.cos(S.edge_lat)
+        return dh, uz * S.east_tan
