@@ -209,10 +209,12 @@ def combine_ranks(seconds, cells, device, world):
 # halves every term (its state and stencil weights are FP32).
 STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
 
-# DRAM bytes (read + write) per launch of the batched stage kernel k_phase_batch,
-# mean over the launches of one ncu capture (None until taken for the current
-# kernel; remove the entry when the kernel changes).
-PHASE_TRAFFIC_PER_LAUNCH = {}
+# DRAM bytes (read + write) of the batched RK stage (the k_phase_batch launches of
+# one stage) per live member-cell, from one ncu capture of the same jet at
+# Jmin=4..Jmax=8 with 16 members (205.8 MB per stage over 305 146 member-cells,
+# cold cache per launch; profiles/k_phase_batch_jet_J4-8_16members.md), scaled to a
+# launch by the member-cells it processes; remove the entry when the kernel changes.
+PHASE_TRAFFIC_PER_CELL_STAGE = {"fp32": 674.4}
 
 
 def _live(m):
@@ -398,6 +400,17 @@ def run_ours(a, rank, world):
                 lstats[k] += v
         lstats["train_samples"] = int(len(y))
         lstats["train_loss"] = [float(losses[0]), float(losses[-1])]
+        # the same members without the proposal (the exact rules alone), for comparison
+        for m in ms:
+            m.set_learned(0)
+        for _ in range(a.warmup):
+            sww.step_ensemble(ms, -1.0, 1, True)
+        t2, c2 = _timed(sww, ms, a.steps, flush, stream)
+        t2, c2 = combine_ranks(sum(t2), sum(c2), "cuda", world)
+        lstats["without_proposal"] = {"value": c2 / t2, "ms_per_step": 1e3 * t2 / a.steps,
+                                      "active_cells_per_step": c2 / a.steps / max(world, 1) / len(ms)}
+        for m in ms:
+            m.set_learned(2, learned, a.tau)
 
     # live timing of the dominant kernel of the timed steps: the batched RK stage
     # (k_phase_batch, one launch per phase over all members), from CUDA events the
@@ -427,7 +440,9 @@ def run_ours(a, rank, world):
             roofline = {"bound": "hbm", "kernel": "k_phase_batch (RK stage phases, all members)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": f"{peak_src} (burst copy)",
-                        "traffic": PHASE_TRAFFIC_PER_LAUNCH.get(prec), "avg_launch_us": s_ms * 1e3 / s_n,
+                        "traffic": (PHASE_TRAFFIC_PER_CELL_STAGE[prec] * sbytes / STAGE_BYTES_PER_CELL[prec] / s_n
+                                    if prec in PHASE_TRAFFIC_PER_CELL_STAGE else None),
+                        "avg_launch_us": s_ms * 1e3 / s_n,
                         "launches": s_n, "algorithmic_bytes_per_launch": sbytes / s_n,
                         "bytes_per_live_cell_per_stage": STAGE_BYTES_PER_CELL[prec],
                         "stage_share_of_step": (s_ms / 1e3) / max(sum(times), 1e-30)}
