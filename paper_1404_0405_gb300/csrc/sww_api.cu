@@ -176,6 +176,8 @@ struct sww_handle {
         int* h_err = nullptr;
         cudaEvent_t ev = nullptr;
         unsigned grid = 0;
+        uint8_t* out = nullptr;     // device read-back records (BatchOut per member)
+        uint8_t* h_out = nullptr;   // pinned copy
     } ens;
     unsigned* bar = nullptr;
     int* err = nullptr;
@@ -236,6 +238,7 @@ struct sww_handle {
         if (h_err) cudaFreeHost(h_err);
         if (ens.h_refs) cudaFreeHost(ens.h_refs);
         if (ens.h_err) cudaFreeHost(ens.h_err);
+        if (ens.h_out) cudaFreeHost(ens.h_out);
         if (ens.ev) cudaEventDestroy(ens.ev);
         if (h_dt) cudaFreeHost(h_dt);
         for (void* p : allocs) cudaFree(p);
@@ -659,11 +662,12 @@ MaskArgsT<R> mask_args(const sww_handle* h, int j0, int j1, bool allow_tail = tr
 
 // Mask construction and inverse transform.  Levels above top + 1 hold no live point
 // and can gain none in one adaptation, so the byte-wide passes stop there.
+// significance, proposal, mask, patch lists (Sec. 2.3), from the stored
+// coefficients and thresholds
 template <class R>
-void mask_and_inverse(sww_handle* h) {
+void mask_only(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = std::min(h->jtop + 1, h->cfg.jmax);
     cudaStream_t s = h->stream;
-    auto& lv = lvl<R>(h);
     {
         Trace tm(h, SWW_K_MASK);
         MaskArgsT<R> a = mask_args<R>(h, j0, j1);
@@ -696,6 +700,14 @@ void mask_and_inverse(sww_handle* h) {
         if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 1, h->sig_any, s);
         launch_concat(dlv<R>(h), j0, h->cfg.jmax, h->all_list, h->all_count, s);
     }
+}
+
+template <class R>
+void mask_and_inverse(sww_handle* h) {
+    const int j0 = h->cfg.jmin, j1 = std::min(h->jtop + 1, h->cfg.jmax);
+    cudaStream_t s = h->stream;
+    auto& lv = lvl<R>(h);
+    mask_only<R>(h);
     // inverse transform of the retained coefficients, coarse to fine, ghosts per level
     for (int j = j0 + 1; j <= j1; ++j) {
         { Trace t(h, SWW_K_INVERSE); launch_inverse(lv[j], lv[j - 1], work_level<R>(h, j), s); }
@@ -745,11 +757,15 @@ const RKStage* stages(int rk, int& n) {
 // whole step.
 // part 0: the whole step; 1: time step and RK base only; 2: after the stages
 // (partial transform, ghosts, adaptation, read-backs); 3: adaptation and
-// read-backs only (the rest ran batched over an ensemble)
+// read-backs only (the rest ran batched over an ensemble); 4: the mask only
 template <class R>
 void one_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     const int j0 = h->cfg.jmin;
     auto& lv = lvl<R>(h);
+    if (part == 4) {   // the mask alone (coefficients, thresholds and inverse batched)
+        mask_only<R>(h);
+        return;
+    }
     if (part == 0 || part == 1) {
         if (dt > 0) {
             count_launch(1);
@@ -821,69 +837,132 @@ void run_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     });
 }
 
-// The RK stages of every member of an ensemble on the first member's stream, after
-// every member's part 1 and before its part 2: one persistent launch per stage
-// (k_stage_batch), or (phased) one regular launch per phase of a stage over all
-// members.
+// Device buffers of ensemble steps led by `lead` (allocated on first use).
 template <class R>
-void ensemble_stages(sww_handle* const* hs, int n, bool phased, double dt) {
+void ensure_ensemble(sww_handle* lead) {
+    auto& E = lead->ens;
+    if (E.refs) return;
+    E.refs = lead->alloc<uint8_t>(sizeof(MemberRef<double>) * 128);
+    E.bar = lead->alloc<unsigned>(STAGE_BAR_WORDS);
+    E.err = lead->alloc<int>(1);
+    E.out = lead->alloc<uint8_t>(sizeof(BatchOut) * 128);
+    ck(cudaMemset(E.bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "memset");
+    ck(cudaMemset(E.err, 0, sizeof(int)), "memset");
+    ck(cudaMallocHost(&E.h_refs, sizeof(MemberRef<double>) * 128), "cudaMallocHost");
+    ck(cudaMallocHost(&E.h_err, sizeof(int)), "cudaMallocHost");
+    ck(cudaMallocHost(&E.h_out, sizeof(BatchOut) * 128), "cudaMallocHost");
+    *E.h_err = 0;
+    ck(cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming), "cudaEventCreate");
+}
+
+// Member refs of this step on the lead's stream (after every member's previous
+// work: the members' streams are joined into the lead's), the largest top level
+// and j1, and the bounds of the members' level-j list entries.
+template <class R>
+BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& entries, int& j1_max) {
     sww_handle* lead = hs[0];
     auto& E = lead->ens;
-    if (!E.refs) {
-        E.refs = lead->alloc<uint8_t>(sizeof(MemberRef<double>) * 128);
-        E.bar = lead->alloc<unsigned>(STAGE_BAR_WORDS);
-        E.err = lead->alloc<int>(1);
-        ck(cudaMemset(E.bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "memset");
-        ck(cudaMemset(E.err, 0, sizeof(int)), "memset");
-        ck(cudaMallocHost(&E.h_refs, sizeof(MemberRef<double>) * 128), "cudaMallocHost");
-        ck(cudaMallocHost(&E.h_err, sizeof(int)), "cudaMallocHost");
-        *E.h_err = 0;
-        ck(cudaEventCreateWithFlags(&E.ev, cudaEventDisableTiming), "cudaEventCreate");
-    }
-    if (!phased && !E.grid) {
-        E.grid = stage_batch_grid<R>(lead->nsm);
-        if (!E.grid) throw CudaError("persistent ensemble stage cannot run");
-    }
     MemberRef<R>* refs = reinterpret_cast<MemberRef<R>*>(E.h_refs);
     int jtop = 0;
+    j1_max = 0;
     for (int i = 0; i < n; ++i) {
         sww_handle* h = hs[i];
-        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop, h->red, h->cfg.cfl};
+        const int j1 = std::min(h->jtop + 1, h->cfg.jmax);
+        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop, h->red, h->cfg.cfl,
+                               h->thr, eps_coeff(h->cfg), h->cfg.advect, j1, h->cfg.jmax, h->err};
         jtop = std::max(jtop, h->jtop);
+        j1_max = std::max(j1_max, j1);
         if (i > 0) {
             ck(cudaEventRecord(h->ev_out, h->stream), "ensemble join");
             ck(cudaStreamWaitEvent(lead->stream, h->ev_out, 0), "ensemble join");
         }
     }
     ck(cudaMemcpyAsync(E.refs, refs, sizeof(MemberRef<R>) * n, cudaMemcpyHostToDevice, lead->stream), "refs");
+    entries.assign(j1_max + 1, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = lead->cfg.jmin; j <= std::min(j1_max, hs[i]->cfg.jmax); ++j)
+            entries[j] += meta(hs[i], j).npatch + 1;
     int ns;
     const RKStage* st = stages(lead->cfg.rk, ns);
-    // bound of the members' level-j list entries (for the phases' grid sizes)
-    std::vector<int64_t> entries(jtop + 1, 0);
-    for (int i = 0; i < n; ++i)
-        for (int j = lead->cfg.jmin; j <= std::min(jtop, hs[i]->cfg.jmax); ++j) entries[j] += meta(hs[i], j).npatch + 1;
-    BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
-                   lead->cfg.H, lead->cfg.g, st[0], E.bar, E.err, 0.0};
-    // (traced on the first member: its records cover all members)
-    if (phased) {
-        Trace t(lead, SWW_K_DT);
-        ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, lead->stream), "batched ensemble step");
+    return BatchArgs<R>{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
+                        lead->cfg.H, lead->cfg.g, st[0], E.bar, E.err, 0.0, E.out};
+}
+
+// The RK stages of every member of an ensemble as one persistent launch per stage
+// (k_stage_batch) on the first member's stream, after every member's part 1 and
+// before its part 2.
+template <class R>
+void ensemble_stages(sww_handle* const* hs, int n) {
+    sww_handle* lead = hs[0];
+    ensure_ensemble<R>(lead);
+    auto& E = lead->ens;
+    if (!E.grid) {
+        E.grid = stage_batch_grid<R>(lead->nsm);
+        if (!E.grid) throw CudaError("persistent ensemble stage cannot run");
     }
+    std::vector<int64_t> entries;
+    int j1_max = 0;
+    BatchArgs<R> a = ensemble_refs<R>(hs, n, entries, j1_max);
+    int ns;
+    const RKStage* st = stages(lead->cfg.rk, ns);
     for (int k = 0; k < ns; ++k) {
         Trace t(lead, SWW_K_STAGE);
         a.st = st[k];
-        if (phased)
-            ck(launch_stage_batch_phases(a, entries.data(), lead->nsm, lead->stream), "batched ensemble stage");
-        else
-            ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
-    }
-    if (phased) {
-        Trace t(lead, SWW_K_PARTIAL);
-        ck(launch_batch_post(a, entries.data(), lead->nsm, lead->stream), "batched ensemble step");
+        ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
     }
     ck(cudaMemcpyAsync(E.h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, lead->stream), "err");
     ck(cudaEventRecord(E.ev, lead->stream), "ensemble fork");
     for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
+}
+
+// One step of every member with the work batched over members (persistent = 3), on
+// the first member's stream: time step and RK base, the stage phases, the partial
+// transform and ghosts, the coefficients and thresholds; each member's mask on its
+// own stream; then the inverse transform and ghosts and the read-back records of
+// all members (copied to pinned memory; the caller synchronises the first
+// member's stream).  The records cover all members.
+template <class R>
+void ensemble_phased(sww_handle* const* hs, int n, double dt, bool do_adapt) {
+    sww_handle* lead = hs[0];
+    ensure_ensemble<R>(lead);
+    auto& E = lead->ens;
+    cudaStream_t s = lead->stream;
+    std::vector<int64_t> entries;
+    int j1_max = 0;
+    BatchArgs<R> a = ensemble_refs<R>(hs, n, entries, j1_max);
+    int ns;
+    const RKStage* st = stages(lead->cfg.rk, ns);
+    {
+        Trace t(lead, SWW_K_DT);
+        ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, s), "batched ensemble step");
+    }
+    for (int k = 0; k < ns; ++k) {
+        Trace t(lead, SWW_K_STAGE);
+        a.st = st[k];
+        ck(launch_stage_batch_phases(a, entries.data(), lead->nsm, s), "batched ensemble stage");
+    }
+    {
+        Trace t(lead, SWW_K_PARTIAL);
+        ck(launch_batch_post(a, entries.data(), lead->nsm, s), "batched ensemble step");
+    }
+    if (do_adapt) {
+        {
+            Trace t(lead, SWW_K_COEFF);
+            ck(launch_batch_adapt_pre(a, entries.data(), lead->nsm, s), "batched ensemble step");
+        }
+        // each member's mask on its own stream, then back to the lead's
+        ck(cudaEventRecord(E.ev, s), "ensemble fork");
+        for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
+        for (int i = 0; i < n; ++i) run_step(hs[i], dt, true, 4);
+        for (int i = 1; i < n; ++i) {
+            ck(cudaEventRecord(hs[i]->ev_out, hs[i]->stream), "ensemble join");
+            ck(cudaStreamWaitEvent(s, hs[i]->ev_out, 0), "ensemble join");
+        }
+        Trace t(lead, SWW_K_INVERSE);
+        ck(launch_batch_adapt_post(a, entries.data(), j1_max, lead->nsm, s), "batched ensemble step");
+    }
+    ck(launch_batch_out(a, s), "batched ensemble step");
+    ck(cudaMemcpyAsync(E.h_out, E.out, sizeof(BatchOut) * n, cudaMemcpyDeviceToHost, s), "read-back");
 }
 
 int check_level(const sww_handle* h, int level) {
@@ -1256,16 +1335,34 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         };
         int rc = SWW_OK;
         if (batched) {
-            // phased: the time step, RK base, stages, partial transform and ghosts of
-            // all members run batched; each member then adapts on its own stream
+            if (phased) {
+                // the whole step batched over the members but their masks
+                for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
+                    by_prec(hs[0], [&](auto r) {
+                        ensemble_phased<decltype(r)>(hs, n, dt, do_adapt != 0);
+                        return 0;
+                    });
+                    check_launch();
+                    ck(cudaStreamSynchronize(hs[0]->stream), "step");
+                    const BatchOut* o = reinterpret_cast<const BatchOut*>(hs[0]->ens.h_out);
+                    for (int i = 0; i < n && rc == SWW_OK; ++i) {
+                        sww_handle* h = hs[i];
+                        *h->h_dt = o[i].dt;
+                        *h->h_err = o[i].err;
+                        for (int j = 0; j <= h->cfg.jmax && j < 16; ++j) h->h_counts[j] = o[i].counts[j];
+                        rc = finish(h);
+                    }
+                }
+                join_out();
+                return rc;
+            }
             for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
-                if (!phased)
-                    for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
+                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
                 by_prec(hs[0], [&](auto r) {
-                    ensemble_stages<decltype(r)>(hs, n, phased, dt);
+                    ensemble_stages<decltype(r)>(hs, n);
                     return 0;
                 });
-                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, phased ? 3 : 2);
+                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 2);
                 check_launch();
                 for (int i = 0; i < n; ++i) {
                     int r = finish(hs[i]);

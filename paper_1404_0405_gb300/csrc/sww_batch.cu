@@ -25,7 +25,10 @@ namespace {
 constexpr int BATCH_TPB = 256;
 constexpr int MAXL = 12;
 constexpr int MAXM = 128;
-enum { PH_FILL = 0, PH_FLUX, PH_NODE, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL };
+enum {
+    PH_FILL = 0, PH_FLUX, PH_NODE, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL,
+    PH_DETAILS, PH_MAXABS, PH_THRESH, PH_INV_A, PH_INV_B, PH_INV_FILL, PH_OUT
+};
 
 struct MaxU64 {
     __device__ unsigned long long operator()(unsigned long long x, unsigned long long y) const { return x > y ? x : y; }
@@ -73,7 +76,8 @@ __global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int p
     const int m = blockIdx.x / bpm, b = blockIdx.x % bpm;
     const MemberRef<R>* mr = a.m + m;
     const int jtop = mr->jtop;
-    if (phase == PH_DT_FINAL) {   // one block per member
+    // one block per member
+    if (phase == PH_DT_FINAL) {
         if (threadIdx.x == 0) {
             const double w = __longlong_as_double(static_cast<long long>(mr->red[0]));
             const double r = mr->red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(mr->red[1]));
@@ -81,13 +85,33 @@ __global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int p
         }
         return;
     }
+    if (phase == PH_THRESH) {   // relative thresholds on the live maxima (a prescribed velocity has none)
+        if (threadIdx.x == 0) {
+            mr->thr[0] = mr->eps_c * __longlong_as_double(static_cast<long long>(mr->red[2]));
+            mr->thr[1] = mr->advect ? INFINITY : mr->eps_c * __longlong_as_double(static_cast<long long>(mr->red[3]));
+        }
+        return;
+    }
+    if (phase == PH_OUT) {
+        BatchOut* o = reinterpret_cast<BatchOut*>(a.out) + m;
+        const int t = threadIdx.x;
+        if (t < 16) o->counts[t] = (t >= a.jmin && t <= mr->jmax) ? *mr->lvs[t].npatches : 0;
+        if (t == 0) {
+            o->dt = *mr->dt;
+            o->err = *mr->err;
+        }
+        return;
+    }
     // level-serial phases skip the members that do not reach the level
     if (phase == PH_FILL && j > jtop) return;
     if ((phase == PH_RESTRICT || phase == PH_DIV || phase == PH_PARTIAL) && j > jtop - 1) return;
-    // the member's records of the levels the phase reads
+    const bool inv = phase == PH_INV_A || phase == PH_INV_B || phase == PH_INV_FILL;
+    if (inv && j > mr->j1) return;
+    // the member's records of the levels the phase reads (the inverse transform
+    // reaches one level above the top)
     const bool serial = phase == PH_RESTRICT || phase == PH_DIV || phase == PH_PARTIAL;
-    const int lo = phase == PH_FILL ? j - 1 : serial ? j : a.jmin;
-    const int hi = (phase == PH_RESTRICT || phase == PH_PARTIAL) ? j + 1 : (phase == PH_FILL || phase == PH_DIV) ? j : jtop;
+    const int lo = (phase == PH_FILL || phase == PH_INV_A || phase == PH_INV_FILL) ? j - 1 : (serial || inv) ? j : a.jmin;
+    const int hi = (phase == PH_RESTRICT || phase == PH_PARTIAL) ? j + 1 : (phase == PH_FILL || phase == PH_DIV || inv) ? j : jtop;
     {
         const int words = int((hi - lo + 1) * sizeof(DevLevelT<R>) / sizeof(int));
         const int* src = reinterpret_cast<const int*>(mr->lvs + lo);
@@ -143,6 +167,8 @@ __global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int p
                     mr->red[0] = 0ull;
                     mr->red[1] = ~0ull;
                 }
+                mr->red[2] = 0ull;
+                mr->red[3] = 0ull;
             }
             member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
                                           [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
@@ -178,6 +204,51 @@ __global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int p
             }
             break;
         }
+        case PH_DETAILS:
+            member_items<K_NODE | K_EDGE | K_CEDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                                    [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t el) {
+                                                        if (L.J > a.jmin) details_item(L, (&L)[-1], kind, id, el);
+                                                    });
+            break;
+        case PH_MAXABS: {
+            // max |dh| over live nodes, max |u| over live edges (bit patterns)
+            __shared__ unsigned long long shm[BATCH_TPB / 32];
+            unsigned long long hmax = 0, umax = 0;
+            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE) {
+                                                  if (L.nflag[id] & LIVE) hmax = max(hmax, dbits(fabs(double(L.dh[id]))));
+                                              } else if (L.eflag[id] & LIVE) {
+                                                  umax = max(umax, dbits(fabs(double(L.u[id]))));
+                                              }
+                                          });
+            hmax = block_reduce_u64(hmax, MaxU64(), shm);
+            umax = block_reduce_u64(umax, MaxU64(), shm);
+            if (threadIdx.x == 0) {
+                if (hmax) atomicMax(&mr->red[2], hmax);
+                if (umax) atomicMax(&mr->red[3], umax);
+            }
+            break;
+        }
+        case PH_INV_A:
+            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              inverse_a_item(L, (&L)[-1], kind, id);
+                                          });
+            break;
+        case PH_INV_B:
+            member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                 [&](const DevLevelT<R>& L, int, int64_t id, int64_t) { inverse_b_item(L, id); });
+            break;
+        case PH_INV_FILL:
+            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
+                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
+                                              if (kind == K_NODE)
+                                                  fill_node(L, (&L)[-1], id);
+                                              else
+                                                  fill_edge(L, (&L)[-1], id);
+                                          });
+            break;
         case PH_PARTIAL:
             // R_h at covered nodes of level j from level j + 1 (Eq. Rh)
             member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
@@ -277,6 +348,43 @@ cudaError_t launch_batch_post(const BatchArgs<R>& a, const int64_t* level_entrie
     return e;
 }
 
+template <class R>
+cudaError_t launch_batch_adapt_pre(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
+    int64_t all = 0;
+    for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
+    cudaError_t e = batch_go(a, PH_DETAILS, 0, batch_bpm(a, all, 7, nsm), s);
+    if (e == cudaSuccess) e = batch_go(a, PH_MAXABS, 0, batch_bpm(a, all, 4, nsm), s);
+    if (e == cudaSuccess) e = batch_go(a, PH_THRESH, 0, 1, s);
+    return e;
+}
+
+template <class R>
+cudaError_t launch_batch_adapt_post(const BatchArgs<R>& a, const int64_t* level_entries, int j1_max, int nsm,
+                                    cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM || j1_max + 1 > MAXL) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (int j = a.jmin + 1; j <= j1_max && e == cudaSuccess; ++j) {
+        const int k = batch_bpm(a, level_entries[j], 4, nsm);
+        e = batch_go(a, PH_INV_A, j, k, s);
+        if (e == cudaSuccess) e = batch_go(a, PH_INV_B, j, batch_bpm(a, level_entries[j], 1, nsm), s);
+        if (e == cudaSuccess) e = batch_go(a, PH_INV_FILL, j, k, s);
+    }
+    return e;
+}
+
+template <class R>
+cudaError_t launch_batch_out(const BatchArgs<R>& a, cudaStream_t s) {
+    if (a.nm < 1 || a.nm > MAXM) return cudaErrorInvalidValue;
+    return batch_go(a, PH_OUT, 0, 1, s);
+}
+
+template cudaError_t launch_batch_adapt_pre<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_batch_adapt_pre<float>(const BatchArgs<float>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_batch_adapt_post<double>(const BatchArgs<double>&, const int64_t*, int, int, cudaStream_t);
+template cudaError_t launch_batch_adapt_post<float>(const BatchArgs<float>&, const int64_t*, int, int, cudaStream_t);
+template cudaError_t launch_batch_out<double>(const BatchArgs<double>&, cudaStream_t);
+template cudaError_t launch_batch_out<float>(const BatchArgs<float>&, cudaStream_t);
 template cudaError_t launch_batch_pre<double>(const BatchArgs<double>&, const int64_t*, int, double, cudaStream_t);
 template cudaError_t launch_batch_pre<float>(const BatchArgs<float>&, const int64_t*, int, double, cudaStream_t);
 template cudaError_t launch_batch_post<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);

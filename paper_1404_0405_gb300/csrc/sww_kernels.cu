@@ -120,78 +120,28 @@ __global__ void k_partial(DevLevelT<R> C, DevLevelT<R> F, const int32_t* list, c
     });
 }
 
-// wavelet coefficients at live points (Eqs. 1-2; velocity transform of Sec. 4.1):
-// h~ at odd nodes, u~ at interior fine edges, u~_E at the edges of the coarse element
-// under each even fine element
+// wavelet coefficients at live points (body details_item)
 template <class R>
 __global__ void k_details(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
                           int jmin) {
     DevLevelT<R> none{};
     ITEMS(K_NODE | K_EDGE | K_CEDGE, lvs, none, list, count, P) {
         if (L.J == jmin) return;
-        const DevLevelT<R>& C = lvs[L.J - 1];
-        if (kind == K_NODE) {
-            if (L.f2c[id] < 0 && (L.nflag[id] & LIVE)) L.hdet[id] = height_detail(L, id);
-        } else if (kind == K_EDGE) {
-            if (L.fe_kind[id] == 2 && (L.eflag[id] & LIVE)) L.ui[id] = L.u[id] - predict(L, C.u, id);
-        } else {
-            int32_t ce = L.f2c[el];
-            if (ce < 0) return;
-            int64_t E = id * C.nelem + ce;
-            int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-            if ((L.eflag[h0] & LIVE) || (L.eflag[h1] & LIVE)) {
-                R a = L.u[h0] - predict(L, C.u, h0);
-                R b = L.u[h1] - predict(L, C.u, h1);
-                L.ue[E] = R(0.5) * (a - b);
-            }
-        }
+        details_item(L, lvs[L.J - 1], kind, id, el);
     });
 }
 
 // inverse transform of the retained coefficients onto the live points of F:
-// (a) even nodes and all edges from level C, (b) odd nodes from the even ones.
-// Coefficients count only where the point was live before the adaptation.
+// (a) even nodes and all edges from level C, (b) odd nodes from the even ones
+// (bodies inverse_a_item, inverse_b_item)
 template <class R>
 __global__ void k_inverse_a(DevLevelT<R> F, DevLevelT<R> C, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, F, list, count, P) {
-        if (kind == K_NODE) {
-            if (!(L.nflag[id] & LIVE) || L.f2c[id] < 0) return;
-            int32_t k = L.f2c[id];
-            R s = C.dh[k];
-            for (int q = 0; q < 12; ++q) {
-                int32_t m = C.mk_i[q * C.N + k];
-                if (m >= 0 && (L.nflag[m] & LIVE) && (L.nflag[m] & WASLIVE)) s -= C.mk_w[q * C.N + k] * L.hdet[m];
-            }
-            L.dh[id] = s;
-            return;
-        }
-        int64_t i = id;
-        if (L.advect || !(L.eflag[i] & LIVE)) return;   // a prescribed velocity is kept as set
-        int fk = L.fe_kind[i];
-        R Pr = predict(L, C.u, i);
-        if (fk == 2) {
-            L.u[i] = Pr + ((L.eflag[i] & WASLIVE) ? L.ui[i] : R(0));
-        } else {
-            int64_t E = L.fe_ce[i];
-            int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-            int32_t other = fk == 0 ? h1 : h0;
-            R Po = predict(L, C.u, other);
-            R delta = R(0.5) * (R(2) * C.u[E] - Pr - Po);
-            R d = ((L.eflag[h0] | L.eflag[h1]) & WASLIVE) ? L.ue[E] : R(0);
-            L.u[i] = Pr + delta + (fk == 0 ? d : -d);
-        }
-    });
+    ITEMS(K_NODE | K_EDGE, (const DevLevelT<R>*)nullptr, F, list, count, P) { inverse_a_item(L, C, kind, id); });
 }
 
 template <class R>
 __global__ void k_inverse_b(DevLevelT<R> F, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, F, list, count, P) {
-        if (!(L.nflag[id] & LIVE) || L.f2c[id] >= 0) return;
-        R s = (L.nflag[id] & WASLIVE) ? L.hdet[id] : R(0);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) s += L.ptw[q * L.N + id] * L.dh[L.par[q * L.N + id]];
-        L.dh[id] = s;
-    });
+    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, F, list, count, P) { inverse_b_item(L, id); });
 }
 
 // ---------------------------------------------------------------------------- reductions

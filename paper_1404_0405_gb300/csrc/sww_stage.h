@@ -40,8 +40,15 @@ struct MemberRef {
     const int32_t* all_count;
     double* dt;
     int jtop;
-    unsigned long long* red;   // [2] reduction words of the CFL time step
+    unsigned long long* red;   // [4] reduction words: CFL time step [0, 1], live maxima [2, 3]
     double cfl;
+    // adaptation (batched phases around the members' own masks)
+    double* thr;               // [2] thresholds eps_h, eps_u
+    double eps_c;              // relative coefficient tolerance (eps, or eps^{3/2})
+    int advect;                // prescribed velocity: no velocity threshold
+    int j1;                    // top level of the inverse transform (min(jtop + 1, jmax))
+    int jmax;
+    const int* err;            // barrier error flag of the member's persistent stages
 };
 
 // One persistent RK stage of nm members (m: device array of nm refs, nm <= 128)
@@ -55,6 +62,16 @@ struct BatchArgs {
     unsigned* bar;
     int* err;
     double dt_given;   // phases before the stages: > 0 sets every member's time step
+    void* out;         // read-back records, one per member (BATCH_OUT_BYTES each)
+};
+
+// Read-back record of one member after a batched step: dt, the error flag and the
+// active patch count of each level 0..15.
+struct BatchOut {
+    double dt;
+    int32_t err;
+    int32_t counts[16];
+    int32_t pad;
 };
 
 // co-resident blocks of the stage kernel on nsm SMs (0 when it cannot run)
@@ -83,5 +100,16 @@ cudaError_t launch_batch_pre(const BatchArgs<R>& a, const int64_t* level_entries
 // ghosts (Jmin+1 up to the top) of every member.
 template <class R>
 cudaError_t launch_batch_post(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s);
+// Before the members' masks: wavelet coefficients, live maxima and thresholds.
+template <class R>
+cudaError_t launch_batch_adapt_pre(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s);
+// After them: the inverse transform and ghosts, level by level up to each
+// member's j1 (level_entries up to the largest j1).
+template <class R>
+cudaError_t launch_batch_adapt_post(const BatchArgs<R>& a, const int64_t* level_entries, int j1_max, int nsm,
+                                    cudaStream_t s);
+// The read-back records (BatchOut) of every member into a.out.
+template <class R>
+cudaError_t launch_batch_out(const BatchArgs<R>& a, cudaStream_t s);
 
 }  // namespace sww
