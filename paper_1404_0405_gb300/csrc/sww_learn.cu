@@ -33,56 +33,69 @@ __device__ __forceinline__ float feat_log(double x) { return float(log2(1.0 + x)
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// Own features of a patch (one warp per patch): log2(1 + max|h~|/eps_h) over its
-// live odd nodes, log2(1 + max|u~|/eps_u) over its live interior edges and the pair
-// coefficients of the coarse edges under its even nodes, and the fraction of its
-// nodes that are live.  An inactive patch has no live point: all three are 0.
+// Own features of a patch: log2(1 + max|h~|/eps_h) over its live odd nodes,
+// log2(1 + max|u~|/eps_u) over its live interior edges and the pair coefficients of
+// the coarse edges under its even nodes, and the fraction of its nodes that are
+// live.  An inactive patch has no live point: all three are 0.  A warp takes 32
+// consecutive patches: each lane clears an inactive one, then the warp works
+// through the active ones together (one lane per node of the patch).
 template <class R>
 __global__ void k_feat_own(const DevLevelT<R>* __restrict__ lvs, Span sp, const double* __restrict__ thr) {
     const int lane = threadIdx.x & 31;
-    int j;
-    int64_t P;
-    if (!lfind(sp, lgid() >> 5, j, P)) return;
-    const DevLevelT<R>& L = lvs[j];
-    const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
-    const bool pole = P == L.npatch;
-    if (!pole && !L.pflag[P]) {
-        if (lane == 0) L.pfeat[0 * np1 + P] = 0.f, L.pfeat[1 * np1 + P] = 0.f, L.pfeat[6 * np1 + P] = 0.f;
-        return;
-    }
-    const DevLevelT<R>& C = lvs[j - 1];
-    R mh = R(0), mu = R(0);
-    int live = 0;
-    const int64_t nn = pole ? 2 : pp;
-    for (int64_t l = lane; l < nn; l += 32) {
-        const int64_t v = pole ? L.nelem + l : P * pp + l;
-        const uint8_t f = L.nflag[v];
-        live += (f & LIVE) ? 1 : 0;
-        if ((f & LIVE) && L.f2c[v] < 0) mh = fmax(mh, fabs(L.hdet[v]));
-        if (pole) continue;
-        for (int o = 0; o < 3; ++o) {
-            const int64_t e = o * L.nelem + v;
-            if ((L.eflag[e] & LIVE) && L.fe_kind[e] == 2) mu = fmax(mu, fabs(L.ui[e]));
+    int mj = 0;
+    int64_t mP = 0;
+    bool mine = lfind(sp, lgid(), mj, mP);
+    if (mine) {
+        const DevLevelT<R>& L = lvs[mj];
+        const int64_t np1 = L.npatch + 1;
+        if (mP != L.npatch && !L.pflag[mP]) {
+            L.pfeat[0 * np1 + mP] = 0.f, L.pfeat[1 * np1 + mP] = 0.f, L.pfeat[6 * np1 + mP] = 0.f;
+            mine = false;
         }
-        const int32_t ce = L.f2c[v];
-        if (ce >= 0 && ce < C.nelem) {
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, mine);
+    while (todo) {
+        const int src = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int j = __shfl_sync(0xffffffffu, mj, src);
+        const int64_t P = __shfl_sync(0xffffffffu, mP, src);
+        const DevLevelT<R>& L = lvs[j];
+        const DevLevelT<R>& C = lvs[j - 1];
+        const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
+        const bool pole = P == L.npatch;
+        R mh = R(0), mu = R(0);
+        int live = 0;
+        const int64_t nn = pole ? 2 : pp;
+        for (int64_t l = lane; l < nn; l += 32) {
+            const int64_t v = pole ? L.nelem + l : P * pp + l;
+            const uint8_t f = L.nflag[v];
+            live += (f & LIVE) ? 1 : 0;
+            if ((f & LIVE) && L.f2c[v] < 0) mh = fmax(mh, fabs(L.hdet[v]));
+            if (pole) continue;
             for (int o = 0; o < 3; ++o) {
-                const int64_t E = o * C.nelem + ce;
-                const int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-                if ((L.eflag[h0] | L.eflag[h1]) & LIVE) mu = fmax(mu, fabs(L.ue[E]));
+                const int64_t e = o * L.nelem + v;
+                if ((L.eflag[e] & LIVE) && L.fe_kind[e] == 2) mu = fmax(mu, fabs(L.ui[e]));
+            }
+            const int32_t ce = L.f2c[v];
+            if (ce >= 0 && ce < C.nelem) {
+                for (int o = 0; o < 3; ++o) {
+                    const int64_t E = o * C.nelem + ce;
+                    const int32_t h0 = C.half[E], h1 = C.half[C.E + E];
+                    if ((L.eflag[h0] | L.eflag[h1]) & LIVE) mu = fmax(mu, fabs(L.ue[E]));
+                }
             }
         }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-        mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-        live += __shfl_xor_sync(0xffffffffu, live, o);
-    }
-    if (lane == 0) {
-        const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
-        L.pfeat[0 * np1 + P] = feat_log(double(mh) / eh);
-        L.pfeat[1 * np1 + P] = feat_log(double(mu) / eu);
-        L.pfeat[6 * np1 + P] = float(live) / float(nn);
+        for (int o = 16; o > 0; o >>= 1) {
+            mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+            mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+            live += __shfl_xor_sync(0xffffffffu, live, o);
+        }
+        if (lane == 0) {
+            const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
+            L.pfeat[0 * np1 + P] = feat_log(double(mh) / eh);
+            L.pfeat[1 * np1 + P] = feat_log(double(mu) / eu);
+            L.pfeat[6 * np1 + P] = float(live) / float(nn);
+        }
     }
 }
 
@@ -291,7 +304,7 @@ void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const doubl
     const int64_t n = patches_f.off[patches_f.jb + 1 - patches_f.ja];
     if (n <= 0) return;
     count_launch(2);
-    k_feat_own<R><<<blocks_for(n * 32, 256), 256, 0, s>>>(lvs, patches_f, thr);
+    k_feat_own<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, thr);
     k_feat_ctx<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, jmin, jmax);
 }
 
