@@ -67,7 +67,7 @@ def parse():
     p.add_argument("--plain-steps", type=int, default=10)
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--err-steps", type=int, default=20)
-    p.add_argument("--tau", type=float, default=0.5)
+    p.add_argument("--tau", type=float, default=0.9, help="proposal threshold on the perceptron probability")
     p.add_argument("--no-learned", action="store_true", help="chosen form without the learned proposal")
     p.add_argument("--no-tune", action="store_true", help="chosen form without the autotuner (patch, 4 blocks/SM)")
     p.add_argument("--no-cpu-baseline", action="store_true")
