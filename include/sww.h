@@ -163,6 +163,12 @@ int sww_get_grid(const sww_handle* h, int level, double* node_xyz, int32_t* edge
  * device_ptrs != 0: dh, u are device pointers. */
 int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs);
 
+/* The same from fields on a full level J in Jmin..Jmax (dh[N_J], u[E_J]): levels
+ * Jmin..J receive them and their restrictions and are all live; the levels above
+ * J hold no point until adaptation refines into them.  With a prescribed
+ * velocity (advect) J must be Jmax (SWW_E_ARG otherwise). */
+int sww_set_state_level(sww_handle* h, int level, const double* dh, const double* u, int device_ptrs);
+
 /* Adapt the grid (Sec. 2.3): wavelet coefficients at live points, thresholds
  * (eps_h, eps_u > 0 given explicitly, else eps times the live maxima),
  * significance, neighbours in space and scale, graded closure, ghost band,

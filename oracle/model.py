@@ -58,17 +58,22 @@ class Model:
         self.eps_h = self.eps_u = None
 
     # ------------------------------------------------------------------ state
-    def set_uniform(self, dh_f, u_f):
-        """Fields on the full level Jmax; every coarser level gets their
-        restriction (R_h, R_u) and every point is live."""
+    def set_uniform(self, dh_f, u_f, level=None):
+        """Fields on the full level Jmax (or `level`); every coarser level gets
+        their restriction (R_h, R_u) and every point up to that level is live;
+        the levels above it hold no point."""
         Hy = self.Hy
-        self.dh[self.jmax], self.u[self.jmax] = dh_f.astype(np.float64).copy(), u_f.astype(np.float64).copy()
-        for j in range(self.jmax, self.jmin, -1):
+        J = self.jmax if level is None else level
+        self.dh[J], self.u[J] = dh_f.astype(np.float64).copy(), u_f.astype(np.float64).copy()
+        for j in range(J, self.jmin, -1):
             self.dh[j - 1] = transform.restrict_height(Hy, j, self.dh[j])
             self.u[j - 1] = transform.restrict_velocity(Hy, j, self.u[j])
+        for j in range(J + 1, self.jmax + 1):
+            self.dh[j] = np.full(Hy.levels[j].N, np.nan)
+            self.u[j] = np.full(Hy.levels[j].E, np.nan)
         self.u_set = {j: self.u[j].copy() for j in self.levels}
-        self.live_n = {j: np.ones(Hy.levels[j].N, dtype=bool) for j in self.levels}
-        self.live_e = {j: np.ones(Hy.levels[j].E, dtype=bool) for j in self.levels}
+        self.live_n = {j: np.full(Hy.levels[j].N, j <= J) for j in self.levels}
+        self.live_e = {j: np.full(Hy.levels[j].E, j <= J) for j in self.levels}
         self.ghost_n = {j: np.zeros(Hy.levels[j].N, dtype=bool) for j in self.levels}
         self.ghost_e = {j: np.zeros(Hy.levels[j].E, dtype=bool) for j in self.levels}
 

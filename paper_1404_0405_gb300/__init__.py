@@ -30,7 +30,7 @@ EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_
            "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
            "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
            "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
-           "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load"]
+           "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_get_state": [P, I, P, P],
         "sww_save": [P, ctypes.c_char_p],
         "sww_load": [P, ctypes.c_char_p],
+        "sww_set_state_level": [P, I, P, P, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -220,14 +221,18 @@ class Model:
         return xyz, en
 
     # ------------------------------------------------------------------ state
-    def set_state(self, dh, u):
-        """Fields on the full level Jmax (numpy host arrays or torch CUDA tensors, float64)."""
+    def set_state(self, dh, u, level=None):
+        """Fields on the full level Jmax, or on `level` (levels above it start
+        empty); numpy host arrays or torch CUDA tensors, float64."""
         if isinstance(dh, np.ndarray):
             dh = np.ascontiguousarray(dh, dtype=np.float64)
             u = np.ascontiguousarray(u, dtype=np.float64)
         pd, dev = _ptr(dh)
         pu, _ = _ptr(u)
-        _check(load().sww_set_state(self._h, pd, pu, dev))
+        if level is None:
+            _check(load().sww_set_state(self._h, pd, pu, dev))
+        else:
+            _check(load().sww_set_state_level(self._h, int(level), pd, pu, dev))
 
     def adapt(self, eps_h=-1.0, eps_u=-1.0):
         _check(load().sww_adapt(self._h, eps_h, eps_u))

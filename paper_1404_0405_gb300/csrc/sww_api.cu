@@ -1149,8 +1149,9 @@ int sww_get_grid(const sww_handle* h, int level, double* node_xyz, int32_t* edge
     return SWW_OK;
 }
 
-int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
-    if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
+// Fields on the full level J; coarser levels get their restriction, every point
+// of levels Jmin..J becomes live and the levels above J are empty.
+static int set_state_at(sww_handle* h, const double* dh, const double* u, int J, int device_ptrs) {
     return guarded([&]() -> int {
         const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
         cudaStream_t s = h->stream;
@@ -1158,29 +1159,37 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
             using R = decltype(r);
             Join jn(h);
             auto& lv = lvl<R>(h);
-            DevLevelT<R>& F = lv[j1];
+            DevLevelT<R>& F = lv[J];
             cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
             if constexpr (std::is_same<R, double>::value) {
                 ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
                 ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
             } else {
                 // FP64 input rounded once to the working precision
-                if (!h->stage) h->stage = h->alloc<double>(std::max(F.N, F.E));
+                if (!h->stage) h->stage = h->alloc<double>(std::max(meta(h, j1).N, meta(h, j1).E));
                 ck(cudaMemcpyAsync(h->stage, dh, F.N * sizeof(double), kind, s), "set_state dh");
                 launch_convert(h->stage, F.dh, F.N, s);
                 ck(cudaMemcpyAsync(h->stage, u, F.E * sizeof(double), kind, s), "set_state u");
                 launch_convert(h->stage, F.u, F.E, s);
             }
-            for (int j = j1; j > j0; --j) launch_restrict_full(lv[j - 1], lv[j], s);
-            MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
+            for (int j = J; j > j0; --j) launch_restrict_full(lv[j - 1], lv[j], s);
+            MaskArgsT<R> a = mask_args<R>(h, j0, J, false);
             launch_live_all(dlv<R>(h), a.nodes, a.edges, s);
+            for (int j = J + 1; j <= j1; ++j) {
+                const DevLevelT<R>& L = lv[j];
+                ck(cudaMemsetAsync(L.nflag, 0, L.N, s), "memset flags");
+                ck(cudaMemsetAsync(L.eflag, 0, L.E, s), "memset flags");
+                ck(cudaMemsetAsync(L.dh, 0, L.N * sizeof(R), s), "memset state");
+                ck(cudaMemsetAsync(L.u, 0, L.E * sizeof(R), s), "memset state");
+            }
             // the list-based mask expects the band bytes zero away from its candidates
             for (int j = j0; j <= j1; ++j) {
                 ck(cudaMemsetAsync(lv[j].band0, 0, lv[j].N, s), "memset band");
                 ck(cudaMemsetAsync(lv[j].band1, 0, lv[j].N, s), "memset band");
             }
-            if (j1 > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
-            launch_patches_all(dlv<R>(h), a.patches, s);
+            if (J > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
+            MaskArgsT<R> b = mask_args<R>(h, j0, j1, false);
+            launch_patches_all(dlv<R>(h), b.patches, s);
             launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);
             read_counts<R>(h);
             check_launch();
@@ -1193,6 +1202,20 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
         h->steps = 0;
         return SWW_OK;
     });
+}
+
+int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
+    if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
+    return set_state_at(h, dh, u, h->cfg.jmax, device_ptrs);
+}
+
+int sww_set_state_level(sww_handle* h, int level, const double* dh, const double* u, int device_ptrs) {
+    if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (h->cfg.advect && level != h->cfg.jmax)
+        return fail(SWW_E_ARG, "a prescribed velocity is set on Jmax (it holds on every level)");
+    return set_state_at(h, dh, u, level, device_ptrs);
 }
 
 int sww_adapt(sww_handle* h, double eps_h, double eps_u) {

@@ -300,3 +300,39 @@ def test_advect_adaptive_steps_match(built, kind, rk):
     for j in range(2, 5):
         assert np.array_equal(P.lib.get(j, P.sww.U), u_set[j])   # never written
     assert abs(P.lib.stats()["mass"] / m0 - 1) < 1e-14
+
+
+# ----------------------------------------------------------------------------- state on a coarser level
+
+
+def test_state_set_on_a_coarser_level_matches(built):
+    """Fields given on level 3 of 2..5: levels above start empty and adaptation
+    refines into them (one level per adaptation by the adjacent-in-scale rule)."""
+    import paper_1404_0405_gb300 as sww
+    Hy = grid.Hierarchy(2, 5)
+    ora = model.Model(Hy, eps=1e-2)
+    lib = sww.Model(2, 5, patch=4, eps=1e-2)
+    maps = {j: LevelMap(*lib.grid(j), Hy.levels[j]) for j in range(2, 6)}
+    L = Hy.levels[3]
+    dh, u = workloads.Workload("jet", seed=0).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    ora.set_uniform(dh, u, level=3)
+    lib.set_state(maps[3].nodes_to_lib(dh), maps[3].edges_to_lib(u), level=3)
+    assert lib.stats()["live_nodes"][4] == 0 and lib.stats()["live_nodes"][5] == 0
+    ora.adapt()
+    lib.adapt()
+    for _ in range(3):
+        dt = ora.dt_cfl()
+        ora.step(dt)
+        lib.step(-1.0, 1, True)
+        assert abs(lib.stats()["dt"] / dt - 1) < 1e-12
+    assert ora.live_n[5].sum() > 0
+    for j in range(2, 6):
+        M = maps[j]
+        nf = M.nodes_to_ora(lib.get(j, sww.NODE_FLAGS))
+        assert np.array_equal((nf & 1) > 0, ora.live_n[j]) and np.array_equal((nf & 2) > 0, ora.ghost_n[j])
+        mn = ora.live_n[j] | ora.ghost_n[j]
+        if mn.any():
+            assert rel_err(M.nodes_to_ora(lib.get(j, sww.DH))[mn], ora.dh[j][mn]) < TOL
+        me = ora.live_e[j] | ora.ghost_e[j]
+        if me.any():
+            assert rel_err(M.edges_to_ora(lib.get(j, sww.U))[me], ora.u[j][me]) < TOL

@@ -15,6 +15,10 @@ Workloads (all seeded; numpy PCG64):
     height bumps of 120 m (e-folding radius 500 km) at seeded sites.
   * ``tc2``: Williamson test case 2 (solid-body zonal flow, u0 = 2 pi R / 12 d,
     g*H = 2.94e4 m^2/s^2), depth from the same gradient-wind balance.
+  * ``turbulence``: random-phase vorticity with energy spectrum (l/32)^2 below
+    degree 32 and (l/32)^-3 above (degrees 1..96), rms velocity 20 m/s, depth in
+    geostrophic balance with f0 = 2 Omega sin 45 deg about a 10 km mean (the
+    spectrum's shape and the balance are readings).
   * ``tc1_cosine`` / ``tc1_smooth``: the advection test of Sec. 7.1 -- a bell
     of height 1000 m and radius L = R/3 centred at lat 0, lon 0 (the cosine
     bell (H/2)(1 + cos(pi r/L)) for r < L, or the smooth bell
@@ -86,6 +90,46 @@ class _Harmonic:
                 out += a * P[(l, 0)]
             else:
                 out += math.sqrt(2.0) * P[(l, m)] * (a * np.cos(m * lon) + b * np.sin(m * lon))
+        return out
+
+
+class _Spectral:
+    """A real spherical-harmonic series sum_{l,m} (a_lm cos(m lon) + b_lm sin(m lon))
+    P_lm(sin lat) of degrees 1..lmax (fully normalised), evaluated at arbitrary
+    points one order m at a time (the Legendre recurrence runs over the points,
+    so memory stays a few arrays of the point count)."""
+
+    def __init__(self, lmax, a, b):
+        self.lmax, self.a, self.b = lmax, a, b   # a[l, m], b[l, m]
+
+    def __call__(self, xyz):
+        lat, lon = _latlon(xyz)
+        x = np.sin(lat)
+        s = np.sqrt(np.clip(1.0 - x * x, 0.0, None))
+        out = np.zeros_like(x)
+        pmm = np.full_like(x, 1.0 / math.sqrt(4.0 * math.pi))
+        for m in range(0, self.lmax + 1):
+            if m > 0:
+                pmm = -math.sqrt((2 * m + 1) / (2.0 * m)) * s * pmm
+            ca = np.zeros_like(x)
+            cb = np.zeros_like(x)
+            p_prev, p = None, pmm
+            for l in range(m, self.lmax + 1):
+                if l == m + 1:
+                    p_prev, p = p, math.sqrt(2 * m + 3) * x * pmm
+                elif l > m + 1:
+                    a_ = math.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+                    b_ = math.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
+                    p_prev, p = p, a_ * (x * p - b_ * p_prev)
+                if l >= 1:
+                    if self.a[l, m] != 0.0:
+                        ca += self.a[l, m] * p
+                    if m > 0 and self.b[l, m] != 0.0:
+                        cb += self.b[l, m] * p
+            if m == 0:
+                out += ca
+            else:
+                out += math.sqrt(2.0) * (ca * np.cos(m * lon) + cb * np.sin(m * lon))
         return out
 
 
@@ -166,6 +210,31 @@ class Workload:
             self.bumps = np.stack([np.cos(lat) * np.cos(lon), np.cos(lat) * np.sin(lon), np.sin(lat)], axis=-1)
             self.bump_amp, self.bump_radius = 120.0, 5.0e5
             self._h = _zonal_balance(self._ujet, radius, omega, g, mean_depth)
+        elif kind == "turbulence":
+            # random-phase vorticity with energy spectrum E(l) ~ (l/32)^2 below
+            # degree 32 and (l/32)^-3 above, rms velocity 20 m/s, the stream
+            # function psi_lm = -R^2 zeta_lm / (l (l + 1)) and geostrophic depth
+            # g dh = f0 psi (f0 = 2 Omega sin 45 deg), mean depth 10 km
+            lmax = 96
+            ls = np.arange(lmax + 1, dtype=np.float64)
+            E = np.where(ls < 32, (ls / 32.0) ** 2, (np.maximum(ls, 1.0) / 32.0) ** -3.0)
+            E[0] = 0.0
+            a = np.zeros((lmax + 1, lmax + 1))
+            b = np.zeros((lmax + 1, lmax + 1))
+            for l in range(1, lmax + 1):
+                ca = rng.standard_normal(l + 1)
+                cb = rng.standard_normal(l + 1)
+                cb[0] = 0.0
+                norm = math.sqrt(np.sum(ca ** 2) + np.sum(cb ** 2))
+                # sum_m |psi_lm|^2 l (l + 1) is the degree's share of the kinetic energy
+                amp = math.sqrt(E[l] / (l * (l + 1))) / norm
+                a[l, : l + 1] = amp * ca
+                b[l, : l + 1] = amp * cb
+            ke = sum(l * (l + 1) * (np.sum(a[l] ** 2) + np.sum(b[l, 1:] ** 2)) for l in range(1, lmax + 1))
+            # mean |u|^2 = sum l (l + 1) psi_lm^2 / (4 pi R^2) for orthonormal harmonics
+            scale = 20.0 / math.sqrt(ke / (4.0 * math.pi * radius ** 2))
+            self._psi = _Spectral(lmax, scale * a, scale * b)
+            self.f0 = 2.0 * omega * math.sin(math.pi / 4)
         elif kind in ("tc1_cosine", "tc1_smooth"):
             self.mean_depth = 0.0
             self.u0 = 2.0 * math.pi * radius / (12.0 * DAY)
@@ -207,6 +276,8 @@ class Workload:
             return self._bell(xyz)
         if self.kind == "harmonic":
             return self.mean_depth + self._scale * self._harm(xyz)
+        if self.kind == "turbulence":
+            return self.mean_depth + self.f0 * self._psi(xyz) / self.g
         if lat is None:
             lat, _ = _latlon(xyz)
         h = self._h(lat)
@@ -224,6 +295,8 @@ class Workload:
             psi = lambda p: self.g * self._scale * self._harm(p) / self.f0
             # u = k x grad(psi);  u . t = -d psi / d n_left
             return -_normal_derivative(psi, mid, tan, self.radius)
+        if self.kind == "turbulence":
+            return -_normal_derivative(self._psi, mid, tan, self.radius)
         if self.kind.startswith("tc1"):
             m = mid / np.linalg.norm(mid, axis=-1, keepdims=True)
             return self.u0 * np.sum(np.cross(self.axis, m) * tan, axis=-1)
