@@ -676,7 +676,7 @@ void mask_only(sww_handle* h) {
         // levels above Jmin up to the mask's top level, then the perceptron
         if (h->learn_mode > 0 && j1 > j0) {
             const Span pf = span_of(h, j0 + 1, j1, [](const DevLevel& L) { return L.npatch + 1; });
-            launch_features(dlv<R>(h), pf, h->thr, j0, h->cfg.jmax, s);
+            launch_features(dlv<R>(h), pf, h->thr, j0, h->cfg.jmax, h->all_list, h->all_count, h->grid_all, s);
             if (h->learn_mode > 1) launch_propose(dlv<R>(h), pf, h->net, h->tau, s);
         }
         const Span props = span_of(h, j0 + 1, h->cfg.jmax, [](const DevLevel& L) { return L.npatch + 1; });

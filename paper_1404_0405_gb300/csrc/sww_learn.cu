@@ -36,29 +36,30 @@ __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(_
 // Own features of a patch: log2(1 + max|h~|/eps_h) over its live odd nodes,
 // log2(1 + max|u~|/eps_u) over its live interior edges and the pair coefficients of
 // the coarse edges under its even nodes, and the fraction of its nodes that are
-// live.  An inactive patch has no live point: all three are 0.  A warp takes 32
-// consecutive patches: each lane clears an inactive one, then the warp works
-// through the active ones together (one lane per node of the patch).
+// live.  An inactive patch has no live point: all three are 0 (k_feat_clear, one
+// thread per patch; the pole entry is cleared too and recomputed when listed).
+// The active patches of levels ja..jb come from the active list, one warp per
+// entry (one lane per node of the patch).
 template <class R>
-__global__ void k_feat_own(const DevLevelT<R>* __restrict__ lvs, Span sp, const double* __restrict__ thr) {
+__global__ void k_feat_clear(const DevLevelT<R>* __restrict__ lvs, Span sp) {
+    int j;
+    int64_t P;
+    if (!lfind(sp, lgid(), j, P)) return;
+    const DevLevelT<R>& L = lvs[j];
+    const int64_t np1 = L.npatch + 1;
+    if (P == L.npatch || !L.pflag[P]) L.pfeat[0 * np1 + P] = 0.f, L.pfeat[1 * np1 + P] = 0.f, L.pfeat[6 * np1 + P] = 0.f;
+}
+
+template <class R>
+__global__ void k_feat_own(const DevLevelT<R>* __restrict__ lvs, int ja, int jb, const int32_t* __restrict__ list,
+                           const int32_t* __restrict__ count, const double* __restrict__ thr) {
     const int lane = threadIdx.x & 31;
-    int mj = 0;
-    int64_t mP = 0;
-    bool mine = lfind(sp, lgid(), mj, mP);
-    if (mine) {
-        const DevLevelT<R>& L = lvs[mj];
-        const int64_t np1 = L.npatch + 1;
-        if (mP != L.npatch && !L.pflag[mP]) {
-            L.pfeat[0 * np1 + mP] = 0.f, L.pfeat[1 * np1 + mP] = 0.f, L.pfeat[6 * np1 + mP] = 0.f;
-            mine = false;
-        }
-    }
-    unsigned todo = __ballot_sync(0xffffffffu, mine);
-    while (todo) {
-        const int src = __ffs(todo) - 1;
-        todo &= todo - 1;
-        const int j = __shfl_sync(0xffffffffu, mj, src);
-        const int64_t P = __shfl_sync(0xffffffffu, mP, src);
+    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = lgid() >> 5; w < *count; w += nw) {
+        const int32_t ent = list[w];
+        const int j = ent >> LVL_SHIFT;
+        if (j < ja || j > jb) continue;
+        const int64_t P = ent & PATCH_MASK;
         const DevLevelT<R>& L = lvs[j];
         const DevLevelT<R>& C = lvs[j - 1];
         const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
@@ -300,11 +301,12 @@ MlpWeights mlp_weights(const float* params) {
 
 template <class R>
 void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const double* thr, int jmin, int jmax,
-                     cudaStream_t s) {
+                     const int32_t* active, const int32_t* active_count, unsigned grid, cudaStream_t s) {
     const int64_t n = patches_f.off[patches_f.jb + 1 - patches_f.ja];
     if (n <= 0) return;
-    count_launch(2);
-    k_feat_own<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, thr);
+    count_launch(3);
+    k_feat_clear<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f);
+    k_feat_own<R><<<grid, 256, 0, s>>>(lvs, patches_f.ja, patches_f.jb, active, active_count, thr);
     k_feat_ctx<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, jmin, jmax);
 }
 
@@ -343,8 +345,10 @@ void launch_mlp_predict(const float* X, int64_t n, const float* params, float* o
     k_mlp_predict<<<unsigned(std::min<int64_t>(blocks_for(n, 256), 4096)), 256, 0, s>>>(X, n, params, out);
 }
 
-template void launch_features<double>(const DevLevelT<double>*, const Span&, const double*, int, int, cudaStream_t);
-template void launch_features<float>(const DevLevelT<float>*, const Span&, const double*, int, int, cudaStream_t);
+template void launch_features<double>(const DevLevelT<double>*, const Span&, const double*, int, int, const int32_t*,
+                                      const int32_t*, unsigned, cudaStream_t);
+template void launch_features<float>(const DevLevelT<float>*, const Span&, const double*, int, int, const int32_t*,
+                                     const int32_t*, unsigned, cudaStream_t);
 template void launch_propose<double>(const DevLevelT<double>*, const Span&, const MlpWeights&, float, cudaStream_t);
 template void launch_propose<float>(const DevLevelT<float>*, const Span&, const MlpWeights&, float, cudaStream_t);
 template void launch_prop_roll<double>(const DevLevelT<double>*, const Span&, int, int32_t*, cudaStream_t);

@@ -26,9 +26,10 @@ constexpr int MLP_GRAD_BLOCKS = 256;
 MlpWeights mlp_weights(const float* params);
 
 // features of the patches of patches_f's levels (levels above Jmin)
+// (active, active_count: the all-level active list; grid: blocks of 256 for it)
 template <class R>
 void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const double* thr, int jmin, int jmax,
-                     cudaStream_t s);
+                     const int32_t* active, const int32_t* active_count, unsigned grid, cudaStream_t s);
 // prop[P] = sigmoid(logit) > tau on the same patches
 template <class R>
 void launch_propose(const DevLevelT<R>* lvs, const Span& patches_f, const MlpWeights& w, float tau, cudaStream_t s);
