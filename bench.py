@@ -23,7 +23,7 @@ equal_error: relative l2 error of the Jmin depth after --err-steps steps of the
 same dt, plain and chosen, against a non-adaptive FP64 run (every point live).
 
 --impl reference runs the FP64 CPU oracle on a bounded sample of the same
-workload (the reference arm for this build).  With --gpus N under torchrun every
+workload (the reference arm).  With --gpus N under torchrun every
 rank runs its own members (seeds offset by rank): weak scaling, no collective on
 the data path.
 """

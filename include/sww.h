@@ -315,7 +315,7 @@ int sww_mass_energy_static(sww_handle* h, const double* dh, const double* u, dou
 
 /* ---------------------------------------------------------------------------
  * Learned refinement proposal (an extension: the paper's criterion is the
- * threshold rule of Sec. 2.3, which stays the judge).
+ * threshold rule of Sec. 2.3, which keeps the last word).
  *
  * After the coefficients and thresholds of an adaptation, each patch of the
  * levels above Jmin that hold active patches gets SWW_MLP_FEATURES features:

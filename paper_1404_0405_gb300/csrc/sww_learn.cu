@@ -2,7 +2,7 @@
 // two-layer perceptron (BF16 weights, FP32 accumulation) that proposes patches for
 // the next mask, and its training kernels (loss gradient and Adam).  The exact
 // threshold rules still build the mask; a proposed patch only adds its nodes to
-// the set T before the graded closure, so the plain criterion stays the judge.
+// the set T before the graded closure, so the plain criterion keeps the last word.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -133,7 +133,7 @@ def test_features_match_definition():
 
 def test_trained_proposal_against_plain_criterion():
     """Train on masks the method produces (three seeds), then run a held-out seed
-    with and without the proposal.  The exact rules stay the judge, so the grid
+    with and without the proposal.  The exact rules keep the last word, so the grid
     with the proposal contains the plain one (never fewer live points), and its
     late refinements (patches the exact set reaches that were not active during
     the step) are no more than the plain criterion's.  The counts are printed."""

@@ -7,7 +7,7 @@ turbulence of other seeds at Jmax=8.
 The initial fields are given on level 7 (sww_set_state_level); adaptation
 refines into the finer levels as the flow asks.  Checked at full size:
 
-* the exact rules stay the judge: at the same state, the grid built with the
+* the exact rules keep the last word: at the same state, the grid built with the
   proposal contains every live point of the grid built without it;
 * mass is conserved over adaptive steps with the proposal;
 * late refinements, over-refinement and live cells with and without the proposal
