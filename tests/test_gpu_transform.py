@@ -167,3 +167,20 @@ def test_checkpoint_refuses_foreign_truncated_and_other_grids(tmp_path):
         fp32.load(path)
     b.load(path)                        # the good file still loads
     assert np.array_equal(b.get(5, sww.DH), a.get(5, sww.DH))
+
+
+def test_state_level_error_paths():
+    """A level out of range, and a prescribed velocity set below Jmax, are
+    refused (SWW_E_ARG) and leave the handle usable."""
+    import paper_1404_0405_gb300 as sww
+    m = sww.Model(2, 4, patch=4, eps=1e-2)
+    N3, E3, _, _ = m.sizes(3)
+    with pytest.raises(sww.SwwError):
+        m.set_state(np.zeros(N3), np.zeros(E3), level=5)
+    adv = sww.Model(2, 4, patch=4, eps=1e-2, advect=True, H=0.0)
+    with pytest.raises(sww.SwwError):
+        adv.set_state(np.zeros(N3), np.zeros(E3), level=3)
+    m.set_state(np.full(N3, 3.0), np.zeros(E3), level=3)
+    m.adapt()
+    h4, u4 = m.get_state(4)
+    assert np.abs(h4 - 3.0).max() < 1e-12 and np.abs(u4).max() == 0.0
