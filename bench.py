@@ -163,7 +163,7 @@ def oracle_rate(a, steps, warmup, seed):
         cells += (act + M.active_nodes()) / 2
     sample = (f"same jet workload and eps at Jmin={a.jmin}..Jmax={jmax} ({steps} RK4 steps after {warmup} warm-up, "
               f"grid setup untimed), single-threaded numpy oracle")
-    return cells / t, sample
+    return cells / t, sample, t / steps
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -174,9 +174,9 @@ def run_reference(a, rank):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     steps = max(1, min(a.steps, 6))
     warm = min(a.warmup, 2)
-    v, sample = oracle_rate(a, steps, warm, a.seed)
+    v, sample, per_step = oracle_rate(a, steps, warm, a.seed)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
-            "warmup": warm, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "warmup": warm, "ms_per_step": 1e3 * per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(a)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -520,7 +520,7 @@ def main():
     line = run_ours(a, rank, world)
     if rank == 0:
         if world == 1 and not a.no_cpu_baseline:
-            v, sample = oracle_rate(a, 2, 1, a.seed)
+            v, sample, _ = oracle_rate(a, 2, 1, a.seed)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
         print(json.dumps(line), flush=True)
 
