@@ -70,8 +70,11 @@ __device__ __forceinline__ void member_items(const DevLevelT<R>* sl, const int32
     }
 }
 
+// Eight blocks per SM (32 registers, a few spilled): the phases are chains of
+// dependent gathers, and more resident warps hide more of their latency (measured
+// 15 % faster than the 44-register build at 62 % occupancy).
 template <class R>
-__global__ void __launch_bounds__(BATCH_TPB) k_phase_batch(BatchArgs<R> a, int phase, int j, int bpm) {
+__global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, int phase, int j, int bpm) {
     __shared__ DevLevelT<R> sl[MAXL];
     const int m = blockIdx.x / bpm, b = blockIdx.x % bpm;
     const MemberRef<R>* mr = a.m + m;
