@@ -211,10 +211,10 @@ STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
 
 # DRAM bytes (read + write) of the batched RK stage (the k_phase_batch launches of
 # one stage) per live member-cell, from one ncu capture of the same jet at
-# Jmin=4..Jmax=8 with 16 members (198.4 MB per stage over 302 856 member-cells,
+# Jmin=4..Jmax=8 with 16 members (203.8 MB per stage over 302 856 member-cells,
 # cold cache per launch; profiles/k_phase_batch_jet_J4-8_16members.md), scaled to a
 # launch by the member-cells it processes; remove the entry when the kernel changes.
-PHASE_TRAFFIC_PER_CELL_STAGE = {"fp32": 655.0}
+PHASE_TRAFFIC_PER_CELL_STAGE = {"fp32": 673.0}
 
 
 def _live(m):
