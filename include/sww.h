@@ -93,10 +93,10 @@ typedef struct {
                           2: inside sww_step_ensemble, each member's stage as one
                           thread-block cluster (up to 16 blocks, hardware barriers
                           between the phases); 3: inside sww_step_ensemble, one regular
-                          launch per phase of each RK stage over all members (the
-                          members' other work overlaps on their streams); -1: one
-                          launch per phase always.  Falls back to -1 where the chosen
-                          launch cannot run.                                          */
+                          launch per phase of the step over all members, each
+                          member's mask on its own stream (see sww_step_ensemble);
+                          -1: one launch per phase always.  Falls back to -1 where
+                          the chosen launch cannot run.                               */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
     double nu;         /* viscosity (m^2/s) of the viscous form (Sec. 3.1): nu div grad dh
@@ -194,17 +194,22 @@ int sww_rhs(sww_handle* h);
 int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
 
 /* nsteps steps of each of n independent ensemble members (distinct handles, each
- * as sww_step alone would advance it).  Every member's step runs on the member's
- * own stream, so the members' kernels overlap on the GPU; each member waits only
- * for its own previous step.  With more than one member the RK stages run as one
- * launch per phase (cooperative launches of different streams do not overlap),
- * unless every member has persistent = 1 (or every member 3) and they share
- * precision, Jmin, patch, H, g and scheme: then each RK stage of all members is
- * one cooperative launch (3: one regular launch per phase over all members)
- * between the members' other work (all members synchronise at every stage).  On entry each member's work is ordered after its
- * caller stream, and on return each caller stream waits for its member.
- * Returns the first error; members then stand at different step counts
- * (sww_stats_get tells which). */
+ * as sww_step alone would advance it, bit for bit).  By default every member's
+ * step runs on the member's own stream, so the members' kernels overlap on the
+ * GPU and each member waits only for its own previous step; with more than one
+ * member the RK stages then run as one launch per phase (cooperative launches of
+ * different streams do not overlap).  When every member has persistent = 1, or
+ * every member 3, and they share precision, Jmin, patch, H, g and scheme (at most
+ * 128 members):
+ *   1: each RK stage of all members is one cooperative launch on the first
+ *      member's stream between the members' other work;
+ *   3: every phase of the step but the mask (time step, RK base, stage phases,
+ *      partial transform, ghosts, coefficients, thresholds, inverse transform,
+ *      read-back) is one regular launch over all members on the first member's
+ *      stream; each member's mask runs on its own stream in between.
+ * On entry each member's work is ordered after its caller stream, and on return
+ * each caller stream waits for its member.  Returns the first error; members
+ * then stand at different step counts (sww_stats_get tells which). */
 int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int adapt);
 
 /* Copy one per-level quantity (SWW_DH ... SWW_SIG) to the host. */
