@@ -41,3 +41,26 @@ def test_error_path_without_compute():
     lib.sww_last_error(buf, 256)
     assert b"jmin" in buf.value
     assert lib.sww_step(None, 1.0, 1, 1) == -1
+
+
+def test_config_checks_without_compute():
+    """Each configuration field out of its range is refused before any device
+    call: the prescribed-velocity flag, the threshold regime, the stage mode,
+    a zero mean depth without a prescribed velocity, a negative viscosity."""
+    import ctypes
+    import paper_1404_0405_gb300 as sww
+    lib = sww.load()
+
+    def cfg(**kw):
+        c = sww.Config(2, 4, 6.371e6, 7.292e-5, 9.80616, 1e4, 8, 0, 0.8, 1e-2)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(256)
+    for kw, word in [({"advect": 2}, b"advect"), ({"regime": 3}, b"regime"), ({"persistent": 4}, b"persistent"),
+                     ({"H": 0.0}, b"H"), ({"nu": -1.0}, b"nu"), ({"eps": -1.0}, b"eps")]:
+        assert lib.sww_create(ctypes.byref(cfg(**kw)), None, ctypes.byref(h)) == -1, kw
+        lib.sww_last_error(buf, 256)
+        assert word in buf.value, (kw, buf.value)
