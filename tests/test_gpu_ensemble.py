@@ -148,3 +148,33 @@ def test_autotuner_picks_the_fastest_trial(tmp_path, monkeypatch):
     assert all(t["rate"] > 0 for t in trials)
     again, _ = autotune.tune(2, 4, 1e-2, fields_of, members=2, patches=(4, 8), blocks=(2, 4), key_extra="test")
     assert again == best                              # cached
+
+
+@pytest.mark.parametrize("adapt", [True, False])
+def test_phased_members_with_proposal_match_single_runs(adapt):
+    """The batched step with each member's learned proposal on (random perceptron
+    weights, so that patches get proposed), and without adaptation: bit for bit
+    the members stepped alone."""
+    import paper_1404_0405_gb300 as sww
+    rng = np.random.default_rng(5)
+    params = rng.normal(0.0, 0.5, sww.MLP_PARAMS).astype(np.float32)
+    jmin, top = 2, max(j for j, _, _ in MEMBERS)
+    base = sww.Model(jmin, top, patch=4)
+    ens, alone = [], []
+    for jmax, eps, seed in MEMBERS:
+        for group in (ens, alone):
+            m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision="fp32", persistent="phased")
+            m.set_state(*_fields(m, seed))
+            m.adapt()
+            m.set_learned(2, params, 0.5)
+            group.append(m)
+    sww.step_ensemble(ens, -1.0, 3, adapt)
+    for m in alone:
+        m.step(-1.0, 3, adapt)
+    for a, b in zip(ens, alone):
+        fa, sa = _snapshot(sww, a)
+        fb, sb = _snapshot(sww, b)
+        assert sa == sb
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+        assert a.learn_stats() == b.learn_stats()
