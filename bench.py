@@ -139,6 +139,32 @@ class Clocks:
 
 # ----------------------------------------------------------------------------- oracle sample
 
+def host_cpu():
+    """Model name and logical core count of the host (context for the CPU figures)."""
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"model": model, "logical_cores": os.cpu_count()}
+
+
 def oracle_rate(a, steps, warmup, seed):
     """Active-cell steps/s of the FP64 CPU oracle on the same workload at
     Jmin..cpu_jmax (grid setup untimed)."""
@@ -178,7 +204,8 @@ def run_reference(a, rank):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
             "warmup": warm, "ms_per_step": 1e3 * per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(a)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -521,7 +548,8 @@ def main():
     if rank == 0:
         if world == 1 and not a.no_cpu_baseline:
             v, sample, _ = oracle_rate(a, 2, 1, a.seed)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                    "host": host_cpu()}
         print(json.dumps(line), flush=True)
 
 
