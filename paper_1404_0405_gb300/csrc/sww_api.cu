@@ -1204,9 +1204,16 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
     });
 }
 
+// host input: every value finite (checked before the device sees it)
+static bool all_finite(const double* x, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
 int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
     if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
-    return set_state_at(h, dh, u, h->cfg.jmax, device_ptrs);
+    return sww_set_state_level(h, h->cfg.jmax, dh, u, device_ptrs);
 }
 
 int sww_set_state_level(sww_handle* h, int level, const double* dh, const double* u, int device_ptrs) {
@@ -1215,6 +1222,8 @@ int sww_set_state_level(sww_handle* h, int level, const double* dh, const double
     if (rc) return rc;
     if (h->cfg.advect && level != h->cfg.jmax)
         return fail(SWW_E_ARG, "a prescribed velocity is set on Jmax (it holds on every level)");
+    if (!device_ptrs && !(all_finite(dh, meta(h, level).N) && all_finite(u, meta(h, level).E)))
+        return fail(SWW_E_NUMERIC, "non-finite value in the initial fields");
     return set_state_at(h, dh, u, level, device_ptrs);
 }
 

@@ -184,3 +184,21 @@ def test_state_level_error_paths():
     m.adapt()
     h4, u4 = m.get_state(4)
     assert np.abs(h4 - 3.0).max() < 1e-12 and np.abs(u4).max() == 0.0
+
+
+def test_non_finite_initial_fields_are_refused():
+    """A NaN or an infinity in host initial fields is refused (SWW_E_NUMERIC)
+    before any device work; valid fields then load as usual."""
+    import paper_1404_0405_gb300 as sww
+    m, (dh, u) = _member(sww, "fp32", jmax=4)
+    for bad_dh, bad_u in ((dh.copy(), u), (dh, u.copy())):
+        arr = bad_dh if bad_dh is not dh else bad_u
+        arr[len(arr) // 2] = np.nan if arr is bad_dh else np.inf
+        with pytest.raises(sww.SwwError, match="non-finite"):
+            m.set_state(bad_dh, bad_u)
+    with pytest.raises(sww.SwwError):
+        m.step(-1.0, 1, True)            # nothing was loaded
+    m.set_state(dh, u)
+    m.adapt()
+    m.step(-1.0, 1, True)
+    assert np.isfinite(m.stats()["mass"])
