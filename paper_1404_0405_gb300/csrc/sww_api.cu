@@ -1204,11 +1204,13 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
     });
 }
 
-// host input: every value finite (checked before the device sees it)
+// host input: every value finite (checked before the device sees it; one pass
+// over the host cores)
 static bool all_finite(const double* x, int64_t n) {
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(x[i])) return false;
-    return true;
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad) schedule(static)
+    for (int64_t i = 0; i < n; ++i) bad |= std::isfinite(x[i]) ? 0 : 1;
+    return bad == 0;
 }
 
 int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
