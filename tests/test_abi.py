@@ -64,3 +64,22 @@ def test_config_checks_without_compute():
         assert lib.sww_create(ctypes.byref(cfg(**kw)), None, ctypes.byref(h)) == -1, kw
         lib.sww_last_error(buf, 256)
         assert word in buf.value, (kw, buf.value)
+
+
+def test_header_is_plain_c_and_links():
+    """include/sww.h compiles as pedantic C99, and a C program using it links
+    against the library (no GPU needed to build; examples/step.c)."""
+    import shutil
+    import subprocess
+    import tempfile
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    path = build()
+    with tempfile.TemporaryDirectory() as d:
+        obj, exe = os.path.join(d, "step.o"), os.path.join(d, "step")
+        subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                        os.path.join(ROOT, "include"), "-c", os.path.join(ROOT, "examples", "step.c"), "-o", obj],
+                       check=True)
+        subprocess.run([gcc, obj, "-L", os.path.dirname(path), "-lsww", "-lm", "-o", exe], check=True)
