@@ -692,4 +692,77 @@ void build_hierarchy(Hierarchy& H, int jmin, int jmax, int patch, double R, doub
     for (int j = jmin + 1; j <= jmax; ++j) pair_tables(H.lv[j - 1], H.lv[j], R);
 }
 
+// Every id a device gather reads lies in its array: a first bad entry is named in
+// *what.  (-1 marks the documented absent entries: ring slots past a pentagon's
+// fifth, parents of even nodes, M_k past its last member.)
+bool validate_tables(const Hierarchy& H, std::string* what) {
+    auto bad = [&](const char* table, int j, int64_t i, int64_t v) {
+        if (what) *what = std::string(table) + " of level " + std::to_string(j) + " at " + std::to_string(i) +
+                          " holds " + std::to_string(v);
+        return false;
+    };
+    auto in = [](int64_t v, int64_t n) { return v >= 0 && v < n; };
+    for (int j = H.jmin; j <= H.jmax; ++j) {
+        const HostLevel& L = H.lv[j];
+        const int64_t N = L.N, E = L.E, T = L.T;
+        for (int k = 0; k < 2; ++k)
+            for (int64_t e = 0; e < E; ++e) {
+                if (!in(L.en[k][e], N)) return bad("en", j, e, L.en[k][e]);
+                if (!in(L.et[k][e], T)) return bad("et", j, e, L.et[k][e]);
+            }
+        for (int k = 0; k < 3; ++k)
+            for (int64_t t = 0; t < T; ++t) {
+                if (!in(L.tn[k][t], N)) return bad("tn", j, t, L.tn[k][t]);
+                if (!in(L.te[k][t] >> 1, E)) return bad("te", j, t, L.te[k][t]);
+            }
+        for (int64_t i = 0; i < N; ++i) {
+            const int dg = L.deg[i];
+            if (dg != 5 && dg != 6) return bad("deg", j, i, dg);
+            for (int k = 0; k < 6; ++k) {
+                const bool used = k < dg;
+                if (used ? !in(L.ring_e[k][i] >> 1, E) : L.ring_e[k][i] != -1) return bad("ring_e", j, i, L.ring_e[k][i]);
+                if (used ? !in(L.ring_n[k][i], N) : L.ring_n[k][i] != -1) return bad("ring_n", j, i, L.ring_n[k][i]);
+                if (used ? !in(L.ring_t[k][i], T) : L.ring_t[k][i] != -1) return bad("ring_t", j, i, L.ring_t[k][i]);
+            }
+        }
+        for (int k = 0; k < COR; ++k)
+            for (int64_t e = 0; e < E; ++e)
+                if (!in(L.cor_i[k][e], E)) return bad("cor_i", j, e, L.cor_i[k][e]);
+        if (j > H.jmin) {
+            const HostLevel& C = H.lv[j - 1];
+            for (int64_t i = 0; i < N; ++i) {
+                const bool odd = L.par[0][i] >= 0;
+                for (int k = 0; k < 4; ++k)
+                    if (odd ? !in(L.par[k][i], N) : L.par[k][i] != -1) return bad("par", j, i, L.par[k][i]);
+            }
+            for (int64_t e = 0; e < E; ++e) {
+                const int kind = L.fe_kind[e];
+                if (kind < 0 || kind > 2) return bad("fe_kind", j, e, kind);
+                // a half names its coarse edge, an interior edge 3 t + c (coarse triangle t)
+                if (!in(L.fe_ce[e], kind == 2 ? 3 * C.T : C.E)) return bad("fe_ce", j, e, L.fe_ce[e]);
+                for (int k = 0; k < VST; ++k)
+                    if (!in(L.vst[k][e], C.E)) return bad("vst", j, e, L.vst[k][e]);
+            }
+        }
+        if (j < H.jmax) {
+            const HostLevel& F = H.lv[j + 1];
+            for (int64_t i = 0; i < N; ++i) {
+                if (!in(L.c2f[i], F.N)) return bad("c2f", j, i, L.c2f[i]);
+                for (int k = 0; k < 12; ++k)
+                    if (L.mk_i[k][i] != -1 && !in(L.mk_i[k][i], F.N)) return bad("mk_i", j, i, L.mk_i[k][i]);
+            }
+            for (int64_t e = 0; e < E; ++e) {
+                if (!in(L.mid[e], F.N)) return bad("mid", j, e, L.mid[e]);
+                for (int k = 0; k < 2; ++k)
+                    if (!in(L.half[k][e], F.E)) return bad("half", j, e, L.half[k][e]);
+                for (int k = 0; k < RF_F; ++k)
+                    if (!in(L.rf_fi[k][e], F.E)) return bad("rf_fi", j, e, L.rf_fi[k][e]);
+                for (int k = 0; k < RF_C; ++k)
+                    if (!in(L.rf_ci[k][e], F.N)) return bad("rf_ci", j, e, L.rf_ci[k][e]);
+            }
+        }
+    }
+    return true;
+}
+
 }  // namespace sww

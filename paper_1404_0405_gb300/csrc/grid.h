@@ -11,6 +11,7 @@
 // The two poles are nodes nelem (north) and nelem + 1 (south).
 #pragma once
 #include <cstdint>
+#include <string>
 #include <vector>
 
 namespace sww {
@@ -77,5 +78,9 @@ void build_hierarchy(Hierarchy& H, int jmin, int jmax, int patch, double radius,
 
 // Table 1 mean spacing sqrt(2 * 4 pi R^2 / (sqrt(3) N_j)).
 double nominal_spacing(int j, double radius);
+
+// Bounds of every index table the device gathers through (false and a message
+// naming the first bad entry otherwise).
+bool validate_tables(const Hierarchy& H, std::string* what);
 
 }  // namespace sww

@@ -381,6 +381,10 @@ std::shared_ptr<Geometry> build_geometry(int jmin, int jmax, int patch, double r
     G->jmin = jmin, G->jmax = jmax, G->patch = patch, G->radius = radius, G->omega = omega;
     Hierarchy H;
     build_hierarchy(H, jmin, jmax, patch, radius, omega);
+    // every id a kernel gathers through must lie in its array (the kernels do not
+    // check them again)
+    std::string what;
+    if (!validate_tables(H, &what)) throw std::runtime_error("grid table out of bounds: " + what);
     G->lv.assign(jmax + 1, DevLevel{});
     G->xyz.assign(jmax + 1, {});
     G->edges.assign(jmax + 1, {});

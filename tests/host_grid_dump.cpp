@@ -31,13 +31,21 @@ static void put_slots(const std::string& dir, const std::string& name, const std
 
 int main(int argc, char** argv) {
     if (argc != 5) {
-        std::fprintf(stderr, "usage: %s JMIN JMAX PATCH OUTDIR\n", argv[0]);
+        std::fprintf(stderr, "usage: %s JMIN JMAX PATCH OUTDIR|--check|--check-corrupt\n", argv[0]);
         return 1;
     }
     int jmin = std::atoi(argv[1]), jmax = std::atoi(argv[2]), patch = std::atoi(argv[3]);
     std::string dir = argv[4];
     Hierarchy H;
     build_hierarchy(H, jmin, jmax, patch, 6.371e6, 7.292e-5);
+    if (dir == "--check" || dir == "--check-corrupt") {
+        // the table validator on the built grid, or on one planted out-of-range id
+        if (dir == "--check-corrupt") H.lv[jmax].cor_i[3][H.lv[jmax].E / 2] = int32_t(H.lv[jmax].E);
+        std::string what;
+        const bool ok = validate_tables(H, &what);
+        std::printf("%s\n", ok ? "tables ok" : what.c_str());
+        return ok ? 0 : 3;
+    }
     for (int j = jmin; j <= jmax; ++j) {
         HostLevel& L = H.lv[j];
         std::string p = "L" + std::to_string(j) + "_";

@@ -35,7 +35,19 @@ def dump(tmp_path_factory):
         a = np.fromfile(out / name, dtype=dtype)
         return a.reshape(shape) if shape else a
 
+    rd.exe = exe
     return rd
+
+
+@pytest.mark.parametrize("patch", [1, 4, 8, 16])
+def test_index_tables_in_bounds(dump, patch):
+    """Every id the device gathers through lies in its array (the validator the
+    library runs on each grid it builds), for every patch side; a planted
+    out-of-range id is found and named."""
+    ok = subprocess.run([dump.exe, "2", "6", str(patch), "--check"], capture_output=True, text=True)
+    assert ok.returncode == 0 and ok.stdout.strip() == "tables ok", ok.stdout
+    bad = subprocess.run([dump.exe, "2", "6", str(patch), "--check-corrupt"], capture_output=True, text=True)
+    assert bad.returncode == 3 and bad.stdout.startswith("cor_i of level 6"), bad.stdout
 
 
 @pytest.fixture(scope="module")
