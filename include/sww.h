@@ -217,6 +217,11 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int a
 /* Copy one per-level quantity (SWW_DH ... SWW_SIG) to the host. */
 int sww_get_level(const sww_handle* h, int level, int what, void* out);
 
+/* The adapted grid of level j (Sec. 2.3): node flags nodes[N_j] and edge flags
+ * edges[E_j] as in SWW_NODE_FLAGS / SWW_EDGE_FLAGS (bit 0 live, bit 1 ghost,
+ * bit 2 covered); either pointer may be null. */
+int sww_get_mask(const sww_handle* h, int level, uint8_t* nodes, uint8_t* edges);
+
 /* Write the depth perturbation and velocity of level j (host arrays). */
 int sww_set_level(sww_handle* h, int level, const double* dh, const double* u);
 

@@ -30,7 +30,8 @@ EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_
            "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
            "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
            "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
-           "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level"]
+           "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level",
+           "sww_get_mask"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
@@ -108,6 +109,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_save": [P, ctypes.c_char_p],
         "sww_load": [P, ctypes.c_char_p],
         "sww_set_state_level": [P, I, P, P, I],
+        "sww_get_mask": [P, I, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -266,6 +268,14 @@ class Model:
             raise ValueError(what)
         _check(load().sww_get_level(self._h, level, what, _ptr(out)[0]))
         return out
+
+    def mask(self, level):
+        """(node flags [N_j], edge flags [E_j]) of level j: bit 0 live, 1 ghost, 2 covered."""
+        N, E, _, _ = self.sizes(level)
+        nodes, edges = np.empty(N, dtype=np.uint8), np.empty(E, dtype=np.uint8)
+        _check(load().sww_get_mask(self._h, level, nodes.ctypes.data_as(ctypes.c_void_p),
+                                   edges.ctypes.data_as(ctypes.c_void_p)))
+        return nodes, edges
 
     def forward(self):
         _check(load().sww_forward(self._h))

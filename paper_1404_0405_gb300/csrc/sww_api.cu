@@ -1496,6 +1496,14 @@ int sww_get_level(const sww_handle* h, int level, int what, void* out) {
     });
 }
 
+int sww_get_mask(const sww_handle* h, int level, uint8_t* nodes, uint8_t* edges) {
+    int rc = check_level(h, level);
+    if (rc) return rc;
+    if (nodes && (rc = sww_get_level(h, level, SWW_NODE_FLAGS, nodes))) return rc;
+    if (edges && (rc = sww_get_level(h, level, SWW_EDGE_FLAGS, edges))) return rc;
+    return SWW_OK;
+}
+
 int sww_set_level(sww_handle* h, int level, const double* dh, const double* u) {
     int rc = check_level(h, level);
     if (rc) return rc;

@@ -202,3 +202,14 @@ def test_non_finite_initial_fields_are_refused():
     m.adapt()
     m.step(-1.0, 1, True)
     assert np.isfinite(m.stats()["mass"])
+
+
+def test_mask_call_matches_level_flags():
+    import paper_1404_0405_gb300 as sww
+    P = Pair(2, 4, kind="jet", seed=6)
+    P.adapt()
+    for j in range(2, 5):
+        nodes, edges = P.lib.mask(j)
+        assert np.array_equal(nodes, P.lib.get(j, sww.NODE_FLAGS))
+        assert np.array_equal(edges, P.lib.get(j, sww.EDGE_FLAGS))
+    P.check_masks()
