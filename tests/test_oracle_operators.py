@@ -87,18 +87,37 @@ def test_resting_state_has_zero_trend(L3):
     assert np.abs(a).max() == 0.0 and np.abs(b).max() == 0.0
 
 
-def test_tc2_balance_improves_with_resolution():
-    """Williamson TC2 is steady; its trend (the discrete imbalance) shrinks in the
-    rms with resolution (Sec. 6.2)."""
+def test_tc2_imbalance_order():
+    """Williamson TC2 (Sec. 6.2) is an exact steady state: the zonal mass flux has
+    zero divergence and the Coriolis force balances the Bernoulli gradient.  The
+    trend of the sampled state is the discrete imbalance, so its decay with
+    resolution is the operators' order of accuracy on this grid.
+
+    On the plain bisection grid (no Heikes-Randall or Xu optimisation, Sec. 3.2)
+    the divergence part converges at first order in the rms (the depth trend
+    falls by about 2.2-2.4 per level, J3..6), while the velocity imbalance falls
+    by only about 1.4 per level in the rms and not at all in the maximum: the
+    known inconsistency of TRiSK's Coriolis and kinetic-energy operators on
+    unoptimised icosahedral grids.  The paper's second-order statement is for its
+    optimised grids.  A sign or weight slip in div, grad, K or q F^perp breaks
+    these rates (the imbalance then stays O(1) of the terms)."""
     g = 9.80616
-    rms = []
-    for J in (3, 4, 5):
+    rms_h, rms_u, max_u = [], [], []
+    for J in (3, 4, 5, 6):
         L = grid.Hierarchy(J, J).levels[J]
         W = workloads.Workload("tc2", mean_depth=2.94e4 / g)
         dh, u = W.fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
         a, b = trisk.trend(L, dh, u, 2.94e4 / g, g)
-        rms.append(math.sqrt(np.mean(b ** 2)))
-    assert rms[1] < rms[0] and rms[2] < rms[1]
+        rms_h.append(math.sqrt(np.mean(a ** 2)))
+        rms_u.append(math.sqrt(np.mean(b ** 2)))
+        max_u.append(np.abs(b).max())
+    rate_h = [rms_h[k] / rms_h[k + 1] for k in range(3)]
+    rate_u = [rms_u[k] / rms_u[k + 1] for k in range(3)]
+    print("TC2 depth-trend rms ratios", rate_h, "velocity-trend rms ratios", rate_u)
+    assert all(1.9 < r < 2.8 for r in rate_h), rate_h          # first order
+    assert all(1.25 < r < 1.6 for r in rate_u), rate_u         # about half order in the rms
+    # the imbalance is a small fraction of the balanced terms (f u ~ 3e-3 m/s^2)
+    assert max(max_u) < 0.15 * 7.292e-5 * 2 * (2 * math.pi * 6.371e6 / (12 * 86400))
 
 
 # ----------------------------------------------------------------------------- transforms
