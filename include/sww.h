@@ -299,6 +299,17 @@ enum {
  * SWW_K_PARTIAL for the partial transform and ghosts after the stages). */
 int sww_profile(sww_handle* h, uint32_t class_mask);
 
+/* Fault injection for tests of the bounded grid barrier of the persistent RK
+ * stage (no counterpart in the paper).  Every barrier wait of the handle's later
+ * stages gives up after spin_cycles SM clock cycles (0: the default, about 2 s),
+ * sets the handle's error flag and lets the stage kernel return; the step then
+ * returns SWW_E_TIMEOUT without advancing t, and the barrier state is reset so
+ * that the next step runs normally.  skip_block >= 0 makes that block of each
+ * persistent stage leave at its first barrier without arriving, so that the other
+ * blocks' waits run out (-1: no block skips).  Synchronises the handle's stream and
+ * drops its captured steps.  SWW_E_ARG for a null handle or spin_cycles < 0. */
+int sww_barrier_fault(sww_handle* h, long long spin_cycles, int skip_block);
+
 /* Sum of the recorded durations (ms[SWW_K_NCLASS]) and of the kernel launches
  * inside the records (launches[SWW_K_NCLASS]) per class since sww_profile;
  * synchronises the stream and clears the records (recording continues). */
@@ -317,12 +328,18 @@ int sww_profile_read(sww_handle* h, double* ms, int64_t* launches);
  * The per-block partial sums go to a fixed 128 KiB device array inside the
  * library (resident on every GPU that loads it, until the process exits), which
  * bounds N_Jmin to 1,048,576 nodes (Jmin <= 8); larger levels return SWW_E_ARG.
+ * dh, u and out must be device or managed memory (checked with
+ * cudaPointerGetAttributes; SWW_E_ARG otherwise); their lengths cannot be seen
+ * here, so the caller guarantees N_Jmin, E_Jmin and 2 values.
  * The call is asynchronous on the caller's stream given to sww_create (dh, u
  * and out are read and written in that stream's order) and makes no cudaMalloc,
  * cudaFree or other allocating call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Every call reuses the same array: calls whose work may
- * overlap on the GPU (other streams, other handles on the same device) race. */
+ * array's device address (cudaGetSymbolAddress) and keeps it for the process;
+ * make that first call before any stream capture, and do not use the call on a
+ * device after a cudaDeviceReset of it.  Every call reuses the same array:
+ * calls whose work may overlap on the GPU (other streams, other handles on the
+ * same device) race.  A CUDA error already pending when the call starts gives
+ * SWW_E_CUDA before any launch. */
 int sww_mass_energy_static(sww_handle* h, const double* dh, const double* u, double* out);
 
 /* ---------------------------------------------------------------------------

@@ -31,13 +31,20 @@ EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_
            "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
            "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
            "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level",
-           "sww_get_mask"]
+           "sww_get_mask", "sww_barrier_fault"]
 KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
 
 class SwwError(RuntimeError):
-    pass
+    """A failed call; ``code`` is the library's negative status (SWW_E_*)."""
+
+    def __init__(self, msg, code=0):
+        super().__init__(msg)
+        self.code = code
+
+
+E_ARG, E_CUDA, E_POOL, E_TIMEOUT, E_STATE, E_NUMERIC = -1, -2, -3, -4, -5, -6
 
 
 class Config(ctypes.Structure):
@@ -110,6 +117,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_load": [P, ctypes.c_char_p],
         "sww_set_state_level": [P, I, P, P, I],
         "sww_get_mask": [P, I, P, P],
+        "sww_barrier_fault": [P, ctypes.c_longlong, I],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -123,7 +131,7 @@ def _check(rc):
     if rc != 0:
         buf = ctypes.create_string_buffer(1024)
         _lib.sww_last_error(buf, 1024)
-        raise SwwError(f"sww error {rc}: {buf.value.decode(errors='replace')}")
+        raise SwwError(f"sww error {rc}: {buf.value.decode(errors='replace')}", rc)
 
 
 def _ptr(a):
@@ -338,8 +346,23 @@ class Model:
 
     def mass_energy_static(self, dh, u, out):
         """Mass and energy of level Jmin into out[2] without any device allocation
-        (dh, u, out: torch CUDA float64 tensors; asynchronous on the caller's stream)."""
+        (dh[N_Jmin], u[E_Jmin], out[2]: contiguous torch CUDA float64 tensors;
+        asynchronous on the caller's stream).  The C call cannot see array lengths,
+        so the tensors are checked here before it."""
+        N, E, _, _ = self.sizes(self.jmin)
+        for name, t, n in (("dh", dh, N), ("u", u, E), ("out", out, 2)):
+            ok = (hasattr(t, "is_cuda") and t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()
+                  and t.numel() == n)
+            if not ok:
+                raise SwwError(f"mass_energy_static: {name} must be a contiguous CUDA float64 tensor of {n} values",
+                               E_ARG)
         _check(load().sww_mass_energy_static(self._h, _ptr(dh)[0], _ptr(u)[0], _ptr(out)[0]))
+
+    def barrier_fault(self, spin_cycles=0, skip_block=-1):
+        """Fault injection for tests of the persistent stage's bounded barrier
+        (sww_barrier_fault): waits give up after spin_cycles clock cycles (0: the
+        default) and block skip_block leaves without arriving (-1: none)."""
+        _check(load().sww_barrier_fault(self._h, int(spin_cycles), int(skip_block)))
 
     # ------------------------------------------------------------------ learned proposal
     def set_learned(self, mode, params=None, tau=0.5):

@@ -18,7 +18,10 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsww.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no contraction into fused multiply-adds, so that the host's grid
+# tables and sums come out the same on x86-64 and on aarch64
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--extended-lambda", "-Xcompiler", "-fPIC", "-Xcompiler", "-fopenmp",
+          "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu", "sww_learn.cu", "sww_stage.cu", "sww_mask.cu",
            "sww_batch.cu"]

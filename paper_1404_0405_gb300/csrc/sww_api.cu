@@ -163,6 +163,10 @@ struct sww_handle {
     // persistent RK stages: blocks of the cooperative launch (0: one launch per phase),
     // barrier state and the error flag of a timed-out barrier (device and pinned copy)
     unsigned stage_blocks = 0, stage_cap = 0;
+    // bounded barrier waits of the persistent stage: spin limit in clock cycles
+    // (0: the default) and a block that skips its arrival (fault injection, -1: none)
+    long long spin_cycles = 0;
+    int skip_block = -1;
     // RK stages as one thread-block cluster of cluster_cap blocks (members of an
     // overlapped ensemble step); 0 when clusters of stage blocks cannot run
     int cluster_cap = 0;
@@ -575,7 +579,8 @@ void stage(sww_handle* h, const RKStage& st) {
     }
     Trace t(h, SWW_K_STAGE);
     StageArgs<R> a{dlv<R>(h), h->all_list, h->all_count, h->S, h->cfg.jmin, h->jtop, h->cfg.jmax,
-                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err, h->use_cluster ? 1 : 0};
+                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err, h->use_cluster ? 1 : 0,
+                   h->spin_cycles, h->skip_block};
     if (h->use_cluster)
         ck(launch_stage_cluster(a, h->cluster_cap, h->stream), "cluster stage launch");
     else
@@ -1921,6 +1926,18 @@ int sww_learn_stats(sww_handle* h, int64_t* out, int reset) {
         }
         ck(cudaStreamSynchronize(h->stream), "learn stats");
         for (int k = 0; k < 3; ++k) out[k] = int64_t(c[k]);
+        return SWW_OK;
+    });
+}
+
+int sww_barrier_fault(sww_handle* h, long long spin_cycles, int skip_block) {
+    if (!h) return fail(SWW_E_ARG, "null handle");
+    if (spin_cycles < 0) return fail(SWW_E_ARG, "spin_cycles < 0");
+    return guarded([&]() -> int {
+        ck(cudaStreamSynchronize(h->stream), "barrier fault");
+        h->spin_cycles = spin_cycles;
+        h->skip_block = skip_block < 0 ? -1 : skip_block;
+        h->drop_graphs();   // captured steps hold the stage arguments
         return SWW_OK;
     });
 }

@@ -69,13 +69,17 @@ __global__ void k_sums_static_final(const double* part, int nblk, double g, doub
         neumaier_add(s1, c1, part[4 * b + 2]);
         neumaier_add(s1, c1, part[4 * b + 3]);
     }
-    double mass = s0 + c0;
-    double c2 = g * mass / area;
+    // the same roundings as the host's resting-state subtraction in sww_stats_get
+    // (no fused multiply-adds), so that both report the same bits
+    const double mass = s0 + c0;
+    const double c2 = __ddiv_rn(__dmul_rn(g, mass), area);
     out[0] = mass;
-    out[1] = (s1 + c1) - 0.5 * c2 * c2 * area;
+    out[1] = __dsub_rn(s1 + c1, __dmul_rn(__dmul_rn(__dmul_rn(0.5, c2), c2), area));
 }
 
-// Device address of g_partials per device, looked up once per device.
+// Device address of g_partials per device, looked up once per device (a
+// cudaDeviceReset of that device ends the library's use of it, as it ends every
+// handle there).
 std::mutex g_mu;
 double* g_addr[64] = {nullptr};
 
@@ -105,6 +109,20 @@ extern "C" int sww_mass_energy_static(sww_handle* h, const double* dh, const dou
     if (nblk > kMaxBlocks)
         return sww::set_error(SWW_E_ARG, "sww_mass_energy_static: Jmin level has more than 1,048,576 nodes "
                                          "(the static scratch holds 4096 blocks of 256)");
+    // the three arrays must be device (or managed) memory: a host address would
+    // reach the kernels (cudaPointerGetAttributes allocates nothing)
+    for (const void* p : {static_cast<const void*>(dh), static_cast<const void*>(u), static_cast<const void*>(out)}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return sww::set_error(SWW_E_ARG, "sww_mass_energy_static: a pointer is not known to CUDA");
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+            return sww::set_error(SWW_E_ARG, "sww_mass_energy_static: dh, u and out must be device memory");
+    }
+    // an error left pending by earlier work is reported as such, not as this call's
+    if (cudaError_t pending = cudaPeekAtLastError(); pending != cudaSuccess)
+        return sww::set_error(SWW_E_CUDA, "sww_mass_energy_static: an earlier CUDA error is pending");
     double* part = nullptr;
     int rc = partials_address(&part);
     if (rc != SWW_OK) return rc;

@@ -41,12 +41,19 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // Grid-wide barrier, two-level: a block arrives at one of GROUPS counters (each in
 // its own 128-byte line), the last of a group at the root counter, and the last of
 // all advances the generation word that the others wait on.  False when the wait
-// timed out or another block reported an error.
-__device__ bool grid_sync(unsigned* bar, int* err) {
+// timed out (after `spin` cycles, <= 0: SPIN_CYCLES) or a block has reported an
+// error; a block that finds the error flag already set does not arrive, so no
+// block passes a barrier once a wait has failed.  Block `skip` (fault injection,
+// -1: none) leaves without arriving.
+__device__ bool grid_sync(unsigned* bar, int* err, long long spin = 0, int skip = -1) {
     __shared__ int ok;
     __syncthreads();
+    if (threadIdx.x == 0) ok = 1;
+    if (threadIdx.x == 0 && (int(blockIdx.x) == skip || *reinterpret_cast<volatile int*>(err))) ok = 0;
+    __syncthreads();
+    if (!ok) return false;
     if (threadIdx.x == 0) {
-        ok = 1;
+        const long long limit = spin > 0 ? spin : SPIN_CYCLES;
         const unsigned groups = gridDim.x < BAR_GROUPS ? gridDim.x : BAR_GROUPS;
         const unsigned grp = blockIdx.x % groups;
         const unsigned in_grp = (gridDim.x - grp + groups - 1) / groups;
@@ -73,7 +80,7 @@ __device__ bool grid_sync(unsigned* bar, int* err) {
                     ok = 0;
                     break;
                 }
-                if (clock64() - t0 > SPIN_CYCLES) {
+                if (clock64() - t0 > limit) {
                     atomicExch(err, 1);
                     ok = 0;
                     break;
@@ -97,7 +104,7 @@ __device__ __forceinline__ bool stage_sync(const StageArgs<R>& a) {
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
         return true;
     }
-    return grid_sync(a.bar, a.err);
+    return grid_sync(a.bar, a.err, a.spin, a.skip);
 }
 
 template <class R>

@@ -29,6 +29,11 @@ struct StageArgs {
     unsigned* bar;
     int* err;
     int cluster;   // 1: the launch is one thread-block cluster (hardware barrier)
+    // bounded barrier waits: a wait gives up after `spin` clock cycles (<= 0: the
+    // default, about 2 s); block `skip` (fault injection for tests, -1: none) leaves
+    // at the first barrier without arriving, so the others' waits run out
+    long long spin = 0;
+    int skip = -1;
 };
 
 // One member of an ensemble stage: its level records (contiguous, levels 0..jmax),

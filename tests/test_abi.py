@@ -41,6 +41,12 @@ def test_error_path_without_compute():
     lib.sww_last_error(buf, 256)
     assert b"jmin" in buf.value
     assert lib.sww_step(None, 1.0, 1, 1) == -1
+    # the allocation-free diagnostics and the barrier fault hook refuse a null
+    # handle before touching CUDA
+    assert lib.sww_mass_energy_static(None, None, None, None) == -1
+    lib.sww_last_error(buf, 256)
+    assert b"null handle" in buf.value
+    assert lib.sww_barrier_fault(None, 0, -1) == -1
 
 
 def test_config_checks_without_compute():

@@ -32,14 +32,14 @@ class Pair:
     """An oracle model and a library model on the same grid and initial state."""
 
     def __init__(self, jmin, jmax, kind="jet", seed=0, eps=1e-2, rk="rk4", patch=4, precision="fp64", nu=0.0,
-                 advect=False, alpha=0.0, persistent=True, regime=0):
+                 advect=False, alpha=0.0, persistent=True, regime=0, share=None):
         import paper_1404_0405_gb300 as sww
         self.sww = sww
         self.Hy = grid.Hierarchy(jmin, jmax)
         H = 0.0 if advect else 1.0e4       # the advection test carries the bell itself
         self.ora = model.Model(self.Hy, H=H, eps=eps, rk=rk, nu=nu, advect=advect, regime=regime)
         self.lib = sww.Model(jmin, jmax, H=H, patch=patch, eps=eps, rk=rk, precision=precision, nu=nu,
-                             advect=advect, persistent=persistent, regime=regime)
+                             advect=advect, persistent=persistent, regime=regime, share=share)
         self.maps = {}
         for j in range(jmin, jmax + 1):
             xyz, en = self.lib.grid(j)

@@ -39,3 +39,47 @@ def test_persistent_stage_matches_phase_launches(precision, advect):
         assert np.array_equal(x, y, equal_nan=True)
     assert sa["mass"] == sb["mass"] and sa["t"] == sb["t"]
     assert sa["kernel_launches"] > 0
+
+
+def test_barrier_wait_runs_out_and_recovers():
+    """The bounded grid barrier: with a short spin limit and one block told (on
+    the host) not to arrive, every other block's wait runs out, the kernel
+    returns, the step reports SWW_E_TIMEOUT without advancing t, and after the
+    fault is cleared the next step equals a step of a handle that never failed.
+    No wait outlasts the limit (about 1 ms here), so nothing hangs."""
+    import paper_1404_0405_gb300 as sww
+
+    def fresh():
+        m = sww.Model(2, 5, patch=4, eps=1e-2, persistent=True)
+        xyz, en = m.grid(5)
+        mid, tan = lib_edge_geometry(xyz, en)
+        dh, u = workloads.Workload("jet", seed=6).fields(xyz, mid, tan)
+        m.set_state(dh, u)
+        m.adapt()
+        return m
+
+    m = fresh()
+    t0 = m.stats()["t"]
+    m.barrier_fault(spin_cycles=2_000_000, skip_block=0)
+    with pytest.raises(sww.SwwError) as ei:
+        m.step(-1.0, 1, True)
+    assert ei.value.code == sww.E_TIMEOUT
+    assert m.stats()["t"] == t0 and m.stats()["steps"] == 0
+    # a second failing step: the reset barrier state times out the same way
+    with pytest.raises(sww.SwwError) as ei:
+        m.step(-1.0, 1, True)
+    assert ei.value.code == sww.E_TIMEOUT
+    m.barrier_fault(0, -1)
+    m.step(-1.0, 1, True)
+    ref = fresh()
+    ref.step(-1.0, 1, True)
+    sm, sr = m.stats(), ref.stats()
+    assert sm["steps"] == 1 and sm["t"] == sr["t"]
+    for j in range(2, 6):
+        for what in (sww.NODE_FLAGS, sww.EDGE_FLAGS):
+            assert np.array_equal(m.get(j, what), ref.get(j, what)), (j, what)
+        for what in (sww.DH, sww.U):
+            x, y = m.get(j, what), ref.get(j, what)
+            live = (m.get(j, sww.NODE_FLAGS if what == sww.DH else sww.EDGE_FLAGS) & sww.LIVE) > 0
+            scale = max(np.abs(y[live]).max(), 1e-300)
+            assert np.abs(x[live] - y[live]).max() <= 1e-12 * scale, (j, what)
