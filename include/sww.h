@@ -81,22 +81,22 @@ typedef struct {
     double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u| (see regime); 0 keeps every point */
     int blocks_per_sm; /* work-list launches: blocks of 256 threads per SM (0: 4)           */
     int precision;     /* SWW_FP64: fields and arithmetic in FP64.  SWW_FP32: fields,
-                          stencils and transforms in FP32 with weights rounded once from
-                          the FP64 tables; thresholds, time step and the compensated
-                          mass/energy sums in FP64 on the FP32 values.  The ABI's
-                          double arrays are converted at the boundary.                */
+                          stencils and transforms in FP32; the spherical geometry
+                          (areas, lengths, kite areas, Coriolis parameter, TRiSK
+                          weights) stays FP64 on the device and is rounded as it
+                          enters FP32 arithmetic, the transform weights are the FP64
+                          tables rounded once; thresholds, time step and the
+                          compensated mass/energy sums in FP64 on the FP32 values.
+                          The ABI's double arrays are converted at the boundary.     */
     int persistent;    /* RK stages.  0: one cooperative launch per stage (all phases of
                           the trend and the update, grid barriers between them) for a
                           handle stepping alone, one launch per phase inside
-                          sww_step_ensemble (the members' steps then overlap); 1: also
-                          one cooperative launch per stage over all ensemble members;
-                          2: inside sww_step_ensemble, each member's stage as one
-                          thread-block cluster (up to 16 blocks, hardware barriers
-                          between the phases); 3: inside sww_step_ensemble, one regular
-                          launch per phase of the step over all members, each
-                          member's mask on its own stream (see sww_step_ensemble);
-                          -1: one launch per phase always.  Falls back to -1 where
-                          the chosen launch cannot run.                               */
+                          sww_step_ensemble (the members' steps then overlap); 3:
+                          inside sww_step_ensemble, one regular launch per phase of
+                          the step over all members, each member's mask on its own
+                          stream (see sww_step_ensemble); -1: one launch per phase
+                          always.  Falls back to -1 where the cooperative launch
+                          cannot run.  Other values give SWW_E_ARG.                  */
     int mask;          /* 0: mask passes over candidate patches (near the active grid);
                           1: dense passes over every point of the levels (same mask)    */
     double nu;         /* viscosity (m^2/s) of the viscous form (Sec. 3.1): nu div grad dh
@@ -200,15 +200,12 @@ int sww_step(sww_handle* h, double dt, int nsteps, int adapt);
  * step runs on the member's own stream, so the members' kernels overlap on the
  * GPU and each member waits only for its own previous step; with more than one
  * member the RK stages then run as one launch per phase (cooperative launches of
- * different streams do not overlap).  When every member has persistent = 1, or
- * every member 3, and they share precision, Jmin, patch, H, g and scheme (at most
- * 128 members):
- *   1: each RK stage of all members is one cooperative launch on the first
- *      member's stream between the members' other work;
- *   3: every phase of the step but the mask (time step, RK base, stage phases,
- *      partial transform, ghosts, coefficients, thresholds, inverse transform,
- *      read-back) is one regular launch over all members on the first member's
- *      stream; each member's mask runs on its own stream in between.
+ * different streams do not overlap).  When every member has persistent = 3 and
+ * they share precision, Jmin, patch, H, g and scheme (at most 128 members),
+ * every phase of the step but the mask (time step, RK base, stage phases,
+ * partial transform, ghosts, coefficients, thresholds, inverse transform,
+ * read-back) is one regular launch over all members on the first member's
+ * stream; each member's mask runs on its own stream in between.
  * On entry each member's work is ordered after its caller stream, and on return
  * each caller stream waits for its member.  Returns the first error; members
  * then stand at different step counts (sww_stats_get tells which). */
@@ -273,10 +270,11 @@ int sww_stats_get(sww_handle* h, sww_stats* st);
 
 /* Kernel classes timed by the tracing hook below. */
 enum {
-    SWW_K_PV = 0,        /* potential vorticity at triangles                         */
-    SWW_K_FLUX = 1,      /* thickness flux at edges                                  */
+    SWW_K_TREND = 0,     /* the structured trend of every active patch: F, q, div F,
+                            K, B, q F^perp of the regular tiles, F and q elsewhere   */
+    SWW_K_IRREG = 1,     /* div F, K, B and q F^perp at the irregular patches        */
     SWW_K_NODE = 2,      /* divergence of the restricted fluxes at coarse nodes      */
-    SWW_K_CORIOLIS = 3,  /* energy-conserving q F^perp at live edges                 */
+    SWW_K_RESERVED = 3,  /* (no launches)                                            */
     SWW_K_RESTRICT = 4,  /* restriction of B, F and q F^perp                         */
     SWW_K_UPDATE = 5,    /* trends and Runge-Kutta stage combination                 */
     SWW_K_FILL = 6,      /* ghost prolongation                                       */
@@ -293,9 +291,9 @@ enum {
  * around every launch group of the kernel classes whose bit is set in class_mask
  * (bit k for class k); 0 stops recording.  Previous records are discarded.  While
  * any class is traced, sww_step runs its kernels directly instead of replaying
- * the captured graph.  In sww_step_ensemble with batched stages (persistent 1
- * or 3) the first member's records cover the batched launches of all members
- * (SWW_K_STAGE per RK stage; with 3 also SWW_K_DT for the time step and RK base,
+ * the captured graph.  In sww_step_ensemble with batched stages (persistent 3)
+ * the first member's records cover the batched launches of all members
+ * (SWW_K_STAGE per RK stage, SWW_K_DT for the time step and RK base,
  * SWW_K_PARTIAL for the partial transform and ghosts after the stages). */
 int sww_profile(sww_handle* h, uint32_t class_mask);
 

@@ -32,7 +32,7 @@ EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_
            "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
            "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level",
            "sww_get_mask", "sww_barrier_fault"]
-KERNEL_CLASSES = ["pv", "flux", "node", "coriolis", "restrict", "update", "fill", "partial", "coeff", "mask",
+KERNEL_CLASSES = ["trend", "irregular", "node", "reserved", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
 
@@ -185,17 +185,15 @@ class Model:
                  cfl=0.8, eps=1e-2, stream=None, share=None, blocks_per_sm=0, precision="fp64", persistent=True,
                  mask="lists", nu=0.0, advect=False, regime=0):
         """share: another Model whose grid and tables this one reuses (sww_create_shared).
-        persistent: True/"auto", "always" (also batched over ensemble members),
-        "cluster" (ensemble members' stages as thread-block clusters), "phased"
-        (ensemble stages as one launch per phase over all members) or
-        False/"never" (see sww_config.persistent).  advect: prescribed velocity
+        persistent: True/"auto", "phased" (ensemble steps as one launch per
+        phase over all members) or False/"never" (see sww_config.persistent).  advect: prescribed velocity
         (see sww_config.advect).  regime: 1 scales the thresholds by eps^{3/2}
         (see sww_config.regime)."""
         lib = load()
         self.jmin, self.jmax = jmin, jmax
         self.cfg = Config(jmin, jmax, radius, omega, g, H, patch, RK4 if rk == "rk4" else SSP43, cfl, eps,
                           blocks_per_sm, {"fp64": 0, "fp32": 1}[precision],
-                          {True: 0, "auto": 0, "always": 1, "cluster": 2, "phased": 3, False: -1, "never": -1}[persistent],
+                          {True: 0, "auto": 0, "phased": 3, False: -1, "never": -1}[persistent],
                           {"lists": 0, "dense": 1}[mask], float(nu), int(bool(advect)), int(regime))
         h = ctypes.c_void_p()
         st = stream if stream is not None else _default_stream()

@@ -24,7 +24,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "--extended-lambda", "-Xcompiler", "
           "-Xcompiler", "-ffp-contract=off",
           "-I", os.path.join(ROOT, "include"), "-I", CSRC]
 SOURCES = ["grid.cpp", "sww_kernels.cu", "sww_api.cu", "sww_noalloc.cu", "sww_learn.cu", "sww_stage.cu", "sww_mask.cu",
-           "sww_batch.cu"]
+           "sww_batch.cu", "sww_tile.cu"]
 # per-file flags: the persistent stage reads values other blocks wrote earlier in the
 # same launch, so its global loads are cached in L2 only
 EXTRA = {"sww_stage.cu": ["-Xptxas", "-dlcm=cg"]}

@@ -9,6 +9,8 @@
 // where the text is silent are stated next to the code that applies them.
 #include "grid.h"
 
+#include "tile.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -319,6 +321,118 @@ void build_geometry(HostLevel& L, double R, double omega) {
             }
         }
         for (; slot < COR; ++slot) L.cor_i[slot][e] = int32_t(e), L.cor_w[slot][e] = 0.0;
+    }
+}
+
+// ----------------------------------------------------------------------------- tiles
+
+// Halo tables of the structured trend kernel (tile.h).  For each patch the local
+// lattice is laid out from its own elements by walking ring neighbours: a node at
+// local position (a, b) whose ring slot k0 points along +a has its neighbour in
+// direction m at ring slot (k0 + m) mod 6, and that neighbour's +a slot follows
+// from where the walk came in.  A tile is regular when every node of its range
+// has six neighbours and every walk agrees; otherwise (a pentagon or a pole in
+// reach, a level whose patch side is not `patch`) it is marked irregular and the
+// kernels take the tabulated path there.
+void build_tiles(HostLevel& L, int patch) {
+    L.tile_halo.clear();
+    L.tile_irr.assign(L.npatch + 1, 1);
+    const int p = int(L.p);
+    if (!(patch == 4 || patch == 8 || patch == 16) || p != patch) return;
+    const tile::Shape S{p};
+    const int W = p + 3, HALO = S.halo();
+    L.tile_halo.assign(size_t(L.npatch) * HALO, -1);
+    Lay Y = layout_of(L);
+    const int64_t np = L.np;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t P = 0; P < L.npatch; ++P) {
+        const int64_t d = P / (np * np), pi = (P / np) % np, pj = P % np;
+        std::vector<int64_t> gid(W * W, -1);
+        std::vector<int> k0(W * W, -1), queue;
+        auto at = [&](int a, int b) { return (a + 1) * W + (b + 1); };
+        auto inside = [&](int a, int b) { return a >= -1 && a <= p + 1 && b >= -1 && b <= p + 1; };
+        // seed: the patch's first element; its +a neighbour is lattice node (i + 1, j)
+        const int64_t v0 = Y.elem(d, pi * p, pj * p), w0 = Y.node(d, pi * p + 1, pj * p);
+        for (int k = 0; k < L.deg[v0]; ++k)
+            if (L.ring_n[k][v0] == w0) k0[at(0, 0)] = k;
+        gid[at(0, 0)] = v0;
+        queue.push_back(at(0, 0));
+        bool ok = k0[at(0, 0)] >= 0;
+        for (size_t qi = 0; qi < queue.size() && ok; ++qi) {
+            const int s = queue[qi], a = s / W - 1, b = s % W - 1;
+            const int64_t v = gid[s];
+            if (L.deg[v] != 6) {
+                ok = false;
+                break;
+            }
+            for (int m = 0; m < 6 && ok; ++m) {
+                const int a2 = a + tile::da(m), b2 = b + tile::db(m);
+                if (!inside(a2, b2)) continue;
+                const int64_t w = L.ring_n[(k0[s] + m) % 6][v];
+                if (L.deg[w] != 6) {
+                    ok = false;
+                    break;
+                }
+                int kv = -1;
+                for (int k = 0; k < 6; ++k)
+                    if (L.ring_n[k][w] == v) kv = k;
+                const int kw = ((kv - (m + 3)) % 6 + 6) % 6;
+                const int s2 = at(a2, b2);
+                if (gid[s2] < 0) {
+                    gid[s2] = w, k0[s2] = kw;
+                    queue.push_back(s2);
+                } else if (gid[s2] != w || k0[s2] != kw) {
+                    ok = false;
+                }
+            }
+        }
+        if (!ok || int(queue.size()) != W * W) continue;
+        // the interior is the patch's own elements, their edges and triangles
+        for (int a = 0; a < p && ok; ++a)
+            for (int b = 0; b < p && ok; ++b) {
+                const int s = at(a, b);
+                const int64_t el = Y.elem(d, pi * p + a, pj * p + b);
+                if (gid[s] != el) ok = false;
+                for (int o = 0; o < 3; ++o)
+                    if (L.ring_e[(k0[s] + o) % 6][gid[s]] != int32_t(2 * (o * L.nelem + el))) ok = false;
+                for (int t = 0; t < 2; ++t)
+                    if (L.ring_t[(k0[s] + t) % 6][gid[s]] != int32_t(t * L.nelem + el)) ok = false;
+            }
+        if (!ok) throw std::runtime_error("tile: interior of a regular patch does not follow the layout");
+        int32_t* H = L.tile_halo.data() + size_t(P) * HALO;
+        for (int s = 0; s < S.nodes(); ++s) {
+            int a, b;
+            tile::pos(p, p + 1, s, a, b);
+            H[s] = int32_t(gid[at(a, b)]);
+        }
+        for (int o = 0; o < 3; ++o)
+            for (int s = 0; s < S.edges(o); ++s) {
+                int a, b;
+                tile::pos(p, S.eB(o), s, a, b);
+                const int q = at(a, b), q2 = at(a + tile::da(o), b + tile::db(o));
+                const int32_t code = L.ring_e[(k0[q] + o) % 6][gid[q]];
+                const int64_t e = code >> 1;
+                const int64_t other = L.en[(code & 1) ? 0 : 1][e];
+                if (other != gid[q2]) throw std::runtime_error("tile: halo edge does not reach its end node");
+                H[S.off_edge(o) + s] = code;
+            }
+        for (int t = 0; t < 2; ++t)
+            for (int s = 0; s < S.tris(); ++s) {
+                int a, b;
+                tile::pos(p, p, s, a, b);
+                const int q = at(a, b);
+                const int64_t tri = L.ring_t[(k0[q] + t) % 6][gid[q]];
+                // local vertices: t0 (a,b), (a+1,b), (a+1,b+1); t1 (a,b), (a+1,b+1), (a,b+1)
+                const int64_t v0l = gid[q];
+                int sft = -1;
+                for (int c = 0; c < 3; ++c)
+                    if (L.tn[c][tri] == v0l) sft = c;
+                const int64_t v1l = gid[t == 0 ? at(a + 1, b) : at(a + 1, b + 1)];
+                if (sft < 0 || L.tn[(1 + sft) % 3][tri] != v1l)
+                    throw std::runtime_error("tile: halo triangle does not hold its nodes in order");
+                H[S.off_tri(t) + s] = int32_t(4 * tri + sft);
+            }
+        L.tile_irr[P] = 0;
     }
 }
 
@@ -658,6 +772,7 @@ void build_hierarchy(Hierarchy& H, int jmin, int jmax, int patch, double R, doub
         if (j >= jmin) {
             build_topology(cur);
             build_geometry(cur, R, omega);
+            build_tiles(cur, patch);
             H.lv[j] = std::move(cur);
             prev.xyz = H.lv[j].xyz;
             prev.J = j, prev.n = H.lv[j].n, prev.p = H.lv[j].p, prev.np = H.lv[j].np, prev.nelem = H.lv[j].nelem, prev.N = H.lv[j].N;
@@ -728,6 +843,21 @@ bool validate_tables(const Hierarchy& H, std::string* what) {
         for (int k = 0; k < COR; ++k)
             for (int64_t e = 0; e < E; ++e)
                 if (!in(L.cor_i[k][e], E)) return bad("cor_i", j, e, L.cor_i[k][e]);
+        if (int64_t(L.tile_irr.size()) != L.npatch + 1) return bad("tile_irr", j, 0, int64_t(L.tile_irr.size()));
+        if (!L.tile_halo.empty()) {
+            const tile::Shape S{int(L.p)};
+            const int HALO = S.halo();
+            if (int64_t(L.tile_halo.size()) != L.npatch * HALO) return bad("tile_halo", j, 0, int64_t(L.tile_halo.size()));
+            for (int64_t P = 0; P < L.npatch; ++P) {
+                if (L.tile_irr[P]) continue;
+                const int32_t* H = L.tile_halo.data() + P * HALO;
+                for (int s = 0; s < HALO; ++s) {
+                    const int64_t v = H[s];
+                    const bool ok = s < S.off_edge(0) ? in(v, N) : s < S.off_tri(0) ? in(v >> 1, E) : in(v >> 2, T) && (v & 3) < 3;
+                    if (!ok) return bad("tile_halo", j, P * HALO + s, v);
+                }
+            }
+        }
         if (j > H.jmin) {
             const HostLevel& C = H.lv[j - 1];
             for (int64_t i = 0; i < N; ++i) {

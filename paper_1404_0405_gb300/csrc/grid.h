@@ -64,6 +64,9 @@ struct HostLevel {
     std::vector<double> rf_fw[RF_F];  //                  weights on fine F (per unit length)
     std::vector<int32_t> rf_ci[RF_C]; //                  fine node ids
     std::vector<double> rf_cw[RF_C];  //                  weights on fine divergences
+    // tiles of the structured trend kernel (tile.h), for patch sides 4, 8 and 16
+    std::vector<int32_t> tile_halo;   // [npatch * halo]: halo ids of each patch (empty without tiles)
+    std::vector<uint8_t> tile_irr;    // [npatch + 1]: 1 where the tile is not regular (the last: poles)
 };
 
 struct Hierarchy {

@@ -84,7 +84,8 @@ struct Geometry {
     int jmin = 0, jmax = 0, patch = 0;
     double radius = 0, omega = 0;
     std::vector<DevLevel> lv;                 // geometry pointers only (FP64 tables)
-    std::vector<DevLevelT<float>> lvf;        // the same with FP32 stencil weights (on demand)
+    std::vector<DevLevelT<float>> lvf;        // the same with FP32 transform weights (on demand)
+    std::vector<int64_t> n_irr;               // entries per level whose tile is not regular (poles included)
     std::mutex mu;
     std::vector<std::vector<double>> xyz;     // host node positions per level (flattened)
     std::vector<std::vector<int32_t>> edges;  // host edge (origin, end) pairs per level
@@ -103,8 +104,8 @@ struct Geometry {
         for (int k = 0; k < count; ++k) std::memcpy(flat.data() + k * n, v[k].data(), n * sizeof(T));
         return up(flat);
     }
-    // FP32 copies of the stencil weights (rounded once from the FP64 tables); the
-    // FP64 areas and lengths stay for the mass and energy sums
+    // FP32 copies of the transform weights (rounded once from the FP64 tables); the
+    // geometry and the TRiSK weights stay FP64
     void ensure_fp32() {
         std::lock_guard<std::mutex> lock(mu);
         if (!lvf.empty()) return;
@@ -118,16 +119,16 @@ struct Geometry {
             F.cor_i = D.cor_i, F.par = D.par, F.fe_kind = D.fe_kind, F.fe_ce = D.fe_ce, F.vst = D.vst;
             F.c2f = D.c2f, F.mid = D.mid, F.half = D.half, F.mk_i = D.mk_i, F.rf_fi = D.rf_fi, F.rf_ci = D.rf_ci;
             F.ppar = D.ppar, F.pnbr = D.pnbr, F.pchild = D.pchild;
-            F.A_i64 = D.A_i64, F.d_e64 = D.d_e64, F.l_e64 = D.l_e64;
+            F.thalo = D.thalo, F.tirr = D.tirr;
+            // the geometry stays FP64 (no FP32 copies)
+            F.A_i = D.A_i, F.A_v = D.A_v, F.kite = D.kite, F.d_e = D.d_e, F.l_e = D.l_e, F.f_v = D.f_v;
+            F.f_n = D.f_n, F.cor_w = D.cor_w;
             auto cv = [&](const double* x, int64_t n) -> const float* {
                 if (!x) return nullptr;
                 float* y = dev_alloc<float>(allocs, n);
                 launch_convert(x, y, n, cudaStream_t(0));
                 return y;
             };
-            F.A_i = cv(D.A_i, D.N), F.A_v = cv(D.A_v, D.T), F.kite = cv(D.kite, 3 * D.T);
-            F.d_e = cv(D.d_e, D.E), F.l_e = cv(D.l_e, D.E), F.f_v = cv(D.f_v, D.T), F.f_n = cv(D.f_n, D.N);
-            F.cor_w = cv(D.cor_w, int64_t(COR) * D.E);
             F.ptw = cv(D.ptw, 4 * D.N);
             F.vw = cv(D.vw, int64_t(VST) * D.E);
             F.mk_w = cv(D.mk_w, 12 * D.N);
@@ -159,6 +160,7 @@ struct sww_handle {
     int learn_mode = 0;
     float tau = 0.5f;
     MlpWeights net{};
+    MlpWeights* d_net = nullptr;   // device copy of net (the mask kernels read it)
     unsigned long long* lstat = nullptr;   // [3] misses, over-refined, proposed (cumulative)
     // persistent RK stages: blocks of the cooperative launch (0: one launch per phase),
     // barrier state and the error flag of a timed-out barrier (device and pinned copy)
@@ -167,10 +169,6 @@ struct sww_handle {
     // (0: the default) and a block that skips its arrival (fault injection, -1: none)
     long long spin_cycles = 0;
     int skip_block = -1;
-    // RK stages as one thread-block cluster of cluster_cap blocks (members of an
-    // overlapped ensemble step); 0 when clusters of stage blocks cannot run
-    int cluster_cap = 0;
-    bool use_cluster = false;
     // buffers of ensemble steps led by this handle (allocated on first use)
     struct {
         uint8_t* refs = nullptr;    // device MemberRef array
@@ -190,6 +188,10 @@ struct sww_handle {
     unsigned long long *red = nullptr, *cnt = nullptr;
     double *thr = nullptr, *dt = nullptr, *part = nullptr, *sums = nullptr;
     int32_t *all_list = nullptr, *all_count = nullptr, *d_counts = nullptr, *sig_any = nullptr;
+    // entries of all_list whose tile is not regular, and a bound on their number
+    int32_t *irr_list = nullptr, *irr_count = nullptr;
+    int64_t irr_bound = 0;
+    uint8_t* self_ref = nullptr;    // device MemberRef of this handle (its own trend launches)
     // candidate lists of the list-based mask (all levels)
     int32_t *cand = nullptr, *cand_count = nullptr, *gcand = nullptr, *gcand_count = nullptr;
     int64_t total_entries = 0;
@@ -293,9 +295,16 @@ void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side
     D.ring_e = G.up_slots(L.ring_e, 6);
     D.A_i = G.up(L.A_i), D.A_v = G.up(L.A_v), D.kite = G.up_slots(L.kite, 3);
     D.d_e = G.up(L.d_e), D.l_e = G.up(L.l_e), D.f_v = G.up(L.f_v), D.f_n = G.up(L.f_n);
-    D.A_i64 = D.A_i, D.d_e64 = D.d_e, D.l_e64 = D.l_e;
     D.cor_i = G.up_slots(L.cor_i, COR);
     D.cor_w = G.up_slots(L.cor_w, COR);
+    D.thalo = L.tile_halo.empty() ? nullptr : G.up(L.tile_halo);
+    D.tirr = G.up(L.tile_irr);
+    {
+        int64_t n = 0;
+        for (uint8_t f : L.tile_irr) n += f;
+        if (int64_t(G.n_irr.size()) <= L.J) G.n_irr.resize(L.J + 1, 0);
+        G.n_irr[L.J] = n;
+    }
     if (fine_side) {
         D.par = G.up_slots(L.par, 4);
         D.ptw = G.up_slots(L.ptw, 4);
@@ -553,10 +562,15 @@ void trend(sww_handle* h) {
     const int j0 = h->cfg.jmin;
     cudaStream_t s = h->stream;
     auto& lv = lvl<R>(h);
-    WorkT<R> W = work_all<R>(h);
     fill_ghosts<R>(h);
-    { Trace t(h, SWW_K_PV); launch_pv_flux(W, h->cfg.H, s); }
-    { Trace t(h, SWW_K_CORIOLIS); launch_node_coriolis(W, h->cfg.g, s); }
+    {
+        // the structured trend of every active patch, then the irregular patches'
+        // node and Coriolis terms (one member: this handle)
+        BatchArgs<R> a{reinterpret_cast<const MemberRef<R>*>(h->self_ref), 1, h->S, j0, h->jtop, h->cfg.H, h->cfg.g,
+                       RKStage{}, nullptr, nullptr, 0.0, nullptr};
+        { Trace t(h, SWW_K_TREND); ck(launch_tile_trend(a, h->total_entries, h->irr_bound, h->nsm, 1, s), "trend"); }
+        { Trace t(h, SWW_K_IRREG); ck(launch_tile_trend(a, h->total_entries, h->irr_bound, h->nsm, 2, s), "trend"); }
+    }
     for (int j = h->jtop - 1; j >= j0; --j) {
         { Trace t(h, SWW_K_RESTRICT); launch_restrict(lv[j], lv[j + 1], work_level<R>(h, j), s); }
         { Trace t(h, SWW_K_NODE); launch_div(lv[j], work_level<R>(h, j), s); }
@@ -572,19 +586,15 @@ void update(sww_handle* h, const RKStage& st) {
 // trend and RK stage: one persistent cooperative launch, or one launch per phase
 template <class R>
 void stage(sww_handle* h, const RKStage& st) {
-    if (!h->stage_blocks && !h->use_cluster) {
+    if (!h->stage_blocks) {
         trend<R>(h);
         update<R>(h, st);
         return;
     }
     Trace t(h, SWW_K_STAGE);
-    StageArgs<R> a{dlv<R>(h), h->all_list, h->all_count, h->S, h->cfg.jmin, h->jtop, h->cfg.jmax,
-                   h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err, h->use_cluster ? 1 : 0,
-                   h->spin_cycles, h->skip_block};
-    if (h->use_cluster)
-        ck(launch_stage_cluster(a, h->cluster_cap, h->stream), "cluster stage launch");
-    else
-        ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
+    StageArgs<R> a{dlv<R>(h), h->all_list, h->all_count, h->irr_list, h->irr_count, h->S, h->cfg.jmin, h->jtop,
+                   h->cfg.jmax, h->cfg.H, h->cfg.g, st, h->dt, h->bar, h->err, h->spin_cycles, h->skip_block};
+    ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
 }
 
 // SWW_E_TIMEOUT (and the flag cleared) when a persistent stage's barrier timed out
@@ -673,42 +683,62 @@ MaskArgsT<R> mask_args(const sww_handle* h, int j0, int j1, bool allow_tail = tr
 // and can gain none in one adaptation, so the byte-wide passes stop there.
 // significance, proposal, mask, patch lists (Sec. 2.3), from the stored
 // coefficients and thresholds
+// The member record of a handle's mask (levels Jmin..min(top + 1, jmax)).
+template <class R>
+MaskMember<R> mask_member(const sww_handle* h) {
+    MaskMember<R> m{};
+    m.lvs = dlv<R>(h);
+    m.active = h->all_list, m.active_count = h->all_count;
+    m.cand = h->cand, m.cand_count = h->cand_count, m.gcand = h->gcand, m.gcand_count = h->gcand_count;
+    m.all = h->all_list, m.all_count = h->all_count, m.irr = h->irr_list, m.irr_count = h->irr_count;
+    m.thr = h->thr, m.sig_any = h->sig_any, m.lstat = h->lstat, m.net = h->d_net;
+    m.logit_tau = std::log(h->tau / (1.f - h->tau));
+    m.learn = h->learn_mode;
+    m.jb = std::min(h->jtop + 1, h->cfg.jmax), m.jmax = h->cfg.jmax;
+    return m;
+}
+
+// The shared part of a mask batch over members whose largest jb and jmax are
+// given (their grids are the same as h's).
+template <class R, int CAP>
+void mask_batch_head(MaskBatch<R, CAP>& b, const sww_handle* h, int nm, int jb_max, int jmax_max) {
+    const int j0 = h->cfg.jmin;
+    auto np1 = [](const DevLevel& L) { return L.npatch + 1; };
+    auto empty = [&]() {
+        Span sp{};
+        sp.ja = sp.jb = j0, sp.tail_j = -1;
+        return sp;
+    };
+    b.nm = nm, b.P = h->S, b.ja = j0, b.jb_max = jb_max, b.jmax_max = jmax_max;
+    b.hops = GHOST_HOPS, b.rings = h->cfg.patch >= 8 ? 1 : 2;
+    b.patches = span_of(h, j0, jb_max, np1);
+    b.patches_f = jb_max > j0 ? span_of(h, j0 + 1, jb_max, np1) : empty();
+    b.props = jmax_max > j0 ? span_of(h, j0 + 1, jmax_max, np1) : empty();
+}
+
+// the candidate lists need patches of at least 4 x 4 (one or two rings reach the
+// five hops of the ghost band)
+bool list_mask(const sww_handle* h) { return h->cfg.mask == 0 && h->cfg.patch >= 4; }
+
+// Significance, proposal, mask, patch lists (Sec. 2.3), from the stored
+// coefficients and thresholds: the learned proposal for this mask (features of the
+// current coefficients on the levels above Jmin up to the mask's top level, then
+// the perceptron), the mask, and the all-level and irregular lists.
 template <class R>
 void mask_only(sww_handle* h) {
     const int j0 = h->cfg.jmin, j1 = std::min(h->jtop + 1, h->cfg.jmax);
     cudaStream_t s = h->stream;
-    {
-        Trace tm(h, SWW_K_MASK);
-        MaskArgsT<R> a = mask_args<R>(h, j0, j1);
-        ck(cudaMemsetAsync(h->sig_any, 0, sizeof(int32_t) * (h->cfg.jmax + 2), s), "memset sig_any");
-        // learned proposal for this mask: features of the current coefficients on the
-        // levels above Jmin up to the mask's top level, then the perceptron
-        if (h->learn_mode > 0 && j1 > j0) {
-            const Span pf = span_of(h, j0 + 1, j1, [](const DevLevel& L) { return L.npatch + 1; });
-            launch_features(dlv<R>(h), pf, h->thr, j0, h->cfg.jmax, h->all_list, h->all_count, h->grid_all, s);
-            if (h->learn_mode > 1) launch_propose(dlv<R>(h), pf, h->net, h->tau, s);
-        }
-        const Span props = span_of(h, j0 + 1, h->cfg.jmax, [](const DevLevel& L) { return L.npatch + 1; });
-        if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 0, h->sig_any, s);
-        // the candidate lists need patches of at least 4 x 4 (one or two rings reach
-        // the five hops of the ghost band)
-        if (h->cfg.mask == 0 && h->cfg.patch >= 4) {
-            MaskListArgs<R> b{};
-            b.lvs = dlv<R>(h), b.host = lvl<R>(h).data(), b.grid_lv = h->grid_lv.data();
-            b.ja = j0, b.jb = j1, b.hops = GHOST_HOPS, b.rings = h->cfg.patch >= 8 ? 1 : 2, b.P = h->S;
-            b.grid = h->grid_all, b.max_entries = h->total_entries;
-            b.active = h->all_list, b.active_count = h->all_count, b.thr = h->thr, b.sig_any = h->sig_any;
-            b.patches = span_of(h, j0, j1, [](const DevLevel& L) { return L.npatch + 1; });
-            b.cand = h->cand, b.cand_count = h->cand_count, b.gcand = h->gcand, b.gcand_count = h->gcand_count;
-            b.lstat = h->lstat;
-            launch_mask_lists(b, s);
-            launch_patch_scan(dlv<R>(h), j0, j1, s);
-        } else {
-            launch_mask(a, s);
-        }
-        if (h->cfg.jmax > j0) launch_prop_roll(dlv<R>(h), props, 1, h->sig_any, s);
-        launch_concat(dlv<R>(h), j0, h->cfg.jmax, h->all_list, h->all_count, s);
-    }
+    Trace tm(h, SWW_K_MASK);
+    MaskBatch<R, 1> b{};
+    mask_batch_head(b, h, 1, j1, h->cfg.jmax);
+    b.m[0] = mask_member<R>(h);
+    launch_proposal_batch(b, h->grid_all, 0, s);
+    if (list_mask(h))
+        launch_mask_batch(b, h->grid_all, s);
+    else
+        launch_mask(mask_args<R>(h, j0, j1), s);
+    launch_proposal_batch(b, h->grid_all, 1, s);
+    launch_concat_batch(b, s);
 }
 
 template <class R>
@@ -810,7 +840,7 @@ void run_step_t(sww_handle* h, double dt, bool do_adapt, int part = 0) {
         one_step<R>(h, dt, do_adapt, part);
         return;
     }
-    const unsigned mode = h->use_cluster ? (0x80000000u | unsigned(h->cluster_cap)) : h->stage_blocks;
+    const unsigned mode = h->stage_blocks;
     auto key = std::make_tuple(part, h->jtop, int(do_adapt), dt > 0 ? dt : -1.0, mode);
     auto it = h->graphs.find(key);
     if (it == h->graphs.end()) {
@@ -846,6 +876,14 @@ void run_step(sww_handle* h, double dt, bool do_adapt, int part = 0) {
     });
 }
 
+// The member record of a handle (its top level and j1 as of the last step).
+template <class R>
+MemberRef<R> member_ref(const sww_handle* h) {
+    const int j1 = std::min(h->jtop + 1, h->cfg.jmax);
+    return MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop, h->red, h->cfg.cfl, h->thr,
+                        eps_coeff(h->cfg), h->cfg.advect, j1, h->cfg.jmax, h->err, h->irr_list, h->irr_count};
+}
+
 // Device buffers of ensemble steps led by `lead` (allocated on first use).
 template <class R>
 void ensure_ensemble(sww_handle* lead) {
@@ -868,7 +906,8 @@ void ensure_ensemble(sww_handle* lead) {
 // work: the members' streams are joined into the lead's), the largest top level
 // and j1, and the bounds of the members' level-j list entries.
 template <class R>
-BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& entries, int& j1_max) {
+BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& entries, int& j1_max,
+                           int64_t& irr_entries) {
     sww_handle* lead = hs[0];
     auto& E = lead->ens;
     MemberRef<R>* refs = reinterpret_cast<MemberRef<R>*>(E.h_refs);
@@ -877,8 +916,9 @@ BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& e
     for (int i = 0; i < n; ++i) {
         sww_handle* h = hs[i];
         const int j1 = std::min(h->jtop + 1, h->cfg.jmax);
-        refs[i] = MemberRef<R>{dlv<R>(h), h->all_list, h->all_count, h->dt, h->jtop, h->red, h->cfg.cfl,
-                               h->thr, eps_coeff(h->cfg), h->cfg.advect, j1, h->cfg.jmax, h->err};
+        refs[i] = member_ref<R>(h);
+        refs[i].jtop = h->jtop;
+        refs[i].j1 = j1;
         jtop = std::max(jtop, h->jtop);
         j1_max = std::max(j1_max, j1);
         if (i > 0) {
@@ -888,6 +928,8 @@ BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& e
     }
     ck(cudaMemcpyAsync(E.refs, refs, sizeof(MemberRef<R>) * n, cudaMemcpyHostToDevice, lead->stream), "refs");
     entries.assign(j1_max + 1, 0);
+    irr_entries = 0;
+    for (int i = 0; i < n; ++i) irr_entries += hs[i]->irr_bound;
     for (int i = 0; i < n; ++i)
         for (int j = lead->cfg.jmin; j <= std::min(j1_max, hs[i]->cfg.jmax); ++j)
             entries[j] += meta(hs[i], j).npatch + 1;
@@ -895,33 +937,6 @@ BatchArgs<R> ensemble_refs(sww_handle* const* hs, int n, std::vector<int64_t>& e
     const RKStage* st = stages(lead->cfg.rk, ns);
     return BatchArgs<R>{reinterpret_cast<const MemberRef<R>*>(E.refs), n, lead->S, lead->cfg.jmin, jtop,
                         lead->cfg.H, lead->cfg.g, st[0], E.bar, E.err, 0.0, E.out};
-}
-
-// The RK stages of every member of an ensemble as one persistent launch per stage
-// (k_stage_batch) on the first member's stream, after every member's part 1 and
-// before its part 2.
-template <class R>
-void ensemble_stages(sww_handle* const* hs, int n) {
-    sww_handle* lead = hs[0];
-    ensure_ensemble<R>(lead);
-    auto& E = lead->ens;
-    if (!E.grid) {
-        E.grid = stage_batch_grid<R>(lead->nsm);
-        if (!E.grid) throw CudaError("persistent ensemble stage cannot run");
-    }
-    std::vector<int64_t> entries;
-    int j1_max = 0;
-    BatchArgs<R> a = ensemble_refs<R>(hs, n, entries, j1_max);
-    int ns;
-    const RKStage* st = stages(lead->cfg.rk, ns);
-    for (int k = 0; k < ns; ++k) {
-        Trace t(lead, SWW_K_STAGE);
-        a.st = st[k];
-        ck(launch_stage_batch(a, E.grid, lead->stream), "persistent ensemble stage");
-    }
-    ck(cudaMemcpyAsync(E.h_err, E.err, sizeof(int), cudaMemcpyDeviceToHost, lead->stream), "err");
-    ck(cudaEventRecord(E.ev, lead->stream), "ensemble fork");
-    for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
 }
 
 // One step of every member with the work batched over members (persistent = 3), on
@@ -938,17 +953,22 @@ void ensemble_phased(sww_handle* const* hs, int n, double dt, bool do_adapt) {
     cudaStream_t s = lead->stream;
     std::vector<int64_t> entries;
     int j1_max = 0;
-    BatchArgs<R> a = ensemble_refs<R>(hs, n, entries, j1_max);
+    int64_t irr_entries = 0;
+    BatchArgs<R> a = ensemble_refs<R>(hs, n, entries, j1_max, irr_entries);
     int ns;
     const RKStage* st = stages(lead->cfg.rk, ns);
     {
         Trace t(lead, SWW_K_DT);
         ck(launch_batch_pre(a, entries.data(), lead->nsm, dt, s), "batched ensemble step");
     }
+    static const int part_cls[5] = {SWW_K_FILL, SWW_K_TREND, SWW_K_IRREG, SWW_K_RESTRICT, SWW_K_UPDATE};
     for (int k = 0; k < ns; ++k) {
         Trace t(lead, SWW_K_STAGE);
         a.st = st[k];
-        ck(launch_stage_batch_phases(a, entries.data(), lead->nsm, s), "batched ensemble stage");
+        for (int part = 0; part < 5; ++part) {
+            Trace tp(lead, part_cls[part]);
+            ck(launch_stage_batch_part(a, entries.data(), irr_entries, lead->nsm, part, s), "batched ensemble stage");
+        }
     }
     {
         Trace t(lead, SWW_K_PARTIAL);
@@ -959,13 +979,33 @@ void ensemble_phased(sww_handle* const* hs, int n, double dt, bool do_adapt) {
             Trace t(lead, SWW_K_COEFF);
             ck(launch_batch_adapt_pre(a, entries.data(), lead->nsm, s), "batched ensemble step");
         }
-        // each member's mask on its own stream, then back to the lead's
-        ck(cudaEventRecord(E.ev, s), "ensemble fork");
-        for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
-        for (int i = 0; i < n; ++i) run_step(hs[i], dt, true, 4);
-        for (int i = 1; i < n; ++i) {
-            ck(cudaEventRecord(hs[i]->ev_out, hs[i]->stream), "ensemble join");
-            ck(cudaStreamWaitEvent(s, hs[i]->ev_out, 0), "ensemble join");
+        bool lists = true;
+        for (int i = 0; i < n; ++i) lists = lists && list_mask(hs[i]);
+        if (lists) {
+            // every member's mask in the same launches on the lead's stream
+            Trace tm(lead, SWW_K_MASK);
+            auto b = std::make_unique<MaskBatch<R, MASK_BATCH_MAX>>();
+            int jb_max = lead->cfg.jmin, jmax_max = lead->cfg.jmin;
+            for (int i = 0; i < n; ++i) {
+                b->m[i] = mask_member<R>(hs[i]);
+                jb_max = std::max(jb_max, b->m[i].jb);
+                jmax_max = std::max(jmax_max, hs[i]->cfg.jmax);
+            }
+            mask_batch_head(*b, lead, n, jb_max, jmax_max);
+            const unsigned grid = unsigned(std::max(1, std::min<int>(int(lead->grid_all), 8 * lead->nsm / n)));
+            launch_proposal_batch(*b, grid, 0, s);
+            launch_mask_batch(*b, grid, s);
+            launch_proposal_batch(*b, grid, 1, s);
+            launch_concat_batch(*b, s);
+        } else {
+            // each member's mask on its own stream, then back to the lead's
+            ck(cudaEventRecord(E.ev, s), "ensemble fork");
+            for (int i = 1; i < n; ++i) ck(cudaStreamWaitEvent(hs[i]->stream, E.ev, 0), "ensemble fork");
+            for (int i = 0; i < n; ++i) run_step(hs[i], dt, true, 4);
+            for (int i = 1; i < n; ++i) {
+                ck(cudaEventRecord(hs[i]->ev_out, hs[i]->stream), "ensemble join");
+                ck(cudaStreamWaitEvent(s, hs[i]->ev_out, 0), "ensemble join");
+            }
         }
         Trace t(lead, SWW_K_INVERSE);
         ck(launch_batch_adapt_post(a, entries.data(), j1_max, lead->nsm, s), "batched ensemble step");
@@ -1009,7 +1049,8 @@ int check_config(const sww_config* cfg) {
     if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
         return fail(SWW_E_ARG, "precision must be SWW_FP64 or SWW_FP32");
     if (cfg->mask != 0 && cfg->mask != 1) return fail(SWW_E_ARG, "mask must be 0 (candidate lists) or 1 (dense)");
-    if (cfg->persistent < -1 || cfg->persistent > 3) return fail(SWW_E_ARG, "persistent must be -1..3");
+    if (cfg->persistent != -1 && cfg->persistent != 0 && cfg->persistent != 3)
+        return fail(SWW_E_ARG, "persistent must be -1, 0 or 3");
     if (!(cfg->nu >= 0)) return fail(SWW_E_ARG, "nu must be >= 0");
     return SWW_OK;
 }
@@ -1058,7 +1099,13 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         }
         h->all_list = h->alloc<int32_t>(total);
         h->all_count = h->alloc<int32_t>(1);
+        h->irr_list = h->alloc<int32_t>(total);
+        h->irr_count = h->alloc<int32_t>(1);
+        ck(cudaMemset(h->irr_count, 0, sizeof(int32_t)), "memset");
         h->total_entries = total;
+        h->irr_bound = 0;
+        for (int j = cfg->jmin; j <= cfg->jmax; ++j)
+            h->irr_bound += (cfg->nu != 0.0 || cfg->advect) ? meta(h, j).npatch + 1 : h->geo->n_irr[j];
         h->cand = h->alloc<int32_t>(total);
         h->gcand = h->alloc<int32_t>(total);
         h->cand_count = h->alloc<int32_t>(1);
@@ -1073,6 +1120,8 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
         *h->h_dt = 0;
         h->red = h->alloc<unsigned long long>(4);
+        h->d_net = h->alloc<MlpWeights>(1);
+        ck(cudaMemset(h->d_net, 0, sizeof(MlpWeights)), "memset");
         h->lstat = h->alloc<unsigned long long>(4);
         ck(cudaMemset(h->lstat, 0, 4 * sizeof(unsigned long long)), "memset");
         h->bar = h->alloc<unsigned>(STAGE_BAR_WORDS);
@@ -1084,9 +1133,8 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         if (cfg->persistent >= 0 && cfg->jmax + 1 <= 12) {
             int coop = 0;
             ck(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "device attribute");
-            if (coop) h->stage_cap = fp32 ? stage_grid<float>(h->nsm) : stage_grid<double>(h->nsm);
+            if (coop) h->stage_cap = fp32 ? stage_grid<float>(h->S, h->nsm) : stage_grid<double>(h->S, h->nsm);
             h->stage_blocks = h->stage_cap;
-            h->cluster_cap = fp32 ? stage_cluster_size<float>() : stage_cluster_size<double>();
         }
         h->cnt = h->alloc<unsigned long long>(4);
         h->thr = h->alloc<double>(2);
@@ -1096,8 +1144,17 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         ck(cudaMemset(h->thr, 0, 2 * sizeof(double)), "memset");
         ck(cudaMemset(h->dt, 0, sizeof(double)), "memset");
         ck(cudaMemset(h->all_count, 0, sizeof(int32_t)), "memset");
-        ck(cudaDeviceSynchronize(), "create");
         h->jtop = cfg->jmax;
+        // the handle's own member record (the fields its trend launches read are fixed)
+        h->self_ref = h->alloc<uint8_t>(sizeof(MemberRef<double>));
+        if (fp32) {
+            MemberRef<float> r = member_ref<float>(h);
+            ck(cudaMemcpy(h->self_ref, &r, sizeof(r), cudaMemcpyHostToDevice), "member record");
+        } else {
+            MemberRef<double> r = member_ref<double>(h);
+            ck(cudaMemcpy(h->self_ref, &r, sizeof(r), cudaMemcpyHostToDevice), "member record");
+        }
+        ck(cudaDeviceSynchronize(), "create");
         return SWW_OK;
     });
     if (rc != SWW_OK) {
@@ -1199,7 +1256,7 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
             if (J > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
             MaskArgsT<R> b = mask_args<R>(h, j0, j1, false);
             launch_patches_all(dlv<R>(h), b.patches, s);
-            launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);
+            launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, s);
             read_counts<R>(h);
             check_launch();
             return 0;
@@ -1340,17 +1397,15 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
             if (hs[k] == hs[i]) return fail(SWW_E_ARG, "a handle appears twice");
     }
     if (n == 0 || nsteps == 0) return SWW_OK;
-    // one persistent launch per RK stage over all members (every member asks for it
-    // with persistent = 1, and they share precision, Jmin, patch side, depth, gravity
-    // and scheme); otherwise the members' whole steps overlap on their own streams
-    // (persistent = 3: one regular launch per phase of a stage over all members)
-    const int want = hs[0]->cfg.persistent;
-    const bool phased = want == 3;
-    bool batched = n > 1 && n <= 128 && (want == 1 || want == 3);
+    // the whole step batched over the members but their masks, one regular launch
+    // per phase over all members, when every member asks for it (persistent = 3)
+    // and they share precision, Jmin, patch side, depth, gravity and scheme;
+    // otherwise the members' whole steps overlap on their own streams
+    bool batched = n > 1 && n <= 128 && hs[0]->cfg.persistent == 3;
     for (int i = 0; i < n && batched; ++i) {
         const sww_config &a = hs[0]->cfg, &b = hs[i]->cfg;
-        batched = (phased || hs[i]->stage_cap > 0) && b.persistent == want && a.precision == b.precision &&
-                  a.jmin == b.jmin && a.patch == b.patch && a.H == b.H && a.g == b.g && a.rk == b.rk;
+        batched = b.persistent == 3 && a.precision == b.precision && a.jmin == b.jmin && a.patch == b.patch &&
+                  a.H == b.H && a.g == b.g && a.rk == b.rk;
     }
     return guarded([&]() -> int {
         for (int i = 0; i < n; ++i) {
@@ -1378,45 +1433,20 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         };
         int rc = SWW_OK;
         if (batched) {
-            if (phased) {
-                // the whole step batched over the members but their masks
-                for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
-                    by_prec(hs[0], [&](auto r) {
-                        ensemble_phased<decltype(r)>(hs, n, dt, do_adapt != 0);
-                        return 0;
-                    });
-                    check_launch();
-                    ck(cudaStreamSynchronize(hs[0]->stream), "step");
-                    const BatchOut* o = reinterpret_cast<const BatchOut*>(hs[0]->ens.h_out);
-                    for (int i = 0; i < n && rc == SWW_OK; ++i) {
-                        sww_handle* h = hs[i];
-                        *h->h_dt = o[i].dt;
-                        *h->h_err = o[i].err;
-                        for (int j = 0; j <= h->cfg.jmax && j < 16; ++j) h->h_counts[j] = o[i].counts[j];
-                        rc = finish(h);
-                    }
-                }
-                join_out();
-                return rc;
-            }
             for (int s = 0; s < nsteps && rc == SWW_OK; ++s) {
-                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 1);
                 by_prec(hs[0], [&](auto r) {
-                    ensemble_stages<decltype(r)>(hs, n);
+                    ensemble_phased<decltype(r)>(hs, n, dt, do_adapt != 0);
                     return 0;
                 });
-                for (int i = 0; i < n; ++i) run_step(hs[i], dt, do_adapt != 0, 2);
                 check_launch();
-                for (int i = 0; i < n; ++i) {
-                    int r = finish(hs[i]);
-                    if (rc == SWW_OK) rc = r;
-                }
-                auto& E = hs[0]->ens;
-                if (rc == SWW_OK && *E.h_err) {
-                    *E.h_err = 0;
-                    ck(cudaMemset(E.err, 0, sizeof(int)), "reset err");
-                    ck(cudaMemset(E.bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "reset barrier");
-                    rc = fail(SWW_E_TIMEOUT, "a grid barrier of the persistent ensemble stage timed out");
+                ck(cudaStreamSynchronize(hs[0]->stream), "step");
+                const BatchOut* o = reinterpret_cast<const BatchOut*>(hs[0]->ens.h_out);
+                for (int i = 0; i < n && rc == SWW_OK; ++i) {
+                    sww_handle* h = hs[i];
+                    *h->h_dt = o[i].dt;
+                    *h->h_err = o[i].err;
+                    for (int j = 0; j <= h->cfg.jmax && j < 16; ++j) h->h_counts[j] = o[i].counts[j];
+                    rc = finish(h);
                 }
             }
             join_out();
@@ -1425,21 +1455,17 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
         // otherwise every member's step is one graph launch on the member's own
         // stream, the members advancing in turn, each waiting only for its own
         // previous step.  Cooperative launches of different streams do not overlap,
-        // so a member's RK stage runs as one launch per phase, or (persistent = 2)
-        // as one thread-block cluster with hardware barriers between the phases
+        // so a member's RK stage runs as one launch per phase
         std::vector<unsigned> own(n);
         for (int i = 0; i < n; ++i) {
             own[i] = hs[i]->stage_blocks;
-            if (n > 1) {
-                hs[i]->stage_blocks = 0;
-                hs[i]->use_cluster = hs[i]->cluster_cap > 0 && hs[i]->cfg.persistent == 2;
-            }
+            if (n > 1) hs[i]->stage_blocks = 0;
         }
         struct Restore {
             sww_handle* const* hs;
             std::vector<unsigned>& own;
             ~Restore() {
-                for (size_t i = 0; i < own.size(); ++i) hs[i]->stage_blocks = own[i], hs[i]->use_cluster = false;
+                for (size_t i = 0; i < own.size(); ++i) hs[i]->stage_blocks = own[i];
             }
         } restore{hs, own};
         auto launch = [&](sww_handle* h) {
@@ -1752,7 +1778,7 @@ int sww_load(sww_handle* h, const char* path) {
                 ck(cudaMemcpyAsync(h->thr, thr, sizeof(thr), cudaMemcpyHostToDevice, s), "load thr");
                 MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
                 launch_patches_all(dlv<R>(h), a.patches, s);
-                launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, s);
+                launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, s);
                 read_counts<R>(h);
                 check_launch();
                 ck(cudaStreamSynchronize(s), "load");   // host buffers live on this frame
@@ -1860,7 +1886,10 @@ int sww_set_learned(sww_handle* h, int mode, const float* params, float tau) {
         ck(cudaStreamSynchronize(h->stream), "set_learned");
         h->learn_mode = mode;
         h->tau = tau;
-        if (params) h->net = mlp_weights(params);
+        if (params) {
+            h->net = mlp_weights(params);
+            ck(cudaMemcpy(h->d_net, &h->net, sizeof(MlpWeights), cudaMemcpyHostToDevice), "weights");
+        }
         h->drop_graphs();
         return SWW_OK;
     });

@@ -1,7 +1,8 @@
 // RK stage of every member of an ensemble as one regular launch per phase (the
 // phases of one trend evaluation and its stage update, Sec. 3.1, in the order of
-// the persistent stage): ghosts level by level, q and F, div/K/B and q F^perp, the
-// restrictions level by level, the update.  The kernel boundary is the barrier.
+// the persistent stage): ghosts level by level, the structured trend and the
+// irregular patches (sww_tile.cu), the restrictions level by level, the update.
+// The kernel boundary is the barrier.
 //
 // Blocks come in groups, one group per member: a block copies the level records of
 // its member that the phase touches into shared memory once, then strides over
@@ -26,7 +27,7 @@ constexpr int BATCH_TPB = 256;
 constexpr int MAXL = 12;
 constexpr int MAXM = 128;
 enum {
-    PH_FILL = 0, PH_FLUX, PH_NODE, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL,
+    PH_FILL = 0, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL,
     PH_DETAILS, PH_MAXABS, PH_THRESH, PH_INV_A, PH_INV_B, PH_INV_FILL, PH_OUT
 };
 
@@ -131,24 +132,6 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
                                                   fill_node(L, (&L)[-1], id);
                                               else
                                                   fill_edge(L, (&L)[-1], id);
-                                          });
-            break;
-        case PH_FLUX:
-            member_items<K_EDGE | K_TRI>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
-                                         [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                             if (kind == K_EDGE)
-                                                 flux_at(L, id, H);
-                                             else
-                                                 pv_at(L, id, H);
-                                         });
-            break;
-        case PH_NODE:
-            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
-                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                              if (kind == K_NODE)
-                                                  node_at(L, id, g);
-                                              else
-                                                  coriolis_at(L, id);
                                           });
             break;
         case PH_RESTRICT:
@@ -283,7 +266,8 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
 }  // namespace
 
 template <class R>
-cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s) {
+cudaError_t launch_stage_batch_part(const BatchArgs<R>& a, const int64_t* level_entries, int64_t irr_entries, int nsm,
+                                    int part, cudaStream_t s) {
     if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
     int64_t all = 0;
     for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
@@ -300,14 +284,32 @@ cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* leve
         return cudaGetLastError();
     };
     cudaError_t e = cudaSuccess;
-    for (int j = a.jmin + 1; j <= a.jtop_max && e == cudaSuccess; ++j) e = go(PH_FILL, j, bpm(level_entries[j], 4));
-    if (e == cudaSuccess) e = go(PH_FLUX, 0, bpm(all, 5));
-    if (e == cudaSuccess) e = go(PH_NODE, 0, bpm(all, 4));
-    for (int j = a.jtop_max - 1; j >= a.jmin && e == cudaSuccess; --j) {
-        e = go(PH_RESTRICT, j, bpm(level_entries[j], 4));
-        if (e == cudaSuccess) e = go(PH_DIV, j, bpm(level_entries[j], 1));
+    switch (part) {
+        case 0:
+            for (int j = a.jmin + 1; j <= a.jtop_max && e == cudaSuccess; ++j) e = go(PH_FILL, j, bpm(level_entries[j], 4));
+            break;
+        case 1:
+        case 2:
+            e = launch_tile_trend(a, all, irr_entries, nsm, part, s);
+            break;
+        case 3:
+            for (int j = a.jtop_max - 1; j >= a.jmin && e == cudaSuccess; --j) {
+                e = go(PH_RESTRICT, j, bpm(level_entries[j], 4));
+                if (e == cudaSuccess) e = go(PH_DIV, j, bpm(level_entries[j], 1));
+            }
+            break;
+        default:
+            e = go(PH_UPDATE, 0, bpm(all, 4));
     }
-    if (e == cudaSuccess) e = go(PH_UPDATE, 0, bpm(all, 4));
+    return e;
+}
+
+template <class R>
+cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int64_t irr_entries, int nsm,
+                                      cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (int part = 0; part < 5 && e == cudaSuccess; ++part)
+        e = launch_stage_batch_part(a, level_entries, irr_entries, nsm, part, s);
     return e;
 }
 
@@ -392,7 +394,13 @@ template cudaError_t launch_batch_pre<double>(const BatchArgs<double>&, const in
 template cudaError_t launch_batch_pre<float>(const BatchArgs<float>&, const int64_t*, int, double, cudaStream_t);
 template cudaError_t launch_batch_post<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);
 template cudaError_t launch_batch_post<float>(const BatchArgs<float>&, const int64_t*, int, cudaStream_t);
-template cudaError_t launch_stage_batch_phases<double>(const BatchArgs<double>&, const int64_t*, int, cudaStream_t);
-template cudaError_t launch_stage_batch_phases<float>(const BatchArgs<float>&, const int64_t*, int, cudaStream_t);
+template cudaError_t launch_stage_batch_part<double>(const BatchArgs<double>&, const int64_t*, int64_t, int, int,
+                                                     cudaStream_t);
+template cudaError_t launch_stage_batch_part<float>(const BatchArgs<float>&, const int64_t*, int64_t, int, int,
+                                                    cudaStream_t);
+template cudaError_t launch_stage_batch_phases<double>(const BatchArgs<double>&, const int64_t*, int64_t, int,
+                                                       cudaStream_t);
+template cudaError_t launch_stage_batch_phases<float>(const BatchArgs<float>&, const int64_t*, int64_t, int,
+                                                      cudaStream_t);
 
 }  // namespace sww

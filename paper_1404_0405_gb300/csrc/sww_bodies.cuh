@@ -3,9 +3,21 @@
 // Included inside an anonymous namespace of each translation unit.
 #pragma once
 
+#include "f64conv.cuh"
+
 __device__ __forceinline__ int64_t gid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 template <class R>
 __device__ __forceinline__ R esign(int32_t code) { return (code & 1) ? R(-1) : R(1); }
+// an FP64 geometry value entering arithmetic of the working precision (FP32: the
+// integer-pipe rounding of f64conv.cuh)
+template <class R>
+__device__ __forceinline__ R to_r(double x);
+template <>
+__device__ __forceinline__ double to_r<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float to_r<float>(double x) { return f64_to_f32_rn(x); }
+template <class R>
+__device__ __forceinline__ R geo(const double* __restrict__ p, int64_t i) { return to_r<R>(p[i]); }
 
 template <class Lv>
 __device__ __forceinline__ int32_t ring_nbr(const Lv& L, int32_t code) {
@@ -113,12 +125,13 @@ __device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
     int32_t c0 = L.te[t], c1 = L.te[L.T + t], c2 = L.te[2 * L.T + t];
     if (!(L.nflag[n0] & AVAIL) || !(L.nflag[n1] & AVAIL) || !(L.nflag[n2] & AVAIL)) return;
     if (!(L.eflag[c0 >> 1] & AVAIL) || !(L.eflag[c1 >> 1] & AVAIL) || !(L.eflag[c2 >> 1] & AVAIL)) return;
-    R circ = esign<R>(c0) * L.u[c0 >> 1] * L.d_e[c0 >> 1] + esign<R>(c1) * L.u[c1 >> 1] * L.d_e[c1 >> 1] +
-             esign<R>(c2) * L.u[c2 >> 1] * L.d_e[c2 >> 1];
-    R hv = L.kite[t] * (H + L.dh[n0]) + L.kite[L.T + t] * (H + L.dh[n1]) + L.kite[2 * L.T + t] * (H + L.dh[n2]);
-    R Av = L.A_v[t];
+    R circ = esign<R>(c0) * L.u[c0 >> 1] * geo<R>(L.d_e, c0 >> 1) + esign<R>(c1) * L.u[c1 >> 1] * geo<R>(L.d_e, c1 >> 1) +
+             esign<R>(c2) * L.u[c2 >> 1] * geo<R>(L.d_e, c2 >> 1);
+    R hv = geo<R>(L.kite, t) * (H + L.dh[n0]) + geo<R>(L.kite, L.T + t) * (H + L.dh[n1]) +
+           geo<R>(L.kite, 2 * L.T + t) * (H + L.dh[n2]);
+    R Av = geo<R>(L.A_v, t);
     if (L.nu != 0.0) L.zeta[t] = circ / Av;
-    L.q[t] = (circ / Av + L.f_v[t]) / (hv / Av);
+    L.q[t] = (circ / Av + geo<R>(L.f_v, t)) / (hv / Av);
 }
 
 // thickness flux F = h_e u at an edge
@@ -129,7 +142,7 @@ __device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
     if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
     L.F[e] = R(0.5) * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
     // viscous form: diffusive height flux -nu grad(dh) (joins F in the divergence)
-    if (L.nu != 0.0) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / L.d_e[e];
+    if (L.nu != 0.0) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / geo<R>(L.d_e, e);
 }
 
 // divergence of the height flux (with the diffusive flux of the viscous form) at a node
@@ -143,9 +156,9 @@ __device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
         int32_t code = L.ring_e[k * L.N + v];
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
-        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
+        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * geo<R>(L.l_e, e);
     }
-    L.c[v] = div / L.A_i[v];
+    L.c[v] = div / geo<R>(L.A_i, v);
 }
 
 // divergence, kinetic energy and Bernoulli function at a node
@@ -161,11 +174,12 @@ __device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
         int64_t e = code >> 1;
         if (!(L.eflag[e] & AVAIL)) return;
         R ue = L.u[e];
-        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * L.l_e[e];
-        if (visc) du += esign<R>(code) * ue * L.l_e[e];
-        ke += R(0.25) * L.l_e[e] * L.d_e[e] * ue * ue;
+        const R le = geo<R>(L.l_e, e);
+        div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * le;
+        if (visc) du += esign<R>(code) * ue * le;
+        ke += R(0.25) * le * geo<R>(L.d_e, e) * ue * ue;
     }
-    R A = L.A_i[v];
+    R A = geo<R>(L.A_i, v);
     // viscous form: -nu div u joins B (so that -grad B gains +nu grad div u)
     if (visc) ke -= R(L.nu) * du;
     L.c[v] = div / A;
@@ -181,7 +195,7 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) {
         int32_t e2 = L.cor_i[k * L.E + e];
-        R w = L.cor_w[k * L.E + e];
+        R w = geo<R>(L.cor_w, k * L.E + e);
         R q2 = R(0.5) * (L.q[L.et[e2]] + L.q[L.et[L.E + e2]]);
         s += w * L.F[e2] * R(0.5) * (qe + q2);
     }
@@ -195,7 +209,7 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
                 if ((code >> 1) == e) gp += esign<R>(code) * L.zeta[t];
             }
         }
-        s -= R(L.nu) * gp / L.l_e[e];
+        s -= R(L.nu) * gp / geo<R>(L.l_e, e);
     }
     L.Q[e] = s;
 }
@@ -228,7 +242,7 @@ __device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, co
         L.ut[e] = R(0);
         return;
     }
-    R k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / L.d_e[e];
+    R k = L.Q[e] - (L.B[L.en[L.E + e]] - L.B[L.en[e]]) / geo<R>(L.d_e, e);
     L.ut[e] = k;
     if (st.apply) rk_apply(st, dt, k, &L.u[e], &L.u0[e], &L.ua[e]);
 }
@@ -369,7 +383,7 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
         }
 #pragma unroll
         for (int k = 0; k < 11; ++k) s += L.rf_cw[k * L.E + i] * F.c[L.rf_ci[k * L.E + i]];
-        L.F[i] = s / L.l_e[i];
+        L.F[i] = s / geo<R>(L.l_e, i);
         if (visc) L.Fd[i] = R(0);
     }
     if (ca && cb && !L.advect) L.Q[i] = R(0.5) * (F.Q[L.half[i]] + F.Q[L.half[L.E + i]]);
@@ -498,3 +512,87 @@ __device__ __forceinline__ void covered_node(const DevLevelT<R>& C, const DevLev
     }
     C.nflag[k] |= COVERED;
 }
+
+// ---------------------------------------------------------------------------- patch lists (Sec. 5.2)
+
+// The ascending list of level L's flagged patches (+ the pole entry when a pole is
+// live or ghost), one block of any width (ballot and a warp-total prefix).
+template <class R>
+__device__ void patch_scan_level(const DevLevelT<R>& L) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t tag = int32_t(L.J) << LVL_SHIFT;
+    for (int64_t start = 0; start < L.npatch; start += blockDim.x) {
+        int64_t i = start + threadIdx.x;
+        int f = (i < L.npatch) ? L.pflag[i] : 0;
+        unsigned bal = __ballot_sync(0xffffffffu, f);
+        int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[w] = __popc(bal);
+        __syncthreads();
+        int off = 0;
+        for (int k = 0; k < w; ++k) off += warp_tot[k];
+        if (f) L.patches[base + off + pre] = tag | int32_t(i);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int k = 0; k < nw; ++k) tot += warp_tot[k];
+            base += tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int n = base;
+        if ((L.nflag[L.nelem] | L.nflag[L.nelem + 1]) & AVAIL) L.patches[n++] = tag | int32_t(L.npatch);
+        *L.npatches = n;
+    }
+}
+
+// The all-level list of levels jmin..jmax from the levels' lists, and its entries
+// whose tile is not regular (the irregular list, same order); one block.
+template <class R>
+__device__ void concat_lists(const DevLevelT<R>* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count,
+                             int32_t* irr, int32_t* irr_count) {
+    __shared__ int base, ibase;
+    __shared__ int warp_tot[32];
+    if (threadIdx.x == 0) base = 0, ibase = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = jmin; j <= jmax; ++j) {
+        const DevLevelT<R>& L = lvs[j];
+        const int n = *L.npatches;
+        const bool all_irr = L.nu != 0.0 || L.advect || L.thalo == nullptr;
+        // all entries in level order; the entries whose tile is not regular (see
+        // tile_regular) also into the irregular list, in the same order
+        for (int start = 0; start < n; start += blockDim.x) {
+            const int i = start + threadIdx.x;
+            int32_t ent = 0;
+            int f = 0;
+            if (i < n) {
+                ent = L.patches[i];
+                all[base + i] = ent;
+                const int64_t pat = ent & PATCH_MASK;
+                f = (all_irr || pat >= L.npatch || L.tirr[pat]) ? 1 : 0;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) warp_tot[w] = __popc(bal);
+            __syncthreads();
+            int off = 0;
+            for (int k = 0; k < w; ++k) off += warp_tot[k];
+            if (f) irr[ibase + off + __popc(bal & ((1u << lane) - 1u))] = ent;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int k = 0; k < nw; ++k) tot += warp_tot[k];
+                ibase += tot;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) base += n;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base, *irr_count = ibase;
+}
+

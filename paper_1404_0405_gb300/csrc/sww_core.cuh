@@ -18,10 +18,14 @@ constexpr int MLP_PARAMS = NF * NH + NH + NH + 1;   // W1[NF][NH], b1[NH], w2[NH
 constexpr int LVL_SHIFT = 27;
 constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
 
-// One level on the device, with fields and stencil weights in the working
-// precision R (double, or float for the FP32 form, whose weights are the FP64
-// tables rounded once).  All arrays are dense over the level (see grid.h for the
-// element layout); slot-major tables store slot s of item i at s*count + i.
+// One level on the device, with fields in the working precision R (double, or
+// float for the FP32 form).  The spherical geometry (areas, lengths, kites, the
+// Coriolis parameter and the TRiSK reconstruction weights) is FP64 in both forms:
+// the FP32 form reads the FP64 tables and rounds each value as it enters FP32
+// arithmetic.  The transform weights (lifting, velocity prediction, flux
+// restriction) are in R (the FP64 tables rounded once for the FP32 form).  All
+// arrays are dense over the level (see grid.h for the element layout); slot-major
+// tables store slot s of item i at s*count + i.
 template <class R>
 struct DevLevelT {
     int J;
@@ -35,12 +39,10 @@ struct DevLevelT {
     const uint8_t* deg;            // [N]
     const int32_t *ring_e;         // [6*N] (2e + edge points into the node), -1 padded
     const int32_t* f2c;            // [N] coarse node at the same place (-1: odd node)
-    // geometry
-    const R *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
+    // geometry (FP64 in every precision form)
+    const double *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
     const int32_t* cor_i;          // [10*E]
-    const R* cor_w;                // [10*E]
-    // FP64 geometry of the global mass and energy sums
-    const double *A_i64, *d_e64, *l_e64;
+    const double* cor_w;           // [10*E]
     // fine side of the pair (J-1, J)
     const int32_t* par;            // [4*N] prediction parents of odd nodes (fine ids)
     const R* ptw;                  // [4*N] s~_km
@@ -58,6 +60,10 @@ struct DevLevelT {
     const int32_t* ppar;           // [npatch+1] patch of level J-1 under each patch (-1 on the coarsest level)
     const int32_t* pnbr;           // [NB*(npatch+1)] patches with a node within two hops, -1 padded
     const int32_t* pchild;         // [4*(npatch+1)] patches of level J+1 over each patch, -1 padded
+    // tiles of the structured trend (tile.h): halo ids per patch (null without
+    // tiles) and the irregular flag of each patch (index npatch: the poles, 1)
+    const int32_t* thalo;          // [npatch * halo]
+    const uint8_t* tirr;           // [npatch + 1]
     // state and work arrays
     R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
     R *F, *q, *B, *c, *Q;

@@ -245,11 +245,11 @@ __global__ void k_sums(DevLevelT<R> L, double H, double g, double* part) {
     int64_t v = gid();
     double m = 0, en = 0;
     if (v < L.N) {
-        double h = H + double(L.dh[v]), A = L.A_i64[v], ke = 0.0;
+        double h = H + double(L.dh[v]), A = L.A_i[v], ke = 0.0;
         for (int k = 0; k < L.deg[v]; ++k) {
             int64_t e = L.ring_e[k * L.N + v] >> 1;
             double ue = double(L.u[e]);
-            ke += 0.25 * L.l_e64[e] * L.d_e64[e] * ue * ue;
+            ke += 0.25 * L.l_e[e] * L.d_e[e] * ue * ue;
         }
         m = A * h;
         en = g * h * (0.5 * g * h * A + ke);
@@ -508,53 +508,13 @@ template <class R>
 __global__ void k_patch_scan(const DevLevelT<R>* __restrict__ lvs, int ja, const int32_t* sig_any, int tail_j) {
     int j = ja + int(blockIdx.x);
     if (j == tail_j && !sig_any[j - 1]) return;
-    const DevLevelT<R>& L = lvs[j];
-    __shared__ int warp_tot[32];
-    __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int32_t tag = int32_t(L.J) << LVL_SHIFT;
-    for (int64_t start = 0; start < L.npatch; start += blockDim.x) {
-        int64_t i = start + threadIdx.x;
-        int f = (i < L.npatch) ? L.pflag[i] : 0;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
-        int pre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warp_tot[w] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int k = 0; k < w; ++k) off += warp_tot[k];
-        if (f) L.patches[base + off + pre] = tag | int32_t(i);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int k = 0; k < nw; ++k) tot += warp_tot[k];
-            base += tot;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        int n = base;
-        if ((L.nflag[L.nelem] | L.nflag[L.nelem + 1]) & AVAIL) L.patches[n++] = tag | int32_t(L.npatch);
-        *L.npatches = n;
-    }
+    patch_scan_level(lvs[j]);
 }
 
-// concatenation of the level lists jmin..jmax into one list
 template <class R>
-__global__ void k_concat(const DevLevelT<R>* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count) {
-    __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    for (int j = jmin; j <= jmax; ++j) {
-        const DevLevelT<R>& L = lvs[j];
-        int n = *L.npatches;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) all[base + i] = L.patches[i];
-        __syncthreads();
-        if (threadIdx.x == 0) base += n;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *count = base;
+__global__ void k_concat(const DevLevelT<R>* __restrict__ lvs, int jmin, int jmax, int32_t* all, int32_t* count,
+                         int32_t* irr, int32_t* irr_count) {
+    concat_lists(lvs, jmin, jmax, all, count, irr, irr_count);
 }
 
 }  // namespace
@@ -702,9 +662,10 @@ void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s) 
 }
 
 template <class R>
-void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s) {
+void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
+                   int32_t* irr_count, cudaStream_t s) {
     g_launches++;
-    k_concat<R><<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count);
+    k_concat<R><<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count, irr, irr_count);
 }
 
 template <class R>
@@ -757,7 +718,7 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
                                     cudaStream_t);                                                           \
     template void launch_mark_support<R>(const WorkT<R>&, cudaStream_t);                                     \
     template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
-    template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, cudaStream_t);         \
+    template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, int32_t*, int32_t*, cudaStream_t);         \
     template void launch_patch_scan<R>(const DevLevelT<R>*, int, int, cudaStream_t);                         \
     template int sums_blocks<R>(const DevLevelT<R>&);                                                        \
     template void launch_sums<R>(const DevLevelT<R>&, double, double, double*, double*, cudaStream_t);       \

@@ -89,8 +89,11 @@ template <class R> void launch_mask(const MaskArgsT<R>& a, cudaStream_t s);
 template <class R> void launch_live_all(const DevLevelT<R>* lvs, const Span& nodes, const Span& edges, cudaStream_t s);
 template <class R> void launch_covered_all(const DevLevelT<R>* lvs, const Span& nodes_c, cudaStream_t s);
 template <class R> void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream_t s);
+// the all-level active list from the levels' lists, and its entries whose tile is
+// not regular (irregular list, same order)
 template <class R>
-void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, cudaStream_t s);
+void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
+                   int32_t* irr_count, cudaStream_t s);
 // ascending active-patch lists of levels ja..jb from the patch flags
 template <class R> void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s);
 template <class R> int sums_blocks(const DevLevelT<R>& L);

@@ -20,162 +20,9 @@ namespace {
 
 __device__ __forceinline__ int64_t lgid() { return int64_t(blockIdx.x) * blockDim.x + threadIdx.x; }
 
-__device__ __forceinline__ bool lfind(const Span& sp, int64_t t, int& j, int64_t& i) {
-    for (j = sp.ja; j <= sp.jb; ++j)
-        if (t < sp.off[j + 1 - sp.ja]) {
-            i = t - sp.off[j - sp.ja];
-            return true;
-        }
-    return false;
-}
 
-__device__ __forceinline__ float feat_log(double x) { return float(log2(1.0 + x)); }
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// Own features of a patch: log2(1 + max|h~|/eps_h) over its live odd nodes,
-// log2(1 + max|u~|/eps_u) over its live interior edges and the pair coefficients of
-// the coarse edges under its even nodes, and the fraction of its nodes that are
-// live.  An inactive patch has no live point: all three are 0 (k_feat_clear, one
-// thread per patch; the pole entry is cleared too and recomputed when listed).
-// The active patches of levels ja..jb come from the active list, one warp per
-// entry (one lane per node of the patch).
-template <class R>
-__global__ void k_feat_clear(const DevLevelT<R>* __restrict__ lvs, Span sp) {
-    int j;
-    int64_t P;
-    if (!lfind(sp, lgid(), j, P)) return;
-    const DevLevelT<R>& L = lvs[j];
-    const int64_t np1 = L.npatch + 1;
-    if (P == L.npatch || !L.pflag[P]) L.pfeat[0 * np1 + P] = 0.f, L.pfeat[1 * np1 + P] = 0.f, L.pfeat[6 * np1 + P] = 0.f;
-}
-
-template <class R>
-__global__ void k_feat_own(const DevLevelT<R>* __restrict__ lvs, int ja, int jb, const int32_t* __restrict__ list,
-                           const int32_t* __restrict__ count, const double* __restrict__ thr) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t w = lgid() >> 5; w < *count; w += nw) {
-        const int32_t ent = list[w];
-        const int j = ent >> LVL_SHIFT;
-        if (j < ja || j > jb) continue;
-        const int64_t P = ent & PATCH_MASK;
-        const DevLevelT<R>& L = lvs[j];
-        const DevLevelT<R>& C = lvs[j - 1];
-        const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
-        const bool pole = P == L.npatch;
-        R mh = R(0), mu = R(0);
-        int live = 0;
-        const int64_t nn = pole ? 2 : pp;
-        for (int64_t l = lane; l < nn; l += 32) {
-            const int64_t v = pole ? L.nelem + l : P * pp + l;
-            const uint8_t f = L.nflag[v];
-            live += (f & LIVE) ? 1 : 0;
-            if ((f & LIVE) && L.f2c[v] < 0) mh = fmax(mh, fabs(L.hdet[v]));
-            if (pole) continue;
-            for (int o = 0; o < 3; ++o) {
-                const int64_t e = o * L.nelem + v;
-                if ((L.eflag[e] & LIVE) && L.fe_kind[e] == 2) mu = fmax(mu, fabs(L.ui[e]));
-            }
-            const int32_t ce = L.f2c[v];
-            if (ce >= 0 && ce < C.nelem) {
-                for (int o = 0; o < 3; ++o) {
-                    const int64_t E = o * C.nelem + ce;
-                    const int32_t h0 = C.half[E], h1 = C.half[C.E + E];
-                    if ((L.eflag[h0] | L.eflag[h1]) & LIVE) mu = fmax(mu, fabs(L.ue[E]));
-                }
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            mh = fmax(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-            mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-            live += __shfl_xor_sync(0xffffffffu, live, o);
-        }
-        if (lane == 0) {
-            const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
-            L.pfeat[0 * np1 + P] = feat_log(double(mh) / eh);
-            L.pfeat[1 * np1 + P] = feat_log(double(mu) / eu);
-            L.pfeat[6 * np1 + P] = float(live) / float(nn);
-        }
-    }
-}
-
-// Context features (one thread per patch): the coarse patch's own features (zero on
-// the level above Jmin, which carries no coefficients), the maxima over the
-// neighbour patches, and the level's depth in Jmin..Jmax.
-template <class R>
-__global__ void k_feat_ctx(const DevLevelT<R>* __restrict__ lvs, Span sp, int jmin, int jmax) {
-    int j;
-    int64_t P;
-    if (!lfind(sp, lgid(), j, P)) return;
-    const DevLevelT<R>& L = lvs[j];
-    const DevLevelT<R>& C = lvs[j - 1];
-    const int64_t np1 = L.npatch + 1, cnp1 = C.npatch + 1;
-    float f2 = 0, f3 = 0, f4 = 0, f5 = 0;
-    const int32_t cp = L.ppar[P];
-    if (j - 1 > jmin && cp >= 0) f2 = C.pfeat[0 * cnp1 + cp], f3 = C.pfeat[1 * cnp1 + cp];
-    for (int k = 0; k < NB; ++k) {
-        const int32_t Q = L.pnbr[k * np1 + P];
-        if (Q < 0) break;
-        f4 = fmaxf(f4, L.pfeat[0 * np1 + Q]);
-        f5 = fmaxf(f5, L.pfeat[1 * np1 + Q]);
-    }
-    L.pfeat[2 * np1 + P] = f2;
-    L.pfeat[3 * np1 + P] = f3;
-    L.pfeat[4 * np1 + P] = f4;
-    L.pfeat[5 * np1 + P] = f5;
-    L.pfeat[7 * np1 + P] = float(j - jmin) / float(jmax > jmin ? jmax - jmin : 1);
-}
-
-// perceptron logit of one feature vector x[NF] (weights already BF16-rounded)
-__device__ __forceinline__ float mlp_logit(const MlpWeights& w, const float* x, float* a_out, float* z_out) {
-    float out = w.b2;
-    for (int h = 0; h < NH; ++h) {
-        float z = w.b1[h];
-#pragma unroll
-        for (int f = 0; f < NF; ++f) z = fmaf(x[f], __bfloat162float(w.w1[f * NH + h]), z);
-        const float a = z > 0.f ? z : 0.f;
-        if (a_out) a_out[h] = a, z_out[h] = z;
-        out = fmaf(a, __bfloat162float(w.w2[h]), out);
-    }
-    return out;
-}
-
-template <class R>
-__global__ void k_propose(const DevLevelT<R>* __restrict__ lvs, Span sp, MlpWeights wp, float logit_tau) {
-    __shared__ MlpWeights w;   // staged once per block (indexed loads from the parameter would go to local memory)
-    if (threadIdx.x == 0) w = wp;
-    __syncthreads();
-    int j;
-    int64_t P;
-    if (!lfind(sp, lgid(), j, P)) return;
-    const DevLevelT<R>& L = lvs[j];
-    const int64_t np1 = L.npatch + 1;
-    // only patches that are not active yet: an active patch stays under the exact rules
-    const bool active = P < L.npatch ? L.pflag[P] != 0 : L.pfeat[6 * np1 + P] > 0.f;
-    float x[NF];
-#pragma unroll
-    for (int f = 0; f < NF; ++f) x[f] = L.pfeat[f * np1 + P];
-    L.prop[P] = (!active && mlp_logit(w, x, nullptr, nullptr) > logit_tau) ? 1 : 0;
-}
-
-// before a mask (post == 0): clear the exact-set flags and mark every level with a
-// proposed patch as able to gain points (any[j - 1], the flag a tail level checks);
-// after it (post == 1): the proposal it applied becomes the previous one
-template <class R>
-__global__ void k_prop_roll(const DevLevelT<R>* __restrict__ lvs, Span sp, int post, int32_t* any) {
-    int j;
-    int64_t P;
-    if (!lfind(sp, lgid(), j, P)) return;
-    const DevLevelT<R>& L = lvs[j];
-    if (post) {
-        L.prop_prev[P] = L.prop[P];
-        L.prop[P] = 0;
-    } else {
-        L.pexact[P] = 0;
-        if (L.prop[P]) any[j - 1] = 1;
-    }
-}
 
 // ------------------------------------------------------------------ training
 
@@ -299,34 +146,6 @@ MlpWeights mlp_weights(const float* params) {
     return w;
 }
 
-template <class R>
-void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const double* thr, int jmin, int jmax,
-                     const int32_t* active, const int32_t* active_count, unsigned grid, cudaStream_t s) {
-    const int64_t n = patches_f.off[patches_f.jb + 1 - patches_f.ja];
-    if (n <= 0) return;
-    count_launch(3);
-    k_feat_clear<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f);
-    k_feat_own<R><<<grid, 256, 0, s>>>(lvs, patches_f.ja, patches_f.jb, active, active_count, thr);
-    k_feat_ctx<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, jmin, jmax);
-}
-
-template <class R>
-void launch_propose(const DevLevelT<R>* lvs, const Span& patches_f, const MlpWeights& w, float tau, cudaStream_t s) {
-    const int64_t n = patches_f.off[patches_f.jb + 1 - patches_f.ja];
-    if (n <= 0) return;
-    count_launch(1);
-    const float logit_tau = std::log(tau / (1.f - tau));
-    k_propose<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches_f, w, logit_tau);
-}
-
-template <class R>
-void launch_prop_roll(const DevLevelT<R>* lvs, const Span& patches, int post, int32_t* any, cudaStream_t s) {
-    const int64_t n = patches.off[patches.jb + 1 - patches.ja];
-    if (n <= 0) return;
-    count_launch(1);
-    k_prop_roll<R><<<blocks_for(n, 256), 256, 0, s>>>(lvs, patches, post, any);
-}
-
 void launch_mlp_grad(const float* X, const float* y, int64_t n, const float* params, float pos_w, float* work,
                      float* out, cudaStream_t s) {
     count_launch(2);
@@ -344,15 +163,6 @@ void launch_mlp_predict(const float* X, int64_t n, const float* params, float* o
     count_launch(1);
     k_mlp_predict<<<unsigned(std::min<int64_t>(blocks_for(n, 256), 4096)), 256, 0, s>>>(X, n, params, out);
 }
-
-template void launch_features<double>(const DevLevelT<double>*, const Span&, const double*, int, int, const int32_t*,
-                                      const int32_t*, unsigned, cudaStream_t);
-template void launch_features<float>(const DevLevelT<float>*, const Span&, const double*, int, int, const int32_t*,
-                                     const int32_t*, unsigned, cudaStream_t);
-template void launch_propose<double>(const DevLevelT<double>*, const Span&, const MlpWeights&, float, cudaStream_t);
-template void launch_propose<float>(const DevLevelT<float>*, const Span&, const MlpWeights&, float, cudaStream_t);
-template void launch_prop_roll<double>(const DevLevelT<double>*, const Span&, int, int32_t*, cudaStream_t);
-template void launch_prop_roll<float>(const DevLevelT<float>*, const Span&, int, int32_t*, cudaStream_t);
 
 }  // namespace sww
 

@@ -18,25 +18,26 @@ struct MlpWeights {
     float b2;
 };
 
+// perceptron logit of one feature vector x[NF] (weights already BF16-rounded)
+__device__ __forceinline__ float mlp_logit(const MlpWeights& w, const float* x, float* a_out, float* z_out) {
+    float out = w.b2;
+    for (int h = 0; h < NH; ++h) {
+        float z = w.b1[h];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) z = fmaf(x[f], __bfloat162float(w.w1[f * NH + h]), z);
+        const float a = z > 0.f ? z : 0.f;
+        if (a_out) a_out[h] = a, z_out[h] = z;
+        out = fmaf(a, __bfloat162float(w.w2[h]), out);
+    }
+    return out;
+}
+
 // Blocks of the gradient kernel; the caller's work buffer holds
 // MLP_GRAD_BLOCKS * (MLP_PARAMS + 1) floats.
 constexpr int MLP_GRAD_BLOCKS = 256;
 
 // BF16-rounded weights of FP32 master parameters (W1, b1, w2, b2 in that order).
 MlpWeights mlp_weights(const float* params);
-
-// features of the patches of patches_f's levels (levels above Jmin)
-// (active, active_count: the all-level active list; grid: blocks of 256 for it)
-template <class R>
-void launch_features(const DevLevelT<R>* lvs, const Span& patches_f, const double* thr, int jmin, int jmax,
-                     const int32_t* active, const int32_t* active_count, unsigned grid, cudaStream_t s);
-// prop[P] = sigmoid(logit) > tau on the same patches
-template <class R>
-void launch_propose(const DevLevelT<R>* lvs, const Span& patches_f, const MlpWeights& w, float tau, cudaStream_t s);
-// post == 0 (before a mask): pexact <- 0 and any[j - 1] <- 1 for every level j with a
-// proposed patch; post == 1 (after it): prop_prev <- prop, prop <- 0
-template <class R>
-void launch_prop_roll(const DevLevelT<R>* lvs, const Span& patches, int post, int32_t* any, cudaStream_t s);
 
 // out[0..MLP_PARAMS) = mean gradient, out[MLP_PARAMS] = mean loss
 void launch_mlp_grad(const float* X, const float* y, int64_t n, const float* params, float pos_w, float* work,

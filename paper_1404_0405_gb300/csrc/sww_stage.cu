@@ -3,12 +3,14 @@
 // barriers instead of kernel boundaries:
 //
 //   ghosts of levels Jmin+1..top (coarse to fine, one phase per level)
-//   -> q at triangles, F at edges (all levels)
-//   -> div, K, B at nodes, q F^perp at edges (all levels)
+//   -> the trend of every active patch: the structured tile of a regular patch
+//      (F, q, div F, K, B, q F^perp), F and q from the tabulated bodies elsewhere
+//   -> div, K, B and q F^perp at the points of the irregular patches
 //   -> restriction of B, F, q F^perp and div, top-1 down to Jmin (two phases a level)
 //   -> RK stage update of the live points (all levels)
 //
-// The level records are staged in shared memory once per block.  Loads of this
+// The level records are staged in shared memory once per block; the tile of the
+// patch a block works on is staged in dynamic shared memory.  Loads of this
 // translation unit bypass L1 (compiled with -dlcm=cg): values written by other
 // blocks in one phase are read in the next.  Every barrier wait is bounded: after
 // about two seconds a block sets the error flag and the kernel returns.
@@ -20,12 +22,14 @@
 #include "sww_core.cuh"
 #include "sww_kernels.h"
 #include "sww_stage.h"
+#include "tile.h"
 
 namespace sww {
 
 namespace {
 
 #include "sww_bodies.cuh"
+#include "sww_tile.cuh"
 
 constexpr int STAGE_TPB = 512;
 constexpr int MAXL = 12;
@@ -94,21 +98,15 @@ __device__ bool grid_sync(unsigned* bar, int* err, long long spin = 0, int skip 
     return ok != 0;
 }
 
-// Barrier between phases: the grid barrier of a cooperative launch, or the
-// hardware barrier of a thread-block cluster when the launch is one cluster (all
-// its blocks are co-scheduled, and every thread runs every phase).
+// barrier between phases: the grid barrier of the cooperative launch
 template <class R>
 __device__ __forceinline__ bool stage_sync(const StageArgs<R>& a) {
-    if (a.cluster) {
-        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-        return true;
-    }
     return grid_sync(a.bar, a.err, a.spin, a.skip);
 }
 
-template <class R>
+template <class R, int P>
 __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevLevelT<R> sl[MAXL];
     {
         const int words = int((a.jmax + 1) * sizeof(DevLevelT<R>) / sizeof(int));
@@ -131,14 +129,35 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
         });
         if (!stage_sync(a)) return;
     }
-    ITEMS(K_EDGE | K_TRI, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
-        if (kind == K_EDGE)
-            flux_at(L, id, H);
-        else
-            pv_at(L, id, H);
-    });
+    {
+        // one active patch per block at a time
+        TilePlan<P, STAGE_TPB> plan;
+        plan.init();
+        const int n = *a.all_count;
+        for (int e = blockIdx.x; e < n; e += gridDim.x) {
+            const int32_t ent = a.all_list[e];
+            const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
+            const int64_t pat = ent & PATCH_MASK;
+            if (tile_regular(L, pat)) {
+                TileCodes<P, STAGE_TPB> codes;
+                codes.load(L, pat, plan);
+                tile_trend<R, P, STAGE_TPB>(L, pat, H, g, plan, codes, smem);
+            } else {
+                for (int it = threadIdx.x; it < 5 * a.P; it += blockDim.x) {
+                    auto body = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t) {
+                        if (kind == K_EDGE)
+                            flux_at(LL, id, H);
+                        else
+                            pv_at(LL, id, H);
+                    };
+                    visit_item<K_EDGE | K_TRI>(L, pat, uint32_t(it), a.P, body);
+                }
+            }
+            __syncthreads();
+        }
+    }
     if (!stage_sync(a)) return;
-    ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
+    ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.irr_list, a.irr_count, a.P) {
         if (kind == K_NODE)
             node_at(L, id, g);
         else
@@ -165,206 +184,51 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
     });
 }
 
-// ------------------------------------------------------------------ ensembles
-
-constexpr int MAXM = 128;
-
-// Items of one phase over the members of an ensemble.  mode < 0: each member's
-// all-level list; else the level-j list of the members whose top level is at
-// least j + mode (0 ghosts, -1 restriction).  body(L, kind, id, el, member).
-template <int KINDS, class R, class Body>
-__device__ __forceinline__ void batch_items(const BatchArgs<R>& a, int j, int mode, int64_t* pre, Body body) {
-    if (threadIdx.x == 0) {
-        int64_t acc = 0;
-        for (int m = 0; m < a.nm; ++m) {
-            pre[m] = acc;
-            const MemberRef<R>& M = a.m[m];
-            if (mode < 0)
-                acc += *M.all_count;
-            else if (j <= M.jtop + mode)
-                acc += *M.lvs[j].npatches;
-        }
-        pre[a.nm] = acc;
-    }
-    __syncthreads();
-    constexpr int NS = slots_of<KINDS>();
-    const int64_t S = int64_t(NS) * a.P;
-    const int64_t n = pre[a.nm] * S;
-    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    for (int64_t it = gid(); it < n; it += stride) {
-        const int64_t e = it / S;
-        int lo = 0, hi = a.nm - 1;   // last member whose first entry is <= e
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (pre[mid] <= e) lo = mid; else hi = mid - 1;
-        }
-        const MemberRef<R>& M = a.m[lo];
-        const int32_t ent = mode < 0 ? M.all_list[e - pre[lo]] : M.lvs[j].patches[e - pre[lo]];
-        const DevLevelT<R>& L = M.lvs[ent >> LVL_SHIFT];
-        auto b = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t el) { body(LL, kind, id, el, M); };
-        visit_item<KINDS>(L, int64_t(ent & PATCH_MASK), uint32_t(it - e * S), a.P, b);
-    }
-    __syncthreads();
+template <class R, int P>
+unsigned stage_grid_p(int nsm) {
+    constexpr size_t smem = Tile<R, P>::BYTES;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_stage<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<R, P>, STAGE_TPB, smem) != cudaSuccess) return 0;
+    return unsigned(std::max(per_sm, 0) * nsm);
 }
 
-// One RK stage of every member of an ensemble, the phases of k_stage in order,
-// each phase over all members (the levels of member m are a contiguous record
-// array, so the coarser and finer records of L are (&L)[-1] and (&L)[1]).
-template <class R>
-__global__ void __launch_bounds__(STAGE_TPB) k_stage_batch(BatchArgs<R> a) {
-    __shared__ int64_t pre[MAXM + 1];
-    const R H = R(a.H), g = R(a.g);
-    for (int j = a.jmin + 1; j <= a.jtop_max; ++j) {
-        batch_items<K_NODE | K_EDGE>(a, j, 0, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
-            if (kind == K_NODE)
-                fill_node(L, (&L)[-1], id);
-            else
-                fill_edge(L, (&L)[-1], id);
-        });
-        if (!grid_sync(a.bar, a.err)) return;
-    }
-    batch_items<K_EDGE | K_TRI>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
-        if (kind == K_EDGE)
-            flux_at(L, id, H);
-        else
-            pv_at(L, id, H);
-    });
-    if (!grid_sync(a.bar, a.err)) return;
-    batch_items<K_NODE | K_EDGE>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
-        if (kind == K_NODE)
-            node_at(L, id, g);
-        else
-            coriolis_at(L, id);
-    });
-    if (!grid_sync(a.bar, a.err)) return;
-    for (int j = a.jtop_max - 1; j >= a.jmin; --j) {
-        batch_items<K_NODE | K_EDGE>(a, j, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>&) {
-            restrict_item(L, (&L)[1], kind, id);
-        });
-        if (!grid_sync(a.bar, a.err)) return;
-        batch_items<K_NODE>(a, j, -1, pre, [&](const DevLevelT<R>& L, int, int64_t id, int64_t, const MemberRef<R>&) {
-            div_at(L, id);
-        });
-        if (!grid_sync(a.bar, a.err)) return;
-    }
-    batch_items<K_NODE | K_EDGE>(a, 0, -1, pre, [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t, const MemberRef<R>& M) {
-        const R dt = R(*M.dt);
-        if (kind == K_NODE)
-            update_node(L, id, a.st, dt);
-        else
-            update_edge(L, id, a.st, dt);
-    });
+template <class R, int P>
+cudaError_t launch_stage_p(const StageArgs<R>& a, unsigned grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(STAGE_TPB);
+    cfg.dynamicSmemBytes = Tile<R, P>::BYTES;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch(1);
+    return cudaLaunchKernelEx(&cfg, k_stage<R, P>, a);
 }
 
 }  // namespace
 
+// patch area -> tile side of the stage kernel (sides 1 and 2 have no regular tile)
 template <class R>
-unsigned stage_grid(int nsm) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<R>, STAGE_TPB, 0) != cudaSuccess) return 0;
-    return unsigned(std::max(per_sm, 0) * nsm);
+unsigned stage_grid(int P, int nsm) {
+    return P == 64 ? stage_grid_p<R, 8>(nsm) : P == 256 ? stage_grid_p<R, 16>(nsm) : stage_grid_p<R, 4>(nsm);
 }
 
 template <class R>
 cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s) {
     if (a.jmax + 1 > MAXL) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(STAGE_TPB);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    count_launch(1);
-    return cudaLaunchKernelEx(&cfg, k_stage<R>, a);
+    return a.P == 64 ? launch_stage_p<R, 8>(a, grid, s) : a.P == 256 ? launch_stage_p<R, 16>(a, grid, s)
+                                                                    : launch_stage_p<R, 4>(a, grid, s);
 }
 
-// One RK stage as a single thread-block cluster (up to 16 blocks): for members of an
-// ensemble whose steps overlap on their own streams.
-template <class R>
-cudaError_t launch_stage_cluster(const StageArgs<R>& a, int blocks, cudaStream_t s) {
-    if (a.jmax + 1 > MAXL || !a.cluster) return cudaErrorInvalidValue;
-    if (blocks > 8) {
-        cudaError_t e = cudaFuncSetAttribute(k_stage<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-    }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(STAGE_TPB);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = blocks;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    count_launch(1);
-    return cudaLaunchKernelEx(&cfg, k_stage<R>, a);
-}
-
-// largest cluster of stage blocks that can be resident (16, else 8, else 0)
-template <class R>
-int stage_cluster_size() {
-    for (int c : {16, 8}) {
-        if (c > 8 && cudaFuncSetAttribute(k_stage<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-            continue;
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(STAGE_TPB);
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = c;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, k_stage<R>, &cfg) == cudaSuccess && n > 0) return c;
-        cudaGetLastError();
-    }
-    return 0;
-}
-
-template <class R>
-unsigned stage_batch_grid(int nsm) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_batch<R>, STAGE_TPB, 0) != cudaSuccess) return 0;
-    return unsigned(std::max(per_sm, 0) * nsm);
-}
-
-template <class R>
-cudaError_t launch_stage_batch(const BatchArgs<R>& a, unsigned grid, cudaStream_t s) {
-    if (a.nm < 1 || a.nm > MAXM) return cudaErrorInvalidValue;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(STAGE_TPB);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    count_launch(1);
-    return cudaLaunchKernelEx(&cfg, k_stage_batch<R>, a);
-}
-
-template unsigned stage_grid<double>(int);
-template unsigned stage_grid<float>(int);
+template unsigned stage_grid<double>(int, int);
+template unsigned stage_grid<float>(int, int);
 template cudaError_t launch_stage<double>(const StageArgs<double>&, unsigned, cudaStream_t);
 template cudaError_t launch_stage<float>(const StageArgs<float>&, unsigned, cudaStream_t);
-template cudaError_t launch_stage_cluster<double>(const StageArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_stage_cluster<float>(const StageArgs<float>&, int, cudaStream_t);
-template int stage_cluster_size<double>();
-template int stage_cluster_size<float>();
-template unsigned stage_batch_grid<double>(int);
-template unsigned stage_batch_grid<float>(int);
-template cudaError_t launch_stage_batch<double>(const BatchArgs<double>&, unsigned, cudaStream_t);
-template cudaError_t launch_stage_batch<float>(const BatchArgs<float>&, unsigned, cudaStream_t);
 
 }  // namespace sww

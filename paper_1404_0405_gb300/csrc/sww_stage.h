@@ -21,6 +21,8 @@ struct StageArgs {
     const DevLevelT<R>* lvs;
     const int32_t* all_list;
     const int32_t* all_count;
+    const int32_t* irr_list;    // entries of all_list whose tile is not regular
+    const int32_t* irr_count;
     int P;
     int jmin, jtop, jmax;
     double H, g;
@@ -28,7 +30,6 @@ struct StageArgs {
     const double* dt;
     unsigned* bar;
     int* err;
-    int cluster;   // 1: the launch is one thread-block cluster (hardware barrier)
     // bounded barrier waits: a wait gives up after `spin` clock cycles (<= 0: the
     // default, about 2 s); block `skip` (fault injection for tests, -1: none) leaves
     // at the first barrier without arriving, so the others' waits run out
@@ -54,10 +55,12 @@ struct MemberRef {
     int j1;                    // top level of the inverse transform (min(jtop + 1, jmax))
     int jmax;
     const int* err;            // barrier error flag of the member's persistent stages
+    const int32_t* irr_list;   // entries of all_list whose tile is not regular
+    const int32_t* irr_count;
 };
 
-// One persistent RK stage of nm members (m: device array of nm refs, nm <= 128)
-// with a common patch area P, Jmin, mean depth H and gravity g.
+// One RK stage of nm members (m: device array of nm refs, nm <= 128) with a common
+// patch area P, Jmin, mean depth H and gravity g.
 template <class R>
 struct BatchArgs {
     const MemberRef<R>* m;
@@ -79,24 +82,30 @@ struct BatchOut {
     int32_t pad;
 };
 
-// co-resident blocks of the stage kernel on nsm SMs (0 when it cannot run)
+// co-resident blocks of the stage kernel for patch area P on nsm SMs (0 when it
+// cannot run)
 template <class R>
-unsigned stage_grid(int nsm);
+unsigned stage_grid(int P, int nsm);
 template <class R>
 cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s);
+// The trend of a stage over all members (sww_tile.cu): the structured kernel over
+// every active patch (parts bit 0), then the tabulated node and Coriolis bodies
+// over the irregular patches (bit 1).  entries and irr_entries bound the members'
+// all-level and irregular list entries in total.
 template <class R>
-cudaError_t launch_stage_cluster(const StageArgs<R>& a, int blocks, cudaStream_t s);
-template <class R>
-int stage_cluster_size();
-template <class R>
-unsigned stage_batch_grid(int nsm);
-template <class R>
-cudaError_t launch_stage_batch(const BatchArgs<R>& a, unsigned grid, cudaStream_t s);
-// The same stage as one regular launch per phase over all members (level-serial
+cudaError_t launch_tile_trend(const BatchArgs<R>& a, int64_t entries, int64_t irr_entries, int nsm, int parts,
+                              cudaStream_t s);
+// One RK stage as one regular launch per phase over all members (level-serial
 // phases once per level); level_entries[j] bounds the members' level-j list
-// entries in total (for the grid sizes).
+// entries in total, irr_entries their irregular entries (for the grid sizes).
 template <class R>
-cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int nsm, cudaStream_t s);
+cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* level_entries, int64_t irr_entries, int nsm,
+                                      cudaStream_t s);
+// The same stage in parts: 0 the ghosts, 1 the structured trend, 2 the irregular
+// patches, 3 the restrictions and divergences level by level, 4 the update.
+template <class R>
+cudaError_t launch_stage_batch_part(const BatchArgs<R>& a, const int64_t* level_entries, int64_t irr_entries, int nsm,
+                                    int part, cudaStream_t s);
 // Before the stages of a step, over all members: the RK base copy and the time
 // step (dt > 0 for every member, else each member's CFL step).
 template <class R>

@@ -1,0 +1,336 @@
+// Structured trend of one regular patch (Sec. 3.1 operators; Sec. 5.2 patches):
+// the tile of tile.h staged in shared memory, neighbours at constant offsets,
+// the energy-conserving Coriolis weights derived from the kite areas.
+//
+// Included inside an anonymous namespace after sww_bodies.cuh.  All threads of
+// the block call tile_trend together (it synchronises the block).
+//
+// Per tile: depth and velocity with their flags over the tile range (velocity
+// signs turned to the local directions), edge lengths d_e and l_e, and for
+// each triangle its three kite areas, its area and its Coriolis parameter --
+// the FP64 geometry rounded to the working precision R as it is staged.  Then
+//   F = h_e u at every available edge, q = (curl u + f)/h_v at every available
+//   triangle (kite-weighted h_v), the kite fractions R of every node of
+//   [0, p]^2 (its six kites over their sum);
+//   div F, K and B = g dh + K at the patch's available nodes, and at its live
+//   edges q F^perp = (1/d_e) sum over the ten edges e' of the two cells of
+//   n_{e,i} n_{e',i} (1/2 - sum of the fractions passed counter-clockwise from e
+//   to e') l_{e'} F_{e'} (q_e + q_{e'})/2.
+// The outputs are those of the tabulated bodies (flux_at, pv_at, node_at,
+// coriolis_at): F at available edges, q at available triangles, c and B at
+// available nodes, Q at live edges, for the patch's own points.
+#pragma once
+// (tile.h is included at file scope by the translation unit)
+
+template <class R, int P>
+struct Tile {
+    static constexpr int W = P + 3;   // node positions per side, a = -1 .. P + 1
+    static constexpr int NN = W * W;
+    static constexpr tile::Shape S{P};
+    static constexpr int HALO = S.halo();
+    // shared-memory layout (bytes)
+    static constexpr size_t OFF_DH = 0;                              // R[NN]
+    static constexpr size_t OFF_U = OFF_DH + sizeof(R) * NN;         // R[3 NN] (local direction)
+    static constexpr size_t OFF_F = OFF_U + sizeof(R) * 3 * NN;      // R[3 NN]
+    static constexpr size_t OFF_DE = OFF_F + sizeof(R) * 3 * NN;     // R[3 NN]
+    static constexpr size_t OFF_LE = OFF_DE + sizeof(R) * 3 * NN;    // R[3 NN]
+    static constexpr size_t OFF_Q = OFF_LE + sizeof(R) * 3 * NN;     // R[2 NN]
+    static constexpr size_t OFF_KT = OFF_Q + sizeof(R) * 2 * NN;     // R[6 NN]: kite c of triangle t at (3t + c) NN
+    static constexpr size_t OFF_IS = OFF_KT + sizeof(R) * 6 * NN;    // R[NN]: 1 / (sum of a node's six kites)
+    static constexpr size_t OFF_NF = OFF_IS + sizeof(R) * NN;        // uint8[NN]
+    static constexpr size_t OFF_EF = OFF_NF + NN;                    // uint8[3 NN]
+    static constexpr size_t BYTES = (OFF_EF + 3 * NN + 15) / 16 * 16;
+
+    __device__ static int at(int a, int b) { return (a + 1) * W + (b + 1); }
+};
+
+// The slots of a tile one thread stages, for NT threads (slot i of thread t is
+// node x = t + i NT, edge y = t + i NT, triangle z = t + i NT): own points as
+// -(offset) - 1 (offset of the element in the patch, with o P^2 or t P^2 added for
+// edges and triangles), halo points as their index in the patch's halo table,
+// positions outside the block ranges as NONE.  The same for every tile.
+template <int P, int NT>
+struct TilePlan {
+    static constexpr int W = P + 3, NN = W * W;
+    static constexpr int SN = (NN + NT - 1) / NT, SE = (3 * NN + NT - 1) / NT, ST = (2 * NN + NT - 1) / NT;
+    static constexpr int NONE = -(1 << 30);
+    int n[SN], e[SE], t[ST];
+
+    __device__ void init() {
+        constexpr tile::Shape S{P};
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < SN; ++i) {
+            const int x = tid + i * NT;
+            int a = x / W - 1, b = x % W - 1;
+            n[i] = x >= NN ? NONE : (a >= 0 && a < P && b >= 0 && b < P) ? -(a * P + b) - 1 : tile::slot(P, P + 1, a, b);
+        }
+#pragma unroll
+        for (int i = 0; i < SE; ++i) {
+            const int y = tid + i * NT, o = y / NN, x = y - o * NN;
+            int a = x / W - 1, b = x % W - 1;
+            e[i] = (y >= 3 * NN || a > S.eA(o) || b > S.eB(o)) ? NONE
+                   : (a >= 0 && a < P && b >= 0 && b < P) ? -(o * P * P + a * P + b) - 1
+                                                          : S.off_edge(o) + tile::slot(P, S.eB(o), a, b);
+        }
+#pragma unroll
+        for (int i = 0; i < ST; ++i) {
+            const int z = tid + i * NT, tt = z / NN, x = z - tt * NN;
+            int a = x / W - 1, b = x % W - 1;
+            t[i] = (z >= 2 * NN || a > P || b > P) ? NONE
+                   : (a >= 0 && a < P && b >= 0 && b < P) ? -(tt * P * P + a * P + b) - 1
+                                                          : S.off_tri(tt) + tile::slot(P, P, a, b);
+        }
+    }
+};
+
+// the structured path applies: a regular tile of a level with tiles, inviscid and
+// with the velocity free (the viscous and advection forms take the tabulated path)
+template <class R>
+__device__ __forceinline__ bool tile_regular(const DevLevelT<R>& L, int64_t pat) {
+    return pat < L.npatch && L.thalo != nullptr && L.tirr[pat] == 0 && L.nu == 0.0 && !L.advect;
+}
+
+// position (a, b) of tile slot x = (a + 1) W + (b + 1)
+template <int W>
+__device__ __forceinline__ void tpos(int x, int& a, int& b) {
+    a = x / W - 1;
+    b = x % W - 1;
+}
+
+// Tile offsets, relative to node slot x, of the ring of a node: ring edge k (edge
+// slot: 0..2 the node's own edges o = k, 3..5 the edges coming in from (a-1, b),
+// (a-1, b-1), (a, b-1)) and ring triangle k (between ring edges k and k+1).
+template <int W, int NN>
+__device__ __forceinline__ constexpr int ring_edge_off(int k) {
+    return k == 0 ? 0 : k == 1 ? NN : k == 2 ? 2 * NN : k == 3 ? -W : k == 4 ? NN - W - 1 : 2 * NN - 1;
+}
+template <int W, int NN>
+__device__ __forceinline__ constexpr int ring_tri_off(int k) {
+    return k == 0 ? 0 : k == 1 ? NN : k == 2 ? -W : k == 3 ? NN - W - 1 : k == 4 ? -W - 1 : NN - 1;
+}
+
+// Offset, in the kite array, of ring kite k of the node at slot 0: the node's
+// vertex in ring triangle k (t0 (a,b) 0, t1 (a,b) 0, t0 (a-1,b) 1, t1 (a-1,b-1) 1,
+// t0 (a-1,b-1) 2, t1 (a,b-1) 2) at (3 t + c) NN plus the triangle's slot offset.
+template <int W, int NN>
+__device__ __forceinline__ constexpr int kite_off(int k) {
+    return ring_tri_off<W, NN>(k) - (k & 1) * NN + (3 * (k & 1) + (k >> 1)) * NN;
+}
+
+// q F^perp at the live edge of orientation O from node slot x: the two cells'
+// contributions n_{e,i} sum_{m=1..5} n_{e',i} (1/2 - sum of the fractions passed) l_{e'}
+// F_{e'} (q_e + q_{e'})/2, over d_e (edge e sits at ring position O of its origin and
+// O + 3 of its end); a node's kite fractions are its kites times is (1 / their sum)
+template <class R, int W, int NN, int O>
+__device__ __forceinline__ R tile_coriolis(int x, const R* q, const R* F, const R* le, const R* de, const R* kt,
+                                           const R* is) {
+    constexpr int xe = O == 0 ? W : O == 1 ? W + 1 : 1;   // end node slot - origin node slot
+    const int y = O * NN + x;
+    const R qe = R(0.5) * (q[x + ring_tri_off<W, NN>(O)] + q[x + ring_tri_off<W, NN>((O + 5) % 6)]);
+    const R inv_d = R(1) / de[y];
+    R s = R(0);
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int xv = side == 0 ? x : x + xe;
+        const int k = side == 0 ? O : O + 3;
+        const R ne = side == 0 ? R(1) : R(-1);
+        const R inv_s = is[xv];
+        R csum = R(0);
+#pragma unroll
+        for (int m = 1; m < 6; ++m) {
+            const int kk = (k + m) % 6, kp = (k + m + 5) % 6;
+            csum += kt[kite_off<W, NN>(kp) + xv] * inv_s;
+            const int y2 = xv + ring_edge_off<W, NN>(kk);
+            const R n2 = kk < 3 ? R(1) : R(-1);
+            const R q2 = R(0.5) * (q[xv + ring_tri_off<W, NN>(kk)] + q[xv + ring_tri_off<W, NN>((kk + 5) % 6)]);
+            const R w = ne * n2 * (R(0.5) - csum) * le[y2] * inv_d;
+            s += w * F[y2] * R(0.5) * (qe + q2);
+        }
+    }
+    return s;
+}
+
+// The halo ids a thread's slots need for one tile (own slots: unused), loaded one
+// tile ahead so that their latency overlaps the previous tile's work.
+template <int P, int NT>
+struct TileCodes {
+    using PL = TilePlan<P, NT>;
+    int32_t n[PL::SN], e[PL::SE], t[PL::ST];
+
+    template <class Lv>
+    __device__ void load(const Lv& L, int64_t pat, const PL& plan) {
+        constexpr tile::Shape S{P};
+        const int32_t* __restrict__ halo = L.thalo + pat * S.halo();
+#pragma unroll
+        for (int i = 0; i < PL::SN; ++i) n[i] = plan.n[i] >= 0 ? halo[plan.n[i]] : 0;
+#pragma unroll
+        for (int i = 0; i < PL::SE; ++i) e[i] = plan.e[i] >= 0 ? halo[plan.e[i]] : 0;
+#pragma unroll
+        for (int i = 0; i < PL::ST; ++i) t[i] = plan.t[i] >= 0 ? halo[plan.t[i]] : 0;
+    }
+};
+
+template <class R, int P, int NT>
+__device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const TilePlan<P, NT>& plan,
+                           const TileCodes<P, NT>& codes, unsigned char* smem) {
+    using T = Tile<R, P>;
+    using PL = TilePlan<P, NT>;
+    constexpr int W = T::W, NN = T::NN, PP = P * P;
+    R* dh = reinterpret_cast<R*>(smem + T::OFF_DH);
+    R* u = reinterpret_cast<R*>(smem + T::OFF_U);
+    R* F = reinterpret_cast<R*>(smem + T::OFF_F);
+    R* de = reinterpret_cast<R*>(smem + T::OFF_DE);
+    R* le = reinterpret_cast<R*>(smem + T::OFF_LE);
+    R* q = reinterpret_cast<R*>(smem + T::OFF_Q);
+    R* kt = reinterpret_cast<R*>(smem + T::OFF_KT);
+    R* is = reinterpret_cast<R*>(smem + T::OFF_IS);
+    uint8_t* nf = smem + T::OFF_NF;
+    uint8_t* ef = smem + T::OFF_EF;
+    const int64_t base = pat * PP;
+    const int tid = threadIdx.x;
+    // --- stage: nodes, edges (velocity turned to the local direction), triangles
+    // (their area and Coriolis parameter kept in registers for q)
+#pragma unroll
+    for (int i = 0; i < PL::SN; ++i) {
+        const int c = plan.n[i];
+        if (c == PL::NONE) continue;
+        const int x = tid + i * NT;
+        const int64_t v = c < 0 ? base + (-c - 1) : int64_t(codes.n[i]);
+        dh[x] = L.dh[v];
+        nf[x] = L.nflag[v];
+    }
+#pragma unroll
+    for (int i = 0; i < PL::SE; ++i) {
+        const int c = plan.e[i], y = tid + i * NT;
+        if (c == PL::NONE) {
+            if (y < 3 * NN) ef[y] = 0;
+            continue;
+        }
+        int64_t e;
+        bool rev;
+        if (c < 0) {
+            const int k = -c - 1, o = k / PP;
+            e = o * L.nelem + base + (k - o * PP);
+            rev = false;
+        } else {
+            const int32_t code = codes.e[i];
+            e = code >> 1;
+            rev = code & 1;
+        }
+        const R ue = L.u[e];
+        u[y] = rev ? -ue : ue;
+        ef[y] = L.eflag[e];
+        de[y] = geo<R>(L.d_e, e);
+        le[y] = geo<R>(L.l_e, e);
+    }
+    R tav[PL::ST], tfv[PL::ST];
+#pragma unroll
+    for (int i = 0; i < PL::ST; ++i) {
+        const int c = plan.t[i], z = tid + i * NT;
+        tav[i] = R(1), tfv[i] = R(0);
+        if (c == PL::NONE) continue;
+        int64_t tr;
+        int sft;
+        if (c < 0) {
+            const int k = -c - 1, t = k / PP;
+            tr = t * L.nelem + base + (k - t * PP);
+            sft = 0;
+        } else {
+            const int32_t code = codes.t[i];
+            tr = code >> 2;
+            sft = code & 3;
+        }
+        const int t = z / NN, x = z - t * NN;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const int gc = cc + sft < 3 ? cc + sft : cc + sft - 3;
+            kt[(3 * t + cc) * NN + x] = geo<R>(L.kite, gc * L.T + tr);
+        }
+        tav[i] = geo<R>(L.A_v, tr);
+        tfv[i] = geo<R>(L.f_v, tr);
+    }
+    __syncthreads();
+    // --- F at edges, q at triangles, the kite sums of the nodes of [0, P]^2
+#pragma unroll
+    for (int i = 0; i < PL::SE; ++i) {
+        const int y = tid + i * NT;
+        if (plan.e[i] == PL::NONE) continue;
+        const int o = y / NN, x = y - o * NN;
+        R f = R(0);
+        if (ef[y] & AVAIL) {
+            const int x2 = x + (o == 0 ? W : o == 1 ? W + 1 : 1);
+            if ((nf[x] & AVAIL) && (nf[x2] & AVAIL)) {
+                f = R(0.5) * ((H + dh[x]) + (H + dh[x2])) * u[y];
+                if (plan.e[i] < 0) L.F[o * L.nelem + base + (-plan.e[i] - 1 - o * PP)] = f;
+            }
+        }
+        F[y] = f;
+    }
+#pragma unroll
+    for (int i = 0; i < PL::ST; ++i) {
+        const int c = plan.t[i], z = tid + i * NT;
+        if (c == PL::NONE) continue;
+        const int t = z / NN, x = z - t * NN;
+        // vertices and counter-clockwise sides: t0 (a,b),(a+1,b),(a+1,b+1) with sides
+        // o0(a,b) +, o2(a+1,b) +, o1(a,b) -;  t1 (a,b),(a+1,b+1),(a,b+1) with sides
+        // o1(a,b) +, o0(a,b+1) -, o2(a,b) -
+        const int n1 = t == 0 ? x + W : x + W + 1, n2 = t == 0 ? x + W + 1 : x + 1;
+        const int s0 = t == 0 ? x : NN + x, s1 = t == 0 ? 2 * NN + x + W : x + 1, s2 = t == 0 ? NN + x : 2 * NN + x;
+        R qq = R(0);
+        if ((nf[x] & AVAIL) && (nf[n1] & AVAIL) && (nf[n2] & AVAIL) && (ef[s0] & AVAIL) && (ef[s1] & AVAIL) &&
+            (ef[s2] & AVAIL)) {
+            const R circ = u[s0] * de[s0] + (t == 0 ? R(1) : R(-1)) * u[s1] * de[s1] + R(-1) * u[s2] * de[s2];
+            const R hv = kt[(3 * t) * NN + x] * (H + dh[x]) + kt[(3 * t + 1) * NN + x] * (H + dh[n1]) +
+                         kt[(3 * t + 2) * NN + x] * (H + dh[n2]);
+            qq = (circ / tav[i] + tfv[i]) / (hv / tav[i]);
+            if (c < 0) L.q[t * L.nelem + base + (-c - 1 - t * PP)] = qq;
+        }
+        q[z] = qq;
+    }
+#pragma unroll
+    for (int i = 0; i < PL::SN; ++i) {
+        const int x = tid + i * NT;
+        if (x >= NN) continue;
+        const int a = x / W - 1, b = x % W - 1;
+        if (a < 0 || b < 0 || a > P || b > P) continue;
+        // the node's six kites: t0 (a,b) vertex 0, t1 (a,b) 0, t0 (a-1,b) 1,
+        // t1 (a-1,b-1) 1, t0 (a-1,b-1) 2, t1 (a,b-1) 2
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s += kt[kite_off<W, NN>(k) + x];
+        is[x] = R(1) / s;
+    }
+    __syncthreads();
+    // --- the patch's own nodes (div F, K, B) and live edges (energy-conserving
+    // q F^perp), in one pass of PP + 3 PP items (orientation uniform over a warp when
+    // P * P is a multiple of 32)
+    for (int w = tid; w < 4 * PP; w += NT) {
+        if (w < PP) {
+            const int i = w, x = T::at(i / P, i % P);
+            if (!(nf[x] & AVAIL)) continue;
+            bool ok = true;
+            R div = R(0), ke = R(0);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int y = x + ring_edge_off<W, NN>(k);
+                ok = ok && (ef[y] & AVAIL);
+                const R n = k < 3 ? R(1) : R(-1);
+                div += n * F[y] * le[y];
+                ke += R(0.25) * le[y] * de[y] * u[y] * u[y];
+            }
+            if (!ok) continue;
+            const int64_t v = base + i;
+            const R A = geo<R>(L.A_i, v);
+            L.c[v] = div / A;
+            L.B[v] = g * dh[x] + ke / A;
+        } else {
+            const int o = (w - PP) / PP, i = (w - PP) - o * PP, x = T::at(i / P, i % P);
+            if (!(ef[o * NN + x] & LIVE)) continue;
+            const R Q = o == 0 ? tile_coriolis<R, W, NN, 0>(x, q, F, le, de, kt, is)
+                               : o == 1 ? tile_coriolis<R, W, NN, 1>(x, q, F, le, de, kt, is)
+                                        : tile_coriolis<R, W, NN, 2>(x, q, F, le, de, kt, is);
+            L.Q[o * L.nelem + base + i] = Q;
+        }
+    }
+}

@@ -42,14 +42,11 @@ def _snapshot(sww, m):
     return out, (st["t"], st["mass"], st["energy"], st["steps"])
 
 
-@pytest.mark.parametrize("precision,persistent", [("fp64", "auto"), ("fp32", "auto"), ("fp64", "always"),
-                                                  ("fp32", "always"), ("fp64", "cluster"), ("fp32", "cluster"),
-                                                  ("fp64", "phased"), ("fp32", "phased")])
+@pytest.mark.parametrize("precision,persistent", [("fp64", "auto"), ("fp32", "auto"), ("fp64", "phased"),
+                                                  ("fp32", "phased")])
 def test_shared_members_match_single_runs(precision, persistent):
-    """persistent "auto": the members' steps overlap on their streams; "always":
-    one cooperative launch per RK stage over all members; "cluster": each member's
-    stage as one thread-block cluster; "phased": one regular launch per phase of a
-    stage over all members."""
+    """persistent "auto": the members' steps overlap on their streams; "phased":
+    one regular launch per phase of a stage over all members."""
     import paper_1404_0405_gb300 as sww
     jmin, top = 2, max(j for j, _, _ in MEMBERS)
     base = sww.Model(jmin, top, patch=4)
@@ -75,7 +72,7 @@ def test_shared_members_match_single_runs(precision, persistent):
             assert bad.size == 0, f"member {i} {k}: {bad.size} differ, first {bad[:5]}, {x[bad[:3]]} vs {y[bad[:3]]}"
 
 
-@pytest.mark.parametrize("persistent", ["always", "phased"])
+@pytest.mark.parametrize("persistent", ["auto", "phased"])
 def test_batched_members_with_given_time_step(persistent):
     """A given time step (the same for every member) through the batched stages."""
     import paper_1404_0405_gb300 as sww
