@@ -19,8 +19,10 @@ its partial transform and grid adaptation.
 value = (live nodes over all levels and members, averaged over each step's start
 and end) x steps / seconds, with per-step CUDA-event times (the L2 cache is
 flushed between steps with a 512 MiB write outside the timed events).
-equal_error: relative l2 error of the Jmin depth after --err-steps steps of the
-same dt, plain and chosen, against a non-adaptive FP64 run (every point live).
+equal_error: relative l2 errors of the Jmin depth and velocity after one model
+day (--err-days) of the same dt, plain and chosen, against a non-adaptive FP64
+run (every point live).  learned_turbulence: the learned-mask configuration
+(turbulence, Jmax=10) timed with and without the proposal.
 
 --impl reference runs the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm).  With --gpus N under torchrun every
@@ -42,6 +44,9 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# the oracle's worker processes are single-threaded numpy (one per host core)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 # ensemble members run on their own streams: let them use separate hardware queues
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
@@ -66,12 +71,16 @@ def parse():
     p.add_argument("--members", type=int, default=64, help="ensemble members of the chosen form")
     p.add_argument("--plain-steps", type=int, default=10)
     p.add_argument("--train-steps", type=int, default=10)
-    p.add_argument("--err-steps", type=int, default=20)
+    p.add_argument("--err-steps", type=int, default=-1,
+                   help="steps of the equal-error runs (-1: --err-days model days; 0: skip)")
+    p.add_argument("--err-days", type=float, default=1.0)
+    p.add_argument("--turb-steps", type=int, default=5,
+                   help="timed steps of the turbulence configuration with and without the proposal (0: skip)")
     p.add_argument("--tau", type=float, default=0.9, help="proposal threshold on the perceptron probability")
     p.add_argument("--no-learned", action="store_true", help="chosen form without the learned proposal")
     p.add_argument("--no-tune", action="store_true", help="chosen form without the autotuner (patch, 4 blocks/SM)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-jmax", type=int, default=6, help="finest level of the oracle sample")
+    p.add_argument("--cpu-jmax", type=int, default=8, help="finest level of the oracle's hierarchy")
     return p.parse_args()
 
 
@@ -165,47 +174,111 @@ def host_cpu():
     return {"model": model, "logical_cores": os.cpu_count()}
 
 
-def oracle_rate(a, steps, warmup, seed):
-    """Active-cell steps/s of the FP64 CPU oracle on the same workload at
-    Jmin..cpu_jmax (grid setup untimed)."""
+def _oracle_worker(hy, a, jmax, k, go, res, barrier):
+    """One member of the benchmark's workload (seed + k) stepped by the oracle, in a
+    worker forked before any CUDA call: waits for (steps, warmup), then adapts,
+    takes the warm-up steps, meets the other workers, and times its steps."""
     import workloads
-    from oracle import grid, model
-    jmax = min(a.cpu_jmax, a.jmax)
-    Hy = grid.Hierarchy(a.jmin, jmax)
-    M = model.Model(Hy, eps=a.eps, rk="rk4", cfl=0.8)
-    L = Hy.levels[jmax]
-    dh, u = workloads.Workload("jet", seed=seed).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
-    M.set_uniform(dh, u)
-    M.adapt()
-    M.adapt()
-    for _ in range(warmup):
-        M.step(M.dt_cfl())
-    cells, t = 0, 0.0
-    for _ in range(steps):
-        act = M.active_nodes()
+    from oracle import model
+    steps, warmup = go.get()
+    try:
+        M = model.Model(hy, eps=a.eps, rk="rk4", cfl=0.8)
+        L = hy.levels[jmax]
+        dh, u = workloads.Workload("jet", seed=a.seed + k).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+        M.set_uniform(dh, u)
+        M.adapt()
+        M.adapt()
+        for _ in range(warmup):
+            M.step(M.dt_cfl())
+        barrier.wait()
+        cells, t0 = 0.0, time.perf_counter()
+        for _ in range(steps):
+            act = M.active_nodes()
+            M.step(M.dt_cfl())
+            cells += (act + M.active_nodes()) / 2
+        res.put((k, cells, time.perf_counter() - t0, steps))
+    except Exception as e:   # reported to the parent, which then leaves the figure out
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        res.put((k, None, repr(e), 0))
+
+
+class OraclePool:
+    """The FP64 CPU oracle on the host cores: the hierarchy of Jmin..jmax is built
+    once here and shared (copy on write) by one worker process per core, forked
+    before this process makes any CUDA call; worker k steps the member of seed
+    seed + k of the same workload.  run() times them together."""
+
+    def __init__(self, a, jmax, nproc):
+        import multiprocessing as mp
+        from oracle import grid
         t0 = time.perf_counter()
-        M.step(M.dt_cfl())
-        t += time.perf_counter() - t0
-        cells += (act + M.active_nodes()) / 2
-    sample = (f"same jet workload and eps at Jmin={a.jmin}..Jmax={jmax} ({steps} RK4 steps after {warmup} warm-up, "
-              f"grid setup untimed), single-threaded numpy oracle")
-    return cells / t, sample, t / steps
+        self.jmax, self.nproc = jmax, nproc
+        self.hy = grid.Hierarchy(a.jmin, jmax)
+        self.setup_s = time.perf_counter() - t0
+        ctx = mp.get_context("fork")
+        self.go, self.res = ctx.Queue(), ctx.Queue()
+        self.barrier = ctx.Barrier(nproc)
+        self.procs = [ctx.Process(target=_oracle_worker, args=(self.hy, a, jmax, k, self.go, self.res, self.barrier),
+                                  daemon=True) for k in range(nproc)]
+        for p in self.procs:
+            p.start()
+
+    def run(self, steps, warmup, timeout=1200):
+        """(rate over all workers, median single-worker rate, seconds of the slowest
+        worker, steps per worker) or None when a worker failed."""
+        for _ in self.procs:
+            self.go.put((steps, warmup))
+        out = [self.res.get(timeout=timeout) for _ in self.procs]
+        for p in self.procs:
+            p.join(timeout=60)
+        if any(o[1] is None for o in out):
+            return None
+        secs = max(o[2] for o in out)
+        return (sum(o[1] for o in out) / secs, statistics.median(o[1] / o[2] for o in out), secs, steps)
+
+    def sample(self, a, steps, warmup):
+        return (f"the benchmark's jet workload and eps with the finest level capped at Jmax={self.jmax} "
+                f"(Jmin={a.jmin}; the GPU run's cap is {a.jmax}), "
+                f"{self.nproc} members (seeds {a.seed}..{a.seed + self.nproc - 1}) in {self.nproc} forked "
+                f"single-threaded numpy oracle processes, one per host core, {steps} RK4 step(s) each after "
+                f"{warmup} warm-up step(s); grid setup and adaptation before the steps untimed")
+
+
+def oracle_cores():
+    """Host cores for the oracle workers."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return max(1, os.cpu_count() or 1)
 
 
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(a, rank):
+    """The oracle arm: the same metric and config on the host cores, a member per
+    core; the --steps K / --warmup W are spread over the workers (each takes
+    ceil(K / cores) timed and ceil(W / cores) warm-up steps)."""
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    steps = max(1, min(a.steps, 6))
-    warm = min(a.warmup, 2)
-    v, sample, per_step = oracle_rate(a, steps, warm, a.seed)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": steps,
-            "warmup": warm, "ms_per_step": 1e3 * per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(a)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                             "host": host_cpu()},
+    cores = oracle_cores()
+    pool = OraclePool(a, min(a.cpu_jmax, a.jmax), cores)
+    steps = max(1, math.ceil(a.steps / cores))
+    warm = math.ceil(a.warmup / cores)
+    r = pool.run(steps, warm)
+    if r is None:
+        print(json.dumps({"impl": "reference", "unavailable": "an oracle worker failed"}), flush=True)
+        return
+    v, single, secs, _ = r
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": steps * cores, "warmup": warm * cores, "ms_per_step": 1e3 * secs / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": pool.sample(a, steps, warm), "single_process": single,
+                             "host": host_cpu(), "setup_s": pool.setup_s},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,23 +302,33 @@ def combine_ranks(seconds, cells, device, world):
 # ----------------------------------------------------------------------------- our arm
 
 # Algorithmic bytes per live cell (one node, three edges, two triangles) of one
-# persistent RK stage at the minimum a fused stage must move: the state read
-# (dh, u: 32 B), the RK base read and the new state written (64 B), and the
-# geometry in its minimal form (cell and dual areas, 3 d_e, 3 l_e, kite fractions,
-# Coriolis at the dual cells: 17 words, 136 B) -- 232 B in FP64; the FP32 form
-# halves every term (its state and stencil weights are FP32).
-STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 116}
+# RK stage at the minimum a fused stage must move: the state read (dh, u: 32 B in
+# FP64, 16 B in FP32), the RK base read and the new state written (64 B; 32 B),
+# and the FP64 geometry in its minimal form (cell area, 3 d_e, 3 l_e, 6 kite
+# areas, 2 dual areas, Coriolis at the 2 dual cells: 17 words, 136 B, FP64 in
+# both forms) -- 232 B in FP64, 184 B in FP32.
+STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 184}
 
-# DRAM bytes (read + write) of the batched RK stage (the k_phase_batch launches of
-# one stage) per live member-cell, from one ncu capture of the same jet at
-# Jmin=4..Jmax=8 with 16 members (203.8 MB per stage over 302 856 member-cells,
-# cold cache per launch; profiles/k_phase_batch_jet_J4-8_16members.md), scaled to a
-# launch by the member-cells it processes; remove the entry when the kernel changes.
-PHASE_TRAFFIC_PER_CELL_STAGE = {"fp32": 673.0}
+# Algorithmic bytes per available cell (live or ghost node, with its three edges
+# and two triangles) of the structured trend kernel k_tile_trend: dh and u read
+# (4 words), the flags (4 B), the 17 FP64 geometry words (136 B), and F, q, div F,
+# B and q F^perp written (8 words) -- 12 words + 140 B: 188 B in FP32, 236 B in FP64.
+TREND_BYTES_PER_CELL = {"fp64": 236, "fp32": 188}
+
+# DRAM bytes (read + write) of k_tile_trend per available cell, from the ncu
+# capture of the same jet at Jmin=4..Jmax=8 with 16 members
+# (profiles/k_tile_trend_jet_J4-8_16members.md), scaled to a launch by the cells it
+# processes; remove the entry when the kernel changes.
+TREND_TRAFFIC_PER_CELL = {}
 
 
 def _live(m):
     return sum(m.stats()["live_nodes"].values())
+
+
+def _avail(m):
+    st = m.stats()
+    return sum(st["live_nodes"].values()) + sum(st["ghost_nodes"].values())
 
 
 _SAMPLINGS = {}
@@ -293,11 +376,12 @@ def _timed(sww, ms, steps, flush, stream):
     return times, cells
 
 
-def _equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, steps):
-    """Relative l2 error of the Jmin depth after `steps` steps of a fixed dt, for the
-    plain form (FP64, exact mask) and the chosen form (FP32, learned proposal),
-    against a non-adaptive FP64 run (eps = 0: every point live) substepped at its own
-    CFL limit to the same final time."""
+def _equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, steps, days):
+    """Relative l2 errors of the Jmin depth and velocity at the final time (after
+    `steps` steps of a fixed dt, or `days` model days when steps < 0), for the plain
+    form (FP64, exact mask) and the chosen form (FP32, learned proposal), against a
+    non-adaptive FP64 run (eps = 0: every point live) substepped at its own CFL
+    limit to the same final time."""
     import numpy as np
 
     def state(b):
@@ -323,23 +407,129 @@ def _equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, st
         return m
 
     plain, chosen, ref = make("fp64", a.eps), make("fp32", a.eps, learned), make("fp64", 0.0)
-    dt = plain.stats()["dt"] or 0.0
-    if dt <= 0:
-        plain.step(-1.0, 1, True)
-        dt = plain.stats()["dt"]
-        plain = make("fp64", a.eps)
+    plain.step(-1.0, 1, True)
+    dt = plain.stats()["dt"]
+    plain.close()
+    plain = make("fp64", a.eps)
+    if steps < 0:
+        steps = max(1, int(round(days * 86400.0 / dt)))
     ref.step(-1.0, 1, False)
     sub = max(1, math.ceil(dt / ref.stats()["dt"]))
+    ref.close()
     ref = make("fp64", 0.0)
+    t0 = time.perf_counter()
     for m in (plain, chosen):
         m.step(dt, steps, True)
     ref.step(dt / sub, steps * sub, False)
-    r = ref.get(a.jmin, sww.DH)
-    err = lambda m: float(np.linalg.norm(m.get(a.jmin, sww.DH) - r) / np.linalg.norm(r))
-    out = {"steps": steps, "dt_s": dt, "reference_substeps": sub, "plain_fp64": err(plain),
-           "chosen": err(chosen)}
-    out["ratio"] = out["chosen"] / max(out["plain_fp64"], 1e-300)
+    r_h, r_u = ref.get(a.jmin, sww.DH), ref.get(a.jmin, sww.U)
+
+    def err(m):
+        return {"dh": float(np.linalg.norm(m.get(a.jmin, sww.DH) - r_h) / np.linalg.norm(r_h)),
+                "u": float(np.linalg.norm(m.get(a.jmin, sww.U) - r_u) / np.linalg.norm(r_u))}
+
+    ep, ec = err(plain), err(chosen)
+    out = {"steps": steps, "dt_s": dt, "model_days": steps * dt / 86400.0, "reference_substeps": sub,
+           "level": a.jmin, "plain_fp64": ep, "chosen": ec, "ratio": ec["dh"] / max(ep["dh"], 1e-300),
+           "ratio_u": ec["u"] / max(ep["u"], 1e-300), "wall_s": time.perf_counter() - t0}
+    for m in (plain, chosen, ref):
+        m.close()
     return out
+
+
+def _turbulence(sww, workloads, a, steps, flush, peak, prec_bytes):
+    """The learned-mask configuration timed with and without the proposal:
+    decaying turbulence at Jmin=5..Jmax=10, eps=5e-3, FP32, one member given on
+    level 7 and stepped with one launch per phase; the proposal trained on
+    turbulence of two other seeds at Jmax=8.
+    From the same state (a checkpoint after 6 steps), `steps` steps each way:
+    active-cell steps/s, late refinements (misses), over-refinement, live cells,
+    and the structured trend kernel's roofline on this large grid."""
+    import tempfile
+
+    import numpy as np
+    import torch
+    from paper_1404_0405_gb300 import learn
+    jmin, jmax, jset, eps = 5, 10, 7, 5e-3
+    t_setup = time.perf_counter()
+
+    def member(b, seed, j1=jmax):
+        # one launch per phase (the structured trend is a launch of its own, timed)
+        m = sww.Model(jmin, j1, eps=eps, precision="fp32", share=b, persistent=False)
+        xyz, en = m.grid(jset)
+        mid, tan = edge_geometry(xyz, en)
+        m.set_state(*workloads.Workload("turbulence", seed=seed).fields(xyz, mid, tan), level=jset)
+        m.adapt()
+        return m
+
+    Xs, ys = [], []
+    tb = sww.Model(jmin, 8, eps=eps, precision="fp32")
+    for sd in (1, 2):
+        m = member(tb, sd, 8)
+        X, y = learn.collect(m, 8)
+        Xs.append(X), ys.append(y)
+        m.close()
+    params, _ = learn.train(np.concatenate(Xs), np.concatenate(ys), epochs=300)
+    base = sww.Model(jmin, jmax, eps=eps, precision="fp32")
+    m = member(base, 7)
+    m.step(-1.0, 6, True)
+    out = {"workload": "decaying rotating turbulence, Jmin=5..Jmax=10, eps=5e-3 relative, RK4, FP32, one member "
+                       "(fields given on level 7, 6 steps of spin-up); proposal trained on two other seeds at Jmax=8",
+           "setup_s": 0.0}
+    with tempfile.TemporaryDirectory() as d:
+        ck = os.path.join(d, "turb.ckpt")
+        m.save(ck)
+        stream = torch.cuda.current_stream()
+        out["setup_s"] = time.perf_counter() - t_setup
+        for name, mode in (("with_proposal", 2), ("without_proposal", 0)):
+            m.load(ck)
+            m.set_learned(mode, params if mode else None, 0.5)
+            m.learn_stats(reset=True)
+            times, cells = _timed_single(sww, m, steps, flush, stream)
+            st = m.stats()
+            ls = m.learn_stats(reset=True)
+            rec = {"value": sum(cells) / sum(times), "ms_per_step": 1e3 * sum(times) / steps,
+                   "live_cells_per_step": sum(cells) / steps, "misses": ls["misses"], "over": ls["over"],
+                   "proposed": ls["proposed"], "top_level": max(j for j, n in st["live_nodes"].items() if n > 0)}
+            out[name] = rec
+        # roofline of the structured trend on this grid (the run without the proposal)
+        m.load(ck)
+        m.set_learned(0)
+        m.profile(["trend"])
+        tb_bytes = 0.0
+        for _ in range(steps):
+            tb_bytes += prec_bytes * _avail(m) * 4
+            flush.zero_()
+            m.step(-1.0, 1, True)
+        t_ms, t_n = m.profile_read()["trend"]
+        m.profile([])
+        if t_n > 0:
+            ach = tb_bytes / (t_ms / 1e3) / 1e9
+            out["roofline_trend"] = {"kernel": "k_tile_trend", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                     "frac": ach / peak, "avg_launch_us": t_ms * 1e3 / t_n, "launches": t_n,
+                                     "algorithmic_bytes_per_launch": tb_bytes / t_n,
+                                     "available_cells_per_launch": tb_bytes / prec_bytes / t_n}
+    m.close()
+    base.close()
+    tb.close()
+    return out
+
+
+def _timed_single(sww, m, steps, flush, stream):
+    """CUDA-event time of each step of one member (L2 flushed before each) and the
+    live cells advanced."""
+    import torch
+    times, cells = [], []
+    for _ in range(steps):
+        c0 = _live(m)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        m.step(-1.0, 1, True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        cells.append(0.5 * (c0 + _live(m)))
+    return times, cells
 
 
 def run_ours(a, rank, world):
@@ -432,17 +622,22 @@ def run_ours(a, rank, world):
             m.set_learned(0)
         for _ in range(a.warmup):
             sww.step_ensemble(ms, -1.0, 1, True)
+        for m in ms:
+            m.learn_stats(reset=True)
         t2, c2 = _timed(sww, ms, a.steps, flush, stream)
         t2, c2 = combine_ranks(sum(t2), sum(c2), "cuda", world)
+        plain_misses = sum(m.learn_stats(reset=True)["misses"] for m in ms)
         lstats["without_proposal"] = {"value": c2 / t2, "ms_per_step": 1e3 * t2 / a.steps,
-                                      "active_cells_per_step": c2 / a.steps / max(world, 1) / len(ms)}
+                                      "active_cells_per_step": c2 / a.steps / max(world, 1) / len(ms),
+                                      "misses": plain_misses}
         for m in ms:
             m.set_learned(2, learned, a.tau)
 
-    # live timing of the dominant kernel of the timed steps: the batched RK stage
-    # (k_phase_batch, one launch per phase over all members), from CUDA events the
-    # library records on the first member's stream around each RK stage, over the
-    # same number of ensemble steps (L2 flushed before each)
+    # live timing of the dominant kernel of the timed steps, the structured trend
+    # k_tile_trend (one launch per RK stage over all members), and of the whole
+    # batched stage, from CUDA events the library records on the first member's
+    # stream around each launch group, over the same number of ensemble steps (L2
+    # flushed before each)
     prec = "fp32" if dtype == "f32" else "fp64"
     peaks = {}
     try:
@@ -450,29 +645,49 @@ def run_ours(a, rank, world):
         peak, peak_src = peaks["hbm_gbs"], "measured"
     except (OSError, KeyError, ValueError):
         peak, peak_src = 6800.0, "fallback"
-    roofline = None
+    roofline = roofline_stage = None
     if a.form == "chosen":
         m0 = ms[0]
-        m0.profile(["stage"])
-        sbytes = 0.0
+        classes = ["trend", "irregular", "fill", "restrict", "update", "stage", "dt", "partial", "coeff", "mask",
+                   "inverse"]
+        m0.profile(classes)
+        tbytes = sbytes = 0.0
         for _ in range(a.steps):
-            c = sum(_live(m) for m in ms)
-            sbytes += STAGE_BYTES_PER_CELL[prec] * c * 4
+            tbytes += TREND_BYTES_PER_CELL[prec] * sum(_avail(m) for m in ms) * 4
+            sbytes += STAGE_BYTES_PER_CELL[prec] * sum(_live(m) for m in ms) * 4
             flush.zero_()
             sww.step_ensemble(ms, -1.0, 1, True)
-        s_ms, s_n = m0.profile_read()["stage"]
+        prof = m0.profile_read()
         m0.profile([])
-        if s_n > 0:
-            achieved = sbytes / (s_ms / 1e3) / 1e9
-            roofline = {"bound": "hbm", "kernel": "k_phase_batch (RK stage phases, all members)",
+        t_ms, t_n = prof["trend"]
+        s_ms, s_n = prof["stage"]
+        if t_n > 0:
+            achieved = tbytes / (t_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "kernel": "k_tile_trend (structured trend of every active patch, all members)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                         "peak_source": f"{peak_src} (burst copy)",
-                        "traffic": (PHASE_TRAFFIC_PER_CELL_STAGE[prec] * sbytes / STAGE_BYTES_PER_CELL[prec] / s_n
-                                    if prec in PHASE_TRAFFIC_PER_CELL_STAGE else None),
-                        "avg_launch_us": s_ms * 1e3 / s_n,
-                        "launches": s_n, "algorithmic_bytes_per_launch": sbytes / s_n,
-                        "bytes_per_live_cell_per_stage": STAGE_BYTES_PER_CELL[prec],
-                        "stage_share_of_step": (s_ms / 1e3) / max(sum(times), 1e-30)}
+                        "traffic": (TREND_TRAFFIC_PER_CELL[prec] * tbytes / TREND_BYTES_PER_CELL[prec] / t_n
+                                    if prec in TREND_TRAFFIC_PER_CELL else None),
+                        "avg_launch_us": t_ms * 1e3 / t_n, "launches": t_n,
+                        "algorithmic_bytes_per_launch": tbytes / t_n,
+                        "available_cells_per_launch": tbytes / TREND_BYTES_PER_CELL[prec] / t_n,
+                        "bytes_per_available_cell": TREND_BYTES_PER_CELL[prec],
+                        "share_of_step": (t_ms / 1e3) / max(sum(times), 1e-30)}
+        if s_n > 0:
+            nst = 4 * a.steps
+            ach = sbytes / (s_ms / 1e3) / 1e9
+            roofline_stage = {"kernels": "every launch of the RK stages (ghosts, trend, irregular patches, "
+                                         "restrictions, update)",
+                              "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                              "stage_us": s_ms * 1e3 / nst, "launches_per_stage": s_n / nst,
+                              "bytes_per_live_cell_per_stage": STAGE_BYTES_PER_CELL[prec],
+                              "share_of_step": (s_ms / 1e3) / max(sum(times), 1e-30),
+                              "part_us_per_stage": {k: prof[k][0] * 1e3 / nst for k in
+                                                    ("fill", "trend", "irregular", "restrict", "update")},
+                              "step_us": {k: prof[k][0] * 1e3 / a.steps for k in
+                                          ("dt", "stage", "partial", "coeff", "mask", "inverse")},
+                              "step_launches": {k: prof[k][1] / a.steps for k in
+                                                ("dt", "stage", "partial", "coeff", "mask", "inverse")}}
     # the persistent RK stage of the plain form's single member (fused trend + update)
     pm = plain_m[0]
     pm.profile(["stage"])
@@ -491,8 +706,10 @@ def run_ours(a, rank, world):
                       "bytes_per_live_cell": STAGE_BYTES_PER_CELL["fp64"]}
 
     # equal error: chosen vs plain against a non-adaptive run of the same workload
-    err = (_equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, a.err_steps)
-           if a.err_steps > 0 else None)
+    err = (_equal_error(sww, workloads, base, cbase, cpatch, cbps, a, learned, seed, a.err_steps, a.err_days)
+           if a.err_steps != 0 else None)
+    turb = (_turbulence(sww, workloads, a, a.turb_steps, flush, peak, TREND_BYTES_PER_CELL["fp32"])
+            if a.turb_steps > 0 and a.form == "chosen" else None)
 
     # end to end through the public API from pinned host buffers
     S = _sampling(workloads, cbase, a.jmax)
@@ -529,8 +746,9 @@ def run_ours(a, rank, world):
                            "compression": (10 * 4 ** a.jmax + 2) / (cells_all / a.steps / max(world, 1) / len(ms)),
                            "setup_s": setup_s},
                 "plain": plain, "chosen_vs_plain": value / plain["value"], "equal_error": err,
-                "learned_proposal": lstats, "clocks": clk, "e2e": e2e, "gpu_launches": int(launches),
-                "roofline": roofline, "roofline_persistent_stage": stage_roof}
+                "learned_proposal": lstats, "learned_turbulence": turb, "clocks": clk, "e2e": e2e,
+                "gpu_launches": int(launches),
+                "roofline": roofline, "roofline_stage": roofline_stage, "roofline_persistent_stage": stage_roof}
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -544,12 +762,19 @@ def main():
     if a.impl == "reference":
         run_reference(a, rank)
         return
+    # the oracle's workers are forked before any CUDA call, and run after the GPU part
+    pool = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        pool = OraclePool(a, min(a.cpu_jmax, a.jmax), oracle_cores())
     line = run_ours(a, rank, world)
     if rank == 0:
-        if world == 1 and not a.no_cpu_baseline:
-            v, sample, _ = oracle_rate(a, 2, 1, a.seed)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-                                    "host": host_cpu()}
+        if pool is not None:
+            r = pool.run(1, 1)
+            if r is not None:
+                v, single, secs, steps = r
+                line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
+                                        "sample": pool.sample(a, 1, 1), "single_process": single,
+                                        "host": host_cpu(), "setup_s": pool.setup_s}
         print(json.dumps(line), flush=True)
 
 

@@ -54,11 +54,9 @@ __global__ void k_set(double* p, double v) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
 }
 
+// reduction words of the time step (see RED_WORDS): the maxima start at zero
 __global__ void k_reset_red(unsigned long long* red) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        red[0] = 0ull;
-        red[1] = ~0ull;
-    }
+    if (blockIdx.x == 0 && threadIdx.x < RED_WORDS) red[threadIdx.x] = 0ull;
 }
 
 template <class R>
@@ -114,8 +112,8 @@ struct Geometry {
             const DevLevel& D = lv[j];
             DevLevelT<float>& F = out[j];
             F.J = D.J, F.n = D.n, F.p = D.p, F.np = D.np, F.nelem = D.nelem, F.N = D.N, F.E = D.E, F.T = D.T;
-            F.npatch = D.npatch, F.dx = D.dx;
-            F.en = D.en, F.et = D.et, F.tn = D.tn, F.te = D.te, F.deg = D.deg, F.ring_e = D.ring_e, F.f2c = D.f2c;
+            F.npatch = D.npatch, F.dx = D.dx, F.kx2 = D.kx2;
+            F.en = D.en, F.et = D.et, F.tn = D.tn, F.te = D.te, F.deg = D.deg, F.ring_e = D.ring_e, F.ring_n = D.ring_n, F.f2c = D.f2c;
             F.cor_i = D.cor_i, F.par = D.par, F.fe_kind = D.fe_kind, F.fe_ce = D.fe_ce, F.vst = D.vst;
             F.c2f = D.c2f, F.mid = D.mid, F.half = D.half, F.mk_i = D.mk_i, F.rf_fi = D.rf_fi, F.rf_ci = D.rf_ci;
             F.ppar = D.ppar, F.pnbr = D.pnbr, F.pchild = D.pchild;
@@ -287,12 +285,14 @@ void upload_geometry(Geometry& G, HostLevel& L, bool fine_side, bool coarse_side
     DevLevel D{};
     D.J = L.J, D.n = L.n, D.p = L.p, D.np = L.np, D.nelem = L.nelem, D.N = L.N, D.E = L.E, D.T = L.T, D.npatch = L.npatch;
     D.dx = nominal_spacing(L.J, G.radius);
+    D.kx2 = (M_PI / D.dx) * (M_PI / D.dx);
     D.en = G.up_slots(L.en, 2);
     D.et = G.up_slots(L.et, 2);
     D.tn = G.up_slots(L.tn, 3);
     D.te = G.up_slots(L.te, 3);
     D.deg = G.up(L.deg);
     D.ring_e = G.up_slots(L.ring_e, 6);
+    D.ring_n = G.up_slots(L.ring_n, 6);
     D.A_i = G.up(L.A_i), D.A_v = G.up(L.A_v), D.kite = G.up_slots(L.kite, 3);
     D.d_e = G.up(L.d_e), D.l_e = G.up(L.l_e), D.f_v = G.up(L.f_v), D.f_n = G.up(L.f_n);
     D.cor_i = G.up_slots(L.cor_i, COR);
@@ -447,6 +447,9 @@ void alloc_state(sww_handle* h, int j) {
     ck(cudaMemset(D.pfeat, 0, NF * (D.npatch + 1) * sizeof(float)), "memset");
     D.patches = h->alloc<int32_t>(D.npatch + 1);
     D.npatches = h->alloc<int32_t>(1);
+    D.wl = h->alloc<int32_t>(3 * N + 2 * E);
+    D.wl_n = h->alloc<int32_t>(WL_KINDS);
+    ck(cudaMemset(D.wl_n, 0, WL_KINDS * sizeof(int32_t)), "memset");
     uint8_t** cf[] = {&D.zflag, &D.sflag, &D.cflag, &D.lflag, &D.gflag};
     for (auto p : cf) {
         *p = h->alloc<uint8_t>(D.npatch + 1);
@@ -612,7 +615,7 @@ void compute_dt(sww_handle* h) {
     count_launch(1);
     k_reset_red<<<1, 32, 0, h->stream>>>(h->red);
     launch_dt(work_all<R>(h), h->cfg.H, h->cfg.g, h->red, h->stream);
-    launch_dt_final(h->red, h->cfg.cfl, h->dt, h->stream);
+    launch_dt_final<R>(dlv<R>(h), h->red, h->cfg.cfl, h->dt, h->stream);
 }
 
 // list sizes of every level into pinned host memory (read after the next sync)
@@ -738,7 +741,7 @@ void mask_only(sww_handle* h) {
     else
         launch_mask(mask_args<R>(h, j0, j1), s);
     launch_proposal_batch(b, h->grid_all, 1, s);
-    launch_concat_batch(b, s);
+    launch_concat_batch(b, h->grid_all, s);
 }
 
 template <class R>
@@ -764,7 +767,7 @@ void adapt(sww_handle* h, double eh, double eu) {
     { Trace t(h, SWW_K_COEFF); launch_details(work_all<R>(h), h->cfg.jmin, s); }
     {
         Trace t(h, SWW_K_MASK);
-        ck(cudaMemsetAsync(h->red, 0, 2 * sizeof(unsigned long long), s), "memset red");
+        ck(cudaMemsetAsync(h->red + 2, 0, 2 * sizeof(unsigned long long), s), "memset red");
         launch_maxabs(work_all<R>(h), h->red, s);
         launch_thresholds(h->red, eps_coeff(h->cfg), eh, eu, h->cfg.advect, h->thr, s);
     }
@@ -996,7 +999,7 @@ void ensemble_phased(sww_handle* const* hs, int n, double dt, bool do_adapt) {
             launch_proposal_batch(*b, grid, 0, s);
             launch_mask_batch(*b, grid, s);
             launch_proposal_batch(*b, grid, 1, s);
-            launch_concat_batch(*b, s);
+            launch_concat_batch(*b, grid, s);
         } else {
             // each member's mask on its own stream, then back to the lead's
             ck(cudaEventRecord(E.ev, s), "ensemble fork");
@@ -1119,7 +1122,8 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         ck(cudaMallocHost(&h->h_dt, sizeof(double)), "cudaMallocHost");
         std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
         *h->h_dt = 0;
-        h->red = h->alloc<unsigned long long>(4);
+        h->red = h->alloc<unsigned long long>(RED_WORDS);
+        ck(cudaMemset(h->red, 0, RED_WORDS * sizeof(unsigned long long)), "memset");
         h->d_net = h->alloc<MlpWeights>(1);
         ck(cudaMemset(h->d_net, 0, sizeof(MlpWeights)), "memset");
         h->lstat = h->alloc<unsigned long long>(4);
@@ -1256,7 +1260,7 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
             if (J > j0) launch_covered_all(dlv<R>(h), a.nodes_c, s);
             MaskArgsT<R> b = mask_args<R>(h, j0, j1, false);
             launch_patches_all(dlv<R>(h), b.patches, s);
-            launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, s);
+            launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, h->S, h->grid_all, s);
             read_counts<R>(h);
             check_launch();
             return 0;
@@ -1778,7 +1782,7 @@ int sww_load(sww_handle* h, const char* path) {
                 ck(cudaMemcpyAsync(h->thr, thr, sizeof(thr), cudaMemcpyHostToDevice, s), "load thr");
                 MaskArgsT<R> a = mask_args<R>(h, j0, j1, false);
                 launch_patches_all(dlv<R>(h), a.patches, s);
-                launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, s);
+                launch_concat(dlv<R>(h), j0, j1, h->all_list, h->all_count, h->irr_list, h->irr_count, h->S, h->grid_all, s);
                 read_counts<R>(h);
                 check_launch();
                 ck(cudaStreamSynchronize(s), "load");   // host buffers live on this frame

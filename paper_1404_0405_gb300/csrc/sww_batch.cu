@@ -71,6 +71,21 @@ __device__ __forceinline__ void member_items(const DevLevelT<R>* sl, const int32
     }
 }
 
+// items of work lists k0 and k1 (k1 < 0: none) of level L, block b of the
+// member's bpm blocks: body(0, id) for list k0, body(1, id) for list k1
+template <class R, class Body>
+__device__ __forceinline__ void member_wl(const DevLevelT<R>& L, int k0, int k1, int b, int bpm, Body body) {
+    const int n0 = L.wl_n[k0], n1 = k1 >= 0 ? L.wl_n[k1] : 0;
+    const int32_t* __restrict__ l0 = L.wl + wl_off(L, k0);
+    const int32_t* __restrict__ l1 = k1 >= 0 ? L.wl + wl_off(L, k1) : l0;
+    for (int i = b * int(blockDim.x) + int(threadIdx.x); i < n0 + n1; i += bpm * int(blockDim.x)) {
+        if (i < n0)
+            body(0, int64_t(l0[i]));
+        else
+            body(1, int64_t(l1[i - n0]));
+    }
+}
+
 // Eight blocks per SM (32 registers, a few spilled): the phases are chains of
 // dependent gathers, and more resident warps hide more of their latency (measured
 // 15 % faster than the 44-register build at 62 % occupancy).
@@ -83,9 +98,7 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
     // one block per member
     if (phase == PH_DT_FINAL) {
         if (threadIdx.x == 0) {
-            const double w = __longlong_as_double(static_cast<long long>(mr->red[0]));
-            const double r = mr->red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(mr->red[1]));
-            *mr->dt = mr->cfl * fmin(1.0 / w, r);
+            *mr->dt = cfl_step<R>(mr->lvs, mr->red, mr->cfl);
         }
         return;
     }
@@ -126,35 +139,33 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
     const R H = R(a.H), g = R(a.g);
     switch (phase) {
         case PH_FILL:
-            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
-                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                              if (kind == K_NODE)
-                                                  fill_node(L, (&L)[-1], id);
-                                              else
-                                                  fill_edge(L, (&L)[-1], id);
-                                          });
+        case PH_INV_FILL:
+            // ghost nodes and edges of level j from level j - 1
+            member_wl(sl[j], WL_GN, WL_GE, b, bpm, [&](int k, int64_t id) {
+                if (k == 0)
+                    fill_node(sl[j], sl[j - 1], id);
+                else
+                    fill_edge(sl[j], sl[j - 1], id);
+            });
             break;
         case PH_RESTRICT:
-            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
-                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                              restrict_item(L, (&L)[1], kind, id);
-                                          });
+            // covered nodes and the edges with a covered end of level j
+            member_wl(sl[j], WL_CN, WL_RE, b, bpm,
+                      [&](int k, int64_t id) { restrict_item(sl[j], sl[j + 1], k == 0 ? K_NODE : K_EDGE, id); });
             break;
         case PH_DIV:
-            member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
-                                 [&](const DevLevelT<R>& L, int, int64_t id, int64_t) { div_at(L, id); });
+            member_wl(sl[j], WL_DN, -1, b, bpm, [&](int, int64_t id) { div_at(sl[j], id); });
             break;
         case PH_SAVE:
             // the RK base, and the time step: given (a.dt > 0) or its reduction words reset
             if (b == 0 && threadIdx.x == 0) {
                 if (a.dt_given > 0) {
                     *mr->dt = a.dt_given;
+                    mr->red[2] = 0ull;
+                    mr->red[3] = 0ull;
                 } else {
-                    mr->red[0] = 0ull;
-                    mr->red[1] = ~0ull;
+                    for (int w = 0; w < RED_WORDS; ++w) mr->red[w] = 0ull;
                 }
-                mr->red[2] = 0ull;
-                mr->red[3] = 0ull;
             }
             member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
                                           [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
@@ -166,28 +177,30 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
                                           });
             break;
         case PH_DT: {
-            // omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max; none with a prescribed
-            // velocity), dx/|u| at live edges (min), as bit patterns of non-negative doubles
+            // largest omega^2 over live nodes (none with a prescribed velocity) and,
+            // per level, largest |u| over live edges with u != 0 (NaN left out); the
+            // step in PH_DT_FINAL (as k_dt and k_dt_final)
             __shared__ unsigned long long sh[BATCH_TPB / 32];
-            unsigned long long wmax = 0, rmin = ~0ull;
+            __shared__ unsigned long long slev[RED_WORDS - RED_LEVEL];
+            if (threadIdx.x < RED_WORDS - RED_LEVEL) slev[threadIdx.x] = 0ull;
+            __syncthreads();
+            unsigned long long wmax = 0;
+            LevelMax um;
             member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
                                           [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
                                               if (kind == K_NODE) {
                                                   if (L.advect || !(L.nflag[id] & LIVE)) return;
-                                                  const double f = double(L.f_n[id]), kx = M_PI / L.dx;
-                                                  const double w = sqrt(f * f + a.g * (a.H + double(L.dh[id])) * kx * kx);
-                                                  wmax = max(wmax, dbits(w));
+                                                  wmax = max(wmax, dbits(omega2_at(L, id, a.H, a.g)));
                                               } else if (L.eflag[id] & LIVE) {
-                                                  const double au = fabs(double(L.u[id]));
-                                                  if (au > 0) rmin = min(rmin, dbits(L.dx / au));
+                                                  const unsigned long long k = abs_key(L.u[id]);
+                                                  if (k && k <= inf_key<R>()) um.add(L.J, k, slev);
                                               }
                                           });
-            wmax = block_reduce_u64(wmax, MaxU64(), sh);
-            rmin = block_reduce_u64(rmin, MinU64(), sh);
-            if (threadIdx.x == 0) {
-                if (wmax) atomicMax(&mr->red[0], wmax);
-                if (rmin != ~0ull) atomicMin(&mr->red[1], rmin);
-            }
+            um.flush(slev);
+            wmax = block_reduce_u64(wmax, MaxU64(), sh);   // synchronises the block: slev is complete
+            if (threadIdx.x == 0 && wmax) atomicMax(&mr->red[0], wmax);
+            if (threadIdx.x < RED_WORDS - RED_LEVEL && slev[threadIdx.x])
+                atomicMax(&mr->red[RED_LEVEL + threadIdx.x], slev[threadIdx.x]);
             break;
         }
         case PH_DETAILS:
@@ -197,22 +210,23 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
                                                     });
             break;
         case PH_MAXABS: {
-            // max |dh| over live nodes, max |u| over live edges (bit patterns)
+            // max |dh| over live nodes, max |u| over live edges (keys of the field
+            // type, widened to FP64 once per block, as k_maxabs)
             __shared__ unsigned long long shm[BATCH_TPB / 32];
             unsigned long long hmax = 0, umax = 0;
             member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
                                           [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
                                               if (kind == K_NODE) {
-                                                  if (L.nflag[id] & LIVE) hmax = max(hmax, dbits(fabs(double(L.dh[id]))));
+                                                  if (L.nflag[id] & LIVE) hmax = max(hmax, abs_key(L.dh[id]));
                                               } else if (L.eflag[id] & LIVE) {
-                                                  umax = max(umax, dbits(fabs(double(L.u[id]))));
+                                                  umax = max(umax, abs_key(L.u[id]));
                                               }
                                           });
             hmax = block_reduce_u64(hmax, MaxU64(), shm);
             umax = block_reduce_u64(umax, MaxU64(), shm);
             if (threadIdx.x == 0) {
-                if (hmax) atomicMax(&mr->red[2], hmax);
-                if (umax) atomicMax(&mr->red[3], umax);
+                if (hmax) atomicMax(&mr->red[2], dbits(key_value<R>(hmax)));
+                if (umax) atomicMax(&mr->red[3], dbits(key_value<R>(umax)));
             }
             break;
         }
@@ -226,19 +240,10 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
             member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
                                  [&](const DevLevelT<R>& L, int, int64_t id, int64_t) { inverse_b_item(L, id); });
             break;
-        case PH_INV_FILL:
-            member_items<K_NODE | K_EDGE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
-                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                              if (kind == K_NODE)
-                                                  fill_node(L, (&L)[-1], id);
-                                              else
-                                                  fill_edge(L, (&L)[-1], id);
-                                          });
-            break;
         case PH_PARTIAL:
             // R_h at covered nodes of level j from level j + 1 (Eq. Rh)
-            member_items<K_NODE>(sl, sl[j].patches, *sl[j].npatches, a.P, b, bpm,
-                                 [&](const DevLevelT<R>& L, int, int64_t id, int64_t) {
+            member_wl(sl[j], WL_CN, -1, b, bpm, [&](int, int64_t id) {
+                                     const DevLevelT<R>& L = sl[j];
                                      if (!(L.nflag[id] & COVERED)) return;
                                      const DevLevelT<R>& F = (&L)[1];
                                      R v = F.dh[L.c2f[id]];

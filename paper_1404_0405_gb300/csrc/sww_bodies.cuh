@@ -19,11 +19,6 @@ __device__ __forceinline__ float to_r<float>(double x) { return f64_to_f32_rn(x)
 template <class R>
 __device__ __forceinline__ R geo(const double* __restrict__ p, int64_t i) { return to_r<R>(p[i]); }
 
-template <class Lv>
-__device__ __forceinline__ int32_t ring_nbr(const Lv& L, int32_t code) {
-    int64_t e = code >> 1;
-    return (code & 1) ? L.en[e] : L.en[L.E + e];
-}
 
 template <class R>
 __device__ __forceinline__ R predict(const DevLevelT<R>& F, const R* __restrict__ uc, int64_t fe) {
@@ -43,6 +38,65 @@ __device__ __forceinline__ R height_detail(const DevLevelT<R>& F, int64_t x) {
 
 __device__ __forceinline__ unsigned long long dbits(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
+// ---------------------------------------------------------------------------- CFL step and field maxima
+
+// |x| as an unsigned key ordered like |x|: with the sign bit cleared, IEEE numbers
+// order like their bit patterns, and NaN keys lie above the key of +infinity
+__device__ __forceinline__ unsigned long long abs_key(float x) { return __float_as_uint(x) & 0x7fffffffu; }
+__device__ __forceinline__ unsigned long long abs_key(double x) { return dbits(x) & 0x7fffffffffffffffull; }
+template <class R>
+__device__ __forceinline__ unsigned long long inf_key() {
+    return sizeof(R) == 4 ? 0x7f800000ull : 0x7ff0000000000000ull;
+}
+// the magnitude a key stands for, as a double (exact: widening keeps the value)
+template <class R>
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return sizeof(R) == 4 ? double(__uint_as_float(unsigned(k))) : __longlong_as_double(static_cast<long long>(k));
+}
+
+// squared CFL frequency f^2 + g h (pi/dx)^2 at node id, in FP64 with the products
+// and sums rounded in the written order (no contraction).  The time step takes the
+// square root of the maximum only: a correctly rounded square root is monotone, so
+// that equals the maximum of the roots.
+template <class R>
+__device__ __forceinline__ double omega2_at(const DevLevelT<R>& L, int64_t id, double H, double g) {
+    const double f = L.f_n[id];
+    return __dadd_rn(__dmul_rn(f, f), __dmul_rn(__dmul_rn(g, __dadd_rn(H, double(L.dh[id]))), L.kx2));
+}
+
+// Running maximum of a key per level over one thread's items, flushed into the
+// block's per-level words (shared memory) when the level changes: a thread meets
+// its items in list order, which is level order, so it flushes a few times.
+struct LevelMax {
+    int j = -1;
+    unsigned long long k = 0;
+    __device__ __forceinline__ void flush(unsigned long long* sm) {
+        if (k) atomicMax(sm + j, k);
+    }
+    __device__ __forceinline__ void add(int jj, unsigned long long key, unsigned long long* sm) {
+        if (jj != j) {
+            flush(sm);
+            j = jj;
+            k = 0;
+        }
+        k = key > k ? key : k;
+    }
+};
+
+// Advective bound min over live edges of dx_j / |u| (Sec. 3.1's CFL condition):
+// for one level, a correctly rounded dx_j / a falls as a grows, so the minimum is
+// dx_j over the level's largest |u|; then the step cfl * min(1/omega, that bound).
+template <class R>
+__device__ __forceinline__ double cfl_step(const DevLevelT<R>* lvs, const unsigned long long* red, double cfl) {
+    const double w = sqrt(__longlong_as_double(static_cast<long long>(red[0])));
+    double r = INFINITY;
+    for (int j = 0; j < RED_WORDS - RED_LEVEL; ++j) {
+        const unsigned long long k = red[RED_LEVEL + j];
+        if (k) r = fmin(r, lvs[j].dx / key_value<R>(k));
+    }
+    return cfl * fmin(1.0 / w, r);
 }
 
 // Item kinds of a work-list entry, in slot order.
@@ -159,6 +213,18 @@ __device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
         div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * geo<R>(L.l_e, e);
     }
     L.c[v] = div / geo<R>(L.A_i, v);
+}
+
+// a node whose divergence the restricted fluxes change: available, with a covered
+// node among itself and its neighbours (an edge is restricted when an end is
+// covered).  The work list WL_DN holds exactly these nodes.
+template <class R>
+__device__ __forceinline__ bool restricted_div_node(const DevLevelT<R>& L, int64_t v) {
+    const uint8_t f = L.nflag[v];
+    if (!(f & AVAIL)) return false;
+    bool d = (f & COVERED) != 0;
+    for (int k = 0; k < L.deg[v] && !d; ++k) d = (L.nflag[L.ring_n[k * L.N + v]] & COVERED) != 0;
+    return d;
 }
 
 // divergence, kinetic energy and Bernoulli function at a node
@@ -432,12 +498,12 @@ template <class R>
 __device__ __forceinline__ void adjacent_node(const DevLevelT<R>& F, const DevLevelT<R>& C, bool children, int64_t x) {
     const int dg = F.deg[x];
     uint8_t t = F.sig[x];
-    for (int k = 0; k < dg && !t; ++k) t = F.sig[ring_nbr(F, F.ring_e[k * F.N + x])];
+    for (int k = 0; k < dg && !t; ++k) t = F.sig[F.ring_n[k * F.N + x]];
     if (!t && children) {
         const int32_t cx = F.f2c[x];
         if (cx >= 0 && C.sig[cx]) t = 1;
         for (int k = 0; k < dg && !t; ++k) {
-            const int32_t y = ring_nbr(F, F.ring_e[k * F.N + x]);
+            const int32_t y = F.ring_n[k * F.N + x];
             const int32_t cy = F.f2c[y];
             if (cy >= 0 && C.sig[cy]) t = 1;
         }
@@ -488,7 +554,7 @@ __device__ __forceinline__ void dilate_node(const DevLevelT<R>& L, int64_t x, bo
     uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
     uint8_t t = in[x];
     const int dg = L.deg[x];
-    for (int k = 0; k < dg && !t; ++k) t = in[ring_nbr(L, L.ring_e[k * L.N + x])];
+    for (int k = 0; k < dg && !t; ++k) t = in[L.ring_n[k * L.N + x]];
     out[x] = t;
 }
 
@@ -515,38 +581,73 @@ __device__ __forceinline__ void covered_node(const DevLevelT<R>& C, const DevLev
 
 // ---------------------------------------------------------------------------- patch lists (Sec. 5.2)
 
+// The indices of the nonzero bytes of flag[0..n) into out (tag | index), in
+// ascending order, by one block: each thread takes 32 consecutive flags per pass
+// (two 16-byte loads), the block forms an exclusive prefix of the counts, and each
+// thread writes its entries.  flag must be 16-byte aligned.  Returns the count (in
+// every thread).
+__device__ int compact_flags(const uint8_t* __restrict__ flag, int64_t n, int32_t tag, int32_t* __restrict__ out) {
+    __shared__ int wsum[32];
+    __shared__ int total;
+    if (threadIdx.x == 0) total = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t start = 0; start < n; start += 32 * int64_t(blockDim.x)) {
+        const int64_t i0 = start + 32 * int64_t(threadIdx.x);
+        unsigned bits = 0u;
+        if (i0 + 32 <= n) {
+            const uint4 a = *reinterpret_cast<const uint4*>(flag + i0);
+            const uint4 b = *reinterpret_cast<const uint4*>(flag + i0 + 16);
+            const unsigned words[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) bits |= (((words[q] >> (8 * k)) & 0xffu) ? 1u : 0u) << (4 * q + k);
+        } else {
+            for (int k = 0; k < 32 && i0 + k < n; ++k) bits |= (flag[i0 + k] ? 1u : 0u) << k;
+        }
+        const int cnt = __popc(bits);
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        if (w == 0) {
+            int v = lane < nw ? wsum[lane] : 0, iv = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, iv, o);
+                if (lane >= o) iv += t;
+            }
+            if (lane < nw) wsum[lane] = iv - v;   // exclusive prefix over warps
+        }
+        __syncthreads();
+        int pos = total + wsum[w] + incl - cnt;
+        while (bits) {
+            const int k = __ffs(bits) - 1;
+            out[pos++] = tag | int32_t(i0 + k);
+            bits &= bits - 1u;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) total += wsum[w] + incl;
+        __syncthreads();
+    }
+    return total;
+}
+
 // The ascending list of level L's flagged patches (+ the pole entry when a pole is
 // live or ghost), one block of any width (ballot and a warp-total prefix).
 template <class R>
 __device__ void patch_scan_level(const DevLevelT<R>& L) {
-    __shared__ int warp_tot[32];
-    __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int32_t tag = int32_t(L.J) << LVL_SHIFT;
-    for (int64_t start = 0; start < L.npatch; start += blockDim.x) {
-        int64_t i = start + threadIdx.x;
-        int f = (i < L.npatch) ? L.pflag[i] : 0;
-        unsigned bal = __ballot_sync(0xffffffffu, f);
-        int pre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warp_tot[w] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int k = 0; k < w; ++k) off += warp_tot[k];
-        if (f) L.patches[base + off + pre] = tag | int32_t(i);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int k = 0; k < nw; ++k) tot += warp_tot[k];
-            base += tot;
-        }
-        __syncthreads();
-    }
+    const int32_t tag = int32_t(L.J) << LVL_SHIFT;
+    const int n = compact_flags(L.pflag, L.npatch, tag, L.patches);
     if (threadIdx.x == 0) {
-        int n = base;
-        if ((L.nflag[L.nelem] | L.nflag[L.nelem + 1]) & AVAIL) L.patches[n++] = tag | int32_t(L.npatch);
-        *L.npatches = n;
+        int m = n;
+        if ((L.nflag[L.nelem] | L.nflag[L.nelem + 1]) & AVAIL) L.patches[m++] = tag | int32_t(L.npatch);
+        *L.npatches = m;
     }
 }
 
@@ -594,5 +695,49 @@ __device__ void concat_lists(const DevLevelT<R>* __restrict__ lvs, int jmin, int
         __syncthreads();
     }
     if (threadIdx.x == 0) *count = base, *irr_count = ibase;
+    // the point work lists are rebuilt from these lists next (wl_build)
+    for (int j = jmin + int(threadIdx.x); j <= jmax && threadIdx.x < 32; j += 32)
+        if (lvs[j].wl_n)
+            for (int k = 0; k < WL_KINDS; ++k) lvs[j].wl_n[k] = 0;
+}
+
+// offset of work list k of a level in wl
+template <class R>
+__device__ __forceinline__ int64_t wl_off(const DevLevelT<R>& L, int k) {
+    return k == WL_GN ? 0 : k == WL_GE ? L.N : k == WL_CN ? L.N + L.E : k == WL_RE ? 2 * L.N + L.E : 2 * L.N + 2 * L.E;
+}
+
+// warp-aggregated append of v to work list k of L when pred (the lanes of the warp
+// that reach the call take part)
+template <class R>
+__device__ __forceinline__ void wl_push(const DevLevelT<R>& L, int k, bool pred, int32_t v) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    if (!pred) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&L.wl_n[k], __popc(m));
+    base = __shfl_sync(m, base, leader);
+    L.wl[wl_off(L, k) + base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// The point work lists of one item of an active patch (node or edge, see
+// visit_item): ghost points, covered nodes, edges with a covered end, and
+// available nodes with a covered node among themselves and their neighbours (their
+// divergence changes with the restricted fluxes).  The order of the lists is not
+// fixed; every item's work is independent of it.
+template <class R>
+__device__ __forceinline__ void wl_item(const DevLevelT<R>& L, int kind, int64_t id) {
+    if (kind == K_NODE) {
+        const uint8_t f = L.nflag[id];
+        wl_push(L, WL_GN, (f & GHOST) != 0, int32_t(id));
+        wl_push(L, WL_CN, (f & COVERED) != 0, int32_t(id));
+        wl_push(L, WL_DN, restricted_div_node(L, id), int32_t(id));
+    } else {
+        const uint8_t f = L.eflag[id];
+        wl_push(L, WL_GE, (f & GHOST) != 0, int32_t(id));
+        const bool r = ((L.nflag[L.en[id]] | L.nflag[L.en[L.E + id]]) & COVERED) != 0;
+        wl_push(L, WL_RE, r, int32_t(id));
+    }
 }
 

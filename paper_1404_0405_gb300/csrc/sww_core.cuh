@@ -14,9 +14,19 @@ constexpr uint8_t AVAIL = LIVE | GHOST;
 constexpr int NF = 8, NH = 32, NB = 24;
 constexpr int MLP_PARAMS = NF * NH + NH + NH + 1;   // W1[NF][NH], b1[NH], w2[NH], b2
 
+// Work lists of a level (DevLevelT::wl): ghost nodes, ghost edges, covered nodes,
+// edges with a covered end, nodes whose divergence the restriction changes.
+constexpr int WL_GN = 0, WL_GE = 1, WL_CN = 2, WL_RE = 3, WL_DN = 4, WL_KINDS = 5;
+
 // Work-list entry: (level << LVL_SHIFT) | patch; patch == npatch stands for the two poles.
 constexpr int LVL_SHIFT = 27;
 constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
+
+// Reduction words of a handle: [0] the largest squared CFL frequency (bits of a
+// non-negative double), [1] unused, [2] and [3] max |dh| and max |u| over live
+// points (bits of non-negative doubles), [RED_LEVEL + j] the largest |u| over the
+// live edges of level j (abs_key of the field type), for levels 0..11.
+constexpr int RED_LEVEL = 4, RED_WORDS = RED_LEVEL + 12;
 
 // One level on the device, with fields in the working precision R (double, or
 // float for the FP32 form).  The spherical geometry (areas, lengths, kites, the
@@ -26,11 +36,13 @@ constexpr int32_t PATCH_MASK = (1 << LVL_SHIFT) - 1;
 // restriction) are in R (the FP64 tables rounded once for the FP32 form).  All
 // arrays are dense over the level (see grid.h for the element layout); slot-major
 // tables store slot s of item i at s*count + i.
+
 template <class R>
 struct DevLevelT {
     int J;
     int64_t n, p, np, nelem, N, E, T, npatch;
     double dx;                     // Table 1 spacing of the level (m)
+    double kx2;                    // (pi / dx)^2, the squared wavenumber of the CFL bound
     double nu;                     // viscosity (m^2/s) of the viscous form; 0: inviscid
     int advect;                    // 1: prescribed velocity (advection test case): u never changes
     // topology
@@ -38,6 +50,7 @@ struct DevLevelT {
     const int32_t *tn, *te;        // [3*T] nodes, side edges (2e + against)
     const uint8_t* deg;            // [N]
     const int32_t *ring_e;         // [6*N] (2e + edge points into the node), -1 padded
+    const int32_t* ring_n;         // [6*N] the neighbour across ring edge k, -1 padded
     const int32_t* f2c;            // [N] coarse node at the same place (-1: odd node)
     // geometry (FP64 in every precision form)
     const double *A_i, *A_v, *kite, *d_e, *l_e, *f_v, *f_n;
@@ -77,6 +90,13 @@ struct DevLevelT {
     uint8_t* pexact;               // [npatch+1] patch holds a point of the exact rules' set
     int32_t* patches;              // [npatch + 1] active patch list (+ pole entry), level-tagged
     int32_t* npatches;             // [1]
+    // work lists of the stage's point-wise phases, rebuilt with the active lists
+    // (after every adaptation): ghost nodes [N], ghost edges [E], covered nodes [N],
+    // edges with a covered end [E], available nodes with a covered node among them and
+    // their neighbours [N], at offsets 0, N, N+E, 2N+E, 2N+2E of wl; their counts in
+    // wl_n[0..4]
+    int32_t* wl;
+    int32_t* wl_n;
     // candidate patches of the list-based mask (index npatch: the two poles)
     uint8_t *zflag, *sflag, *cflag, *lflag, *gflag;   // [npatch+1] seeds, significance, candidates,
                                                       //   live nodes, ghost candidates

@@ -102,7 +102,9 @@ __global__ void k_restrict(DevLevelT<R> C, DevLevelT<R> F, const int32_t* list, 
 
 template <class R>
 __global__ void k_div(DevLevelT<R> C, const int32_t* list, const int32_t* count, int P) {
-    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, list, count, P) { div_at(L, id); });
+    ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, list, count, P) {
+        if (restricted_div_node(L, id)) div_at(L, id);
+    });
 }
 
 // R_h at covered nodes of C from level F (Eq. Rh; coefficients of non-live points are zero)
@@ -172,7 +174,8 @@ struct AddOp {
     __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a + b; }
 };
 
-// max |dh| over live nodes, max |u| over live edges (bit patterns of non-negative doubles)
+// max |dh| over live nodes, max |u| over live edges: compared as keys of the field
+// type, widened to FP64 once per block (bit patterns of non-negative doubles)
 template <class R>
 __global__ void k_maxabs(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int S,
                          unsigned long long* red) {
@@ -181,46 +184,50 @@ __global__ void k_maxabs(const DevLevelT<R>* __restrict__ lvs, const int32_t* li
     unsigned long long a = 0, b = 0;
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
         if (kind == K_NODE) {
-            if (L.nflag[id] & LIVE) a = max(a, dbits(fabs(double(L.dh[id]))));
+            if (L.nflag[id] & LIVE) a = max(a, abs_key(L.dh[id]));
         } else if (L.eflag[id] & LIVE) {
-            b = max(b, dbits(fabs(double(L.u[id]))));
+            b = max(b, abs_key(L.u[id]));
         }
     });
     a = block_reduce(a, MaxOp(), sh, 0ull);
-    if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
+    if (threadIdx.x == 0 && a) atomicMax(&red[2], dbits(key_value<R>(a)));
     b = block_reduce(b, MaxOp(), sh, 0ull);
-    if (threadIdx.x == 0 && b) atomicMax(&red[1], b);
+    if (threadIdx.x == 0 && b) atomicMax(&red[3], dbits(key_value<R>(b)));
 }
 
-// omega = sqrt(f^2 + g h (pi/dx)^2) at live nodes (max; none with a prescribed
-// velocity, which carries no waves), dx/|u| at live edges (min)
+// largest omega^2 = f^2 + g h (pi/dx)^2 over live nodes (none with a prescribed
+// velocity, which carries no waves) and, per level, the largest |u| over live
+// edges with u != 0 (NaN left out, as dx/|u| with u NaN takes no part); the step
+// itself in k_dt_final
 template <class R>
 __global__ void k_dt(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int S, double H,
                      double g, unsigned long long* red) {
     __shared__ unsigned long long sh[32];
+    __shared__ unsigned long long slev[RED_WORDS - RED_LEVEL];
+    if (threadIdx.x < RED_WORDS - RED_LEVEL) slev[threadIdx.x] = 0ull;
+    __syncthreads();
     DevLevelT<R> none{};
-    unsigned long long a = 0, b = ~0ull;
+    unsigned long long a = 0;
+    LevelMax um;
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, S) {
         if (kind == K_NODE) {
             if (L.advect || !(L.nflag[id] & LIVE)) return;
-            double f = double(L.f_n[id]), kx = M_PI / L.dx;
-            a = max(a, dbits(sqrt(f * f + g * (H + double(L.dh[id])) * kx * kx)));
+            a = max(a, dbits(omega2_at(L, id, H, g)));
         } else if (L.eflag[id] & LIVE) {
-            double au = fabs(double(L.u[id]));
-            if (au > 0) b = min(b, dbits(L.dx / au));
+            const unsigned long long k = abs_key(L.u[id]);
+            if (k && k <= inf_key<R>()) um.add(L.J, k, slev);
         }
     });
-    a = block_reduce(a, MaxOp(), sh, 0ull);
+    um.flush(slev);
+    a = block_reduce(a, MaxOp(), sh, 0ull);   // synchronises the block: slev is complete
     if (threadIdx.x == 0 && a) atomicMax(&red[0], a);
-    b = block_reduce(b, MinOp(), sh, ~0ull);
-    if (threadIdx.x == 0 && b != ~0ull) atomicMin(&red[1], b);
+    if (threadIdx.x < RED_WORDS - RED_LEVEL && slev[threadIdx.x]) atomicMax(&red[RED_LEVEL + threadIdx.x], slev[threadIdx.x]);
 }
 
-__global__ void k_dt_final(const unsigned long long* red, double cfl, double* dt) {
+template <class R>
+__global__ void k_dt_final(const DevLevelT<R>* lvs, const unsigned long long* red, double cfl, double* dt) {
     if (threadIdx.x || blockIdx.x) return;
-    double w = __longlong_as_double(static_cast<long long>(red[0]));
-    double r = red[1] == ~0ull ? INFINITY : __longlong_as_double(static_cast<long long>(red[1]));
-    *dt = cfl * fmin(1.0 / w, r);
+    *dt = cfl_step<R>(lvs, red, cfl);
 }
 
 // a prescribed velocity takes no part in the significance test (eps_u infinite
@@ -228,8 +235,8 @@ __global__ void k_dt_final(const unsigned long long* red, double cfl, double* dt
 __global__ void k_thresholds(const unsigned long long* red, double eps, double eps_h, double eps_u, int advect,
                              double* thr) {
     if (threadIdx.x || blockIdx.x) return;
-    thr[0] = eps_h > 0 ? eps_h : eps * __longlong_as_double(static_cast<long long>(red[0]));
-    thr[1] = eps_u > 0 ? eps_u : advect ? INFINITY : eps * __longlong_as_double(static_cast<long long>(red[1]));
+    thr[0] = eps_h > 0 ? eps_h : eps * __longlong_as_double(static_cast<long long>(red[2]));
+    thr[1] = eps_u > 0 ? eps_u : advect ? INFINITY : eps * __longlong_as_double(static_cast<long long>(red[3]));
 }
 
 // Neumaier-compensated partial sums of mass and energy over level Jmin (dense)
@@ -517,6 +524,14 @@ __global__ void k_concat(const DevLevelT<R>* __restrict__ lvs, int jmin, int jma
     concat_lists(lvs, jmin, jmax, all, count, irr, irr_count);
 }
 
+// the point work lists of every level from the all-level list
+template <class R>
+__global__ void k_wl_build(const DevLevelT<R>* __restrict__ lvs, const int32_t* __restrict__ list,
+                           const int32_t* __restrict__ count, int P) {
+    DevLevelT<R> none{};
+    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) { wl_item(L, kind, id); });
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------- launchers
@@ -576,9 +591,10 @@ template <class R>
 void launch_dt(const WorkT<R>& W, double H, double g, unsigned long long* red, cudaStream_t s) {
     LIST(k_dt<R>, W.lvs, W.list, W.count, W.S, H, g, red);
 }
-void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
+template <class R>
+void launch_dt_final(const DevLevelT<R>* lvs, const unsigned long long* red, double cfl, double* dt, cudaStream_t s) {
     g_launches++;
-    k_dt_final<<<1, 32, 0, s>>>(red, cfl, dt);
+    k_dt_final<R><<<1, 32, 0, s>>>(lvs, red, cfl, dt);
 }
 void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, int advect, double* thr,
                        cudaStream_t s) {
@@ -663,9 +679,10 @@ void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s) 
 
 template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
-                   int32_t* irr_count, cudaStream_t s) {
-    g_launches++;
+                   int32_t* irr_count, int P, unsigned grid, cudaStream_t s) {
+    g_launches += 2;
     k_concat<R><<<1, 1024, 0, s>>>(lvs, jmin, jmax, all, count, irr, irr_count);
+    k_wl_build<R><<<grid, TPB, 0, s>>>(lvs, all, count, P);
 }
 
 template <class R>
@@ -710,6 +727,7 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
     template void launch_inverse<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t); \
     template void launch_maxabs<R>(const WorkT<R>&, unsigned long long*, cudaStream_t);                      \
     template void launch_dt<R>(const WorkT<R>&, double, double, unsigned long long*, cudaStream_t);          \
+    template void launch_dt_final<R>(const DevLevelT<R>*, const unsigned long long*, double, double*, cudaStream_t); \
     template void launch_restrict_full<R>(const DevLevelT<R>&, const DevLevelT<R>&, cudaStream_t);           \
     template void launch_mask<R>(const MaskArgsT<R>&, cudaStream_t);                                         \
     template void launch_live_all<R>(const DevLevelT<R>*, const Span&, const Span&, cudaStream_t);           \
@@ -718,7 +736,8 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
                                     cudaStream_t);                                                           \
     template void launch_mark_support<R>(const WorkT<R>&, cudaStream_t);                                     \
     template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
-    template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, int32_t*, int32_t*, cudaStream_t);         \
+    template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, int32_t*, int32_t*, int,     \
+                                   unsigned, cudaStream_t);         \
     template void launch_patch_scan<R>(const DevLevelT<R>*, int, int, cudaStream_t);                         \
     template int sums_blocks<R>(const DevLevelT<R>&);                                                        \
     template void launch_sums<R>(const DevLevelT<R>&, double, double, double*, double*, cudaStream_t);       \

@@ -70,7 +70,8 @@ template <class R> void launch_details(const WorkT<R>& W, int jmin, cudaStream_t
 template <class R> void launch_inverse(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s);
 template <class R> void launch_maxabs(const WorkT<R>& W, unsigned long long* red, cudaStream_t s);
 template <class R> void launch_dt(const WorkT<R>& W, double H, double g, unsigned long long* red, cudaStream_t s);
-void launch_dt_final(const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
+template <class R>
+void launch_dt_final(const DevLevelT<R>* lvs, const unsigned long long* red, double cfl, double* dt, cudaStream_t s);
 void launch_thresholds(const unsigned long long* red, double eps, double eh, double eu, int advect, double* thr,
                        cudaStream_t s);
 
@@ -89,11 +90,12 @@ template <class R> void launch_mask(const MaskArgsT<R>& a, cudaStream_t s);
 template <class R> void launch_live_all(const DevLevelT<R>* lvs, const Span& nodes, const Span& edges, cudaStream_t s);
 template <class R> void launch_covered_all(const DevLevelT<R>* lvs, const Span& nodes_c, cudaStream_t s);
 template <class R> void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream_t s);
-// the all-level active list from the levels' lists, and its entries whose tile is
-// not regular (irregular list, same order)
+// the all-level active list from the levels' lists, its entries whose tile is not
+// regular (irregular list, same order), and the levels' point work lists (patch
+// area P; grid: blocks of the list launch)
 template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
-                   int32_t* irr_count, cudaStream_t s);
+                   int32_t* irr_count, int P, unsigned grid, cudaStream_t s);
 // ascending active-patch lists of levels ja..jb from the patch flags
 template <class R> void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s);
 template <class R> int sums_blocks(const DevLevelT<R>& L);

@@ -344,31 +344,8 @@ __global__ void k_flag_scan(const __grid_constant__ MaskBatch<R, CAP> B, int whi
     const uint8_t* flag = which == 1 ? L.cflag : L.gflag;
     int32_t* out = which == 1 ? L.cand : L.gcand;
     int32_t* nout = which == 1 ? L.ncand : L.ngcand;
-    __shared__ int warp_tot[32];
-    __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int32_t tag = int32_t(L.J) << LVL_SHIFT;
-    for (int64_t start = 0; start <= L.npatch; start += blockDim.x) {
-        const int64_t i = start + threadIdx.x;
-        const int f = (i <= L.npatch) ? flag[i] : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int pre = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warp_tot[w] = __popc(bal);
-        __syncthreads();
-        int off = 0;
-        for (int k = 0; k < w; ++k) off += warp_tot[k];
-        if (f) out[base + off + pre] = tag | int32_t(i);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int tot = 0;
-            for (int k = 0; k < nw; ++k) tot += warp_tot[k];
-            base += tot;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *nout = base;
+    const int n = compact_flags(flag, L.npatch + 1, int32_t(L.J) << LVL_SHIFT, out);
+    if (threadIdx.x == 0) *nout = n;
 }
 
 // concatenation of the candidate lists of the member's levels ja..jb (one block)
@@ -536,6 +513,14 @@ __global__ void k_concat_b(const __grid_constant__ MaskBatch<R, CAP> B) {
     concat_lists(M.lvs, B.ja, M.jmax, M.all, M.all_count, M.irr, M.irr_count);
 }
 
+// the point work lists of the member's levels from its all-level list
+template <class R, int CAP>
+__global__ void k_wl_build_b(const __grid_constant__ MaskBatch<R, CAP> B) {
+    MEMBER;
+    DevLevelT<R> none{};
+    ITEMS(K_NODE | K_EDGE, M.lvs, none, M.all, M.all_count, B.P) { wl_item(L, kind, id); });
+}
+
 }  // namespace
 
 namespace {
@@ -618,15 +603,16 @@ void launch_mask_batch(const MaskBatch<R, CAP>& b, unsigned grid, cudaStream_t s
 }
 
 template <class R, int CAP>
-void launch_concat_batch(const MaskBatch<R, CAP>& b, cudaStream_t s) {
+void launch_concat_batch(const MaskBatch<R, CAP>& b, unsigned grid, cudaStream_t s) {
     if (b.nm < 1 || b.nm > CAP) throw std::runtime_error("mask batch size");
     go(k_concat_b<R, CAP>, 1u, unsigned(b.nm), 1024, s, b);
+    go(k_wl_build_b<R, CAP>, grid, unsigned(b.nm), TPB, s, b);
 }
 
 #define MASK_INST(R, CAP)                                                                                   \
     template void launch_mask_batch<R, CAP>(const MaskBatch<R, CAP>&, unsigned, cudaStream_t);            \
     template void launch_proposal_batch<R, CAP>(const MaskBatch<R, CAP>&, unsigned, int, cudaStream_t);   \
-    template void launch_concat_batch<R, CAP>(const MaskBatch<R, CAP>&, cudaStream_t);
+    template void launch_concat_batch<R, CAP>(const MaskBatch<R, CAP>&, unsigned, cudaStream_t);
 MASK_INST(double, 1)
 MASK_INST(float, 1)
 MASK_INST(double, MASK_BATCH_MAX)

@@ -53,8 +53,9 @@ void launch_mask_batch(const MaskBatch<R, CAP>& b, unsigned grid, cudaStream_t s
 // proposal roll before a mask (post 0) or after it (post 1)
 template <class R, int CAP>
 void launch_proposal_batch(const MaskBatch<R, CAP>& b, unsigned grid, int post, cudaStream_t s);
-// the all-level and irregular lists of every member from its level lists
+// the all-level and irregular lists of every member from its level lists, and the
+// levels' point work lists (grid: blocks per member of the list launch)
 template <class R, int CAP>
-void launch_concat_batch(const MaskBatch<R, CAP>& b, cudaStream_t s);
+void launch_concat_batch(const MaskBatch<R, CAP>& b, unsigned grid, cudaStream_t s);
 
 }  // namespace sww

@@ -172,7 +172,9 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
             restrict_item(L, F, kind, id);
         });
         if (!stage_sync(a)) return;
-        ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, C.patches, C.npatches, a.P) { div_at(L, id); });
+        ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, C.patches, C.npatches, a.P) {
+            if (restricted_div_node(L, id)) div_at(L, id);
+        });
         if (!stage_sync(a)) return;
     }
     const R dt = R(a.dt ? *a.dt : 0.0);

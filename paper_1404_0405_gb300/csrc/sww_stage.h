@@ -46,7 +46,7 @@ struct MemberRef {
     const int32_t* all_count;
     double* dt;
     int jtop;
-    unsigned long long* red;   // [4] reduction words: CFL time step [0, 1], live maxima [2, 3]
+    unsigned long long* red;   // [RED_WORDS] reduction words (CFL step, live maxima; see RED_WORDS)
     double cfl;
     // adaptation (batched phases around the members' own masks)
     double* thr;               // [2] thresholds eps_h, eps_u

@@ -42,8 +42,13 @@ __device__ __forceinline__ void stage_records(DevLevelT<R>* sl, const MemberRef<
     __syncthreads();
 }
 
+// resident blocks per SM the tile kernel is built for: six for 8 x 8 tiles (40
+// registers), four for 16 x 16 (their per-thread slot plan is larger)
+template <int P>
+constexpr int tile_min_blocks() { return P >= 16 ? 4 : 6; }
+
 template <class R, int P>
-__global__ void __launch_bounds__(TILE_TPB, 6) k_tile_trend(BatchArgs<R> a, int bpm) {
+__global__ void __launch_bounds__(TILE_TPB, tile_min_blocks<P>()) k_tile_trend(BatchArgs<R> a, int bpm) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ DevLevelT<R> sl[MAXL];
     const int m = blockIdx.x / bpm, b = blockIdx.x % bpm;

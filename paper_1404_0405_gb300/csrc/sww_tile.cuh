@@ -177,17 +177,28 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
     using T = Tile<R, P>;
     using PL = TilePlan<P, NT>;
     constexpr int W = T::W, NN = T::NN, PP = P * P;
-    R* dh = reinterpret_cast<R*>(smem + T::OFF_DH);
-    R* u = reinterpret_cast<R*>(smem + T::OFF_U);
-    R* F = reinterpret_cast<R*>(smem + T::OFF_F);
-    R* de = reinterpret_cast<R*>(smem + T::OFF_DE);
-    R* le = reinterpret_cast<R*>(smem + T::OFF_LE);
-    R* q = reinterpret_cast<R*>(smem + T::OFF_Q);
-    R* kt = reinterpret_cast<R*>(smem + T::OFF_KT);
-    R* is = reinterpret_cast<R*>(smem + T::OFF_IS);
-    uint8_t* nf = smem + T::OFF_NF;
-    uint8_t* ef = smem + T::OFF_EF;
-    const int64_t base = pat * PP;
+    R* __restrict__ dh = reinterpret_cast<R*>(smem + T::OFF_DH);
+    R* __restrict__ u = reinterpret_cast<R*>(smem + T::OFF_U);
+    R* __restrict__ F = reinterpret_cast<R*>(smem + T::OFF_F);
+    R* __restrict__ de = reinterpret_cast<R*>(smem + T::OFF_DE);
+    R* __restrict__ le = reinterpret_cast<R*>(smem + T::OFF_LE);
+    R* __restrict__ q = reinterpret_cast<R*>(smem + T::OFF_Q);
+    R* __restrict__ kt = reinterpret_cast<R*>(smem + T::OFF_KT);
+    R* __restrict__ is = reinterpret_cast<R*>(smem + T::OFF_IS);
+    uint8_t* __restrict__ nf = smem + T::OFF_NF;
+    uint8_t* __restrict__ ef = smem + T::OFF_EF;
+    // the level's fields, read once from its record (which sits in shared memory)
+    const int32_t nelem = int32_t(L.nelem), ntri = int32_t(L.T);
+    const R* __restrict__ g_dh = L.dh;
+    const R* __restrict__ g_u = L.u;
+    const uint8_t* __restrict__ g_nf = L.nflag;
+    const uint8_t* __restrict__ g_ef = L.eflag;
+    const double* __restrict__ g_de = L.d_e;
+    const double* __restrict__ g_le = L.l_e;
+    const double* __restrict__ g_kite = L.kite;
+    const double* __restrict__ g_av = L.A_v;
+    const double* __restrict__ g_fv = L.f_v;
+    const int32_t base = int32_t(pat) * PP;
     const int tid = threadIdx.x;
     // --- stage: nodes, edges (velocity turned to the local direction), triangles
     // (their area and Coriolis parameter kept in registers for q)
@@ -196,9 +207,9 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
         const int c = plan.n[i];
         if (c == PL::NONE) continue;
         const int x = tid + i * NT;
-        const int64_t v = c < 0 ? base + (-c - 1) : int64_t(codes.n[i]);
-        dh[x] = L.dh[v];
-        nf[x] = L.nflag[v];
+        const int32_t v = c < 0 ? base + (-c - 1) : codes.n[i];
+        dh[x] = g_dh[v];
+        nf[x] = g_nf[v];
     }
 #pragma unroll
     for (int i = 0; i < PL::SE; ++i) {
@@ -207,22 +218,22 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             if (y < 3 * NN) ef[y] = 0;
             continue;
         }
-        int64_t e;
+        int32_t e;
         bool rev;
         if (c < 0) {
             const int k = -c - 1, o = k / PP;
-            e = o * L.nelem + base + (k - o * PP);
+            e = o * nelem + base + (k - o * PP);
             rev = false;
         } else {
             const int32_t code = codes.e[i];
             e = code >> 1;
             rev = code & 1;
         }
-        const R ue = L.u[e];
+        const R ue = g_u[e];
         u[y] = rev ? -ue : ue;
-        ef[y] = L.eflag[e];
-        de[y] = geo<R>(L.d_e, e);
-        le[y] = geo<R>(L.l_e, e);
+        ef[y] = g_ef[e];
+        de[y] = geo<R>(g_de, e);
+        le[y] = geo<R>(g_le, e);
     }
     R tav[PL::ST], tfv[PL::ST];
 #pragma unroll
@@ -230,11 +241,11 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
         const int c = plan.t[i], z = tid + i * NT;
         tav[i] = R(1), tfv[i] = R(0);
         if (c == PL::NONE) continue;
-        int64_t tr;
+        int32_t tr;
         int sft;
         if (c < 0) {
             const int k = -c - 1, t = k / PP;
-            tr = t * L.nelem + base + (k - t * PP);
+            tr = t * nelem + base + (k - t * PP);
             sft = 0;
         } else {
             const int32_t code = codes.t[i];
@@ -245,10 +256,10 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
             const int gc = cc + sft < 3 ? cc + sft : cc + sft - 3;
-            kt[(3 * t + cc) * NN + x] = geo<R>(L.kite, gc * L.T + tr);
+            kt[(3 * t + cc) * NN + x] = geo<R>(g_kite, int64_t(gc) * ntri + tr);
         }
-        tav[i] = geo<R>(L.A_v, tr);
-        tfv[i] = geo<R>(L.f_v, tr);
+        tav[i] = geo<R>(g_av, tr);
+        tfv[i] = geo<R>(g_fv, tr);
     }
     __syncthreads();
     // --- F at edges, q at triangles, the kite sums of the nodes of [0, P]^2
@@ -262,7 +273,7 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             const int x2 = x + (o == 0 ? W : o == 1 ? W + 1 : 1);
             if ((nf[x] & AVAIL) && (nf[x2] & AVAIL)) {
                 f = R(0.5) * ((H + dh[x]) + (H + dh[x2])) * u[y];
-                if (plan.e[i] < 0) L.F[o * L.nelem + base + (-plan.e[i] - 1 - o * PP)] = f;
+                if (plan.e[i] < 0) L.F[o * nelem + base + (-plan.e[i] - 1 - o * PP)] = f;
             }
         }
         F[y] = f;
@@ -284,7 +295,7 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             const R hv = kt[(3 * t) * NN + x] * (H + dh[x]) + kt[(3 * t + 1) * NN + x] * (H + dh[n1]) +
                          kt[(3 * t + 2) * NN + x] * (H + dh[n2]);
             qq = (circ / tav[i] + tfv[i]) / (hv / tav[i]);
-            if (c < 0) L.q[t * L.nelem + base + (-c - 1 - t * PP)] = qq;
+            if (c < 0) L.q[t * nelem + base + (-c - 1 - t * PP)] = qq;
         }
         q[z] = qq;
     }
@@ -320,7 +331,7 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
                 ke += R(0.25) * le[y] * de[y] * u[y] * u[y];
             }
             if (!ok) continue;
-            const int64_t v = base + i;
+            const int32_t v = base + i;
             const R A = geo<R>(L.A_i, v);
             L.c[v] = div / A;
             L.B[v] = g * dh[x] + ke / A;
@@ -330,7 +341,7 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             const R Q = o == 0 ? tile_coriolis<R, W, NN, 0>(x, q, F, le, de, kt, is)
                                : o == 1 ? tile_coriolis<R, W, NN, 1>(x, q, F, le, de, kt, is)
                                         : tile_coriolis<R, W, NN, 2>(x, q, F, le, de, kt, is);
-            L.Q[o * L.nelem + base + i] = Q;
+            L.Q[o * nelem + base + i] = Q;
         }
     }
 }

@@ -61,6 +61,8 @@ int main(int argc, char** argv) {
         put_slots(dir, p + "cor_i", L.cor_i, COR);
         put_slots(dir, p + "cor_w", L.cor_w, COR);
         put_slots(dir, p + "et", L.et, 2);
+        put(dir, p + "tile_irr", L.tile_irr);
+        put(dir, p + "tile_halo", L.tile_halo);
         if (j > jmin) {
             put_slots(dir, p + "par", L.par, 4);
             put_slots(dir, p + "akm", L.akm, 4);

@@ -159,3 +159,76 @@ def test_restricted_flux(dump, ora, maps):
         cw = dump(f"L{j - 1}_rf_cw", np.float64, (11, -1))
         lib = np.sum(fw * Mf.edges_to_lib(Ff)[fi], axis=0) + np.sum(cw * Mf.nodes_to_lib(c)[ci], axis=0)
         assert np.abs(Mc.edges_to_ora(lib) - ref).max() < geo_tol(j) * np.abs(ref).max()
+
+
+def _halo_positions(p):
+    """The halo slots of a tile of side p, in table order, as (kind, a, b, o): nodes
+    (a, b in -1..p+1), edges o = 0, 1, 2 from (a, b) along +a, +a+b, +b (a in -1..p
+    or -1..p+1, b likewise, so that both ends are in the node range), triangles t0
+    (a,b),(a+1,b),(a+1,b+1) and t1 (a,b),(a+1,b+1),(a,b+1) (a, b in -1..p); each
+    block row-major without the patch's own positions 0..p-1."""
+    def block(A, B):
+        return [(a, b) for a in range(-1, A + 1) for b in range(-1, B + 1) if not (0 <= a < p and 0 <= b < p)]
+    out = [("n", a, b, 0) for a, b in block(p + 1, p + 1)]
+    for o, (A, B) in enumerate([(p, p + 1), (p, p), (p + 1, p)]):
+        out += [("e", a, b, o) for a, b in block(A, B)]
+    for t in range(2):
+        out += [("t", a, b, t) for a, b in block(p, p)]
+    return out
+
+
+def test_tiles_are_lattice_neighbourhoods(dump):
+    """Every regular tile's halo table lays out a triangular lattice around its
+    patch (Sec. 5.2): each listed edge joins the nodes at its two lattice
+    positions in its stated direction, each listed triangle holds its three
+    lattice nodes counter-clockwise with the stated vertex first, every node is a
+    hexagon (degree 6), and the tiles near the twelve pentagons -- 40 patches per
+    level once a lozenge side holds more than one patch -- are the irregular ones."""
+    lay = _halo_positions(PATCH)
+    p = PATCH
+    for j in range(JMIN, JMAX + 1):
+        xyz = dump(f"L{j}_xyz", np.float64, (-1, 3))
+        en = dump(f"L{j}_en", np.int32, (2, -1)).T
+        tn = dump(f"L{j}_tn", np.int32, (3, -1)).T
+        irr = dump(f"L{j}_tile_irr", np.uint8)
+        halo = dump(f"L{j}_tile_halo", np.int32)
+        n = 2 ** j
+        np_ = n // p if n >= p else 1
+        npatch = 10 * np_ * np_
+        assert irr.size == npatch + 1 and irr[-1] == 1
+        if n <= p:   # one patch per lozenge: every tile holds pentagons
+            assert irr.all()
+            continue
+        assert halo.size == npatch * len(lay)
+        assert int(irr[:-1].sum()) == (npatch if np_ <= 2 else 40), (j, int(irr[:-1].sum()))
+        halo = halo.reshape(npatch, len(lay))
+        nelem = 10 * n * n
+        deg = np.bincount(en.ravel(), minlength=xyz.shape[0])
+        for P in np.flatnonzero(irr[:-1] == 0)[:25]:
+            node = {}
+            for a in range(p):
+                for b in range(p):
+                    node[(a, b)] = P * p * p + a * p + b
+            for (kind, a, b, o), v in zip(lay, halo[P]):
+                if kind == "n":
+                    node[(a, b)] = int(v)
+            assert all(deg[v] == 6 for v in node.values())
+            step = [(1, 0), (1, 1), (0, 1)]
+            for (kind, a, b, o), v in zip(lay, halo[P]):
+                if kind == "e":
+                    e, rev = int(v) >> 1, int(v) & 1
+                    ends = (node[(a, b)], node[(a + step[o][0], b + step[o][1])])
+                    assert tuple(en[e]) == (ends[::-1] if rev else ends)
+                elif kind == "t":
+                    t, sft = int(v) >> 2, int(v) & 3
+                    loc = [(a, b), (a + 1, b), (a + 1, b + 1)] if o == 0 else [(a, b), (a + 1, b + 1), (a, b + 1)]
+                    ids = [node[q] for q in loc]
+                    assert [int(tn[t][(c + sft) % 3]) for c in range(3)] == ids
+                    x0, x1, x2 = xyz[ids]
+                    assert np.dot(np.cross(x1 - x0, x2 - x0), x0 + x1 + x2) > 0   # counter-clockwise
+            # the own edges and triangles follow the element layout
+            for a in range(p):
+                for b in range(p):
+                    el = P * p * p + a * p + b
+                    for o in range(3):
+                        assert tuple(en[o * nelem + el]) == (node[(a, b)], node[(a + step[o][0], b + step[o][1])])
