@@ -326,9 +326,12 @@ def _live(m):
     return sum(m.stats()["live_nodes"].values())
 
 
-def _avail(m):
-    st = m.stats()
+def _avail_st(st):
     return sum(st["live_nodes"].values()) + sum(st["ghost_nodes"].values())
+
+
+def _avail(m):
+    return _avail_st(m.stats())
 
 
 _SAMPLINGS = {}
@@ -495,9 +498,11 @@ def _turbulence(sww, workloads, a, steps, flush, peak, prec_bytes):
         m.load(ck)
         m.set_learned(0)
         m.profile(["trend"])
-        tb_bytes = 0.0
+        tb_bytes = tb_patches = 0.0
         for _ in range(steps):
-            tb_bytes += prec_bytes * _avail(m) * 4
+            st = m.stats()
+            tb_bytes += prec_bytes * _avail_st(st) * 4
+            tb_patches += sum(st["active_patches"].values()) * 4
             flush.zero_()
             m.step(-1.0, 1, True)
         t_ms, t_n = m.profile_read()["trend"]
@@ -507,7 +512,9 @@ def _turbulence(sww, workloads, a, steps, flush, peak, prec_bytes):
             out["roofline_trend"] = {"kernel": "k_tile_trend", "achieved": ach, "peak": peak, "unit": "GB/s",
                                      "frac": ach / peak, "avg_launch_us": t_ms * 1e3 / t_n, "launches": t_n,
                                      "algorithmic_bytes_per_launch": tb_bytes / t_n,
-                                     "available_cells_per_launch": tb_bytes / prec_bytes / t_n}
+                                     "available_cells_per_launch": tb_bytes / prec_bytes / t_n,
+                                     "patches_per_launch": tb_patches / t_n,
+                                     "patch_fill": tb_bytes / prec_bytes / max(tb_patches, 1.0) / m.cfg.patch ** 2}
     m.close()
     base.close()
     tb.close()
@@ -651,10 +658,12 @@ def run_ours(a, rank, world):
         classes = ["trend", "irregular", "fill", "restrict", "update", "stage", "dt", "partial", "coeff", "mask",
                    "inverse"]
         m0.profile(classes)
-        tbytes = sbytes = 0.0
+        tbytes = sbytes = tpatches = 0.0
         for _ in range(a.steps):
-            tbytes += TREND_BYTES_PER_CELL[prec] * sum(_avail(m) for m in ms) * 4
-            sbytes += STAGE_BYTES_PER_CELL[prec] * sum(_live(m) for m in ms) * 4
+            sts = [m.stats() for m in ms]
+            tbytes += TREND_BYTES_PER_CELL[prec] * sum(_avail_st(st) for st in sts) * 4
+            sbytes += STAGE_BYTES_PER_CELL[prec] * sum(sum(st["live_nodes"].values()) for st in sts) * 4
+            tpatches += sum(sum(st["active_patches"].values()) for st in sts) * 4
             flush.zero_()
             sww.step_ensemble(ms, -1.0, 1, True)
         prof = m0.profile_read()
@@ -671,6 +680,8 @@ def run_ours(a, rank, world):
                         "avg_launch_us": t_ms * 1e3 / t_n, "launches": t_n,
                         "algorithmic_bytes_per_launch": tbytes / t_n,
                         "available_cells_per_launch": tbytes / TREND_BYTES_PER_CELL[prec] / t_n,
+                        "patches_per_launch": tpatches / t_n,
+                        "patch_fill": tbytes / TREND_BYTES_PER_CELL[prec] / max(tpatches, 1.0) / cpatch ** 2,
                         "bytes_per_available_cell": TREND_BYTES_PER_CELL[prec],
                         "share_of_step": (t_ms / 1e3) / max(sum(times), 1e-30)}
         if s_n > 0:
