@@ -612,7 +612,9 @@ def run_ours(a, rank, world):
     torch.cuda.synchronize()
     clocks = Clocks(dev)
     clocks.start()
+    torch.cuda.profiler.start()   # the timed steps are the profiler's range (ncu --profile-from-start off)
     times, cells = _timed(sww, ms, a.steps, flush, stream)
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
     launches = ms[0].stats()["kernel_launches"] - launches0   # process-wide counter: every member
     total_all, cells_all = combine_ranks(sum(times), sum(cells), "cuda", world)
