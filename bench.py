@@ -315,11 +315,12 @@ STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 184}
 # B and q F^perp written (8 words) -- 12 words + 140 B: 188 B in FP32, 236 B in FP64.
 TREND_BYTES_PER_CELL = {"fp64": 236, "fp32": 188}
 
-# DRAM bytes (read + write) of k_tile_trend per available cell, from the ncu
-# capture of the same jet at Jmin=4..Jmax=8 with 16 members
-# (profiles/k_tile_trend_jet_J4-8_16members.md), scaled to a launch by the cells it
-# processes; remove the entry when the kernel changes.
-TREND_TRAFFIC_PER_CELL = {}
+# DRAM bytes (read + write) of k_tile_trend per available cell, from an ncu
+# full-set capture of the same jet at Jmin=4..Jmax=8 with 16 members (52.4 MB for
+# 495 961 cells), scaled to a launch by the cells it processes.  The geometry
+# share falls as more members read the same tables, so at 64 members this
+# overstates the traffic.  Remove the entry when the kernel changes.
+TREND_TRAFFIC_PER_CELL = {"fp32": 105.7}
 
 
 def _live(m):
