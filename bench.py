@@ -174,29 +174,49 @@ def host_cpu():
     return {"model": model, "logical_cores": os.cpu_count()}
 
 
+def member_seeds(seed, rank, n):
+    """Workload seeds of the n members of one rank (ranks 1000 seeds apart)."""
+    return [seed + 1000 * rank + k for k in range(n)]
+
+
+def oracle_member(hy, eps, seed, jmax):
+    """The oracle's member of the benchmark's workload: the jet of `seed` given on
+    level jmax of the hierarchy, adapted (twice: the second pass sees the first's
+    grid)."""
+    import workloads
+    from oracle import model
+    M = model.Model(hy, eps=eps, rk="rk4", cfl=0.8)
+    L = hy.levels[jmax]
+    dh, u = workloads.Workload("jet", seed=seed).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
+    M.set_uniform(dh, u)
+    M.adapt()
+    M.adapt()
+    return M
+
+
+def oracle_steps(M, steps):
+    """Active-cell steps (mean of each step's start and end) and seconds of `steps`
+    CFL steps of an oracle member."""
+    cells, t0 = 0.0, time.perf_counter()
+    for _ in range(steps):
+        act = M.active_nodes()
+        M.step(M.dt_cfl())
+        cells += (act + M.active_nodes()) / 2
+    return cells, time.perf_counter() - t0
+
+
 def _oracle_worker(hy, a, jmax, k, go, res, barrier):
     """One member of the benchmark's workload (seed + k) stepped by the oracle, in a
     worker forked before any CUDA call: waits for (steps, warmup), then adapts,
     takes the warm-up steps, meets the other workers, and times its steps."""
-    import workloads
-    from oracle import model
     steps, warmup = go.get()
     try:
-        M = model.Model(hy, eps=a.eps, rk="rk4", cfl=0.8)
-        L = hy.levels[jmax]
-        dh, u = workloads.Workload("jet", seed=a.seed + k).fields(L.xyz, L.edge_midpoints(), L.edge_tangents())
-        M.set_uniform(dh, u)
-        M.adapt()
-        M.adapt()
+        M = oracle_member(hy, a.eps, a.seed + k, jmax)
         for _ in range(warmup):
             M.step(M.dt_cfl())
         barrier.wait()
-        cells, t0 = 0.0, time.perf_counter()
-        for _ in range(steps):
-            act = M.active_nodes()
-            M.step(M.dt_cfl())
-            cells += (act + M.active_nodes()) / 2
-        res.put((k, cells, time.perf_counter() - t0, steps))
+        cells, secs = oracle_steps(M, steps)
+        res.put((k, cells, secs, steps))
     except Exception as e:   # reported to the parent, which then leaves the figure out
         try:
             barrier.abort()
@@ -316,11 +336,9 @@ STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 184}
 TREND_BYTES_PER_CELL = {"fp64": 236, "fp32": 188}
 
 # DRAM bytes (read + write) of k_tile_trend per available cell, from an ncu
-# full-set capture of the same jet at Jmin=4..Jmax=8 with 16 members (52.4 MB for
-# 495 961 cells), scaled to a launch by the cells it processes.  The geometry
-# share falls as more members read the same tables, so at 64 members this
-# overstates the traffic.  Remove the entry when the kernel changes.
-TREND_TRAFFIC_PER_CELL = {"fp32": 105.7}
+# full-set capture of the same jet at Jmin=4..Jmax=8 with 16 members, scaled to a
+# launch by the cells it processes (empty until the current kernel is captured).
+TREND_TRAFFIC_PER_CELL = {}
 
 
 def _live(m):
@@ -551,7 +569,7 @@ def run_ours(a, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
-    seed = a.seed + 1000 * rank
+    seed = member_seeds(a.seed, rank, 1)[0]
     t_setup = time.perf_counter()
     base = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8)
     stream = torch.cuda.current_stream()
@@ -586,7 +604,7 @@ def run_ours(a, rank, world):
         if cpatch != a.patch:
             cbase = sww.Model(a.jmin, a.jmax, patch=cpatch, eps=a.eps, rk="rk4", cfl=0.8)
     if a.form == "chosen" and a.no_learned:
-        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], persistent="phased",
+        ms = _members(sww, workloads, cbase, a, "fp32", member_seeds(a.seed, rank, a.members), persistent="phased",
                       patch=cpatch, bps=cbps)
         dtype = "f32"
     elif a.form == "chosen":
@@ -596,7 +614,7 @@ def run_ours(a, rank, world):
         X, y = np.concatenate(Xs), np.concatenate(ys)
         learned, losses = learn.train(X, y, epochs=300)
         del train_m
-        ms = _members(sww, workloads, cbase, a, "fp32", [seed + k for k in range(a.members)], learned,
+        ms = _members(sww, workloads, cbase, a, "fp32", member_seeds(a.seed, rank, a.members), learned,
                       persistent="phased", patch=cpatch, bps=cbps)
         dtype = "f32"
     else:

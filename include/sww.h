@@ -46,7 +46,7 @@ enum {
     SWW_E_ARG = -1,      /* invalid argument (bad level, null pointer, bad config) */
     SWW_E_CUDA = -2,     /* a CUDA call failed; the handle should be destroyed */
     SWW_E_POOL = -3,     /* device memory exhausted at creation */
-    SWW_E_TIMEOUT = -4,  /* a bounded device wait (grid barrier of a persistent stage) gave up */
+    SWW_E_TIMEOUT = -4,  /* a bounded device wait (a grid barrier of a persistent stage, or a tile's bulk copy) gave up */
     SWW_E_STATE = -5,    /* call out of order (e.g. step before set_state) */
     SWW_E_NUMERIC = -6   /* non-finite value detected in the state */
 };
@@ -75,7 +75,7 @@ typedef struct {
     double omega;      /* rotation rate (1/s)                                          */
     double g;          /* gravity (m/s^2)                                              */
     double H;          /* mean depth (m)                                               */
-    int patch;         /* patch side p (power of two); levels with 2^j < p use 2^j     */
+    int patch;         /* patch side p: 4, 8 or 16; levels with 2^j < p use 2^j        */
     int rk;            /* SWW_RK4 or SWW_SSP43                                         */
     double cfl;        /* dt = cfl * min(1/omega_max, min dx/|u|) when dt <= 0         */
     double eps;        /* relative threshold: eps_h = eps*max|dh|, eps_u = eps*max|u| (see regime); 0 keeps every point */

@@ -136,6 +136,35 @@ struct Geometry {
         ck(cudaDeviceSynchronize(), "fp32 tables");
         lvf.swap(out);
     }
+    // geometry blocks of the structured trend in precision R (on demand): the
+    // FP64 tables rounded once, as the stencils round them on use
+    bool tgeo_f64 = false, tgeo_f32 = false;
+    template <class R>
+    void ensure_tile_geo() {
+        std::lock_guard<std::mutex> lock(mu);
+        constexpr bool f32 = std::is_same<R, float>::value;
+        bool& done = f32 ? tgeo_f32 : tgeo_f64;
+        if (done) return;
+        for (int j = jmin; j <= jmax; ++j) {
+            DevLevelT<R>& D = *level_rec<R>(j);
+            if (!D.thalo) continue;
+            const size_t words = tile_geo_words<R>(patch);
+            if (!words || D.p != patch) throw std::runtime_error("tile geometry: patch side");
+            R* out = dev_alloc<R>(allocs, size_t(D.npatch) * words);
+            ck(cudaMemset(out, 0, size_t(D.npatch) * words * sizeof(R)), "memset");
+            ck(build_tile_geo<R>(D, patch, out, cudaStream_t(0)), "tile geometry");
+            D.tgeo = out;
+        }
+        ck(cudaDeviceSynchronize(), "tile geometry");
+        done = true;
+    }
+    template <class R>
+    DevLevelT<R>* level_rec(int j) {
+        if constexpr (std::is_same<R, float>::value)
+            return &lvf[j];
+        else
+            return &lv[j];
+    }
     ~Geometry() {
         for (void* p : allocs) cudaFree(p);
     }
@@ -421,6 +450,8 @@ void alloc_state(sww_handle* h, int j) {
         D = h->geo->lvf[j];
     else
         D = h->geo->lv[j];
+    // a level with tiles has its geometry blocks (the structured trend copies them)
+    if (D.thalo && !D.tgeo) throw std::runtime_error("tile geometry blocks missing");
     const int64_t N = D.N, E = D.E, T = D.T;
     const int64_t coarse_E = j > h->cfg.jmin ? h->geo->lv[j - 1].E : 1;
     R** dN[] = {&D.dh, &D.dh0, &D.dha, &D.dht, &D.B, &D.c, &D.hdet};
@@ -600,13 +631,14 @@ void stage(sww_handle* h, const RKStage& st) {
     ck(launch_stage(a, h->stage_blocks, h->stream), "persistent stage launch");
 }
 
-// SWW_E_TIMEOUT (and the flag cleared) when a persistent stage's barrier timed out
+// SWW_E_TIMEOUT (and the flag cleared) when a persistent stage's barrier or a tile's
+// bulk copy timed out
 int barrier_status(sww_handle* h) {
     if (!*h->h_err) return SWW_OK;
     *h->h_err = 0;
     ck(cudaMemset(h->err, 0, sizeof(int)), "reset err");
     ck(cudaMemset(h->bar, 0, STAGE_BAR_WORDS * sizeof(unsigned)), "reset barrier");
-    return fail(SWW_E_TIMEOUT, "a grid barrier of the persistent RK stage timed out");
+    return fail(SWW_E_TIMEOUT, "a bounded wait of the RK stage (grid barrier or bulk copy) timed out");
 }
 
 template <class R>
@@ -1045,8 +1077,7 @@ int check_config(const sww_config* cfg) {
     if (!(cfg->radius > 0) || !(cfg->g > 0) || !depth_ok || !(cfg->cfl > 0))
         return fail(SWW_E_ARG, "radius, g and cfl must be positive, H positive (>= 0 with advect)");
     if (!(cfg->eps >= 0)) return fail(SWW_E_ARG, "eps must be >= 0 (0: every point significant, no compression)");
-    if (cfg->patch < 1 || (cfg->patch & (cfg->patch - 1)) || cfg->patch > 16)
-        return fail(SWW_E_ARG, "patch must be a power of two <= 16");
+    if (cfg->patch != 4 && cfg->patch != 8 && cfg->patch != 16) return fail(SWW_E_ARG, "patch must be 4, 8 or 16");
     if (cfg->rk != SWW_RK4 && cfg->rk != SWW_SSP43) return fail(SWW_E_ARG, "rk must be SWW_RK4 or SWW_SSP43");
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32) return fail(SWW_E_ARG, "blocks_per_sm must be 0..32");
     if (cfg->precision != SWW_FP64 && cfg->precision != SWW_FP32)
@@ -1073,7 +1104,12 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         ck(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev), "device attribute");
         h->geo = geo ? geo : build_geometry(cfg->jmin, cfg->jmax, cfg->patch, cfg->radius, cfg->omega);
         const bool fp32 = cfg->precision == SWW_FP32;
-        if (fp32) h->geo->ensure_fp32();
+        if (fp32) {
+            h->geo->ensure_fp32();
+            h->geo->ensure_tile_geo<float>();
+        } else {
+            h->geo->ensure_tile_geo<double>();
+        }
         h->lv.assign(fp32 ? 0 : cfg->jmax + 1, DevLevelT<double>{});
         h->lvf.assign(fp32 ? cfg->jmax + 1 : 0, DevLevelT<float>{});
         h->grid_lv.assign(cfg->jmax + 1, 1);

@@ -708,7 +708,9 @@ __device__ __forceinline__ int64_t wl_off(const DevLevelT<R>& L, int k) {
 }
 
 // warp-aggregated append of v to work list k of L when pred (the lanes of the warp
-// that reach the call take part)
+// that reach the call take part).  All lanes of a warp belong to one level: the
+// work-list build visits 4 x P items per list entry (node and edge slots), with
+// P >= 16 (patch sides 4, 8, 16) a multiple of 32.
 template <class R>
 __device__ __forceinline__ void wl_push(const DevLevelT<R>& L, int k, bool pred, int32_t v) {
     const unsigned act = __activemask();

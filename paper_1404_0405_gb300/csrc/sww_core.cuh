@@ -77,6 +77,7 @@ struct DevLevelT {
     // tiles) and the irregular flag of each patch (index npatch: the poles, 1)
     const int32_t* thalo;          // [npatch * halo]
     const uint8_t* tirr;           // [npatch + 1]
+    const R* tgeo;                 // [npatch * geometry block words]: geometry blocks of the regular patches
     // state and work arrays
     R *dh, *u, *dh0, *u0, *dha, *ua, *dht, *ut;
     R *F, *q, *B, *c, *Q;

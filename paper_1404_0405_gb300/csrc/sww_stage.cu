@@ -13,7 +13,8 @@
 // patch a block works on is staged in dynamic shared memory.  Loads of this
 // translation unit bypass L1 (compiled with -dlcm=cg): values written by other
 // blocks in one phase are read in the next.  Every barrier wait is bounded: after
-// about two seconds a block sets the error flag and the kernel returns.
+// about two seconds a block sets the error flag and the kernel returns; so does
+// the wait for a patch's geometry block (a bulk copy).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +29,7 @@ namespace sww {
 
 namespace {
 
+#include "bulk.cuh"
 #include "sww_bodies.cuh"
 #include "sww_tile.cuh"
 
@@ -131,30 +133,22 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
     }
     {
         // one active patch per block at a time
-        TilePlan<P, STAGE_TPB> plan;
-        plan.init();
-        const int n = *a.all_count;
-        for (int e = blockIdx.x; e < n; e += gridDim.x) {
-            const int32_t ent = a.all_list[e];
-            const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
-            const int64_t pat = ent & PATCH_MASK;
-            if (tile_regular(L, pat)) {
-                TileCodes<P, STAGE_TPB> codes;
-                codes.load(L, pat, plan);
-                tile_trend<R, P, STAGE_TPB>(L, pat, H, g, plan, codes, smem);
-            } else {
-                for (int it = threadIdx.x; it < 5 * a.P; it += blockDim.x) {
-                    auto body = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t) {
-                        if (kind == K_EDGE)
-                            flux_at(LL, id, H);
-                        else
-                            pv_at(LL, id, H);
-                    };
-                    visit_item<K_EDGE | K_TRI>(L, pat, uint32_t(it), a.P, body);
-                }
-            }
-            __syncthreads();
-        }
+        const long long limit = a.spin > 0 ? a.spin : SPIN_CYCLES;
+        const int area = a.P;
+        const bool ok = tile_sweep<R, P, STAGE_TPB>(lv, a.all_list, *a.all_count, int(blockIdx.x), int(gridDim.x), H, g,
+                                                    smem, a.err, limit, [&](const DevLevelT<R>& L, int64_t pat) {
+                                                        for (int it = threadIdx.x; it < 5 * area; it += blockDim.x) {
+                                                            auto body = [&](const DevLevelT<R>& LL, int kind, int64_t id,
+                                                                            int64_t) {
+                                                                if (kind == K_EDGE)
+                                                                    flux_at(LL, id, H);
+                                                                else
+                                                                    pv_at(LL, id, H);
+                                                            };
+                                                            visit_item<K_EDGE | K_TRI>(L, pat, uint32_t(it), area, body);
+                                                        }
+                                                    });
+        if (!ok) return;
     }
     if (!stage_sync(a)) return;
     ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.irr_list, a.irr_count, a.P) {
@@ -189,8 +183,9 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
 template <class R, int P>
 unsigned stage_grid_p(int nsm) {
     constexpr size_t smem = Tile<R, P>::BYTES;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_stage<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
+    // the dynamic tile and the static level records together may pass the default
+    // 48 KB: the dynamic size is always declared
+    if (cudaFuncSetAttribute(k_stage<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess)
         return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<R, P>, STAGE_TPB, smem) != cudaSuccess) return 0;

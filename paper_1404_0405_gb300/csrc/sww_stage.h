@@ -54,7 +54,7 @@ struct MemberRef {
     int advect;                // prescribed velocity: no velocity threshold
     int j1;                    // top level of the inverse transform (min(jtop + 1, jmax))
     int jmax;
-    const int* err;            // barrier error flag of the member's persistent stages
+    int* err;                  // error flag of the member's bounded waits (barriers, bulk copies)
     const int32_t* irr_list;   // entries of all_list whose tile is not regular
     const int32_t* irr_count;
 };
@@ -88,6 +88,13 @@ template <class R>
 unsigned stage_grid(int P, int nsm);
 template <class R>
 cudaError_t launch_stage(const StageArgs<R>& a, unsigned grid, cudaStream_t s);
+// words of the geometry block of one tile of side `side` (4, 8 or 16; 0 otherwise)
+template <class R>
+size_t tile_geo_words(int side);
+// the geometry blocks of L's regular patches into out ([npatch * words], zeroed by
+// the caller), for tiles of side `side` (sww_tile.cu)
+template <class R>
+cudaError_t build_tile_geo(const DevLevelT<R>& L, int side, R* out, cudaStream_t s);
 // The trend of a stage over all members (sww_tile.cu): the structured kernel over
 // every active patch (parts bit 0), then the tabulated node and Coriolis bodies
 // over the irregular patches (bit 1).  entries and irr_entries bound the members'

@@ -5,12 +5,15 @@
 //   k_tile_trend  one block per active patch at a time (blocks grouped per
 //                 member, striding over the member's all-level list): a regular
 //                 patch runs tile_trend (F, q, div F, K, B, q F^perp from its tile in
-//                 shared memory); an irregular one (a pentagon or a pole within
+//                 shared memory, its geometry block brought in by a bulk copy one
+//                 patch ahead); an irregular one (a pentagon or a pole within
 //                 reach, a level whose patch side differs, the viscous and
 //                 advection forms) gets F and q from the tabulated bodies.
 //   k_tile_irr    div F, K, B and q F^perp at the points of the irregular
 //                 patches (the member's irregular list), from the F and q that
 //                 k_tile_trend wrote for them and their neighbours.
+//   k_tile_geo    the geometry blocks of a level's regular patches (once per grid
+//                 and precision).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,12 +28,14 @@ namespace sww {
 
 namespace {
 
+#include "bulk.cuh"
 #include "sww_bodies.cuh"
 #include "sww_tile.cuh"
 
 constexpr int TILE_TPB = 256;
 constexpr int MAXL = 12;
 constexpr int MAXM = 128;
+constexpr long long COPY_WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz: a bulk copy that has not landed
 
 // the member's level records jmin..jmax into shared memory
 template <class R>
@@ -54,42 +59,29 @@ __global__ void __launch_bounds__(TILE_TPB, tile_min_blocks<P>()) k_tile_trend(B
     const int m = blockIdx.x / bpm, b = blockIdx.x % bpm;
     const MemberRef<R>* mr = a.m + m;
     stage_records(sl, mr, a.jmin);
-    const R H = R(a.H), g = R(a.g);
-    TilePlan<P, TILE_TPB> plan;
-    plan.init();
-    TileCodes<P, TILE_TPB> cur, nxt;
-    const int n = *mr->all_count;
-    if (b < n) {
-        const int32_t ent = mr->all_list[b];
-        const DevLevelT<R>& L = sl[ent >> LVL_SHIFT];
-        if (tile_regular(L, ent & PATCH_MASK)) cur.load(L, ent & PATCH_MASK, plan);
-    }
-    for (int e = b; e < n; e += bpm) {
-        const int32_t ent = mr->all_list[e];
-        const DevLevelT<R>& L = sl[ent >> LVL_SHIFT];
-        const int64_t pat = ent & PATCH_MASK;
-        // the next patch's halo ids, in flight while this one is worked on
-        if (e + bpm < n) {
-            const int32_t ent2 = mr->all_list[e + bpm];
-            const DevLevelT<R>& L2 = sl[ent2 >> LVL_SHIFT];
-            if (tile_regular(L2, ent2 & PATCH_MASK)) nxt.load(L2, ent2 & PATCH_MASK, plan);
-        }
-        if (tile_regular(L, pat)) {
-            tile_trend<R, P, TILE_TPB>(L, pat, H, g, plan, cur, smem);
-        } else {
-            for (int it = threadIdx.x; it < 5 * a.P; it += blockDim.x) {
-                auto body = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t) {
-                    if (kind == K_EDGE)
-                        flux_at(LL, id, H);
-                    else
-                        pv_at(LL, id, H);
-                };
-                visit_item<K_EDGE | K_TRI>(L, pat, uint32_t(it), a.P, body);
-            }
-        }
-        __syncthreads();   // the tile's shared memory is reused by the next patch
-        cur = nxt;
-    }
+    const R H = R(a.H);
+    const int area = a.P;
+    tile_sweep<R, P, TILE_TPB>(sl, mr->all_list, *mr->all_count, b, bpm, H, R(a.g), smem, mr->err, COPY_WAIT_CYCLES,
+                               [&](const DevLevelT<R>& L, int64_t pat) {
+                                   for (int it = threadIdx.x; it < 5 * area; it += blockDim.x) {
+                                       auto body = [&](const DevLevelT<R>& LL, int kind, int64_t id, int64_t) {
+                                           if (kind == K_EDGE)
+                                               flux_at(LL, id, H);
+                                           else
+                                               pv_at(LL, id, H);
+                                       };
+                                       visit_item<K_EDGE | K_TRI>(L, pat, uint32_t(it), area, body);
+                                   }
+                               });
+}
+
+// the geometry block of every regular patch of L (one block per patch)
+template <class R, int P>
+__global__ void __launch_bounds__(TILE_TPB) k_tile_geo(DevLevelT<R> L, R* out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int64_t pat = blockIdx.x;
+    if (pat >= L.npatch || L.tirr[pat]) return;
+    tile_geo_build<R, P, TILE_TPB>(L, pat, out + pat * TileGeo<R, P>::WORDS, reinterpret_cast<R*>(smem));
 }
 
 template <class R>
@@ -120,9 +112,13 @@ cudaError_t launch_trend_p(const BatchArgs<R>& a, int64_t entries, int64_t irr_e
                            cudaStream_t s) {
     constexpr size_t smem = Tile<R, P>::BYTES;
     if (parts & 1) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_trend<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
+    // the dynamic tile and the static level records together may pass the default
+    // 48 KB: the dynamic size is always declared (once)
+    static bool declared = false;
+    if (!declared) {
+        cudaError_t e0 = cudaFuncSetAttribute(k_tile_trend<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e0 != cudaSuccess) return e0;
+        declared = true;
     }
     // blocks per member: one per active patch up to a full GPU over all members
     static int per_sm = 0;   // resident blocks per SM (the same on every GPU of a process here)
@@ -156,13 +152,50 @@ cudaError_t launch_tile_trend(const BatchArgs<R>& a, int64_t entries, int64_t ir
                               cudaStream_t s) {
     if (a.nm < 1 || a.nm > MAXM) return cudaErrorInvalidValue;
     switch (a.P) {
+        case 16: return launch_trend_p<R, 4>(a, entries, irr_entries, nsm, parts, s);
         case 64: return launch_trend_p<R, 8>(a, entries, irr_entries, nsm, parts, s);
         case 256: return launch_trend_p<R, 16>(a, entries, irr_entries, nsm, parts, s);
-        default: return launch_trend_p<R, 4>(a, entries, irr_entries, nsm, parts, s);   // sides 1, 2: no regular tile
+        default: return cudaErrorInvalidValue;   // patch sides are 4, 8 or 16
+    }
+}
+
+namespace {
+template <class R, int P>
+cudaError_t tile_geo_p(const DevLevelT<R>& L, R* out, cudaStream_t s) {
+    constexpr size_t smem = sizeof(R) * 6 * TileGeo<R, P>::NN;   // the kites, for the inverse sums
+    static_assert(smem <= 48 * 1024, "kite scratch");
+    if (L.npatch < 1) return cudaSuccess;
+    count_launch(1);
+    k_tile_geo<R, P><<<unsigned(L.npatch), TILE_TPB, smem, s>>>(L, out);
+    return cudaGetLastError();
+}
+}  // namespace
+
+template <class R>
+size_t tile_geo_words(int side) {
+    switch (side) {
+        case 4: return size_t(TileGeo<R, 4>::WORDS);
+        case 8: return size_t(TileGeo<R, 8>::WORDS);
+        case 16: return size_t(TileGeo<R, 16>::WORDS);
+        default: return 0;
+    }
+}
+
+template <class R>
+cudaError_t build_tile_geo(const DevLevelT<R>& L, int side, R* out, cudaStream_t s) {
+    switch (side) {
+        case 4: return tile_geo_p<R, 4>(L, out, s);
+        case 8: return tile_geo_p<R, 8>(L, out, s);
+        case 16: return tile_geo_p<R, 16>(L, out, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
 template cudaError_t launch_tile_trend<double>(const BatchArgs<double>&, int64_t, int64_t, int, int, cudaStream_t);
 template cudaError_t launch_tile_trend<float>(const BatchArgs<float>&, int64_t, int64_t, int, int, cudaStream_t);
+template size_t tile_geo_words<double>(int);
+template size_t tile_geo_words<float>(int);
+template cudaError_t build_tile_geo<double>(const DevLevelT<double>&, int, double*, cudaStream_t);
+template cudaError_t build_tile_geo<float>(const DevLevelT<float>&, int, float*, cudaStream_t);
 
 }  // namespace sww

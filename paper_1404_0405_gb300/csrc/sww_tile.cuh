@@ -2,25 +2,43 @@
 // the tile of tile.h staged in shared memory, neighbours at constant offsets,
 // the energy-conserving Coriolis weights derived from the kite areas.
 //
-// Included inside an anonymous namespace after sww_bodies.cuh.  All threads of
-// the block call tile_trend together (it synchronises the block).
+// Included inside an anonymous namespace after sww_bodies.cuh and bulk.cuh.  All
+// threads of the block call tile_trend and tile_sweep together (they synchronise
+// the block).
 //
 // Per tile: depth and velocity with their flags over the tile range (velocity
-// signs turned to the local directions), edge lengths d_e and l_e, and for
-// each triangle its three kite areas, its area and its Coriolis parameter --
-// the FP64 geometry rounded to the working precision R as it is staged.  Then
+// signs turned to the local directions), gathered through the patch's halo
+// table; and the patch's geometry block (TileGeo: edge lengths d_e and l_e, for
+// each triangle its three kite areas, its area and its Coriolis parameter, the
+// inverse kite sums of the nodes and the cell areas), the FP64 tables rounded
+// once to the working precision exactly as the stencils round them, brought in
+// whole by one bulk copy while the previous patch is worked on.  Then
 //   F = h_e u at every available edge, q = (curl u + f)/h_v at every available
-//   triangle (kite-weighted h_v), the kite fractions R of every node of
-//   [0, p]^2 (its six kites over their sum);
+//   triangle (kite-weighted h_v);
 //   div F, K and B = g dh + K at the patch's available nodes, and at its live
 //   edges q F^perp = (1/d_e) sum over the ten edges e' of the two cells of
 //   n_{e,i} n_{e',i} (1/2 - sum of the fractions passed counter-clockwise from e
-//   to e') l_{e'} F_{e'} (q_e + q_{e'})/2.
+//   to e') l_{e'} F_{e'} (q_e + q_{e'})/2, a node's kite fractions being its six
+//   kites over their sum.
 // The outputs are those of the tabulated bodies (flux_at, pv_at, node_at,
 // coriolis_at): F at available edges, q at available triangles, c and B at
 // available nodes, Q at live edges, for the patch's own points.
 #pragma once
 // (tile.h is included at file scope by the translation unit)
+
+// Geometry block of one regular patch over the tile's slot ranges, in R: the FP64
+// tables rounded once (geo<R>) to the values the stencils use.  Word offsets:
+// d_e and l_e at edge slots, kite c of triangle slot (t, x) at (3 t + c) NN + x,
+// the inverse kite sum at node slots of [0, P]^2, A_v and f_v at triangle slots,
+// A_i of the patch's own nodes; padded to a multiple of 16 bytes (a bulk copy).
+template <class R, int P>
+struct TileGeo {
+    static constexpr int W = P + 3, NN = W * W, PP = P * P;
+    static constexpr int DE = 0, LE = DE + 3 * NN, KT = LE + 3 * NN, IS = KT + 6 * NN, AV = IS + NN, FV = AV + 2 * NN,
+                         AI = FV + 2 * NN;
+    static constexpr int WORDS = ((AI + PP) * int(sizeof(R)) + 15) / 16 * 16 / int(sizeof(R));
+    static constexpr uint32_t BYTES = uint32_t(WORDS) * uint32_t(sizeof(R));
+};
 
 template <class R, int P>
 struct Tile {
@@ -28,18 +46,18 @@ struct Tile {
     static constexpr int NN = W * W;
     static constexpr tile::Shape S{P};
     static constexpr int HALO = S.halo();
+    using G = TileGeo<R, P>;
+    static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
     // shared-memory layout (bytes)
-    static constexpr size_t OFF_DH = 0;                              // R[NN]
-    static constexpr size_t OFF_U = OFF_DH + sizeof(R) * NN;         // R[3 NN] (local direction)
-    static constexpr size_t OFF_F = OFF_U + sizeof(R) * 3 * NN;      // R[3 NN]
-    static constexpr size_t OFF_DE = OFF_F + sizeof(R) * 3 * NN;     // R[3 NN]
-    static constexpr size_t OFF_LE = OFF_DE + sizeof(R) * 3 * NN;    // R[3 NN]
-    static constexpr size_t OFF_Q = OFF_LE + sizeof(R) * 3 * NN;     // R[2 NN]
-    static constexpr size_t OFF_KT = OFF_Q + sizeof(R) * 2 * NN;     // R[6 NN]: kite c of triangle t at (3t + c) NN
-    static constexpr size_t OFF_IS = OFF_KT + sizeof(R) * 6 * NN;    // R[NN]: 1 / (sum of a node's six kites)
-    static constexpr size_t OFF_NF = OFF_IS + sizeof(R) * NN;        // uint8[NN]
-    static constexpr size_t OFF_EF = OFF_NF + NN;                    // uint8[3 NN]
-    static constexpr size_t BYTES = (OFF_EF + 3 * NN + 15) / 16 * 16;
+    static constexpr size_t OFF_GEO = 0;                                 // R[2][G::WORDS]: two geometry buffers
+    static constexpr size_t OFF_DH = OFF_GEO + 2 * size_t(G::BYTES);     // R[NN]
+    static constexpr size_t OFF_U = OFF_DH + sizeof(R) * NN;             // R[3 NN] (local direction)
+    static constexpr size_t OFF_F = OFF_U + sizeof(R) * 3 * NN;          // R[3 NN]
+    static constexpr size_t OFF_Q = OFF_F + sizeof(R) * 3 * NN;          // R[2 NN]
+    static constexpr size_t OFF_BAR = up16(OFF_Q + sizeof(R) * 2 * NN);  // uint64[2]: the buffers' mbarriers
+    static constexpr size_t OFF_NF = OFF_BAR + 16;                       // uint8[NN]
+    static constexpr size_t OFF_EF = OFF_NF + NN;                        // uint8[3 NN]
+    static constexpr size_t BYTES = up16(OFF_EF + 3 * NN);
 
     __device__ static int at(int a, int b) { return (a + 1) * W + (b + 1); }
 };
@@ -171,37 +189,114 @@ struct TileCodes {
     }
 };
 
+// Edge e and its direction flip (halo) of edge slot code c, codes entry hc.
+template <int P>
+__device__ __forceinline__ int32_t slot_edge(int c, int32_t hc, int32_t nelem, int32_t base, bool& rev) {
+    constexpr int PP = P * P;
+    if (c < 0) {
+        const int k = -c - 1, o = k / PP;
+        rev = false;
+        return o * nelem + base + (k - o * PP);
+    }
+    rev = hc & 1;
+    return hc >> 1;
+}
+
+// The geometry block of regular patch `pat` of L into out (all threads of one
+// block; kt: shared scratch of 6 NN values).  Each value is rounded from the FP64
+// tables by geo<R>; the inverse kite sums are summed in the order tile_trend used
+// to sum them.
 template <class R, int P, int NT>
-__device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const TilePlan<P, NT>& plan,
-                           const TileCodes<P, NT>& codes, unsigned char* smem) {
+__device__ void tile_geo_build(const DevLevelT<R>& L, int64_t pat, R* __restrict__ out, R* kt) {
+    using G = TileGeo<R, P>;
+    using PL = TilePlan<P, NT>;
+    constexpr int W = G::W, NN = G::NN, PP = G::PP;
+    PL plan;
+    plan.init();
+    TileCodes<P, NT> codes;
+    codes.load(L, pat, plan);
+    const int32_t nelem = int32_t(L.nelem), ntri = int32_t(L.T), base = int32_t(pat) * PP;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < PL::SE; ++i) {
+        const int c = plan.e[i], y = tid + i * NT;
+        if (c == PL::NONE) continue;
+        bool rev;
+        const int32_t e = slot_edge<P>(c, codes.e[i], nelem, base, rev);
+        out[G::DE + y] = geo<R>(L.d_e, e);
+        out[G::LE + y] = geo<R>(L.l_e, e);
+    }
+#pragma unroll
+    for (int i = 0; i < PL::ST; ++i) {
+        const int c = plan.t[i], z = tid + i * NT;
+        if (c == PL::NONE) continue;
+        int32_t tr;
+        int sft;
+        if (c < 0) {
+            const int k = -c - 1, t = k / PP;
+            tr = t * nelem + base + (k - t * PP);
+            sft = 0;
+        } else {
+            tr = codes.t[i] >> 2;
+            sft = codes.t[i] & 3;
+        }
+        const int t = z / NN, x = z - t * NN;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+            const int gc = cc + sft < 3 ? cc + sft : cc + sft - 3;
+            const R k = geo<R>(L.kite, int64_t(gc) * ntri + tr);
+            kt[(3 * t + cc) * NN + x] = k;
+            out[G::KT + (3 * t + cc) * NN + x] = k;
+        }
+        out[G::AV + z] = geo<R>(L.A_v, tr);
+        out[G::FV + z] = geo<R>(L.f_v, tr);
+    }
+    __syncthreads();
+    for (int x = tid; x < NN; x += NT) {
+        const int a = x / W - 1, b = x % W - 1;
+        if (a < 0 || b < 0 || a > P || b > P) continue;
+        // the node's six kites: t0 (a,b) vertex 0, t1 (a,b) 0, t0 (a-1,b) 1,
+        // t1 (a-1,b-1) 1, t0 (a-1,b-1) 2, t1 (a,b-1) 2
+        R s = R(0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s += kt[kite_off<W, NN>(k) + x];
+        out[G::IS + x] = R(1) / s;
+    }
+    for (int i = tid; i < PP; i += NT) out[G::AI + i] = geo<R>(L.A_i, base + i);
+}
+
+// The trend of one regular tile (all threads of the block): its fields gathered
+// into the tile, its geometry block already in `geo` (shared memory) when `ok`.
+// False, for every thread, when some thread's `ok` is false (nothing is computed).
+template <class R, int P, int NT>
+__device__ bool tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const TilePlan<P, NT>& plan,
+                           const TileCodes<P, NT>& codes, unsigned char* smem, const R* geo, bool ok) {
     using T = Tile<R, P>;
+    using G = TileGeo<R, P>;
     using PL = TilePlan<P, NT>;
     constexpr int W = T::W, NN = T::NN, PP = P * P;
     R* __restrict__ dh = reinterpret_cast<R*>(smem + T::OFF_DH);
     R* __restrict__ u = reinterpret_cast<R*>(smem + T::OFF_U);
     R* __restrict__ F = reinterpret_cast<R*>(smem + T::OFF_F);
-    R* __restrict__ de = reinterpret_cast<R*>(smem + T::OFF_DE);
-    R* __restrict__ le = reinterpret_cast<R*>(smem + T::OFF_LE);
     R* __restrict__ q = reinterpret_cast<R*>(smem + T::OFF_Q);
-    R* __restrict__ kt = reinterpret_cast<R*>(smem + T::OFF_KT);
-    R* __restrict__ is = reinterpret_cast<R*>(smem + T::OFF_IS);
     uint8_t* __restrict__ nf = smem + T::OFF_NF;
     uint8_t* __restrict__ ef = smem + T::OFF_EF;
+    const R* __restrict__ de = geo + G::DE;
+    const R* __restrict__ le = geo + G::LE;
+    const R* __restrict__ kt = geo + G::KT;
+    const R* __restrict__ is = geo + G::IS;
+    const R* __restrict__ av = geo + G::AV;
+    const R* __restrict__ fv = geo + G::FV;
+    const R* __restrict__ ai = geo + G::AI;
     // the level's fields, read once from its record (which sits in shared memory)
-    const int32_t nelem = int32_t(L.nelem), ntri = int32_t(L.T);
+    const int32_t nelem = int32_t(L.nelem);
     const R* __restrict__ g_dh = L.dh;
     const R* __restrict__ g_u = L.u;
     const uint8_t* __restrict__ g_nf = L.nflag;
     const uint8_t* __restrict__ g_ef = L.eflag;
-    const double* __restrict__ g_de = L.d_e;
-    const double* __restrict__ g_le = L.l_e;
-    const double* __restrict__ g_kite = L.kite;
-    const double* __restrict__ g_av = L.A_v;
-    const double* __restrict__ g_fv = L.f_v;
     const int32_t base = int32_t(pat) * PP;
     const int tid = threadIdx.x;
-    // --- stage: nodes, edges (velocity turned to the local direction), triangles
-    // (their area and Coriolis parameter kept in registers for q)
+    // --- stage: nodes, edges (velocity turned to the local direction)
 #pragma unroll
     for (int i = 0; i < PL::SN; ++i) {
         const int c = plan.n[i];
@@ -218,51 +313,14 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             if (y < 3 * NN) ef[y] = 0;
             continue;
         }
-        int32_t e;
         bool rev;
-        if (c < 0) {
-            const int k = -c - 1, o = k / PP;
-            e = o * nelem + base + (k - o * PP);
-            rev = false;
-        } else {
-            const int32_t code = codes.e[i];
-            e = code >> 1;
-            rev = code & 1;
-        }
+        const int32_t e = slot_edge<P>(c, codes.e[i], nelem, base, rev);
         const R ue = g_u[e];
         u[y] = rev ? -ue : ue;
         ef[y] = g_ef[e];
-        de[y] = geo<R>(g_de, e);
-        le[y] = geo<R>(g_le, e);
     }
-    R tav[PL::ST], tfv[PL::ST];
-#pragma unroll
-    for (int i = 0; i < PL::ST; ++i) {
-        const int c = plan.t[i], z = tid + i * NT;
-        tav[i] = R(1), tfv[i] = R(0);
-        if (c == PL::NONE) continue;
-        int32_t tr;
-        int sft;
-        if (c < 0) {
-            const int k = -c - 1, t = k / PP;
-            tr = t * nelem + base + (k - t * PP);
-            sft = 0;
-        } else {
-            const int32_t code = codes.t[i];
-            tr = code >> 2;
-            sft = code & 3;
-        }
-        const int t = z / NN, x = z - t * NN;
-#pragma unroll
-        for (int cc = 0; cc < 3; ++cc) {
-            const int gc = cc + sft < 3 ? cc + sft : cc + sft - 3;
-            kt[(3 * t + cc) * NN + x] = geo<R>(g_kite, int64_t(gc) * ntri + tr);
-        }
-        tav[i] = geo<R>(g_av, tr);
-        tfv[i] = geo<R>(g_fv, tr);
-    }
-    __syncthreads();
-    // --- F at edges, q at triangles, the kite sums of the nodes of [0, P]^2
+    if (!__syncthreads_and(ok)) return false;
+    // --- F at edges, q at triangles
 #pragma unroll
     for (int i = 0; i < PL::SE; ++i) {
         const int y = tid + i * NT;
@@ -294,23 +352,11 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             const R circ = u[s0] * de[s0] + (t == 0 ? R(1) : R(-1)) * u[s1] * de[s1] + R(-1) * u[s2] * de[s2];
             const R hv = kt[(3 * t) * NN + x] * (H + dh[x]) + kt[(3 * t + 1) * NN + x] * (H + dh[n1]) +
                          kt[(3 * t + 2) * NN + x] * (H + dh[n2]);
-            qq = (circ / tav[i] + tfv[i]) / (hv / tav[i]);
+            const R A = av[z];
+            qq = (circ / A + fv[z]) / (hv / A);
             if (c < 0) L.q[t * nelem + base + (-c - 1 - t * PP)] = qq;
         }
         q[z] = qq;
-    }
-#pragma unroll
-    for (int i = 0; i < PL::SN; ++i) {
-        const int x = tid + i * NT;
-        if (x >= NN) continue;
-        const int a = x / W - 1, b = x % W - 1;
-        if (a < 0 || b < 0 || a > P || b > P) continue;
-        // the node's six kites: t0 (a,b) vertex 0, t1 (a,b) 0, t0 (a-1,b) 1,
-        // t1 (a-1,b-1) 1, t0 (a-1,b-1) 2, t1 (a,b-1) 2
-        R s = R(0);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) s += kt[kite_off<W, NN>(k) + x];
-        is[x] = R(1) / s;
     }
     __syncthreads();
     // --- the patch's own nodes (div F, K, B) and live edges (energy-conserving
@@ -320,19 +366,19 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
         if (w < PP) {
             const int i = w, x = T::at(i / P, i % P);
             if (!(nf[x] & AVAIL)) continue;
-            bool ok = true;
+            bool okr = true;
             R div = R(0), ke = R(0);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 const int y = x + ring_edge_off<W, NN>(k);
-                ok = ok && (ef[y] & AVAIL);
+                okr = okr && (ef[y] & AVAIL);
                 const R n = k < 3 ? R(1) : R(-1);
                 div += n * F[y] * le[y];
                 ke += R(0.25) * le[y] * de[y] * u[y] * u[y];
             }
-            if (!ok) continue;
+            if (!okr) continue;
             const int32_t v = base + i;
-            const R A = geo<R>(L.A_i, v);
+            const R A = ai[i];
             L.c[v] = div / A;
             L.B[v] = g * dh[x] + ke / A;
         } else {
@@ -344,4 +390,68 @@ __device__ void tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
             L.Q[o * nelem + base + i] = Q;
         }
     }
+    return true;
+}
+
+// The trend of the active patches first, first + stride, ... (< n) of an
+// all-level list, by one block: regular patches by tile_trend, each one's
+// geometry block brought in by a bulk copy started while the block works on the
+// patch before (two buffers, one mbarrier each); other patches by other(L, pat).
+// False, with *err set, when a copy did not complete within `limit` cycles (the
+// block then waits, again at most `limit`, for the copy it started next, and
+// leaves).
+template <class R, int P, int NT, class Other>
+__device__ bool tile_sweep(const DevLevelT<R>* lv, const int32_t* list, int n, int first, int stride, R H, R g,
+                           unsigned char* smem, int* err, long long limit, Other other) {
+    using T = Tile<R, P>;
+    using G = TileGeo<R, P>;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + T::OFF_BAR);
+    R* gbuf = reinterpret_cast<R*>(smem + T::OFF_GEO);
+    if (threadIdx.x == 0) {
+        mbar_init(bar);
+        mbar_init(bar + 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    TilePlan<P, NT> plan;
+    plan.init();
+    TileCodes<P, NT> cur, nxt;
+    // list entry e: when its tile is regular, its halo ids into c and the bulk copy
+    // of its geometry block into buffer k started
+    auto start = [&](int e, int k, TileCodes<P, NT>& c) -> bool {
+        const int32_t ent = list[e];
+        const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
+        const int64_t pat = ent & PATCH_MASK;
+        if (!tile_regular(L, pat)) return false;
+        c.load(L, pat, plan);
+        if (threadIdx.x == 0) {
+            fence_async_shared();   // the buffer's last readers are behind the block barrier
+            bulk_load(gbuf + k * G::WORDS, L.tgeo + pat * G::WORDS, G::BYTES, bar + k);
+        }
+        return true;
+    };
+    unsigned ph = 0;   // bit k: parity of buffer k's next phase
+    bool reg = first < n && start(first, 0, cur);
+    int k = 0;
+    for (int e = first; e < n; e += stride, k ^= 1) {
+        const int32_t ent = list[e];
+        const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
+        const int64_t pat = ent & PATCH_MASK;
+        const bool reg_next = e + stride < n && start(e + stride, k ^ 1, nxt);
+        if (reg) {
+            const bool ok = mbar_wait(bar + k, (ph >> k) & 1u, limit);
+            ph ^= 1u << k;
+            if (!tile_trend<R, P, NT>(L, pat, H, g, plan, cur, smem, gbuf + k * G::WORDS, ok)) {
+                if (threadIdx.x == 0) atomicExch(err, 1);
+                if (reg_next) mbar_wait(bar + (k ^ 1), (ph >> (k ^ 1)) & 1u, limit);
+                return false;
+            }
+        } else {
+            other(L, pat);
+        }
+        __syncthreads();   // the tile's shared memory is reused by the next patch
+        cur = nxt;
+        reg = reg_next;
+    }
+    return true;
 }

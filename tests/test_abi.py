@@ -52,7 +52,8 @@ def test_error_path_without_compute():
 def test_config_checks_without_compute():
     """Each configuration field out of its range is refused before any device
     call: the prescribed-velocity flag, the threshold regime, the stage mode,
-    a zero mean depth without a prescribed velocity, a negative viscosity."""
+    a zero mean depth without a prescribed velocity, a negative viscosity, a
+    negative eps, a patch side other than 4, 8 or 16."""
     import ctypes
     import paper_1404_0405_gb300 as sww
     lib = sww.load()
@@ -66,7 +67,8 @@ def test_config_checks_without_compute():
     h = ctypes.c_void_p()
     buf = ctypes.create_string_buffer(256)
     for kw, word in [({"advect": 2}, b"advect"), ({"regime": 3}, b"regime"), ({"persistent": 4}, b"persistent"),
-                     ({"H": 0.0}, b"H"), ({"nu": -1.0}, b"nu"), ({"eps": -1.0}, b"eps")]:
+                     ({"H": 0.0}, b"H"), ({"nu": -1.0}, b"nu"), ({"eps": -1.0}, b"eps"),
+                     ({"patch": 2}, b"patch"), ({"patch": 32}, b"patch")]:
         assert lib.sww_create(ctypes.byref(cfg(**kw)), None, ctypes.byref(h)) == -1, kw
         lib.sww_last_error(buf, 256)
         assert word in buf.value, (kw, buf.value)
