@@ -1,8 +1,10 @@
-// One-dimensional bulk copies from global to shared memory by the tensor memory
-// accelerator (cp.async.bulk), each completing on an mbarrier in shared memory
-// (PTX ISA: cp.async.bulk, mbarrier).  A copy moves a multiple of 16 bytes between
-// 16-byte aligned addresses.  Waits are bounded: a wait that does not see its
-// phase complete within `limit` clock cycles returns false.
+// Asynchronous copies from global to shared memory (PTX ISA: cp.async.bulk,
+// mbarrier, cp.async).  One-dimensional bulk copies by the tensor memory
+// accelerator complete on an mbarrier in shared memory; a bulk copy moves a
+// multiple of 16 bytes between 16-byte aligned addresses, and the waits on its
+// mbarrier are bounded (a wait that does not see its phase complete within
+// `limit` clock cycles returns false).  Element copies (4 or 8 bytes) complete
+// per thread.
 #pragma once
 #include <cstdint>
 
@@ -55,3 +57,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
         if (clock64() - t0 > limit) return false;
     }
 }
+
+// Element copies from global to shared memory that do not hold the issuing thread
+// (cp.async, size 4 or 8 bytes, both addresses aligned to it); a thread's copies
+// are grouped by async_commit and waited for by async_wait_all.
+template <int BYTES>
+__device__ __forceinline__ void async_copy(void* dst, const void* src) {
+    static_assert(BYTES == 4 || BYTES == 8, "element copy size");
+    if constexpr (BYTES == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }

@@ -464,9 +464,12 @@ void alloc_state(sww_handle* h, int j) {
     D.nu = h->cfg.nu;
     D.advect = h->cfg.advect;
     D.ue = h->alloc<R>(coarse_E);
+    // byte arrays padded to a multiple of 16 bytes (zeroed): the structured trend
+    // copies the aligned 32-bit word holding a flag
+    const int64_t N16 = (N + 15) / 16 * 16, E16 = (E + 15) / 16 * 16;
     uint8_t** bN[] = {&D.nflag, &D.sig, &D.tmask, &D.band0, &D.band1};
-    for (auto p : bN) *p = h->alloc<uint8_t>(N);
-    D.eflag = h->alloc<uint8_t>(E);
+    for (auto p : bN) *p = h->alloc<uint8_t>(N16);
+    D.eflag = h->alloc<uint8_t>(E16);
     D.pflag = h->alloc<uint8_t>(D.npatch);
     ck(cudaMemset(D.pflag, 0, D.npatch), "memset");
     D.pfeat = h->alloc<float>(NF * (D.npatch + 1));
@@ -494,8 +497,8 @@ void alloc_state(sww_handle* h, int j) {
     for (auto p : dN) ck(cudaMemset(*p, 0, N * sizeof(R)), "memset");
     for (auto p : dE) ck(cudaMemset(*p, 0, E * sizeof(R)), "memset");
     ck(cudaMemset(D.q, 0, T * sizeof(R)), "memset");
-    for (auto p : bN) ck(cudaMemset(*p, 0, N), "memset");
-    ck(cudaMemset(D.eflag, 0, E), "memset");
+    for (auto p : bN) ck(cudaMemset(*p, 0, N16), "memset");
+    ck(cudaMemset(D.eflag, 0, E16), "memset");
     ck(cudaMemset(D.ue, 0, coarse_E * sizeof(R)), "memset");
     ck(cudaMemset(D.npatches, 0, sizeof(int32_t)), "memset");
     lvl<R>(h)[j] = D;

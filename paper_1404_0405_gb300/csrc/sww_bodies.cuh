@@ -222,9 +222,14 @@ template <class R>
 __device__ __forceinline__ bool restricted_div_node(const DevLevelT<R>& L, int64_t v) {
     const uint8_t f = L.nflag[v];
     if (!(f & AVAIL)) return false;
-    bool d = (f & COVERED) != 0;
-    for (int k = 0; k < L.deg[v] && !d; ++k) d = (L.nflag[L.ring_n[k * L.N + v]] & COVERED) != 0;
-    return d;
+    if (f & COVERED) return true;
+    // the neighbours' flags, their loads issued together (no early exit)
+    const int dg = L.deg[v];
+    uint8_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        if (k < dg) acc |= L.nflag[L.ring_n[k * L.N + v]];
+    return (acc & COVERED) != 0;
 }
 
 // divergence, kinetic energy and Bernoulli function at a node
@@ -460,9 +465,19 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
 // significance at level F (Sec. 2.3): odd node with |h~| >= eps_h; both ends of an
 // interior edge with |u~| >= eps_u; both ends and the midpoint of a coarse edge with
 // |u~_E| >= eps_u; only points live before the adaptation carry coefficients
+// The significance threshold e (FP64) as a threshold of the field type: the least
+// R value >= e, so that |x| >= e and |x| >= sig_thr<R>(e) agree for every x of type
+// R (infinity and NaN included); the tests below then compare in R.
 template <class R>
-__device__ __forceinline__ bool sig_node(const DevLevelT<R>& F, int64_t i, double eh) {
-    if (F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(double(F.hdet[i])) >= eh) {
+__device__ __forceinline__ R sig_thr(double e);
+template <>
+__device__ __forceinline__ double sig_thr<double>(double e) { return e; }
+template <>
+__device__ __forceinline__ float sig_thr<float>(double e) { return __double2float_ru(e); }
+
+template <class R>
+__device__ __forceinline__ bool sig_node(const DevLevelT<R>& F, int64_t i, R eh) {
+    if (F.f2c[i] < 0 && (F.nflag[i] & LIVE) && fabs(F.hdet[i]) >= eh) {
         F.sig[i] = 1;
         return true;
     }
@@ -470,8 +485,8 @@ __device__ __forceinline__ bool sig_node(const DevLevelT<R>& F, int64_t i, doubl
 }
 
 template <class R>
-__device__ __forceinline__ bool sig_edge(const DevLevelT<R>& F, int64_t i, double eu) {
-    if (F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(double(F.ui[i])) >= eu) {
+__device__ __forceinline__ bool sig_edge(const DevLevelT<R>& F, int64_t i, R eu) {
+    if (F.fe_kind[i] == 2 && (F.eflag[i] & LIVE) && fabs(F.ui[i]) >= eu) {
         F.sig[F.en[i]] = 1;
         F.sig[F.en[F.E + i]] = 1;
         return true;
@@ -480,9 +495,9 @@ __device__ __forceinline__ bool sig_edge(const DevLevelT<R>& F, int64_t i, doubl
 }
 
 template <class R>
-__device__ __forceinline__ bool sig_cedge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i, double eu) {
+__device__ __forceinline__ bool sig_cedge(const DevLevelT<R>& F, const DevLevelT<R>& C, int64_t i, R eu) {
     const int32_t h0 = C.half[i], h1 = C.half[C.E + i];
-    if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(double(F.ue[i])) >= eu) {
+    if (((F.eflag[h0] & LIVE) || (F.eflag[h1] & LIVE)) && fabs(F.ue[i]) >= eu) {
         F.sig[C.c2f[C.en[i]]] = 1;
         F.sig[C.c2f[C.en[C.E + i]]] = 1;
         F.sig[C.mid[i]] = 1;
@@ -496,16 +511,23 @@ __device__ __forceinline__ bool sig_cedge(const DevLevelT<R>& F, const DevLevelT
 // recorded per patch for the proposal's statistics)
 template <class R>
 __device__ __forceinline__ void adjacent_node(const DevLevelT<R>& F, const DevLevelT<R>& C, bool children, int64_t x) {
-    const int dg = F.deg[x];
+    // significance bytes are 0 or 1; each group of loads is issued together
     uint8_t t = F.sig[x];
-    for (int k = 0; k < dg && !t; ++k) t = F.sig[F.ring_n[k * F.N + x]];
-    if (!t && children) {
-        const int32_t cx = F.f2c[x];
-        if (cx >= 0 && C.sig[cx]) t = 1;
-        for (int k = 0; k < dg && !t; ++k) {
-            const int32_t y = F.ring_n[k * F.N + x];
-            const int32_t cy = F.f2c[y];
-            if (cy >= 0 && C.sig[cy]) t = 1;
+    if (!t) {
+        const int dg = F.deg[x];
+        int32_t y[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) y[k] = k < dg ? F.ring_n[k * F.N + x] : int32_t(x);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) t |= F.sig[y[k]];
+        if (!t && children) {
+            int32_t cy[7];
+            cy[6] = F.f2c[x];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cy[k] = F.f2c[y[k]];
+#pragma unroll
+            for (int k = 0; k < 7; ++k)
+                if (cy[k] >= 0) t |= C.sig[cy[k]];
         }
     }
     const int64_t P = x < F.nelem ? x / (F.p * F.p) : F.npatch;
@@ -552,9 +574,14 @@ template <class R>
 __device__ __forceinline__ void dilate_node(const DevLevelT<R>& L, int64_t x, bool forward) {
     const uint8_t* __restrict__ in = forward ? L.band0 : L.band1;
     uint8_t* __restrict__ out = forward ? L.band1 : L.band0;
+    // band bytes are 0 or 1; the neighbours' loads are issued together
     uint8_t t = in[x];
-    const int dg = L.deg[x];
-    for (int k = 0; k < dg && !t; ++k) t = in[L.ring_n[k * L.N + x]];
+    if (!t) {
+        const int dg = L.deg[x];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (k < dg) t |= in[L.ring_n[k * L.N + x]];
+    }
     out[x] = t;
 }
 

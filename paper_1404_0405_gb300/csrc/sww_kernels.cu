@@ -420,9 +420,10 @@ __global__ void k_sig(const DevLevelT<R>* __restrict__ lvs, Span sp, const doubl
         const DevLevelT<R>& F = lvs[j];
         const DevLevelT<R>& C = lvs[j - 1];
         bool any = false;
-        if (i < F.N) any |= sig_node(F, i, thr[0]);
-        if (i < F.E) any |= sig_edge(F, i, thr[1]);
-        if (i < C.E) any |= sig_cedge(F, C, i, thr[1]);
+        const R eh = sig_thr<R>(thr[0]), eu = sig_thr<R>(thr[1]);
+        if (i < F.N) any |= sig_node(F, i, eh);
+        if (i < F.E) any |= sig_edge(F, i, eu);
+        if (i < C.E) any |= sig_cedge(F, C, i, eu);
         if (any) sig_any[j] = 1;
     });
 }

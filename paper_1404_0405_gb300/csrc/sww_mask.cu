@@ -56,7 +56,8 @@ __device__ __forceinline__ bool span_find(const Span& sp, int64_t t, int& j, int
     return false;
 }
 
-__device__ __forceinline__ float feat_log(double x) { return float(log2(1.0 + x)); }
+// log2(1 + x) of a feature ratio, in FP32 (the features are FP32 values)
+__device__ __forceinline__ float feat_log(float x) { return log2f(1.0f + x); }
 
 // ------------------------------------------------------------------ learned proposal
 
@@ -116,7 +117,8 @@ __global__ void k_feat_own(const __grid_constant__ MaskBatch<R, CAP> B) {
     if (!M.learn) return;
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const double* thr = M.thr;
+    // the thresholds once per thread, in FP32
+    const float eh = float(M.thr[0] > 0 ? M.thr[0] : 1.0), eu = float(M.thr[1] > 0 ? M.thr[1] : 1.0);
     for (int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; w < *M.active_count; w += nw) {
         const int32_t ent = M.active[w];
         const int j = ent >> LVL_SHIFT;
@@ -154,9 +156,8 @@ __global__ void k_feat_own(const __grid_constant__ MaskBatch<R, CAP> B) {
             live += __shfl_xor_sync(0xffffffffu, live, o);
         }
         if (lane == 0) {
-            const double eh = thr[0] > 0 ? thr[0] : 1.0, eu = thr[1] > 0 ? thr[1] : 1.0;
-            L.pfeat[0 * np1 + P] = feat_log(double(mh) / eh);
-            L.pfeat[1 * np1 + P] = feat_log(double(mu) / eu);
+            L.pfeat[0 * np1 + P] = feat_log(float(mh) / eh);
+            L.pfeat[1 * np1 + P] = feat_log(float(mu) / eu);
             L.pfeat[6 * np1 + P] = float(live) / float(nn);
         }
     }
@@ -178,11 +179,20 @@ __global__ void k_feat_ctx(const __grid_constant__ MaskBatch<R, CAP> B) {
     float f2 = 0, f3 = 0, f4 = 0, f5 = 0;
     const int32_t cp = L.ppar[P];
     if (j - 1 > B.ja && cp >= 0) f2 = C.pfeat[0 * cnp1 + cp], f3 = C.pfeat[1 * cnp1 + cp];
-    for (int k = 0; k < NB; ++k) {
-        const int32_t Q = L.pnbr[k * np1 + P];
-        if (Q < 0) break;
-        f4 = fmaxf(f4, L.pfeat[0 * np1 + Q]);
-        f5 = fmaxf(f5, L.pfeat[1 * np1 + Q]);
+    // the neighbours eight at a time, each group's loads issued together (max is
+    // order-independent)
+#pragma unroll
+    for (int k0 = 0; k0 < NB; k0 += 8) {
+        int32_t Q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Q[k] = L.pnbr[(k0 + k) * np1 + P];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (Q[k] >= 0) {
+                f4 = fmaxf(f4, L.pfeat[0 * np1 + Q[k]]);
+                f5 = fmaxf(f5, L.pfeat[1 * np1 + Q[k]]);
+            }
+        if (Q[7] < 0) break;
     }
     L.pfeat[2 * np1 + P] = f2;
     L.pfeat[3 * np1 + P] = f3;
@@ -242,7 +252,7 @@ __global__ void k_sig_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
     DevLevelT<R> none{};
     const DevLevelT<R>* lvs = M.lvs;
-    const double eh = M.thr[0], eu = M.thr[1];
+    const R eh = sig_thr<R>(M.thr[0]), eu = sig_thr<R>(M.thr[1]);
     int32_t* sig_any = M.sig_any;
     ITEMS(K_NODE | K_EDGE | K_CEDGE, lvs, none, M.active, M.active_count, B.P) {
         if (L.J == B.ja) return;
@@ -286,6 +296,25 @@ __global__ void k_seed(const __grid_constant__ MaskBatch<R, CAP> B) {
     }
 }
 
+// whether a neighbour patch of P (pnbr, -1 padded) has its byte set in `in` (bytes
+// 0 or 1): the neighbours read eight at a time, each group's loads issued together
+template <class Lv>
+__device__ __forceinline__ uint8_t nbr_any(const Lv& L, int64_t P, int64_t np1, const uint8_t* in) {
+    static_assert(NB % 8 == 0, "neighbour groups");
+    uint8_t c = 0;
+#pragma unroll
+    for (int k0 = 0; k0 < NB; k0 += 8) {
+        int32_t Q[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Q[k] = L.pnbr[(k0 + k) * np1 + P];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (Q[k] >= 0) c |= in[Q[k]];
+        if (c || Q[7] < 0) break;
+    }
+    return c;
+}
+
 // one ring around the flagged patches of level j: out = in + neighbours of in.  The
 // final pass writes the candidates and marks the patch under each candidate as a
 // seed of level j-1.  `all`: every patch is a candidate.
@@ -299,11 +328,7 @@ __global__ void k_ring(const __grid_constant__ MaskBatch<R, CAP> B, int j, int s
     const int64_t np1 = L.npatch + 1;
     const uint8_t* in = src == 0 ? L.zflag : L.gflag;
     uint8_t c = all ? 1 : in[P];
-    for (int k = 0; k < NB && !c; ++k) {
-        const int32_t Q = L.pnbr[k * np1 + P];
-        if (Q < 0) break;
-        c = in[Q];
-    }
+    if (!c) c = nbr_any(L, P, np1, in);
     if (final_pass) {
         L.cflag[P] = c;
         if (c && push && L.ppar[P] >= 0) M.lvs[j - 1].zflag[L.ppar[P]] = 1;
@@ -325,11 +350,7 @@ __global__ void k_gring(const __grid_constant__ MaskBatch<R, CAP> B, int pass) {
     const int64_t np1 = L.npatch + 1;
     const uint8_t* in = pass == 0 ? L.lflag : L.cflag;
     uint8_t c = j == B.ja ? 1 : in[P];
-    for (int k = 0; k < NB && !c; ++k) {
-        const int32_t Q = L.pnbr[k * np1 + P];
-        if (Q < 0) break;
-        c = in[Q];
-    }
+    if (!c) c = nbr_any(L, P, np1, in);
     (pass == 0 && B.rings == 2 ? L.cflag : L.gflag)[P] = c;
 }
 

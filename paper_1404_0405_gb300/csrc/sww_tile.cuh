@@ -7,8 +7,9 @@
 // the block).
 //
 // Per tile: depth and velocity with their flags over the tile range (velocity
-// signs turned to the local directions), gathered through the patch's halo
-// table; and the patch's geometry block (TileGeo: edge lengths d_e and l_e, for
+// signs turned to the local directions), copied asynchronously through the
+// patch's halo table while the previous patch is worked on; and the patch's
+// geometry block (TileGeo: edge lengths d_e and l_e, for
 // each triangle its three kite areas, its area and its Coriolis parameter, the
 // inverse kite sums of the nodes and the cell areas), the FP64 tables rounded
 // once to the working precision exactly as the stencils round them, brought in
@@ -48,16 +49,20 @@ struct Tile {
     static constexpr int HALO = S.halo();
     using G = TileGeo<R, P>;
     static constexpr size_t up16(size_t x) { return (x + 15) / 16 * 16; }
-    // shared-memory layout (bytes)
-    static constexpr size_t OFF_GEO = 0;                                 // R[2][G::WORDS]: two geometry buffers
-    static constexpr size_t OFF_DH = OFF_GEO + 2 * size_t(G::BYTES);     // R[NN]
-    static constexpr size_t OFF_U = OFF_DH + sizeof(R) * NN;             // R[3 NN] (local direction)
-    static constexpr size_t OFF_F = OFF_U + sizeof(R) * 3 * NN;          // R[3 NN]
-    static constexpr size_t OFF_Q = OFF_F + sizeof(R) * 3 * NN;          // R[2 NN]
-    static constexpr size_t OFF_BAR = up16(OFF_Q + sizeof(R) * 2 * NN);  // uint64[2]: the buffers' mbarriers
-    static constexpr size_t OFF_NF = OFF_BAR + 16;                       // uint8[NN]
-    static constexpr size_t OFF_EF = OFF_NF + NN;                        // uint8[3 NN]
-    static constexpr size_t BYTES = up16(OFF_EF + 3 * NN);
+    // shared-memory layout (bytes): two geometry buffers and two buffers of staged
+    // fields (patch i of a block's sweep uses buffers i mod 2), F and q, the
+    // geometry buffers' mbarriers
+    static constexpr size_t OFF_GEO = 0;   // R[2][G::WORDS]
+    // staged fields: dh[NN], u[3 NN] (local direction), the flag words as copied
+    // nfw[NN], efw[3 NN] (uint32), the flags nf[NN], ef[3 NN]
+    static constexpr size_t STAGED = up16(sizeof(R) * 4 * NN + 4 * 4 * NN + 4 * NN);
+    static constexpr size_t OFF_STG = OFF_GEO + 2 * size_t(G::BYTES);   // [2][STAGED]
+    static constexpr size_t ST_DH = 0, ST_U = sizeof(R) * NN, ST_NFW = sizeof(R) * 4 * NN, ST_EFW = ST_NFW + 4 * NN,
+                            ST_NF = ST_EFW + 4 * 3 * NN, ST_EF = ST_NF + NN;
+    static constexpr size_t OFF_F = OFF_STG + 2 * STAGED;                 // R[3 NN]
+    static constexpr size_t OFF_Q = OFF_F + sizeof(R) * 3 * NN;           // R[2 NN]
+    static constexpr size_t OFF_BAR = up16(OFF_Q + sizeof(R) * 2 * NN);   // uint64[2]
+    static constexpr size_t BYTES = OFF_BAR + 16;
 
     __device__ static int at(int a, int b) { return (a + 1) * W + (b + 1); }
 };
@@ -106,7 +111,9 @@ struct TilePlan {
 // with the velocity free (the viscous and advection forms take the tabulated path)
 template <class R>
 __device__ __forceinline__ bool tile_regular(const DevLevelT<R>& L, int64_t pat) {
-    return pat < L.npatch && L.thalo != nullptr && L.tirr[pat] == 0 && L.nu == 0.0 && !L.advect;
+    // nu == 0 tested on its bits (either sign of zero), on the integer pipe
+    return pat < L.npatch && L.thalo != nullptr && L.tirr[pat] == 0 &&
+           (static_cast<unsigned long long>(__double_as_longlong(L.nu)) << 1) == 0 && !L.advect;
 }
 
 // position (a, b) of tile slot x = (a + 1) W + (b + 1)
@@ -265,22 +272,70 @@ __device__ void tile_geo_build(const DevLevelT<R>& L, int64_t pat, R* __restrict
     for (int i = tid; i < PP; i += NT) out[G::AI + i] = geo<R>(L.A_i, base + i);
 }
 
-// The trend of one regular tile (all threads of the block): its fields gathered
-// into the tile, its geometry block already in `geo` (shared memory) when `ok`.
-// False, for every thread, when some thread's `ok` is false (nothing is computed).
+// Starts this thread's element copies of the fields of tile (L, pat) into staged
+// buffer `stg`: dh and u at its slots, and for the flags the aligned 32-bit word
+// holding each flag byte (the flag arrays are padded to a multiple of 16 bytes),
+// with the byte's position in the word and the velocity's direction flip left in
+// nf and ef for tile_trend to apply.
 template <class R, int P, int NT>
+__device__ __forceinline__ void tile_fetch(const DevLevelT<R>& L, int64_t pat, const TilePlan<P, NT>& plan,
+                                           const TileCodes<P, NT>& codes, unsigned char* stg) {
+    using T = Tile<R, P>;
+    using PL = TilePlan<P, NT>;
+    constexpr int PP = P * P;
+    R* dh = reinterpret_cast<R*>(stg + T::ST_DH);
+    R* u = reinterpret_cast<R*>(stg + T::ST_U);
+    uint32_t* nfw = reinterpret_cast<uint32_t*>(stg + T::ST_NFW);
+    uint32_t* efw = reinterpret_cast<uint32_t*>(stg + T::ST_EFW);
+    uint8_t* nf = stg + T::ST_NF;
+    uint8_t* ef = stg + T::ST_EF;
+    const int32_t nelem = int32_t(L.nelem), base = int32_t(pat) * PP;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < PL::SN; ++i) {
+        const int c = plan.n[i];
+        if (c == PL::NONE) continue;
+        const int x = tid + i * NT;
+        const int32_t v = c < 0 ? base + (-c - 1) : codes.n[i];
+        async_copy<sizeof(R)>(dh + x, L.dh + v);
+        async_copy<4>(nfw + x, L.nflag + (v & ~3));
+        nf[x] = uint8_t(v & 3);
+    }
+#pragma unroll
+    for (int i = 0; i < PL::SE; ++i) {
+        const int c = plan.e[i], y = tid + i * NT;
+        if (c == PL::NONE) continue;
+        bool rev;
+        const int32_t e = slot_edge<P>(c, codes.e[i], nelem, base, rev);
+        async_copy<sizeof(R)>(u + y, L.u + e);
+        async_copy<4>(efw + y, L.eflag + (e & ~3));
+        ef[y] = uint8_t((e & 3) | (rev ? 4 : 0));
+    }
+    async_commit();
+}
+
+// The trend of one regular tile (all threads of the block): its fields fetched
+// into staged-field buffer `k` (tile_fetch), its geometry block in `geo` (shared
+// memory) once wait_geo() has returned true.  After the staging barrier the
+// block's earlier tiles are done with every buffer but k's, and after_stage()
+// runs (it may refill them).  False, for every thread, when wait_geo() failed for
+// some thread (nothing is computed).
+template <class R, int P, int NT, class WaitGeo, class AfterStage>
 __device__ bool tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const TilePlan<P, NT>& plan,
-                           const TileCodes<P, NT>& codes, unsigned char* smem, const R* geo, bool ok) {
+                           unsigned char* smem, int k, const R* geo, WaitGeo wait_geo, AfterStage after_stage) {
     using T = Tile<R, P>;
     using G = TileGeo<R, P>;
     using PL = TilePlan<P, NT>;
     constexpr int W = T::W, NN = T::NN, PP = P * P;
-    R* __restrict__ dh = reinterpret_cast<R*>(smem + T::OFF_DH);
-    R* __restrict__ u = reinterpret_cast<R*>(smem + T::OFF_U);
+    unsigned char* stg = smem + T::OFF_STG + k * T::STAGED;
+    R* __restrict__ dh = reinterpret_cast<R*>(stg + T::ST_DH);
+    R* __restrict__ u = reinterpret_cast<R*>(stg + T::ST_U);
+    const uint32_t* __restrict__ nfw = reinterpret_cast<const uint32_t*>(stg + T::ST_NFW);
+    const uint32_t* __restrict__ efw = reinterpret_cast<const uint32_t*>(stg + T::ST_EFW);
+    uint8_t* __restrict__ nf = stg + T::ST_NF;
+    uint8_t* __restrict__ ef = stg + T::ST_EF;
     R* __restrict__ F = reinterpret_cast<R*>(smem + T::OFF_F);
     R* __restrict__ q = reinterpret_cast<R*>(smem + T::OFF_Q);
-    uint8_t* __restrict__ nf = smem + T::OFF_NF;
-    uint8_t* __restrict__ ef = smem + T::OFF_EF;
     const R* __restrict__ de = geo + G::DE;
     const R* __restrict__ le = geo + G::LE;
     const R* __restrict__ kt = geo + G::KT;
@@ -288,38 +343,32 @@ __device__ bool tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
     const R* __restrict__ av = geo + G::AV;
     const R* __restrict__ fv = geo + G::FV;
     const R* __restrict__ ai = geo + G::AI;
-    // the level's fields, read once from its record (which sits in shared memory)
     const int32_t nelem = int32_t(L.nelem);
-    const R* __restrict__ g_dh = L.dh;
-    const R* __restrict__ g_u = L.u;
-    const uint8_t* __restrict__ g_nf = L.nflag;
-    const uint8_t* __restrict__ g_ef = L.eflag;
     const int32_t base = int32_t(pat) * PP;
     const int tid = threadIdx.x;
-    // --- stage: nodes, edges (velocity turned to the local direction)
+    // --- the fields tile_fetch copied for this thread's slots: the flag bytes out of
+    // their words (the byte's position was left in nf/ef), the velocity turned to the
+    // local direction
+    async_wait_all();
 #pragma unroll
     for (int i = 0; i < PL::SN; ++i) {
-        const int c = plan.n[i];
-        if (c == PL::NONE) continue;
         const int x = tid + i * NT;
-        const int32_t v = c < 0 ? base + (-c - 1) : codes.n[i];
-        dh[x] = g_dh[v];
-        nf[x] = g_nf[v];
+        if (plan.n[i] == PL::NONE) continue;
+        nf[x] = uint8_t(nfw[x] >> (8 * nf[x]));
     }
 #pragma unroll
     for (int i = 0; i < PL::SE; ++i) {
-        const int c = plan.e[i], y = tid + i * NT;
-        if (c == PL::NONE) {
+        const int y = tid + i * NT;
+        if (plan.e[i] == PL::NONE) {
             if (y < 3 * NN) ef[y] = 0;
             continue;
         }
-        bool rev;
-        const int32_t e = slot_edge<P>(c, codes.e[i], nelem, base, rev);
-        const R ue = g_u[e];
-        u[y] = rev ? -ue : ue;
-        ef[y] = g_ef[e];
+        const uint8_t m = ef[y];
+        ef[y] = uint8_t(efw[y] >> (8 * (m & 3)));
+        if (m & 4) u[y] = -u[y];
     }
-    if (!__syncthreads_and(ok)) return false;
+    if (!__syncthreads_and(wait_geo())) return false;
+    after_stage();
     // --- F at edges, q at triangles
 #pragma unroll
     for (int i = 0; i < PL::SE; ++i) {
@@ -394,12 +443,15 @@ __device__ bool tile_trend(const DevLevelT<R>& L, int64_t pat, R H, R g, const T
 }
 
 // The trend of the active patches first, first + stride, ... (< n) of an
-// all-level list, by one block: regular patches by tile_trend, each one's
-// geometry block brought in by a bulk copy started while the block works on the
-// patch before (two buffers, one mbarrier each); other patches by other(L, pat).
-// False, with *err set, when a copy did not complete within `limit` cycles (the
-// block then waits, again at most `limit`, for the copy it started next, and
-// leaves).
+// all-level list, by one block: regular patches by tile_trend, other patches by
+// other(L, pat).  Patch i of the sweep uses buffers i mod 2 (staged fields,
+// geometry).  The next patch's fields (element copies, tile_fetch) and geometry
+// block (a bulk copy) are started right after this patch's staging barrier, once
+// every thread is done with the patch before, which used those buffers; the
+// halo ids they need are loaded a patch earlier still.  So one barrier separates
+// consecutive patches, and the copies run while this patch is worked on.  False,
+// with *err set, when a bulk copy did not complete within `limit` cycles (the
+// block then gives it one more bounded wait and leaves).
 template <class R, int P, int NT, class Other>
 __device__ bool tile_sweep(const DevLevelT<R>* lv, const int32_t* list, int n, int first, int stride, R H, R g,
                            unsigned char* smem, int* err, long long limit, Other other) {
@@ -415,43 +467,69 @@ __device__ bool tile_sweep(const DevLevelT<R>* lv, const int32_t* list, int n, i
     __syncthreads();
     TilePlan<P, NT> plan;
     plan.init();
-    TileCodes<P, NT> cur, nxt;
-    // list entry e: when its tile is regular, its halo ids into c and the bulk copy
-    // of its geometry block into buffer k started
-    auto start = [&](int e, int k, TileCodes<P, NT>& c) -> bool {
+    auto regular = [&](int e) -> bool {
+        if (e >= n) return false;
+        const int32_t ent = list[e];
+        return tile_regular(lv[ent >> LVL_SHIFT], ent & PATCH_MASK);
+    };
+    auto codes_of = [&](int e, TileCodes<P, NT>& c) {
+        const int32_t ent = list[e];
+        c.load(lv[ent >> LVL_SHIFT], ent & PATCH_MASK, plan);
+    };
+    // list entry e (regular, halo ids c) into buffers k: its fields and, from
+    // thread 0, its geometry block
+    auto start = [&](int e, const TileCodes<P, NT>& c, int k) {
         const int32_t ent = list[e];
         const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
         const int64_t pat = ent & PATCH_MASK;
-        if (!tile_regular(L, pat)) return false;
-        c.load(L, pat, plan);
+        tile_fetch<R, P, NT>(L, pat, plan, c, smem + T::OFF_STG + k * T::STAGED);
         if (threadIdx.x == 0) {
-            fence_async_shared();   // the buffer's last readers are behind the block barrier
+            fence_async_shared();   // the buffer's last readers are behind a block barrier
             bulk_load(gbuf + k * G::WORDS, L.tgeo + pat * G::WORDS, G::BYTES, bar + k);
         }
-        return true;
     };
+    TileCodes<P, NT> c1, c2;   // halo ids of the next patch and of the one after
+    bool reg = regular(first);
+    bool reg1 = regular(first + stride);
+    if (reg) {
+        TileCodes<P, NT> c0;
+        codes_of(first, c0);
+        start(first, c0, 0);
+    }
+    if (reg1) codes_of(first + stride, c1);
     unsigned ph = 0;   // bit k: parity of buffer k's next phase
-    bool reg = first < n && start(first, 0, cur);
     int k = 0;
     for (int e = first; e < n; e += stride, k ^= 1) {
         const int32_t ent = list[e];
         const DevLevelT<R>& L = lv[ent >> LVL_SHIFT];
         const int64_t pat = ent & PATCH_MASK;
-        const bool reg_next = e + stride < n && start(e + stride, k ^ 1, nxt);
+        const bool reg2 = regular(e + 2 * stride);
+        if (reg2) codes_of(e + 2 * stride, c2);
         if (reg) {
-            const bool ok = mbar_wait(bar + k, (ph >> k) & 1u, limit);
+            const uint32_t parity = (ph >> k) & 1u;
             ph ^= 1u << k;
-            if (!tile_trend<R, P, NT>(L, pat, H, g, plan, cur, smem, gbuf + k * G::WORDS, ok)) {
+            const bool done = tile_trend<R, P, NT>(
+                L, pat, H, g, plan, smem, k, gbuf + k * G::WORDS, [&]() { return mbar_wait(bar + k, parity, limit); },
+                [&]() {
+                    if (reg1) start(e + stride, c1, k ^ 1);
+                });
+            if (!done) {
+                // this patch's bulk copy did not land in time: report it, give it one
+                // more bounded wait, and leave (nothing else was started)
                 if (threadIdx.x == 0) atomicExch(err, 1);
-                if (reg_next) mbar_wait(bar + (k ^ 1), (ph >> (k ^ 1)) & 1u, limit);
+                mbar_wait(bar + k, parity, limit);
                 return false;
             }
         } else {
+            // the tabulated path shares no buffer with the tiles; the next copies wait
+            // for the block barrier that ends this patch
             other(L, pat);
+            __syncthreads();
+            if (reg1) start(e + stride, c1, k ^ 1);
         }
-        __syncthreads();   // the tile's shared memory is reused by the next patch
-        cur = nxt;
-        reg = reg_next;
+        c1 = c2;
+        reg = reg1;
+        reg1 = reg2;
     }
     return true;
 }
