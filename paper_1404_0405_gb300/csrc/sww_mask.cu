@@ -42,6 +42,26 @@ constexpr int TPB = 256;
 
 #define MEMBER const MaskMember<R>& M = B.m[blockIdx.y]
 
+constexpr int MAXL = 12;
+
+// The member's level records ja..jb copied into shared memory by every thread of
+// the block (then a block barrier), so that the item bodies take their field
+// addresses from shared memory; returns the staged array (indexed by level).  The
+// mask kernels stage every level Jmin..Jmax of the member: a list left by the
+// previous mask (its candidates) may name levels above this mask's top.
+template <class R>
+__device__ __forceinline__ const DevLevelT<R>* stage_levels(DevLevelT<R>* sl, const DevLevelT<R>* lvs, int ja, int jb) {
+    const int words = int((jb - ja + 1) * sizeof(DevLevelT<R>) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(lvs + ja);
+    int* dst = reinterpret_cast<int*>(sl + ja);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    return sl;
+}
+#define STAGE_LEVELS                \
+    __shared__ DevLevelT<R> sl_[MAXL]; \
+    const DevLevelT<R>* lvs = stage_levels(sl_, M.lvs, B.ja, M.jmax)
+
 template <class Lv>
 __device__ __forceinline__ int64_t patch_of(const Lv& L, int64_t x) {
     return x < L.nelem ? x / (L.p * L.p) : L.npatch;
@@ -115,6 +135,7 @@ template <class R, int CAP>
 __global__ void k_feat_own(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
     if (!M.learn) return;
+    STAGE_LEVELS;
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     // the thresholds once per thread, in FP32
@@ -124,8 +145,8 @@ __global__ void k_feat_own(const __grid_constant__ MaskBatch<R, CAP> B) {
         const int j = ent >> LVL_SHIFT;
         if (j <= B.ja || j > M.jb) continue;
         const int64_t P = ent & PATCH_MASK;
-        const DevLevelT<R>& L = M.lvs[j];
-        const DevLevelT<R>& C = M.lvs[j - 1];
+        const DevLevelT<R>& L = lvs[j];
+        const DevLevelT<R>& C = lvs[j - 1];
         const int64_t pp = L.p * L.p, np1 = L.npatch + 1;
         const bool pole = P == L.npatch;
         R mh = R(0), mu = R(0);
@@ -241,8 +262,9 @@ __global__ void k_clear_flags(const __grid_constant__ MaskBatch<R, CAP> B) {
 template <class R, int CAP>
 __global__ void k_clear_sig_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_NODE, M.lvs, none, M.cand, M.cand_count, B.P) { L.sig[id] = 0; });
+    ITEMS(K_NODE, lvs, none, M.cand, M.cand_count, B.P) { L.sig[id] = 0; });
 }
 
 // significance over the items of the active patches above Jmin; the patch of each
@@ -250,8 +272,8 @@ __global__ void k_clear_sig_list(const __grid_constant__ MaskBatch<R, CAP> B) {
 template <class R, int CAP>
 __global__ void k_sig_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    const DevLevelT<R>* lvs = M.lvs;
     const R eh = sig_thr<R>(M.thr[0]), eu = sig_thr<R>(M.thr[1]);
     int32_t* sig_any = M.sig_any;
     ITEMS(K_NODE | K_EDGE | K_CEDGE, lvs, none, M.active, M.active_count, B.P) {
@@ -393,8 +415,8 @@ __global__ void k_cat(const __grid_constant__ MaskBatch<R, CAP> B, int which) {
 template <class R, int CAP>
 __global__ void k_adjacent_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    const DevLevelT<R>* lvs = M.lvs;
     ITEMS(K_NODE, lvs, none, M.cand, M.cand_count, B.P) {
         if (L.J == B.ja) return;
         adjacent_node(L, lvs[L.J - 1], L.J - 1 > B.ja, id);
@@ -406,17 +428,19 @@ template <class R, int CAP>
 __global__ void k_close_list(const __grid_constant__ MaskBatch<R, CAP> B, int j) {
     MEMBER;
     if (j > M.jb) return;
-    const DevLevelT<R>& F = M.lvs[j];
+    STAGE_LEVELS;
+    const DevLevelT<R>& F = lvs[j];
     const bool has_finer = j < M.jb;
-    const DevLevelT<R>& Fp = M.lvs[has_finer ? j + 1 : j];
+    const DevLevelT<R>& Fp = lvs[has_finer ? j + 1 : j];
     ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, F, F.cand, F.ncand, B.P) { close_node(L, Fp, has_finer, id); });
 }
 
 template <class R, int CAP>
 __global__ void k_live_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_NODE, M.lvs, none, M.cand, M.cand_count, B.P) {
+    ITEMS(K_NODE, lvs, none, M.cand, M.cand_count, B.P) {
         if (live_node(L, id, L.J == B.ja)) L.lflag[patch_of(L, id)] = 1;
     });
 }
@@ -424,16 +448,18 @@ __global__ void k_live_list(const __grid_constant__ MaskBatch<R, CAP> B) {
 template <class R, int CAP>
 __global__ void k_live_edges_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_EDGE, M.lvs, none, M.cand, M.cand_count, B.P) { live_edge(L, id); });
+    ITEMS(K_EDGE, lvs, none, M.cand, M.cand_count, B.P) { live_edge(L, id); });
 }
 
 template <class R, int CAP>
 __global__ void k_dilate_list(const __grid_constant__ MaskBatch<R, CAP> B, int forward) {
     MEMBER;
     if (M.jb == B.ja) return;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_NODE, M.lvs, none, M.gcand, M.gcand_count, B.P) {
+    ITEMS(K_NODE, lvs, none, M.gcand, M.gcand_count, B.P) {
         if (L.J == B.ja) return;
         dilate_node(L, id, forward != 0);
     });
@@ -443,8 +469,9 @@ template <class R, int CAP>
 __global__ void k_ghost_list(const __grid_constant__ MaskBatch<R, CAP> B, int in_band1) {
     MEMBER;
     if (M.jb == B.ja) return;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_NODE | K_EDGE, M.lvs, none, M.gcand, M.gcand_count, B.P) {
+    ITEMS(K_NODE | K_EDGE, lvs, none, M.gcand, M.gcand_count, B.P) {
         if (L.J == B.ja) return;
         const uint8_t* band = in_band1 ? L.band1 : L.band0;
         if (kind == K_NODE)
@@ -458,8 +485,8 @@ template <class R, int CAP>
 __global__ void k_covered_list(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
     if (M.jb == B.ja) return;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    const DevLevelT<R>* lvs = M.lvs;
     const int jtop = M.jb;
     ITEMS(K_NODE, lvs, none, M.cand, M.cand_count, B.P) {
         if (L.J >= jtop) return;
@@ -538,8 +565,9 @@ __global__ void k_concat_b(const __grid_constant__ MaskBatch<R, CAP> B) {
 template <class R, int CAP>
 __global__ void k_wl_build_b(const __grid_constant__ MaskBatch<R, CAP> B) {
     MEMBER;
+    STAGE_LEVELS;
     DevLevelT<R> none{};
-    ITEMS(K_NODE | K_EDGE, M.lvs, none, M.all, M.all_count, B.P) { wl_item(L, kind, id); });
+    ITEMS(K_NODE | K_EDGE, lvs, none, M.all, M.all_count, B.P) { wl_item(L, kind, id); });
 }
 
 }  // namespace
