@@ -573,7 +573,9 @@ def run_ours(a, rank, world):
         dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
     seed = member_seeds(a.seed, rank, 1)[0]
     t_setup = time.perf_counter()
+    free0 = torch.cuda.mem_get_info()[0]
     base = sww.Model(a.jmin, a.jmax, patch=a.patch, eps=a.eps, rk="rk4", cfl=0.8)
+    grid_bytes = free0 - torch.cuda.mem_get_info()[0]   # the shared FP64 grid tables and one FP64 handle
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
@@ -621,12 +623,26 @@ def run_ours(a, rank, world):
         dtype = "f32"
     else:
         ms, dtype = plain_m, "f64"
+    # device memory of one more member of the timed kind (its state, flags, lists
+    # and work lists; the grid tables are shared)
+    member_bytes = None
+    if a.form == "chosen":
+        free1 = torch.cuda.mem_get_info()[0]
+        probe = _members(sww, workloads, cbase, a, "fp32", [seed + 777], persistent="phased", patch=cpatch, bps=cbps)
+        member_bytes = free1 - torch.cuda.mem_get_info()[0]
+        probe[0].close()
+        del probe
     setup_s = time.perf_counter() - t_setup
     for _ in range(a.warmup):
         sww.step_ensemble(ms, -1.0, 1, True)
     for m in ms:
         if learned is not None:
             m.learn_stats(reset=True)
+    # the library's launch counter is process-wide and read through stats(), which
+    # launches kernels itself (the live-cell counts around every timed step too):
+    # its own launches are counted and taken out
+    k_stats = ms[0].stats()["kernel_launches"]
+    k_stats = ms[0].stats()["kernel_launches"] - k_stats
     launches0 = ms[0].stats()["kernel_launches"]
     if world > 1:
         torch.distributed.barrier()
@@ -637,7 +653,7 @@ def run_ours(a, rank, world):
     times, cells = _timed(sww, ms, a.steps, flush, stream)
     torch.cuda.profiler.stop()
     clk = clocks.stop()
-    launches = ms[0].stats()["kernel_launches"] - launches0   # process-wide counter: every member
+    launches = ms[0].stats()["kernel_launches"] - launches0 - (2 * len(ms) * a.steps + 1) * k_stats
     total_all, cells_all = combine_ranks(sum(times), sum(cells), "cuda", world)
     value = cells_all / total_all
     if learned is not None:
@@ -778,7 +794,8 @@ def run_ours(a, rank, world):
                            "blocks_per_sm": cbps or 4, "autotune": tuned,
                            "active_cells_per_step": cells_all / a.steps / max(world, 1) / len(ms),
                            "compression": (10 * 4 ** a.jmax + 2) / (cells_all / a.steps / max(world, 1) / len(ms)),
-                           "setup_s": setup_s},
+                           "setup_s": setup_s,
+                           "device_bytes": {"grid_and_fp64_handle": grid_bytes, "per_member": member_bytes}},
                 "plain": plain, "chosen_vs_plain": value / plain["value"], "equal_error": err,
                 "learned_proposal": lstats, "learned_turbulence": turb, "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(launches),
