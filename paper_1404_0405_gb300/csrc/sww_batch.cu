@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
                                      if (!(L.nflag[id] & COVERED)) return;
                                      const DevLevelT<R>& F = (&L)[1];
                                      R v = F.dh[L.c2f[id]];
+#pragma unroll
                                      for (int q = 0; q < 12; ++q) {
                                          const int32_t mm = L.mk_i[q * L.N + id];
                                          if (mm < 0 || !(F.nflag[mm] & LIVE)) continue;
@@ -257,12 +258,13 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
             break;
         default: {
             const R dt = R(*mr->dt);
+            const RKStageR<R> sr(a.st);
             member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
                                           [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
                                               if (kind == K_NODE)
-                                                  update_node(L, id, a.st, dt);
+                                                  update_node(L, id, sr, dt);
                                               else
-                                                  update_edge(L, id, a.st, dt);
+                                                  update_edge(L, id, sr, dt);
                                           });
         }
     }

@@ -40,6 +40,13 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
     return static_cast<unsigned long long>(__double_as_longlong(x));
 }
 
+// the viscous form (nu != 0), tested on the bits of nu (either sign of zero is
+// zero) on the integer pipe: the per-point bodies ask at every point
+template <class Lv>
+__device__ __forceinline__ bool viscous(const Lv& L) {
+    return (dbits(L.nu) << 1) != 0;
+}
+
 // ---------------------------------------------------------------------------- CFL step and field maxima
 
 // |x| as an unsigned key ordered like |x|: with the sign bit cleared, IEEE numbers
@@ -184,7 +191,7 @@ __device__ __forceinline__ void pv_at(const DevLevelT<R>& L, int64_t t, R H) {
     R hv = geo<R>(L.kite, t) * (H + L.dh[n0]) + geo<R>(L.kite, L.T + t) * (H + L.dh[n1]) +
            geo<R>(L.kite, 2 * L.T + t) * (H + L.dh[n2]);
     R Av = geo<R>(L.A_v, t);
-    if (L.nu != 0.0) L.zeta[t] = circ / Av;
+    if (viscous(L)) L.zeta[t] = circ / Av;
     L.q[t] = (circ / Av + geo<R>(L.f_v, t)) / (hv / Av);
 }
 
@@ -196,22 +203,26 @@ __device__ __forceinline__ void flux_at(const DevLevelT<R>& L, int64_t e, R H) {
     if (!(L.nflag[a] & AVAIL) || !(L.nflag[b] & AVAIL)) return;
     L.F[e] = R(0.5) * ((H + L.dh[a]) + (H + L.dh[b])) * L.u[e];
     // viscous form: diffusive height flux -nu grad(dh) (joins F in the divergence)
-    if (L.nu != 0.0) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / geo<R>(L.d_e, e);
+    if (viscous(L)) L.Fd[e] = -R(L.nu) * (L.dh[b] - L.dh[a]) / geo<R>(L.d_e, e);
 }
 
 // divergence of the height flux (with the diffusive flux of the viscous form) at a node
 template <class R>
 __device__ __forceinline__ void div_at(const DevLevelT<R>& L, int64_t v) {
     if (!(L.nflag[v] & AVAIL)) return;
-    int dg = L.deg[v];
+    const int dg = L.deg[v];
     R div = R(0);
-    const bool visc = L.nu != 0.0;
-    for (int k = 0; k < dg; ++k) {
-        int32_t code = L.ring_e[k * L.N + v];
-        int64_t e = code >> 1;
-        if (!(L.eflag[e] & AVAIL)) return;
+    bool ok = true;   // every ring edge available (else nothing is written)
+    const bool visc = viscous(L);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k >= dg) break;
+        const int32_t code = L.ring_e[k * L.N + v];
+        const int64_t e = code >> 1;
+        ok = ok && (L.eflag[e] & AVAIL);
         div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * geo<R>(L.l_e, e);
     }
+    if (!ok) return;
     L.c[v] = div / geo<R>(L.A_i, v);
 }
 
@@ -237,19 +248,23 @@ template <class R>
 __device__ __forceinline__ void node_at(const DevLevelT<R>& L, int64_t v, R g) {
     if (L.advect) return div_at(L, v);   // prescribed velocity: no Bernoulli function
     if (!(L.nflag[v] & AVAIL)) return;
-    int dg = L.deg[v];
+    const int dg = L.deg[v];
     R div = R(0), ke = R(0), du = R(0);
-    const bool visc = L.nu != 0.0;
-    for (int k = 0; k < dg; ++k) {
-        int32_t code = L.ring_e[k * L.N + v];
-        int64_t e = code >> 1;
-        if (!(L.eflag[e] & AVAIL)) return;
+    bool ok = true;   // every ring edge available (else nothing is written)
+    const bool visc = viscous(L);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        if (k >= dg) break;
+        const int32_t code = L.ring_e[k * L.N + v];
+        const int64_t e = code >> 1;
+        ok = ok && (L.eflag[e] & AVAIL);
         R ue = L.u[e];
         const R le = geo<R>(L.l_e, e);
         div += esign<R>(code) * (visc ? L.F[e] + L.Fd[e] : L.F[e]) * le;
         if (visc) du += esign<R>(code) * ue * le;
         ke += R(0.25) * le * geo<R>(L.d_e, e) * ue * ue;
     }
+    if (!ok) return;
     R A = geo<R>(L.A_i, v);
     // viscous form: -nu div u joins B (so that -grad B gains +nu grad div u)
     if (visc) ke -= R(L.nu) * du;
@@ -271,7 +286,7 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
         s += w * L.F[e2] * R(0.5) * (qe + q2);
     }
     // viscous form: -nu grad^perp curl u, grad^perp zeta = (1/l_e) sum_{v at e} t_{e,v} zeta_v
-    if (L.nu != 0.0) {
+    if (viscous(L)) {
         R gp = R(0);
         for (int side = 0; side < 2; ++side) {
             const int32_t t = L.et[side * L.E + e];
@@ -288,18 +303,29 @@ __device__ __forceinline__ void coriolis_at(const DevLevelT<R>& L, int64_t e) {
 // trend and one Runge-Kutta stage at a live point (terms with a zero coefficient
 // are skipped, so stale storage never enters):
 //   y <- a*y0 + b*y + (cdt*dt)*k + (ddt*dt)*acc,   acc <- al*acc + be*k
+// An RK stage in the working precision: the coefficients converted and their zero
+// tests taken once per thread, not at every point (the FP64 pipe is narrow)
 template <class R>
-__device__ __forceinline__ void rk_apply(const RKStage& st, R dt, R k, R* y, const R* y0, R* acc) {
-    R v = R(st.cdt) * dt * k;
-    if (st.a != 0.0) v += R(st.a) * *y0;
-    if (st.b != 0.0) v += R(st.b) * *y;
-    if (st.ddt != 0.0) v += R(st.ddt) * dt * *acc;
-    if (st.al != 0.0 || st.be != 0.0) *acc = (st.al != 0.0 ? R(st.al) * *acc : R(0)) + R(st.be) * k;
+struct RKStageR {
+    R a, b, cdt, ddt, al, be;
+    bool apply, ha, hb, hddt, hacc, hal;
+    __device__ explicit RKStageR(const RKStage& st)
+        : a(R(st.a)), b(R(st.b)), cdt(R(st.cdt)), ddt(R(st.ddt)), al(R(st.al)), be(R(st.be)), apply(st.apply != 0),
+          ha(st.a != 0.0), hb(st.b != 0.0), hddt(st.ddt != 0.0), hacc(st.al != 0.0 || st.be != 0.0), hal(st.al != 0.0) {}
+};
+
+template <class R>
+__device__ __forceinline__ void rk_apply(const RKStageR<R>& st, R dt, R k, R* y, const R* y0, R* acc) {
+    R v = st.cdt * dt * k;
+    if (st.ha) v += st.a * *y0;
+    if (st.hb) v += st.b * *y;
+    if (st.hddt) v += st.ddt * dt * *acc;
+    if (st.hacc) *acc = (st.hal ? st.al * *acc : R(0)) + st.be * k;
     *y = v;
 }
 
 template <class R>
-__device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, const RKStage& st, R dt) {
+__device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, const RKStageR<R>& st, R dt) {
     if (!(L.nflag[v] & LIVE)) return;
     R k = -L.c[v];
     L.dht[v] = k;
@@ -307,7 +333,7 @@ __device__ __forceinline__ void update_node(const DevLevelT<R>& L, int64_t v, co
 }
 
 template <class R>
-__device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, const RKStage& st, R dt) {
+__device__ __forceinline__ void update_edge(const DevLevelT<R>& L, int64_t e, const RKStageR<R>& st, R dt) {
     if (!(L.eflag[e] & LIVE)) return;
     if (L.advect) {   // prescribed velocity: zero trend, u untouched
         L.ut[e] = R(0);
@@ -394,6 +420,7 @@ __device__ __forceinline__ void inverse_a_item(const DevLevelT<R>& L, const DevL
         if (!(L.nflag[id] & LIVE) || L.f2c[id] < 0) return;
         int32_t k = L.f2c[id];
         R s = C.dh[k];
+#pragma unroll
         for (int q = 0; q < 12; ++q) {
             int32_t m = C.mk_i[q * C.N + k];
             if (m >= 0 && (L.nflag[m] & LIVE) && (L.nflag[m] & WASLIVE)) s -= C.mk_w[q * C.N + k] * L.hdet[m];
@@ -445,7 +472,7 @@ __device__ __forceinline__ void restrict_item(const DevLevelT<R>& L, const DevLe
     if (ca || cb) {
         // the restricted total height flux (mass flux plus the viscous form's
         // diffusive flux) goes to F; the coarse diffusive flux is then zero
-        const bool visc = L.nu != 0.0;
+        const bool visc = viscous(L);
         R s = R(0);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -599,11 +626,13 @@ __device__ __forceinline__ void ghost_edge(const DevLevelT<R>& L, int64_t e, con
 template <class R>
 __device__ __forceinline__ void covered_node(const DevLevelT<R>& C, const DevLevelT<R>& F, int64_t k) {
     if (!(F.nflag[C.c2f[k]] & LIVE)) return;
+    bool all = true;   // the loads issued together (no early exit)
+#pragma unroll
     for (int q = 0; q < 12; ++q) {
         const int32_t m = C.mk_i[q * C.N + k];
-        if (m >= 0 && !(F.nflag[m] & LIVE)) return;
+        if (m >= 0 && !(F.nflag[m] & LIVE)) all = false;
     }
-    C.nflag[k] |= COVERED;
+    if (all) C.nflag[k] |= COVERED;
 }
 
 // ---------------------------------------------------------------------------- patch lists (Sec. 5.2)
@@ -691,7 +720,7 @@ __device__ void concat_lists(const DevLevelT<R>* __restrict__ lvs, int jmin, int
     for (int j = jmin; j <= jmax; ++j) {
         const DevLevelT<R>& L = lvs[j];
         const int n = *L.npatches;
-        const bool all_irr = L.nu != 0.0 || L.advect || L.thalo == nullptr;
+        const bool all_irr = viscous(L) || L.advect || L.thalo == nullptr;
         // all entries in level order; the entries whose tile is not regular (see
         // tile_regular) also into the irregular list, in the same order
         for (int start = 0; start < n; start += blockDim.x) {

@@ -63,11 +63,12 @@ __global__ void k_update(const DevLevelT<R>* __restrict__ lvs, const int32_t* li
                          RKStage st, const double* __restrict__ dtp) {
     DevLevelT<R> none{};
     R dt = R(dtp ? *dtp : 0.0);
+    const RKStageR<R> sr(st);
     ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
         if (kind == K_NODE)
-            update_node(L, id, st, dt);
+            update_node(L, id, sr, dt);
         else
-            update_edge(L, id, st, dt);
+            update_edge(L, id, sr, dt);
     });
 }
 
@@ -113,6 +114,7 @@ __global__ void k_partial(DevLevelT<R> C, DevLevelT<R> F, const int32_t* list, c
     ITEMS(K_NODE, (const DevLevelT<R>*)nullptr, C, list, count, P) {
         if (!(L.nflag[id] & COVERED)) return;
         R s = F.dh[L.c2f[id]];
+#pragma unroll
         for (int q = 0; q < 12; ++q) {
             int32_t m = L.mk_i[q * L.N + id];
             if (m < 0 || !(F.nflag[m] & LIVE)) continue;

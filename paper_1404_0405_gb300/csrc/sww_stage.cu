@@ -172,11 +172,12 @@ __global__ void __launch_bounds__(STAGE_TPB) k_stage(StageArgs<R> a) {
         if (!stage_sync(a)) return;
     }
     const R dt = R(a.dt ? *a.dt : 0.0);
+    const RKStageR<R> sr(a.st);
     ITEMS(K_NODE | K_EDGE, lv, lv[a.jmin], a.all_list, a.all_count, a.P) {
         if (kind == K_NODE)
-            update_node(L, id, a.st, dt);
+            update_node(L, id, sr, dt);
         else
-            update_edge(L, id, a.st, dt);
+            update_edge(L, id, sr, dt);
     });
 }
 

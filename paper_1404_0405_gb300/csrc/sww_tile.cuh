@@ -111,9 +111,7 @@ struct TilePlan {
 // with the velocity free (the viscous and advection forms take the tabulated path)
 template <class R>
 __device__ __forceinline__ bool tile_regular(const DevLevelT<R>& L, int64_t pat) {
-    // nu == 0 tested on its bits (either sign of zero), on the integer pipe
-    return pat < L.npatch && L.thalo != nullptr && L.tirr[pat] == 0 &&
-           (static_cast<unsigned long long>(__double_as_longlong(L.nu)) << 1) == 0 && !L.advect;
+    return pat < L.npatch && L.thalo != nullptr && L.tirr[pat] == 0 && !viscous(L) && !L.advect;
 }
 
 // position (a, b) of tile slot x = (a + 1) W + (b + 1)
