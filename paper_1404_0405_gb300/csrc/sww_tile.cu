@@ -47,10 +47,12 @@ __device__ __forceinline__ void stage_records(DevLevelT<R>* sl, const MemberRef<
     __syncthreads();
 }
 
-// resident blocks per SM the tile kernel is built for: six for 8 x 8 tiles (40
-// registers), four for 16 x 16 (their per-thread slot plan is larger)
+// resident blocks per SM the tile kernel is built for: five for 8 x 8 tiles (48
+// registers; measured 5 % faster than six blocks at 40 registers, which spilled
+// the copy pipeline's state), four for 16 x 16 (their per-thread slot plan is
+// larger)
 template <int P>
-constexpr int tile_min_blocks() { return P >= 16 ? 4 : 6; }
+constexpr int tile_min_blocks() { return P >= 16 ? 4 : 5; }
 
 template <class R, int P>
 __global__ void __launch_bounds__(TILE_TPB, tile_min_blocks<P>()) k_tile_trend(BatchArgs<R> a, int bpm) {
