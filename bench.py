@@ -336,11 +336,11 @@ STAGE_BYTES_PER_CELL = {"fp64": 232, "fp32": 184}
 TREND_BYTES_PER_CELL = {"fp64": 236, "fp32": 188}
 
 # DRAM bytes (read + write) of k_tile_trend per available cell, from an ncu
-# full-set capture of the same jet at Jmin=4..Jmax=8 with 16 members (45.5 MB for
+# full-set capture of the same jet at Jmin=4..Jmax=8 with 16 members (42.6 MB for
 # 495 961 cells), scaled to a launch by the cells it processes.  The geometry
 # share falls as more members read the same blocks, so at 64 members this
 # overstates the traffic.  Remove the entry when the kernel changes.
-TREND_TRAFFIC_PER_CELL = {"fp32": 91.8}
+TREND_TRAFFIC_PER_CELL = {"fp32": 85.9}
 
 
 def _live(m):
