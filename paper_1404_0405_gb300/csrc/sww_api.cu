@@ -1030,7 +1030,9 @@ void ensemble_phased(sww_handle* const* hs, int n, double dt, bool do_adapt) {
                 jmax_max = std::max(jmax_max, hs[i]->cfg.jmax);
             }
             mask_batch_head(*b, lead, n, jb_max, jmax_max);
-            const unsigned grid = unsigned(std::max(1, std::min<int>(int(lead->grid_all), 8 * lead->nsm / n)));
+            // blocks per member of the list passes: two waves of 8 blocks of 256 per SM
+            // over all members (measured 8 % faster than one wave on the 64-member jet)
+            const unsigned grid = unsigned(std::max(1, std::min<int>(int(lead->grid_all), 16 * lead->nsm / n)));
             launch_proposal_batch(*b, grid, 0, s);
             launch_mask_batch(*b, grid, s);
             launch_proposal_batch(*b, grid, 1, s);

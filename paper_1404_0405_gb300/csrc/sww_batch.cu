@@ -28,7 +28,7 @@ constexpr int MAXL = 12;
 constexpr int MAXM = 128;
 enum {
     PH_FILL = 0, PH_RESTRICT, PH_DIV, PH_UPDATE, PH_SAVE, PH_DT, PH_DT_FINAL, PH_PARTIAL,
-    PH_DETAILS, PH_MAXABS, PH_THRESH, PH_INV_A, PH_INV_B, PH_INV_FILL, PH_OUT
+    PH_DETAILS, PH_THRESH, PH_INV_A, PH_INV_B, PH_INV_FILL, PH_OUT
 };
 
 struct MaxU64 {
@@ -203,25 +203,22 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
                 atomicMax(&mr->red[RED_LEVEL + threadIdx.x], slev[threadIdx.x]);
             break;
         }
-        case PH_DETAILS:
-            member_items<K_NODE | K_EDGE | K_CEDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
-                                                    [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t el) {
-                                                        if (L.J > a.jmin) details_item(L, (&L)[-1], kind, id, el);
-                                                    });
-            break;
-        case PH_MAXABS: {
-            // max |dh| over live nodes, max |u| over live edges (keys of the field
-            // type, widened to FP64 once per block, as k_maxabs)
+        case PH_DETAILS: {
+            // the wavelet coefficients (levels above Jmin) and, in the same pass, max |dh|
+            // over live nodes and max |u| over live edges of every level (keys of the
+            // field type, widened to FP64 once per block, as k_maxabs; the details only
+            // read dh and u)
             __shared__ unsigned long long shm[BATCH_TPB / 32];
             unsigned long long hmax = 0, umax = 0;
-            member_items<K_NODE | K_EDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
-                                          [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t) {
-                                              if (kind == K_NODE) {
-                                                  if (L.nflag[id] & LIVE) hmax = max(hmax, abs_key(L.dh[id]));
-                                              } else if (L.eflag[id] & LIVE) {
-                                                  umax = max(umax, abs_key(L.u[id]));
-                                              }
-                                          });
+            member_items<K_NODE | K_EDGE | K_CEDGE>(sl, mr->all_list, *mr->all_count, a.P, b, bpm,
+                                                    [&](const DevLevelT<R>& L, int kind, int64_t id, int64_t el) {
+                                                        if (kind == K_NODE) {
+                                                            if (L.nflag[id] & LIVE) hmax = max(hmax, abs_key(L.dh[id]));
+                                                        } else if (kind == K_EDGE) {
+                                                            if (L.eflag[id] & LIVE) umax = max(umax, abs_key(L.u[id]));
+                                                        }
+                                                        if (L.J > a.jmin) details_item(L, (&L)[-1], kind, id, el);
+                                                    });
             hmax = block_reduce_u64(hmax, MaxU64(), shm);
             umax = block_reduce_u64(umax, MaxU64(), shm);
             if (threadIdx.x == 0) {
@@ -278,9 +275,10 @@ cudaError_t launch_stage_batch_part(const BatchArgs<R>& a, const int64_t* level_
     if (a.nm < 1 || a.nm > MAXM || a.jtop_max + 1 > MAXL) return cudaErrorInvalidValue;
     int64_t all = 0;
     for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
-    // blocks per member: enough for the member's share of the bound, at most a
-    // full GPU (8 blocks of 256 per SM) over all members
-    const int cap = std::max(1, 8 * nsm / a.nm);
+    // blocks per member: enough for the member's share of the bound, at most two
+    // waves of 8 blocks of 256 per SM over all members (measured a little faster
+    // than one wave: the members' shares are uneven)
+    const int cap = std::max(1, 16 * nsm / a.nm);
     auto bpm = [&](int64_t entries, int slots) {
         const int64_t per = (entries + a.nm - 1) / a.nm * a.P * slots;
         return int(std::max<int64_t>(1, std::min<int64_t>((per + BATCH_TPB - 1) / BATCH_TPB, cap)));
@@ -322,7 +320,7 @@ cudaError_t launch_stage_batch_phases(const BatchArgs<R>& a, const int64_t* leve
 
 template <class R>
 static int batch_bpm(const BatchArgs<R>& a, int64_t entries, int slots, int nsm) {
-    const int cap = std::max(1, 8 * nsm / a.nm);
+    const int cap = std::max(1, 16 * nsm / a.nm);   // two waves, as in launch_stage_batch_part
     const int64_t per = (entries + a.nm - 1) / a.nm * a.P * slots;
     return int(std::max<int64_t>(1, std::min<int64_t>((per + BATCH_TPB - 1) / BATCH_TPB, cap)));
 }
@@ -366,7 +364,6 @@ cudaError_t launch_batch_adapt_pre(const BatchArgs<R>& a, const int64_t* level_e
     int64_t all = 0;
     for (int j = a.jmin; j <= a.jtop_max; ++j) all += level_entries[j];
     cudaError_t e = batch_go(a, PH_DETAILS, 0, batch_bpm(a, all, 7, nsm), s);
-    if (e == cudaSuccess) e = batch_go(a, PH_MAXABS, 0, batch_bpm(a, all, 4, nsm), s);
     if (e == cudaSuccess) e = batch_go(a, PH_THRESH, 0, 1, s);
     return e;
 }

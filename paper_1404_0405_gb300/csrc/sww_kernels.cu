@@ -31,33 +31,6 @@ constexpr int TPB = 256;
 
 // ---------------------------------------------------------------------------- list kernels
 
-// pass 1 of a trend: potential vorticity at triangles and thickness flux at edges
-// (both read only the state)
-template <class R>
-__global__ void k_pv_flux(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P, R H) {
-    DevLevelT<R> none{};
-    ITEMS(K_EDGE | K_TRI, lvs, none, list, count, P) {
-        if (kind == K_EDGE)
-            flux_at(L, id, H);
-        else
-            pv_at(L, id, H);
-    });
-}
-
-// pass 2: divergence, kinetic energy and Bernoulli function at nodes, Coriolis
-// tendency at edges (both read pass-1 results of neighbours)
-template <class R>
-__global__ void k_node_coriolis(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
-                                R g) {
-    DevLevelT<R> none{};
-    ITEMS(K_NODE | K_EDGE, lvs, none, list, count, P) {
-        if (kind == K_NODE)
-            node_at(L, id, g);
-        else
-            coriolis_at(L, id);
-    });
-}
-
 template <class R>
 __global__ void k_update(const DevLevelT<R>* __restrict__ lvs, const int32_t* list, const int32_t* count, int P,
                          RKStage st, const double* __restrict__ dtp) {
@@ -546,14 +519,6 @@ template <class R>
 static int64_t span(const DevLevelT<R>& L) { return L.E > L.N ? L.E : L.N; }
 
 template <class R>
-void launch_pv_flux(const WorkT<R>& W, double H, cudaStream_t s) {
-    LIST(k_pv_flux<R>, W.lvs, W.list, W.count, W.S, R(H));
-}
-template <class R>
-void launch_node_coriolis(const WorkT<R>& W, double g, cudaStream_t s) {
-    LIST(k_node_coriolis<R>, W.lvs, W.list, W.count, W.S, R(g));
-}
-template <class R>
 void launch_update(const WorkT<R>& W, const RKStage& st, const double* dt, cudaStream_t s) {
     LIST(k_update<R>, W.lvs, W.list, W.count, W.S, st, dt);
 }
@@ -675,12 +640,6 @@ void launch_patches_all(const DevLevelT<R>* lvs, const Span& patches, cudaStream
 }
 
 template <class R>
-void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s) {
-    g_launches++;
-    k_patch_scan<R><<<unsigned(jb - ja + 1), 1024, 0, s>>>(lvs, ja, nullptr, -1);
-}
-
-template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
                    int32_t* irr_count, int P, unsigned grid, cudaStream_t s) {
     g_launches += 2;
@@ -718,8 +677,6 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
 }
 
 #define SWW_INSTANTIATE(R)                                                                                   \
-    template void launch_pv_flux<R>(const WorkT<R>&, double, cudaStream_t);                                  \
-    template void launch_node_coriolis<R>(const WorkT<R>&, double, cudaStream_t);                            \
     template void launch_update<R>(const WorkT<R>&, const RKStage&, const double*, cudaStream_t);            \
     template void launch_save_base<R>(const WorkT<R>&, cudaStream_t);                                        \
     template void launch_fill<R>(const DevLevelT<R>&, const DevLevelT<R>&, const WorkT<R>&, cudaStream_t);   \
@@ -741,7 +698,6 @@ void launch_convert(const A* x, B* y, int64_t n, cudaStream_t s) {
     template void launch_patches_all<R>(const DevLevelT<R>*, const Span&, cudaStream_t);                     \
     template void launch_concat<R>(const DevLevelT<R>*, int, int, int32_t*, int32_t*, int32_t*, int32_t*, int,     \
                                    unsigned, cudaStream_t);         \
-    template void launch_patch_scan<R>(const DevLevelT<R>*, int, int, cudaStream_t);                         \
     template int sums_blocks<R>(const DevLevelT<R>&);                                                        \
     template void launch_sums<R>(const DevLevelT<R>&, double, double, double*, double*, cudaStream_t);       \
     template void launch_count<R>(const DevLevelT<R>&, unsigned long long*, cudaStream_t);

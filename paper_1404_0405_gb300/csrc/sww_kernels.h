@@ -56,8 +56,6 @@ struct MaskArgsT {
 
 // Launchers; R = double (FP64 form) or float (FP32 form), instantiated for both.
 // list kernels (active patches)
-template <class R> void launch_pv_flux(const WorkT<R>& W, double H, cudaStream_t s);
-template <class R> void launch_node_coriolis(const WorkT<R>& W, double g, cudaStream_t s);
 template <class R> void launch_update(const WorkT<R>& W, const RKStage& st, const double* dt, cudaStream_t s);
 template <class R> void launch_save_base(const WorkT<R>& W, cudaStream_t s);
 template <class R> void launch_fill(const DevLevelT<R>& F, const DevLevelT<R>& C, const WorkT<R>& W, cudaStream_t s);
@@ -96,8 +94,6 @@ template <class R> void launch_patches_all(const DevLevelT<R>* lvs, const Span& 
 template <class R>
 void launch_concat(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* all, int32_t* count, int32_t* irr,
                    int32_t* irr_count, int P, unsigned grid, cudaStream_t s);
-// ascending active-patch lists of levels ja..jb from the patch flags
-template <class R> void launch_patch_scan(const DevLevelT<R>* lvs, int ja, int jb, cudaStream_t s);
 template <class R> int sums_blocks(const DevLevelT<R>& L);
 template <class R>
 void launch_sums(const DevLevelT<R>& L, double H, double g, double* part, double* out, cudaStream_t s);

@@ -138,10 +138,11 @@ cudaError_t launch_trend_p(const BatchArgs<R>& a, int64_t entries, int64_t irr_e
     if (e != cudaSuccess) return e;
     }
     if (!(parts & 2)) return cudaSuccess;
-    // the irregular patches: a bound on their items per member
+    // the irregular patches: a bound on their items per member, at most two waves
+    // of 8 blocks per SM over all members
     const int64_t items = (irr_entries + a.nm - 1) / a.nm * 4 * a.P;
     const int bpm2 = int(std::max<int64_t>(1, std::min<int64_t>((items + TILE_TPB - 1) / TILE_TPB,
-                                                                   std::max(1, 8 * nsm / a.nm))));
+                                                                   std::max(1, 16 * nsm / a.nm))));
     count_launch(1);
     k_tile_irr<R><<<unsigned(a.nm * bpm2), TILE_TPB, 0, s>>>(a, bpm2);
     return cudaGetLastError();
