@@ -299,7 +299,8 @@ int sww_profile(sww_handle* h, uint32_t class_mask);
 
 /* Fault injection for tests of the bounded grid barrier of the persistent RK
  * stage (no counterpart in the paper).  Every barrier wait of the handle's later
- * stages gives up after spin_cycles SM clock cycles (0: the default, about 2 s),
+ * persistent stages (and their waits for a patch's geometry copy) gives up after
+ * spin_cycles SM clock cycles (0: the default, about 2 s),
  * sets the handle's error flag and lets the stage kernel return; the step then
  * returns SWW_E_TIMEOUT without advancing t, and the barrier state is reset so
  * that the next step runs normally.  skip_block >= 0 makes that block of each
