@@ -65,6 +65,22 @@ __global__ void k_gather_counts(const DevLevelT<R>* lvs, int jmin, int jmax, int
     if (j <= jmax) out[j] = *lvs[j].npatches;
 }
 
+// active patches of levels jmin..jmax for the statistics (the pole entry, the
+// largest index of an ascending list, left out), one thread per level
+template <class R>
+__global__ void k_stat_patches(const DevLevelT<R>* lvs, int jmin, int jmax, unsigned long long* out) {
+    const int j = jmin + int(threadIdx.x);
+    if (j > jmax) return;
+    const DevLevelT<R>& L = lvs[j];
+    const int32_t n = *L.npatches;
+    const bool pole = n > 0 && int64_t(L.patches[n - 1] & PATCH_MASK) == L.npatch;
+    out[j] = static_cast<unsigned long long>(n - (pole ? 1 : 0));
+}
+
+// statistics words of a handle: live nodes, ghost nodes and live edges of level j
+// at 3 j .. 3 j + 2, active patches of level j at STAT_PATCHES + j (levels 0..15)
+constexpr int STAT_PATCHES = 48, STAT_WORDS = 64;
+
 constexpr int GHOST_HOPS = 5;
 
 template <typename T>
@@ -1181,7 +1197,7 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
             if (coop) h->stage_cap = fp32 ? stage_grid<float>(h->S, h->nsm) : stage_grid<double>(h->S, h->nsm);
             h->stage_blocks = h->stage_cap;
         }
-        h->cnt = h->alloc<unsigned long long>(4);
+        h->cnt = h->alloc<unsigned long long>(STAT_WORDS);
         h->thr = h->alloc<double>(2);
         h->dt = h->alloc<double>(1);
         h->sums = h->alloc<double>(2);
@@ -1877,38 +1893,34 @@ int sww_stats_get(sww_handle* h, sww_stats* st) {
     if (!h || !st) return fail(SWW_E_ARG, "null argument");
     return guarded([&]() -> int {
         std::memset(st, 0, sizeof(*st));
-        for (int j = h->cfg.jmin; j <= h->cfg.jmax && j < 16; ++j) {
-            unsigned long long c[3] = {0, 0, 0};
-            {
-                Join jn(h);
-                ck(cudaMemsetAsync(h->cnt, 0, 3 * sizeof(unsigned long long), h->stream), "memset cnt");
-                by_prec(h, [&](auto r) {
-                    launch_count(lvl<decltype(r)>(h)[j], h->cnt, h->stream);
-                    return 0;
-                });
-                ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
-            }
-            ck(cudaStreamSynchronize(h->stream), "stats");
-            st->live_nodes[j] = int64_t(c[0]);
-            st->ghost_nodes[j] = int64_t(c[1]);
-            st->live_edges[j] = int64_t(c[2]);
-            int32_t np = 0;
-            int rc = sww_get_patches(h, j, nullptr, &np);
-            if (rc) return rc;
-            st->active_patches[j] = np;
-        }
+        const int j0 = h->cfg.jmin, j1 = std::min(h->cfg.jmax, 15);
+        // every level's counts, the active patch counts, the Jmin sums and the
+        // thresholds on the handle's stream, read back with one synchronisation
+        unsigned long long c[STAT_WORDS];
         double s[2], th[2];
         {
             Join jn(h);
+            ck(cudaMemsetAsync(h->cnt, 0, STAT_WORDS * sizeof(unsigned long long), h->stream), "memset cnt");
             by_prec(h, [&](auto r) {
-                launch_sums(lvl<decltype(r)>(h)[h->cfg.jmin], h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
+                using R = decltype(r);
+                for (int j = j0; j <= j1; ++j) launch_count(lvl<R>(h)[j], h->cnt + 3 * j, h->stream);
+                count_launch(1);
+                k_stat_patches<R><<<1, 32, 0, h->stream>>>(dlv<R>(h), j0, j1, h->cnt + STAT_PATCHES);
+                launch_sums(lvl<R>(h)[j0], h->cfg.H, h->cfg.g, h->part, h->sums, h->stream);
                 return 0;
             });
+            ck(cudaMemcpyAsync(c, h->cnt, sizeof(c), cudaMemcpyDeviceToHost, h->stream), "cnt");
             ck(cudaMemcpyAsync(s, h->sums, sizeof(s), cudaMemcpyDeviceToHost, h->stream), "sums");
             ck(cudaMemcpyAsync(th, h->thr, sizeof(th), cudaMemcpyDeviceToHost, h->stream), "thr");
             check_launch();
         }
         ck(cudaStreamSynchronize(h->stream), "stats");
+        for (int j = j0; j <= j1; ++j) {
+            st->live_nodes[j] = int64_t(c[3 * j]);
+            st->ghost_nodes[j] = int64_t(c[3 * j + 1]);
+            st->live_edges[j] = int64_t(c[3 * j + 2]);
+            st->active_patches[j] = int64_t(c[STAT_PATCHES + j]);
+        }
         double AS = 4.0 * M_PI * h->cfg.radius * h->cfg.radius;
         double c2 = h->cfg.g * s[0] / AS;
         st->mass = s[0];
