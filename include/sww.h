@@ -167,8 +167,9 @@ int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_p
  * Jmin..J receive them and their restrictions and are all live; the levels above
  * J hold no point until adaptation refines into them.  With a prescribed
  * velocity (advect) J must be Jmax (SWW_E_ARG otherwise).  Host fields with a
- * non-finite value are refused (SWW_E_NUMERIC) before any device work; device
- * fields are taken as given. */
+ * non-finite value are refused (SWW_E_NUMERIC) before the handle's state
+ * changes (they are copied into the handle's FP64 staging buffer and checked
+ * there); device fields are taken as given. */
 int sww_set_state_level(sww_handle* h, int level, const double* dh, const double* u, int device_ptrs);
 
 /* Adapt the grid (Sec. 2.3): wavelet coefficients at live points, thresholds

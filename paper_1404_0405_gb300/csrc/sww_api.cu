@@ -77,6 +77,15 @@ __global__ void k_stat_patches(const DevLevelT<R>* lvs, int jmin, int jmax, unsi
     out[j] = static_cast<unsigned long long>(n - (pole ? 1 : 0));
 }
 
+// sets *flag when a value of x[0..n) is not finite (exponent bits all ones)
+__global__ void k_nonfinite(const double* __restrict__ x, int64_t n, unsigned* flag) {
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    bool bad = false;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+        bad = bad || ((static_cast<unsigned long long>(__double_as_longlong(x[i])) >> 52) & 0x7ffull) == 0x7ffull;
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 // statistics words of a handle: live nodes, ghost nodes and live edges of level j
 // at 3 j .. 3 j + 2, active patches of level j at STAT_PATCHES + j (levels 0..15)
 constexpr int STAT_PATCHES = 48, STAT_WORDS = 64;
@@ -198,7 +207,7 @@ struct sww_handle {
     std::vector<DevLevelT<double>> lv;
     std::vector<DevLevelT<float>> lvf;
     void* d_lvs = nullptr;          // device copy of lv or lvf
-    double* stage = nullptr;        // FP64 staging buffer of FP32 handles (set_state)
+    double* stage = nullptr;        // FP64 staging buffer of host or FP32 input (set_state; N + E of Jmax)
     // learned refinement proposal: 0 off, 1 features only, 2 features and proposal
     int learn_mode = 0;
     float tau = 0.5f;
@@ -1282,21 +1291,48 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
     return guarded([&]() -> int {
         const int j0 = h->cfg.jmin, j1 = h->cfg.jmax;
         cudaStream_t s = h->stream;
+        const int64_t NJ = meta(h, J).N, EJ = meta(h, J).E;
+        // host fields: both copied into the FP64 staging buffer and checked there for
+        // a non-finite value (one kernel, one read-back), refused before the state
+        // changes; the state is then filled from the staging buffer
+        const bool staged = !device_ptrs;
+        if (staged) {
+            if (!h->stage) h->stage = h->alloc<double>(meta(h, j1).N + meta(h, j1).E);
+            unsigned bad = 0;
+            {
+                Join jn(h);
+                ck(cudaMemcpyAsync(h->stage, dh, NJ * sizeof(double), cudaMemcpyHostToDevice, s), "set_state dh");
+                ck(cudaMemcpyAsync(h->stage + NJ, u, EJ * sizeof(double), cudaMemcpyHostToDevice, s), "set_state u");
+                unsigned* flag = reinterpret_cast<unsigned*>(h->cnt);
+                ck(cudaMemsetAsync(flag, 0, sizeof(unsigned), s), "memset flag");
+                count_launch(1);
+                k_nonfinite<<<unsigned(std::min<int64_t>((NJ + EJ + 255) / 256, 4 * int64_t(h->nsm))), 256, 0, s>>>(
+                    h->stage, NJ + EJ, flag);
+                ck(cudaMemcpyAsync(&bad, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "flag");
+                check_launch();
+            }
+            ck(cudaStreamSynchronize(s), "set_state check");
+            if (bad) return fail(SWW_E_NUMERIC, "non-finite value in the initial fields");
+            dh = h->stage;
+            u = h->stage + NJ;
+        }
         by_prec(h, [&](auto r) {
             using R = decltype(r);
             Join jn(h);
             auto& lv = lvl<R>(h);
             DevLevelT<R>& F = lv[J];
-            cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
             if constexpr (std::is_same<R, double>::value) {
-                ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), kind, s), "set_state dh");
-                ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), kind, s), "set_state u");
-            } else {
+                ck(cudaMemcpyAsync(F.dh, dh, F.N * sizeof(double), cudaMemcpyDeviceToDevice, s), "set_state dh");
+                ck(cudaMemcpyAsync(F.u, u, F.E * sizeof(double), cudaMemcpyDeviceToDevice, s), "set_state u");
+            } else if (staged) {
                 // FP64 input rounded once to the working precision
-                if (!h->stage) h->stage = h->alloc<double>(std::max(meta(h, j1).N, meta(h, j1).E));
-                ck(cudaMemcpyAsync(h->stage, dh, F.N * sizeof(double), kind, s), "set_state dh");
+                launch_convert(dh, F.dh, F.N, s);
+                launch_convert(u, F.u, F.E, s);
+            } else {
+                if (!h->stage) h->stage = h->alloc<double>(meta(h, j1).N + meta(h, j1).E);
+                ck(cudaMemcpyAsync(h->stage, dh, F.N * sizeof(double), cudaMemcpyDeviceToDevice, s), "set_state dh");
                 launch_convert(h->stage, F.dh, F.N, s);
-                ck(cudaMemcpyAsync(h->stage, u, F.E * sizeof(double), kind, s), "set_state u");
+                ck(cudaMemcpyAsync(h->stage, u, F.E * sizeof(double), cudaMemcpyDeviceToDevice, s), "set_state u");
                 launch_convert(h->stage, F.u, F.E, s);
             }
             for (int j = J; j > j0; --j) launch_restrict_full(lv[j - 1], lv[j], s);
@@ -1331,15 +1367,6 @@ static int set_state_at(sww_handle* h, const double* dh, const double* u, int J,
     });
 }
 
-// host input: every value finite (checked before the device sees it; one pass
-// over the host cores)
-static bool all_finite(const double* x, int64_t n) {
-    int bad = 0;
-#pragma omp parallel for reduction(| : bad) schedule(static)
-    for (int64_t i = 0; i < n; ++i) bad |= std::isfinite(x[i]) ? 0 : 1;
-    return bad == 0;
-}
-
 int sww_set_state(sww_handle* h, const double* dh, const double* u, int device_ptrs) {
     if (!h || !dh || !u) return fail(SWW_E_ARG, "null argument");
     return sww_set_state_level(h, h->cfg.jmax, dh, u, device_ptrs);
@@ -1351,8 +1378,6 @@ int sww_set_state_level(sww_handle* h, int level, const double* dh, const double
     if (rc) return rc;
     if (h->cfg.advect && level != h->cfg.jmax)
         return fail(SWW_E_ARG, "a prescribed velocity is set on Jmax (it holds on every level)");
-    if (!device_ptrs && !(all_finite(dh, meta(h, level).N) && all_finite(u, meta(h, level).E)))
-        return fail(SWW_E_NUMERIC, "non-finite value in the initial fields");
     return set_state_at(h, dh, u, level, device_ptrs);
 }
 

@@ -188,7 +188,7 @@ def test_state_level_error_paths():
 
 def test_non_finite_initial_fields_are_refused():
     """A NaN or an infinity in host initial fields is refused (SWW_E_NUMERIC)
-    before any device work; valid fields then load as usual."""
+    before the handle's state changes; valid fields then load as usual."""
     import paper_1404_0405_gb300 as sww
     m, (dh, u) = _member(sww, "fp32", jmax=4)
     for bad_dh, bad_u in ((dh.copy(), u), (dh, u.copy())):
