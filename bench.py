@@ -344,7 +344,8 @@ TREND_TRAFFIC_PER_CELL = {"fp32": 85.9}
 
 
 def _live(m):
-    return sum(m.stats()["live_nodes"].values())
+    # the count the last set_state, adapt or step brought back (no device work)
+    return m.live_nodes()
 
 
 def _avail_st(st):
@@ -639,8 +640,8 @@ def run_ours(a, rank, world):
         if learned is not None:
             m.learn_stats(reset=True)
     # the library's launch counter is process-wide and read through stats(), which
-    # launches kernels itself (the live-cell counts around every timed step too):
-    # its own launches are counted and taken out
+    # launches kernels itself: its own launches are counted and taken out (the
+    # live-cell counts around the timed steps launch nothing)
     k_stats = ms[0].stats()["kernel_launches"]
     k_stats = ms[0].stats()["kernel_launches"] - k_stats
     launches0 = ms[0].stats()["kernel_launches"]
@@ -653,7 +654,7 @@ def run_ours(a, rank, world):
     times, cells = _timed(sww, ms, a.steps, flush, stream)
     torch.cuda.profiler.stop()
     clk = clocks.stop()
-    launches = ms[0].stats()["kernel_launches"] - launches0 - (2 * len(ms) * a.steps + 1) * k_stats
+    launches = ms[0].stats()["kernel_launches"] - launches0 - k_stats
     total_all, cells_all = combine_ranks(sum(times), sum(cells), "cuda", world)
     value = cells_all / total_all
     if learned is not None:
@@ -780,9 +781,10 @@ def run_ours(a, rank, world):
     e2e_s, ecells = combine_ranks(time.perf_counter() - t0, ecells, "cuda", world)
     N, E, _, _ = base.sizes(a.jmax)
     e2e = {"value": ecells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * (N + E) * len(ms) / a.steps),
-           "d2h_bytes_per_step": int(len(ms) * (8 + 8 * 70)),
+           "d2h_bytes_per_step": int(len(ms) * sww.BATCH_OUT_BYTES),
            "note": "per member sww_set_state from pinned host arrays and sww_adapt once, then per step "
-                   "sww_step_ensemble and sww_stats_get of every member"}
+                   "sww_step_ensemble (its read-back: each member's dt, error flag, patch and live "
+                   "counts) and sww_live_nodes of every member"}
 
     line = None
     if rank == 0:

@@ -25,13 +25,17 @@ MLP_PARAMS = MLP_FEATURES * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
 MLP_WORK = 256 * (MLP_PARAMS + 1)
 P_FEATURES, P_EXACT, P_PROPOSAL, P_ACTIVE = range(4)
 RK4, SSP43 = 0, 1
+# bytes a batched ensemble step copies back to the host per member: its time step,
+# error flag, and the active patch and live node counts of levels 0..15
+BATCH_OUT_BYTES = 144
+
 EXPORTS = ["sww_create", "sww_destroy", "sww_level_sizes", "sww_get_grid", "sww_set_state", "sww_adapt",
            "sww_mask_from_coeffs", "sww_rhs", "sww_step", "sww_get_level", "sww_set_level", "sww_get_patches",
            "sww_stats_get", "sww_last_error", "sww_profile", "sww_profile_read", "sww_mass_energy_static",
            "sww_create_shared", "sww_step_ensemble", "sww_set_learned", "sww_propose", "sww_get_patch_data",
            "sww_learn_stats", "sww_mlp_loss_grad", "sww_mlp_adam", "sww_mlp_predict", "sww_forward", "sww_inverse",
            "sww_get_coeffs", "sww_set_coeffs", "sww_get_state", "sww_save", "sww_load", "sww_set_state_level",
-           "sww_get_mask", "sww_barrier_fault"]
+           "sww_get_mask", "sww_barrier_fault", "sww_live_nodes"]
 KERNEL_CLASSES = ["trend", "irregular", "node", "reserved", "restrict", "update", "fill", "partial", "coeff", "mask",
                   "inverse", "dt", "stage"]
 
@@ -94,6 +98,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "sww_get_level": [P, I, I, P],
         "sww_set_level": [P, I, P, P],
         "sww_get_patches": [P, I, P, ctypes.POINTER(ctypes.c_int32)],
+        "sww_live_nodes": [P, ctypes.POINTER(ctypes.c_int64)],
         "sww_stats_get": [P, ctypes.POINTER(Stats)],
         "sww_last_error": [ctypes.c_char_p, ctypes.c_size_t],
         "sww_profile": [P, ctypes.c_uint32],
@@ -320,6 +325,13 @@ class Model:
         a = None if dh is None else np.ascontiguousarray(dh, dtype=np.float64)
         b = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
         _check(load().sww_set_level(self._h, level, None if a is None else _ptr(a)[0], None if b is None else _ptr(b)[0]))
+
+    def live_nodes(self):
+        """Live nodes over every level as of the last set_state, adapt or step
+        (sww_live_nodes: no device work)."""
+        n = ctypes.c_int64()
+        _check(load().sww_live_nodes(self._h, ctypes.byref(n)))
+        return n.value
 
     def patches(self, level):
         n = self.sizes(level)[3]

@@ -59,10 +59,15 @@ __global__ void k_reset_red(unsigned long long* red) {
     if (blockIdx.x == 0 && threadIdx.x < RED_WORDS) red[threadIdx.x] = 0ull;
 }
 
+// per level: the active patch list's size at out[j], the live nodes at
+// out[jmax + 1 + j]
 template <class R>
 __global__ void k_gather_counts(const DevLevelT<R>* lvs, int jmin, int jmax, int32_t* out) {
     int j = jmin + int(threadIdx.x);
-    if (j <= jmax) out[j] = *lvs[j].npatches;
+    if (j <= jmax) {
+        out[j] = *lvs[j].npatches;
+        out[jmax + 1 + j] = lvs[j].wl_n[WL_LIVE];
+    }
 }
 
 // active patches of levels jmin..jmax for the statistics (the pole entry, the
@@ -247,7 +252,7 @@ struct sww_handle {
     // candidate lists of the list-based mask (all levels)
     int32_t *cand = nullptr, *cand_count = nullptr, *gcand = nullptr, *gcand_count = nullptr;
     int64_t total_entries = 0;
-    int32_t* h_counts = nullptr;    // pinned: per-level list sizes after each step
+    int32_t* h_counts = nullptr;    // pinned: per-level list sizes, then live nodes, after each step
     double* h_dt = nullptr;         // pinned: time step of the last step
     int S = 64, jtop = 0, nsm = 152;
     unsigned grid_all = 1;
@@ -507,8 +512,8 @@ void alloc_state(sww_handle* h, int j) {
     D.patches = h->alloc<int32_t>(D.npatch + 1);
     D.npatches = h->alloc<int32_t>(1);
     D.wl = h->alloc<int32_t>(3 * N + 2 * E);
-    D.wl_n = h->alloc<int32_t>(WL_KINDS);
-    ck(cudaMemset(D.wl_n, 0, WL_KINDS * sizeof(int32_t)), "memset");
+    D.wl_n = h->alloc<int32_t>(WL_WORDS);
+    ck(cudaMemset(D.wl_n, 0, WL_WORDS * sizeof(int32_t)), "memset");
     uint8_t** cf[] = {&D.zflag, &D.sflag, &D.cflag, &D.lflag, &D.gflag};
     for (auto p : cf) {
         *p = h->alloc<uint8_t>(D.npatch + 1);
@@ -683,7 +688,8 @@ template <class R>
 void read_counts(sww_handle* h) {
     count_launch(1);
     k_gather_counts<R><<<1, 32, 0, h->stream>>>(dlv<R>(h), h->cfg.jmin, h->cfg.jmax, h->d_counts);
-    ck(cudaMemcpyAsync(h->h_counts, h->d_counts, sizeof(int32_t) * (h->cfg.jmax + 1), cudaMemcpyDeviceToHost, h->stream),
+    ck(cudaMemcpyAsync(h->h_counts, h->d_counts, sizeof(int32_t) * 2 * (h->cfg.jmax + 1), cudaMemcpyDeviceToHost,
+                       h->stream),
        "counts");
 }
 
@@ -1181,12 +1187,13 @@ int create_handle(const sww_config* cfg, void* stream, std::shared_ptr<Geometry>
         h->gcand_count = h->alloc<int32_t>(1);
         ck(cudaMemset(h->cand_count, 0, sizeof(int32_t)), "memset");
         ck(cudaMemset(h->gcand_count, 0, sizeof(int32_t)), "memset");
-        h->d_counts = h->alloc<int32_t>(cfg->jmax + 1);
+        h->d_counts = h->alloc<int32_t>(2 * (cfg->jmax + 1));
+        ck(cudaMemset(h->d_counts, 0, sizeof(int32_t) * 2 * (cfg->jmax + 1)), "memset");
         h->sig_any = h->alloc<int32_t>(cfg->jmax + 2);
         ck(cudaMemset(h->sig_any, 0, sizeof(int32_t) * (cfg->jmax + 2)), "memset");
-        ck(cudaMallocHost(&h->h_counts, sizeof(int32_t) * (cfg->jmax + 1)), "cudaMallocHost");
+        ck(cudaMallocHost(&h->h_counts, sizeof(int32_t) * 2 * (cfg->jmax + 1)), "cudaMallocHost");
         ck(cudaMallocHost(&h->h_dt, sizeof(double)), "cudaMallocHost");
-        std::memset(h->h_counts, 0, sizeof(int32_t) * (cfg->jmax + 1));
+        std::memset(h->h_counts, 0, sizeof(int32_t) * 2 * (cfg->jmax + 1));
         *h->h_dt = 0;
         h->red = h->alloc<unsigned long long>(RED_WORDS);
         ck(cudaMemset(h->red, 0, RED_WORDS * sizeof(unsigned long long)), "memset");
@@ -1531,7 +1538,10 @@ int sww_step_ensemble(sww_handle* const* hs, int n, double dt, int nsteps, int d
                     sww_handle* h = hs[i];
                     *h->h_dt = o[i].dt;
                     *h->h_err = o[i].err;
-                    for (int j = 0; j <= h->cfg.jmax && j < 16; ++j) h->h_counts[j] = o[i].counts[j];
+                    for (int j = 0; j <= h->cfg.jmax && j < 16; ++j) {
+                        h->h_counts[j] = o[i].counts[j];
+                        h->h_counts[h->cfg.jmax + 1 + j] = o[i].live[j];
+                    }
                     rc = finish(h);
                 }
             }
@@ -1877,6 +1887,14 @@ int sww_load(sww_handle* h, const char* path) {
             return SWW_OK;
         });
     });
+}
+
+int sww_live_nodes(const sww_handle* h, int64_t* total) {
+    if (!h || !total) return fail(SWW_E_ARG, "null argument");
+    int64_t n = 0;
+    for (int j = h->cfg.jmin; j <= h->cfg.jmax; ++j) n += h->h_counts[h->cfg.jmax + 1 + j];
+    *total = h->has_state ? n : 0;
+    return SWW_OK;
 }
 
 int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count) {

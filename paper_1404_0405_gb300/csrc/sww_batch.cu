@@ -112,7 +112,11 @@ __global__ void __launch_bounds__(BATCH_TPB, 8) k_phase_batch(BatchArgs<R> a, in
     if (phase == PH_OUT) {
         BatchOut* o = reinterpret_cast<BatchOut*>(a.out) + m;
         const int t = threadIdx.x;
-        if (t < 16) o->counts[t] = (t >= a.jmin && t <= mr->jmax) ? *mr->lvs[t].npatches : 0;
+        if (t < 16) {
+            const bool in = t >= a.jmin && t <= mr->jmax;
+            o->counts[t] = in ? *mr->lvs[t].npatches : 0;
+            o->live[t] = in ? mr->lvs[t].wl_n[WL_LIVE] : 0;
+        }
         if (t == 0) {
             o->dt = *mr->dt;
             o->err = *mr->err;

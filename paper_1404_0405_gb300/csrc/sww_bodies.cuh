@@ -754,7 +754,7 @@ __device__ void concat_lists(const DevLevelT<R>* __restrict__ lvs, int jmin, int
     // the point work lists are rebuilt from these lists next (wl_build)
     for (int j = jmin + int(threadIdx.x); j <= jmax && threadIdx.x < 32; j += 32)
         if (lvs[j].wl_n)
-            for (int k = 0; k < WL_KINDS; ++k) lvs[j].wl_n[k] = 0;
+            for (int k = 0; k < WL_WORDS; ++k) lvs[j].wl_n[k] = 0;
 }
 
 // offset of work list k of a level in wl
@@ -782,12 +782,17 @@ __device__ __forceinline__ void wl_push(const DevLevelT<R>& L, int k, bool pred,
 // The point work lists of one item of an active patch (node or edge, see
 // visit_item): ghost points, covered nodes, edges with a covered end, and
 // available nodes with a covered node among themselves and their neighbours (their
-// divergence changes with the restricted fluxes).  The order of the lists is not
-// fixed; every item's work is independent of it.
+// divergence changes with the restricted fluxes); and the count of live nodes.
+// The order of the lists is not fixed; every item's work is independent of it.
 template <class R>
 __device__ __forceinline__ void wl_item(const DevLevelT<R>& L, int kind, int64_t id) {
     if (kind == K_NODE) {
         const uint8_t f = L.nflag[id];
+        {   // the level's live nodes (warp-aggregated)
+            const unsigned act = __activemask();
+            const unsigned m = __ballot_sync(act, (f & LIVE) != 0);
+            if ((threadIdx.x & 31) == __ffs(act) - 1 && m) atomicAdd(&L.wl_n[WL_LIVE], __popc(m));
+        }
         wl_push(L, WL_GN, (f & GHOST) != 0, int32_t(id));
         wl_push(L, WL_CN, (f & COVERED) != 0, int32_t(id));
         wl_push(L, WL_DN, restricted_div_node(L, id), int32_t(id));

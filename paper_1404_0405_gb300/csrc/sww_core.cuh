@@ -15,8 +15,9 @@ constexpr int NF = 8, NH = 32, NB = 24;
 constexpr int MLP_PARAMS = NF * NH + NH + NH + 1;   // W1[NF][NH], b1[NH], w2[NH], b2
 
 // Work lists of a level (DevLevelT::wl): ghost nodes, ghost edges, covered nodes,
-// edges with a covered end, nodes whose divergence the restriction changes.
-constexpr int WL_GN = 0, WL_GE = 1, WL_CN = 2, WL_RE = 3, WL_DN = 4, WL_KINDS = 5;
+// edges with a covered end, nodes whose divergence the restriction changes; and the
+// level's live-node count, taken in the same pass (wl_n[WL_LIVE]).
+constexpr int WL_GN = 0, WL_GE = 1, WL_CN = 2, WL_RE = 3, WL_DN = 4, WL_KINDS = 5, WL_LIVE = 5, WL_WORDS = 6;
 
 // Work-list entry: (level << LVL_SHIFT) | patch; patch == npatch stands for the two poles.
 constexpr int LVL_SHIFT = 27;
@@ -95,7 +96,7 @@ struct DevLevelT {
     // (after every adaptation): ghost nodes [N], ghost edges [E], covered nodes [N],
     // edges with a covered end [E], available nodes with a covered node among them and
     // their neighbours [N], at offsets 0, N, N+E, 2N+E, 2N+2E of wl; their counts in
-    // wl_n[0..4]
+    // wl_n[0..4]; wl_n[WL_LIVE] the level's live nodes
     int32_t* wl;
     int32_t* wl_n;
     // candidate patches of the list-based mask (index npatch: the two poles)

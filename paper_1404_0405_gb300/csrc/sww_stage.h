@@ -70,17 +70,19 @@ struct BatchArgs {
     unsigned* bar;
     int* err;
     double dt_given;   // phases before the stages: > 0 sets every member's time step
-    void* out;         // read-back records, one per member (BATCH_OUT_BYTES each)
+    void* out;         // read-back records, one per member (BatchOut, below)
 };
 
-// Read-back record of one member after a batched step: dt, the error flag and the
-// active patch count of each level 0..15.
+// Read-back record of one member after a batched step: dt, the error flag, and the
+// active patch count and the live nodes of each level 0..15.
 struct BatchOut {
     double dt;
     int32_t err;
     int32_t counts[16];
+    int32_t live[16];   // live nodes of each level
     int32_t pad;
 };
+static_assert(sizeof(BatchOut) == 144, "read-back record size (the Python binding's BATCH_OUT_BYTES)");
 
 // co-resident blocks of the stage kernel for patch area P on nsm SMs (0 when it
 // cannot run)

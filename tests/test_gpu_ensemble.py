@@ -175,3 +175,37 @@ def test_phased_members_with_proposal_match_single_runs(adapt):
         for k in fa:
             assert np.array_equal(fa[k], fb[k]), k
         assert a.learn_stats() == b.learn_stats()
+
+
+@pytest.mark.parametrize("persistent", ["auto", "phased"])
+def test_live_node_count_follows_the_mask(persistent):
+    """sww_live_nodes (the count the last set_state, adapt or step brought back)
+    equals the live nodes counted from the flags by sww_stats_get, after every
+    call that changes the mask, for single and ensemble steps."""
+    import paper_1404_0405_gb300 as sww
+    jmin, top = 2, max(j for j, _, _ in MEMBERS)
+    base = sww.Model(jmin, top, patch=4)
+    ms = []
+    for jmax, eps, seed in MEMBERS:
+        m = sww.Model(jmin, jmax, patch=4, eps=eps, share=base, precision="fp32", persistent=persistent)
+        assert m.live_nodes() == 0
+        m.set_state(*_fields(m, seed))
+        ms.append(m)
+
+    def check(where):
+        for i, m in enumerate(ms):
+            want = sum(m.stats()["live_nodes"].values())
+            assert want > 0
+            assert m.live_nodes() == want, f"{where}, member {i}"
+
+    check("set_state")
+    for m in ms:
+        m.adapt()
+    check("adapt")
+    ms[0].step(-1.0, 2, True)
+    ms[1].step(-1.0, 1, False)
+    check("single steps")
+    sww.step_ensemble(ms, -1.0, 3, True)
+    check("ensemble steps")
+    sww.step_ensemble(ms, 120.0, 1, False)
+    check("ensemble step without adaptation")
