@@ -770,21 +770,29 @@ def run_ours(a, rank, world):
         host.append((torch.from_numpy(dh).pin_memory().numpy(), torch.from_numpy(u).pin_memory().numpy()))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    t_set = t_adapt = 0.0   # host time in the calls (each returns after its work)
     for m, (dh, u) in zip(ms, host):
+        t1 = time.perf_counter()
         m.set_state(dh, u)
+        t2 = time.perf_counter()
         m.adapt()
+        t_set, t_adapt = t_set + (t2 - t1), t_adapt + (time.perf_counter() - t2)
+    t_steps = time.perf_counter()
     ecells = 0.0
     for _ in range(a.steps):
         sww.step_ensemble(ms, -1.0, 1, True)
         ecells += sum(_live(m) for m in ms)
     torch.cuda.synchronize()
-    e2e_s, ecells = combine_ranks(time.perf_counter() - t0, ecells, "cuda", world)
+    t_end = time.perf_counter()
+    e2e_s, ecells = combine_ranks(t_end - t0, ecells, "cuda", world)
     N, E, _, _ = base.sizes(a.jmax)
     e2e = {"value": ecells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(8 * (N + E) * len(ms) / a.steps),
            "d2h_bytes_per_step": int(len(ms) * sww.BATCH_OUT_BYTES),
+           "breakdown_ms": {"set_state": 1e3 * t_set, "adapt": 1e3 * t_adapt, "steps": 1e3 * (t_end - t_steps)},
+           "set_state_h2d_gbs": 8 * (N + E) * len(ms) / max(t_set, 1e-9) / 1e9,
            "note": "per member sww_set_state from pinned host arrays and sww_adapt once, then per step "
                    "sww_step_ensemble (its read-back: each member's dt, error flag, patch and live "
-                   "counts) and sww_live_nodes of every member"}
+                   "counts) and sww_live_nodes of every member; breakdown_ms on rank 0's host clock"}
 
     line = None
     if rank == 0:

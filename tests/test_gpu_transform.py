@@ -188,12 +188,17 @@ def test_state_level_error_paths():
 
 def test_non_finite_initial_fields_are_refused():
     """A NaN or an infinity in host initial fields is refused (SWW_E_NUMERIC)
-    before the handle's state changes; valid fields then load as usual."""
+    before the handle's state changes, wherever it sits (the first, middle and
+    last value of either field); valid fields then load as usual."""
     import paper_1404_0405_gb300 as sww
     m, (dh, u) = _member(sww, "fp32", jmax=4)
-    for bad_dh, bad_u in ((dh.copy(), u), (dh, u.copy())):
-        arr = bad_dh if bad_dh is not dh else bad_u
-        arr[len(arr) // 2] = np.nan if arr is bad_dh else np.inf
+    n, total = len(dh), len(dh) + len(u)
+    for i in (0, n // 2, n - 1, n, n + len(u) // 2, total - 1):
+        bad_dh, bad_u = (dh.copy(), u) if i < n else (dh, u.copy())
+        if i < n:
+            bad_dh[i] = np.nan
+        else:
+            bad_u[i - n] = np.inf
         with pytest.raises(sww.SwwError, match="non-finite"):
             m.set_state(bad_dh, bad_u)
     with pytest.raises(sww.SwwError):
@@ -213,3 +218,24 @@ def test_mask_call_matches_level_flags():
         assert np.array_equal(nodes, P.lib.get(j, sww.NODE_FLAGS))
         assert np.array_equal(edges, P.lib.get(j, sww.EDGE_FLAGS))
     P.check_masks()
+
+
+def test_host_fields_load_alike_from_pageable_pinned_and_device_memory():
+    """The same fields from pageable host arrays, pinned host arrays and CUDA
+    tensors give the same state, bit for bit, on every level."""
+    import torch
+    import paper_1404_0405_gb300 as sww
+    got = []
+    for kind in ("pageable", "pinned", "device"):
+        m, (dh, u) = _member(sww, "fp64", jmax=5)
+        if kind == "pinned":
+            dh, u = (torch.from_numpy(x).pin_memory().numpy() for x in (dh, u))
+        elif kind == "device":
+            dh, u = (torch.from_numpy(x).cuda() for x in (dh, u))
+        m.set_state(dh, u)
+        m.adapt()
+        got.append(_snapshot(sww, m))
+    for other in got[1:]:
+        assert other[1] == got[0][1]
+        for x, y in zip(got[0][0], other[0]):
+            assert np.array_equal(x, y)
