@@ -267,10 +267,11 @@ int sww_load(sww_handle* h, const char* path);
 int sww_get_patches(const sww_handle* h, int level, int32_t* out, int32_t* count);
 
 /* Live nodes over every level (the adapted grid's size, Sec. 2.3), as of the
- * handle's last sww_set_state, sww_adapt or step: the count those calls already
- * brought back with their read-back, so this call does no device work and does
- * not synchronise.  *total is 0 before the first sww_set_state.  SWW_E_ARG for a
- * null argument. */
+ * handle's last call that set its mask (sww_set_state, sww_set_state_level,
+ * sww_adapt, sww_mask_from_coeffs, sww_step, sww_step_ensemble, sww_load): the
+ * count those calls already brought back with their read-back, so this call does
+ * no device work and does not synchronise.  *total is 0 before the first state is
+ * set.  SWW_E_ARG for a null argument. */
 int sww_live_nodes(const sww_handle* h, int64_t* total);
 
 /* Diagnostics (synchronises the stream). */
