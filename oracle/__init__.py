@@ -25,5 +25,6 @@ garbled or ambiguous the reading taken is stated in the docstring.
 
 Parity unpinned: the basic flux restriction R_F0 against the paper's own formula,
 which rests on a figure absent from the text.  R_F0 is pinned only by the
-commutation identity R_h(div F) = div(R_F F) and by uniform-flow consistency.
+commutation identity R_h(div F) = div(R_F F) and by the convergence of a smooth
+flow's restricted flux to the coarse flux as the levels refine.
 """
