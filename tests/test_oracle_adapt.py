@@ -1,8 +1,13 @@
 """Pins for the oracle's adapted grid and adaptive step (Sec. 2.3, Sec. 3.1).
 
 * the mask equals a literal set construction written with Python sets and
-  loops (one rule at a time, as the rules are stated);
-* the ghost band equals breadth-first distances;
+  loops (one rule at a time, as the rules are stated), and so does the
+  significance step;
+* the ghost band equals breadth-first distances, and the ghost values equal
+  the inverse transform of the full levels with zero coefficients away from
+  live points;
+* the thresholds read live points only; Delta t equals a brute-force CFL
+  minimum over every live point;
 * mass is conserved to roundoff over adaptive steps (Sec. 4.1, Eq. divRcommute);
 * trends at covered coarse nodes are the restriction of the fine trends;
 * the adapted solution tracks the uniform fine solution with an error that
@@ -174,19 +179,25 @@ def test_uniform_field_is_reproduced_exactly():
 
 
 def test_dt_is_cfl_minimum():
+    """Delta t = CFL min(1/omega_max, min dx/|u|) over the live points (Sec. 3.1,
+    reading 2: omega = sqrt(f^2 + g h (pi/dx)^2), f = 2 Omega sin(latitude), dx the
+    level's Table 1 spacing), by brute force over every live node and edge."""
     M = make_model()
-    dt = M.dt_cfl()
-    # brute force over live points with the reading omega = sqrt(f^2 + g h (pi/dx)^2)
+    M.step(200.0)
     best = math.inf
     for j in M.levels:
         L = M.Hy.levels[j]
         dx = grid.nominal_spacing(j, L.radius)
-        for i in np.nonzero(M.live_n[j])[0][:: max(1, L.N // 200)]:
-            f = 2 * M.Hy.omega * L.xyz[i, 2]
-            w = math.sqrt(f * f + M.g * (M.H + M.dh[j][i]) * (math.pi / dx) ** 2)
-            best = min(best, 1 / w)
-    assert dt <= M.cfl * best * (1 + 1e-12)
-    assert dt > 0.3 * M.cfl * best
+        for i in np.nonzero(M.live_n[j])[0]:
+            x, y, z = (float(v) for v in L.xyz[i])
+            f = 2.0 * M.Hy.omega * z / math.sqrt(x * x + y * y + z * z)
+            w = math.sqrt(f * f + M.g * (M.H + float(M.dh[j][i])) * (math.pi / dx) ** 2)
+            best = min(best, 1.0 / w)
+        for e in np.nonzero(M.live_e[j])[0]:
+            a = abs(float(M.u[j][e]))
+            if a > 0:
+                best = min(best, dx / a)
+    assert abs(M.dt_cfl() - M.cfl * best) <= 1e-14 * M.cfl * best
 
 
 def test_error_controlled_by_eps():
@@ -255,3 +266,89 @@ def test_uniform_reconstruction_error_bounded_by_threshold(kind, seed):
     h5, u5 = M.get_uniform(5)
     assert M.live_n[5].sum() == 0
     assert np.abs(h5 - 7.0).max() < 1e-12 and np.abs(u5).max() == 0.0
+
+
+def test_significance_matches_literal_rules():
+    """Step 1 of the mask (Sec. 2.3, reading 1) by loops over the points: an odd
+    node with a significant height coefficient; both ends and the midpoint of a
+    coarse edge with a significant velocity coefficient; both ends of an interior
+    fine edge with a significant one; only live points carry coefficients."""
+    M = make_model(2, 4)
+    Hy = M.Hy
+    rng = np.random.default_rng(3)
+    for j in (3, 4):
+        C, F = Hy.levels[j - 1], Hy.levels[j]
+        VS = M.VS[j]
+        odd = Hy.odd[j]
+        hdet = np.where(M.live_n[j][odd], rng.standard_normal(odd.size), np.nan)
+        any_half = M.live_e[j][VS.half[:, 0]] | M.live_e[j][VS.half[:, 1]]
+        ue = np.where(any_half, rng.standard_normal(C.E), np.nan)
+        ui = np.where(M.live_e[j][VS.int_edge], rng.standard_normal(VS.int_edge.shape), np.nan)
+        eps_h, eps_u = 1.2, 1.5
+        S = adapt.significance(Hy, j, M.live_n[j], M.live_e[j], hdet, ue, ui, VS, eps_h, eps_u)
+        want = set()
+        for r, m in enumerate(odd):
+            if M.live_n[j][m] and abs(hdet[r]) >= eps_h:
+                want.add(int(m))
+        for E in range(C.E):
+            if not np.isnan(ue[E]) and abs(ue[E]) >= eps_u:
+                want |= {int(C.edges[E, 0]), int(C.edges[E, 1]), int(Hy.mid[j - 1][E])}
+        for t in range(C.T):
+            for c in range(3):
+                fe = VS.int_edge[t, c]
+                if M.live_e[j][fe] and abs(ui[t, c]) >= eps_u:
+                    want |= {int(F.edges[fe, 0]), int(F.edges[fe, 1])}
+        assert set(np.nonzero(S)[0].tolist()) == want
+
+
+def test_ghost_values_are_the_zero_detail_inverse():
+    """Ghost values (reading, step 5) are the inverse transform (Eqs. 1-2) of the
+    full levels with every coefficient away from live points set to zero: build
+    the full levels from Jmin up with the transforms alone, then compare the live
+    and ghost values of every level after an adaptive step."""
+    M = make_model(2, 5)
+    M.step(200.0)
+    Hy = M.Hy
+    hfull, ufull = M.dh[2].copy(), M.u[2].copy()
+    for j in range(3, 6):
+        C, F = Hy.levels[j - 1], Hy.levels[j]
+        VS = M.VS[j]
+        odd = Hy.odd[j]
+        with np.errstate(invalid="ignore"):
+            d = transform.height_detail(Hy, j, M.dh[j])
+            de, di = transform.velocity_detail(VS, ufull, M.u[j])
+        d = np.where(M.live_n[j][odd], d, 0.0)
+        any_half = M.live_e[j][VS.half[:, 0]] | M.live_e[j][VS.half[:, 1]]
+        de = np.where(any_half, de, 0.0)
+        di = np.where(M.live_e[j][VS.int_edge], di, 0.0)
+        assert np.isfinite(d).all() and np.isfinite(de).all() and np.isfinite(di).all()
+        hfull = transform.inverse_height(Hy, j, hfull, d)
+        ufull = transform.inverse_velocity(VS, ufull, de, di, F.E)
+        for name, full, got, live, ghost in (("dh", hfull, M.dh[j], M.live_n[j], M.ghost_n[j]),
+                                             ("u", ufull, M.u[j], M.live_e[j], M.ghost_e[j])):
+            scale = np.abs(full).max()
+            assert ghost.sum() > 0
+            assert np.abs(got[live] - full[live]).max() <= 1e-12 * scale, (name, j, "live")
+            assert np.abs(got[ghost] - full[ghost]).max() <= 1e-12 * scale, (name, j, "ghost")
+
+
+def test_thresholds_read_live_points_only():
+    """eps_h = eps max|dh| and eps_u = eps max|u| over the live points (reading 11):
+    a large ghost value leaves them alone, a large live value sets them; with eps
+    read as the trend tolerance (regime 1) both scale by eps^{3/2}, i.e. by
+    sqrt(eps) against regime 0 (reading 22)."""
+    M = make_model(2, 4)
+    th = M.thresholds()
+    j = 4
+    gn, ge = np.nonzero(M.ghost_n[j])[0], np.nonzero(M.ghost_e[j])[0]
+    assert gn.size and ge.size
+    M.dh[j][gn[0]], M.u[j][ge[0]] = 1e9, 1e9
+    assert M.thresholds() == th
+    M.regime = 1
+    r = M.thresholds()
+    assert math.isclose(r[0], th[0] * math.sqrt(M.eps), rel_tol=1e-14)
+    assert math.isclose(r[1], th[1] * math.sqrt(M.eps), rel_tol=1e-14)
+    M.regime = 0
+    ln, le = np.nonzero(M.live_n[j])[0], np.nonzero(M.live_e[j])[0]
+    M.dh[j][ln[0]], M.u[j][le[0]] = -1e9, 1e9
+    assert M.thresholds() == (M.eps * 1e9, M.eps * 1e9)

@@ -4,7 +4,8 @@
   and round half to even with numpy's rint;
 * the chain-rule gradient against central finite differences of the loss;
 * closed forms: logit 0 gives loss log 2 for either label; a zero network's
-  gradient of b2 is the mean of (p - y) weighted by the class weight;
+  gradient of b2 is the mean of (p - y) weighted by the class weight; Adam's
+  bias-corrected step under a constant gradient;
 * the mask with an external proposal: extra nodes join T before the closure, as
   a literal set construction."""
 import math
@@ -69,6 +70,21 @@ def test_closed_forms():
     y = np.array([1.0, 0.0, 0.0, 1.0])
     L, _, _, _, db2 = mlp.loss_grad(X, y, z, b, b, 0.0, 2.0)
     assert abs(db2 - np.mean(2.0 * y * (0.5 - 1) + (1 - y) * 0.5)) < 1e-15
+
+
+def test_adam_steps_of_a_constant_gradient():
+    """Adam (Kingma & Ba) with its bias corrections: under a constant gradient the
+    corrected moments are the gradient and its square at every step, so each
+    update is lr g / (|g| + eps), the first one included."""
+    rng = np.random.default_rng(2)
+    g = rng.standard_normal(50)
+    p = rng.standard_normal(50)
+    m, v = np.zeros(50), np.zeros(50)
+    lr = 1e-3
+    for t in range(1, 6):
+        q, m, v = mlp.adam(p, g, m, v, t, lr)
+        assert np.allclose(p - q, lr * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+        p = q
 
 
 def test_mask_with_external_proposal():
