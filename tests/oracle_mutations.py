@@ -80,6 +80,14 @@ MUTATIONS = [  # (oracle file, text, replacement, label[, why it cannot change a
  ("mlp.py", "g = (pos_w * y * (p - 1.0) + (1.0 - y) * p) / n", "g = (y * (p - 1.0) + (1.0 - y) * p) / n", "gradient without pos_w"),
  ("mlp.py", "return L, X.T @ dz, dz.sum(axis=0), a.T @ g, float(g.sum())", "return L, X.T @ dz, dz.sum(axis=0), z.T @ g, float(g.sum())", "w2 gradient pre-activation"),
  ("mlp.py", "mh = m / (1 - b1 ** t)", "mh = m", "Adam bias correction"),
+ ("transform.py", "np.subtract.at(even, Hy.K[j].ravel(), (s * hdet[:, None]).ravel())", "np.add.at(even, Hy.K[j].ravel(), (s * hdet[:, None]).ravel())", "inverse update sign"),
+ ("transform.py", "hf[Hy.odd[j]] = hdet + np.sum(st * even[Hy.K[j]], axis=1)", "hf[Hy.odd[j]] = hdet + np.sum(st * hc[Hy.K[j]], axis=1)", "inverse predicts from coarse"),
+ ("model.py", "        return self.live_n[j + 1][: C.N] & ~bad", "        return ~bad", "covered without the even node",
+  "equivalent under the closure: a live odd node of M_k makes k's even node live (k is one of its parents)"),
+ ("model.py", "                F[j][rf] = Fint[rf] / C.l_e[rf]", "                F[j][rf] = Fint[rf] / C.d_e[rf]", "restricted flux over d_e"),
+ ("model.py", "dx = grid.nominal_spacing(j, L.radius)", "dx = grid.nominal_spacing(self.jmax, L.radius)", "dt spacing of Jmax"),
+ ("trisk.py", "out += np.where(ok, L.nbr_sign[:, k] * F[ee] * L.l_e[ee], 0.0)", "out += np.where(ok, F[ee] * L.l_e[ee], 0.0)", "div without orientation"),
+ ("adapt.py", "        out[nb[ok & S]] = True", "        out[nb[ok]] = True", "dilate everything"),
 ]
 
 
