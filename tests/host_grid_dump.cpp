@@ -58,6 +58,8 @@ int main(int argc, char** argv) {
         put(dir, p + "A_v", L.A_v);
         put(dir, p + "d_e", L.d_e);
         put(dir, p + "l_e", L.l_e);
+        put(dir, p + "f_v", L.f_v);
+        put(dir, p + "f_n", L.f_n);
         put_slots(dir, p + "cor_i", L.cor_i, COR);
         put_slots(dir, p + "cor_w", L.cor_w, COR);
         put_slots(dir, p + "et", L.et, 2);
@@ -66,12 +68,15 @@ int main(int argc, char** argv) {
         if (j > jmin) {
             put_slots(dir, p + "par", L.par, 4);
             put_slots(dir, p + "akm", L.akm, 4);
+            put_slots(dir, p + "ptw", L.ptw, 4);
             put_slots(dir, p + "vst", L.vst, VST);
             put_slots(dir, p + "vw", L.vw, VST);
         }
         if (j < jmax) {
             put(dir, p + "c2f", L.c2f);
             put_slots(dir, p + "half", L.half, 2);
+            put_slots(dir, p + "mk_i", L.mk_i, 12);
+            put_slots(dir, p + "mk_w", L.mk_w, 12);
             put_slots(dir, p + "rf_fi", L.rf_fi, RF_F);
             put_slots(dir, p + "rf_fw", L.rf_fw, RF_F);
             put_slots(dir, p + "rf_ci", L.rf_ci, RF_C);

@@ -83,6 +83,48 @@ def test_topology_and_geometry(dump, ora, maps):
         assert np.array_equal(M.tri[et[0]], left_ora)
 
 
+def test_coriolis_parameters(dump, ora, maps):
+    """f = 2 Omega sin(latitude) at the triangles' circumcentres (the hexagon
+    vertices) and at the nodes."""
+    two_omega = 2.0 * ora.omega
+    for j in range(JMIN, JMAX + 1):
+        L, M = ora.levels[j], maps[j]
+        fv = dump(f"L{j}_f_v", np.float64)
+        assert np.abs(fv - L.f_v[M.tri]).max() < geo_tol(j) * two_omega
+        fn = dump(f"L{j}_f_n", np.float64)
+        assert np.abs(fn - two_omega * L.xyz[M.node, 2]).max() < 1e-12 * two_omega
+
+
+def test_lifting_weights(dump, ora, maps):
+    """Predict weights s~_km = A_km / A_m of every odd fine node (Eq. 1) and update
+    weights s_km = A_km / A_k of every coarse node over M_k (Eq. 2)."""
+    for j in range(JMIN + 1, JMAX + 1):
+        C, Mc, Mf = ora.levels[j - 1], maps[j - 1], maps[j]
+        par = dump(f"L{j}_par", np.int32, (4, -1))
+        ptw = dump(f"L{j}_ptw", np.float64, (4, -1))
+        odd_lib = np.nonzero(par[0] >= 0)[0]
+        r = Mf.node[odd_lib] - C.N
+        K, st = ora.K[j][r], ora.Akm[j][r] / ora.Am[j][r][:, None]
+        lib_par = Mf.node[par[:, odd_lib].T]
+        o1, o2 = np.argsort(lib_par, axis=1), np.argsort(K, axis=1)
+        rows = np.arange(r.size)[:, None]
+        assert np.array_equal(lib_par[rows, o1], K[rows, o2])
+        assert np.abs(ptw[:, odd_lib].T[rows, o1] - st[rows, o2]).max() < geo_tol(j)
+        # update weights, coarse node by coarse node
+        want = {}
+        for rr in range(ora.K[j].shape[0]):
+            for col in range(ora.K[j].shape[1]):
+                k = int(ora.K[j][rr, col])
+                want.setdefault(k, {})[C.N + rr] = ora.Akm[j][rr, col] / C.A_i[k]
+        mk_i = dump(f"L{j - 1}_mk_i", np.int32, (12, -1))
+        mk_w = dump(f"L{j - 1}_mk_w", np.float64, (12, -1))
+        for kl in range(C.N):
+            got = {int(Mf.node[m]): w for m, w in zip(mk_i[:, kl], mk_w[:, kl]) if m >= 0}
+            ref = want[int(Mc.node[kl])]
+            assert got.keys() == ref.keys()
+            assert max(abs(got[m] - ref[m]) for m in ref) < geo_tol(j)
+
+
 def test_coriolis_weights(dump, ora, maps):
     rng = np.random.default_rng(0)
     for j in range(JMIN, JMAX + 1):
