@@ -47,6 +47,9 @@ def test_error_path_without_compute():
     lib.sww_last_error(buf, 256)
     assert b"null handle" in buf.value
     assert lib.sww_barrier_fault(None, 0, -1) == -1
+    # the live-node count reads host memory only; a null handle or output is refused
+    n = ctypes.c_int64(7)
+    assert lib.sww_live_nodes(None, ctypes.byref(n)) == -1 and n.value == 7
 
 
 def test_config_checks_without_compute():
